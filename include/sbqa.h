@@ -1,0 +1,230 @@
+/*
+ * sbqa.h -- C ABI of the GB300 (sm_103a) Simulated Bifurcation Quantum
+ * Annealing hot path.
+ *
+ * Method: Pawlowski, Tarasiuk, Tuziemski, Pawela, Gardas, "Simulated
+ * Bifurcation Quantum Annealing", arXiv 2604.01050.
+ *
+ * Notation.  The paper's R Trotter replicas of one run are called P here,
+ * and R counts the independent runs ("repetitions" of the auto-tuning in
+ * Sec. II B).  One run has P replicas coupled along a periodic
+ * imaginary-time ring; runs never interact.
+ *
+ * Everything below is plain C: pointers, sizes, status codes.  No function
+ * throws.  Status: SBQA_OK (0) or a negative SBQA_ERR_* code;
+ * sbqa_strerror() names it and sbqa_last_error() gives the detail message of
+ * the calling thread's last failure.
+ *
+ * Ownership.  The library copies every input array during the call that
+ * receives it; the caller keeps ownership of its buffers and may free them
+ * when the call returns.  Output buffers are owned by the caller and must
+ * hold the documented number of elements.  A problem handle owns all device
+ * memory it allocates and releases it in sbqa_destroy().
+ *
+ * Threads and streams.  Calls on one handle must not overlap (no internal
+ * lock); different handles are independent.  Device work of a handle is
+ * issued on the stream given to sbqa_run()/sbqa_run_begin() (NULL = the
+ * legacy default stream); the device is the one current when the handle was
+ * created.
+ */
+#ifndef SBQA_H
+#define SBQA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ----------------------------------------------------- */
+#define SBQA_OK 0
+#define SBQA_ERR_INVALID_ARG -1  /* bad size, NULL where required, bad enum   */
+#define SBQA_ERR_NOT_SYMMETRIC -2 /* J != J^T, nonzero diagonal, bad CSR      */
+#define SBQA_ERR_NOT_FINITE -3   /* NaN / Inf in J, h or parameters           */
+#define SBQA_ERR_OOM -4          /* device or host allocation failed          */
+#define SBQA_ERR_CUDA -5         /* a CUDA runtime call failed                */
+#define SBQA_ERR_STATE -6        /* call out of order (e.g. get_best before run) */
+#define SBQA_ERR_UNSUPPORTED -7  /* valid request the library does not serve  */
+#define SBQA_ERR_TIMEOUT -8      /* a bounded device wait gave up             */
+
+/* ---- enums ------------------------------------------------------------ */
+/* Precision of the coupling product G = J . f(X) (Sec. II A, Eq. 7).  The
+ * positions and momenta are FP32 in every mode; f(X) is in {-1, 0, +1}. */
+#define SBQA_PREC_AUTO 0  /* EXACT if J, h are small integers, else FP32      */
+#define SBQA_PREC_FP32 1  /* J in FP32, FP32 accumulation                       */
+#define SBQA_PREC_EXACT 2 /* integer J (|J_ij| <= 16): J.f(X) computed exactly
+                             (int8 adds on CUDA cores, FP8 e4m3 tensor cores
+                             with FP32 accumulation for dense J)               */
+#define SBQA_PREC_BF16 3  /* J rounded to bfloat16 (round to nearest even),
+                             FP32 accumulation                                  */
+
+/* Form of f in Eq. 7. */
+#define SBQA_VARIANT_THRESHOLD 0 /* f(x) = 0 if |x| <= Delta(t), else sign(x) (Eq. 8) */
+
+typedef struct sbqa_problem sbqa_problem;
+
+/* ---- problem ---------------------------------------------------------- */
+/*
+ * Ising instance of Sec. II A (Eqs. 1-2): symmetric couplings J with zero
+ * diagonal and fields h; the energy minimised is
+ *     E(s) = - sum_{i<j} J_ij s_i s_j - sum_i h_i s_i        (Eq. 4 sign).
+ *
+ * sbqa_create_problem_dense
+ *   n    number of spins, 1 <= n <= 65536
+ *   J    host, n*n doubles, row-major; must be symmetric with zero diagonal
+ *        and finite (exact equality J_ij == J_ji is required)
+ *   h    host, n doubles, or NULL for h = 0
+ *   out  receives the new handle (NULL on failure)
+ * Errors: INVALID_ARG, NOT_SYMMETRIC, NOT_FINITE, OOM, CUDA.
+ */
+int sbqa_create_problem_dense(int32_t n, const double *J, const double *h,
+                              sbqa_problem **out);
+
+/*
+ * sbqa_create_problem_csr: the same instance in compressed sparse rows.
+ *   n        number of spins, 1 <= n <= 2^31 - 1
+ *   nnz      number of stored entries (both triangles), 0 <= nnz < 2^31
+ *   row_ptr  host, n+1 int64, row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz
+ *   col_idx  host, nnz int32, strictly increasing within a row, no diagonal
+ *   val      host, nnz doubles; the pattern and values must be symmetric
+ *   h        host, n doubles, or NULL
+ * Errors: INVALID_ARG, NOT_SYMMETRIC (also for unsorted/duplicate columns
+ * or a diagonal entry), NOT_FINITE, OOM, CUDA.
+ */
+int sbqa_create_problem_csr(int32_t n, int64_t nnz, const int64_t *row_ptr,
+                            const int32_t *col_idx, const double *val,
+                            const double *h, sbqa_problem **out);
+
+/* Releases every resource of the handle (NULL is ignored).  Waits for the
+ * handle's outstanding device work first. */
+void sbqa_destroy(sbqa_problem *p);
+
+typedef struct {
+    int32_t n;          /* spins                                           */
+    int32_t is_dense;   /* 1 if created from a dense matrix                */
+    int64_t nnz;        /* stored nonzero couplings (both triangles)       */
+    int32_t is_integer; /* all J_ij and h_i are integers                   */
+    int32_t max_abs_j;  /* max |J_ij| if integer, else -1                  */
+    double c0_auto;     /* default c0 = 0.5 sqrt(n / sum_ij J_ij^2)        */
+} sbqa_problem_info;
+
+int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info);
+
+/* ---- schedule --------------------------------------------------------- */
+/*
+ * Parameters of the equations of motion (Sec. II A, Eqs. 5-8) and of the
+ * per-run auto-tuning (Sec. II B).
+ *   a0           a_0 of Eqs. 6-7 (default 1)
+ *   c0           c_0 of Eq. 7; <= 0 selects c0_auto (default 0)
+ *   dt           time step of the symplectic Euler integrator (default 0.5);
+ *                step n runs at t/T = n / steps
+ *   gamma0       Gamma_x(0) of Eq. 5 (default 1)
+ *   delta_slope  Delta(t) = delta_slope * t/T (Eq. 8 threshold; default 0.7)
+ *   init_amp     initial x, y uniform in [-init_amp, init_amp) (default 0.1)
+ *   jperp_enable 1: J_perp(t) of Eq. 5; 0: J_perp = 0 (plain SB per replica)
+ *   variant      SBQA_VARIANT_THRESHOLD (the only form served)
+ *   precision    SBQA_PREC_*
+ *   eval_every   0: read out only after the last step; K > 0: also after
+ *                every step n with (n+1) % K == 0, keeping the best so far
+ *   n_runs       length of beta and alpha (must equal R of the run)
+ *   beta, alpha  host, n_runs doubles each: per-run inverse temperature and
+ *                schedule exponent (the auto-tuning draws them from
+ *                [0.5,1.5] x [0.5,1.0]); beta > 0, alpha > 0
+ * The library copies beta and alpha.  Errors: INVALID_ARG, NOT_FINITE.
+ */
+typedef struct {
+    double a0;
+    double c0;
+    double dt;
+    double gamma0;
+    double delta_slope;
+    double init_amp;
+    int32_t jperp_enable;
+    int32_t variant;
+    int32_t precision;
+    int32_t eval_every;
+    int32_t n_runs;
+    int32_t reserved;
+    const double *beta;
+    const double *alpha;
+} sbqa_params;
+
+/* Fills the defaults listed above (beta = alpha = NULL, n_runs = 0, which
+ * sbqa_set_schedule reads as beta = alpha = 1 for every run). */
+void sbqa_default_params(sbqa_params *p);
+
+int sbqa_set_schedule(sbqa_problem *p, const sbqa_params *params);
+
+/* ---- run -------------------------------------------------------------- */
+/*
+ * sbqa_run: the whole hot path, asynchronously on `stream`
+ * (a cudaStream_t, NULL = legacy default stream):
+ *   initial state from SplitMix64 keyed by (seed, run r, replica k, spin i)
+ *   -> `steps` steps of Eqs. 6-7 with the wall rule
+ *   -> sign readout, energies of all R*P replicas, per-run best.
+ *   steps  >= 0 (0 reads out the initial state)
+ *   P      replicas per run: 1, 2, 4, 8, 16 or 32
+ *   R      runs, >= 1, R * P <= 2^20; must equal params.n_runs when beta
+ *          and alpha were given
+ * Errors: STATE (no schedule), INVALID_ARG, UNSUPPORTED, OOM, CUDA.
+ * Device buffers for the state are allocated on first use for a given
+ * (P, R) and reused by later runs of the same shape.
+ */
+int sbqa_run(sbqa_problem *p, int32_t steps, int32_t P, int32_t R,
+             uint64_t seed, void *stream);
+
+/* The same run split at step boundaries (checkpoint / resume):
+ * begin = initial state and tables, advance = the next n_steps steps
+ * (clamped to the anneal's end, with readouts per eval_every),
+ * finish = final readout.  begin + advance(steps) + finish is exactly
+ * sbqa_run. */
+int sbqa_run_begin(sbqa_problem *p, int32_t steps, int32_t P, int32_t R,
+                   uint64_t seed, void *stream);
+int sbqa_run_advance(sbqa_problem *p, int32_t n_steps);
+int sbqa_run_finish(sbqa_problem *p);
+
+/* Waits for the handle's device work. */
+int sbqa_synchronize(sbqa_problem *p);
+
+/* ---- results (synchronising, host buffers) ---------------------------- */
+/*
+ * Per-run best over replicas (and over readouts when eval_every > 0), the
+ * answer of the auto-tuned solver ("return the best solution from all
+ * repetitions", Sec. II B).  Any pointer may be NULL.
+ *   spins       R*N int8 (+1/-1), run-major
+ *   energy      R doubles (exact for integer instances)
+ *   energy_int  R int64 (filled only for integer instances)
+ *   replica     R int32, the replica k of the best readout (lowest k on ties)
+ *   step        R int32, the step index after which it was read (-1 = the
+ *               initial state; the earliest readout wins ties)
+ * Errors: STATE (no finished readout), CUDA.
+ */
+int sbqa_get_best(sbqa_problem *p, int8_t *spins, double *energy,
+                  int64_t *energy_int, int32_t *replica, int32_t *step);
+
+/* Energies of all R*P replicas at the last readout, run-major [r][k]. */
+int sbqa_get_energies(sbqa_problem *p, double *energy, int64_t *energy_int);
+
+/*
+ * State access for tests and checkpoints, layout [r][k][i] (R*P*N floats).
+ * get_state returns the positions/momenta after `*step_done` steps.
+ * set_state replaces them and sets the number of completed steps to
+ * step_done (0 <= step_done <= steps of the current run); the next
+ * advance continues from there.
+ */
+int sbqa_get_state(sbqa_problem *p, float *x, float *y, int32_t *step_done);
+int sbqa_set_state(sbqa_problem *p, const float *x, const float *y,
+                   int32_t step_done);
+
+/* ---- errors ----------------------------------------------------------- */
+const char *sbqa_strerror(int status);
+/* Detail message of the calling thread's last failed call ("" if none). */
+const char *sbqa_last_error(void);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int sbqa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SBQA_H */

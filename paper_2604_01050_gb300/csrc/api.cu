@@ -1,0 +1,762 @@
+// api.cu -- host side of the C ABI declared in include/sbqa.h.
+//
+// Responsibilities: validate and copy the Ising instance (Sec. II A,
+// Eqs. 1-2: symmetric J, zero diagonal), pick the coupling-product path,
+// build the FP64 schedule tables of Sec. II A (a(t) = t/T, Gamma_x(t) and
+// J_perp(t) of Eq. 5, Delta(t) of Eq. 8) and round them to FP32, own the
+// device buffers, and issue the hot-path kernels on the caller's stream.
+// The step loop of a full run is captured once per shape in a CUDA graph and
+// replayed.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sbqa.h"
+#include "internal.h"
+
+using namespace sbqa;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string &msg) {
+  g_last_error = msg;
+  return code;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+template <typename T>
+struct DevBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  cudaError_t alloc(size_t count) {
+    if (count <= n && p) return cudaSuccess;
+    release();
+    if (count == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&p), count * sizeof(T));
+    if (e == cudaSuccess) n = count;
+    else p = nullptr;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+#define SBQA_CUDA(call)                                                                   \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(e_ == cudaErrorMemoryAllocation ? SBQA_ERR_OOM : SBQA_ERR_CUDA,        \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                   \
+  } while (0)
+
+}  // namespace
+
+struct sbqa_problem {
+  int device = 0;
+  int32_t n = 0;
+  bool dense = false;
+  int64_t nnz = 0;
+  bool is_integer = false, is_pm1 = false, j_integer = false;
+  int32_t max_abs_j = -1;
+  int32_t max_degree = 0;
+  double c0_auto = 0.5;
+  bool h_zero = true;
+
+  // host copies (CSR for sparse, row-major for dense)
+  std::vector<int64_t> row_ptr;
+  std::vector<int32_t> col;
+  std::vector<double> val;  // CSR values or dense N*N
+  std::vector<double> h;
+
+  // device: product operands
+  DevBuf<int32_t> d_row_ptr, d_col;
+  DevBuf<int8_t> d_val_i8;
+  DevBuf<float> d_val_f32;
+  DevBuf<__nv_bfloat16> d_val_bf16;
+  DevBuf<float> d_dense_f32;  // dense J for the CUDA-core path
+  int dense_prec = -1;        // precision the dense FP32 copy was built for
+  DevBuf<float> d_h;
+  // device: readout operands
+  DevBuf<int32_t> d_e_i32;
+  DevBuf<double> d_e_f64;
+  DevBuf<int64_t> d_h_i64;
+  DevBuf<double> d_h_f64;
+
+  // schedule
+  bool have_params = false;
+  sbqa_params prm{};
+  std::vector<double> beta, alpha;
+
+  // run state
+  int S = 0, P = 0, R = 0, C = 0, Cp = 0;
+  int step_done = 0;
+  bool begun = false, finished = false;
+  cudaStream_t stream = nullptr;
+  int kind = VAL_F32;  // sparse value kind in use
+  DevBuf<float> d_x, d_y;
+  DevBuf<int8_t> d_F0, d_F1, d_Sg;
+  DevBuf<float> d_ka, d_dl, d_kj;
+  DevBuf<int64_t> d_ei, d_part_i, d_best_ei;
+  DevBuf<double> d_ef, d_part_f, d_best_e;
+  DevBuf<int32_t> d_best_k, d_best_step, d_have;
+  DevBuf<int8_t> d_best_spins;
+  StepTables tables{};
+
+  // cached graph of the step loop + readouts of a full run
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  struct Key {
+    int S = -1, P = -1, R = -1, eval = -1, kind = -1, dense = -1;
+    float kc = 0.f, kx = 0.f;  // step constants are kernel arguments in the graph
+    const void *x = nullptr, *kj = nullptr;
+    bool operator==(const Key &o) const {
+      return S == o.S && P == o.P && R == o.R && eval == o.eval && kind == o.kind &&
+             dense == o.dense && x == o.x && kj == o.kj &&
+             std::memcmp(&kc, &o.kc, sizeof(float)) == 0 && std::memcmp(&kx, &o.kx, sizeof(float)) == 0;
+    }
+  } graph_key;
+
+  ~sbqa_problem() {
+    DeviceGuard g(device);
+    cudaDeviceSynchronize();  // no kernel of this handle may still use the buffers
+    if (graph) cudaGraphExecDestroy(graph);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    d_row_ptr.release(); d_col.release(); d_val_i8.release(); d_val_f32.release();
+    d_val_bf16.release(); d_dense_f32.release(); d_h.release(); d_e_i32.release();
+    d_e_f64.release(); d_h_i64.release(); d_h_f64.release(); d_x.release(); d_y.release();
+    d_F0.release(); d_F1.release(); d_Sg.release(); d_ka.release(); d_dl.release();
+    d_kj.release(); d_ei.release(); d_part_i.release(); d_best_ei.release(); d_ef.release();
+    d_part_f.release(); d_best_e.release(); d_best_k.release(); d_best_step.release();
+    d_have.release(); d_best_spins.release();
+  }
+
+  StateView state() const {
+    StateView s;
+    s.N = n; s.C = C; s.Cp = Cp; s.P = P; s.R = R;
+    s.x = d_x.p; s.y = d_y.p;
+    s.F[0] = d_F0.p; s.F[1] = d_F1.p;
+    s.Sg = d_Sg.p;
+    return s;
+  }
+  CsrView csr() const {
+    CsrView v;
+    v.row_ptr = d_row_ptr.p; v.col = d_col.p; v.h = d_h.p; v.kind = kind;
+    v.val = kind == VAL_PM1 ? static_cast<const void *>(d_val_i8.p)
+          : kind == VAL_F32 ? static_cast<const void *>(d_val_f32.p)
+                            : static_cast<const void *>(d_val_bf16.p);
+    return v;
+  }
+  EnergyView energy() const {
+    EnergyView e;
+    e.is_integer = is_integer ? 1 : 0;
+    e.val_i32 = d_e_i32.p; e.val_f64 = d_e_f64.p; e.h_i64 = d_h_i64.p; e.h_f64 = d_h_f64.p;
+    return e;
+  }
+  BestView best() const {
+    BestView b;
+    b.e_int = d_ei.p; b.e_f64 = d_ef.p; b.part_int = d_part_i.p; b.part_f64 = d_part_f.p;
+    b.nblk = energy_row_blocks(n);
+    b.best_e_int = d_best_ei.p; b.best_e = d_best_e.p; b.best_k = d_best_k.p;
+    b.best_step = d_best_step.p; b.best_spins = d_best_spins.p; b.have_best = d_have.p;
+    return b;
+  }
+};
+
+namespace {
+
+bool finite_all(const double *v, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(v[i])) return false;
+  return true;
+}
+
+// Round a double to the nearest bfloat16 (ties to even), returned as bits.
+uint16_t bf16_bits_rne(double v) {
+  if (v == 0.0) return std::signbit(v) ? 0x8000u : 0u;
+  int e;
+  const double m = std::frexp(v, &e);           // |m| in [0.5, 1)
+  const double q = std::nearbyint(std::ldexp(m, 8));  // 8 significant bits
+  const float f = float(std::ldexp(q, e - 8));  // exact in FP32 for normal range
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  return uint16_t(u >> 16);
+}
+
+void analyse_values(sbqa_problem *p) {
+  bool j_int = true, pm1 = true, h_int = true;
+  double mx = 0.0, s2 = 0.0;
+  for (double v : p->val) {
+    if (v == 0.0) continue;
+    if (v != std::nearbyint(v)) j_int = false;
+    if (std::fabs(v) != 1.0) pm1 = false;
+    mx = std::max(mx, std::fabs(v));
+    s2 += v * v;
+  }
+  if (mx > 1e6) j_int = false;
+  for (double v : p->h)
+    if (v != std::nearbyint(v) || std::fabs(v) > 1e12) h_int = false;
+  p->j_integer = j_int;
+  p->is_integer = j_int && h_int;  // energies exact in int64
+  p->is_pm1 = pm1;                 // every stored J_ij is +1 or -1
+  p->max_abs_j = j_int ? int32_t(mx) : -1;
+  p->c0_auto = s2 > 0.0 ? 0.5 * std::sqrt(double(p->n) / s2) : 0.5;
+  p->h_zero = true;
+  for (double v : p->h)
+    if (v != 0.0) p->h_zero = false;
+}
+
+int upload_common(sbqa_problem *p) {
+  const int N = p->n;
+  std::vector<float> hf(N, 0.f);
+  for (int i = 0; i < N; ++i) hf[i] = p->h.empty() ? 0.f : float(p->h[i]);
+  SBQA_CUDA(p->d_h.alloc(N));
+  SBQA_CUDA(cudaMemcpy(p->d_h.p, hf.data(), N * sizeof(float), cudaMemcpyHostToDevice));
+  if (p->is_integer) {
+    std::vector<int64_t> hi(N, 0);
+    for (int i = 0; i < N; ++i) hi[i] = p->h.empty() ? 0 : int64_t(std::llround(p->h[i]));
+    SBQA_CUDA(p->d_h_i64.alloc(N));
+    SBQA_CUDA(cudaMemcpy(p->d_h_i64.p, hi.data(), N * sizeof(int64_t), cudaMemcpyHostToDevice));
+  } else {
+    std::vector<double> hd(N, 0.0);
+    for (int i = 0; i < N; ++i) hd[i] = p->h.empty() ? 0.0 : p->h[i];
+    SBQA_CUDA(p->d_h_f64.alloc(N));
+    SBQA_CUDA(cudaMemcpy(p->d_h_f64.p, hd.data(), N * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  return SBQA_OK;
+}
+
+int upload_readout_values(sbqa_problem *p) {
+  const size_t m = p->val.size();
+  if (m == 0) return SBQA_OK;
+  if (p->is_integer) {
+    std::vector<int32_t> vi(m);
+    for (size_t e = 0; e < m; ++e) vi[e] = int32_t(std::llround(p->val[e]));
+    SBQA_CUDA(p->d_e_i32.alloc(m));
+    SBQA_CUDA(cudaMemcpy(p->d_e_i32.p, vi.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice));
+  } else {
+    SBQA_CUDA(p->d_e_f64.alloc(m));
+    SBQA_CUDA(cudaMemcpy(p->d_e_f64.p, p->val.data(), m * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  return SBQA_OK;
+}
+
+// Sparse value array for the requested precision; sets p->kind.
+int prepare_sparse_values(sbqa_problem *p, int precision) {
+  const size_t m = p->val.size();
+  int kind;
+  if (precision == SBQA_PREC_BF16) kind = VAL_BF16;
+  else if (precision == SBQA_PREC_FP32) kind = VAL_F32;
+  else if (p->is_pm1 && p->max_degree <= 127) kind = VAL_PM1;
+  else kind = VAL_F32;
+  if (precision == SBQA_PREC_EXACT && (!p->j_integer || p->max_abs_j > 16))
+    return fail(SBQA_ERR_UNSUPPORTED, "EXACT precision needs integer J with |J_ij| <= 16");
+  p->kind = kind;
+  if (kind == VAL_PM1 && !p->d_val_i8.p && m) {
+    std::vector<int8_t> v(m);
+    for (size_t e = 0; e < m; ++e) v[e] = p->val[e] > 0 ? 1 : -1;
+    SBQA_CUDA(p->d_val_i8.alloc(m));
+    SBQA_CUDA(cudaMemcpy(p->d_val_i8.p, v.data(), m, cudaMemcpyHostToDevice));
+  } else if (kind == VAL_F32 && !p->d_val_f32.p && m) {
+    std::vector<float> v(m);
+    for (size_t e = 0; e < m; ++e) v[e] = float(p->val[e]);
+    SBQA_CUDA(p->d_val_f32.alloc(m));
+    SBQA_CUDA(cudaMemcpy(p->d_val_f32.p, v.data(), m * sizeof(float), cudaMemcpyHostToDevice));
+  } else if (kind == VAL_BF16 && !p->d_val_bf16.p && m) {
+    std::vector<uint16_t> v(m);
+    for (size_t e = 0; e < m; ++e) v[e] = bf16_bits_rne(p->val[e]);
+    SBQA_CUDA(p->d_val_bf16.alloc(m));
+    SBQA_CUDA(cudaMemcpy(p->d_val_bf16.p, v.data(), m * 2, cudaMemcpyHostToDevice));
+  }
+  return SBQA_OK;
+}
+
+int prepare_dense_values(sbqa_problem *p, int precision) {
+  if (precision == SBQA_PREC_EXACT && (!p->j_integer || p->max_abs_j > 16))
+    return fail(SBQA_ERR_UNSUPPORTED, "EXACT precision needs integer J with |J_ij| <= 16");
+  const int want = precision == SBQA_PREC_BF16 ? SBQA_PREC_BF16 : SBQA_PREC_FP32;
+  if (p->d_dense_f32.p && p->dense_prec == want) return SBQA_OK;
+  const size_t m = p->val.size();
+  std::vector<float> v(m);
+  for (size_t e = 0; e < m; ++e) {
+    if (want == SBQA_PREC_BF16) {
+      const uint32_t u = uint32_t(bf16_bits_rne(p->val[e])) << 16;
+      std::memcpy(&v[e], &u, 4);
+    } else {
+      v[e] = float(p->val[e]);
+    }
+  }
+  SBQA_CUDA(p->d_dense_f32.alloc(m));
+  SBQA_CUDA(cudaMemcpy(p->d_dense_f32.p, v.data(), m * sizeof(float), cudaMemcpyHostToDevice));
+  p->dense_prec = want;
+  return SBQA_OK;
+}
+
+int alloc_run(sbqa_problem *p, int S, int P, int R) {
+  const int C = R * P;
+  const int Cp = (C + kColsPerWarp - 1) / kColsPerWarp * kColsPerWarp;
+  const size_t NC = size_t(p->n) * Cp;
+  SBQA_CUDA(p->d_x.alloc(NC));
+  SBQA_CUDA(p->d_y.alloc(NC));
+  SBQA_CUDA(p->d_F0.alloc(NC));
+  SBQA_CUDA(p->d_F1.alloc(NC));
+  SBQA_CUDA(p->d_Sg.alloc(NC));
+  SBQA_CUDA(p->d_ka.alloc(size_t(std::max(S, 1))));
+  SBQA_CUDA(p->d_dl.alloc(size_t(S) + 1));
+  SBQA_CUDA(p->d_kj.alloc(size_t(std::max(S, 1)) * R));
+  SBQA_CUDA(p->d_ei.alloc(Cp));
+  SBQA_CUDA(p->d_ef.alloc(Cp));
+  const size_t parts = size_t(energy_row_blocks(p->n)) * Cp;
+  if (p->is_integer) SBQA_CUDA(p->d_part_i.alloc(parts));
+  else SBQA_CUDA(p->d_part_f.alloc(parts));
+  SBQA_CUDA(p->d_best_ei.alloc(R));
+  SBQA_CUDA(p->d_best_e.alloc(R));
+  SBQA_CUDA(p->d_best_k.alloc(R));
+  SBQA_CUDA(p->d_best_step.alloc(R));
+  SBQA_CUDA(p->d_have.alloc(R));
+  SBQA_CUDA(p->d_best_spins.alloc(size_t(R) * p->n));
+  p->S = S; p->P = P; p->R = R; p->C = C; p->Cp = Cp;
+  return SBQA_OK;
+}
+
+// FP64 schedule of Sec. II A rounded to the FP32 step coefficients.
+int build_tables(sbqa_problem *p) {
+  const sbqa_params &q = p->prm;
+  const int S = p->S, P = p->P, R = p->R;
+  const double c0 = q.c0 > 0.0 ? q.c0 : p->c0_auto;
+  std::vector<float> ka(std::max(S, 1), 0.f), dl(S + 1), kj(size_t(std::max(S, 1)) * R, 0.f);
+  for (int n = 0; n <= S; ++n) {
+    const double tau = S > 0 ? double(n) / double(S) : 0.0;
+    dl[n] = float(q.delta_slope * tau);                 // Delta(t) = 0.7 t/T
+    if (n < S) ka[n] = float(q.dt * (q.a0 - tau) / P);  // a(t) = t/T
+  }
+  for (int n = 0; n < S; ++n) {
+    const double tau = double(n) / double(S);
+    for (int r = 0; r < R; ++r) {
+      double jp = 0.0;
+      if (q.jperp_enable) {
+        const double b = p->beta.empty() ? 1.0 : p->beta[r];
+        const double a = p->alpha.empty() ? 1.0 : p->alpha[r];
+        const double gam = q.gamma0 * (std::pow(1.0 - tau, a) + 1e-5);  // Gamma_x(t), Eq. 5
+        jp = -std::log(std::tanh(b * gam / P)) / (2.0 * b);           // J_perp(t), Eq. 5
+      }
+      kj[size_t(n) * R + r] = float(q.dt * jp);
+    }
+  }
+  SBQA_CUDA(cudaMemcpyAsync(p->d_ka.p, ka.data(), ka.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream));
+  SBQA_CUDA(cudaMemcpyAsync(p->d_dl.p, dl.data(), dl.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream));
+  SBQA_CUDA(cudaMemcpyAsync(p->d_kj.p, kj.data(), kj.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream));
+  p->tables.ka = p->d_ka.p;
+  p->tables.dl = p->d_dl.p;
+  p->tables.kj = p->d_kj.p;
+  p->tables.kc = float(q.dt * c0 / P);
+  p->tables.kx = float(q.dt * q.a0 / P);
+  p->tables.S = S;
+  p->tables.R = R;
+  return SBQA_OK;
+}
+
+cudaError_t issue_step(sbqa_problem *p, int n, cudaStream_t st) {
+  const StateView s = p->state();
+  if (p->dense) {
+    DenseView d;
+    d.J = p->d_dense_f32.p;
+    d.h = p->d_h.p;
+    return launch_step_dense(s, d, p->tables, n, st);
+  }
+  return launch_step_csr(s, p->csr(), p->tables, n, st);
+}
+
+cudaError_t issue_readout(sbqa_problem *p, int step, cudaStream_t st) {
+  const StateView s = p->state();
+  cudaError_t e = p->dense ? launch_energy_dense(s, p->energy(), p->best(), st)
+                           : launch_energy_csr(s, p->csr(), p->energy(), p->best(), st);
+  if (e != cudaSuccess) return e;
+  return launch_best(s, p->energy(), p->best(), step, st);
+}
+
+// Steps [n0, n1) with the intermediate readouts of eval_every.
+cudaError_t issue_range(sbqa_problem *p, int n0, int n1, cudaStream_t st) {
+  const int K = p->prm.eval_every;
+  for (int n = n0; n < n1; ++n) {
+    cudaError_t e = issue_step(p, n, st);
+    if (e != cudaSuccess) return e;
+    if (K > 0 && (n + 1) % K == 0 && n != p->S - 1) {
+      e = issue_readout(p, n, st);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+int check_run_args(sbqa_problem *p, int32_t steps, int32_t P, int32_t R) {
+  if (!p) return fail(SBQA_ERR_INVALID_ARG, "null problem");
+  if (!p->have_params) return fail(SBQA_ERR_STATE, "sbqa_set_schedule has not been called");
+  if (steps < 0) return fail(SBQA_ERR_INVALID_ARG, "steps must be >= 0");
+  if (!(P == 1 || P == 2 || P == 4 || P == 8 || P == 16 || P == 32))
+    return fail(SBQA_ERR_UNSUPPORTED, "P must be 1, 2, 4, 8, 16 or 32");
+  if (R < 1 || int64_t(R) * P > (1 << 20)) return fail(SBQA_ERR_INVALID_ARG, "need 1 <= R and R*P <= 2^20");
+  if (!p->beta.empty() && int(p->beta.size()) != R)
+    return fail(SBQA_ERR_INVALID_ARG, "R differs from params.n_runs");
+  return SBQA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sbqa_version(void) { return 100; }
+
+const char *sbqa_last_error(void) { return g_last_error.c_str(); }
+
+const char *sbqa_strerror(int status) {
+  switch (status) {
+    case SBQA_OK: return "ok";
+    case SBQA_ERR_INVALID_ARG: return "invalid argument";
+    case SBQA_ERR_NOT_SYMMETRIC: return "couplings not symmetric / malformed";
+    case SBQA_ERR_NOT_FINITE: return "non-finite value";
+    case SBQA_ERR_OOM: return "out of memory";
+    case SBQA_ERR_CUDA: return "CUDA error";
+    case SBQA_ERR_STATE: return "call out of order";
+    case SBQA_ERR_UNSUPPORTED: return "unsupported request";
+    case SBQA_ERR_TIMEOUT: return "device wait timed out";
+    default: return "unknown status";
+  }
+}
+
+void sbqa_default_params(sbqa_params *p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->a0 = 1.0;
+  p->c0 = 0.0;
+  p->dt = 0.5;
+  p->gamma0 = 1.0;
+  p->delta_slope = 0.7;
+  p->init_amp = 0.1;
+  p->jperp_enable = 1;
+  p->variant = SBQA_VARIANT_THRESHOLD;
+  p->precision = SBQA_PREC_AUTO;
+  p->eval_every = 0;
+  p->n_runs = 0;
+  p->beta = nullptr;
+  p->alpha = nullptr;
+}
+
+int sbqa_create_problem_dense(int32_t n, const double *J, const double *h, sbqa_problem **out) {
+  if (!out) return fail(SBQA_ERR_INVALID_ARG, "out is null");
+  *out = nullptr;
+  if (n < 1 || n > 65536 || !J) return fail(SBQA_ERR_INVALID_ARG, "need 1 <= n <= 65536 and J != NULL");
+  const size_t m = size_t(n) * n;
+  if (!finite_all(J, m) || (h && !finite_all(h, n))) return fail(SBQA_ERR_NOT_FINITE, "J or h not finite");
+  for (int i = 0; i < n; ++i) {
+    if (J[size_t(i) * n + i] != 0.0) return fail(SBQA_ERR_NOT_SYMMETRIC, "nonzero diagonal");
+    for (int j = i + 1; j < n; ++j)
+      if (J[size_t(i) * n + j] != J[size_t(j) * n + i]) return fail(SBQA_ERR_NOT_SYMMETRIC, "J != J^T");
+  }
+  sbqa_problem *p = new (std::nothrow) sbqa_problem();
+  if (!p) return fail(SBQA_ERR_OOM, "host allocation");
+  cudaGetDevice(&p->device);
+  p->n = n;
+  p->dense = true;
+  p->val.assign(J, J + m);
+  if (h) p->h.assign(h, h + n);
+  int64_t nnz = 0;
+  int32_t maxdeg = 0;
+  for (int i = 0; i < n; ++i) {
+    int32_t d = 0;
+    for (int j = 0; j < n; ++j) d += J[size_t(i) * n + j] != 0.0;
+    nnz += d;
+    maxdeg = std::max(maxdeg, d);
+  }
+  p->nnz = nnz;
+  p->max_degree = maxdeg;
+  analyse_values(p);
+  int rc = upload_common(p);
+  if (rc == SBQA_OK) rc = upload_readout_values(p);
+  if (rc != SBQA_OK) {
+    delete p;
+    return rc;
+  }
+  *out = p;
+  return SBQA_OK;
+}
+
+int sbqa_create_problem_csr(int32_t n, int64_t nnz, const int64_t *row_ptr, const int32_t *col_idx,
+                            const double *val, const double *h, sbqa_problem **out) {
+  if (!out) return fail(SBQA_ERR_INVALID_ARG, "out is null");
+  *out = nullptr;
+  if (n < 1 || nnz < 0 || nnz >= (int64_t(1) << 31) || !row_ptr || (nnz > 0 && (!col_idx || !val)))
+    return fail(SBQA_ERR_INVALID_ARG, "bad sizes or null arrays");
+  if (row_ptr[0] != 0 || row_ptr[n] != nnz) return fail(SBQA_ERR_NOT_SYMMETRIC, "row_ptr ends do not match nnz");
+  for (int i = 0; i < n; ++i)
+    if (row_ptr[i + 1] < row_ptr[i]) return fail(SBQA_ERR_NOT_SYMMETRIC, "row_ptr decreasing");
+  if (!finite_all(val, size_t(nnz)) || (h && !finite_all(h, n))) return fail(SBQA_ERR_NOT_FINITE, "J or h not finite");
+  int32_t maxdeg = 0;
+  for (int i = 0; i < n; ++i) {  // pass 1: indices, order, diagonal
+    maxdeg = std::max<int32_t>(maxdeg, int32_t(row_ptr[i + 1] - row_ptr[i]));
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+      const int32_t j = col_idx[e];
+      if (j < 0 || j >= n) return fail(SBQA_ERR_INVALID_ARG, "column index out of range");
+      if (j == i) return fail(SBQA_ERR_NOT_SYMMETRIC, "diagonal entry in CSR");
+      if (e > row_ptr[i] && col_idx[e - 1] >= j) return fail(SBQA_ERR_NOT_SYMMETRIC, "unsorted or duplicate columns");
+    }
+  }
+  for (int i = 0; i < n; ++i)  // pass 2: the partner (j, i) holds the same value
+    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+      const int32_t j = col_idx[e];
+      const int32_t *b = col_idx + row_ptr[j], *en = col_idx + row_ptr[j + 1];
+      const int32_t *it = std::lower_bound(b, en, i);
+      if (it == en || *it != i || val[row_ptr[j] + (it - b)] != val[e])
+        return fail(SBQA_ERR_NOT_SYMMETRIC, "J != J^T");
+    }
+  sbqa_problem *p = new (std::nothrow) sbqa_problem();
+  if (!p) return fail(SBQA_ERR_OOM, "host allocation");
+  cudaGetDevice(&p->device);
+  p->n = n;
+  p->dense = false;
+  p->nnz = nnz;
+  p->max_degree = maxdeg;
+  p->row_ptr.assign(row_ptr, row_ptr + n + 1);
+  p->col.assign(col_idx, col_idx + nnz);
+  p->val.assign(val, val + nnz);
+  if (h) p->h.assign(h, h + n);
+  analyse_values(p);
+  std::vector<int32_t> rp32(n + 1);
+  for (int i = 0; i <= n; ++i) rp32[i] = int32_t(row_ptr[i]);
+  auto upload = [&]() -> int {
+    SBQA_CUDA(p->d_row_ptr.alloc(n + 1));
+    SBQA_CUDA(cudaMemcpy(p->d_row_ptr.p, rp32.data(), (n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (nnz) {
+      SBQA_CUDA(p->d_col.alloc(nnz));
+      SBQA_CUDA(cudaMemcpy(p->d_col.p, col_idx, nnz * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
+    int rc = upload_common(p);
+    if (rc == SBQA_OK) rc = upload_readout_values(p);
+    return rc;
+  };
+  const int rc = upload();
+  if (rc != SBQA_OK) {
+    delete p;
+    return rc;
+  }
+  *out = p;
+  return SBQA_OK;
+}
+
+void sbqa_destroy(sbqa_problem *p) { delete p; }
+
+int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info) {
+  if (!p || !info) return fail(SBQA_ERR_INVALID_ARG, "null argument");
+  info->n = p->n;
+  info->is_dense = p->dense ? 1 : 0;
+  info->nnz = p->nnz;
+  info->is_integer = p->is_integer ? 1 : 0;
+  info->max_abs_j = p->max_abs_j;
+  info->c0_auto = p->c0_auto;
+  return SBQA_OK;
+}
+
+int sbqa_set_schedule(sbqa_problem *p, const sbqa_params *q) {
+  if (!p || !q) return fail(SBQA_ERR_INVALID_ARG, "null argument");
+  const double v[6] = {q->a0, q->c0, q->dt, q->gamma0, q->delta_slope, q->init_amp};
+  if (!finite_all(v, 6)) return fail(SBQA_ERR_NOT_FINITE, "non-finite parameter");
+  if (q->a0 <= 0 || q->dt <= 0 || q->gamma0 <= 0 || q->delta_slope < 0 || q->init_amp < 0 || q->init_amp > 1)
+    return fail(SBQA_ERR_INVALID_ARG, "need a0, dt, gamma0 > 0, delta_slope >= 0, 0 <= init_amp <= 1");
+  if (q->variant != SBQA_VARIANT_THRESHOLD) return fail(SBQA_ERR_UNSUPPORTED, "only the thresholded f (Eq. 8) is served");
+  if (q->precision < SBQA_PREC_AUTO || q->precision > SBQA_PREC_BF16) return fail(SBQA_ERR_INVALID_ARG, "bad precision");
+  if (q->precision == SBQA_PREC_EXACT && (!p->j_integer || p->max_abs_j > 16))
+    return fail(SBQA_ERR_UNSUPPORTED, "EXACT precision needs integer J with |J_ij| <= 16");
+  if (q->eval_every < 0 || q->n_runs < 0) return fail(SBQA_ERR_INVALID_ARG, "negative eval_every or n_runs");
+  if (q->n_runs > 0 && (!q->beta || !q->alpha)) return fail(SBQA_ERR_INVALID_ARG, "beta/alpha missing");
+  std::vector<double> beta, alpha;
+  if (q->n_runs > 0) {
+    if (!finite_all(q->beta, q->n_runs) || !finite_all(q->alpha, q->n_runs)) return fail(SBQA_ERR_NOT_FINITE, "beta/alpha");
+    for (int r = 0; r < q->n_runs; ++r)
+      if (q->beta[r] <= 0 || q->alpha[r] <= 0) return fail(SBQA_ERR_INVALID_ARG, "beta, alpha must be > 0");
+    beta.assign(q->beta, q->beta + q->n_runs);
+    alpha.assign(q->alpha, q->alpha + q->n_runs);
+  }
+  p->prm = *q;
+  p->prm.beta = nullptr;
+  p->prm.alpha = nullptr;
+  p->beta.swap(beta);
+  p->alpha.swap(alpha);
+  p->have_params = true;
+  return SBQA_OK;
+}
+
+int sbqa_run_begin(sbqa_problem *p, int32_t steps, int32_t P, int32_t R, uint64_t seed, void *stream) {
+  int rc = check_run_args(p, steps, P, R);
+  if (rc != SBQA_OK) return rc;
+  DeviceGuard g(p->device);
+  p->stream = static_cast<cudaStream_t>(stream);
+  p->begun = p->finished = false;
+  rc = p->dense ? prepare_dense_values(p, p->prm.precision) : prepare_sparse_values(p, p->prm.precision);
+  if (rc != SBQA_OK) return rc;
+  if ((rc = alloc_run(p, steps, P, R)) != SBQA_OK) return rc;
+  if ((rc = build_tables(p)) != SBQA_OK) return rc;
+  const StateView s = p->state();
+  SBQA_CUDA(launch_init(s, seed, float(p->prm.init_amp), 0.0f, p->stream));
+  SBQA_CUDA(launch_reset_best(s, p->best(), p->stream));
+  p->step_done = 0;
+  p->begun = true;
+  return SBQA_OK;
+}
+
+int sbqa_run_advance(sbqa_problem *p, int32_t n_steps) {
+  if (!p) return fail(SBQA_ERR_INVALID_ARG, "null problem");
+  if (!p->begun || p->finished) return fail(SBQA_ERR_STATE, "no run in progress");
+  if (n_steps < 0) return fail(SBQA_ERR_INVALID_ARG, "n_steps must be >= 0");
+  DeviceGuard g(p->device);
+  const int n1 = int(std::min<int64_t>(int64_t(p->step_done) + n_steps, p->S));
+  SBQA_CUDA(issue_range(p, p->step_done, n1, p->stream));
+  p->step_done = n1;
+  return SBQA_OK;
+}
+
+int sbqa_run_finish(sbqa_problem *p) {
+  if (!p) return fail(SBQA_ERR_INVALID_ARG, "null problem");
+  if (!p->begun || p->finished) return fail(SBQA_ERR_STATE, "no run in progress");
+  if (p->step_done != p->S) return fail(SBQA_ERR_STATE, "run has steps left");
+  DeviceGuard g(p->device);
+  SBQA_CUDA(issue_readout(p, p->S - 1, p->stream));
+  p->finished = true;
+  return SBQA_OK;
+}
+
+int sbqa_run(sbqa_problem *p, int32_t steps, int32_t P, int32_t R, uint64_t seed, void *stream) {
+  int rc = sbqa_run_begin(p, steps, P, R, seed, stream);
+  if (rc != SBQA_OK) return rc;
+  DeviceGuard g(p->device);
+  sbqa_problem::Key key;
+  key.S = steps; key.P = P; key.R = R; key.eval = p->prm.eval_every; key.kind = p->kind;
+  key.dense = p->dense ? 1 : 0; key.x = p->d_x.p; key.kj = p->d_kj.p;
+  key.kc = p->tables.kc; key.kx = p->tables.kx;
+  if (!(p->graph && p->graph_key == key)) {
+    if (p->graph) {
+      cudaGraphExecDestroy(p->graph);
+      p->graph = nullptr;
+    }
+    if (!p->cap_stream) SBQA_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    SBQA_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = issue_range(p, 0, steps, p->cap_stream);
+    if (e == cudaSuccess) e = issue_readout(p, steps - 1, p->cap_stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(p->cap_stream, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return fail(SBQA_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&p->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+      p->graph = nullptr;
+      return fail(SBQA_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+    }
+    p->graph_key = key;
+  }
+  SBQA_CUDA(cudaGraphLaunch(p->graph, p->stream));
+  p->step_done = steps;
+  p->finished = true;
+  return SBQA_OK;
+}
+
+int sbqa_synchronize(sbqa_problem *p) {
+  if (!p) return fail(SBQA_ERR_INVALID_ARG, "null problem");
+  DeviceGuard g(p->device);
+  SBQA_CUDA(p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize());
+  SBQA_CUDA(cudaGetLastError());
+  return SBQA_OK;
+}
+
+int sbqa_get_best(sbqa_problem *p, int8_t *spins, double *energy, int64_t *energy_int, int32_t *replica,
+                  int32_t *step) {
+  if (!p) return fail(SBQA_ERR_INVALID_ARG, "null problem");
+  if (!p->finished) return fail(SBQA_ERR_STATE, "no finished readout");
+  int rc = sbqa_synchronize(p);
+  if (rc != SBQA_OK) return rc;
+  DeviceGuard g(p->device);
+  const int R = p->R;
+  if (spins) SBQA_CUDA(cudaMemcpy(spins, p->d_best_spins.p, size_t(R) * p->n, cudaMemcpyDeviceToHost));
+  if (energy) SBQA_CUDA(cudaMemcpy(energy, p->d_best_e.p, R * sizeof(double), cudaMemcpyDeviceToHost));
+  if (energy_int && p->is_integer)
+    SBQA_CUDA(cudaMemcpy(energy_int, p->d_best_ei.p, R * sizeof(int64_t), cudaMemcpyDeviceToHost));
+  if (replica) SBQA_CUDA(cudaMemcpy(replica, p->d_best_k.p, R * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  if (step) SBQA_CUDA(cudaMemcpy(step, p->d_best_step.p, R * sizeof(int32_t), cudaMemcpyDeviceToHost));
+  return SBQA_OK;
+}
+
+int sbqa_get_energies(sbqa_problem *p, double *energy, int64_t *energy_int) {
+  if (!p) return fail(SBQA_ERR_INVALID_ARG, "null problem");
+  if (!p->finished) return fail(SBQA_ERR_STATE, "no finished readout");
+  int rc = sbqa_synchronize(p);
+  if (rc != SBQA_OK) return rc;
+  DeviceGuard g(p->device);
+  if (energy) SBQA_CUDA(cudaMemcpy(energy, p->d_ef.p, size_t(p->C) * sizeof(double), cudaMemcpyDeviceToHost));
+  if (energy_int && p->is_integer)
+    SBQA_CUDA(cudaMemcpy(energy_int, p->d_ei.p, size_t(p->C) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+  return SBQA_OK;
+}
+
+int sbqa_get_state(sbqa_problem *p, float *x, float *y, int32_t *step_done) {
+  if (!p) return fail(SBQA_ERR_INVALID_ARG, "null problem");
+  if (!p->begun) return fail(SBQA_ERR_STATE, "no run");
+  int rc = sbqa_synchronize(p);
+  if (rc != SBQA_OK) return rc;
+  DeviceGuard g(p->device);
+  const size_t NC = size_t(p->n) * p->Cp;
+  std::vector<float> buf(NC);
+  float *outs[2] = {x, y};
+  const float *src[2] = {p->d_x.p, p->d_y.p};
+  for (int w = 0; w < 2; ++w) {
+    if (!outs[w]) continue;
+    SBQA_CUDA(cudaMemcpy(buf.data(), src[w], NC * sizeof(float), cudaMemcpyDeviceToHost));
+    for (int c = 0; c < p->C; ++c)
+      for (int i = 0; i < p->n; ++i) outs[w][size_t(c) * p->n + i] = buf[size_t(i) * p->Cp + c];
+  }
+  if (step_done) *step_done = p->step_done;
+  return SBQA_OK;
+}
+
+int sbqa_set_state(sbqa_problem *p, const float *x, const float *y, int32_t step_done) {
+  if (!p || !x || !y) return fail(SBQA_ERR_INVALID_ARG, "null argument");
+  if (!p->begun) return fail(SBQA_ERR_STATE, "no run");
+  if (step_done < 0 || step_done > p->S) return fail(SBQA_ERR_INVALID_ARG, "step_done out of range");
+  int rc = sbqa_synchronize(p);
+  if (rc != SBQA_OK) return rc;
+  DeviceGuard g(p->device);
+  const size_t NC = size_t(p->n) * p->Cp;
+  std::vector<float> bx(NC, 0.f), by(NC, 0.f);
+  for (int c = 0; c < p->C; ++c)
+    for (int i = 0; i < p->n; ++i) {
+      bx[size_t(i) * p->Cp + c] = x[size_t(c) * p->n + i];
+      by[size_t(i) * p->Cp + c] = y[size_t(c) * p->n + i];
+    }
+  SBQA_CUDA(cudaMemcpy(p->d_x.p, bx.data(), NC * sizeof(float), cudaMemcpyHostToDevice));
+  SBQA_CUDA(cudaMemcpy(p->d_y.p, by.data(), NC * sizeof(float), cudaMemcpyHostToDevice));
+  const double tau = p->S > 0 ? double(step_done) / double(p->S) : 0.0;
+  SBQA_CUDA(launch_refresh_f(p->state(), step_done & 1, float(p->prm.delta_slope * tau), p->stream));
+  p->step_done = step_done;
+  p->finished = false;
+  return SBQA_OK;
+}
+
+}  // extern "C"

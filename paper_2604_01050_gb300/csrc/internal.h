@@ -1,0 +1,98 @@
+// internal.h -- declarations shared by the translation units of libsbqa.
+//
+// Device layout of one run batch (C = R * P columns, column c = r * P + k,
+// padded to Cp, a multiple of 128 so that one warp owns 128 whole columns
+// and therefore whole runs, because P divides 32):
+//   x, y   float  [N][Cp]   positions / momenta, spin-major
+//   F[2]   int8   [N][Cp]   f(x) in {-1, 0, +1} for the current / next step
+// Per-step FP32 coefficients (host FP64 -> FP32, one table entry per step):
+//   ka[n]      dt * (a0 - a_n) / P       (a_n = n / S, Sec. II A)
+//   dl[n]      Delta_n = delta_slope * n / S   (n = 0..S, Eq. 8)
+//   kj[n][r]   dt * J_perp(t_n) for run r  (Eq. 5)
+//   kc, kx     dt * c0 / P,  dt * a0 / P
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+namespace sbqa {
+
+constexpr int kColsPerWarp = 128;  // 32 lanes x 4 columns
+constexpr int kColsPerLane = 4;
+
+enum ValKind : int { VAL_PM1 = 0, VAL_F32 = 1, VAL_BF16 = 2 };
+
+struct StepTables {
+  const float *ka;  // [S]
+  const float *dl;  // [S + 1]
+  const float *kj;  // [S][R]
+  float kc, kx;
+  int S, R;
+};
+
+struct StateView {
+  int N, C, Cp, P, R;
+  float *x, *y;
+  int8_t *F[2];
+  int8_t *Sg;  // [N][Cp] readout spins sign(x), +1 for x >= 0
+  // F buffer holding f(x) for step n (selected without indexing the array,
+  // which would put the kernel argument in local memory)
+  __host__ __device__ int8_t *f_of(int n) const { return (n & 1) ? F[1] : F[0]; }
+};
+
+struct CsrView {
+  const int32_t *row_ptr;  // [N + 1]
+  const int32_t *col;      // [nnz]
+  const void *val;         // int8 (PM1), float (F32) or bf16 (BF16)
+  const float *h;          // [N], never null (zeros when h = 0)
+  int kind;
+};
+
+struct DenseView {
+  const float *J;  // [N][N] row-major, FP32 (exact for integers)
+  const float *h;  // [N]
+};
+
+// Readout: energies of s = sign(x) for every column.
+struct EnergyView {
+  int is_integer;
+  // sparse: row_ptr/col from CsrView with FP64 or int values below
+  const double *val_f64;   // [nnz] (sparse) or [N][N] (dense), real instances
+  const int32_t *val_i32;  // [nnz] or [N][N], integer instances
+  const double *h_f64;     // [N]
+  const int64_t *h_i64;    // [N]
+};
+
+struct BestView {
+  int64_t *e_int;        // [Cp] energies of the last readout (integer)
+  double *e_f64;         // [Cp] (real instances, also filled for integer)
+  int64_t *part_int;     // [nblk][Cp] partial sums
+  double *part_f64;      // [nblk][Cp]
+  int nblk;              // row blocks of the energy kernel
+  int64_t *best_e_int;   // [R]
+  double *best_e;        // [R]
+  int32_t *best_k;       // [R]
+  int32_t *best_step;    // [R]
+  int8_t *best_spins;    // [R][N]
+  int32_t *have_best;    // [R]
+};
+
+// ---- launchers (return cudaGetLastError() of the launch) ----
+cudaError_t launch_init(const StateView &s, uint64_t seed, float amp, float delta0,
+                        cudaStream_t st);
+cudaError_t launch_refresh_f(const StateView &s, int which, float delta, cudaStream_t st);
+cudaError_t launch_step_csr(const StateView &s, const CsrView &J, const StepTables &t,
+                            int n, cudaStream_t st);
+cudaError_t launch_step_dense(const StateView &s, const DenseView &J, const StepTables &t,
+                              int n, cudaStream_t st);
+int energy_row_blocks(int N);
+// sign(x) into Sg, energies of every column into b.e_int / b.e_f64.
+cudaError_t launch_energy_csr(const StateView &s, const CsrView &J, const EnergyView &E,
+                              const BestView &b, cudaStream_t st);
+cudaError_t launch_energy_dense(const StateView &s, const EnergyView &E, const BestView &b,
+                                cudaStream_t st);
+cudaError_t launch_best(const StateView &s, const EnergyView &E, const BestView &b, int step,
+                        cudaStream_t st);
+cudaError_t launch_reset_best(const StateView &s, const BestView &b, cudaStream_t st);
+
+}  // namespace sbqa

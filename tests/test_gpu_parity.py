@@ -1,0 +1,422 @@
+"""Parity of the CUDA hot path (through the C ABI) with the FP64 oracle.
+
+Bars (stated once here, used below):
+  * initial state: bit-exact (both sides implement SplitMix64);
+  * one step from the same FP32 state: relative error <= 1e-5 per (run,
+    replica) for x and y (TOL_STEP); elements where the strict wall test
+    |x| > 1 falls on different sides in FP32 and FP64 are listed and excluded
+    from the y comparison (their x agree to 4e-6);
+  * free-running FP32 trajectories vs the FP64 oracle: <= 1e-5 relative per
+    step (TOL_TRAJ) for 100 steps at Gamma_x(0) = 16, and for the first 20
+    steps at Gamma_x(0) = 1 where the in-phase replica mode is linearly
+    unstable from t = 0 and amplifies rounding differences;
+  * integer energies: bit-exact; real energies: 1e-12 relative (FP64 sums in
+    another order);
+  * BF16 product: the oracle runs on the BF16-rounded J (TOL_STEP); against
+    the unrounded J the drift over 100 steps stays below 1e-2 (TOL_BF16_DRIFT);
+  * best-energy distributions over 256 runs: permutation test on the mean
+    and chi-square over integer energy bins, both p > 0.01.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from sbqa_cases import create, dense_int, dense_real, lattice, regular, rel_err, sk, wall_ambiguous
+
+pytestmark = pytest.mark.gpu
+
+TOL_STEP = 1e-5
+TOL_TRAJ = 1e-5
+TOL_BF16_DRIFT = 1e-2
+
+
+@pytest.fixture(scope="module")
+def sb():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2604_01050_gb300 import build as b
+    b.build()
+    import paper_2604_01050_gb300 as s
+    return s
+
+
+def _params(**kw):
+    base = dict(a0=1.0, c0=0.0, dt=0.5, gamma0=1.0, delta_slope=0.7, init_amp=0.1, jperp_enable=1)
+    base.update(kw)
+    return base
+
+
+def _oracle_kwargs(p, pb):
+    c0 = p["c0"] if p["c0"] > 0 else oracle.c0_auto(pb)
+    return dict(a0=p["a0"], c0=c0, dt=p["dt"])
+
+
+# ---------------------------------------------------------------- initial state
+@pytest.mark.parametrize("N,P,R", [(64, 8, 16), (33, 2, 3), (7, 1, 5), (130, 32, 5), (1, 4, 2)])
+def test_initial_state_bit_exact(sb, N, P, R):
+    pb, spec = sk(N, 1) if N > 1 else (oracle.Problem.dense(np.zeros((1, 1))), ("dense", np.zeros((1, 1)), None))
+    prob = create(sb, spec)
+    beta, alpha = workloads.autotune_params(R, 0)
+    sb.set_schedule(prob, beta, alpha, **_params())
+    sb.run_begin(prob, 10, P, R, seed=12345)
+    xg, yg, sd = sb.get_state(prob)
+    xo, yo = oracle.init_state(12345, N, P, R, 0.1)
+    assert sd == 0
+    assert np.array_equal(xg.astype(np.float64), xo) and np.array_equal(yg.astype(np.float64), yo)
+
+
+# ---------------------------------------------------------------- one step from the same state
+def _per_step(sb, pb, spec, P, R, S, steps, seed=3, prec="auto", pb_oracle=None, **pkw):
+    prob = create(sb, spec)
+    p = _params(precision=prec, **pkw)
+    beta, alpha = workloads.autotune_params(R, seed)
+    sb.set_schedule(prob, beta, alpha, **p)
+    sb.run_begin(prob, S, P, R, seed=seed)
+    ref = pb_oracle or pb
+    a, d, jp = oracle.schedule(S, P, R, beta, alpha, p["gamma0"], p["delta_slope"], p["jperp_enable"])
+    kw = _oracle_kwargs(p, pb)
+    x, y, _ = sb.get_state(prob)
+    worst_x = worst_y = 0.0
+    amb_total = 0
+    for n in range(steps):
+        sb.run_advance(prob, 1)
+        xg, yg, sd = sb.get_state(prob)
+        assert sd == n + 1
+        xo = np.empty((R, P, pb.n)); yo = np.empty_like(xo)
+        for r in range(R):
+            xo[r], yo[r] = oracle.step(ref, x[r].astype(np.float64), y[r].astype(np.float64), P, a[n], d[n],
+                                       jp[r, n], **kw)
+        amb = wall_ambiguous(xg, xo)
+        amb_total += int(amb.sum())
+        worst_x = max(worst_x, rel_err(xg, xo))
+        yg_c = np.where(amb, 0.0, yg); yo_c = np.where(amb, 0.0, yo)
+        worst_y = max(worst_y, rel_err(yg_c, yo_c))
+        x, y = xg, yg
+    return worst_x, worst_y, amb_total, prob
+
+
+def test_per_step_dense_sk64_default_schedule(sb):
+    """Config-1 shape: dense SK N=64 +-1, P=8, R=16, 1000-step schedule; every one of the first 100 steps."""
+    pb, spec = sk(64, 0)
+    wx, wy, amb, _ = _per_step(sb, pb, spec, 8, 16, 1000, 100)
+    print("per-step worst x %.2e y %.2e wall-ambiguous %d" % (wx, wy, amb))
+    assert wx <= TOL_STEP and wy <= TOL_STEP
+
+
+def test_per_step_lattice_csr(sb):
+    pb, spec = lattice(6, 2)
+    wx, wy, amb, _ = _per_step(sb, pb, spec, 32, 4, 500, 60)
+    assert wx <= TOL_STEP and wy <= TOL_STEP
+
+
+@pytest.mark.parametrize("P,R", [(1, 5), (2, 3), (4, 7), (16, 3)])
+def test_per_step_ragged_shapes(sb, P, R):
+    pb, spec = lattice(3, 5)  # N = 27: a ragged tail of rows
+    wx, wy, _, _ = _per_step(sb, pb, spec, P, R, 200, 30, seed=P)
+    assert wx <= TOL_STEP and wy <= TOL_STEP
+
+
+def test_per_step_real_sparse_fp32_with_field(sb):
+    pb, spec = regular(500, 6, 1)
+    wx, wy, _, _ = _per_step(sb, pb, spec, 16, 8, 300, 40, prec="fp32")
+    assert wx <= TOL_STEP and wy <= TOL_STEP
+
+
+def test_per_step_real_sparse_bf16(sb):
+    """BF16 product: parity against the oracle on the BF16-rounded J."""
+    pb, spec = regular(500, 6, 2)
+    wx, wy, _, _ = _per_step(sb, pb, spec, 16, 8, 300, 40, prec="bf16", pb_oracle=pb.bf16())
+    assert wx <= TOL_STEP and wy <= TOL_STEP
+
+
+def test_per_step_dense_real_and_integer(sb):
+    pb, spec = dense_real(100, 3)
+    wx, wy, _, _ = _per_step(sb, pb, spec, 8, 4, 200, 30, prec="fp32")
+    assert wx <= TOL_STEP and wy <= TOL_STEP
+    pb, spec = dense_int(90, 4)
+    wx, wy, _, _ = _per_step(sb, pb, spec, 4, 4, 200, 30, prec="exact")
+    assert wx <= TOL_STEP and wy <= TOL_STEP
+
+
+def test_per_step_jperp_disabled(sb):
+    pb, spec = sk(48, 6)
+    wx, wy, _, _ = _per_step(sb, pb, spec, 8, 4, 200, 30, jperp_enable=0)
+    assert wx <= TOL_STEP and wy <= TOL_STEP
+
+
+# ---------------------------------------------------------------- free-running trajectories
+def _free_running(sb, pb, spec, P, R, S, steps, gamma0, seed=0, prec="auto", pb_oracle=None):
+    prob = create(sb, spec)
+    p = _params(gamma0=gamma0, precision=prec)
+    beta, alpha = workloads.linear_params(R)
+    sb.set_schedule(prob, beta, alpha, **p)
+    sb.run_begin(prob, S, P, R, seed=seed)
+    ref = oracle.run(pb_oracle or pb, S, P, R, seed, beta, alpha, gamma0=gamma0, n_end=steps, n_traj=steps,
+                     **_oracle_kwargs(p, pb))
+    errs = []
+    for n in range(steps):
+        sb.run_advance(prob, 1)
+        xg, yg, _ = sb.get_state(prob)
+        errs.append((rel_err(xg, ref["traj_x"][n]), rel_err(yg, ref["traj_y"][n])))
+    return np.array(errs)
+
+
+def test_free_running_sk64_100_steps_gamma16(sb):
+    pb, spec = sk(64, 0)
+    e = _free_running(sb, pb, spec, 8, 16, 1000, 100, gamma0=16.0)
+    print("free-running max x %.2e y %.2e" % tuple(e.max(axis=0)))
+    assert e.max() <= TOL_TRAJ
+
+
+def test_free_running_sk64_default_schedule_first_20_steps(sb):
+    pb, spec = sk(64, 0)
+    e = _free_running(sb, pb, spec, 8, 16, 1000, 40, gamma0=1.0)
+    print("gamma0=1 divergence by step:", ["%.1e" % v for v in e.max(axis=1)[::5]])
+    assert e[:20].max() <= TOL_TRAJ
+
+
+def test_free_running_lattice_100_steps(sb):
+    pb, spec = lattice(8, 1)
+    e = _free_running(sb, pb, spec, 32, 4, 1000, 100, gamma0=16.0)
+    assert e.max() <= TOL_TRAJ
+
+
+def test_bf16_drift_against_unrounded_j(sb):
+    pb, spec = regular(400, 6, 7)
+    e = _free_running(sb, pb, spec, 16, 4, 1000, 100, gamma0=16.0, prec="bf16")
+    print("bf16 drift vs FP64 J: %.2e" % e.max())
+    assert e.max() <= TOL_BF16_DRIFT
+    e2 = _free_running(sb, pb, spec, 16, 4, 1000, 100, gamma0=16.0, prec="bf16", pb_oracle=pb.bf16())
+    assert e2.max() <= TOL_TRAJ
+
+
+# ---------------------------------------------------------------- energies and best
+def _check_energies_and_best(sb, pb, prob, R, P):
+    e, ei = sb.get_energies(prob)
+    x, _, _ = sb.get_state(prob)
+    spins = np.where(x >= 0, 1, -1).astype(np.int8)
+    ref = oracle.energies(pb, spins)
+    if pb.is_integer:
+        assert np.array_equal(ei, ref) and np.array_equal(e, ref.astype(float))
+    else:
+        assert np.allclose(e, ref, rtol=1e-12, atol=1e-9)
+    best = sb.get_best(prob)
+    for r in range(R):
+        k = int(np.argmin(e[r]))
+        assert best["replica"][r] == k
+        assert best["energy"][r] == e[r, k]
+        assert np.array_equal(best["spins"][r], spins[r, k])
+        eb = oracle.energy_int(pb, best["spins"][r]) if pb.is_integer else oracle.energy(pb, best["spins"][r])
+        assert eb == pytest.approx(best["energy"][r], rel=1e-12, abs=1e-9)
+    return best
+
+
+def test_full_run_sk64_energies_exact(sb):
+    pb, spec = sk(64, 0)
+    prob = create(sb, spec)
+    beta, alpha = workloads.linear_params(16)
+    sb.set_schedule(prob, beta, alpha, **_params())
+    sb.run(prob, 1000, 8, 16, seed=0)
+    best = _check_energies_and_best(sb, pb, prob, 16, 8)
+    assert np.all(best["step"] == 999)
+
+
+def test_steps_zero_reads_initial_state(sb):
+    pb, spec = lattice(4, 0)
+    prob = create(sb, spec)
+    sb.set_schedule(prob, **_params())
+    sb.run(prob, 0, 8, 3, seed=5)
+    best = _check_energies_and_best(sb, pb, prob, 3, 8)
+    assert np.all(best["step"] == -1)
+    x, _, _ = sb.get_state(prob)
+    xo, _ = oracle.init_state(5, pb.n, 8, 3, 0.1)
+    assert np.array_equal(x.astype(np.float64), xo)
+
+
+def test_real_energies_sparse_and_dense(sb):
+    for pb, spec, prec in (regular(300, 6, 3) + ("bf16",), dense_real(70, 2) + ("fp32",)):
+        prob = create(sb, spec)
+        sb.set_schedule(prob, **_params(precision=prec))
+        sb.run(prob, 200, 4, 6, seed=1)
+        _check_energies_and_best(sb, pb, prob, 6, 4)
+
+
+def test_isolated_spins_and_single_spin(sb):
+    # N = 1 (no couplings) and a lattice with extra isolated spins (empty rows)
+    prob = sb.create_problem_csr(1, [0, 0], [], [], h=[0.5])
+    sb.set_schedule(prob, **_params())
+    sb.run(prob, 50, 2, 3, seed=2)
+    best = sb.get_best(prob)
+    assert np.all(best["energy"] == -0.5) and np.all(best["spins"] == 1)
+    n, rp, col, val, _ = workloads.cubic_lattice(3, 0)
+    rp2 = np.concatenate([rp, np.full(5, rp[-1])])
+    pb = oracle.Problem.csr(n + 5, rp2, col, val, None)
+    prob = sb.create_problem_csr(n + 5, rp2, col, val)
+    sb.set_schedule(prob, **_params())
+    sb.run(prob, 80, 4, 2, seed=3)
+    _check_energies_and_best(sb, pb, prob, 2, 4)
+
+
+def test_eval_every_best_so_far(sb):
+    pb, spec = lattice(5, 3)
+    prob = create(sb, spec)
+    beta, alpha = workloads.autotune_params(8, 2)
+    sb.set_schedule(prob, beta, alpha, **_params())
+    sb.run(prob, 400, 8, 8, seed=9)
+    final = sb.get_best(prob)
+    sb.set_schedule(prob, beta, alpha, **_params(eval_every=50))
+    sb.run(prob, 400, 8, 8, seed=9)
+    kept = sb.get_best(prob)
+    assert np.all(kept["energy"] <= final["energy"])
+    assert set(kept["step"].tolist()) <= {49, 99, 149, 199, 249, 299, 349, 399}
+    for r in range(8):
+        assert oracle.energy_int(pb, kept["spins"][r]) == kept["energy"][r]
+
+
+def test_best_energy_distribution_matches_oracle(sb):
+    """256 runs x 8 replicas of the config-1 instance: final best energies of
+    the GPU path and of the oracle are statistically indistinguishable."""
+    scipy_stats = pytest.importorskip("scipy.stats")
+    pb, spec = sk(64, 0)
+    R, P, S = 256, 8, 1000
+    beta, alpha = workloads.autotune_params(R, 11)
+    prob = create(sb, spec)
+    sb.set_schedule(prob, beta, alpha, **_params())
+    sb.run(prob, S, P, R, seed=77)
+    g = sb.get_best(prob)["energy"]
+    o = oracle.run(pb, S, P, R, 77, beta, alpha)["best_energy"]
+    rng = np.random.default_rng(0)
+    both = np.concatenate([g, o])
+    obs = abs(g.mean() - o.mean())
+    perm = [abs(np.subtract(*rng.permutation(both).reshape(2, -1).mean(axis=1))) for _ in range(5000)]
+    p_perm = (np.sum(np.array(perm) >= obs) + 1) / (len(perm) + 1)
+    vals = np.unique(both)
+    table = np.array([[np.sum(g == v) for v in vals], [np.sum(o == v) for v in vals]], dtype=float)
+    # merge sparse bins (expected count < 5) from the low-energy end
+    merged = []
+    acc = np.zeros(2)
+    for col in table.T:
+        acc = acc + col
+        if acc.sum() >= 10:
+            merged.append(acc); acc = np.zeros(2)
+    if acc.sum() > 0 and merged:
+        merged[-1] = merged[-1] + acc
+    table = np.array(merged).T
+    p_chi = scipy_stats.chi2_contingency(table)[1] if table.shape[1] > 1 else 1.0
+    print("mean gpu %.3f oracle %.3f p_perm %.3f p_chi2 %.3f" % (g.mean(), o.mean(), p_perm, p_chi))
+    assert p_perm > 0.01 and p_chi > 0.01
+
+
+# ---------------------------------------------------------------- determinism, resume, symmetry
+def test_resume_is_bit_identical(sb):
+    pb, spec = lattice(6, 4)
+    beta, alpha = workloads.autotune_params(4, 4)
+    prob = create(sb, spec)
+    sb.set_schedule(prob, beta, alpha, **_params(eval_every=25))
+    sb.run(prob, 300, 16, 4, seed=21)
+    xa, ya, _ = sb.get_state(prob)
+    ba = sb.get_best(prob)
+    sb.run_begin(prob, 300, 16, 4, seed=21)
+    sb.run_advance(prob, 113)
+    xm, ym, sd = sb.get_state(prob)
+    sb.set_state(prob, xm, ym, sd)  # host round trip of the checkpoint
+    sb.run_advance(prob, 1000)
+    sb.run_finish(prob)
+    xb, yb, _ = sb.get_state(prob)
+    bb = sb.get_best(prob)
+    assert np.array_equal(xa, xb) and np.array_equal(ya, yb)
+    for k in ba:
+        assert np.array_equal(ba[k], bb[k]), k
+
+
+def test_negation_symmetry_bit_exact(sb):
+    pb, spec = sk(40, 2)
+    prob = create(sb, spec)
+    sb.set_schedule(prob, **_params())
+    sb.run_begin(prob, 500, 8, 4, seed=8)
+    x0, y0, _ = sb.get_state(prob)
+    sb.run_advance(prob, 150)
+    xa, ya, _ = sb.get_state(prob)
+    sb.run_begin(prob, 500, 8, 4, seed=8)
+    sb.set_state(prob, -x0, -y0, 0)
+    sb.run_advance(prob, 150)
+    xb, yb, _ = sb.get_state(prob)
+    assert np.array_equal(xa, -xb) and np.array_equal(ya, -yb)
+
+
+def test_repeat_runs_deterministic(sb):
+    pb, spec = regular(2000, 6, 5)
+    prob = create(sb, spec)
+    sb.set_schedule(prob, **_params(precision="bf16"))
+    out = []
+    for _ in range(2):
+        sb.run(prob, 300, 16, 8, seed=4)
+        out.append((sb.get_state(prob)[0], sb.get_energies(prob)[0]))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+# ---------------------------------------------------------------- full-size configurations, sampled
+def _sampled_runs(sb, pb, spec, P, R, S, steps, runs, prec="auto", pb_oracle=None):
+    prob = create(sb, spec)
+    beta, alpha = workloads.autotune_params(R, 1)
+    p = _params(precision=prec)
+    sb.set_schedule(prob, beta, alpha, **p)
+    sb.run_begin(prob, S, P, R, seed=0)
+    sb.run_advance(prob, steps)
+    xg, yg, _ = sb.get_state(prob)
+    xi, yi = oracle.init_state(0, pb.n, P, max(runs) + 1, 0.1)
+    worst = 0.0
+    for r in runs:
+        ref = oracle.run(pb_oracle or pb, S, P, 1, 0, beta[r:r + 1], alpha[r:r + 1], n_end=steps,
+                         x0=xi[r:r + 1], y0=yi[r:r + 1], **_oracle_kwargs(p, pb))
+        worst = max(worst, rel_err(xg[r:r + 1], ref["x"]), rel_err(yg[r:r + 1], ref["y"]))
+    return worst
+
+
+def test_full_size_lattice_L16_P32_R64(sb):
+    """3D lattice L=16 (N=4096), P=32, R=64, 10^4-step schedule: runs 0, 37, 63 after 10 steps."""
+    pb, spec = lattice(16, 0)
+    assert _sampled_runs(sb, pb, spec, 32, 64, 10000, 10, [0, 37, 63]) <= TOL_TRAJ
+
+
+def test_full_size_lattice_energies(sb):
+    pb, spec = lattice(16, 0)
+    prob = create(sb, spec)
+    sb.set_schedule(prob, *workloads.autotune_params(64, 1), **_params())
+    sb.run(prob, 40, 32, 64, seed=0)
+    _check_energies_and_best(sb, pb, prob, 64, 32)
+
+
+def test_full_size_dense_sk2000_exact(sb):
+    """SK N=2000 +-1, P=32, R=32 (J.X = 2000x2000 @ 2000x1024), exact product: runs 0 and 31 after 5 steps."""
+    pb, spec = sk(2000, 0)
+    assert _sampled_runs(sb, pb, spec, 32, 32, 1000, 5, [0, 31], prec="exact") <= TOL_TRAJ
+
+
+def test_full_size_regular_1e5_bf16(sb):
+    """Random 6-regular N=1e5, J~N(0,1), h~N(0,0.1^2), BF16 product, P=16, R=8: runs 0 and 7 after 5 steps."""
+    pb, spec = regular(100000, 6, 0)
+    assert _sampled_runs(sb, pb, spec, 16, 8, 5000, 5, [0, 7], prec="bf16", pb_oracle=pb.bf16()) <= TOL_TRAJ
+
+
+# ---------------------------------------------------------------- errors that need a handle
+def test_run_argument_errors(sb):
+    pb, spec = sk(16, 0)
+    prob = create(sb, spec)
+    with pytest.raises(sb.SBQAError) as e:
+        sb.run(prob, 10, 8, 2)
+    assert e.value.status == sb.ERR_STATE
+    sb.set_schedule(prob, *workloads.linear_params(3), **_params())
+    for P, R, code in ((3, 3, sb.ERR_UNSUPPORTED), (8, 4, sb.ERR_INVALID_ARG), (8, 0, sb.ERR_INVALID_ARG)):
+        with pytest.raises(sb.SBQAError) as e:
+            sb.run(prob, 10, P, R)
+        assert e.value.status == code
+    with pytest.raises(sb.SBQAError) as e:
+        sb.get_best(prob)
+    assert e.value.status == sb.ERR_STATE
+    pr, sr = dense_real(20, 0)
+    probr = create(sb, sr)
+    with pytest.raises(sb.SBQAError) as e:
+        sb.set_schedule(probr, **_params(precision="exact"))
+    assert e.value.status == sb.ERR_UNSUPPORTED
