@@ -207,6 +207,7 @@ def main():
     from paper_2604_01050_gb300 import build as _b
     _b.build()
     import paper_2604_01050_gb300 as sb
+    from paper_2604_01050_gb300 import multi
 
     inst = make_instance(cfg)
     N = n_of(inst)
@@ -224,7 +225,7 @@ def main():
     prob = create(inst)
     sb.set_schedule(prob, beta, alpha, precision=cfg["prec"])
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    seed0 = 1000 * rank
+    seed0 = multi.rank_seed(0, rank)
 
     def barrier():
         if dist is not None:
@@ -259,10 +260,7 @@ def main():
     ms0 = [a.elapsed_time(b) for a, b in ev0]
     ms_solve = statistics.mean(ms)
     ms_zero = statistics.mean(ms0)
-    if dist is not None:
-        t = torch.tensor([ms_solve], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_solve = float(t.item())
+    ms_solve = multi.max_over_ranks(ms_solve)
     value = world * upd_per_solve / (ms_solve * 1e-3)
     step_ms = max(ms_solve - ms_zero, 1e-9) / S
     achieved_gbs = BYTES_PER_UPDATE * N * P * R / (step_ms * 1e-3) / 1e9

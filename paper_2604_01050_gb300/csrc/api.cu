@@ -94,6 +94,14 @@ struct sbqa_problem {
   DevBuf<__nv_bfloat16> d_val_bf16;
   DevBuf<float> d_dense_f32;  // dense J for the CUDA-core path
   int dense_prec = -1;        // precision the dense FP32 copy was built for
+  // dense integer J on the tensor cores: e4m3 copies padded to Kp
+  bool use_tc = false;
+  int Kp = 0;
+  DevBuf<uint8_t> d_J8, d_FT;
+  void *tc_plan = nullptr;
+  const void *tc_plan_ft = nullptr;  // FT buffer the plan was made for
+  int tc_plan_cp = 0;
+  DevBuf<int> d_err;
   DevBuf<float> d_h;
   // device: readout operands
   DevBuf<int32_t> d_e_i32;
@@ -125,12 +133,12 @@ struct sbqa_problem {
   cudaGraphExec_t graph = nullptr;
   cudaStream_t cap_stream = nullptr;
   struct Key {
-    int S = -1, P = -1, R = -1, eval = -1, kind = -1, dense = -1;
+    int S = -1, P = -1, R = -1, eval = -1, kind = -1, dense = -1, tc = -1;
     float kc = 0.f, kx = 0.f;  // step constants are kernel arguments in the graph
     const void *x = nullptr, *kj = nullptr;
     bool operator==(const Key &o) const {
       return S == o.S && P == o.P && R == o.R && eval == o.eval && kind == o.kind &&
-             dense == o.dense && x == o.x && kj == o.kj &&
+             dense == o.dense && tc == o.tc && x == o.x && kj == o.kj &&
              std::memcmp(&kc, &o.kc, sizeof(float)) == 0 && std::memcmp(&kx, &o.kx, sizeof(float)) == 0;
     }
   } graph_key;
@@ -140,6 +148,8 @@ struct sbqa_problem {
     cudaDeviceSynchronize();  // no kernel of this handle may still use the buffers
     if (graph) cudaGraphExecDestroy(graph);
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (tc_plan) tc_plan_free(tc_plan);
+    d_J8.release(); d_FT.release(); d_err.release();
     d_row_ptr.release(); d_col.release(); d_val_i8.release(); d_val_f32.release();
     d_val_bf16.release(); d_dense_f32.release(); d_h.release(); d_e_i32.release();
     d_e_f64.release(); d_h_i64.release(); d_h_f64.release(); d_x.release(); d_y.release();
@@ -182,6 +192,8 @@ struct sbqa_problem {
 };
 
 namespace {
+
+constexpr int kTcMinN = 256;  // smaller dense instances stay on the CUDA-core kernel
 
 bool finite_all(const double *v, size_t n) {
   for (size_t i = 0; i < n; ++i)
@@ -289,9 +301,34 @@ int prepare_sparse_values(sbqa_problem *p, int precision) {
   return SBQA_OK;
 }
 
+// e4m3 bits of a small integer (|v| <= 16, exact): 1.mmm x 2^e, bias 7.
+uint8_t e4m3_of_int(int v) {
+  if (v == 0) return 0;
+  const uint8_t sign = v < 0 ? 0x80 : 0x00;
+  int a = v < 0 ? -v : v, e = 0;
+  while ((a >> (e + 1)) != 0) ++e;          // a in [2^e, 2^(e+1))
+  const int mant = ((a << 3) >> e) & 7;     // 3 fraction bits (exact for a <= 16)
+  return uint8_t(sign | ((e + 7) << 3) | mant);
+}
+
+int prepare_tc_values(sbqa_problem *p) {
+  if (p->d_J8.p) return SBQA_OK;
+  const int N = p->n, Kp = (N + 127) / 128 * 128;
+  std::vector<uint8_t> j8(size_t(Kp) * Kp, 0);
+  for (int i = 0; i < N; ++i)
+    for (int j = 0; j < N; ++j) j8[size_t(i) * Kp + j] = e4m3_of_int(int(std::llround(p->val[size_t(i) * N + j])));
+  SBQA_CUDA(p->d_J8.alloc(j8.size()));
+  SBQA_CUDA(cudaMemcpy(p->d_J8.p, j8.data(), j8.size(), cudaMemcpyHostToDevice));
+  p->Kp = Kp;
+  return SBQA_OK;
+}
+
 int prepare_dense_values(sbqa_problem *p, int precision) {
   if (precision == SBQA_PREC_EXACT && (!p->j_integer || p->max_abs_j > 16))
     return fail(SBQA_ERR_UNSUPPORTED, "EXACT precision needs integer J with |J_ij| <= 16");
+  p->use_tc = (precision == SBQA_PREC_AUTO || precision == SBQA_PREC_EXACT) && p->j_integer &&
+              p->max_abs_j <= 16 && p->n >= kTcMinN;
+  if (p->use_tc) return prepare_tc_values(p);
   const int want = precision == SBQA_PREC_BF16 ? SBQA_PREC_BF16 : SBQA_PREC_FP32;
   if (p->d_dense_f32.p && p->dense_prec == want) return SBQA_OK;
   const size_t m = p->val.size();
@@ -333,7 +370,20 @@ int alloc_run(sbqa_problem *p, int S, int P, int R) {
   SBQA_CUDA(p->d_best_step.alloc(R));
   SBQA_CUDA(p->d_have.alloc(R));
   SBQA_CUDA(p->d_best_spins.alloc(size_t(R) * p->n));
+  SBQA_CUDA(p->d_err.alloc(1));
   p->S = S; p->P = P; p->R = R; p->C = C; p->Cp = Cp;
+  if (p->use_tc) {
+    SBQA_CUDA(p->d_FT.alloc(size_t(2) * Cp * p->Kp));
+    if (!p->tc_plan || p->tc_plan_ft != p->d_FT.p || p->tc_plan_cp != Cp) {
+      if (p->tc_plan) tc_plan_free(p->tc_plan);
+      p->tc_plan = nullptr;
+      if (!tc_plan_make(&p->tc_plan, p->d_J8.p, p->d_FT.p, p->Kp, Cp))
+        return fail(SBQA_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+      SBQA_CUDA(tc_set_attributes());
+      p->tc_plan_ft = p->d_FT.p;
+      p->tc_plan_cp = Cp;
+    }
+  }
   return SBQA_OK;
 }
 
@@ -376,6 +426,7 @@ int build_tables(sbqa_problem *p) {
 
 cudaError_t issue_step(sbqa_problem *p, int n, cudaStream_t st) {
   const StateView s = p->state();
+  if (p->use_tc) return launch_step_dense_tc(p->tc_plan, s, p->Kp, p->d_FT.p, p->d_err.p, p->d_h.p, p->tables, n, st);
   if (p->dense) {
     DenseView d;
     d.J = p->d_dense_f32.p;
@@ -614,7 +665,9 @@ int sbqa_run_begin(sbqa_problem *p, int32_t steps, int32_t P, int32_t R, uint64_
   if ((rc = alloc_run(p, steps, P, R)) != SBQA_OK) return rc;
   if ((rc = build_tables(p)) != SBQA_OK) return rc;
   const StateView s = p->state();
+  SBQA_CUDA(cudaMemsetAsync(p->d_err.p, 0, sizeof(int), p->stream));
   SBQA_CUDA(launch_init(s, seed, float(p->prm.init_amp), 0.0f, p->stream));
+  if (p->use_tc) SBQA_CUDA(launch_f_to_ft8(s, 0, p->d_FT.p, p->Kp, 0, p->stream));
   SBQA_CUDA(launch_reset_best(s, p->best(), p->stream));
   p->step_done = 0;
   p->begun = true;
@@ -649,7 +702,7 @@ int sbqa_run(sbqa_problem *p, int32_t steps, int32_t P, int32_t R, uint64_t seed
   sbqa_problem::Key key;
   key.S = steps; key.P = P; key.R = R; key.eval = p->prm.eval_every; key.kind = p->kind;
   key.dense = p->dense ? 1 : 0; key.x = p->d_x.p; key.kj = p->d_kj.p;
-  key.kc = p->tables.kc; key.kx = p->tables.kx;
+  key.kc = p->tables.kc; key.kx = p->tables.kx; key.tc = p->use_tc ? 1 : 0;
   if (!(p->graph && p->graph_key == key)) {
     if (p->graph) {
       cudaGraphExecDestroy(p->graph);
@@ -684,6 +737,11 @@ int sbqa_synchronize(sbqa_problem *p) {
   DeviceGuard g(p->device);
   SBQA_CUDA(p->stream ? cudaStreamSynchronize(p->stream) : cudaDeviceSynchronize());
   SBQA_CUDA(cudaGetLastError());
+  if (p->d_err.p) {
+    int err = 0;
+    SBQA_CUDA(cudaMemcpy(&err, p->d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err != 0) return fail(SBQA_ERR_TIMEOUT, "a bounded device wait gave up (code " + std::to_string(err) + ")");
+  }
   return SBQA_OK;
 }
 
@@ -754,6 +812,8 @@ int sbqa_set_state(sbqa_problem *p, const float *x, const float *y, int32_t step
   SBQA_CUDA(cudaMemcpy(p->d_y.p, by.data(), NC * sizeof(float), cudaMemcpyHostToDevice));
   const double tau = p->S > 0 ? double(step_done) / double(p->S) : 0.0;
   SBQA_CUDA(launch_refresh_f(p->state(), step_done & 1, float(p->prm.delta_slope * tau), p->stream));
+  if (p->use_tc)
+    SBQA_CUDA(launch_f_to_ft8(p->state(), step_done & 1, p->d_FT.p, p->Kp, step_done & 1, p->stream));
   p->step_done = step_done;
   p->finished = false;
   return SBQA_OK;

@@ -85,6 +85,15 @@ cudaError_t launch_step_csr(const StateView &s, const CsrView &J, const StepTabl
                             int n, cudaStream_t st);
 cudaError_t launch_step_dense(const StateView &s, const DenseView &J, const StepTables &t,
                               int n, cudaStream_t st);
+// Dense integer couplings on tcgen05 (step_dense_tc.cu).  The plan holds the
+// TMA descriptors of J8 [Kp][Kp] and FT [2][Cp][Kp] (e4m3).
+bool tc_plan_make(void **plan, const uint8_t *J8, uint8_t *FT, int Kp, int Cp);
+void tc_plan_free(void *plan);
+cudaError_t tc_set_attributes();  // dynamic shared memory limit of the tcgen05 kernels
+cudaError_t launch_step_dense_tc(const void *plan, const StateView &s, int Kp, uint8_t *FT, int *err,
+                                 const float *h, const StepTables &t, int n, cudaStream_t st);
+cudaError_t launch_f_to_ft8(const StateView &s, int which, uint8_t *FT, int Kp, int buffer, cudaStream_t st);
+
 int energy_row_blocks(int N);
 // sign(x) into Sg, energies of every column into b.e_int / b.e_f64.
 cudaError_t launch_energy_csr(const StateView &s, const CsrView &J, const EnergyView &E,

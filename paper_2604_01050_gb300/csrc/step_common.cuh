@@ -57,14 +57,13 @@ __device__ __forceinline__ uint32_t pack4(int8_t a, int8_t b, int8_t c, int8_t d
 }
 
 // Applies the step to the lane's 4 columns of row i.  G = coupling sums,
-// hi = h_i.  Loads x, y of (i, c4..c4+3), writes x, y and F_next.
+// hi = h_i, xv / yv = x, y of (i, c4..c4+3) loaded by the caller (so the
+// loads can be issued before the coupling product).  Writes x, y, F_next.
 template <int P>
 __device__ __forceinline__ void sb_update4(const StateView &s, const StepTables &t, int n,
                                            int i, int c4, const float G[4], float hi,
-                                           int8_t *Fout) {
+                                           float4 xv, float4 yv, int8_t *Fout) {
   const size_t off = size_t(i) * s.Cp + c4;
-  float4 xv = *reinterpret_cast<const float4 *>(s.x + off);
-  float4 yv = *reinterpret_cast<const float4 *>(s.y + off);
   float xs[4] = {xv.x, xv.y, xv.z, xv.w};
   float ys[4] = {yv.x, yv.y, yv.z, yv.w};
   float xm[4], xp[4];
@@ -95,6 +94,15 @@ __device__ __forceinline__ void sb_update4(const StateView &s, const StepTables 
   *reinterpret_cast<float4 *>(s.x + off) = make_float4(xs[0], xs[1], xs[2], xs[3]);
   *reinterpret_cast<float4 *>(s.y + off) = make_float4(ys[0], ys[1], ys[2], ys[3]);
   *reinterpret_cast<uint32_t *>(Fout + off) = pack4(f[0], f[1], f[2], f[3]);
+}
+
+template <int P>
+__device__ __forceinline__ void sb_update4(const StateView &s, const StepTables &t, int n,
+                                           int i, int c4, const float G[4], float hi, int8_t *Fout) {
+  const size_t off = size_t(i) * s.Cp + c4;
+  const float4 xv = *reinterpret_cast<const float4 *>(s.x + off);
+  const float4 yv = *reinterpret_cast<const float4 *>(s.y + off);
+  sb_update4<P>(s, t, n, i, c4, G, hi, xv, yv, Fout);
 }
 
 __device__ __forceinline__ float sbyte(uint32_t w, int j) {

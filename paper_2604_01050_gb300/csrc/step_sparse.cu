@@ -15,6 +15,13 @@
 
 namespace sbqa {
 
+template <int KIND>
+__device__ __forceinline__ float load_val(const void *val, int e) {
+  if constexpr (KIND == VAL_PM1) return float(__ldg(static_cast<const int8_t *>(val) + e));
+  else if constexpr (KIND == VAL_F32) return __ldg(static_cast<const float *>(val) + e);
+  else return __bfloat162float(static_cast<const __nv_bfloat16 *>(val)[e]);
+}
+
 template <int P, int KIND>
 __global__ void __launch_bounds__(256) k_step_csr(StateView s, CsrView J, StepTables t, int n) {
   const int warps_per_row = s.Cp / kColsPerWarp;
@@ -25,37 +32,54 @@ __global__ void __launch_bounds__(256) k_step_csr(StateView s, CsrView J, StepTa
   const int c4 = (wid - i * warps_per_row) * kColsPerWarp + lane * kColsPerLane;
   const int8_t *Fin = s.f_of(n);
   int8_t *Fout = s.f_of(n + 1);
-  const int e0 = J.row_ptr[i], e1 = J.row_ptr[i + 1];
+  // state loads first: they do not depend on the product
+  const size_t off = size_t(i) * s.Cp + c4;
+  const float4 xv = *reinterpret_cast<const float4 *>(s.x + off);
+  const float4 yv = *reinterpret_cast<const float4 *>(s.y + off);
+  const float hi = __ldg(J.h + i);
+  const int e0 = __ldg(J.row_ptr + i), deg = __ldg(J.row_ptr + i + 1) - e0;
+  const int8_t *Fc = Fin + c4;
+  uint32_t acc = 0;                  // VAL_PM1: 4 packed int8 sums
+  float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
+  // The row's (col, J) entries are read 32 at a time, one per lane, and
+  // broadcast by shuffle; the F gathers of 8 entries are issued together.
+  for (int base = 0; base < deg; base += 32) {
+    const int cnt = min(32, deg - base);
+    int my_col = 0;
+    float my_w = 0.f;
+    if (lane < cnt) {
+      my_col = __ldg(J.col + e0 + base + lane);
+      my_w = load_val<KIND>(J.val, e0 + base + lane);
+    }
+    for (int q = 0; q < cnt; q += 8) {
+      uint32_t f4[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int j = __shfl_sync(0xffffffffu, my_col, q + u);
+        f4[u] = (q + u < cnt) ? __ldg(reinterpret_cast<const uint32_t *>(Fc + size_t(j) * s.Cp)) : 0u;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float w = __shfl_sync(0xffffffffu, my_w, q + u);
+        if constexpr (KIND == VAL_PM1) {
+          acc = (w > 0.f) ? __vadd4(acc, f4[u]) : __vsub4(acc, f4[u]);  // f4 = 0 past the row end
+        } else {
+          g0 = fmaf(w, sbyte(f4[u], 0), g0);
+          g1 = fmaf(w, sbyte(f4[u], 1), g1);
+          g2 = fmaf(w, sbyte(f4[u], 2), g2);
+          g3 = fmaf(w, sbyte(f4[u], 3), g3);
+        }
+      }
+    }
+  }
   float G[4];
   if constexpr (KIND == VAL_PM1) {
-    const int8_t *v = static_cast<const int8_t *>(J.val);
-    uint32_t acc = 0;
-    for (int e = e0; e < e1; ++e) {
-      const int j = __ldg(J.col + e);
-      const uint32_t f4 = __ldg(reinterpret_cast<const uint32_t *>(Fin + size_t(j) * s.Cp + c4));
-      acc = (__ldg(v + e) > 0) ? __vadd4(acc, f4) : __vsub4(acc, f4);
-    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) G[q] = sbyte(acc, q);
   } else {
-    float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
-    for (int e = e0; e < e1; ++e) {
-      const int j = __ldg(J.col + e);
-      float w;
-      if constexpr (KIND == VAL_F32) {
-        w = __ldg(static_cast<const float *>(J.val) + e);
-      } else {
-        w = __bfloat162float(static_cast<const __nv_bfloat16 *>(J.val)[e]);
-      }
-      const uint32_t f4 = __ldg(reinterpret_cast<const uint32_t *>(Fin + size_t(j) * s.Cp + c4));
-      g0 = fmaf(w, sbyte(f4, 0), g0);
-      g1 = fmaf(w, sbyte(f4, 1), g1);
-      g2 = fmaf(w, sbyte(f4, 2), g2);
-      g3 = fmaf(w, sbyte(f4, 3), g3);
-    }
     G[0] = g0; G[1] = g1; G[2] = g2; G[3] = g3;
   }
-  sb_update4<P>(s, t, n, i, c4, G, __ldg(J.h + i), Fout);
+  sb_update4<P>(s, t, n, i, c4, G, hi, xv, yv, Fout);
 }
 
 template <int P>
