@@ -216,6 +216,55 @@ int sbqa_get_state(sbqa_problem *p, float *x, float *y, int32_t *step_done);
 int sbqa_set_state(sbqa_problem *p, const float *x, const float *y,
                    int32_t step_done);
 
+/* ---- energies without device allocation -------------------------------- */
+/*
+ * sbqa_energies_csr_noalloc -- Ising energies of caller-supplied spin
+ * configurations for a CSR instance, using no device allocation at all.
+ * The paper has no counterpart: this is a service entry point for callers
+ * that cannot call cudaMalloc where they need energies, e.g. code that is in
+ * the middle of capturing a CUDA graph (allocation is not a capturable
+ * operation), real-time loops that must never block in the allocator, and
+ * host frameworks that own all device memory through their own pool.
+ *
+ * Every pointer except `stream` is a DEVICE pointer owned by the caller:
+ *   n         spins, >= 1
+ *   row_ptr   int32[n+1], col_idx int32[nnz]: the CSR pattern (as in
+ *             sbqa_create_problem_csr, symmetric, no diagonal; not re-checked)
+ *   val_i32 / val_f64   couplings, exactly one non-NULL: int32 for integer
+ *             instances (exact int64 energies), double otherwise
+ *   h_i64 / h_f64       fields matching the value type, or NULL for h = 0
+ *   spins     int8 [n][ld], +1/-1; column c (0 <= c < count) is one
+ *             configuration (the spin-major layout of the solver's state)
+ *   ld        row stride of spins in bytes, >= count
+ *   count     number of configurations, >= 1
+ *   energy_int  int64[count] or NULL (integer instances only)
+ *   energy    double[count]; required for real instances, optional otherwise
+ *   stream    cudaStream_t (NULL = legacy default stream); the call is
+ *             asynchronous on it
+ * E(s) = -sum_{i<j} J_ij s_i s_j - sum_i h_i s_i, summed in a fixed order
+ * (the same as the solver's readout), so results match sbqa_get_energies.
+ *
+ * Memory: the partial sums live in one file-scope device array of 4 MiB that
+ * is part of the library image; every GPU that loads the library reserves it
+ * until the process exits.  A call needs ceil(n/32) * ceil(count/128)*128
+ * partial sums of 8 bytes; larger requests fail with SBQA_ERR_UNSUPPORTED
+ * (e.g. n = 4096 allows up to 4096 configurations).  Nothing is allocated,
+ * freed or cleared: every scratch entry that is read was written earlier in
+ * the same call.
+ * All calls share that array and it keeps the last call's contents, so calls
+ * whose kernels overlap on the GPU (different streams, or several host
+ * threads) race and must be ordered by the caller.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.
+ * Errors: INVALID_ARG, UNSUPPORTED (size beyond the scratch), CUDA.
+ */
+int sbqa_energies_csr_noalloc(int32_t n, const int32_t *row_ptr,
+                              const int32_t *col_idx, const int32_t *val_i32,
+                              const double *val_f64, const int64_t *h_i64,
+                              const double *h_f64, const int8_t *spins,
+                              int32_t ld, int32_t count, int64_t *energy_int,
+                              double *energy, void *stream);
+
 /* ---- errors ----------------------------------------------------------- */
 const char *sbqa_strerror(int status);
 /* Detail message of the calling thread's last failed call ("" if none). */

@@ -37,7 +37,7 @@ EXPORTS = (
     "sbqa_get_problem_info", "sbqa_default_params", "sbqa_set_schedule", "sbqa_run",
     "sbqa_run_begin", "sbqa_run_advance", "sbqa_run_finish", "sbqa_synchronize",
     "sbqa_get_best", "sbqa_get_energies", "sbqa_get_state", "sbqa_set_state",
-    "sbqa_strerror", "sbqa_last_error", "sbqa_version",
+    "sbqa_strerror", "sbqa_last_error", "sbqa_version", "sbqa_energies_csr_noalloc",
 )
 
 
@@ -89,6 +89,7 @@ def _load():
         "sbqa_strerror": (ctypes.c_char_p, [ctypes.c_int]),
         "sbqa_last_error": (ctypes.c_char_p, []),
         "sbqa_version": (ctypes.c_int, []),
+        "sbqa_energies_csr_noalloc": (ctypes.c_int, [i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -262,3 +263,15 @@ def set_state(pb: Problem, x, y, step_done):
     y = np.ascontiguousarray(y, dtype=np.float32)
     _check(lib.sbqa_set_state(pb.handle, _p(x, ctypes.c_float), _p(y, ctypes.c_float), int(step_done)),
            "set_state")
+
+
+def energies_csr_noalloc(n, row_ptr, col_idx, spins, ld, count, val_i32=0, val_f64=0, h_i64=0, h_f64=0,
+                         energy_int=0, energy=0, stream=None):
+    """Energies of ``count`` spin configurations with no device allocation.
+
+    Every array argument is a device address (an int, e.g. ``tensor.data_ptr()``;
+    0 for NULL); see sbqa_energies_csr_noalloc in include/sbqa.h."""
+    _check(lib.sbqa_energies_csr_noalloc(int(n), row_ptr, col_idx, val_i32 or None, val_f64 or None,
+                                         h_i64 or None, h_f64 or None, spins, int(ld), int(count),
+                                         energy_int or None, energy or None, _stream(stream) or None),
+           "energies_csr_noalloc")

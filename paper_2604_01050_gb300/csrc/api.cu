@@ -70,6 +70,8 @@ struct DevBuf {
 
 }  // namespace
 
+int sbqa::set_error(int code, const std::string &msg) { return fail(code, msg); }
+
 struct sbqa_problem {
   int device = 0;
   int32_t n = 0;

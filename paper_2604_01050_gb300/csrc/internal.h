@@ -12,6 +12,7 @@
 //   kc, kx     dt * c0 / P,  dt * a0 / P
 #pragma once
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 
@@ -76,6 +77,10 @@ struct BestView {
   int8_t *best_spins;    // [R][N]
   int32_t *have_best;    // [R]
 };
+
+// Records msg as the calling thread's detail message (sbqa_last_error) and
+// returns code.
+int set_error(int code, const std::string &msg);
 
 // ---- launchers (return cudaGetLastError() of the launch) ----
 cudaError_t launch_init(const StateView &s, uint64_t seed, float amp, float delta0,
