@@ -176,6 +176,160 @@ def run_reference(args, cfg):
     return 0
 
 
+# ------------------------------------------------------------------ serving stream
+def run_serving(args):
+    """Poisson stream through the batching engine: p50/p99 latency."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2604_01050_gb300 import build as _b
+    _b.build()
+    from paper_2604_01050_gb300 import serving
+    pool = serving.make_pool(12, seed=0)
+    reqs = serving.make_requests(pool, args.requests, steps=2000, R=16, seed=1)
+    stream = torch.cuda.Stream()
+    serving.run_stream(reqs[:6], None, stream=stream)  # warm-up (autotune, first launches)
+    closed = serving.run_stream(reqs, None, stream=stream)
+    capacity = len(reqs) / closed["makespan_s"]
+    loads = {}
+    for f in (0.5, 0.8):
+        out = serving.run_stream(reqs, f * capacity, stream=stream, seed=int(10 * f))
+        loads["%.1fx" % f] = serving.summary(out)
+    head = loads["0.8x"]
+    line = {"metric": "p99 solve latency", "value": head["p99_s"], "unit": "s", "n_gpus": 1,
+            "steps": len(reqs), "warmup": 6, "ms_per_step": 1e3 * head["mean_s"], "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "Poisson stream of SK +-1 (dense) and 3D lattice (CSR) requests, "
+                                   "N log-uniform in 64..8192, P in {8,16,32}, R=16, 2000 steps; "
+                                   "continuous batching engine, chunk 50 steps",
+                       "requests": len(reqs), "capacity_req_per_s": capacity,
+                       "closed_loop_updates_per_s": closed["updates"] / closed["makespan_s"]},
+            "p50_s": head["p50_s"], "loads": loads, "gpu_launches": None}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ time-to-epsilon
+def plain_fp32_solve(J, h, S, P, R, x0, y0, tables, kc, kx, dev):
+    """The plain per-instance FP32 GPU path: per step one library product
+    (torch sparse/dense matmul) and separate elementwise kernels, state in
+    [N][R*P] FP32 -- the baseline the fused path is compared with."""
+    import torch
+    x = x0.clone(); y = y0.clone()
+    ka, dl, kj = tables
+    N = x.shape[0]
+    C = R * P
+    hcol = torch.zeros(N, 1, device=dev) if h is None else h.view(N, 1)
+    kjcols = kj.repeat_interleave(P, dim=1)  # [S][C]
+    idx = torch.arange(C, device=dev)
+    km = (idx // P) * P + (idx % P + P - 1) % P
+    kp = (idx // P) * P + (idx % P + 1) % P
+    F = torch.where(x.abs() > dl[0], torch.sign(x), torch.zeros_like(x))
+    for n in range(S):
+        G = J @ F
+        y = y + kc * (G + hcol) - ka[n] * x + kjcols[n] * (x[:, km] + x[:, kp])
+        x = x + kx * y
+        wall = x.abs() > 1
+        x = torch.where(wall, torch.sign(x), x)
+        y = torch.where(wall, torch.zeros_like(y), y)
+        F = torch.where(x.abs() > dl[n + 1], torch.sign(x), torch.zeros_like(x))
+    return x
+
+
+def schedule_tables(S, P, R, beta, alpha, gamma0=1.0, delta_slope=0.7, a0=1.0, dt=0.5):
+    """FP32 step coefficients of the plain path, from the schedule of Sec. II A
+    (a(t) = t/T, Gamma_x(t) and J_perp(t) of Eq. 5, Delta(t) of Eq. 8)."""
+    tau = np.arange(S + 1) / S
+    dl = delta_slope * tau
+    ka = dt * (a0 - tau[:S]) / P
+    gam = gamma0 * ((1.0 - tau[:S, None]) ** alpha[None, :] + 1e-5)
+    jp = -np.log(np.tanh(beta[None, :] * gam / P)) / (2.0 * beta[None, :])
+    return ka, dl, dt * jp
+
+
+def tte_seconds(tau, p, p_target=0.99):
+    """Eq. 10; p = 0 gives inf, p >= p_target gives tau."""
+    import math
+    if p <= 0.0:
+        return math.inf
+    if p >= p_target:
+        return tau
+    return tau * math.log(1.0 - p_target) / math.log(1.0 - p)
+
+
+def run_tte(args):
+    """Time-to-epsilon (Eq. 10, p_target = 0.99) of the fused path and of the
+    plain FP32 path on the same instance, schedule and initial states."""
+    import math
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    from paper_2604_01050_gb300 import build as _b
+    _b.build()
+    import paper_2604_01050_gb300 as sb
+    L, P, R, S, eps = args.tte_L, 16, 64, args.tte_steps, args.eps
+    n, rp, col, val, hh = workloads.cubic_lattice(L, 3)
+    beta, alpha = workloads.autotune_params(R, 3)
+    prob = sb.create_problem_csr(n, rp, col, val, hh)
+    sb.set_schedule(prob, beta, alpha, gamma0=args.gamma0)
+    # reference energy: best over long, wide searches with the fused path
+    E0 = math.inf
+    for sd in range(8):
+        sb.run(prob, 20 * S, P, R, seed=900 + sd)
+        E0 = min(E0, float(sb.get_best(prob)["energy"].min()))
+    target = E0 + eps * abs(E0)
+    reps = 5
+    # fused path: whole solves through the C ABI (init, steps, readout, best to host)
+    sb.run(prob, S, P, R, seed=7)
+    sb.get_best(prob)
+    t0 = time.perf_counter()
+    hits = []
+    for k in range(reps):
+        sb.run(prob, S, P, R, seed=7 + k)
+        hits.append(sb.get_best(prob)["energy"] <= target)
+    t_fused = (time.perf_counter() - t0) / reps
+    p_fused = float(np.mean(hits))
+    # plain path: same initial states and tables, FP32 torch ops per step
+    ka, dl, kj = schedule_tables(S, P, R, beta, alpha, gamma0=args.gamma0)
+    c0 = 0.5 * math.sqrt(n / float(np.sum(val ** 2)))
+    kc, kx = 0.5 * c0 / P, 0.5 * 1.0 / P
+    tabs = (torch.tensor(ka, dtype=torch.float32, device=dev), torch.tensor(dl, dtype=torch.float32, device=dev),
+            torch.tensor(kj, dtype=torch.float32, device=dev))
+    Jt = torch.sparse_csr_tensor(torch.tensor(rp), torch.tensor(col.astype(np.int64)), torch.tensor(val),
+                                 size=(n, n), dtype=torch.float32, device=dev)
+    starts = []
+    for k in range(reps):
+        sb.run_begin(prob, S, P, R, seed=7 + k)
+        x0, y0, _ = sb.get_state(prob)
+        starts.append((torch.from_numpy(x0.reshape(R * P, n).T.copy()).to(dev),
+                       torch.from_numpy(y0.reshape(R * P, n).T.copy()).to(dev)))
+    plain_fp32_solve(Jt, None, 20, P, R, starts[0][0], starts[0][1], tabs, kc, kx, dev)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hits = []
+    for k in range(reps):
+        xf = plain_fp32_solve(Jt, None, S, P, R, starts[k][0], starts[k][1], tabs, kc, kx, dev)
+        spins = torch.where(xf >= 0, 1.0, -1.0)
+        e = -0.5 * (spins * (Jt @ spins)).sum(dim=0).double()
+        best = e.view(R, P).min(dim=1).values.cpu().numpy()
+        hits.append(best <= target)
+    t_plain = (time.perf_counter() - t0) / reps
+    p_plain = float(np.mean(hits))
+    tte_f = tte_seconds(t_fused / R, p_fused)
+    tte_p = tte_seconds(t_plain / R, p_plain)
+    line = {"metric": "time-to-epsilon", "value": tte_f, "unit": "s", "n_gpus": 1, "steps": reps, "warmup": 1,
+            "ms_per_step": 1e3 * t_fused, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "3D cubic lattice L=%d (N=%d), J=+-1, P=%d, R=%d, %d steps, gamma0=%g"
+                                   % (L, n, P, R, S, args.gamma0),
+                       "epsilon": eps, "E0": E0, "E0_source": "best of 8 x %d runs of %d steps" % (R, 20 * S),
+                       "p_target": 0.99},
+            "fused": {"s_per_solve": t_fused, "p_success": p_fused, "tte_s": tte_f},
+            "plain_fp32_torch": {"s_per_solve": t_plain, "p_success": p_plain, "tte_s": tte_p},
+            "tte_speedup": (tte_p / tte_f) if math.isfinite(tte_p) and math.isfinite(tte_f) else None}
+    print(json.dumps(line))
+    return 0
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -183,10 +337,19 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default=DEFAULT, choices=sorted(CONFIGS))
+    ap.add_argument("--config", default=DEFAULT, choices=sorted(CONFIGS) + ["serving", "tte"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
+    ap.add_argument("--requests", type=int, default=48, help="serving: requests in the stream")
+    ap.add_argument("--eps", type=float, default=0.01, help="tte: target optimality gap")
+    ap.add_argument("--gamma0", type=float, default=16.0, help="tte: Gamma_x(0)")
+    ap.add_argument("--tte-L", type=int, default=10)
+    ap.add_argument("--tte-steps", type=int, default=1000)
     args = ap.parse_args()
+    if args.config == "serving":
+        return run_serving(args)
+    if args.config == "tte":
+        return run_tte(args)
     cfg = CONFIGS[args.config]
     if args.impl == "reference":
         return run_reference(args, cfg)
@@ -256,6 +419,7 @@ def main():
             sb.run(prob, 0, P, R, seed=seed0 + k, stream=stream)
             ev0[k][1].record(stream)
         torch.cuda.synchronize()
+    info = prob.info()
     ms = [a.elapsed_time(b) for a, b in ev]
     ms0 = [a.elapsed_time(b) for a, b in ev0]
     ms_solve = statistics.mean(ms)
@@ -314,7 +478,10 @@ def main():
                    "precision": cfg["prec"], "l2": "flushed (512 MB write) before every timed solve; "
                                                    "state (%.0f MB) stays L2-resident within a solve"
                                                    % (N * P * R * 10 / 1e6),
-                   "parallelism": "independent runs per GPU (weak scaling)"},
+                   "parallelism": "independent runs per GPU (weak scaling)",
+                   "step_kernel": ["csr", "dense_cuda_core", "dense_tcgen05_fp8"][info.step_kernel],
+                   "csr_variant": info.step_variant,
+                   "autotune_ms_per_step": [round(v, 5) for v in info.variant_ms]},
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved_gbs / hbm_peak, "traffic": None, "kernel": "k_step_csr",
                      "step_ms": step_ms, "peak_source": peak_src,

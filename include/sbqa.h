@@ -106,6 +106,13 @@ typedef struct {
     int32_t is_integer; /* all J_ij and h_i are integers                   */
     int32_t max_abs_j;  /* max |J_ij| if integer, else -1                  */
     double c0_auto;     /* default c0 = 0.5 sqrt(n / sum_ij J_ij^2)        */
+    int32_t step_kernel;  /* coupling-product kernel of the last run: 0 CSR,
+                             1 dense CUDA cores, 2 dense tcgen05 FP8; -1 none */
+    int32_t step_variant; /* CSR kernel variant picked by the autotuner:
+                             4 << v consecutive replica columns per lane;
+                             -1 before the first run                      */
+    float variant_ms[4];  /* autotuner timing of each CSR variant (ms per
+                             step; 0 = not timed / not eligible)           */
 } sbqa_problem_info;
 
 int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info);
@@ -215,6 +222,62 @@ int sbqa_get_energies(sbqa_problem *p, double *energy, int64_t *energy_int);
 int sbqa_get_state(sbqa_problem *p, float *x, float *y, int32_t *step_done);
 int sbqa_set_state(sbqa_problem *p, const float *x, const float *y,
                    int32_t step_done);
+
+/* ---- batching engine ---------------------------------------------------- */
+/*
+ * Continuous batching of many solves on one GPU (no counterpart in the
+ * paper, which runs the repetitions of one instance in parallel, Sec. II B;
+ * the engine extends that to many instances).  A request is a problem handle
+ * (with its schedule set) plus steps, P, R and seed; its result is the
+ * per-run best of sbqa_get_best.  Requests are admitted in arrival order
+ * whenever a slot and room in the engine's device arena are free; their
+ * state stays resident in the arena; at every sbqa_engine_step all active
+ * requests advance by up to `chunk_steps` steps (CSR requests together in
+ * one batched launch per step); finished requests are read out and leave.
+ * A request's result is bit-identical to sbqa_run of the same request.
+ * The problem handles must outlive their requests.  One engine is driven by
+ * one host thread.
+ *
+ * sbqa_engine_create
+ *   arena_bytes  device memory reserved for request state (>= 1 MiB)
+ *   max_slots    requests active at the same time (1..4096)
+ *   chunk_steps  steps per sbqa_engine_step (>= 1)
+ * Errors: INVALID_ARG, OOM.
+ */
+typedef struct sbqa_engine sbqa_engine;
+
+int sbqa_engine_create(int64_t arena_bytes, int32_t max_slots,
+                       int32_t chunk_steps, sbqa_engine **out);
+void sbqa_engine_destroy(sbqa_engine *e);
+
+/* Queues a request; *id receives its number (0, 1, ... in submit order).
+ * steps >= 1; P and R as for sbqa_run.  Errors: STATE (no schedule),
+ * INVALID_ARG, UNSUPPORTED, OOM (request larger than the arena). */
+int sbqa_engine_submit(sbqa_engine *e, sbqa_problem *p, int32_t steps,
+                       int32_t P, int32_t R, uint64_t seed, int32_t *id);
+
+/* Admits what fits, advances every active request by up to chunk_steps
+ * steps on `stream` (a cudaStream_t), reads out the finished ones and waits
+ * for the device.  *n_done receives how many finished; the first `cap` of
+ * their ids go to done_ids (host, may be NULL when cap = 0).
+ * Errors: CUDA, TIMEOUT. */
+int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done,
+                     int32_t *done_ids, int32_t cap);
+
+/* Result of a finished request (host buffers, any may be NULL):
+ * spins R*N int8, energy R doubles, energy_int R int64 (integer instances),
+ * replica R int32 -- as sbqa_get_best.  Errors: INVALID_ARG, STATE. */
+int sbqa_engine_result(sbqa_engine *e, int32_t id, int8_t *spins,
+                       double *energy, int64_t *energy_int,
+                       int32_t *replica);
+
+typedef struct {
+    int32_t queued, active, finished;
+    int64_t arena_bytes, arena_used;
+    int64_t updates_issued; /* replica-spin updates advanced so far */
+} sbqa_engine_stats_t;
+
+int sbqa_engine_stats(const sbqa_engine *e, sbqa_engine_stats_t *s);
 
 /* ---- energies without device allocation -------------------------------- */
 /*

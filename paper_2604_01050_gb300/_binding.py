@@ -38,6 +38,8 @@ EXPORTS = (
     "sbqa_run_begin", "sbqa_run_advance", "sbqa_run_finish", "sbqa_synchronize",
     "sbqa_get_best", "sbqa_get_energies", "sbqa_get_state", "sbqa_set_state",
     "sbqa_strerror", "sbqa_last_error", "sbqa_version", "sbqa_energies_csr_noalloc",
+    "sbqa_engine_create", "sbqa_engine_destroy", "sbqa_engine_submit", "sbqa_engine_step",
+    "sbqa_engine_result", "sbqa_engine_stats",
 )
 
 
@@ -50,7 +52,14 @@ class SBQAError(RuntimeError):
 class ProblemInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("is_dense", ctypes.c_int32), ("nnz", ctypes.c_int64),
                 ("is_integer", ctypes.c_int32), ("max_abs_j", ctypes.c_int32),
-                ("c0_auto", ctypes.c_double)]
+                ("c0_auto", ctypes.c_double), ("step_kernel", ctypes.c_int32),
+                ("step_variant", ctypes.c_int32), ("variant_ms", ctypes.c_float * 4)]
+
+
+class EngineStats(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_int32), ("active", ctypes.c_int32), ("finished", ctypes.c_int32),
+                ("arena_bytes", ctypes.c_int64), ("arena_used", ctypes.c_int64),
+                ("updates_issued", ctypes.c_int64)]
 
 
 class Params(ctypes.Structure):
@@ -90,6 +99,12 @@ def _load():
         "sbqa_last_error": (ctypes.c_char_p, []),
         "sbqa_version": (ctypes.c_int, []),
         "sbqa_energies_csr_noalloc": (ctypes.c_int, [i32, vp, vp, vp, vp, vp, vp, vp, i32, i32, vp, vp, vp]),
+        "sbqa_engine_create": (ctypes.c_int, [i64, i32, i32, P(vp)]),
+        "sbqa_engine_destroy": (None, [vp]),
+        "sbqa_engine_submit": (ctypes.c_int, [vp, vp, i32, i32, i32, u64, P(i32)]),
+        "sbqa_engine_step": (ctypes.c_int, [vp, vp, P(i32), P(i32), i32]),
+        "sbqa_engine_result": (ctypes.c_int, [vp, i32, P(ctypes.c_int8), P(dbl), P(i64), P(i32)]),
+        "sbqa_engine_stats": (ctypes.c_int, [vp, P(EngineStats)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -275,3 +290,65 @@ def energies_csr_noalloc(n, row_ptr, col_idx, spins, ld, count, val_i32=0, val_f
                                          h_i64 or None, h_f64 or None, spins, int(ld), int(count),
                                          energy_int or None, energy or None, _stream(stream) or None),
            "energies_csr_noalloc")
+
+
+class Engine:
+    """Owning wrapper of one ``sbqa_engine*`` (continuous batching)."""
+
+    def __init__(self, handle):
+        self._h = ctypes.c_void_p(handle)
+        self.requests = {}  # id -> (problem, R, N)
+
+    def __del__(self):
+        self.destroy()
+
+    def destroy(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib.sbqa_engine_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    @property
+    def handle(self):
+        return self._h
+
+
+def engine_create(arena_bytes, max_slots, chunk_steps) -> Engine:
+    out = ctypes.c_void_p()
+    _check(lib.sbqa_engine_create(int(arena_bytes), int(max_slots), int(chunk_steps), ctypes.byref(out)),
+           "engine_create")
+    return Engine(out.value)
+
+
+def engine_submit(eng: Engine, pb: Problem, steps, P, R, seed=0) -> int:
+    rid = ctypes.c_int32()
+    _check(lib.sbqa_engine_submit(eng.handle, pb.handle, int(steps), int(P), int(R), ctypes.c_uint64(seed),
+                                  ctypes.byref(rid)), "engine_submit")
+    eng.requests[rid.value] = (pb, int(R), pb.n, bool(pb.info().is_integer))
+    return rid.value
+
+
+def engine_step(eng: Engine, stream=None, cap=4096):
+    n = ctypes.c_int32()
+    ids = np.empty(cap, dtype=np.int32)
+    _check(lib.sbqa_engine_step(eng.handle, _stream(stream) or None, ctypes.byref(n), _p(ids, ctypes.c_int32),
+                                int(cap)), "engine_step")
+    return ids[:min(n.value, cap)].tolist()
+
+
+def engine_result(eng: Engine, rid):
+    if rid not in eng.requests:
+        _check(lib.sbqa_engine_result(eng.handle, int(rid), None, None, None, None), "engine_result")
+    _, R, N, _ = eng.requests[rid]
+    spins = np.empty((R, N), dtype=np.int8)
+    e = np.empty(R)
+    ei = np.zeros(R, dtype=np.int64)
+    k = np.empty(R, dtype=np.int32)
+    _check(lib.sbqa_engine_result(eng.handle, int(rid), _p(spins, ctypes.c_int8), _p(e, ctypes.c_double),
+                                  _p(ei, ctypes.c_int64), _p(k, ctypes.c_int32)), "engine_result")
+    return {"spins": spins, "energy": e, "energy_int": ei, "replica": k}
+
+
+def engine_stats(eng: Engine):
+    st = EngineStats()
+    _check(lib.sbqa_engine_stats(eng.handle, ctypes.byref(st)), "engine_stats")
+    return {f: getattr(st, f) for f, _ in EngineStats._fields_}

@@ -17,6 +17,7 @@
 
 #include "../../include/sbqa.h"
 #include "internal.h"
+#include "problem.h"
 
 using namespace sbqa;
 
@@ -40,25 +41,6 @@ struct DeviceGuard {
   }
 };
 
-template <typename T>
-struct DevBuf {
-  T *p = nullptr;
-  size_t n = 0;
-  cudaError_t alloc(size_t count) {
-    if (count <= n && p) return cudaSuccess;
-    release();
-    if (count == 0) return cudaSuccess;
-    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&p), count * sizeof(T));
-    if (e == cudaSuccess) n = count;
-    else p = nullptr;
-    return e;
-  }
-  void release() {
-    if (p) cudaFree(p);
-    p = nullptr;
-    n = 0;
-  }
-};
 
 #define SBQA_CUDA(call)                                                                   \
   do {                                                                                    \
@@ -72,126 +54,23 @@ struct DevBuf {
 
 int sbqa::set_error(int code, const std::string &msg) { return fail(code, msg); }
 
-struct sbqa_problem {
-  int device = 0;
-  int32_t n = 0;
-  bool dense = false;
-  int64_t nnz = 0;
-  bool is_integer = false, is_pm1 = false, j_integer = false;
-  int32_t max_abs_j = -1;
-  int32_t max_degree = 0;
-  double c0_auto = 0.5;
-  bool h_zero = true;
+sbqa_problem::~sbqa_problem() {
+  DeviceGuard g(device);
+  cudaDeviceSynchronize();  // no kernel of this handle may still use the buffers
+  if (graph) cudaGraphExecDestroy(graph);
+  if (cap_stream) cudaStreamDestroy(cap_stream);
+  if (tc_plan) tc_plan_free(tc_plan);
+  d_J8.release(); d_FT.release(); d_err.release();
+  d_row_ptr.release(); d_col.release(); d_col_pm1.release(); d_npos.release(); d_val_f32.release();
+  d_val_bf16.release(); d_dense_f32.release(); d_h.release(); d_e_i32.release();
+  d_e_f64.release(); d_h_i64.release(); d_h_f64.release(); d_x.release(); d_y.release();
+  d_F0.release(); d_F1.release(); d_Sg.release(); d_ka.release(); d_dl.release();
+  d_kj.release(); d_ei.release(); d_part_i.release(); d_best_ei.release(); d_ef.release();
+  d_part_f.release(); d_best_e.release(); d_best_k.release(); d_best_step.release();
+  d_have.release(); d_best_spins.release();
+}
 
-  // host copies (CSR for sparse, row-major for dense)
-  std::vector<int64_t> row_ptr;
-  std::vector<int32_t> col;
-  std::vector<double> val;  // CSR values or dense N*N
-  std::vector<double> h;
 
-  // device: product operands
-  DevBuf<int32_t> d_row_ptr, d_col;
-  DevBuf<int8_t> d_val_i8;
-  DevBuf<float> d_val_f32;
-  DevBuf<__nv_bfloat16> d_val_bf16;
-  DevBuf<float> d_dense_f32;  // dense J for the CUDA-core path
-  int dense_prec = -1;        // precision the dense FP32 copy was built for
-  // dense integer J on the tensor cores: e4m3 copies padded to Kp
-  bool use_tc = false;
-  int Kp = 0;
-  DevBuf<uint8_t> d_J8, d_FT;
-  void *tc_plan = nullptr;
-  const void *tc_plan_ft = nullptr;  // FT buffer the plan was made for
-  int tc_plan_cp = 0;
-  DevBuf<int> d_err;
-  DevBuf<float> d_h;
-  // device: readout operands
-  DevBuf<int32_t> d_e_i32;
-  DevBuf<double> d_e_f64;
-  DevBuf<int64_t> d_h_i64;
-  DevBuf<double> d_h_f64;
-
-  // schedule
-  bool have_params = false;
-  sbqa_params prm{};
-  std::vector<double> beta, alpha;
-
-  // run state
-  int S = 0, P = 0, R = 0, C = 0, Cp = 0;
-  int step_done = 0;
-  bool begun = false, finished = false;
-  cudaStream_t stream = nullptr;
-  int kind = VAL_F32;  // sparse value kind in use
-  DevBuf<float> d_x, d_y;
-  DevBuf<int8_t> d_F0, d_F1, d_Sg;
-  DevBuf<float> d_ka, d_dl, d_kj;
-  DevBuf<int64_t> d_ei, d_part_i, d_best_ei;
-  DevBuf<double> d_ef, d_part_f, d_best_e;
-  DevBuf<int32_t> d_best_k, d_best_step, d_have;
-  DevBuf<int8_t> d_best_spins;
-  StepTables tables{};
-
-  // cached graph of the step loop + readouts of a full run
-  cudaGraphExec_t graph = nullptr;
-  cudaStream_t cap_stream = nullptr;
-  struct Key {
-    int S = -1, P = -1, R = -1, eval = -1, kind = -1, dense = -1, tc = -1;
-    float kc = 0.f, kx = 0.f;  // step constants are kernel arguments in the graph
-    const void *x = nullptr, *kj = nullptr;
-    bool operator==(const Key &o) const {
-      return S == o.S && P == o.P && R == o.R && eval == o.eval && kind == o.kind &&
-             dense == o.dense && tc == o.tc && x == o.x && kj == o.kj &&
-             std::memcmp(&kc, &o.kc, sizeof(float)) == 0 && std::memcmp(&kx, &o.kx, sizeof(float)) == 0;
-    }
-  } graph_key;
-
-  ~sbqa_problem() {
-    DeviceGuard g(device);
-    cudaDeviceSynchronize();  // no kernel of this handle may still use the buffers
-    if (graph) cudaGraphExecDestroy(graph);
-    if (cap_stream) cudaStreamDestroy(cap_stream);
-    if (tc_plan) tc_plan_free(tc_plan);
-    d_J8.release(); d_FT.release(); d_err.release();
-    d_row_ptr.release(); d_col.release(); d_val_i8.release(); d_val_f32.release();
-    d_val_bf16.release(); d_dense_f32.release(); d_h.release(); d_e_i32.release();
-    d_e_f64.release(); d_h_i64.release(); d_h_f64.release(); d_x.release(); d_y.release();
-    d_F0.release(); d_F1.release(); d_Sg.release(); d_ka.release(); d_dl.release();
-    d_kj.release(); d_ei.release(); d_part_i.release(); d_best_ei.release(); d_ef.release();
-    d_part_f.release(); d_best_e.release(); d_best_k.release(); d_best_step.release();
-    d_have.release(); d_best_spins.release();
-  }
-
-  StateView state() const {
-    StateView s;
-    s.N = n; s.C = C; s.Cp = Cp; s.P = P; s.R = R;
-    s.x = d_x.p; s.y = d_y.p;
-    s.F[0] = d_F0.p; s.F[1] = d_F1.p;
-    s.Sg = d_Sg.p;
-    return s;
-  }
-  CsrView csr() const {
-    CsrView v;
-    v.row_ptr = d_row_ptr.p; v.col = d_col.p; v.h = d_h.p; v.kind = kind;
-    v.val = kind == VAL_PM1 ? static_cast<const void *>(d_val_i8.p)
-          : kind == VAL_F32 ? static_cast<const void *>(d_val_f32.p)
-                            : static_cast<const void *>(d_val_bf16.p);
-    return v;
-  }
-  EnergyView energy() const {
-    EnergyView e;
-    e.is_integer = is_integer ? 1 : 0;
-    e.val_i32 = d_e_i32.p; e.val_f64 = d_e_f64.p; e.h_i64 = d_h_i64.p; e.h_f64 = d_h_f64.p;
-    return e;
-  }
-  BestView best() const {
-    BestView b;
-    b.e_int = d_ei.p; b.e_f64 = d_ef.p; b.part_int = d_part_i.p; b.part_f64 = d_part_f.p;
-    b.nblk = energy_row_blocks(n);
-    b.best_e_int = d_best_ei.p; b.best_e = d_best_e.p; b.best_k = d_best_k.p;
-    b.best_step = d_best_step.p; b.best_spins = d_best_spins.p; b.have_best = d_have.p;
-    return b;
-  }
-};
 
 namespace {
 
@@ -284,11 +163,23 @@ int prepare_sparse_values(sbqa_problem *p, int precision) {
   if (precision == SBQA_PREC_EXACT && (!p->j_integer || p->max_abs_j > 16))
     return fail(SBQA_ERR_UNSUPPORTED, "EXACT precision needs integer J with |J_ij| <= 16");
   p->kind = kind;
-  if (kind == VAL_PM1 && !p->d_val_i8.p && m) {
-    std::vector<int8_t> v(m);
-    for (size_t e = 0; e < m; ++e) v[e] = p->val[e] > 0 ? 1 : -1;
-    SBQA_CUDA(p->d_val_i8.alloc(m));
-    SBQA_CUDA(cudaMemcpy(p->d_val_i8.p, v.data(), m, cudaMemcpyHostToDevice));
+  if (kind == VAL_PM1 && !p->d_npos.p) {
+    // each row: columns of the +1 entries, then of the -1 entries
+    std::vector<int32_t> col(m), npos(p->n);
+    for (int i = 0; i < p->n; ++i) {
+      int64_t w = p->row_ptr[i];
+      for (int64_t e = p->row_ptr[i]; e < p->row_ptr[i + 1]; ++e)
+        if (p->val[e] > 0) col[w++] = p->col[e];
+      npos[i] = int32_t(w - p->row_ptr[i]);
+      for (int64_t e = p->row_ptr[i]; e < p->row_ptr[i + 1]; ++e)
+        if (p->val[e] < 0) col[w++] = p->col[e];
+    }
+    SBQA_CUDA(p->d_npos.alloc(p->n));
+    SBQA_CUDA(cudaMemcpy(p->d_npos.p, npos.data(), p->n * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (m) {
+      SBQA_CUDA(p->d_col_pm1.alloc(m));
+      SBQA_CUDA(cudaMemcpy(p->d_col_pm1.p, col.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
   } else if (kind == VAL_F32 && !p->d_val_f32.p && m) {
     std::vector<float> v(m);
     for (size_t e = 0; e < m; ++e) v[e] = float(p->val[e]);
@@ -389,41 +280,8 @@ int alloc_run(sbqa_problem *p, int S, int P, int R) {
   return SBQA_OK;
 }
 
-// FP64 schedule of Sec. II A rounded to the FP32 step coefficients.
 int build_tables(sbqa_problem *p) {
-  const sbqa_params &q = p->prm;
-  const int S = p->S, P = p->P, R = p->R;
-  const double c0 = q.c0 > 0.0 ? q.c0 : p->c0_auto;
-  std::vector<float> ka(std::max(S, 1), 0.f), dl(S + 1), kj(size_t(std::max(S, 1)) * R, 0.f);
-  for (int n = 0; n <= S; ++n) {
-    const double tau = S > 0 ? double(n) / double(S) : 0.0;
-    dl[n] = float(q.delta_slope * tau);                 // Delta(t) = 0.7 t/T
-    if (n < S) ka[n] = float(q.dt * (q.a0 - tau) / P);  // a(t) = t/T
-  }
-  for (int n = 0; n < S; ++n) {
-    const double tau = double(n) / double(S);
-    for (int r = 0; r < R; ++r) {
-      double jp = 0.0;
-      if (q.jperp_enable) {
-        const double b = p->beta.empty() ? 1.0 : p->beta[r];
-        const double a = p->alpha.empty() ? 1.0 : p->alpha[r];
-        const double gam = q.gamma0 * (std::pow(1.0 - tau, a) + 1e-5);  // Gamma_x(t), Eq. 5
-        jp = -std::log(std::tanh(b * gam / P)) / (2.0 * b);           // J_perp(t), Eq. 5
-      }
-      kj[size_t(n) * R + r] = float(q.dt * jp);
-    }
-  }
-  SBQA_CUDA(cudaMemcpyAsync(p->d_ka.p, ka.data(), ka.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream));
-  SBQA_CUDA(cudaMemcpyAsync(p->d_dl.p, dl.data(), dl.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream));
-  SBQA_CUDA(cudaMemcpyAsync(p->d_kj.p, kj.data(), kj.size() * sizeof(float), cudaMemcpyHostToDevice, p->stream));
-  p->tables.ka = p->d_ka.p;
-  p->tables.dl = p->d_dl.p;
-  p->tables.kj = p->d_kj.p;
-  p->tables.kc = float(q.dt * c0 / P);
-  p->tables.kx = float(q.dt * q.a0 / P);
-  p->tables.S = S;
-  p->tables.R = R;
-  return SBQA_OK;
+  return problem_build_tables(p, p->S, p->P, p->R, p->d_ka.p, p->d_dl.p, p->d_kj.p, &p->tables, p->stream);
 }
 
 cudaError_t issue_step(sbqa_problem *p, int n, cudaStream_t st) {
@@ -435,13 +293,55 @@ cudaError_t issue_step(sbqa_problem *p, int n, cudaStream_t st) {
     d.h = p->d_h.p;
     return launch_step_dense(s, d, p->tables, n, st);
   }
-  return launch_step_csr(s, p->csr(), p->tables, n, st);
+  return launch_step_csr(s, p->csr(), p->tables, n, p->csr_variant < 0 ? 0 : p->csr_variant, st);
+}
+
+// Autotuner of the CSR step kernel: times every variant on this problem's
+// shape (a few launches each, on the freshly allocated state buffers, before
+// the initial state is written) and keeps the fastest.  Results are cached
+// per handle and shape; skipped while the stream is being captured.
+int autotune_csr(sbqa_problem *p) {
+  if (p->dense) return SBQA_OK;
+  if (p->csr_variant >= 0 && p->csr_variant_cp == p->Cp && p->csr_variant_kind == p->kind) return SBQA_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  SBQA_CUDA(cudaStreamIsCapturing(p->stream, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return SBQA_OK;
+  const StateView s = p->state();
+  const CsrView J = p->csr();
+  const int nv = csr_step_variants(), reps = 8;
+  cudaEvent_t e0, e1;
+  SBQA_CUDA(cudaEventCreate(&e0));
+  SBQA_CUDA(cudaEventCreate(&e1));
+  float best_ms = 1e30f;
+  int best = 0;
+  const int n = 0;
+  for (int v = 0; v < nv && p->S > 0; ++v) {
+    if (!csr_step_variant_ok(v, p->Cp)) continue;
+    for (int w = 0; w < 2; ++w) SBQA_CUDA(launch_step_csr(s, J, p->tables, n, v, p->stream));
+    SBQA_CUDA(cudaEventRecord(e0, p->stream));
+    for (int w = 0; w < reps; ++w) SBQA_CUDA(launch_step_csr(s, J, p->tables, n, v, p->stream));
+    SBQA_CUDA(cudaEventRecord(e1, p->stream));
+    SBQA_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    SBQA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (v < 4) p->variant_ms[v] = ms / reps;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->csr_variant = best;
+  p->csr_variant_cp = p->Cp;
+  p->csr_variant_kind = p->kind;
+  return SBQA_OK;
 }
 
 cudaError_t issue_readout(sbqa_problem *p, int step, cudaStream_t st) {
   const StateView s = p->state();
   cudaError_t e = p->dense ? launch_energy_dense(s, p->energy(), p->best(), st)
-                           : launch_energy_csr(s, p->csr(), p->energy(), p->best(), st);
+                           : launch_energy_csr(s, p->csr_readout(), p->energy(), p->best(), st);
   if (e != cudaSuccess) return e;
   return launch_best(s, p->energy(), p->best(), step, st);
 }
@@ -473,6 +373,63 @@ int check_run_args(sbqa_problem *p, int32_t steps, int32_t P, int32_t R) {
 }
 
 }  // namespace
+
+// ---- helpers shared with the batching engine (problem.h) ----
+int sbqa::problem_check_run(sbqa_problem *p, int32_t steps, int32_t P, int32_t R) {
+  return check_run_args(p, steps, P, R);
+}
+
+int sbqa::problem_prepare_values(sbqa_problem *p) {
+  DeviceGuard g(p->device);
+  return p->dense ? prepare_dense_values(p, p->prm.precision) : prepare_sparse_values(p, p->prm.precision);
+}
+
+// FP64 schedule of Sec. II A rounded to the FP32 step coefficients.
+int sbqa::problem_build_tables(const sbqa_problem *p, int S, int P, int R, float *d_ka, float *d_dl, float *d_kj,
+                               StepTables *t, cudaStream_t st) {
+  const sbqa_params &q = p->prm;
+  const double c0 = q.c0 > 0.0 ? q.c0 : p->c0_auto;
+  std::vector<float> ka(std::max(S, 1), 0.f), dl(S + 1), kj(size_t(std::max(S, 1)) * R, 0.f);
+  for (int n = 0; n <= S; ++n) {
+    const double tau = S > 0 ? double(n) / double(S) : 0.0;
+    dl[n] = float(q.delta_slope * tau);                 // Delta(t) = 0.7 t/T
+    if (n < S) ka[n] = float(q.dt * (q.a0 - tau) / P);  // a(t) = t/T
+  }
+  for (int n = 0; n < S; ++n) {
+    const double tau = double(n) / double(S);
+    for (int r = 0; r < R; ++r) {
+      double jp = 0.0;
+      if (q.jperp_enable) {
+        const double b = p->beta.empty() ? 1.0 : p->beta[r];
+        const double a = p->alpha.empty() ? 1.0 : p->alpha[r];
+        const double gam = q.gamma0 * (std::pow(1.0 - tau, a) + 1e-5);  // Gamma_x(t), Eq. 5
+        jp = -std::log(std::tanh(b * gam / P)) / (2.0 * b);           // J_perp(t), Eq. 5
+      }
+      kj[size_t(n) * R + r] = float(q.dt * jp);
+    }
+  }
+  SBQA_CUDA(cudaMemcpyAsync(d_ka, ka.data(), ka.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+  SBQA_CUDA(cudaMemcpyAsync(d_dl, dl.data(), dl.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+  SBQA_CUDA(cudaMemcpyAsync(d_kj, kj.data(), kj.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+  t->ka = d_ka;
+  t->dl = d_dl;
+  t->kj = d_kj;
+  t->kc = float(q.dt * c0 / P);
+  t->kx = float(q.dt * q.a0 / P);
+  t->S = S;
+  t->R = R;
+  return SBQA_OK;
+}
+
+CsrView sbqa::problem_csr_view(const sbqa_problem *p) { return p->csr(); }
+CsrView sbqa::problem_csr_readout_view(const sbqa_problem *p) { return p->csr_readout(); }
+EnergyView sbqa::problem_energy_view(const sbqa_problem *p) { return p->energy(); }
+DenseView sbqa::problem_dense_view(const sbqa_problem *p) {
+  DenseView d;
+  d.J = p->d_dense_f32.p;
+  d.h = p->d_h.p;
+  return d;
+}
 
 extern "C" {
 
@@ -624,6 +581,9 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info) {
   info->is_integer = p->is_integer ? 1 : 0;
   info->max_abs_j = p->max_abs_j;
   info->c0_auto = p->c0_auto;
+  info->step_kernel = !p->begun ? -1 : (p->use_tc ? 2 : (p->dense ? 1 : 0));
+  info->step_variant = p->dense ? -1 : p->csr_variant;
+  for (int v = 0; v < 4; ++v) info->variant_ms[v] = p->variant_ms[v];
   return SBQA_OK;
 }
 
@@ -666,6 +626,7 @@ int sbqa_run_begin(sbqa_problem *p, int32_t steps, int32_t P, int32_t R, uint64_
   if (rc != SBQA_OK) return rc;
   if ((rc = alloc_run(p, steps, P, R)) != SBQA_OK) return rc;
   if ((rc = build_tables(p)) != SBQA_OK) return rc;
+  if ((rc = autotune_csr(p)) != SBQA_OK) return rc;
   const StateView s = p->state();
   SBQA_CUDA(cudaMemsetAsync(p->d_err.p, 0, sizeof(int), p->stream));
   SBQA_CUDA(launch_init(s, seed, float(p->prm.init_amp), 0.0f, p->stream));
@@ -704,7 +665,7 @@ int sbqa_run(sbqa_problem *p, int32_t steps, int32_t P, int32_t R, uint64_t seed
   sbqa_problem::Key key;
   key.S = steps; key.P = P; key.R = R; key.eval = p->prm.eval_every; key.kind = p->kind;
   key.dense = p->dense ? 1 : 0; key.x = p->d_x.p; key.kj = p->d_kj.p;
-  key.kc = p->tables.kc; key.kx = p->tables.kx; key.tc = p->use_tc ? 1 : 0;
+  key.kc = p->tables.kc; key.kx = p->tables.kx; key.tc = p->use_tc ? 1 : 0; key.variant = p->csr_variant;
   if (!(p->graph && p->graph_key == key)) {
     if (p->graph) {
       cudaGraphExecDestroy(p->graph);

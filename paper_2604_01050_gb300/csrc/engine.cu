@@ -1,0 +1,426 @@
+// engine.cu -- continuous-batching engine for many SBQA solves on one GPU.
+//
+// Requests (a problem handle with its schedule + steps, P, R, seed) queue in
+// arrival order.  At every chunk boundary the engine admits queued requests
+// while a slot and room in its device arena are free (strict FIFO), builds
+// their schedule tables and initial state, and then advances every active
+// request by up to `chunk` steps: all CSR requests together in one batched
+// launch per step (k_step_batched over a work list of 8-row x 128-column
+// items), dense requests with their own step kernels in the same stream.
+// A request whose last step falls inside the chunk is read out (energies of
+// all replicas, best per run), its result copied to the host and its slot
+// and arena space released.  Each element is computed exactly as by
+// sbqa_run, so a request's result does not depend on what else is running.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/sbqa.h"
+#include "internal.h"
+#include "problem.h"
+
+using namespace sbqa;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// First-fit allocator over one device allocation, free blocks coalesced.
+struct Arena {
+  uint8_t *base = nullptr;
+  size_t bytes = 0;
+  std::map<size_t, size_t> free_blocks;  // offset -> size
+  size_t used = 0;
+
+  bool alloc(size_t n, size_t *off) {
+    for (auto it = free_blocks.begin(); it != free_blocks.end(); ++it) {
+      if (it->second >= n) {
+        *off = it->first;
+        const size_t rest = it->second - n, o = it->first;
+        free_blocks.erase(it);
+        if (rest) free_blocks[o + n] = rest;
+        used += n;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t n) {
+    used -= n;
+    auto it = free_blocks.emplace(off, n).first;
+    auto nx = std::next(it);
+    if (nx != free_blocks.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_blocks.erase(nx);
+    }
+    if (it != free_blocks.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_blocks.erase(it);
+      }
+    }
+  }
+};
+
+enum ReqState { QUEUED = 0, ACTIVE = 1, DONE = 2 };
+
+struct Request {
+  int id = -1;
+  sbqa_problem *prob = nullptr;
+  int S = 0, P = 0, R = 0, C = 0, Cp = 0, nblk = 0;
+  uint64_t seed = 0;
+  int state = QUEUED;
+  int slot = -1;
+  int n0 = 0;  // steps done
+  size_t off = 0, bytes = 0;
+  // carved device buffers
+  float *x, *y, *ka, *dl, *kj;
+  uint8_t *F0, *F1, *FT;
+  int8_t *Sg, *best_spins;
+  int64_t *ei, *part_i, *best_ei;
+  double *ef, *part_f, *best_e;
+  int32_t *best_k, *best_step, *have;
+  int *err;
+  StepTables tables{};
+  void *tc_plan = nullptr;
+  // results (host)
+  std::vector<int8_t> spins;
+  std::vector<double> energy;
+  std::vector<int64_t> energy_int;
+  std::vector<int32_t> replica;
+
+  StateView state_view() const {
+    StateView s;
+    s.N = prob->n; s.C = C; s.Cp = Cp; s.P = P; s.R = R;
+    s.x = x; s.y = y; s.F[0] = F0; s.F[1] = F1; s.Sg = Sg;
+    return s;
+  }
+  BestView best_view() const {
+    BestView b;
+    b.e_int = ei; b.e_f64 = ef; b.part_int = part_i; b.part_f64 = part_f; b.nblk = nblk;
+    b.best_e_int = best_ei; b.best_e = best_e; b.best_k = best_k; b.best_step = best_step;
+    b.best_spins = best_spins; b.have_best = have;
+    return b;
+  }
+};
+
+}  // namespace
+
+struct sbqa_engine {
+  int device = 0;
+  Arena arena;
+  int max_slots = 0, chunk = 0;
+  std::vector<Request> reqs;
+  std::deque<int> queue;
+  std::vector<int> slot_req;  // slot -> request id, -1 free
+  SlotDesc *d_slots = nullptr;
+  WorkItem *d_items = nullptr;
+  int *d_n_items = nullptr;
+  size_t items_cap = 0;
+  int sms = 0;
+  int64_t steps_done_total = 0;  // replica-spin updates issued, for statistics
+
+  ~sbqa_engine() {
+    cudaDeviceSynchronize();
+    for (auto &r : reqs)
+      if (r.tc_plan) tc_plan_free(r.tc_plan);
+    if (arena.base) cudaFree(arena.base);
+    if (d_slots) cudaFree(d_slots);
+    if (d_items) cudaFree(d_items);
+    if (d_n_items) cudaFree(d_n_items);
+  }
+};
+
+namespace {
+
+#define ENG_CUDA(call)                                                                          \
+  do {                                                                                          \
+    cudaError_t e_ = (call);                                                                    \
+    if (e_ != cudaSuccess)                                                                      \
+      return set_error(e_ == cudaErrorMemoryAllocation ? SBQA_ERR_OOM : SBQA_ERR_CUDA,          \
+                       std::string(#call) + ": " + cudaGetErrorString(e_));                     \
+  } while (0)
+
+size_t request_bytes(const sbqa_problem *p, int S, int P, int R, bool tc, int Kp) {
+  const int C = R * P, Cp = (C + kColsPerWarp - 1) / kColsPerWarp * kColsPerWarp;
+  const size_t N = size_t(p->n), NC = N * Cp;
+  const size_t nblk = size_t(energy_row_blocks(p->n));
+  size_t b = 0;
+  b += align_up(NC * 4) * 2;               // x, y
+  b += align_up(NC) * 3;                   // F0, F1, Sg
+  b += align_up(size_t(std::max(S, 1)) * 4) + align_up(size_t(S + 1) * 4) + align_up(size_t(std::max(S, 1)) * R * 4);
+  b += align_up(size_t(Cp) * 8) * 2;       // energies
+  b += align_up(nblk * Cp * 8);            // partial sums
+  b += align_up(size_t(R) * 8) * 2 + align_up(size_t(R) * 4) * 3 + align_up(size_t(R) * N);
+  b += align_up(4);                        // error flag
+  if (tc) b += align_up(size_t(2) * Cp * Kp);
+  return b;
+}
+
+void carve(Request &r, uint8_t *base, bool tc, int Kp) {
+  const size_t N = size_t(r.prob->n), NC = N * r.Cp;
+  size_t o = 0;
+  auto take = [&](size_t n) {
+    uint8_t *p = base + o;
+    o += align_up(n);
+    return p;
+  };
+  r.x = reinterpret_cast<float *>(take(NC * 4));
+  r.y = reinterpret_cast<float *>(take(NC * 4));
+  r.F0 = take(NC);
+  r.F1 = take(NC);
+  r.Sg = reinterpret_cast<int8_t *>(take(NC));
+  r.ka = reinterpret_cast<float *>(take(size_t(std::max(r.S, 1)) * 4));
+  r.dl = reinterpret_cast<float *>(take(size_t(r.S + 1) * 4));
+  r.kj = reinterpret_cast<float *>(take(size_t(std::max(r.S, 1)) * r.R * 4));
+  r.ei = reinterpret_cast<int64_t *>(take(size_t(r.Cp) * 8));
+  r.ef = reinterpret_cast<double *>(take(size_t(r.Cp) * 8));
+  uint8_t *part = take(size_t(r.nblk) * r.Cp * 8);
+  r.part_i = reinterpret_cast<int64_t *>(part);
+  r.part_f = reinterpret_cast<double *>(part);
+  r.best_ei = reinterpret_cast<int64_t *>(take(size_t(r.R) * 8));
+  r.best_e = reinterpret_cast<double *>(take(size_t(r.R) * 8));
+  r.best_k = reinterpret_cast<int32_t *>(take(size_t(r.R) * 4));
+  r.best_step = reinterpret_cast<int32_t *>(take(size_t(r.R) * 4));
+  r.have = reinterpret_cast<int32_t *>(take(size_t(r.R) * 4));
+  r.best_spins = reinterpret_cast<int8_t *>(take(size_t(r.R) * N));
+  r.err = reinterpret_cast<int *>(take(4));
+  r.FT = tc ? take(size_t(2) * r.Cp * Kp) : nullptr;
+}
+
+int admit(sbqa_engine *e, Request &r, int slot, cudaStream_t st) {
+  sbqa_problem *p = r.prob;
+  const bool tc = p->use_tc;
+  r.C = r.R * r.P;
+  r.Cp = (r.C + kColsPerWarp - 1) / kColsPerWarp * kColsPerWarp;
+  r.nblk = energy_row_blocks(p->n);
+  carve(r, e->arena.base + r.off, tc, p->Kp);
+  int rc = problem_build_tables(p, r.S, r.P, r.R, r.ka, r.dl, r.kj, &r.tables, st);
+  if (rc != SBQA_OK) return rc;
+  if (tc) {
+    if (!tc_plan_make(&r.tc_plan, p->d_J8.p, r.FT, p->Kp, r.Cp))
+      return set_error(SBQA_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    ENG_CUDA(tc_set_attributes());
+  }
+  const StateView s = r.state_view();
+  ENG_CUDA(cudaMemsetAsync(r.err, 0, sizeof(int), st));
+  ENG_CUDA(launch_init(s, r.seed, float(p->prm.init_amp), 0.0f, st));
+  if (tc) ENG_CUDA(launch_f_to_ft8(s, 0, r.FT, p->Kp, 0, st));
+  ENG_CUDA(launch_reset_best(s, r.best_view(), st));
+  r.slot = slot;
+  r.n0 = 0;
+  r.state = ACTIVE;
+  e->slot_req[slot] = r.id;
+  return SBQA_OK;
+}
+
+SlotDesc slot_desc(const Request &r) {
+  const sbqa_problem *p = r.prob;
+  const CsrView v = problem_csr_view(p);
+  SlotDesc d{};
+  d.row_ptr = v.row_ptr; d.col = v.col; d.npos = v.npos; d.val = v.val; d.h = v.h; d.kind = v.kind;
+  d.N = p->n; d.C = r.C; d.Cp = r.Cp; d.P = r.P; d.R = r.R; d.S = r.S;
+  d.x = r.x; d.y = r.y; d.F0 = r.F0; d.F1 = r.F1;
+  d.ka = r.ka; d.dl = r.dl; d.kj = r.kj; d.kc = r.tables.kc; d.kx = r.tables.kx;
+  d.n0 = r.n0;
+  return d;
+}
+
+int readout(sbqa_engine *e, Request &r, cudaStream_t st) {
+  (void)e;
+  sbqa_problem *p = r.prob;
+  const StateView s = r.state_view();
+  const EnergyView ev = problem_energy_view(p);
+  cudaError_t err = p->dense ? launch_energy_dense(s, ev, r.best_view(), st)
+                             : launch_energy_csr(s, problem_csr_readout_view(p), ev, r.best_view(), st);
+  if (err == cudaSuccess) err = launch_best(s, ev, r.best_view(), r.S - 1, st);
+  if (err != cudaSuccess) return set_error(SBQA_ERR_CUDA, std::string("engine readout: ") + cudaGetErrorString(err));
+  r.spins.resize(size_t(r.R) * p->n);
+  r.energy.resize(r.R);
+  r.energy_int.assign(r.R, 0);
+  r.replica.resize(r.R);
+  ENG_CUDA(cudaMemcpyAsync(r.spins.data(), r.best_spins, r.spins.size(), cudaMemcpyDeviceToHost, st));
+  ENG_CUDA(cudaMemcpyAsync(r.energy.data(), r.best_e, r.R * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (p->is_integer)
+    ENG_CUDA(cudaMemcpyAsync(r.energy_int.data(), r.best_ei, r.R * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  ENG_CUDA(cudaMemcpyAsync(r.replica.data(), r.best_k, r.R * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  return SBQA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sbqa_engine_create(int64_t arena_bytes, int32_t max_slots, int32_t chunk_steps, sbqa_engine **out) {
+  if (!out) return set_error(SBQA_ERR_INVALID_ARG, "out is null");
+  *out = nullptr;
+  if (arena_bytes < (1 << 20) || max_slots < 1 || max_slots > 4096 || chunk_steps < 1)
+    return set_error(SBQA_ERR_INVALID_ARG, "need arena_bytes >= 1 MiB, 1 <= max_slots <= 4096, chunk_steps >= 1");
+  auto *e = new (std::nothrow) sbqa_engine();
+  if (!e) return set_error(SBQA_ERR_OOM, "host allocation");
+  cudaGetDevice(&e->device);
+  e->max_slots = max_slots;
+  e->chunk = chunk_steps;
+  e->slot_req.assign(max_slots, -1);
+  auto fail_free = [&](int code, const std::string &m) {
+    delete e;
+    return set_error(code, m);
+  };
+  if (cudaMalloc(&e->arena.base, size_t(arena_bytes)) != cudaSuccess) return fail_free(SBQA_ERR_OOM, "engine arena");
+  e->arena.bytes = size_t(arena_bytes);
+  e->arena.free_blocks[0] = size_t(arena_bytes);
+  if (cudaMalloc(&e->d_slots, sizeof(SlotDesc) * max_slots) != cudaSuccess ||
+      cudaMalloc(&e->d_n_items, sizeof(int)) != cudaSuccess)
+    return fail_free(SBQA_ERR_OOM, "engine tables");
+  cudaDeviceGetAttribute(&e->sms, cudaDevAttrMultiProcessorCount, e->device);
+  *out = e;
+  return SBQA_OK;
+}
+
+void sbqa_engine_destroy(sbqa_engine *e) { delete e; }
+
+int sbqa_engine_submit(sbqa_engine *e, sbqa_problem *p, int32_t steps, int32_t P, int32_t R, uint64_t seed,
+                       int32_t *id) {
+  if (!e || !p || !id) return set_error(SBQA_ERR_INVALID_ARG, "null argument");
+  int rc = problem_check_run(p, steps, P, R);
+  if (rc != SBQA_OK) return rc;
+  if (steps < 1) return set_error(SBQA_ERR_INVALID_ARG, "engine requests need steps >= 1");
+  if ((rc = problem_prepare_values(p)) != SBQA_OK) return rc;
+  Request r;
+  r.id = int(e->reqs.size());
+  r.prob = p;
+  r.S = steps; r.P = P; r.R = R; r.seed = seed;
+  r.bytes = request_bytes(p, steps, P, R, p->use_tc, p->Kp);
+  if (r.bytes > e->arena.bytes) return set_error(SBQA_ERR_OOM, "request larger than the engine arena");
+  e->reqs.push_back(std::move(r));
+  e->queue.push_back(e->reqs.back().id);
+  *id = e->reqs.back().id;
+  return SBQA_OK;
+}
+
+int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done, int32_t *done_ids, int32_t cap) {
+  if (!e || !n_done) return set_error(SBQA_ERR_INVALID_ARG, "null argument");
+  *n_done = 0;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int rc;
+  // 1. admission, strict FIFO: by slot and arena room
+  while (!e->queue.empty()) {
+    Request &r = e->reqs[e->queue.front()];
+    int slot = -1;
+    for (int q = 0; q < e->max_slots; ++q)
+      if (e->slot_req[q] < 0) {
+        slot = q;
+        break;
+      }
+    if (slot < 0 || !e->arena.alloc(r.bytes, &r.off)) break;
+    e->queue.pop_front();
+    if ((rc = admit(e, r, slot, st)) != SBQA_OK) return rc;
+  }
+  // 2. slot table and work list of the CSR requests
+  std::vector<SlotDesc> slots(e->max_slots);
+  std::vector<WorkItem> items;
+  std::vector<int> dense_active;
+  for (int q = 0; q < e->max_slots; ++q) {
+    if (e->slot_req[q] < 0) continue;
+    Request &r = e->reqs[e->slot_req[q]];
+    slots[q] = slot_desc(r);
+    if (r.prob->dense) {
+      dense_active.push_back(r.id);
+      continue;
+    }
+    for (int g = 0; g < r.Cp / kColsPerWarp; ++g)
+      for (int r0 = 0; r0 < r.prob->n; r0 += 8) items.push_back(WorkItem{q, r0, g, 0});
+  }
+  if (items.size() > e->items_cap) {
+    if (e->d_items) cudaFree(e->d_items);
+    e->d_items = nullptr;
+    e->items_cap = std::max(items.size(), e->items_cap * 2);
+    ENG_CUDA(cudaMalloc(&e->d_items, e->items_cap * sizeof(WorkItem)));
+  }
+  const int n_items = int(items.size());
+  ENG_CUDA(cudaMemcpyAsync(e->d_slots, slots.data(), slots.size() * sizeof(SlotDesc), cudaMemcpyHostToDevice, st));
+  if (n_items)
+    ENG_CUDA(cudaMemcpyAsync(e->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, st));
+  ENG_CUDA(cudaMemcpyAsync(e->d_n_items, &n_items, sizeof(int), cudaMemcpyHostToDevice, st));
+  // 3. the chunk: one batched launch per step for the CSR requests, own
+  //    launches for the dense ones
+  const int grid = std::max(1, std::min(n_items, e->sms * 3));
+  for (int j = 0; j < e->chunk; ++j) {
+    if (n_items) ENG_CUDA(launch_step_batched(e->d_slots, e->d_items, e->d_n_items, grid, j, st));
+    for (int id : dense_active) {
+      Request &r = e->reqs[id];
+      const int n = r.n0 + j;
+      if (n >= r.S) continue;
+      cudaError_t err;
+      if (r.prob->use_tc)
+        err = launch_step_dense_tc(r.tc_plan, r.state_view(), r.prob->Kp, r.FT, r.err, r.prob->d_h.p, r.tables, n, st);
+      else
+        err = launch_step_dense(r.state_view(), problem_dense_view(r.prob), r.tables, n, st);
+      if (err != cudaSuccess) return set_error(SBQA_ERR_CUDA, std::string("engine step: ") + cudaGetErrorString(err));
+    }
+  }
+  // 4. retire the requests that finished inside the chunk
+  std::vector<int> finished;
+  for (int q = 0; q < e->max_slots; ++q) {
+    if (e->slot_req[q] < 0) continue;
+    Request &r = e->reqs[e->slot_req[q]];
+    const int done_now = std::min(e->chunk, r.S - r.n0);
+    e->steps_done_total += int64_t(done_now) * r.prob->n * r.C;
+    r.n0 += done_now;
+    if (r.n0 >= r.S) {
+      if ((rc = readout(e, r, st)) != SBQA_OK) return rc;
+      finished.push_back(r.id);
+    }
+  }
+  ENG_CUDA(cudaStreamSynchronize(st));
+  for (int id : finished) {
+    Request &r = e->reqs[id];
+    int err = 0;
+    ENG_CUDA(cudaMemcpy(&err, r.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (err) return set_error(SBQA_ERR_TIMEOUT, "a bounded device wait gave up in request " + std::to_string(id));
+    if (r.tc_plan) {
+      tc_plan_free(r.tc_plan);
+      r.tc_plan = nullptr;
+    }
+    e->slot_req[r.slot] = -1;
+    e->arena.release(r.off, r.bytes);
+    r.state = DONE;
+    if (*n_done < cap && done_ids) done_ids[*n_done] = id;
+    ++*n_done;
+  }
+  return SBQA_OK;
+}
+
+int sbqa_engine_result(sbqa_engine *e, int32_t id, int8_t *spins, double *energy, int64_t *energy_int,
+                       int32_t *replica) {
+  if (!e || id < 0 || id >= int(e->reqs.size())) return set_error(SBQA_ERR_INVALID_ARG, "unknown request");
+  const Request &r = e->reqs[id];
+  if (r.state != DONE) return set_error(SBQA_ERR_STATE, "request not finished");
+  if (spins) std::memcpy(spins, r.spins.data(), r.spins.size());
+  if (energy) std::memcpy(energy, r.energy.data(), r.energy.size() * sizeof(double));
+  if (energy_int) std::memcpy(energy_int, r.energy_int.data(), r.energy_int.size() * sizeof(int64_t));
+  if (replica) std::memcpy(replica, r.replica.data(), r.replica.size() * sizeof(int32_t));
+  return SBQA_OK;
+}
+
+int sbqa_engine_stats(const sbqa_engine *e, sbqa_engine_stats_t *s) {
+  if (!e || !s) return set_error(SBQA_ERR_INVALID_ARG, "null argument");
+  s->queued = int32_t(e->queue.size());
+  s->active = 0;
+  for (int q : e->slot_req) s->active += q >= 0;
+  s->finished = 0;
+  for (const auto &r : e->reqs) s->finished += r.state == DONE;
+  s->arena_bytes = int64_t(e->arena.bytes);
+  s->arena_used = int64_t(e->arena.used);
+  s->updates_issued = e->steps_done_total;
+  return SBQA_OK;
+}
+
+}  // extern "C"

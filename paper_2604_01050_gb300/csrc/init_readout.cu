@@ -38,17 +38,17 @@ __global__ void k_init(StateView s, uint64_t seed, float amp, float delta0) {
   if (e >= size_t(s.N) * s.Cp) return;
   const int i = int(e / s.Cp), c = int(e % s.Cp);
   float x = 0.f, y = 0.f;
-  int8_t f = 0;
+  uint8_t f = kFZero;
   if (c < s.C) {
     const uint64_t el = uint64_t(c) * uint64_t(s.N) + uint64_t(i);  // (r * P + k) * N + i
     x = to_uniform(splitmix64_at(seed, 2ull * el), amp);
     y = to_uniform(splitmix64_at(seed, 2ull * el + 1ull), amp);
-    f = thresh(x, delta0);
+    f = uint8_t(fcode(x, delta0));
   }
   s.x[e] = x;
   s.y[e] = y;
   s.F[0][e] = f;
-  s.F[1][e] = 0;
+  s.F[1][e] = kFZero;
 }
 
 cudaError_t launch_init(const StateView &s, uint64_t seed, float amp, float delta0,
@@ -62,7 +62,7 @@ __global__ void k_refresh_f(StateView s, int which, float delta) {
   const size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= size_t(s.N) * s.Cp) return;
   const int c = int(e % s.Cp);
-  s.f_of(which)[e] = (c < s.C) ? thresh(s.x[e], delta) : int8_t(0);
+  s.f_of(which)[e] = (c < s.C) ? uint8_t(fcode(s.x[e], delta)) : kFZero;
 }
 
 cudaError_t launch_refresh_f(const StateView &s, int which, float delta, cudaStream_t st) {

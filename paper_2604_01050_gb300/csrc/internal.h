@@ -4,7 +4,7 @@
 // padded to Cp, a multiple of 128 so that one warp owns 128 whole columns
 // and therefore whole runs, because P divides 32):
 //   x, y   float  [N][Cp]   positions / momenta, spin-major
-//   F[2]   int8   [N][Cp]   f(x) in {-1, 0, +1} for the current / next step
+//   F[2]   uint8  [N][Cp]   f(x) + 1 in {0, 1, 2} for the current / next step
 // Per-step FP32 coefficients (host FP64 -> FP32, one table entry per step):
 //   ka[n]      dt * (a0 - a_n) / P       (a_n = n / S, Sec. II A)
 //   dl[n]      Delta_n = delta_slope * n / S   (n = 0..S, Eq. 8)
@@ -34,17 +34,18 @@ struct StepTables {
 struct StateView {
   int N, C, Cp, P, R;
   float *x, *y;
-  int8_t *F[2];
-  int8_t *Sg;  // [N][Cp] readout spins sign(x), +1 for x >= 0
-  // F buffer holding f(x) for step n (selected without indexing the array,
-  // which would put the kernel argument in local memory)
-  __host__ __device__ int8_t *f_of(int n) const { return (n & 1) ? F[1] : F[0]; }
+  uint8_t *F[2];  // f(x) + 1 codes, double-buffered by step parity
+  int8_t *Sg;     // [N][Cp] readout spins sign(x), +1 for x >= 0
+  // F buffer holding the codes of step n (selected without indexing the
+  // array, which would put the kernel argument in local memory)
+  __host__ __device__ uint8_t *f_of(int n) const { return (n & 1) ? F[1] : F[0]; }
 };
 
 struct CsrView {
   const int32_t *row_ptr;  // [N + 1]
-  const int32_t *col;      // [nnz]
-  const void *val;         // int8 (PM1), float (F32) or bf16 (BF16)
+  const int32_t *col;      // [nnz] (VAL_PM1: each row's +1 entries first)
+  const void *val;         // float (F32) or bf16 (BF16); unused for VAL_PM1
+  const int32_t *npos;     // VAL_PM1: number of +1 entries of each row
   const float *h;          // [N], never null (zeros when h = 0)
   int kind;
 };
@@ -82,12 +83,37 @@ struct BestView {
 // returns code.
 int set_error(int code, const std::string &msg);
 
+// One active request of the batching engine (device copy, read by the
+// batched step kernel).
+struct SlotDesc {
+  const int32_t *row_ptr, *col, *npos;  // CSR (col in the step kernel's order)
+  const void *val;
+  const float *h;
+  int kind;
+  int N, C, Cp, P, R, S;
+  float *x, *y;
+  uint8_t *F0, *F1;
+  const float *ka, *dl, *kj;
+  float kc, kx;
+  int n0;  // steps completed before the current chunk
+  int pad;
+};
+
+// 8 spin rows x 128 replica columns of one slot.
+struct WorkItem {
+  int slot, row0, colgroup, pad;
+};
+
 // ---- launchers (return cudaGetLastError() of the launch) ----
 cudaError_t launch_init(const StateView &s, uint64_t seed, float amp, float delta0,
                         cudaStream_t st);
 cudaError_t launch_refresh_f(const StateView &s, int which, float delta, cudaStream_t st);
+// variant v: 4 << v consecutive columns per lane (picked per problem shape by
+// the autotuner in api.cu); valid when Cp is a multiple of 32 * (4 << v).
+int csr_step_variants();
+bool csr_step_variant_ok(int variant, int Cp);
 cudaError_t launch_step_csr(const StateView &s, const CsrView &J, const StepTables &t,
-                            int n, cudaStream_t st);
+                            int n, int variant, cudaStream_t st);
 cudaError_t launch_step_dense(const StateView &s, const DenseView &J, const StepTables &t,
                               int n, cudaStream_t st);
 // Dense integer couplings on tcgen05 (step_dense_tc.cu).  The plan holds the
@@ -98,6 +124,11 @@ cudaError_t tc_set_attributes();  // dynamic shared memory limit of the tcgen05 
 cudaError_t launch_step_dense_tc(const void *plan, const StateView &s, int Kp, uint8_t *FT, int *err,
                                  const float *h, const StepTables &t, int n, cudaStream_t st);
 cudaError_t launch_f_to_ft8(const StateView &s, int which, uint8_t *FT, int Kp, int buffer, cudaStream_t st);
+
+// Batched CSR step over the work items of all active slots (step_batched.cu);
+// j = step index inside the current chunk, n_items in device memory.
+cudaError_t launch_step_batched(const SlotDesc *slots, const WorkItem *items, const int *n_items, int grid, int j,
+                                cudaStream_t st);
 
 int energy_row_blocks(int N);
 // sign(x) into Sg, energies of every column into b.e_int / b.e_f64.

@@ -1,0 +1,179 @@
+// problem.h -- the problem handle shared by the host side of the library
+// (api.cu: single solves; engine.cu: the batching engine).
+#pragma once
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/sbqa.h"
+#include "internal.h"
+
+namespace sbqa {
+
+template <typename T>
+struct DevBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  cudaError_t alloc(size_t count) {
+    if (count <= n && p) return cudaSuccess;
+    release();
+    if (count == 0) return cudaSuccess;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&p), count * sizeof(T));
+    if (e == cudaSuccess) n = count;
+    else p = nullptr;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+};
+
+}  // namespace sbqa
+
+using sbqa::BestView;
+using sbqa::CsrView;
+using sbqa::DenseView;
+using sbqa::EnergyView;
+using sbqa::StateView;
+using sbqa::StepTables;
+using sbqa::VAL_BF16;
+using sbqa::VAL_F32;
+using sbqa::VAL_PM1;
+
+struct sbqa_problem {
+  int device = 0;
+  int32_t n = 0;
+  bool dense = false;
+  int64_t nnz = 0;
+  bool is_integer = false, is_pm1 = false, j_integer = false;
+  int32_t max_abs_j = -1;
+  int32_t max_degree = 0;
+  double c0_auto = 0.5;
+  bool h_zero = true;
+
+  // host copies (CSR for sparse, row-major for dense)
+  std::vector<int64_t> row_ptr;
+  std::vector<int32_t> col;
+  std::vector<double> val;  // CSR values or dense N*N
+  std::vector<double> h;
+
+  // device: product operands
+  sbqa::DevBuf<int32_t> d_row_ptr, d_col;
+  sbqa::DevBuf<int32_t> d_col_pm1, d_npos;  // +-1 rows with the +1 entries first
+  sbqa::DevBuf<float> d_val_f32;
+  sbqa::DevBuf<__nv_bfloat16> d_val_bf16;
+  sbqa::DevBuf<float> d_dense_f32;  // dense J for the CUDA-core path
+  int dense_prec = -1;        // precision the dense FP32 copy was built for
+  // dense integer J on the tensor cores: e4m3 copies padded to Kp
+  bool use_tc = false;
+  int Kp = 0;
+  sbqa::DevBuf<uint8_t> d_J8, d_FT;
+  void *tc_plan = nullptr;
+  const void *tc_plan_ft = nullptr;  // FT buffer the plan was made for
+  int tc_plan_cp = 0;
+  sbqa::DevBuf<int> d_err;
+  sbqa::DevBuf<float> d_h;
+  // device: readout operands
+  sbqa::DevBuf<int32_t> d_e_i32;
+  sbqa::DevBuf<double> d_e_f64;
+  sbqa::DevBuf<int64_t> d_h_i64;
+  sbqa::DevBuf<double> d_h_f64;
+
+  // schedule
+  bool have_params = false;
+  sbqa_params prm{};
+  std::vector<double> beta, alpha;
+
+  // run state
+  int S = 0, P = 0, R = 0, C = 0, Cp = 0;
+  int step_done = 0;
+  bool begun = false, finished = false;
+  cudaStream_t stream = nullptr;
+  int kind = VAL_F32;  // sparse value kind in use
+  int csr_variant = -1;  // CSR step kernel variant chosen by the autotuner (-1 = not yet)
+  float variant_ms[4] = {0.f, 0.f, 0.f, 0.f};
+  int csr_variant_cp = -1, csr_variant_kind = -1;
+  sbqa::DevBuf<float> d_x, d_y;
+  sbqa::DevBuf<uint8_t> d_F0, d_F1;
+  sbqa::DevBuf<int8_t> d_Sg;
+  sbqa::DevBuf<float> d_ka, d_dl, d_kj;
+  sbqa::DevBuf<int64_t> d_ei, d_part_i, d_best_ei;
+  sbqa::DevBuf<double> d_ef, d_part_f, d_best_e;
+  sbqa::DevBuf<int32_t> d_best_k, d_best_step, d_have;
+  sbqa::DevBuf<int8_t> d_best_spins;
+  StepTables tables{};
+
+  // cached graph of the step loop + readouts of a full run
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  struct Key {
+    int S = -1, P = -1, R = -1, eval = -1, kind = -1, dense = -1, tc = -1, variant = -1;
+    float kc = 0.f, kx = 0.f;  // step constants are kernel arguments in the graph
+    const void *x = nullptr, *kj = nullptr;
+    bool operator==(const Key &o) const {
+      return S == o.S && P == o.P && R == o.R && eval == o.eval && kind == o.kind &&
+             dense == o.dense && tc == o.tc && variant == o.variant && x == o.x && kj == o.kj &&
+             std::memcmp(&kc, &o.kc, sizeof(float)) == 0 && std::memcmp(&kx, &o.kx, sizeof(float)) == 0;
+    }
+  } graph_key;
+
+  ~sbqa_problem();  // waits for the device, releases every buffer (api.cu)
+
+  StateView state() const {
+    StateView s;
+    s.N = n; s.C = C; s.Cp = Cp; s.P = P; s.R = R;
+    s.x = d_x.p; s.y = d_y.p;
+    s.F[0] = d_F0.p; s.F[1] = d_F1.p;
+    s.Sg = d_Sg.p;
+    return s;
+  }
+  // CSR in the caller's entry order (the readout pairs it with the value arrays)
+  CsrView csr_readout() const {
+    CsrView v = csr();
+    v.col = d_col.p;
+    return v;
+  }
+  CsrView csr() const {
+    CsrView v;
+    v.row_ptr = d_row_ptr.p; v.h = d_h.p; v.kind = kind; v.npos = d_npos.p;
+    v.col = kind == VAL_PM1 ? d_col_pm1.p : d_col.p;
+    v.val = kind == VAL_F32 ? static_cast<const void *>(d_val_f32.p)
+                            : static_cast<const void *>(d_val_bf16.p);
+    return v;
+  }
+  EnergyView energy() const {
+    EnergyView e;
+    e.is_integer = is_integer ? 1 : 0;
+    e.val_i32 = d_e_i32.p; e.val_f64 = d_e_f64.p; e.h_i64 = d_h_i64.p; e.h_f64 = d_h_f64.p;
+    return e;
+  }
+  BestView best() const {
+    BestView b;
+    b.e_int = d_ei.p; b.e_f64 = d_ef.p; b.part_int = d_part_i.p; b.part_f64 = d_part_f.p;
+    b.nblk = sbqa::energy_row_blocks(n);
+    b.best_e_int = d_best_ei.p; b.best_e = d_best_e.p; b.best_k = d_best_k.p;
+    b.best_step = d_best_step.p; b.best_spins = d_best_spins.p; b.have_best = d_have.p;
+    return b;
+  }
+};
+
+namespace sbqa {
+
+// Host helpers implemented in api.cu, used by the engine.
+int problem_check_run(sbqa_problem *p, int32_t steps, int32_t P, int32_t R);
+// Device copies of J in the form the current precision needs.
+int problem_prepare_values(sbqa_problem *p);
+// FP64 schedule of Sec. II A rounded to the FP32 step coefficients, written to
+// ka[S], dl[S+1], kj[S][R] (device) on st; *t receives the table view.
+int problem_build_tables(const sbqa_problem *p, int S, int P, int R, float *ka, float *dl, float *kj,
+                         StepTables *t, cudaStream_t st);
+CsrView problem_csr_view(const sbqa_problem *p);
+CsrView problem_csr_readout_view(const sbqa_problem *p);
+EnergyView problem_energy_view(const sbqa_problem *p);
+DenseView problem_dense_view(const sbqa_problem *p);
+
+}  // namespace sbqa

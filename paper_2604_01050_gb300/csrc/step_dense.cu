@@ -18,12 +18,12 @@ constexpr int kDenseBK = 32;
 template <int P>
 __global__ void __launch_bounds__(256) k_step_dense(StateView s, DenseView J, StepTables t, int n) {
   __shared__ float Js[kDenseBM][kDenseBK + 1];
-  __shared__ __align__(16) int8_t Fs[kDenseBK][kColsPerWarp];
+  __shared__ __align__(16) uint8_t Fs[kDenseBK][kColsPerWarp];
   const int row0 = blockIdx.y * kDenseBM;
   const int col0 = blockIdx.x * kColsPerWarp;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int8_t *Fin = s.f_of(n);
-  int8_t *Fout = s.f_of(n + 1);
+  const uint8_t *Fin = s.f_of(n);
+  uint8_t *Fout = s.f_of(n + 1);
   const int N = s.N;
   float acc[4][4];
 #pragma unroll
@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(256) k_step_dense(StateView s, DenseView J, St
     {
       const int r = threadIdx.x >> 3, seg = (threadIdx.x & 7) * 16;
       const int gk = k0 + r;
-      uint4 v = make_uint4(0, 0, 0, 0);
+      uint4 v = make_uint4(kFZero4, kFZero4, kFZero4, kFZero4);  // f = 0 past the last spin
       if (gk < N) v = __ldg(reinterpret_cast<const uint4 *>(Fin + size_t(gk) * s.Cp + col0 + seg));
       *reinterpret_cast<uint4 *>(&Fs[r][seg]) = v;
     }
@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256) k_step_dense(StateView s, DenseView J, St
 #pragma unroll 8
     for (int k = 0; k < kDenseBK; ++k) {
       const uint32_t f4 = *reinterpret_cast<const uint32_t *>(&Fs[k][lane * 4]);
-      const float f0 = sbyte(f4, 0), f1 = sbyte(f4, 1), f2 = sbyte(f4, 2), f3 = sbyte(f4, 3);
+      const float f0 = fdec(f4, 0), f1 = fdec(f4, 1), f2 = fdec(f4, 2), f3 = fdec(f4, 3);
 #pragma unroll
       for (int a = 0; a < 4; ++a) {
         const float w = Js[warp * 4 + a][k];

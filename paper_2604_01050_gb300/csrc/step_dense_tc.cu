@@ -12,13 +12,14 @@
 //   B = FT8  [2][Cp][Kp]              e4m3 f(x) transposed (column c, spin j),
 //                                     K-major, double-buffered by step parity
 // Tile: 128 spin rows x 128 replica columns per CTA (one wave of 128 CTAs for
-// N = 2000, R*P = 1024).  Four TMA stages of 128 x 128-byte tiles of A and B
+// N = 2000, R*P = 1024).  Six TMA stages of 128 x 128-byte tiles of A and B
 // (128-byte swizzle) feed tcgen05.mma M=128 N=128 K=32 (4 per stage); the
 // FP32 accumulator lives in 128 TMEM columns.  Thread 0 of warp 0 issues the
-// TMA loads, thread 0 of warp 1 the MMAs; afterwards all four warps read
-// their 32 TMEM lanes (= spin rows) and run the SBQA update on whole runs of
-// 32 columns held in registers, write x, y, and stage f(x_next) in shared
-// memory, which is then stored transposed into the other FT8 buffer.
+// TMA loads, thread 0 of warp 1 the MMAs.  Afterwards the x, y tiles are
+// brought into shared memory with coalesced loads, every warp reads its 32
+// TMEM lanes (= spin rows) for 64 columns and runs the SBQA update on whole
+// runs of 32 columns, the tiles go back with coalesced stores, and f(x_next)
+// (staged in shared memory) is stored transposed into the other FT8 buffer.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -27,7 +28,8 @@
 
 namespace sbqa {
 
-constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 128, kTcStages = 4;
+constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 128, kTcStages = 6;
+constexpr int kTcThreads = 256;  // 8 warps: all run the epilogue
 constexpr int kTcTile = kTcBM * kTcBK;  // bytes of one operand stage (e4m3)
 constexpr int kTcSmem = 2 * kTcStages * kTcTile + 1024 + 256;
 constexpr uint8_t kE4M3One = 0x38, kE4M3MinusOne = 0xB8;
@@ -43,31 +45,29 @@ __device__ __forceinline__ uint8_t f_to_e4m3(int8_t f) {
   return f == 0 ? uint8_t(0) : (f > 0 ? kE4M3One : kE4M3MinusOne);
 }
 
-// Update of one spin row i for 32 aligned columns c0..c0+31 (whole runs,
-// because P divides 32).  Same arithmetic, in the same order, as sb_update4.
+constexpr int kTileLd = kTcBN + 1;  // padded row of the x, y tiles in shared memory (conflict-free columns)
+
+// Update of one spin row for 32 aligned columns c0..c0+31 (whole runs,
+// because P divides 32); x and y are read from and written back to rows of
+// the shared-memory tiles.  Same arithmetic, in the same order, as sb_update4.
 template <int P>
-__device__ __forceinline__ void sb_update_row32(const StateView &s, const StepTables &t, int n, int i, int c0,
-                                                const uint32_t (&g)[32], float hi, int8_t (&f)[32]) {
+__device__ __forceinline__ void sb_update_row32(const StateView &s, const StepTables &t, int n, int c0,
+                                                const uint32_t (&g)[32], float hi, float *xr, float *yr,
+                                                int8_t (&f)[32]) {
   float xs[32], ys[32];
-  const size_t off = size_t(i) * s.Cp + c0;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const float4 a = *reinterpret_cast<const float4 *>(s.x + off + 4 * q);
-    const float4 b = *reinterpret_cast<const float4 *>(s.y + off + 4 * q);
-    xs[4 * q] = a.x; xs[4 * q + 1] = a.y; xs[4 * q + 2] = a.z; xs[4 * q + 3] = a.w;
-    ys[4 * q] = b.x; ys[4 * q + 1] = b.y; ys[4 * q + 2] = b.z; ys[4 * q + 3] = b.w;
+  for (int j = 0; j < 32; ++j) {
+    xs[j] = xr[j];
+    ys[j] = yr[j];
   }
   const float ka = t.ka[n];
   const float dnext = t.dl[n + 1];
   const float *kjn = t.kj + size_t(n) * t.R;
-  float xo[32], yo[32];
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
     const int k = j % P, base = j - k;
     const float xm = xs[base + (k + P - 1) % P], xp = xs[base + (k + 1) % P];
     f[j] = 0;
-    xo[j] = xs[j];
-    yo[j] = ys[j];
     if (c0 + j >= s.C) continue;
     const float kj = kjn[(c0 + j) / P];
     float yn = fmaf(t.kc, __uint_as_float(g[j]) + hi, ys[j]);
@@ -78,19 +78,14 @@ __device__ __forceinline__ void sb_update_row32(const StateView &s, const StepTa
       xn = copysignf(1.f, xn);
       yn = 0.f;
     }
-    xo[j] = xn;
-    yo[j] = yn;
+    xr[j] = xn;
+    yr[j] = yn;
     f[j] = thresh(xn, dnext);
-  }
-#pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    *reinterpret_cast<float4 *>(s.x + off + 4 * q) = make_float4(xo[4 * q], xo[4 * q + 1], xo[4 * q + 2], xo[4 * q + 3]);
-    *reinterpret_cast<float4 *>(s.y + off + 4 * q) = make_float4(yo[4 * q], yo[4 * q + 1], yo[4 * q + 2], yo[4 * q + 3]);
   }
 }
 
 template <int P>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kTcThreads, 1)
     k_step_dense_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, StateView s,
                     TcArgs a, StepTables t, int n) {
   extern __shared__ uint8_t smem_raw[];
@@ -147,46 +142,79 @@ __global__ void __launch_bounds__(128, 1)
     tc::mma_commit(done);
   }
   __syncwarp();
+
   tc::mbar_wait(done, 0, a.err, tc::ERR_WAIT_DONE);
   tc::tc_fence_after();
 
-  // Epilogue: warp w owns TMEM lanes 32w..32w+31 = spin rows m0 + 32w + lane.
-  uint8_t *sF = sA;  // [128 columns][128 rows] of e4m3 f(x_next); operands are consumed
-  const int rl = warp * 32 + lane;
+  // Epilogue.  The operand stages are consumed; their memory now holds the
+  // x and y tiles (128 rows x 128 columns, padded rows) and the f codes of
+  // the next step.  Global x, y are read and written with coalesced
+  // row-contiguous accesses; each thread then works on one spin row.
+  float *sx = reinterpret_cast<float *>(smem);
+  float *sy = sx + kTcBM * kTileLd;
+  uint8_t *sF = reinterpret_cast<uint8_t *>(sy + kTcBM * kTileLd);  // [128 columns][128 rows]
+  const int cols_valid = min(kTcBN, s.C - n0);  // multiple of P, hence of 4 when P >= 4
+  for (int q = threadIdx.x; q < kTcBM * (kTcBN / 4); q += kTcThreads) {
+    const int r = q / (kTcBN / 4), c = (q % (kTcBN / 4)) * 4;
+    if (m0 + r < s.N && c < cols_valid) {
+      const size_t off = size_t(m0 + r) * s.Cp + n0 + c;
+      const float4 xv = *reinterpret_cast<const float4 *>(s.x + off);
+      const float4 yv = *reinterpret_cast<const float4 *>(s.y + off);
+      float *px = sx + r * kTileLd + c, *py = sy + r * kTileLd + c;
+      px[0] = xv.x; px[1] = xv.y; px[2] = xv.z; px[3] = xv.w;
+      py[0] = yv.x; py[1] = yv.y; py[2] = yv.z; py[3] = yv.w;
+    }
+  }
+  __syncthreads();
+  // warp w: TMEM lanes 32 (w % 4) .. + 31 (= spin rows), columns 64 (w / 4) .. + 63
+  const int quarter = warp & 3, half = warp >> 2;
+  const int rl = quarter * 32 + lane;
   const int i = m0 + rl;
 #pragma unroll 1
-  for (int cc = 0; cc < kTcBN / 32; ++cc) {
+  for (int cc = 0; cc < 2; ++cc) {
+    const int cl = half * 64 + cc * 32;  // first column of the chunk inside the tile
+    const int c0 = n0 + cl;
     uint32_t g[32];
-    tc::tmem_ld_32x32b_x32(tmem + (uint32_t(warp * 32) << 16) + uint32_t(cc * 32), g);
+    tc::tmem_ld_32x32b_x32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(cl), g);
     int8_t f[32];
-    const int c0 = n0 + cc * 32;
     if (i < s.N && c0 < s.C) {
-      sb_update_row32<P>(s, t, n, i, c0, g, __ldg(a.h + i), f);
+      sb_update_row32<P>(s, t, n, c0, g, __ldg(a.h + i), sx + rl * kTileLd + cl, sy + rl * kTileLd + cl, f);
     } else {
 #pragma unroll
       for (int j = 0; j < 32; ++j) f[j] = 0;
     }
 #pragma unroll
-    for (int j = 0; j < 32; ++j) sF[(cc * 32 + j) * kTcBM + rl] = f_to_e4m3(f[j]);
+    for (int j = 0; j < 32; ++j) sF[(cl + j) * kTcBM + rl] = f_to_e4m3(f[j]);
   }
   tc::tc_fence_before();
   __syncthreads();
-  // column n0 + t of FT_next gets rows m0 .. m0 + 127 (128 contiguous bytes)
+  for (int q = threadIdx.x; q < kTcBM * (kTcBN / 4); q += kTcThreads) {
+    const int r = q / (kTcBN / 4), c = (q % (kTcBN / 4)) * 4;
+    if (m0 + r < s.N && c < cols_valid) {
+      const size_t off = size_t(m0 + r) * s.Cp + n0 + c;
+      const float *px = sx + r * kTileLd + c, *py = sy + r * kTileLd + c;
+      *reinterpret_cast<float4 *>(s.x + off) = make_float4(px[0], px[1], px[2], px[3]);
+      *reinterpret_cast<float4 *>(s.y + off) = make_float4(py[0], py[1], py[2], py[3]);
+    }
+  }
+  // column n0 + c of FT_next gets rows m0 .. m0 + 127 (128 contiguous bytes);
+  // two threads per column, 64 bytes each
   {
-    uint8_t *dst = a.FT + (size_t((n + 1) & 1) * s.Cp + n0 + threadIdx.x) * a.Kp + m0;
-    const uint4 *src = reinterpret_cast<const uint4 *>(sF + threadIdx.x * kTcBM);
+    const int c = threadIdx.x >> 1, part = threadIdx.x & 1;
+    uint8_t *dst = a.FT + (size_t((n + 1) & 1) * s.Cp + n0 + c) * a.Kp + m0 + part * 64;
+    const uint4 *src = reinterpret_cast<const uint4 *>(sF + c * kTcBM + part * 64);
 #pragma unroll
-    for (int q = 0; q < kTcBM / 16; ++q) reinterpret_cast<uint4 *>(dst)[q] = src[q];
+    for (int q = 0; q < 4; ++q) reinterpret_cast<uint4 *>(dst)[q] = src[q];
   }
   if (warp == 0) tc::tmem_dealloc(tmem, 128);
 }
 
-// f(x) int8 [N][Cp] -> e4m3 [Cp][Kp] (zeros for padded spins), for buffer b.
+// f codes [N][Cp] -> e4m3 f [Cp][Kp] (zeros for padded spins), for buffer b.
 __global__ void k_f_to_ft8(StateView s, int which, uint8_t *FT, int Kp, int b) {
   const size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x;  // over Cp * Kp
   if (e >= size_t(s.Cp) * Kp) return;
   const int c = int(e / Kp), j = int(e % Kp);
-  const int8_t f = (j < s.N) ? s.f_of(which)[size_t(j) * s.Cp + c] : int8_t(0);
+  const int8_t f = (j < s.N) ? int8_t(int(s.f_of(which)[size_t(j) * s.Cp + c]) - 1) : int8_t(0);
   FT[size_t(b) * s.Cp * Kp + e] = f_to_e4m3(f);
 }
 
@@ -248,7 +276,7 @@ template <int P>
 static cudaError_t launch_tc_p(const TcPlanImpl *p, const StateView &s, const TcArgs &a, const StepTables &t, int n,
                                cudaStream_t st) {
   dim3 grid(s.Cp / kTcBN, a.Kp / kTcBM);
-  k_step_dense_tc<P><<<grid, 128, kTcSmem, st>>>(p->tmA, p->tmB, s, a, t, n);
+  k_step_dense_tc<P><<<grid, kTcThreads, kTcSmem, st>>>(p->tmA, p->tmB, s, a, t, n);
   return cudaGetLastError();
 }
 

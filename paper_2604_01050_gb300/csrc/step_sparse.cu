@@ -1,12 +1,16 @@
 // step_sparse.cu -- one SBQA step for CSR couplings (Sec. II A, Eq. 7 with a
 // sparse J), the coupling product and the update fused in one kernel.
 //
-// A warp owns one spin row i and 128 replica columns (4 per lane).  The row's
-// (col, J) entries are read once per warp (uniform broadcast loads); for each
-// entry the lane reads 4 bytes of F (f(x) of the neighbour spin for its 4
-// columns).  Accumulation:
-//   VAL_PM1   J = +-1: packed byte adds (__vadd4 / __vsub4), exact while the
-//             row degree is <= 127 (checked on the host)
+// A warp owns one spin row i and walks all its replica columns in chunks of
+// 32 W (W = 4, 8 or 16 consecutive columns per lane, picked per problem shape
+// by the autotuner).  The row's (col, J) entries are read 32 at a time, one
+// per lane, and broadcast by shuffle; the lane gathers W bytes of F (the f
+// codes of the neighbour spin for its columns) for several entries at once,
+// so the gathers overlap.  The x, y loads are issued before the product.
+// Accumulation:
+//   VAL_PM1   J = +-1: plain 32-bit adds of packed f + 1 codes, one sum per
+//             sign (rows are stored +1 entries first), exact while the row
+//             degree is <= 127 (checked on the host)
 //   VAL_F32   FP32 J, FP32 accumulation (exact for small-integer J)
 //   VAL_BF16  bfloat16 J, FP32 accumulation
 // Memory per update: x, y read + write (16 B) + F write (1 B); F gathers and
@@ -17,93 +21,162 @@ namespace sbqa {
 
 template <int KIND>
 __device__ __forceinline__ float load_val(const void *val, int e) {
-  if constexpr (KIND == VAL_PM1) return float(__ldg(static_cast<const int8_t *>(val) + e));
-  else if constexpr (KIND == VAL_F32) return __ldg(static_cast<const float *>(val) + e);
+  if constexpr (KIND == VAL_F32) return __ldg(static_cast<const float *>(val) + e);
   else return __bfloat162float(static_cast<const __nv_bfloat16 *>(val)[e]);
 }
 
-template <int P, int KIND>
-__global__ void __launch_bounds__(256) k_step_csr(StateView s, CsrView J, StepTables t, int n) {
-  const int warps_per_row = s.Cp / kColsPerWarp;
-  const int wid = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int i = wid / warps_per_row;
-  if (i >= s.N) return;  // whole warp leaves together
-  const int lane = threadIdx.x & 31;
-  const int c4 = (wid - i * warps_per_row) * kColsPerWarp + lane * kColsPerLane;
-  const int8_t *Fin = s.f_of(n);
-  int8_t *Fout = s.f_of(n + 1);
-  // state loads first: they do not depend on the product
-  const size_t off = size_t(i) * s.Cp + c4;
-  const float4 xv = *reinterpret_cast<const float4 *>(s.x + off);
-  const float4 yv = *reinterpret_cast<const float4 *>(s.y + off);
+// F codes of W consecutive columns (one 4, 8 or 16 byte load).
+template <int W>
+struct FVec;
+template <>
+struct FVec<4> {
+  uint32_t w[1];
+  __device__ __forceinline__ void load(const uint8_t *p) { w[0] = __ldg(reinterpret_cast<const uint32_t *>(p)); }
+  __device__ __forceinline__ void zero(uint32_t z) { w[0] = z; }
+};
+template <>
+struct FVec<8> {
+  uint32_t w[2];
+  __device__ __forceinline__ void load(const uint8_t *p) {
+    const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
+    w[0] = v.x; w[1] = v.y;
+  }
+  __device__ __forceinline__ void zero(uint32_t z) { w[0] = w[1] = z; }
+};
+template <>
+struct FVec<16> {
+  uint32_t w[4];
+  __device__ __forceinline__ void load(const uint8_t *p) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+    w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+  }
+  __device__ __forceinline__ void zero(uint32_t z) { w[0] = w[1] = w[2] = w[3] = z; }
+};
+
+// One warp per (spin row, chunk of 32 W replica columns), W consecutive
+// columns per lane.  The lane issues its x, y loads, then gathers W bytes of
+// f codes per neighbour (U neighbours at a time), accumulates and runs the
+// update.  The row's (col, J) entries are read 32 at a time, one per lane,
+// and broadcast by shuffle.
+template <int P, int KIND, int W>
+__global__ void __launch_bounds__(256, W == 16 ? 2 : (W == 8 ? 3 : 4))
+    k_step_csr(StateView s, CsrView J, StepTables t, int n) {
+  constexpr int U = W == 16 ? 4 : 8;  // gathers in flight per lane
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + warp;
+  if (i >= s.N) return;  // whole warp
+  const float ka = __ldg(t.ka + n), dnext = __ldg(t.dl + n + 1);
   const float hi = __ldg(J.h + i);
-  const int e0 = __ldg(J.row_ptr + i), deg = __ldg(J.row_ptr + i + 1) - e0;
-  const int8_t *Fc = Fin + c4;
-  uint32_t acc = 0;                  // VAL_PM1: 4 packed int8 sums
-  float g0 = 0.f, g1 = 0.f, g2 = 0.f, g3 = 0.f;
-  // The row's (col, J) entries are read 32 at a time, one per lane, and
-  // broadcast by shuffle; the F gathers of 8 entries are issued together.
-  for (int base = 0; base < deg; base += 32) {
-    const int cnt = min(32, deg - base);
-    int my_col = 0;
-    float my_w = 0.f;
-    if (lane < cnt) {
-      my_col = __ldg(J.col + e0 + base + lane);
-      my_w = load_val<KIND>(J.val, e0 + base + lane);
-    }
-    for (int q = 0; q < cnt; q += 8) {
-      uint32_t f4[8];
+  const int e0 = __ldg(J.row_ptr + i), e1 = __ldg(J.row_ptr + i + 1);
+  const int ep = (KIND == VAL_PM1) ? e0 + __ldg(J.npos + i) : e1;
+  const uint8_t *Fin = s.f_of(n);
+  uint8_t *Fout = s.f_of(n + 1);
+  // chunk blockIdx.y of 32 W columns (one chunk per warp keeps many warps in flight)
+  {
+    const int cw = blockIdx.y * 32 * W;
+    const int c0 = cw + lane * W;
+    float xs[W], ys[W];
+    {
+      const size_t off = size_t(i) * s.Cp + c0;
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int j = __shfl_sync(0xffffffffu, my_col, q + u);
-        f4[u] = (q + u < cnt) ? __ldg(reinterpret_cast<const uint32_t *>(Fc + size_t(j) * s.Cp)) : 0u;
+      for (int q = 0; q < W / 4; ++q) {
+        const float4 a = *reinterpret_cast<const float4 *>(s.x + off + 4 * q);
+        const float4 b = *reinterpret_cast<const float4 *>(s.y + off + 4 * q);
+        xs[4 * q] = a.x; xs[4 * q + 1] = a.y; xs[4 * q + 2] = a.z; xs[4 * q + 3] = a.w;
+        ys[4 * q] = b.x; ys[4 * q + 1] = b.y; ys[4 * q + 2] = b.z; ys[4 * q + 3] = b.w;
       }
+    }
+    uint32_t ap[W / 4], am[W / 4];
+    float g[W];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const float w = __shfl_sync(0xffffffffu, my_w, q + u);
-        if constexpr (KIND == VAL_PM1) {
-          acc = (w > 0.f) ? __vadd4(acc, f4[u]) : __vsub4(acc, f4[u]);  // f4 = 0 past the row end
-        } else {
-          g0 = fmaf(w, sbyte(f4[u], 0), g0);
-          g1 = fmaf(w, sbyte(f4[u], 1), g1);
-          g2 = fmaf(w, sbyte(f4[u], 2), g2);
-          g3 = fmaf(w, sbyte(f4[u], 3), g3);
+    for (int q = 0; q < W / 4; ++q) ap[q] = am[q] = 0;
+#pragma unroll
+    for (int q = 0; q < W; ++q) g[q] = 0.f;
+    const uint8_t *Fc = Fin + c0;
+    for (int base = e0; base < e1; base += 32) {
+      const int cnt = min(32, e1 - base);
+      int my_col = 0;
+      float my_w = 0.f;
+      if (lane < cnt) {
+        my_col = __ldg(J.col + base + lane);
+        if constexpr (KIND != VAL_PM1) my_w = load_val<KIND>(J.val, base + lane);
+      }
+      for (int q = 0; q < cnt; q += U) {
+        FVec<W> f[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          const int j = __shfl_sync(0xffffffffu, my_col, q + u);
+          if (q + u < cnt) f[u].load(Fc + size_t(j) * s.Cp);
+          else f[u].zero(KIND == VAL_PM1 ? 0u : kFZero4);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if constexpr (KIND == VAL_PM1) {
+            if (base + q + u < ep) {  // warp-uniform
+#pragma unroll
+              for (int w = 0; w < W / 4; ++w) ap[w] += f[u].w[w];
+            } else {
+#pragma unroll
+              for (int w = 0; w < W / 4; ++w) am[w] += f[u].w[w];
+            }
+          } else {
+            const float wt = __shfl_sync(0xffffffffu, my_w, q + u);  // 0 past the row end
+#pragma unroll
+            for (int c = 0; c < W; ++c) g[c] = fmaf(wt, fdec(f[u].w[c / 4], c % 4), g[c]);
+          }
         }
       }
     }
-  }
-  float G[4];
-  if constexpr (KIND == VAL_PM1) {
+    float G[W];
+    if constexpr (KIND == VAL_PM1) {
+      const int bias = (e1 - ep) - (ep - e0);  // codes carry f + 1
 #pragma unroll
-    for (int q = 0; q < 4; ++q) G[q] = sbyte(acc, q);
-  } else {
-    G[0] = g0; G[1] = g1; G[2] = g2; G[3] = g3;
+      for (int c = 0; c < W; ++c)
+        G[c] = float(int((ap[c / 4] >> (8 * (c % 4))) & 0xffu) - int((am[c / 4] >> (8 * (c % 4))) & 0xffu) + bias);
+    } else {
+#pragma unroll
+      for (int c = 0; c < W; ++c) G[c] = g[c];
+    }
+    sb_updateW<P, W>(s, t, ka, dnext, n, i, c0, G, hi, xs, ys, Fout);
   }
-  sb_update4<P>(s, t, n, i, c4, G, hi, xv, yv, Fout);
 }
 
-template <int P>
-static cudaError_t launch_p(const StateView &s, const CsrView &J, const StepTables &t, int n,
-                            cudaStream_t st) {
-  const long long warps = (long long)s.N * (s.Cp / kColsPerWarp);
-  const unsigned blocks = unsigned((warps + 7) / 8);
+template <int P, int W>
+static cudaError_t launch_pw(const StateView &s, const CsrView &J, const StepTables &t, int n, cudaStream_t st) {
+  const dim3 blocks(unsigned((s.N + 7) / 8), unsigned(s.Cp / (32 * W)));
   switch (J.kind) {
-    case VAL_PM1: k_step_csr<P, VAL_PM1><<<blocks, 256, 0, st>>>(s, J, t, n); break;
-    case VAL_F32: k_step_csr<P, VAL_F32><<<blocks, 256, 0, st>>>(s, J, t, n); break;
-    default: k_step_csr<P, VAL_BF16><<<blocks, 256, 0, st>>>(s, J, t, n); break;
+    case VAL_PM1: k_step_csr<P, VAL_PM1, W><<<blocks, 256, 0, st>>>(s, J, t, n); break;
+    case VAL_F32: k_step_csr<P, VAL_F32, W><<<blocks, 256, 0, st>>>(s, J, t, n); break;
+    default: k_step_csr<P, VAL_BF16, W><<<blocks, 256, 0, st>>>(s, J, t, n); break;
   }
   return cudaGetLastError();
 }
 
-cudaError_t launch_step_csr(const StateView &s, const CsrView &J, const StepTables &t, int n,
+template <int P>
+static cudaError_t launch_p(const StateView &s, const CsrView &J, const StepTables &t, int n, int variant,
                             cudaStream_t st) {
+  switch (variant) {
+    case 2: return launch_pw<P, 16>(s, J, t, n, st);
+    case 1: return launch_pw<P, 8>(s, J, t, n, st);
+    default: return launch_pw<P, 4>(s, J, t, n, st);
+  }
+}
+
+// Variants: W = 4, 8, 16 columns per lane; W needs Cp to be a multiple of 32 W.
+int csr_step_variants() { return 3; }
+
+bool csr_step_variant_ok(int variant, int Cp) { return Cp % (32 * (4 << variant)) == 0; }
+
+cudaError_t launch_step_csr(const StateView &s, const CsrView &J, const StepTables &t, int n, int variant,
+                            cudaStream_t st) {
+  if (!csr_step_variant_ok(variant, s.Cp)) variant = 0;
   switch (s.P) {
-    case 1: return launch_p<1>(s, J, t, n, st);
-    case 2: return launch_p<2>(s, J, t, n, st);
-    case 4: return launch_p<4>(s, J, t, n, st);
-    case 8: return launch_p<8>(s, J, t, n, st);
-    case 16: return launch_p<16>(s, J, t, n, st);
-    case 32: return launch_p<32>(s, J, t, n, st);
+    case 1: return launch_p<1>(s, J, t, n, variant, st);
+    case 2: return launch_p<2>(s, J, t, n, variant, st);
+    case 4: return launch_p<4>(s, J, t, n, variant, st);
+    case 8: return launch_p<8>(s, J, t, n, variant, st);
+    case 16: return launch_p<16>(s, J, t, n, variant, st);
+    case 32: return launch_p<32>(s, J, t, n, variant, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -1,0 +1,101 @@
+"""The batching engine: mixed requests (sparse +-1, sparse BF16, dense on the
+tensor cores, dense on CUDA cores, ragged shapes) give exactly the result of
+solving each alone with sbqa_run, whatever the mix, the chunk size and the
+admission order."""
+import numpy as np
+import pytest
+
+import workloads
+from sbqa_cases import create, dense_int, lattice, regular, sk
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sb():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2604_01050_gb300 import build as b
+    b.build()
+    import paper_2604_01050_gb300 as s
+    return s
+
+
+def _requests(sb):
+    """(problem handle, steps, P, R, seed, precision) of a mixed workload."""
+    out = []
+    for k, (spec, steps, P, R, prec) in enumerate([
+            (lattice(8, 1)[1], 90, 8, 4, "auto"),
+            (regular(500, 6, 3)[1], 130, 16, 2, "bf16"),
+            (sk(300, 2)[1], 70, 8, 3, "exact"),       # tcgen05 FP8 path
+            (sk(100, 5)[1], 100, 4, 5, "auto"),       # dense CUDA-core path
+            (lattice(5, 2)[1], 50, 2, 3, "auto"),     # ragged columns
+            (dense_int(260, 7, jmax=2)[1], 64, 32, 2, "exact"),
+    ]):
+        pb = create(sb, spec)
+        sb.set_schedule(pb, *workloads.autotune_params(R, k), precision=prec, eval_every=0)
+        out.append((pb, steps, P, R, 100 + k))
+    return out
+
+
+def _alone(sb, req):
+    pb, steps, P, R, seed = req
+    sb.run(pb, steps, P, R, seed=seed)
+    return sb.get_best(pb)
+
+
+@pytest.mark.parametrize("chunk,slots,arena_mb", [(32, 16, 512), (7, 3, 512), (50, 16, 40)])
+def test_engine_mix_equals_alone(sb, chunk, slots, arena_mb):
+    reqs = _requests(sb)
+    alone = [_alone(sb, r) for r in reqs]
+    eng = sb.engine_create(arena_mb << 20, slots, chunk)
+    ids = [sb.engine_submit(eng, *r) for r in reqs]
+    done = []
+    for _ in range(10000):
+        done += sb.engine_step(eng)
+        st = sb.engine_stats(eng)
+        assert st["active"] <= slots and st["arena_used"] <= st["arena_bytes"]
+        if len(done) == len(ids):
+            break
+    assert sorted(done) == ids
+    for rid, ref in zip(ids, alone):
+        got = sb.engine_result(eng, rid)
+        assert np.array_equal(got["spins"], ref["spins"]), rid
+        assert np.array_equal(got["energy"], ref["energy"]), rid
+        assert np.array_equal(got["replica"], ref["replica"]), rid
+    st = sb.engine_stats(eng)
+    assert st["finished"] == len(ids) and st["queued"] == 0 and st["active"] == 0 and st["arena_used"] == 0
+
+
+def test_engine_admission_waits_for_memory(sb):
+    """An arena that holds one lattice request at a time runs them one after another."""
+    n, rp, col, val, h = workloads.cubic_lattice(10, 0)
+    pb = sb.create_problem_csr(n, rp, col, val, h)
+    sb.set_schedule(pb, *workloads.autotune_params(8, 0))
+    one = 1000 * 8 * 4 * 11 + (8 << 20) // 8  # about one request's state
+    eng = sb.engine_create(max(one, 1 << 20) * 2, 8, 25)
+    ids = [sb.engine_submit(eng, pb, 60, 16, 8, seed=s) for s in range(3)]
+    order = []
+    while len(order) < 3:
+        order += sb.engine_step(eng)
+        assert sb.engine_stats(eng)["active"] <= 2
+    assert sorted(order) == ids
+    for rid, s in zip(ids, range(3)):
+        sb.run(pb, 60, 16, 8, seed=s)
+        assert np.array_equal(sb.engine_result(eng, rid)["energy"], sb.get_best(pb)["energy"])
+
+
+def test_engine_rejects_bad_requests(sb):
+    pb, spec = sk(32, 0)
+    prob = create(sb, spec)
+    eng = sb.engine_create(64 << 20, 4, 10)
+    with pytest.raises(sb.SBQAError) as e:
+        sb.engine_submit(eng, prob, 10, 8, 2)
+    assert e.value.status == sb.ERR_STATE  # no schedule yet
+    sb.set_schedule(prob)
+    with pytest.raises(sb.SBQAError) as e:
+        sb.engine_submit(eng, prob, 10, 3, 2)
+    assert e.value.status == sb.ERR_UNSUPPORTED
+    with pytest.raises(sb.SBQAError) as e:
+        sb.engine_result(eng, 0)
+    assert e.value.status == sb.ERR_INVALID_ARG
