@@ -276,18 +276,18 @@ def run_tte(args):
     for sd in range(8):
         sb.run(prob, 20 * S, P, R, seed=900 + sd)
         E0 = min(E0, float(sb.get_best(prob)["energy"].min()))
-    target = E0 + eps * abs(E0)
+    eps_list = sorted({eps, 0.06, 0.08, 0.10})
     reps = 5
     # fused path: whole solves through the C ABI (init, steps, readout, best to host)
     sb.run(prob, S, P, R, seed=7)
     sb.get_best(prob)
     t0 = time.perf_counter()
-    hits = []
+    best_f = []
     for k in range(reps):
         sb.run(prob, S, P, R, seed=7 + k)
-        hits.append(sb.get_best(prob)["energy"] <= target)
+        best_f.append(sb.get_best(prob)["energy"])
     t_fused = (time.perf_counter() - t0) / reps
-    p_fused = float(np.mean(hits))
+    best_f = np.concatenate(best_f)
     # plain path: same initial states and tables, FP32 torch ops per step
     ka, dl, kj = schedule_tables(S, P, R, beta, alpha, gamma0=args.gamma0)
     c0 = 0.5 * math.sqrt(n / float(np.sum(val ** 2)))
@@ -305,17 +305,24 @@ def run_tte(args):
     plain_fp32_solve(Jt, None, 20, P, R, starts[0][0], starts[0][1], tabs, kc, kx, dev)  # warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    hits = []
+    best_p = []
     for k in range(reps):
         xf = plain_fp32_solve(Jt, None, S, P, R, starts[k][0], starts[k][1], tabs, kc, kx, dev)
         spins = torch.where(xf >= 0, 1.0, -1.0)
         e = -0.5 * (spins * (Jt @ spins)).sum(dim=0).double()
-        best = e.view(R, P).min(dim=1).values.cpu().numpy()
-        hits.append(best <= target)
+        best_p.append(e.view(R, P).min(dim=1).values.cpu().numpy())
     t_plain = (time.perf_counter() - t0) / reps
-    p_plain = float(np.mean(hits))
-    tte_f = tte_seconds(t_fused / R, p_fused)
-    tte_p = tte_seconds(t_plain / R, p_plain)
+    best_p = np.concatenate(best_p)
+    per_eps = {}
+    for e_ in eps_list:
+        target = E0 + e_ * abs(E0)
+        pf, pp = float(np.mean(best_f <= target)), float(np.mean(best_p <= target))
+        tf, tp = tte_seconds(t_fused / R, pf), tte_seconds(t_plain / R, pp)
+        per_eps["%g" % e_] = {"p_fused": pf, "p_plain": pp, "tte_fused_s": tf, "tte_plain_s": tp,
+                              "speedup": (tp / tf) if math.isfinite(tp) and math.isfinite(tf) else None}
+    head = per_eps["%g" % eps]
+    p_fused, p_plain, tte_f, tte_p = head["p_fused"], head["p_plain"], head["tte_fused_s"], head["tte_plain_s"]
+    gaps_f = (best_f - E0) / abs(E0)
     line = {"metric": "time-to-epsilon", "value": tte_f, "unit": "s", "n_gpus": 1, "steps": reps, "warmup": 1,
             "ms_per_step": 1e3 * t_fused, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
@@ -325,7 +332,8 @@ def run_tte(args):
                        "p_target": 0.99},
             "fused": {"s_per_solve": t_fused, "p_success": p_fused, "tte_s": tte_f},
             "plain_fp32_torch": {"s_per_solve": t_plain, "p_success": p_plain, "tte_s": tte_p},
-            "tte_speedup": (tte_p / tte_f) if math.isfinite(tte_p) and math.isfinite(tte_f) else None}
+            "tte_speedup": head["speedup"], "per_epsilon": per_eps,
+            "gap_quantiles_fused": [float(np.quantile(gaps_f, q)) for q in (0.0, 0.1, 0.5, 0.9)]}
     print(json.dumps(line))
     return 0
 
@@ -341,10 +349,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--requests", type=int, default=48, help="serving: requests in the stream")
-    ap.add_argument("--eps", type=float, default=0.01, help="tte: target optimality gap")
+    ap.add_argument("--eps", type=float, default=0.08, help="tte: target optimality gap of the headline")
     ap.add_argument("--gamma0", type=float, default=16.0, help="tte: Gamma_x(0)")
     ap.add_argument("--tte-L", type=int, default=10)
-    ap.add_argument("--tte-steps", type=int, default=1000)
+    ap.add_argument("--tte-steps", type=int, default=2000)
     args = ap.parse_args()
     if args.config == "serving":
         return run_serving(args)
@@ -468,7 +476,7 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = oracle_sample(cfg, target_s=args.ref_seconds)
-    launches_per_solve = 2 + S + 4
+    launches_per_solve = 1 if info.step_kernel == 3 else 2 + S + 4
     line = {
         "metric": "replica-spin updates/s", "value": value, "unit": "replica-spin updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_solve,
@@ -479,7 +487,7 @@ def main():
                                                    "state (%.0f MB) stays L2-resident within a solve"
                                                    % (N * P * R * 10 / 1e6),
                    "parallelism": "independent runs per GPU (weak scaling)",
-                   "step_kernel": ["csr", "dense_cuda_core", "dense_tcgen05_fp8"][info.step_kernel],
+                   "step_kernel": ["csr", "dense_cuda_core", "dense_tcgen05_fp8", "dense_small_one_launch"][info.step_kernel],
                    "csr_variant": info.step_variant,
                    "autotune_ms_per_step": [round(v, 5) for v in info.variant_ms]},
         "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",

@@ -107,7 +107,8 @@ typedef struct {
     int32_t max_abs_j;  /* max |J_ij| if integer, else -1                  */
     double c0_auto;     /* default c0 = 0.5 sqrt(n / sum_ij J_ij^2)        */
     int32_t step_kernel;  /* coupling-product kernel of the last run: 0 CSR,
-                             1 dense CUDA cores, 2 dense tcgen05 FP8; -1 none */
+                             1 dense CUDA cores, 2 dense tcgen05 FP8, 3 the
+                             one-launch small dense solver; -1 none        */
     int32_t step_variant; /* CSR kernel variant picked by the autotuner:
                              4 << v consecutive replica columns per lane;
                              -1 before the first run                      */

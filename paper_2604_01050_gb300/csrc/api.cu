@@ -267,14 +267,15 @@ int alloc_run(sbqa_problem *p, int S, int P, int R) {
   p->S = S; p->P = P; p->R = R; p->C = C; p->Cp = Cp;
   if (p->use_tc) {
     SBQA_CUDA(p->d_FT.alloc(size_t(2) * Cp * p->Kp));
-    if (!p->tc_plan || p->tc_plan_ft != p->d_FT.p || p->tc_plan_cp != Cp) {
+    if (!p->tc_plan || p->tc_plan_ft != p->d_FT.p || p->tc_plan_cp != Cp || p->tc_plan_x != p->d_x.p) {
       if (p->tc_plan) tc_plan_free(p->tc_plan);
       p->tc_plan = nullptr;
-      if (!tc_plan_make(&p->tc_plan, p->d_J8.p, p->d_FT.p, p->Kp, Cp))
+      if (!tc_plan_make(&p->tc_plan, p->d_J8.p, p->d_FT.p, p->Kp, Cp, p->d_x.p, p->d_y.p, p->n))
         return fail(SBQA_ERR_CUDA, "cuTensorMapEncodeTiled failed");
       SBQA_CUDA(tc_set_attributes());
       p->tc_plan_ft = p->d_FT.p;
       p->tc_plan_cp = Cp;
+      p->tc_plan_x = p->d_x.p;
     }
   }
   return SBQA_OK;
@@ -581,7 +582,7 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info) {
   info->is_integer = p->is_integer ? 1 : 0;
   info->max_abs_j = p->max_abs_j;
   info->c0_auto = p->c0_auto;
-  info->step_kernel = !p->begun ? -1 : (p->use_tc ? 2 : (p->dense ? 1 : 0));
+  info->step_kernel = !p->begun ? -1 : (p->small_path ? 3 : (p->use_tc ? 2 : (p->dense ? 1 : 0)));
   info->step_variant = p->dense ? -1 : p->csr_variant;
   for (int v = 0; v < 4; ++v) info->variant_ms[v] = p->variant_ms[v];
   return SBQA_OK;
@@ -620,6 +621,7 @@ int sbqa_run_begin(sbqa_problem *p, int32_t steps, int32_t P, int32_t R, uint64_
   int rc = check_run_args(p, steps, P, R);
   if (rc != SBQA_OK) return rc;
   DeviceGuard g(p->device);
+  p->small_path = false;
   p->stream = static_cast<cudaStream_t>(stream);
   p->begun = p->finished = false;
   rc = p->dense ? prepare_dense_values(p, p->prm.precision) : prepare_sparse_values(p, p->prm.precision);
@@ -659,6 +661,33 @@ int sbqa_run_finish(sbqa_problem *p) {
 }
 
 int sbqa_run(sbqa_problem *p, int32_t steps, int32_t P, int32_t R, uint64_t seed, void *stream) {
+  // small integer dense instances: the whole solve in one launch
+  if (p && p->have_params && p->dense && p->is_integer && p->prm.eval_every == 0 &&
+      check_run_args(p, steps, P, R) == SBQA_OK && small_eligible(p->n, P, steps)) {
+    DeviceGuard g(p->device);
+    p->stream = static_cast<cudaStream_t>(stream);
+    p->begun = p->finished = false;
+    int rc = prepare_dense_values(p, p->prm.precision);
+    if (rc == SBQA_OK && !p->use_tc) {
+      if ((rc = alloc_run(p, steps, P, R)) != SBQA_OK) return rc;
+      if ((rc = build_tables(p)) != SBQA_OK) return rc;
+      SmallArgs a{};
+      a.N = p->n; a.P = P; a.R = R; a.S = steps; a.Cp = p->Cp; a.seed = seed;
+      a.amp = float(p->prm.init_amp); a.kc = p->tables.kc; a.kx = p->tables.kx;
+      a.J = p->d_dense_f32.p; a.ka = p->d_ka.p; a.dl = p->d_dl.p; a.kj = p->d_kj.p; a.h = p->d_h.p;
+      a.J_i32 = p->d_e_i32.p; a.h_i64 = p->d_h_i64.p;
+      a.x = p->d_x.p; a.y = p->d_y.p; a.Sg = p->d_Sg.p; a.e_int = p->d_ei.p; a.e_f64 = p->d_ef.p;
+      a.best_e_int = p->d_best_ei.p; a.best_e = p->d_best_e.p; a.best_k = p->d_best_k.p;
+      a.best_step = p->d_best_step.p; a.have_best = p->d_have.p; a.best_spins = p->d_best_spins.p;
+      SBQA_CUDA(cudaMemsetAsync(p->d_err.p, 0, sizeof(int), p->stream));
+      SBQA_CUDA(launch_solve_small(a, p->stream));
+      p->step_done = steps;
+      p->begun = p->finished = true;
+      p->small_path = true;
+      return SBQA_OK;
+    }
+    if (rc != SBQA_OK) return rc;
+  }
   int rc = sbqa_run_begin(p, steps, P, R, seed, stream);
   if (rc != SBQA_OK) return rc;
   DeviceGuard g(p->device);

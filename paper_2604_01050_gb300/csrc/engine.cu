@@ -205,7 +205,7 @@ int admit(sbqa_engine *e, Request &r, int slot, cudaStream_t st) {
   int rc = problem_build_tables(p, r.S, r.P, r.R, r.ka, r.dl, r.kj, &r.tables, st);
   if (rc != SBQA_OK) return rc;
   if (tc) {
-    if (!tc_plan_make(&r.tc_plan, p->d_J8.p, r.FT, p->Kp, r.Cp))
+    if (!tc_plan_make(&r.tc_plan, p->d_J8.p, r.FT, p->Kp, r.Cp, r.x, r.y, p->n))
       return set_error(SBQA_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     ENG_CUDA(tc_set_attributes());
   }

@@ -83,6 +83,28 @@ struct BestView {
 // returns code.
 int set_error(int code, const std::string &msg);
 
+// Whole solve of a small integer dense instance in one launch (solve_small.cu).
+struct SmallArgs {
+  int N, P, R, S, Cp;
+  uint64_t seed;
+  float amp, kc, kx;
+  const float *J;        // [N][N] FP32
+  const float *ka, *dl, *kj;
+  const float *h;        // [N]
+  const int32_t *J_i32;  // [N][N]
+  const int64_t *h_i64;  // [N]
+  float *x, *y;          // [N][Cp]
+  int8_t *Sg;
+  int64_t *e_int;
+  double *e_f64;
+  int64_t *best_e_int;
+  double *best_e;
+  int32_t *best_k, *best_step, *have_best;
+  int8_t *best_spins;
+};
+bool small_eligible(int N, int P, int S);
+cudaError_t launch_solve_small(const SmallArgs &a, cudaStream_t st);
+
 // One active request of the batching engine (device copy, read by the
 // batched step kernel).
 struct SlotDesc {
@@ -117,8 +139,9 @@ cudaError_t launch_step_csr(const StateView &s, const CsrView &J, const StepTabl
 cudaError_t launch_step_dense(const StateView &s, const DenseView &J, const StepTables &t,
                               int n, cudaStream_t st);
 // Dense integer couplings on tcgen05 (step_dense_tc.cu).  The plan holds the
-// TMA descriptors of J8 [Kp][Kp] and FT [2][Cp][Kp] (e4m3).
-bool tc_plan_make(void **plan, const uint8_t *J8, uint8_t *FT, int Kp, int Cp);
+// TMA descriptors of J8 [Kp][Kp] and FT [2][Cp][Kp] (e4m3) and of the state
+// x, y [N][Cp] (FP32) of one run batch.
+bool tc_plan_make(void **plan, const uint8_t *J8, uint8_t *FT, int Kp, int Cp, float *x, float *y, int N);
 void tc_plan_free(void *plan);
 cudaError_t tc_set_attributes();  // dynamic shared memory limit of the tcgen05 kernels
 cudaError_t launch_step_dense_tc(const void *plan, const StateView &s, int Kp, uint8_t *FT, int *err,

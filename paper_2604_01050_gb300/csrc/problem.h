@@ -74,6 +74,7 @@ struct sbqa_problem {
   sbqa::DevBuf<uint8_t> d_J8, d_FT;
   void *tc_plan = nullptr;
   const void *tc_plan_ft = nullptr;  // FT buffer the plan was made for
+  const void *tc_plan_x = nullptr;   // state buffer the plan was made for
   int tc_plan_cp = 0;
   sbqa::DevBuf<int> d_err;
   sbqa::DevBuf<float> d_h;
@@ -91,6 +92,7 @@ struct sbqa_problem {
   // run state
   int S = 0, P = 0, R = 0, C = 0, Cp = 0;
   int step_done = 0;
+  bool small_path = false;  // the last sbqa_run used the one-launch small solver
   bool begun = false, finished = false;
   cudaStream_t stream = nullptr;
   int kind = VAL_F32;  // sparse value kind in use

@@ -268,7 +268,6 @@ __device__ __forceinline__ void sb_updateW(const StateView &s, const StepTables 
   uint32_t code[W / 4];
 #pragma unroll
   for (int q = 0; q < W / 4; ++q) code[q] = 0;
-#pragma unroll
   // dt * J_perp of the run of each column (one load per run in the lane)
   float kjv[W];
   if constexpr (P >= W) {

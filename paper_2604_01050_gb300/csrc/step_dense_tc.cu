@@ -12,14 +12,15 @@
 //   B = FT8  [2][Cp][Kp]              e4m3 f(x) transposed (column c, spin j),
 //                                     K-major, double-buffered by step parity
 // Tile: 128 spin rows x 128 replica columns per CTA (one wave of 128 CTAs for
-// N = 2000, R*P = 1024).  Six TMA stages of 128 x 128-byte tiles of A and B
+// N = 2000, R*P = 1024).  Three TMA stages of 128 x 128-byte tiles of A and B
 // (128-byte swizzle) feed tcgen05.mma M=128 N=128 K=32 (4 per stage); the
 // FP32 accumulator lives in 128 TMEM columns.  Thread 0 of warp 0 issues the
-// TMA loads, thread 0 of warp 1 the MMAs.  Afterwards the x, y tiles are
-// brought into shared memory with coalesced loads, every warp reads its 32
-// TMEM lanes (= spin rows) for 64 columns and runs the SBQA update on whole
-// runs of 32 columns, the tiles go back with coalesced stores, and f(x_next)
-// (staged in shared memory) is stored transposed into the other FT8 buffer.
+// TMA loads -- the operand stages and, behind the first stages, the x and y
+// tiles of the CTA (4 boxes of 128 rows x 32 floats each) -- and thread 0 of
+// warp 1 the MMAs.  The epilogue then works in shared memory: every warp
+// reads its 32 TMEM lanes (= spin rows) for 64 columns, updates whole runs of
+// 32 columns in place in the swizzled state boxes and stages f(x_next) as
+// e4m3; finally one thread stores x, y and the transposed f tile with TMA.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -28,10 +29,12 @@
 
 namespace sbqa {
 
-constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 128, kTcStages = 6;
-constexpr int kTcThreads = 256;  // 8 warps: all run the epilogue
-constexpr int kTcTile = kTcBM * kTcBK;  // bytes of one operand stage (e4m3)
-constexpr int kTcSmem = 2 * kTcStages * kTcTile + 1024 + 256;
+constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 128, kTcStages = 3;
+constexpr int kTcThreads = 256;          // 8 warps: all run the epilogue
+constexpr int kTcTile = kTcBM * kTcBK;   // bytes of one operand stage (e4m3)
+constexpr int kTcBox = kTcBM * 128;      // one 128-row x 32-float state box (16 KB)
+constexpr int kTcStateTile = 4 * kTcBox; // x or y tile, 128 rows x 128 columns (64 KB)
+constexpr int kTcSmem = 2 * kTcStages * kTcTile + 2 * kTcStateTile + 1024 + 128;
 constexpr uint8_t kE4M3One = 0x38, kE4M3MinusOne = 0xB8;
 
 struct TcArgs {
@@ -41,35 +44,50 @@ struct TcArgs {
   const float *h;
 };
 
+struct TcMaps {
+  CUtensorMap A, B;  // J8 and FT operand tiles (128 x 128 bytes, 128B swizzle)
+  CUtensorMap X, Y;  // x, y state boxes (128 rows x 32 floats, 128B swizzle)
+  CUtensorMap Fst;   // FT tile store (128 columns x 128 spins bytes, no swizzle)
+};
+
 __device__ __forceinline__ uint8_t f_to_e4m3(int8_t f) {
   return f == 0 ? uint8_t(0) : (f > 0 ? kE4M3One : kE4M3MinusOne);
 }
 
-constexpr int kTileLd = kTcBN + 1;  // padded row of the x, y tiles in shared memory (conflict-free columns)
+// Address of the float4 (16-byte chunk u, 0..7) of row r inside a 128B-swizzled
+// box of 128-byte rows: chunks are permuted by XOR with r mod 8.
+__device__ __forceinline__ float4 *box_chunk(uint8_t *box, int r, int u) {
+  return reinterpret_cast<float4 *>(box + r * 128 + ((u ^ (r & 7)) << 4));
+}
 
 // Update of one spin row for 32 aligned columns c0..c0+31 (whole runs,
-// because P divides 32); x and y are read from and written back to rows of
-// the shared-memory tiles.  Same arithmetic, in the same order, as sb_update4.
+// because P divides 32); x and y are read from and written back to one row of
+// the swizzled shared-memory state boxes.  Same arithmetic, in the same
+// order, as sb_update4.
 template <int P>
-__device__ __forceinline__ void sb_update_row32(const StateView &s, const StepTables &t, int n, int c0,
-                                                const uint32_t (&g)[32], float hi, float *xr, float *yr,
-                                                int8_t (&f)[32]) {
+__device__ __forceinline__ void sb_update_row32(const StateView &s, const StepTables &t, float ka, float dnext,
+                                                const float *kjn, int c0, const uint32_t (&g)[32], float hi,
+                                                uint8_t *xbox, uint8_t *ybox, int r, int8_t (&f)[32]) {
   float xs[32], ys[32];
 #pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    xs[j] = xr[j];
-    ys[j] = yr[j];
+  for (int u = 0; u < 8; ++u) {
+    const float4 a = *box_chunk(xbox, r, u), b = *box_chunk(ybox, r, u);
+    xs[4 * u] = a.x; xs[4 * u + 1] = a.y; xs[4 * u + 2] = a.z; xs[4 * u + 3] = a.w;
+    ys[4 * u] = b.x; ys[4 * u + 1] = b.y; ys[4 * u + 2] = b.z; ys[4 * u + 3] = b.w;
   }
-  const float ka = t.ka[n];
-  const float dnext = t.dl[n + 1];
-  const float *kjn = t.kj + size_t(n) * t.R;
+  float kjv[32 / (P < 32 ? P : 32)];
+#pragma unroll
+  for (int q = 0; q < 32 / (P < 32 ? P : 32); ++q) kjv[q] = (c0 + q * P < s.C) ? __ldg(kjn + c0 / P + q) : 0.f;
+  float xo[32], yo[32];
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
     const int k = j % P, base = j - k;
     const float xm = xs[base + (k + P - 1) % P], xp = xs[base + (k + 1) % P];
     f[j] = 0;
+    xo[j] = xs[j];
+    yo[j] = ys[j];
     if (c0 + j >= s.C) continue;
-    const float kj = kjn[(c0 + j) / P];
+    const float kj = kjv[j / (P < 32 ? P : 32)];
     float yn = fmaf(t.kc, __uint_as_float(g[j]) + hi, ys[j]);
     yn = fmaf(-ka, xs[j], yn);
     yn = fmaf(kj, xm + xp, yn);
@@ -78,24 +96,31 @@ __device__ __forceinline__ void sb_update_row32(const StateView &s, const StepTa
       xn = copysignf(1.f, xn);
       yn = 0.f;
     }
-    xr[j] = xn;
-    yr[j] = yn;
+    xo[j] = xn;
+    yo[j] = yn;
     f[j] = thresh(xn, dnext);
+  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    *box_chunk(xbox, r, u) = make_float4(xo[4 * u], xo[4 * u + 1], xo[4 * u + 2], xo[4 * u + 3]);
+    *box_chunk(ybox, r, u) = make_float4(yo[4 * u], yo[4 * u + 1], yo[4 * u + 2], yo[4 * u + 3]);
   }
 }
 
 template <int P>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    k_step_dense_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, StateView s,
-                    TcArgs a, StepTables t, int n) {
+    k_step_dense_tc(const __grid_constant__ TcMaps m, StateView s, TcArgs a, StepTables t, int n) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t *sA = smem;
   uint8_t *sB = smem + kTcStages * kTcTile;
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + 2 * kTcStages * kTcTile);
+  uint8_t *sX = smem + 2 * kTcStages * kTcTile;
+  uint8_t *sY = sX + kTcStateTile;
+  uint64_t *full = reinterpret_cast<uint64_t *>(sY + kTcStateTile);
   uint64_t *empty = full + kTcStages;
   uint64_t *done = empty + kTcStages;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+  uint64_t *xy_full = done + 1;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(xy_full + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * kTcBN;
@@ -108,9 +133,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       tc::mbar_init(&empty[q], 1);
     }
     tc::mbar_init(done, 1);
+    tc::mbar_init(xy_full, 1);
     tc::fence_mbar_init();
-    tc::prefetch_tmap(&tmA);
-    tc::prefetch_tmap(&tmB);
+    tc::prefetch_tmap(&m.A);
+    tc::prefetch_tmap(&m.B);
+    tc::prefetch_tmap(&m.X);
+    tc::prefetch_tmap(&m.Y);
   }
   if (warp == 0) tc::tmem_alloc(tmem_slot, 128);
   tc::tc_fence_before();
@@ -119,12 +147,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t tmem = *tmem_slot;
 
   if (warp == 0 && lane == 0) {
+    bool xy_issued = false;
     for (int kb = 0; kb < KB; ++kb) {
       const int st = kb % kTcStages, q = kb / kTcStages;
       if (q > 0 && !tc::mbar_wait(&empty[st], (q - 1) & 1, a.err, tc::ERR_WAIT_EMPTY)) break;
       tc::mbar_arrive_expect_tx(&full[st], 2 * kTcTile);
-      tc::tma_load_2d(sA + st * kTcTile, &tmA, &full[st], kb * kTcBK, m0);
-      tc::tma_load_2d(sB + st * kTcTile, &tmB, &full[st], kb * kTcBK, brow);
+      tc::tma_load_2d(sA + st * kTcTile, &m.A, &full[st], kb * kTcBK, m0);
+      tc::tma_load_2d(sB + st * kTcTile, &m.B, &full[st], kb * kTcBK, brow);
+      if (!xy_issued && (kb == kTcStages - 1 || kb == KB - 1)) {
+        // the state tile, needed only by the epilogue, loads behind the first stages
+        tc::mbar_arrive_expect_tx(xy_full, 2 * kTcStateTile);
+        for (int b = 0; b < 4; ++b) {
+          tc::tma_load_2d(sX + b * kTcBox, &m.X, xy_full, n0 + 32 * b, m0);
+          tc::tma_load_2d(sY + b * kTcBox, &m.Y, xy_full, n0 + 32 * b, m0);
+        }
+        xy_issued = true;
+      }
     }
   } else if (warp == 1 && lane == 0) {
     constexpr uint32_t idesc = tc::idesc_f8_e4m3(kTcBM, kTcBN);
@@ -142,43 +180,29 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc::mma_commit(done);
   }
   __syncwarp();
-
-  tc::mbar_wait(done, 0, a.err, tc::ERR_WAIT_DONE);
-  tc::tc_fence_after();
-
-  // Epilogue.  The operand stages are consumed; their memory now holds the
-  // x and y tiles (128 rows x 128 columns, padded rows) and the f codes of
-  // the next step.  Global x, y are read and written with coalesced
-  // row-contiguous accesses; each thread then works on one spin row.
-  float *sx = reinterpret_cast<float *>(smem);
-  float *sy = sx + kTcBM * kTileLd;
-  uint8_t *sF = reinterpret_cast<uint8_t *>(sy + kTcBM * kTileLd);  // [128 columns][128 rows]
-  const int cols_valid = min(kTcBN, s.C - n0);  // multiple of P, hence of 4 when P >= 4
-  for (int q = threadIdx.x; q < kTcBM * (kTcBN / 4); q += kTcThreads) {
-    const int r = q / (kTcBN / 4), c = (q % (kTcBN / 4)) * 4;
-    if (m0 + r < s.N && c < cols_valid) {
-      const size_t off = size_t(m0 + r) * s.Cp + n0 + c;
-      const float4 xv = *reinterpret_cast<const float4 *>(s.x + off);
-      const float4 yv = *reinterpret_cast<const float4 *>(s.y + off);
-      float *px = sx + r * kTileLd + c, *py = sy + r * kTileLd + c;
-      px[0] = xv.x; px[1] = xv.y; px[2] = xv.z; px[3] = xv.w;
-      py[0] = yv.x; py[1] = yv.y; py[2] = yv.z; py[3] = yv.w;
-    }
-  }
-  __syncthreads();
-  // warp w: TMEM lanes 32 (w % 4) .. + 31 (= spin rows), columns 64 (w / 4) .. + 63
+  const float ka = __ldg(t.ka + n), dnext = __ldg(t.dl + n + 1);
+  const float *kjn = t.kj + size_t(n) * t.R;
   const int quarter = warp & 3, half = warp >> 2;
   const int rl = quarter * 32 + lane;
   const int i = m0 + rl;
+  const float hi = i < s.N ? __ldg(a.h + i) : 0.f;
+  tc::mbar_wait(done, 0, a.err, tc::ERR_WAIT_DONE);
+  tc::mbar_wait(xy_full, 0, a.err, tc::ERR_WAIT_FULL);
+  tc::tc_fence_after();
+
+  // Epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (= spin rows) and
+  // columns 64 (w / 4) .. + 63 in two chunks of 32 (one state box each).
+  uint8_t *sF = sA;  // [128 columns][128 spins] e4m3 f(x_next); the operand stages are consumed
 #pragma unroll 1
   for (int cc = 0; cc < 2; ++cc) {
-    const int cl = half * 64 + cc * 32;  // first column of the chunk inside the tile
+    const int b = half * 2 + cc;  // state box
+    const int cl = 32 * b;        // first column of the chunk inside the tile
     const int c0 = n0 + cl;
     uint32_t g[32];
     tc::tmem_ld_32x32b_x32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(cl), g);
     int8_t f[32];
     if (i < s.N && c0 < s.C) {
-      sb_update_row32<P>(s, t, n, c0, g, __ldg(a.h + i), sx + rl * kTileLd + cl, sy + rl * kTileLd + cl, f);
+      sb_update_row32<P>(s, t, ka, dnext, kjn, c0, g, hi, sX + b * kTcBox, sY + b * kTcBox, rl, f);
     } else {
 #pragma unroll
       for (int j = 0; j < 32; ++j) f[j] = 0;
@@ -186,25 +210,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
     for (int j = 0; j < 32; ++j) sF[(cl + j) * kTcBM + rl] = f_to_e4m3(f[j]);
   }
+  tc::fence_proxy_async_smem();
   tc::tc_fence_before();
   __syncthreads();
-  for (int q = threadIdx.x; q < kTcBM * (kTcBN / 4); q += kTcThreads) {
-    const int r = q / (kTcBN / 4), c = (q % (kTcBN / 4)) * 4;
-    if (m0 + r < s.N && c < cols_valid) {
-      const size_t off = size_t(m0 + r) * s.Cp + n0 + c;
-      const float *px = sx + r * kTileLd + c, *py = sy + r * kTileLd + c;
-      *reinterpret_cast<float4 *>(s.x + off) = make_float4(px[0], px[1], px[2], px[3]);
-      *reinterpret_cast<float4 *>(s.y + off) = make_float4(py[0], py[1], py[2], py[3]);
+  if (threadIdx.x == 0) {
+    // x, y boxes back (rows past N are clipped by the tensor map) and the f
+    // tile into the other FT buffer: column n0 + c, spins m0 .. m0 + 127
+    for (int b = 0; b < 4; ++b) {
+      tc::tma_store_2d(&m.X, sX + b * kTcBox, n0 + 32 * b, m0);
+      tc::tma_store_2d(&m.Y, sY + b * kTcBox, n0 + 32 * b, m0);
     }
-  }
-  // column n0 + c of FT_next gets rows m0 .. m0 + 127 (128 contiguous bytes);
-  // two threads per column, 64 bytes each
-  {
-    const int c = threadIdx.x >> 1, part = threadIdx.x & 1;
-    uint8_t *dst = a.FT + (size_t((n + 1) & 1) * s.Cp + n0 + c) * a.Kp + m0 + part * 64;
-    const uint4 *src = reinterpret_cast<const uint4 *>(sF + c * kTcBM + part * 64);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) reinterpret_cast<uint4 *>(dst)[q] = src[q];
+    tc::tma_store_2d(&m.Fst, sF, m0, ((n + 1) & 1) * s.Cp + n0);
+    tc::tma_store_commit_and_wait_read();
   }
   if (warp == 0) tc::tmem_dealloc(tmem, 128);
 }
@@ -232,26 +249,28 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2D uint8 tensor map [rows][cols] (cols contiguous), box 128 x 128, 128B swizzle.
-static bool make_map(CUtensorMap *m, const void *base, uint64_t rows, uint64_t cols) {
+// 2D tensor map [rows][cols] (cols contiguous) with the given box and swizzle.
+static bool make_map(CUtensorMap *m, const void *base, CUtensorMapDataType dt, size_t esize, uint64_t rows,
+                     uint64_t cols, uint32_t box_cols, uint32_t box_rows, CUtensorMapSwizzle sw) {
   auto fn = encode_fn();
   if (!fn) return false;
   const cuuint64_t dims[2] = {cols, rows};
-  const cuuint64_t strides[1] = {cols};
-  const cuuint32_t box[2] = {128, 128};
+  const cuuint64_t strides[1] = {cols * esize};
+  const cuuint32_t box[2] = {box_cols, box_rows};
   const cuuint32_t estr[2] = {1, 1};
-  return fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(base), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  return fn(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-struct TcPlanImpl {
-  CUtensorMap tmA, tmB;
-};
-
-bool tc_plan_make(void **plan, const uint8_t *J8, uint8_t *FT, int Kp, int Cp) {
-  auto *p = new TcPlanImpl();
-  if (!make_map(&p->tmA, J8, uint64_t(Kp), uint64_t(Kp)) || !make_map(&p->tmB, FT, uint64_t(2) * Cp, uint64_t(Kp))) {
+bool tc_plan_make(void **plan, const uint8_t *J8, uint8_t *FT, int Kp, int Cp, float *x, float *y, int N) {
+  auto *p = new TcMaps();
+  const auto U8 = CU_TENSOR_MAP_DATA_TYPE_UINT8, F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const bool ok = make_map(&p->A, J8, U8, 1, uint64_t(Kp), uint64_t(Kp), 128, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
+                  make_map(&p->B, FT, U8, 1, uint64_t(2) * Cp, uint64_t(Kp), 128, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
+                  make_map(&p->X, x, F32, 4, uint64_t(N), uint64_t(Cp), 32, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
+                  make_map(&p->Y, y, F32, 4, uint64_t(N), uint64_t(Cp), 32, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
+                  make_map(&p->Fst, FT, U8, 1, uint64_t(2) * Cp, uint64_t(Kp), 128, 128, CU_TENSOR_MAP_SWIZZLE_NONE);
+  if (!ok) {
     delete p;
     return false;
   }
@@ -259,7 +278,7 @@ bool tc_plan_make(void **plan, const uint8_t *J8, uint8_t *FT, int Kp, int Cp) {
   return true;
 }
 
-void tc_plan_free(void *plan) { delete static_cast<TcPlanImpl *>(plan); }
+void tc_plan_free(void *plan) { delete static_cast<TcMaps *>(plan); }
 
 cudaError_t tc_set_attributes() {
   const void *fns[6] = {(const void *)k_step_dense_tc<1>, (const void *)k_step_dense_tc<2>,
@@ -273,16 +292,16 @@ cudaError_t tc_set_attributes() {
 }
 
 template <int P>
-static cudaError_t launch_tc_p(const TcPlanImpl *p, const StateView &s, const TcArgs &a, const StepTables &t, int n,
+static cudaError_t launch_tc_p(const TcMaps *p, const StateView &s, const TcArgs &a, const StepTables &t, int n,
                                cudaStream_t st) {
   dim3 grid(s.Cp / kTcBN, a.Kp / kTcBM);
-  k_step_dense_tc<P><<<grid, kTcThreads, kTcSmem, st>>>(p->tmA, p->tmB, s, a, t, n);
+  k_step_dense_tc<P><<<grid, kTcThreads, kTcSmem, st>>>(*p, s, a, t, n);
   return cudaGetLastError();
 }
 
 cudaError_t launch_step_dense_tc(const void *plan, const StateView &s, int Kp, uint8_t *FT, int *err, const float *h,
                                  const StepTables &t, int n, cudaStream_t st) {
-  const auto *p = static_cast<const TcPlanImpl *>(plan);
+  const auto *p = static_cast<const TcMaps *>(plan);
   TcArgs a{Kp, FT, err, h};
   switch (s.P) {
     case 1: return launch_tc_p<1>(p, s, a, t, n, st);

@@ -253,6 +253,33 @@ def test_full_run_dense_tensor_core_energies_exact(sb):
     _check_energies_and_best(sb, pb, prob, 8, 16)
 
 
+@pytest.mark.parametrize("N,P,R,S,jmax", [(64, 8, 16, 300, 1), (100, 4, 5, 150, 3), (48, 1, 7, 100, 2),
+                                         (128, 8, 3, 200, 1), (33, 16, 2, 80, 4)])
+def test_small_one_launch_solver_matches_per_step_path(sb, N, P, R, S, jmax):
+    """Small integer dense instances solve in one launch; state, energies and
+    best agree bit for bit with the per-step kernels (begin/advance/finish)."""
+    pb, spec = dense_int(N, N + P, jmax=jmax)
+    prob = create(sb, spec)
+    sb.set_schedule(prob, *workloads.autotune_params(R, N), **_params())
+    sb.run(prob, S, P, R, seed=N)
+    assert prob.info().step_kernel == 3
+    xa, ya, _ = sb.get_state(prob)
+    ea = sb.get_energies(prob)
+    ba = sb.get_best(prob)
+    sb.run_begin(prob, S, P, R, seed=N)
+    sb.run_advance(prob, S)
+    sb.run_finish(prob)
+    assert prob.info().step_kernel == 1
+    xb, yb, _ = sb.get_state(prob)
+    eb = sb.get_energies(prob)
+    bb = sb.get_best(prob)
+    assert np.array_equal(xa, xb) and np.array_equal(ya, yb)
+    assert np.array_equal(ea[0], eb[0]) and np.array_equal(ea[1], eb[1])
+    for k in ba:
+        assert np.array_equal(ba[k], bb[k]), k
+    _check_energies_and_best(sb, pb, prob, R, P)
+
+
 def test_full_run_sk64_energies_exact(sb):
     pb, spec = sk(64, 0)
     prob = create(sb, spec)
