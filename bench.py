@@ -406,6 +406,8 @@ def main():
     with torch.cuda.stream(stream):
         for w in range(args.warmup):
             sb.run(prob, S, P, R, seed=seed0 + w, stream=stream)
+        torch.cuda.synchronize()
+        info = prob.info()  # kernel path and autotuner choice of the full solves
         # zero-step solves time init + readout alone (for the step kernel's share)
         sb.run(prob, 0, P, R, seed=seed0, stream=stream)
         torch.cuda.synchronize()
@@ -427,7 +429,6 @@ def main():
             sb.run(prob, 0, P, R, seed=seed0 + k, stream=stream)
             ev0[k][1].record(stream)
         torch.cuda.synchronize()
-    info = prob.info()
     ms = [a.elapsed_time(b) for a, b in ev]
     ms0 = [a.elapsed_time(b) for a, b in ev0]
     ms_solve = statistics.mean(ms)
@@ -435,14 +436,27 @@ def main():
     ms_solve = multi.max_over_ranks(ms_solve)
     value = world * upd_per_solve / (ms_solve * 1e-3)
     step_ms = max(ms_solve - ms_zero, 1e-9) / S
-    achieved_gbs = BYTES_PER_UPDATE * N * P * R / (step_ms * 1e-3) / 1e9
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    if info.step_kernel == 2:  # dense tcgen05 FP8: a contraction, 2 N^2 R P flops per step
+        flops = 2.0 * N * N * P * R
+        achieved = flops / (step_ms * 1e-3) / 1e12
+        peak = 2.0 * peaks.get("bf16_tflops", 1900.0)  # FP8 = 2 x the measured BF16 dense peak
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_step_dense_tc", "step_ms": step_ms, "peak_source": peak_src,
+                "note": "2 N^2 R P flops per launch / event-timed step time; FP8 peak = 2 x measured BF16"}
+    else:
+        achieved_gbs = BYTES_PER_UPDATE * N * P * R / (step_ms * 1e-3) / 1e9
+        hbm_peak = peaks.get("hbm_gbs", 6800.0)
+        kname = {0: "k_step_csr", 4: "k_solve_csr_persistent", 3: "k_solve_small", 1: "k_step_dense"}[info.step_kernel]
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved_gbs / hbm_peak, "traffic": None, "kernel": kname, "step_ms": step_ms,
+                "peak_source": peak_src,
+                "note": "algorithmic 16 B/update x N*P*R per launch / event-timed step time"}
 
     # e2e: host buffers through the C ABI, every step
     src = inst
@@ -476,7 +490,7 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = oracle_sample(cfg, target_s=args.ref_seconds)
-    launches_per_solve = 1 if info.step_kernel == 3 else 2 + S + 4
+    launches_per_solve = 1 if info.step_kernel == 3 else (2 + 1 + 4 if info.step_kernel == 4 else 2 + S + 4)
     line = {
         "metric": "replica-spin updates/s", "value": value, "unit": "replica-spin updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_solve,
@@ -487,13 +501,12 @@ def main():
                                                    "state (%.0f MB) stays L2-resident within a solve"
                                                    % (N * P * R * 10 / 1e6),
                    "parallelism": "independent runs per GPU (weak scaling)",
-                   "step_kernel": ["csr", "dense_cuda_core", "dense_tcgen05_fp8", "dense_small_one_launch"][info.step_kernel],
+                   "step_kernel": ["csr", "dense_cuda_core", "dense_tcgen05_fp8", "dense_small_one_launch",
+                                   "csr_persistent"][info.step_kernel],
                    "csr_variant": info.step_variant,
-                   "autotune_ms_per_step": [round(v, 5) for v in info.variant_ms]},
-        "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved_gbs / hbm_peak, "traffic": None, "kernel": "k_step_csr",
-                     "step_ms": step_ms, "peak_source": peak_src,
-                     "note": "algorithmic 16 B/update x N*P*R per launch / event-timed step time"},
+                   "autotune_ms_per_step": [round(v, 5) for v in info.variant_ms],
+                   "autotune_persistent_ms_per_step": round(info.persistent_ms, 5)},
+        "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_val, "unit": "replica-spin updates/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "ms": statistics.median(e2e_ms)},

@@ -106,14 +106,18 @@ typedef struct {
     int32_t is_integer; /* all J_ij and h_i are integers                   */
     int32_t max_abs_j;  /* max |J_ij| if integer, else -1                  */
     double c0_auto;     /* default c0 = 0.5 sqrt(n / sum_ij J_ij^2)        */
-    int32_t step_kernel;  /* coupling-product kernel of the last run: 0 CSR,
-                             1 dense CUDA cores, 2 dense tcgen05 FP8, 3 the
-                             one-launch small dense solver; -1 none        */
+    int32_t step_kernel;  /* coupling-product kernel of the last run: 0 CSR
+                             per step, 1 dense CUDA cores, 2 dense tcgen05
+                             FP8, 3 the one-launch small dense solver, 4 the
+                             persistent CSR solver (one cooperative launch
+                             for all steps); -1 none                        */
     int32_t step_variant; /* CSR kernel variant picked by the autotuner:
                              4 << v consecutive replica columns per lane;
                              -1 before the first run                      */
     float variant_ms[4];  /* autotuner timing of each CSR variant (ms per
                              step; 0 = not timed / not eligible)           */
+    float persistent_ms;  /* autotuner timing of the persistent CSR solver
+                             (ms per step; 0 = not eligible)              */
 } sbqa_problem_info;
 
 int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info);
@@ -135,6 +139,11 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info);
  *   eval_every   0: read out only after the last step; K > 0: also after
  *                every step n with (n+1) % K == 0, keeping the best so far
  *   n_runs       length of beta and alpha (must equal R of the run)
+ *   kernel_select  CSR instances: 0 = let the autotuner choose between the
+ *                per-step kernels and the persistent solver (default);
+ *                1 = per-step kernels; 2 = the persistent solver when the
+ *                instance qualifies (+-1 J, degree <= 8, R*P a multiple of
+ *                256), else per-step.  Results are identical either way.
  *   beta, alpha  host, n_runs doubles each: per-run inverse temperature and
  *                schedule exponent (the auto-tuning draws them from
  *                [0.5,1.5] x [0.5,1.0]); beta > 0, alpha > 0
@@ -152,7 +161,7 @@ typedef struct {
     int32_t precision;
     int32_t eval_every;
     int32_t n_runs;
-    int32_t reserved;
+    int32_t kernel_select;
     const double *beta;
     const double *alpha;
 } sbqa_params;

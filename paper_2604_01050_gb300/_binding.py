@@ -53,7 +53,8 @@ class ProblemInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("is_dense", ctypes.c_int32), ("nnz", ctypes.c_int64),
                 ("is_integer", ctypes.c_int32), ("max_abs_j", ctypes.c_int32),
                 ("c0_auto", ctypes.c_double), ("step_kernel", ctypes.c_int32),
-                ("step_variant", ctypes.c_int32), ("variant_ms", ctypes.c_float * 4)]
+                ("step_variant", ctypes.c_int32), ("variant_ms", ctypes.c_float * 4),
+                ("persistent_ms", ctypes.c_float)]
 
 
 class EngineStats(ctypes.Structure):
@@ -68,7 +69,7 @@ class Params(ctypes.Structure):
                 ("init_amp", ctypes.c_double), ("jperp_enable", ctypes.c_int32),
                 ("variant", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("eval_every", ctypes.c_int32), ("n_runs", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("beta", ctypes.POINTER(ctypes.c_double)),
+                ("kernel_select", ctypes.c_int32), ("beta", ctypes.POINTER(ctypes.c_double)),
                 ("alpha", ctypes.POINTER(ctypes.c_double))]
 
 

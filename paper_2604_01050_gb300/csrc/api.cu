@@ -67,7 +67,7 @@ sbqa_problem::~sbqa_problem() {
   d_F0.release(); d_F1.release(); d_Sg.release(); d_ka.release(); d_dl.release();
   d_kj.release(); d_ei.release(); d_part_i.release(); d_best_ei.release(); d_ef.release();
   d_part_f.release(); d_best_e.release(); d_best_k.release(); d_best_step.release();
-  d_have.release(); d_best_spins.release();
+  d_have.release(); d_best_spins.release(); d_bar.release();
 }
 
 
@@ -303,7 +303,10 @@ cudaError_t issue_step(sbqa_problem *p, int n, cudaStream_t st) {
 // per handle and shape; skipped while the stream is being captured.
 int autotune_csr(sbqa_problem *p) {
   if (p->dense) return SBQA_OK;
-  if (p->csr_variant >= 0 && p->csr_variant_cp == p->Cp && p->csr_variant_kind == p->kind) return SBQA_OK;
+  if (p->csr_variant >= 0 && p->csr_variant_cp == p->Cp && p->csr_variant_kind == p->kind &&
+      p->csr_variant_select == p->prm.kernel_select)
+    return SBQA_OK;
+  p->csr_variant_select = p->prm.kernel_select;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   SBQA_CUDA(cudaStreamIsCapturing(p->stream, &cs));
   if (cs != cudaStreamCaptureStatusNone) return SBQA_OK;
@@ -331,6 +334,29 @@ int autotune_csr(sbqa_problem *p) {
       best = v;
     }
   }
+  // the persistent kernel: a few steps in one cooperative launch
+  p->use_persistent = false;
+  p->persistent_ms = 0.f;
+  if (p->persist_blocks == 0) p->persist_blocks = persistent_blocks();
+  if (p->prm.kernel_select == 2 && p->S > 0 && p->persistent_ok()) {
+    SBQA_CUDA(p->d_bar.alloc(1));
+    p->use_persistent = true;
+  } else if (p->prm.kernel_select == 0 && p->S > 0 && p->persistent_ok()) {
+    SBQA_CUDA(p->d_bar.alloc(1));
+    const int steps = std::min(p->S, 24);
+    SBQA_CUDA(launch_solve_csr_persistent(s, J, p->tables, 0, std::min(p->S, 4), p->d_bar.p, p->d_err.p,
+                                          p->persist_blocks, p->stream));
+    SBQA_CUDA(cudaEventRecord(e0, p->stream));
+    SBQA_CUDA(launch_solve_csr_persistent(s, J, p->tables, 0, steps, p->d_bar.p, p->d_err.p, p->persist_blocks,
+                                          p->stream));
+    SBQA_CUDA(cudaEventRecord(e1, p->stream));
+    SBQA_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    SBQA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    p->persistent_ms = ms / steps;
+    p->use_persistent = p->persistent_ms < best_ms / reps;
+    SBQA_CUDA(cudaMemsetAsync(p->d_err.p, 0, sizeof(int), p->stream));
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   p->csr_variant = best;
@@ -350,6 +376,24 @@ cudaError_t issue_readout(sbqa_problem *p, int step, cudaStream_t st) {
 // Steps [n0, n1) with the intermediate readouts of eval_every.
 cudaError_t issue_range(sbqa_problem *p, int n0, int n1, cudaStream_t st) {
   const int K = p->prm.eval_every;
+  if (p->use_persistent && p->persistent_ok()) {
+    // one cooperative launch per stretch between readouts
+    int n = n0;
+    while (n < n1) {
+      int stop = n1;
+      if (K > 0) stop = std::min(n1, (n / K + 1) * K);
+      cudaError_t e = launch_solve_csr_persistent(p->state(), p->csr(), p->tables, n, stop, p->d_bar.p, p->d_err.p,
+                                                  p->persist_blocks, st);
+      if (e != cudaSuccess) return e;
+      const int last = stop - 1;
+      if (K > 0 && (last + 1) % K == 0 && last != p->S - 1) {
+        e = issue_readout(p, last, st);
+        if (e != cudaSuccess) return e;
+      }
+      n = stop;
+    }
+    return cudaSuccess;
+  }
   for (int n = n0; n < n1; ++n) {
     cudaError_t e = issue_step(p, n, st);
     if (e != cudaSuccess) return e;
@@ -582,7 +626,10 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info) {
   info->is_integer = p->is_integer ? 1 : 0;
   info->max_abs_j = p->max_abs_j;
   info->c0_auto = p->c0_auto;
-  info->step_kernel = !p->begun ? -1 : (p->small_path ? 3 : (p->use_tc ? 2 : (p->dense ? 1 : 0)));
+  info->step_kernel = !p->begun ? -1
+                                 : (p->small_path ? 3
+                                                  : (p->use_tc ? 2 : (p->dense ? 1 : (p->use_persistent ? 4 : 0))));
+  info->persistent_ms = p->persistent_ms;
   info->step_variant = p->dense ? -1 : p->csr_variant;
   for (int v = 0; v < 4; ++v) info->variant_ms[v] = p->variant_ms[v];
   return SBQA_OK;
@@ -599,6 +646,7 @@ int sbqa_set_schedule(sbqa_problem *p, const sbqa_params *q) {
   if (q->precision == SBQA_PREC_EXACT && (!p->j_integer || p->max_abs_j > 16))
     return fail(SBQA_ERR_UNSUPPORTED, "EXACT precision needs integer J with |J_ij| <= 16");
   if (q->eval_every < 0 || q->n_runs < 0) return fail(SBQA_ERR_INVALID_ARG, "negative eval_every or n_runs");
+  if (q->kernel_select < 0 || q->kernel_select > 2) return fail(SBQA_ERR_INVALID_ARG, "kernel_select must be 0, 1 or 2");
   if (q->n_runs > 0 && (!q->beta || !q->alpha)) return fail(SBQA_ERR_INVALID_ARG, "beta/alpha missing");
   std::vector<double> beta, alpha;
   if (q->n_runs > 0) {
@@ -691,6 +739,13 @@ int sbqa_run(sbqa_problem *p, int32_t steps, int32_t P, int32_t R, uint64_t seed
   int rc = sbqa_run_begin(p, steps, P, R, seed, stream);
   if (rc != SBQA_OK) return rc;
   DeviceGuard g(p->device);
+  if (p->use_persistent && p->persistent_ok()) {  // no graph: one launch covers the steps
+    SBQA_CUDA(issue_range(p, 0, steps, p->stream));
+    SBQA_CUDA(issue_readout(p, steps - 1, p->stream));
+    p->step_done = steps;
+    p->finished = true;
+    return SBQA_OK;
+  }
   sbqa_problem::Key key;
   key.S = steps; key.P = P; key.R = R; key.eval = p->prm.eval_every; key.kind = p->kind;
   key.dense = p->dense ? 1 : 0; key.x = p->d_x.p; key.kj = p->d_kj.p;

@@ -98,7 +98,11 @@ struct sbqa_problem {
   int kind = VAL_F32;  // sparse value kind in use
   int csr_variant = -1;  // CSR step kernel variant chosen by the autotuner (-1 = not yet)
   float variant_ms[4] = {0.f, 0.f, 0.f, 0.f};
-  int csr_variant_cp = -1, csr_variant_kind = -1;
+  bool use_persistent = false;  // autotuner: one cooperative launch for all steps
+  float persistent_ms = 0.f;    // its timing per step
+  int persist_blocks = 0;
+  sbqa::DevBuf<unsigned> d_bar;  // grid barrier counter of the persistent kernel
+  int csr_variant_cp = -1, csr_variant_kind = -1, csr_variant_select = -1;
   sbqa::DevBuf<float> d_x, d_y;
   sbqa::DevBuf<uint8_t> d_F0, d_F1;
   sbqa::DevBuf<int8_t> d_Sg;
@@ -124,6 +128,10 @@ struct sbqa_problem {
   } graph_key;
 
   ~sbqa_problem();  // waits for the device, releases every buffer (api.cu)
+
+  bool persistent_ok() const {
+    return !dense && kind == sbqa::VAL_PM1 && sbqa::persistent_eligible(n, Cp, max_degree, persist_blocks);
+  }
 
   StateView state() const {
     StateView s;

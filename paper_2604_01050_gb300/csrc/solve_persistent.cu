@@ -1,0 +1,177 @@
+// solve_persistent.cu -- all steps of a CSR run batch in one cooperative launch.
+//
+// For +-1 couplings with row degree <= 8.  The grid is exactly as large as
+// can be co-resident; every warp owns fixed work items (spin row, chunk of
+// 32 W replica columns) for the whole anneal.  Before the first step a warp
+// copies the column indices and signs of its items' rows into shared memory,
+// so a step needs no index loads: per item it gathers the f codes of the
+// (at most 8) neighbours and the x, y of its columns, sums, updates (same
+// arithmetic as k_step_csr) and writes x, y and the next codes.  The codes
+// written by other blocks are read through L2 (ld.global.cg), never the
+// non-coherent path.  Between
+// steps all blocks meet at a grid barrier (a counter in global memory); the
+// wait is bounded: after kBarrierSpins polls a block records an error and
+// stops stepping, so a broken grid ends with a status the host reads.
+#include "step_common.cuh"
+
+namespace sbqa {
+
+constexpr int kPersistMaxDeg = 8;
+constexpr int kPersistW = 8;                   // columns per lane
+constexpr int kPersistMaxItems = 32;           // items per warp kept in shared memory
+constexpr unsigned kBarrierSpins = 1u << 24;  // polls per grid barrier (with backoff: seconds)
+
+struct PersistArgs {
+  StateView s;
+  const int32_t *row_ptr, *col, *npos;  // +-1 CSR, each row's +1 entries first
+  const float *h;
+  StepTables t;
+  int n_begin, n_end;
+  unsigned *bar;  // grid barrier counter (zeroed by the host before the launch)
+  int *err;       // error flag
+};
+
+struct ItemIdx {
+  int32_t col[kPersistMaxDeg];
+  int32_t row, chunk, deg, npos;
+};
+
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, int *err) {
+  __syncthreads();
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(bar, 1u);
+    unsigned v = 0;
+    unsigned it = 0;
+    for (; it < kBarrierSpins; ++it) {
+      asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+      if (v >= target) break;
+      if (it > 64) __nanosleep(64);
+    }
+    s_ok = it < kBarrierSpins;
+    if (!s_ok) atomicCAS(err, 0, 4);
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <int P>
+__global__ void __launch_bounds__(256, 4) k_solve_csr_persistent(PersistArgs a) {
+  extern __shared__ ItemIdx s_items[];  // [8 warps][kPersistMaxItems]
+  const StateView &s = a.s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int chunks = s.Cp / (32 * kPersistW);
+  const int n_items = s.N * chunks;
+  const int warps_total = gridDim.x * 8;
+  const int gw = blockIdx.x * 8 + warp;
+  ItemIdx *mine = s_items + warp * kPersistMaxItems;
+  int my_count = 0;
+  for (int it = gw; it < n_items && my_count < kPersistMaxItems; it += warps_total, ++my_count) {
+    if (lane == 0) {
+      const int row = it / chunks;
+      const int e0 = a.row_ptr[row], e1 = a.row_ptr[row + 1];
+      ItemIdx &m = mine[my_count];
+      m.row = row;
+      m.chunk = it - row * chunks;
+      m.deg = e1 - e0;
+      m.npos = a.npos[row];
+      for (int q = 0; q < kPersistMaxDeg; ++q) m.col[q] = q < m.deg ? a.col[e0 + q] : 0;
+    }
+  }
+  __syncwarp();
+  unsigned target = 0;
+  for (int n = a.n_begin; n < a.n_end; ++n) {
+    const uint8_t *Fin = s.f_of(n);
+    uint8_t *Fout = s.f_of(n + 1);
+    const float ka = __ldg(a.t.ka + n), dnext = __ldg(a.t.dl + n + 1);
+    for (int q = 0; q < my_count; ++q) {
+      const ItemIdx &m = mine[q];
+      const int i = m.row;
+      const int c0 = m.chunk * 32 * kPersistW + lane * kPersistW;
+      const size_t off = size_t(i) * s.Cp + c0;
+      float xs[kPersistW], ys[kPersistW];
+#pragma unroll
+      for (int u = 0; u < kPersistW / 4; ++u) {
+        const float4 xa = *reinterpret_cast<const float4 *>(s.x + off + 4 * u);
+        const float4 ya = *reinterpret_cast<const float4 *>(s.y + off + 4 * u);
+        xs[4 * u] = xa.x; xs[4 * u + 1] = xa.y; xs[4 * u + 2] = xa.z; xs[4 * u + 3] = xa.w;
+        ys[4 * u] = ya.x; ys[4 * u + 1] = ya.y; ys[4 * u + 2] = ya.z; ys[4 * u + 3] = ya.w;
+      }
+      uint2 f[kPersistMaxDeg];
+#pragma unroll
+      for (int e = 0; e < kPersistMaxDeg; ++e)
+        f[e] = e < m.deg ? __ldcg(reinterpret_cast<const uint2 *>(Fin + size_t(m.col[e]) * s.Cp + c0))
+                         : make_uint2(0u, 0u);  // L2 loads: other blocks wrote these codes in this launch
+      uint32_t ap0 = 0, ap1 = 0, am0 = 0, am1 = 0;
+#pragma unroll
+      for (int e = 0; e < kPersistMaxDeg; ++e) {
+        if (e < m.npos) {
+          ap0 += f[e].x;
+          ap1 += f[e].y;
+        } else {
+          am0 += f[e].x;
+          am1 += f[e].y;
+        }
+      }
+      const int bias = (m.deg - m.npos) - m.npos;  // codes carry f + 1
+      float G[kPersistW];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        G[c] = float(int((ap0 >> (8 * c)) & 0xffu) - int((am0 >> (8 * c)) & 0xffu) + bias);
+        G[4 + c] = float(int((ap1 >> (8 * c)) & 0xffu) - int((am1 >> (8 * c)) & 0xffu) + bias);
+      }
+      sb_updateW<P, kPersistW>(s, a.t, ka, dnext, n, i, c0, G, __ldg(a.h + i), xs, ys, Fout);
+    }
+    target += gridDim.x;
+    if (!grid_barrier(a.bar, target, a.err)) break;
+  }
+}
+
+int persistent_blocks() {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_csr_persistent<32>, 256,
+                                                    8 * kPersistMaxItems * sizeof(ItemIdx)) != cudaSuccess)
+    return 0;
+  return sms * per_sm;
+}
+
+bool persistent_eligible(int N, int Cp, int max_degree, int blocks) {
+  if (blocks <= 0 || max_degree > kPersistMaxDeg || Cp % (32 * kPersistW) != 0) return false;
+  const long long items = (long long)N * (Cp / (32 * kPersistW));
+  return items <= (long long)blocks * 8 * kPersistMaxItems;
+}
+
+cudaError_t launch_solve_csr_persistent(const StateView &s, const CsrView &J, const StepTables &t, int n_begin,
+                                        int n_end, unsigned *bar, int *err, int blocks, cudaStream_t st) {
+  PersistArgs a;
+  a.s = s;
+  a.row_ptr = J.row_ptr;
+  a.col = J.col;
+  a.npos = J.npos;
+  a.h = J.h;
+  a.t = t;
+  a.n_begin = n_begin;
+  a.n_end = n_end;
+  a.bar = bar;
+  a.err = err;
+  void *args[] = {&a};
+  const size_t smem = 8 * kPersistMaxItems * sizeof(ItemIdx);
+  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  const void *fn;
+  switch (s.P) {
+    case 1: fn = (const void *)k_solve_csr_persistent<1>; break;
+    case 2: fn = (const void *)k_solve_csr_persistent<2>; break;
+    case 4: fn = (const void *)k_solve_csr_persistent<4>; break;
+    case 8: fn = (const void *)k_solve_csr_persistent<8>; break;
+    case 16: fn = (const void *)k_solve_csr_persistent<16>; break;
+    case 32: fn = (const void *)k_solve_csr_persistent<32>; break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(256), args, smem, st);
+}
+
+}  // namespace sbqa

@@ -280,6 +280,41 @@ def test_small_one_launch_solver_matches_per_step_path(sb, N, P, R, S, jmax):
     _check_energies_and_best(sb, pb, prob, R, P)
 
 
+@pytest.mark.parametrize("L,P,R", [(10, 16, 32), (8, 32, 8), (6, 8, 64)])
+def test_persistent_csr_solver_matches_per_step(sb, L, P, R):
+    """The persistent CSR solver (one cooperative launch, grid barrier per
+    step) and the per-step kernels give bit-identical runs, including the
+    best-so-far readouts between stretches of steps."""
+    pb, spec = lattice(L, L)
+    out = []
+    for sel in (1, 2):
+        prob = create(sb, spec)
+        sb.set_schedule(prob, *workloads.autotune_params(R, L), **_params(kernel_select=sel, eval_every=37))
+        sb.run(prob, 200, P, R, seed=L)
+        assert prob.info().step_kernel == (0 if sel == 1 else 4)
+        out.append((sb.get_state(prob)[:2], sb.get_energies(prob), sb.get_best(prob)))
+    (xa, ya), ea, ba = out[0]
+    (xb, yb), eb, bb = out[1]
+    assert np.array_equal(xa, xb) and np.array_equal(ya, yb)
+    assert np.array_equal(ea[1], eb[1])
+    for k in ba:
+        assert np.array_equal(ba[k], bb[k]), k
+    _check_energies_and_best(sb, pb, prob, R, P)
+
+
+def test_persistent_csr_solver_resume(sb):
+    pb, spec = lattice(8, 2)
+    prob = create(sb, spec)
+    sb.set_schedule(prob, *workloads.autotune_params(16, 2), **_params(kernel_select=2))
+    sb.run(prob, 150, 16, 16, seed=4)
+    xa = sb.get_state(prob)[0]
+    sb.run_begin(prob, 150, 16, 16, seed=4)
+    sb.run_advance(prob, 61)
+    sb.run_advance(prob, 500)
+    sb.run_finish(prob)
+    assert np.array_equal(xa, sb.get_state(prob)[0])
+
+
 def test_full_run_sk64_energies_exact(sb):
     pb, spec = sk(64, 0)
     prob = create(sb, spec)
