@@ -132,10 +132,18 @@ int persistent_blocks() {
   int dev = 0, sms = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_csr_persistent<32>, 256,
-                                                    8 * kPersistMaxItems * sizeof(ItemIdx)) != cudaSuccess)
-    return 0;
-  return sms * per_sm;
+  // the smallest co-resident count over all replica counts, so any P fits the grid
+  const void *fns[] = {(const void *)k_solve_csr_persistent<1>, (const void *)k_solve_csr_persistent<2>,
+                       (const void *)k_solve_csr_persistent<4>, (const void *)k_solve_csr_persistent<8>,
+                       (const void *)k_solve_csr_persistent<16>, (const void *)k_solve_csr_persistent<32>};
+  int best = 1 << 30;
+  for (const void *fn : fns) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 8 * kPersistMaxItems * sizeof(ItemIdx)) !=
+        cudaSuccess)
+      return 0;
+    best = per_sm < best ? per_sm : best;
+  }
+  return sms * best;
 }
 
 bool persistent_eligible(int N, int Cp, int max_degree, int blocks) {
