@@ -442,13 +442,14 @@ def main():
     except Exception:
         pass
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    if info.step_kernel == 2:  # dense tcgen05 FP8: a contraction, 2 N^2 R P flops per step
+    if info.step_kernel in (2, 5):  # dense tcgen05 FP8: a contraction, 2 N^2 R P flops per step
         flops = 2.0 * N * N * P * R
         achieved = flops / (step_ms * 1e-3) / 1e12
         peak = 2.0 * peaks.get("bf16_tflops", 1900.0)  # FP8 = 2 x the measured BF16 dense peak
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_step_dense_tc", "step_ms": step_ms, "peak_source": peak_src,
-                "note": "2 N^2 R P flops per launch / event-timed step time; FP8 peak = 2 x measured BF16"}
+                "traffic": None, "kernel": "k_step_dense_tc" if info.step_kernel == 2 else "k_solve_dense_tc_persistent",
+                "step_ms": step_ms, "peak_source": peak_src,
+                "note": "2 N^2 R P flops per step / event-timed step time; FP8 peak = 2 x measured BF16"}
     else:
         achieved_gbs = BYTES_PER_UPDATE * N * P * R / (step_ms * 1e-3) / 1e9
         hbm_peak = peaks.get("hbm_gbs", 6800.0)
@@ -490,7 +491,10 @@ def main():
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         cpu = oracle_sample(cfg, target_s=args.ref_seconds)
-    launches_per_solve = 1 if info.step_kernel == 3 else (2 + 1 + 4 if info.step_kernel == 4 else 2 + S + 4)
+    # init + reset_best (+ the f -> e4m3 conversion on the tensor-core path) + steps + 4 readout kernels
+    tc_conv = 1 if info.step_kernel in (2, 5) else 0
+    launches_per_solve = (1 if info.step_kernel == 3 else
+                          2 + tc_conv + (1 if info.step_kernel in (4, 5) else S) + 4)
     line = {
         "metric": "replica-spin updates/s", "value": value, "unit": "replica-spin updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_solve,
@@ -502,7 +506,7 @@ def main():
                                                    % (N * P * R * 10 / 1e6),
                    "parallelism": "independent runs per GPU (weak scaling)",
                    "step_kernel": ["csr", "dense_cuda_core", "dense_tcgen05_fp8", "dense_small_one_launch",
-                                   "csr_persistent"][info.step_kernel],
+                                   "csr_persistent", "dense_tcgen05_persistent"][info.step_kernel],
                    "csr_variant": info.step_variant,
                    "autotune_ms_per_step": [round(v, 5) for v in info.variant_ms],
                    "autotune_persistent_ms_per_step": round(info.persistent_ms, 5)},

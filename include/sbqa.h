@@ -110,14 +110,18 @@ typedef struct {
                              per step, 1 dense CUDA cores, 2 dense tcgen05
                              FP8, 3 the one-launch small dense solver, 4 the
                              persistent CSR solver (one cooperative launch
-                             for all steps); -1 none                        */
+                             for all steps), 5 the persistent dense tcgen05
+                             solver (x, y resident in tensor memory); -1
+                             none                                          */
     int32_t step_variant; /* CSR kernel variant picked by the autotuner:
                              4 << v consecutive replica columns per lane;
                              -1 before the first run                      */
     float variant_ms[4];  /* autotuner timing of each CSR variant (ms per
-                             step; 0 = not timed / not eligible)           */
-    float persistent_ms;  /* autotuner timing of the persistent CSR solver
-                             (ms per step; 0 = not eligible)              */
+                             step; 0 = not timed / not eligible); for the
+                             dense tcgen05 path [0] is the per-step kernel */
+    float persistent_ms;  /* autotuner timing of the persistent solver of
+                             the path in use, CSR or dense tcgen05 (ms per
+                             step; 0 = not timed / not eligible)          */
 } sbqa_problem_info;
 
 int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info);
@@ -139,11 +143,14 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info);
  *   eval_every   0: read out only after the last step; K > 0: also after
  *                every step n with (n+1) % K == 0, keeping the best so far
  *   n_runs       length of beta and alpha (must equal R of the run)
- *   kernel_select  CSR instances: 0 = let the autotuner choose between the
- *                per-step kernels and the persistent solver (default);
- *                1 = per-step kernels; 2 = the persistent solver when the
- *                instance qualifies (+-1 J, degree <= 8, R*P a multiple of
- *                256), else per-step.  Results are identical either way.
+ *   kernel_select  0 = let the autotuner choose between the per-step
+ *                kernels and the persistent solver (default); 1 = per-step
+ *                kernels; 2 = the persistent solver when the instance
+ *                qualifies, else per-step.  CSR qualifies with +-1 J,
+ *                degree <= 8 and R*P a multiple of 256; the dense tensor-core
+ *                path when its 128 x 128 tiles (padded N x padded R*P) fit
+ *                the device at once (one per SM).  Results are identical
+ *                either way.
  *   beta, alpha  host, n_runs doubles each: per-run inverse temperature and
  *                schedule exponent (the auto-tuning draws them from
  *                [0.5,1.5] x [0.5,1.0]); beta > 0, alpha > 0

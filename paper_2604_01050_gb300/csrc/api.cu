@@ -67,7 +67,7 @@ sbqa_problem::~sbqa_problem() {
   d_F0.release(); d_F1.release(); d_Sg.release(); d_ka.release(); d_dl.release();
   d_kj.release(); d_ei.release(); d_part_i.release(); d_best_ei.release(); d_ef.release();
   d_part_f.release(); d_best_e.release(); d_best_k.release(); d_best_step.release();
-  d_have.release(); d_best_spins.release(); d_bar.release();
+  d_have.release(); d_best_spins.release(); d_bar.release(); d_tc_flags.release();
 }
 
 
@@ -365,6 +365,67 @@ int autotune_csr(sbqa_problem *p) {
   return SBQA_OK;
 }
 
+// Autotuner of the dense tensor-core path: times the per-step kernel against
+// the persistent solver (same state buffers, before the initial state is
+// written) and keeps the faster; kernel_select 1 or 2 forces one.  Cached
+// per handle, column count, replica count and selection.
+int autotune_tc(sbqa_problem *p) {
+  if (!p->use_tc) {
+    p->use_tc_persistent = false;
+    return SBQA_OK;
+  }
+  if (p->tc_select_cp == p->Cp && p->tc_select == p->prm.kernel_select && p->tc_select_p == p->P) return SBQA_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  SBQA_CUDA(cudaStreamIsCapturing(p->stream, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return SBQA_OK;
+  p->use_tc_persistent = false;
+  p->tc_step_ms = p->tc_persistent_ms = 0.f;
+  if (p->tc_persist_blocks == 0) p->tc_persist_blocks = tc_persistent_blocks();
+  if (p->prm.kernel_select != 1 && p->S > 0 && p->tc_persistent_ok()) {
+    SBQA_CUDA(p->d_tc_flags.alloc(tc_persistent_flag_count(p->Kp, p->Cp)));
+    if (p->prm.kernel_select == 2) {
+      p->use_tc_persistent = true;
+    } else {
+      const StateView s = p->state();
+      cudaEvent_t e0, e1;
+      SBQA_CUDA(cudaEventCreate(&e0));
+      SBQA_CUDA(cudaEventCreate(&e1));
+      const int reps = 8, steps = std::min(p->S, 24);
+      float ms = 0.f;
+      for (int w = 0; w < 2; ++w)
+        SBQA_CUDA(launch_step_dense_tc(p->tc_plan, s, p->Kp, p->d_FT.p, p->d_err.p, p->d_h.p, p->tables, 0,
+                                       p->stream));
+      SBQA_CUDA(cudaEventRecord(e0, p->stream));
+      for (int w = 0; w < reps; ++w)
+        SBQA_CUDA(launch_step_dense_tc(p->tc_plan, s, p->Kp, p->d_FT.p, p->d_err.p, p->d_h.p, p->tables, 0,
+                                       p->stream));
+      SBQA_CUDA(cudaEventRecord(e1, p->stream));
+      SBQA_CUDA(cudaEventSynchronize(e1));
+      SBQA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      p->tc_step_ms = ms / reps;
+      SBQA_CUDA(launch_solve_dense_tc_persistent(p->tc_plan, s, p->Kp, p->d_err.p, p->d_h.p, p->tables, 0,
+                                                 std::min(p->S, 4), p->d_tc_flags.p, p->stream));
+      SBQA_CUDA(cudaEventRecord(e0, p->stream));
+      SBQA_CUDA(launch_solve_dense_tc_persistent(p->tc_plan, s, p->Kp, p->d_err.p, p->d_h.p, p->tables, 0, steps,
+                                                 p->d_tc_flags.p, p->stream));
+      SBQA_CUDA(cudaEventRecord(e1, p->stream));
+      SBQA_CUDA(cudaEventSynchronize(e1));
+      SBQA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      p->tc_persistent_ms = ms / steps;
+      p->use_tc_persistent = p->tc_persistent_ms < p->tc_step_ms;
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      int err = 0;
+      SBQA_CUDA(cudaMemcpy(&err, p->d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+      if (err != 0) return fail(SBQA_ERR_TIMEOUT, "a bounded device wait gave up (code " + std::to_string(err) + ")");
+    }
+  }
+  p->tc_select_cp = p->Cp;
+  p->tc_select = p->prm.kernel_select;
+  p->tc_select_p = p->P;
+  return SBQA_OK;
+}
+
 cudaError_t issue_readout(sbqa_problem *p, int step, cudaStream_t st) {
   const StateView s = p->state();
   cudaError_t e = p->dense ? launch_energy_dense(s, p->energy(), p->best(), st)
@@ -376,14 +437,17 @@ cudaError_t issue_readout(sbqa_problem *p, int step, cudaStream_t st) {
 // Steps [n0, n1) with the intermediate readouts of eval_every.
 cudaError_t issue_range(sbqa_problem *p, int n0, int n1, cudaStream_t st) {
   const int K = p->prm.eval_every;
-  if (p->use_persistent && p->persistent_ok()) {
+  const bool tc_persist = p->use_tc_persistent && p->tc_persistent_ok();
+  if (tc_persist || (p->use_persistent && p->persistent_ok())) {
     // one cooperative launch per stretch between readouts
     int n = n0;
     while (n < n1) {
       int stop = n1;
       if (K > 0) stop = std::min(n1, (n / K + 1) * K);
-      cudaError_t e = launch_solve_csr_persistent(p->state(), p->csr(), p->tables, n, stop, p->d_bar.p, p->d_err.p,
-                                                  p->persist_blocks, st);
+      cudaError_t e = tc_persist ? launch_solve_dense_tc_persistent(p->tc_plan, p->state(), p->Kp, p->d_err.p,
+                                                                    p->d_h.p, p->tables, n, stop, p->d_tc_flags.p, st)
+                                 : launch_solve_csr_persistent(p->state(), p->csr(), p->tables, n, stop, p->d_bar.p,
+                                                               p->d_err.p, p->persist_blocks, st);
       if (e != cudaSuccess) return e;
       const int last = stop - 1;
       if (K > 0 && (last + 1) % K == 0 && last != p->S - 1) {
@@ -628,10 +692,11 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info) {
   info->c0_auto = p->c0_auto;
   info->step_kernel = !p->begun ? -1
                                  : (p->small_path ? 3
-                                                  : (p->use_tc ? 2 : (p->dense ? 1 : (p->use_persistent ? 4 : 0))));
-  info->persistent_ms = p->persistent_ms;
+                                                  : (p->use_tc ? (p->use_tc_persistent && p->tc_persistent_ok() ? 5 : 2)
+                                                               : (p->dense ? 1 : (p->use_persistent ? 4 : 0))));
+  info->persistent_ms = p->use_tc ? p->tc_persistent_ms : p->persistent_ms;
   info->step_variant = p->dense ? -1 : p->csr_variant;
-  for (int v = 0; v < 4; ++v) info->variant_ms[v] = p->variant_ms[v];
+  for (int v = 0; v < 4; ++v) info->variant_ms[v] = p->use_tc ? (v == 0 ? p->tc_step_ms : 0.f) : p->variant_ms[v];
   return SBQA_OK;
 }
 
@@ -677,6 +742,7 @@ int sbqa_run_begin(sbqa_problem *p, int32_t steps, int32_t P, int32_t R, uint64_
   if ((rc = alloc_run(p, steps, P, R)) != SBQA_OK) return rc;
   if ((rc = build_tables(p)) != SBQA_OK) return rc;
   if ((rc = autotune_csr(p)) != SBQA_OK) return rc;
+  if ((rc = autotune_tc(p)) != SBQA_OK) return rc;
   const StateView s = p->state();
   SBQA_CUDA(cudaMemsetAsync(p->d_err.p, 0, sizeof(int), p->stream));
   SBQA_CUDA(launch_init(s, seed, float(p->prm.init_amp), 0.0f, p->stream));
@@ -739,7 +805,8 @@ int sbqa_run(sbqa_problem *p, int32_t steps, int32_t P, int32_t R, uint64_t seed
   int rc = sbqa_run_begin(p, steps, P, R, seed, stream);
   if (rc != SBQA_OK) return rc;
   DeviceGuard g(p->device);
-  if (p->use_persistent && p->persistent_ok()) {  // no graph: one launch covers the steps
+  if ((p->use_persistent && p->persistent_ok()) || (p->use_tc_persistent && p->tc_persistent_ok())) {
+    // no graph: one launch covers the steps
     SBQA_CUDA(issue_range(p, 0, steps, p->stream));
     SBQA_CUDA(issue_readout(p, steps - 1, p->stream));
     p->step_done = steps;

@@ -90,6 +90,16 @@ bool persistent_eligible(int N, int Cp, int max_degree, int blocks);
 cudaError_t launch_solve_csr_persistent(const StateView &s, const CsrView &J, const StepTables &t, int n_begin,
                                         int n_end, unsigned *bar, int *err, int blocks, cudaStream_t st);
 
+// Steps of a dense integer run on the tensor cores in one cooperative launch,
+// x and y resident in tensor memory, per-tile step flags between CTAs
+// (step_dense_tc.cu).  flags holds tc_persistent_flag_count() counters.
+int tc_persistent_blocks();
+bool tc_persistent_eligible(int Kp, int Cp, int blocks);
+size_t tc_persistent_flag_count(int Kp, int Cp);
+cudaError_t launch_solve_dense_tc_persistent(const void *plan, const StateView &s, int Kp, int *err, const float *h,
+                                             const StepTables &t, int n_begin, int n_end, uint32_t *flags,
+                                             cudaStream_t st);
+
 // Whole solve of a small integer dense instance in one launch (solve_small.cu).
 struct SmallArgs {
   int N, P, R, S, Cp;

@@ -103,6 +103,12 @@ struct sbqa_problem {
   int persist_blocks = 0;
   sbqa::DevBuf<unsigned> d_bar;  // grid barrier counter of the persistent kernel
   int csr_variant_cp = -1, csr_variant_kind = -1, csr_variant_select = -1;
+  // dense tcgen05: per-step kernel or the persistent solver (autotuned per Cp and kernel_select)
+  bool use_tc_persistent = false;
+  float tc_step_ms = 0.f, tc_persistent_ms = 0.f;
+  int tc_persist_blocks = 0;
+  int tc_select_cp = -1, tc_select = -1, tc_select_p = -1;
+  sbqa::DevBuf<uint32_t> d_tc_flags;  // per-tile step counters of the persistent solver
   sbqa::DevBuf<float> d_x, d_y;
   sbqa::DevBuf<uint8_t> d_F0, d_F1;
   sbqa::DevBuf<int8_t> d_Sg;
@@ -128,6 +134,10 @@ struct sbqa_problem {
   } graph_key;
 
   ~sbqa_problem();  // waits for the device, releases every buffer (api.cu)
+
+  bool tc_persistent_ok() const {
+    return use_tc && tc_plan && sbqa::tc_persistent_eligible(Kp, Cp, tc_persist_blocks);
+  }
 
   bool persistent_ok() const {
     return !dense && kind == sbqa::VAL_PM1 && sbqa::persistent_eligible(n, Cp, max_degree, persist_blocks);

@@ -226,6 +226,305 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (warp == 0) tc::tmem_dealloc(tmem, 128);
 }
 
+// ---------------------------------------------------------------- persistent solver
+// All steps of a stretch in one cooperative launch.  Each CTA owns one 128 x
+// 128 tile (spin rows x replica columns) for the whole stretch and keeps its x
+// and y in tensor memory next to the accumulator (TMEM columns 0-127: G,
+// 128-255: x, 256-383: y), so shared memory holds six operand stages and a
+// step moves only J and f through the memory system.  A step of tile (mt, ct)
+// needs f_n of the 128 spins of every row tile kb for its columns, which CTA
+// (kb, ct) wrote at the end of its previous step; instead of a grid barrier
+// every CTA publishes a per-tile step counter (release, after its f tile's
+// TMA store has completed) and the producer warp polls the counters of its
+// column group (acquire, then a proxy fence before the TMA loads of those
+// tiles), issuing k-blocks in order as their tiles become ready.  The J tiles
+// of the next step's first stages are loaded while the epilogue runs.  A wait
+// that gives up (2 s, or at once when another CTA has already failed)
+// records an error; every CTA then stops at its next step boundary.
+constexpr int kTpStages = 6;
+constexpr int kTpThreads = 512;  // 16 warps: warp w updates TMEM lanes 32 (w % 4).. and columns 32 (w / 4)..
+constexpr int kTpSmem = 2 * kTpStages * kTcTile + kTcBM * kTcBN + 1024 + 256;
+constexpr uint32_t kTmemX = 128, kTmemY = 256, kTmemCols = 512;
+constexpr uint64_t kFlagTimeoutNs = 2000000000ull;
+
+struct TpArgs {
+  int Kp, Ct, n_begin, n_end;
+  int *err;
+  const float *h;
+  uint32_t *flags;  // [Kp / 128][Ct] steps completed in this launch, zeroed by the host
+};
+
+// One run-aligned chunk of 32 columns of spin row i, in registers (bit
+// patterns of FP32 x, y and the accumulated G).  Same arithmetic, in the same
+// order, as sb_update_row32: all momenta first (they read the old positions of
+// the ring neighbours), then positions, wall and f, whose e4m3 code goes to
+// column j of the transposed f tile (sFcol[j * 128]).
+template <int P>
+__device__ __forceinline__ void sb_update_regs32(const StateView &s, const StepTables &t, float ka, float dnext,
+                                                 const float *kjn, int c0, const uint32_t (&g)[32], float hi,
+                                                 uint32_t (&xr)[32], uint32_t (&yr)[32], uint8_t *sFcol) {
+  constexpr int PR = P < 32 ? P : 32;
+  float kjv[32 / PR];
+#pragma unroll
+  for (int q = 0; q < 32 / PR; ++q) kjv[q] = (c0 + q * P < s.C) ? __ldg(kjn + c0 / P + q) : 0.f;
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    if (c0 + j >= s.C) continue;
+    const int k = j % P, base = j - k;
+    const float xm = __uint_as_float(xr[base + (k + P - 1) % P]), xp = __uint_as_float(xr[base + (k + 1) % P]);
+    const float xj = __uint_as_float(xr[j]);
+    float yn = fmaf(t.kc, __uint_as_float(g[j]) + hi, __uint_as_float(yr[j]));
+    yn = fmaf(-ka, xj, yn);
+    yn = fmaf(kjv[j / PR], xm + xp, yn);
+    yr[j] = __float_as_uint(yn);
+  }
+#pragma unroll
+  for (int j = 0; j < 32; ++j) {
+    uint8_t e = 0;
+    if (c0 + j < s.C) {
+      float xn = fmaf(t.kx, __uint_as_float(yr[j]), __uint_as_float(xr[j]));
+      if (fabsf(xn) > 1.f) {
+        xn = copysignf(1.f, xn);
+        yr[j] = __float_as_uint(0.f);
+      }
+      xr[j] = __float_as_uint(xn);
+      e = f_to_e4m3(thresh(xn, dnext));
+    }
+    sFcol[j * kTcBM] = e;
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kTpThreads, 1)
+    k_solve_dense_tc_persistent(const __grid_constant__ TcMaps m, StateView s, TpArgs a, StepTables t) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + kTpStages * kTcTile;
+  uint8_t *sF = sB + kTpStages * kTcTile;  // [128 columns][128 spins] e4m3 f(x_next)
+  uint64_t *full = reinterpret_cast<uint64_t *>(sF + kTcBM * kTcBN);
+  uint64_t *empty = full + kTpStages;
+  uint64_t *done = empty + kTpStages;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+  int *s_abort = reinterpret_cast<int *>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ct = blockIdx.x, mt = blockIdx.y;
+  const int m0 = mt * kTcBM, n0 = ct * kTcBN;
+  const int KB = a.Kp / kTcBK;
+  const int npre = KB < kTpStages ? KB : kTpStages;  // k-blocks whose J tile is loaded ahead
+  const int quarter = warp & 3, chunk = warp >> 2;
+  const int rl = quarter * 32 + lane, i = m0 + rl;
+  const int cl = 32 * chunk, c0 = n0 + cl;
+  const uint32_t lane_off = uint32_t(quarter * 32) << 16;
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kTpStages; ++q) {
+      tc::mbar_init(&full[q], 1);
+      tc::mbar_init(&empty[q], 1);
+    }
+    tc::mbar_init(done, 1);
+    tc::fence_mbar_init();
+    tc::prefetch_tmap(&m.A);
+    tc::prefetch_tmap(&m.B);
+    tc::prefetch_tmap(&m.Fst);
+    *s_abort = 0;
+  }
+  if (warp == 0) tc::tmem_alloc(tmem_slot, kTmemCols);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  {  // the state tile into TMEM (rows past N hold zeros and stay unchanged)
+    uint32_t xr[32], yr[32];
+    if (i < s.N) {
+      const float4 *px = reinterpret_cast<const float4 *>(s.x + size_t(i) * s.Cp + c0);
+      const float4 *py = reinterpret_cast<const float4 *>(s.y + size_t(i) * s.Cp + c0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float4 vx = px[u], vy = py[u];
+        xr[4 * u] = __float_as_uint(vx.x); xr[4 * u + 1] = __float_as_uint(vx.y);
+        xr[4 * u + 2] = __float_as_uint(vx.z); xr[4 * u + 3] = __float_as_uint(vx.w);
+        yr[4 * u] = __float_as_uint(vy.x); yr[4 * u + 1] = __float_as_uint(vy.y);
+        yr[4 * u + 2] = __float_as_uint(vy.z); yr[4 * u + 3] = __float_as_uint(vy.w);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) xr[j] = yr[j] = 0u;
+    }
+    __syncwarp();
+    tc::tmem_st_32x32b_x32(tmem + lane_off + kTmemX + cl, xr);
+    tc::tmem_st_32x32b_x32(tmem + lane_off + kTmemY + cl, yr);
+    tc::tmem_wait_st();
+  }
+  const float hi = i < s.N ? __ldg(a.h + i) : 0.f;
+  if (warp == 0 && lane == 0 && a.n_begin < a.n_end) {  // J tiles of the first step's first stages
+    for (int kb = 0; kb < npre; ++kb) {
+      tc::mbar_arrive_expect_tx(&full[kb], 2 * kTcTile);
+      tc::tma_load_2d(sA + kb * kTcTile, &m.A, &full[kb], kb * kTcBK, m0);
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+
+  constexpr uint32_t idesc = tc::idesc_f8_e4m3(kTcBM, kTcBN);
+  int n = a.n_begin;
+  bool prefetched = a.n_begin < a.n_end;
+  for (; n < a.n_end; ++n) {
+    const uint32_t q = uint32_t(n - a.n_begin);
+    if (warp == 0) {
+      // producer: f tiles as their row tiles publish step q, J tiles beyond the prefetched ones
+      const int brow = (n & 1) * s.Cp + n0;
+      uint64_t t0 = 0;
+      uint32_t polls = 0;
+      int kb = 0;
+      while (kb < KB) {
+        const int kq = kb + lane;
+        const bool ok = q == 0 || kq >= KB || tc::ld_acquire_gpu(a.flags + kq * a.Ct + ct) >= q;
+        const unsigned ball = __ballot_sync(0xffffffffu, ok);
+        int nready = ball == 0xffffffffu ? 32 : __ffs(~ball) - 1;
+        nready = nready < KB - kb ? nready : KB - kb;
+        if (nready == 0) {
+          int give_up = 0;
+          if (lane == 0) {
+            const uint64_t now = tc::globaltimer_ns();
+            if (t0 == 0) t0 = now;
+            if (*reinterpret_cast<volatile int *>(a.err) != 0) {
+              give_up = 1;
+            } else if (now - t0 > kFlagTimeoutNs || ++polls > (1u << 26)) {
+              atomicCAS(a.err, 0, tc::ERR_WAIT_FLAG);
+              give_up = 1;
+            }
+          }
+          if (__shfl_sync(0xffffffffu, give_up, 0)) {
+            nready = KB - kb;  // proceed with whatever the buffer holds; the run reports the error
+          } else {
+            __nanosleep(64);
+            continue;
+          }
+        }
+        if (lane == 0) {
+          asm volatile("fence.acq_rel.gpu;" ::: "memory");
+          tc::fence_proxy_async_global();
+          for (int j = kb; j < kb + nready; ++j) {
+            const uint32_t g = q * KB + j, st = g % kTpStages, use = g / kTpStages;
+            if (j >= npre) {
+              if (use > 0) tc::mbar_wait(&empty[st], (use - 1) & 1, a.err, tc::ERR_WAIT_EMPTY);
+              tc::mbar_arrive_expect_tx(&full[st], 2 * kTcTile);
+              tc::tma_load_2d(sA + st * kTcTile, &m.A, &full[st], j * kTcBK, m0);
+            }
+            tc::tma_load_2d(sB + st * kTcTile, &m.B, &full[st], j * kTcBK, brow);
+          }
+        }
+        __syncwarp();
+        kb += nready;
+      }
+      // J tiles of the next step's first stages, behind this step's MMAs
+      prefetched = n + 1 < a.n_end;
+      if (lane == 0 && prefetched) {
+        for (int j = 0; j < npre; ++j) {
+          const uint32_t g = (q + 1) * KB + j, st = g % kTpStages, use = g / kTpStages;
+          if (use > 0) tc::mbar_wait(&empty[st], (use - 1) & 1, a.err, tc::ERR_WAIT_EMPTY);
+          tc::mbar_arrive_expect_tx(&full[st], 2 * kTcTile);
+          tc::tma_load_2d(sA + st * kTcTile, &m.A, &full[st], j * kTcBK, m0);
+        }
+      }
+    } else if (warp == 1 && lane == 0) {
+      for (int kb = 0; kb < KB; ++kb) {
+        const uint32_t g = q * KB + kb, st = g % kTpStages, use = g / kTpStages;
+        tc::mbar_wait(&full[st], use & 1, a.err, tc::ERR_WAIT_FULL);
+        tc::tc_fence_after();
+        const uint32_t a0 = tc::smem_u32(sA + st * kTcTile), b0 = tc::smem_u32(sB + st * kTcTile);
+#pragma unroll
+        for (int kk = 0; kk < kTcBK / 32; ++kk)
+          tc::mma_f8(tmem, tc::smem_desc_sw128(a0 + kk * 32), tc::smem_desc_sw128(b0 + kk * 32), idesc,
+                     (kb | kk) != 0 ? 1u : 0u);
+        tc::mma_commit(&empty[st]);
+      }
+      tc::mma_commit(done);
+    }
+    __syncwarp();
+    const float ka = __ldg(t.ka + n), dnext = __ldg(t.dl + n + 1);
+    const float *kjn = t.kj + size_t(n) * t.R;
+    tc::mbar_wait(done, q & 1, a.err, tc::ERR_WAIT_DONE);
+    tc::tc_fence_after();
+    {
+      uint32_t g[32], xr[32], yr[32];
+      tc::tmem_ld_32x32b_x32_nowait(tmem + lane_off + cl, g);
+      tc::tmem_ld_32x32b_x32_nowait(tmem + lane_off + kTmemX + cl, xr);
+      tc::tmem_ld_32x32b_x32_nowait(tmem + lane_off + kTmemY + cl, yr);
+      tc::tmem_wait_ld();
+      tc::reg_fence(g);
+      tc::reg_fence(xr);
+      tc::reg_fence(yr);
+      uint8_t *sFcol = sF + cl * kTcBM + rl;
+      if (i < s.N && c0 < s.C) {
+        sb_update_regs32<P>(s, t, ka, dnext, kjn, c0, g, hi, xr, yr, sFcol);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) sFcol[j * kTcBM] = 0;
+      }
+      __syncwarp();
+      tc::tmem_st_32x32b_x32(tmem + lane_off + kTmemX + cl, xr);
+      tc::tmem_st_32x32b_x32(tmem + lane_off + kTmemY + cl, yr);
+      tc::tmem_wait_st();
+    }
+    tc::fence_proxy_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      // publish f_{n+1} of this tile: spins m0.., columns n0.. of the other FT buffer
+      tc::tma_store_2d(&m.Fst, sF, m0, ((n + 1) & 1) * s.Cp + n0);
+      tc::tma_store_commit_and_wait_all();
+      tc::fence_proxy_async_global();
+      tc::st_release_gpu(a.flags + mt * a.Ct + ct, q + 1);
+      *s_abort = *reinterpret_cast<volatile int *>(a.err);
+    }
+    __syncthreads();
+    tc::tc_fence_after();
+    if (*s_abort != 0) break;
+  }
+  if (n < a.n_end && prefetched && warp == 0 && lane == 0) {
+    // stopped early with J tiles of step n + 1 in flight: complete those stages
+    // (with any f tile) and wait for them, so no copy outlives the block
+    const uint32_t q = uint32_t(n + 1 - a.n_begin);
+    const int brow = ((n + 1) & 1) * s.Cp + n0;
+    for (int j = 0; j < npre; ++j) {
+      const uint32_t g = q * KB + j, st = g % kTpStages, use = g / kTpStages;
+      tc::tma_load_2d(sB + st * kTcTile, &m.B, &full[st], j * kTcBK, brow);
+      tc::mbar_wait(&full[st], use & 1, a.err, tc::ERR_WAIT_FULL);
+    }
+  }
+  __syncwarp();
+  {  // the state tile back to global memory
+    uint32_t xr[32], yr[32];
+    tc::tmem_ld_32x32b_x32_nowait(tmem + lane_off + kTmemX + cl, xr);
+    tc::tmem_ld_32x32b_x32_nowait(tmem + lane_off + kTmemY + cl, yr);
+    tc::tmem_wait_ld();
+    tc::reg_fence(xr);
+    tc::reg_fence(yr);
+    if (i < s.N) {
+      float4 *px = reinterpret_cast<float4 *>(s.x + size_t(i) * s.Cp + c0);
+      float4 *py = reinterpret_cast<float4 *>(s.y + size_t(i) * s.Cp + c0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        px[u] = make_float4(__uint_as_float(xr[4 * u]), __uint_as_float(xr[4 * u + 1]),
+                            __uint_as_float(xr[4 * u + 2]), __uint_as_float(xr[4 * u + 3]));
+        py[u] = make_float4(__uint_as_float(yr[4 * u]), __uint_as_float(yr[4 * u + 1]),
+                            __uint_as_float(yr[4 * u + 2]), __uint_as_float(yr[4 * u + 3]));
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
 // f codes [N][Cp] -> e4m3 f [Cp][Kp] (zeros for padded spins), for buffer b.
 __global__ void k_f_to_ft8(StateView s, int which, uint8_t *FT, int Kp, int b) {
   const size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x;  // over Cp * Kp
@@ -280,6 +579,11 @@ bool tc_plan_make(void **plan, const uint8_t *J8, uint8_t *FT, int Kp, int Cp, f
 
 void tc_plan_free(void *plan) { delete static_cast<TcMaps *>(plan); }
 
+static const void *const kTpFns[6] = {
+    (const void *)k_solve_dense_tc_persistent<1>, (const void *)k_solve_dense_tc_persistent<2>,
+    (const void *)k_solve_dense_tc_persistent<4>, (const void *)k_solve_dense_tc_persistent<8>,
+    (const void *)k_solve_dense_tc_persistent<16>, (const void *)k_solve_dense_tc_persistent<32>};
+
 cudaError_t tc_set_attributes() {
   const void *fns[6] = {(const void *)k_step_dense_tc<1>, (const void *)k_step_dense_tc<2>,
                         (const void *)k_step_dense_tc<4>, (const void *)k_step_dense_tc<8>,
@@ -288,7 +592,45 @@ cudaError_t tc_set_attributes() {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
     if (e != cudaSuccess) return e;
   }
+  for (const void *f : kTpFns) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kTpSmem);
+    if (e != cudaSuccess) return e;
+  }
   return cudaSuccess;
+}
+
+int tc_persistent_blocks() {
+  int dev = 0, sms = 0, best = 1 << 30;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  for (const void *f : kTpFns) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kTpThreads, kTpSmem) != cudaSuccess) return 0;
+    best = per_sm < best ? per_sm : best;
+  }
+  return sms * best;
+}
+
+bool tc_persistent_eligible(int Kp, int Cp, int blocks) {
+  return blocks > 0 && Kp % kTcBM == 0 && Cp % kTcBN == 0 && (Kp / kTcBM) * (Cp / kTcBN) <= blocks;
+}
+
+size_t tc_persistent_flag_count(int Kp, int Cp) { return size_t(Kp / kTcBM) * (Cp / kTcBN); }
+
+cudaError_t launch_solve_dense_tc_persistent(const void *plan, const StateView &s, int Kp, int *err, const float *h,
+                                             const StepTables &t, int n_begin, int n_end, uint32_t *flags,
+                                             cudaStream_t st) {
+  const int idx = s.P == 1 ? 0 : s.P == 2 ? 1 : s.P == 4 ? 2 : s.P == 8 ? 3 : s.P == 16 ? 4 : s.P == 32 ? 5 : -1;
+  if (idx < 0 || Kp % kTcBM != 0 || s.Cp % kTcBN != 0) return cudaErrorInvalidValue;
+  const int Ct = s.Cp / kTcBN;
+  cudaError_t e = cudaMemsetAsync(flags, 0, tc_persistent_flag_count(Kp, s.Cp) * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  TpArgs a{Kp, Ct, n_begin, n_end, err, h, flags};
+  TcMaps maps = *static_cast<const TcMaps *>(plan);
+  StateView sv = s;
+  StepTables tv = t;
+  void *args[] = {&maps, &sv, &a, &tv};
+  return cudaLaunchCooperativeKernel(kTpFns[idx], dim3(Ct, Kp / kTcBM), dim3(kTpThreads), args, kTpSmem, st);
 }
 
 template <int P>

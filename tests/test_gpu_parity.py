@@ -155,20 +155,64 @@ def test_per_step_jperp_disabled(sb):
     assert wx <= TOL_STEP and wy <= TOL_STEP
 
 
+@pytest.mark.parametrize("sel", [1, 2])
 @pytest.mark.parametrize("jmax,P,R", [(1, 8, 5), (3, 32, 4), (16, 2, 7), (16, 16, 9)])
-def test_dense_tensor_core_path_bit_exact_with_cuda_cores(sb, jmax, P, R):
-    """Integer J on the tcgen05 FP8 path (N >= 256) and on the CUDA-core FP32
-    path compute the same exact product and the same update: states agree bit
-    for bit after 60 steps (ragged rows N = 300, ragged columns R * P)."""
+def test_dense_tensor_core_path_bit_exact_with_cuda_cores(sb, jmax, P, R, sel):
+    """Integer J on the tcgen05 FP8 path (N >= 256; per-step kernel for sel=1,
+    the persistent solver for sel=2) and on the CUDA-core FP32 path compute
+    the same exact product and the same update: states agree bit for bit
+    after 60 steps (ragged rows N = 300, ragged columns R * P)."""
     pb, spec = dense_int(300, jmax, jmax=jmax)
     states = []
     for prec in ("exact", "fp32"):
         prob = create(sb, spec)
-        sb.set_schedule(prob, *workloads.autotune_params(R, 2), **_params(precision=prec))
+        sb.set_schedule(prob, *workloads.autotune_params(R, 2), **_params(precision=prec, kernel_select=sel))
         sb.run_begin(prob, 400, P, R, seed=5)
         sb.run_advance(prob, 60)
+        assert prob.info().step_kernel == ({1: 2, 2: 5}[sel] if prec == "exact" else 1)
         states.append(sb.get_state(prob)[:2])
     assert np.array_equal(states[0][0], states[1][0]) and np.array_equal(states[0][1], states[1][1])
+
+
+@pytest.mark.parametrize("N,P,R,jmax", [(300, 8, 40, 3), (512, 16, 16, 1), (1000, 32, 32, 1), (260, 4, 33, 16)])
+def test_persistent_dense_tc_solver_matches_per_step(sb, N, P, R, jmax):
+    """The persistent tcgen05 solver (x, y resident in tensor memory, per-tile
+    step flags between CTAs) and the per-step tcgen05 kernel give
+    bit-identical runs, readouts every 37 steps included; ragged row and
+    column tiles (N = 300, 260; R * P = 320, 132)."""
+    pb, spec = dense_int(N, N + R, jmax=jmax)
+    out = []
+    for sel in (1, 2):
+        prob = create(sb, spec)
+        sb.set_schedule(prob, *workloads.autotune_params(R, N), **_params(kernel_select=sel, eval_every=37))
+        sb.run(prob, 200, P, R, seed=N)
+        assert prob.info().step_kernel == (2 if sel == 1 else 5)
+        out.append((sb.get_state(prob)[:2], sb.get_energies(prob), sb.get_best(prob)))
+    (xa, ya), ea, ba = out[0]
+    (xb, yb), eb, bb = out[1]
+    assert np.array_equal(xa, xb) and np.array_equal(ya, yb)
+    assert np.array_equal(ea[1], eb[1])
+    for k in ba:
+        assert np.array_equal(ba[k], bb[k]), k
+    _check_best_with_readouts(sb, pb, prob, R, 200, 37)
+
+
+def test_persistent_dense_tc_solver_resume(sb):
+    """Stretches of the persistent tcgen05 solver resumed across
+    begin/advance/finish give the state of one uninterrupted run."""
+    pb, spec = sk(384, 9)
+    prob = create(sb, spec)
+    sb.set_schedule(prob, *workloads.autotune_params(16, 9), **_params(kernel_select=2))
+    sb.run(prob, 150, 16, 16, seed=4)
+    xa, ya, _ = sb.get_state(prob)
+    sb.run_begin(prob, 150, 16, 16, seed=4)
+    sb.run_advance(prob, 1)
+    sb.run_advance(prob, 60)
+    sb.run_advance(prob, 500)
+    sb.run_finish(prob)
+    xb, yb, _ = sb.get_state(prob)
+    assert prob.info().step_kernel == 5
+    assert np.array_equal(xa, xb) and np.array_equal(ya, yb)
 
 
 def test_per_step_dense_tensor_core_sk(sb):
