@@ -259,14 +259,34 @@ struct TpArgs {
 // order, as sb_update_row32: all momenta first (they read the old positions of
 // the ring neighbours), then positions, wall and f, whose e4m3 code goes to
 // column j of the transposed f tile (sFcol[j * 128]).
+// J_perp of the runs of a 32-column chunk.  For P >= 4 (at most 8 runs) the
+// values are read before the accumulator is ready, off the critical path; for
+// P < 4 (16 or 32 runs, which would not fit beside the tile in registers) they
+// are read inside the update.
+template <int P>
+struct KjChunk {
+  static constexpr int kRuns = 32 / (P < 32 ? P : 32);
+  static constexpr bool kEarly = P >= 4;
+  float v[kEarly ? kRuns : 1];
+  const float *kjn;
+  __device__ __forceinline__ void load(const StateView &s, const float *kj_step, int c0) {
+    kjn = kj_step;
+    if constexpr (kEarly) {
+#pragma unroll
+      for (int q = 0; q < kRuns; ++q) v[q] = (c0 + q * P < s.C) ? __ldg(kjn + c0 / P + q) : 0.f;
+    }
+  }
+  __device__ __forceinline__ float get(int c0, int q) const {
+    if constexpr (kEarly) return v[q];
+    else return __ldg(kjn + c0 / P + q);
+  }
+};
+
 template <int P>
 __device__ __forceinline__ void sb_update_regs32(const StateView &s, const StepTables &t, float ka, float dnext,
-                                                 const float *kjn, int c0, const uint32_t (&g)[32], float hi,
+                                                 const KjChunk<P> &kj, int c0, const uint32_t (&g)[32], float hi,
                                                  uint32_t (&xr)[32], uint32_t (&yr)[32], uint8_t *sFcol) {
   constexpr int PR = P < 32 ? P : 32;
-  float kjv[32 / PR];
-#pragma unroll
-  for (int q = 0; q < 32 / PR; ++q) kjv[q] = (c0 + q * P < s.C) ? __ldg(kjn + c0 / P + q) : 0.f;
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
     if (c0 + j >= s.C) continue;
@@ -275,7 +295,7 @@ __device__ __forceinline__ void sb_update_regs32(const StateView &s, const StepT
     const float xj = __uint_as_float(xr[j]);
     float yn = fmaf(t.kc, __uint_as_float(g[j]) + hi, __uint_as_float(yr[j]));
     yn = fmaf(-ka, xj, yn);
-    yn = fmaf(kjv[j / PR], xm + xp, yn);
+    yn = fmaf(kj.get(c0, j / PR), xm + xp, yn);
     yr[j] = __float_as_uint(yn);
   }
 #pragma unroll
@@ -447,7 +467,8 @@ __global__ void __launch_bounds__(kTpThreads, 1)
     }
     __syncwarp();
     const float ka = __ldg(t.ka + n), dnext = __ldg(t.dl + n + 1);
-    const float *kjn = t.kj + size_t(n) * t.R;
+    KjChunk<P> kj;
+    kj.load(s, t.kj + size_t(n) * t.R, c0);
     tc::mbar_wait(done, q & 1, a.err, tc::ERR_WAIT_DONE);
     tc::tc_fence_after();
     {
@@ -461,7 +482,7 @@ __global__ void __launch_bounds__(kTpThreads, 1)
       tc::reg_fence(yr);
       uint8_t *sFcol = sF + cl * kTcBM + rl;
       if (i < s.N && c0 < s.C) {
-        sb_update_regs32<P>(s, t, ka, dnext, kjn, c0, g, hi, xr, yr, sFcol);
+        sb_update_regs32<P>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, sFcol);
       } else {
 #pragma unroll
         for (int j = 0; j < 32; ++j) sFcol[j * kTcBM] = 0;
