@@ -60,6 +60,8 @@ extern "C" {
 
 /* Form of f in Eq. 7. */
 #define SBQA_VARIANT_THRESHOLD 0 /* f(x) = 0 if |x| <= Delta(t), else sign(x) (Eq. 8) */
+#define SBQA_VARIANT_BALLISTIC 1 /* f(x) = x: the bSB form of SBM (Sec. II A), with
+                                    the replica coupling of Eq. 7 unchanged   */
 
 typedef struct sbqa_problem sbqa_problem;
 
@@ -111,8 +113,9 @@ typedef struct {
                              FP8, 3 the one-launch small dense solver, 4 the
                              persistent CSR solver (one cooperative launch
                              for all steps), 5 the persistent dense tcgen05
-                             solver (x, y resident in tensor memory); -1
-                             none                                          */
+                             solver (x, y resident in tensor memory), 6 CSR
+                             and 7 dense CUDA cores for the ballistic form
+                             f(x) = x; -1 none                             */
     int32_t step_variant; /* CSR kernel variant picked by the autotuner:
                              4 << v consecutive replica columns per lane;
                              -1 before the first run                      */
@@ -138,7 +141,10 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info);
  *   delta_slope  Delta(t) = delta_slope * t/T (Eq. 8 threshold; default 0.7)
  *   init_amp     initial x, y uniform in [-init_amp, init_amp) (default 0.1)
  *   jperp_enable 1: J_perp(t) of Eq. 5; 0: J_perp = 0 (plain SB per replica)
- *   variant      SBQA_VARIANT_THRESHOLD (the only form served)
+ *   variant      SBQA_VARIANT_THRESHOLD (SBQA, Eq. 8) or
+ *                SBQA_VARIANT_BALLISTIC (f(x) = x; the product runs on FP32
+ *                positions: CSR kernels for sparse J, the CUDA-core kernel
+ *                for dense J; not served by the batching engine)
  *   precision    SBQA_PREC_*
  *   eval_every   0: read out only after the last step; K > 0: also after
  *                every step n with (n+1) % K == 0, keeping the best so far

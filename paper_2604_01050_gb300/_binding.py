@@ -30,6 +30,8 @@ ERR_TIMEOUT = -8
 PREC_AUTO, PREC_FP32, PREC_EXACT, PREC_BF16 = 0, 1, 2, 3
 PRECISIONS = {"auto": PREC_AUTO, "fp32": PREC_FP32, "exact": PREC_EXACT, "bf16": PREC_BF16}
 VARIANT_THRESHOLD = 0
+VARIANT_BALLISTIC = 1
+VARIANTS = {"threshold": VARIANT_THRESHOLD, "ballistic": VARIANT_BALLISTIC}
 
 # Every symbol include/sbqa.h declares.
 EXPORTS = (
@@ -206,11 +208,13 @@ def create_problem_csr(n, row_ptr, col_idx, val, h=None) -> Problem:
 
 def set_schedule(pb: Problem, beta=None, alpha=None, **kw):
     """Keyword names follow ``sbqa_params``; ``precision`` may be a name
-    ('auto', 'fp32', 'exact', 'bf16')."""
+    ('auto', 'fp32', 'exact', 'bf16'), ``variant`` 'threshold' or 'ballistic'."""
     prm = default_params()
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]
+        if k == "variant" and isinstance(v, str):
+            v = VARIANTS[v]
         if k == "jperp_enable":
             v = int(bool(v))
         setattr(prm, k, v)

@@ -64,7 +64,7 @@ sbqa_problem::~sbqa_problem() {
   d_row_ptr.release(); d_col.release(); d_col_pm1.release(); d_npos.release(); d_val_f32.release();
   d_val_bf16.release(); d_dense_f32.release(); d_h.release(); d_e_i32.release();
   d_e_f64.release(); d_h_i64.release(); d_h_f64.release(); d_x.release(); d_y.release();
-  d_F0.release(); d_F1.release(); d_Sg.release(); d_ka.release(); d_dl.release();
+  d_F0.release(); d_F1.release(); d_Fx0.release(); d_Fx1.release(); d_Sg.release(); d_ka.release(); d_dl.release();
   d_kj.release(); d_ei.release(); d_part_i.release(); d_best_ei.release(); d_ef.release();
   d_part_f.release(); d_best_e.release(); d_best_k.release(); d_best_step.release();
   d_have.release(); d_best_spins.release(); d_bar.release(); d_tc_flags.release();
@@ -219,8 +219,9 @@ int prepare_tc_values(sbqa_problem *p) {
 int prepare_dense_values(sbqa_problem *p, int precision) {
   if (precision == SBQA_PREC_EXACT && (!p->j_integer || p->max_abs_j > 16))
     return fail(SBQA_ERR_UNSUPPORTED, "EXACT precision needs integer J with |J_ij| <= 16");
+  // the FP8 tensor-core product is exact only for f in {-1, 0, 1}: thresholded form only
   p->use_tc = (precision == SBQA_PREC_AUTO || precision == SBQA_PREC_EXACT) && p->j_integer &&
-              p->max_abs_j <= 16 && p->n >= kTcMinN;
+              p->max_abs_j <= 16 && p->n >= kTcMinN && !p->ballistic();
   if (p->use_tc) return prepare_tc_values(p);
   const int want = precision == SBQA_PREC_BF16 ? SBQA_PREC_BF16 : SBQA_PREC_FP32;
   if (p->d_dense_f32.p && p->dense_prec == want) return SBQA_OK;
@@ -248,6 +249,11 @@ int alloc_run(sbqa_problem *p, int S, int P, int R) {
   SBQA_CUDA(p->d_y.alloc(NC));
   SBQA_CUDA(p->d_F0.alloc(NC));
   SBQA_CUDA(p->d_F1.alloc(NC));
+  if (p->ballistic()) {
+    SBQA_CUDA(p->d_Fx0.alloc(NC));
+    SBQA_CUDA(p->d_Fx1.alloc(NC));
+    SBQA_CUDA(cudaMemsetAsync(p->d_Fx1.p, 0, NC * sizeof(float), p->stream));
+  }
   SBQA_CUDA(p->d_Sg.alloc(NC));
   SBQA_CUDA(p->d_ka.alloc(size_t(std::max(S, 1))));
   SBQA_CUDA(p->d_dl.alloc(size_t(S) + 1));
@@ -287,6 +293,15 @@ int build_tables(sbqa_problem *p) {
 
 cudaError_t issue_step(sbqa_problem *p, int n, cudaStream_t st) {
   const StateView s = p->state();
+  if (p->ballistic()) {
+    if (p->dense) {
+      DenseView d;
+      d.J = p->d_dense_f32.p;
+      d.h = p->d_h.p;
+      return launch_step_dense_bsb(s, d, p->tables, n, st);
+    }
+    return launch_step_csr_bsb(s, p->csr(), p->tables, n, st);
+  }
   if (p->use_tc) return launch_step_dense_tc(p->tc_plan, s, p->Kp, p->d_FT.p, p->d_err.p, p->d_h.p, p->tables, n, st);
   if (p->dense) {
     DenseView d;
@@ -303,6 +318,11 @@ cudaError_t issue_step(sbqa_problem *p, int n, cudaStream_t st) {
 // per handle and shape; skipped while the stream is being captured.
 int autotune_csr(sbqa_problem *p) {
   if (p->dense) return SBQA_OK;
+  if (p->ballistic()) {  // one kernel form; nothing to choose
+    p->use_persistent = false;
+    if (p->csr_variant < 0) p->csr_variant = 0;
+    return SBQA_OK;
+  }
   if (p->csr_variant >= 0 && p->csr_variant_cp == p->Cp && p->csr_variant_kind == p->kind &&
       p->csr_variant_select == p->prm.kernel_select)
     return SBQA_OK;
@@ -691,6 +711,7 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info) {
   info->max_abs_j = p->max_abs_j;
   info->c0_auto = p->c0_auto;
   info->step_kernel = !p->begun ? -1
+                     : p->ballistic() ? (p->dense ? 7 : 6)
                                  : (p->small_path ? 3
                                                   : (p->use_tc ? (p->use_tc_persistent && p->tc_persistent_ok() ? 5 : 2)
                                                                : (p->dense ? 1 : (p->use_persistent ? 4 : 0))));
@@ -706,7 +727,8 @@ int sbqa_set_schedule(sbqa_problem *p, const sbqa_params *q) {
   if (!finite_all(v, 6)) return fail(SBQA_ERR_NOT_FINITE, "non-finite parameter");
   if (q->a0 <= 0 || q->dt <= 0 || q->gamma0 <= 0 || q->delta_slope < 0 || q->init_amp < 0 || q->init_amp > 1)
     return fail(SBQA_ERR_INVALID_ARG, "need a0, dt, gamma0 > 0, delta_slope >= 0, 0 <= init_amp <= 1");
-  if (q->variant != SBQA_VARIANT_THRESHOLD) return fail(SBQA_ERR_UNSUPPORTED, "only the thresholded f (Eq. 8) is served");
+  if (q->variant != SBQA_VARIANT_THRESHOLD && q->variant != SBQA_VARIANT_BALLISTIC)
+    return fail(SBQA_ERR_INVALID_ARG, "variant must be SBQA_VARIANT_THRESHOLD or SBQA_VARIANT_BALLISTIC");
   if (q->precision < SBQA_PREC_AUTO || q->precision > SBQA_PREC_BF16) return fail(SBQA_ERR_INVALID_ARG, "bad precision");
   if (q->precision == SBQA_PREC_EXACT && (!p->j_integer || p->max_abs_j > 16))
     return fail(SBQA_ERR_UNSUPPORTED, "EXACT precision needs integer J with |J_ij| <= 16");
@@ -747,6 +769,7 @@ int sbqa_run_begin(sbqa_problem *p, int32_t steps, int32_t P, int32_t R, uint64_
   SBQA_CUDA(cudaMemsetAsync(p->d_err.p, 0, sizeof(int), p->stream));
   SBQA_CUDA(launch_init(s, seed, float(p->prm.init_amp), 0.0f, p->stream));
   if (p->use_tc) SBQA_CUDA(launch_f_to_ft8(s, 0, p->d_FT.p, p->Kp, 0, p->stream));
+  if (p->ballistic()) SBQA_CUDA(launch_copy_fx(s, 0, p->stream));
   SBQA_CUDA(launch_reset_best(s, p->best(), p->stream));
   p->step_done = 0;
   p->begun = true;
@@ -777,7 +800,7 @@ int sbqa_run_finish(sbqa_problem *p) {
 int sbqa_run(sbqa_problem *p, int32_t steps, int32_t P, int32_t R, uint64_t seed, void *stream) {
   // small integer dense instances: the whole solve in one launch
   if (p && p->have_params && p->dense && p->is_integer && p->prm.eval_every == 0 &&
-      check_run_args(p, steps, P, R) == SBQA_OK && small_eligible(p->n, P, steps)) {
+      !p->ballistic() && check_run_args(p, steps, P, R) == SBQA_OK && small_eligible(p->n, P, steps)) {
     DeviceGuard g(p->device);
     p->stream = static_cast<cudaStream_t>(stream);
     p->begun = p->finished = false;
@@ -817,6 +840,7 @@ int sbqa_run(sbqa_problem *p, int32_t steps, int32_t P, int32_t R, uint64_t seed
   key.S = steps; key.P = P; key.R = R; key.eval = p->prm.eval_every; key.kind = p->kind;
   key.dense = p->dense ? 1 : 0; key.x = p->d_x.p; key.kj = p->d_kj.p;
   key.kc = p->tables.kc; key.kx = p->tables.kx; key.tc = p->use_tc ? 1 : 0; key.variant = p->csr_variant;
+  key.fvar = p->prm.variant;
   if (!(p->graph && p->graph_key == key)) {
     if (p->graph) {
       cudaGraphExecDestroy(p->graph);
@@ -928,6 +952,7 @@ int sbqa_set_state(sbqa_problem *p, const float *x, const float *y, int32_t step
   SBQA_CUDA(launch_refresh_f(p->state(), step_done & 1, float(p->prm.delta_slope * tau), p->stream));
   if (p->use_tc)
     SBQA_CUDA(launch_f_to_ft8(p->state(), step_done & 1, p->d_FT.p, p->Kp, step_done & 1, p->stream));
+  if (p->ballistic()) SBQA_CUDA(launch_copy_fx(p->state(), step_done & 1, p->stream));
   p->step_done = step_done;
   p->finished = false;
   return SBQA_OK;

@@ -100,6 +100,7 @@ struct Request {
     StateView s;
     s.N = prob->n; s.C = C; s.Cp = Cp; s.P = P; s.R = R;
     s.x = x; s.y = y; s.F[0] = F0; s.F[1] = F1; s.Sg = Sg;
+    s.Fx[0] = s.Fx[1] = nullptr;
     return s;
   }
   BestView best_view() const {
@@ -292,6 +293,8 @@ int sbqa_engine_submit(sbqa_engine *e, sbqa_problem *p, int32_t steps, int32_t P
   int rc = problem_check_run(p, steps, P, R);
   if (rc != SBQA_OK) return rc;
   if (steps < 1) return set_error(SBQA_ERR_INVALID_ARG, "engine requests need steps >= 1");
+  if (p->prm.variant != SBQA_VARIANT_THRESHOLD)
+    return set_error(SBQA_ERR_UNSUPPORTED, "the engine serves the thresholded f (Eq. 8) only");
   if ((rc = problem_prepare_values(p)) != SBQA_OK) return rc;
   Request r;
   r.id = int(e->reqs.size());

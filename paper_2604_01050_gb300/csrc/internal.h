@@ -35,10 +35,12 @@ struct StateView {
   int N, C, Cp, P, R;
   float *x, *y;
   uint8_t *F[2];  // f(x) + 1 codes, double-buffered by step parity
+  float *Fx[2];   // f(x) = x copies of the ballistic form (null otherwise)
   int8_t *Sg;     // [N][Cp] readout spins sign(x), +1 for x >= 0
   // F buffer holding the codes of step n (selected without indexing the
   // array, which would put the kernel argument in local memory)
   __host__ __device__ uint8_t *f_of(int n) const { return (n & 1) ? F[1] : F[0]; }
+  __host__ __device__ float *fx_of(int n) const { return (n & 1) ? Fx[1] : Fx[0]; }
 };
 
 struct CsrView {
@@ -99,6 +101,13 @@ size_t tc_persistent_flag_count(int Kp, int Cp);
 cudaError_t launch_solve_dense_tc_persistent(const void *plan, const StateView &s, int Kp, int *err, const float *h,
                                              const StepTables &t, int n_begin, int n_end, uint32_t *flags,
                                              cudaStream_t st);
+
+// Ballistic form f(x) = x (step_bsb.cu): CSR and dense CUDA-core steps, and
+// the copy x -> Fx[which] that starts the f buffers.
+cudaError_t launch_step_csr_bsb(const StateView &s, const CsrView &J, const StepTables &t, int n, cudaStream_t st);
+cudaError_t launch_step_dense_bsb(const StateView &s, const DenseView &J, const StepTables &t, int n,
+                                  cudaStream_t st);
+cudaError_t launch_copy_fx(const StateView &s, int which, cudaStream_t st);
 
 // Whole solve of a small integer dense instance in one launch (solve_small.cu).
 struct SmallArgs {

@@ -111,6 +111,7 @@ struct sbqa_problem {
   sbqa::DevBuf<uint32_t> d_tc_flags;  // per-tile step counters of the persistent solver
   sbqa::DevBuf<float> d_x, d_y;
   sbqa::DevBuf<uint8_t> d_F0, d_F1;
+  sbqa::DevBuf<float> d_Fx0, d_Fx1;  // f(x) = x buffers of the ballistic form
   sbqa::DevBuf<int8_t> d_Sg;
   sbqa::DevBuf<float> d_ka, d_dl, d_kj;
   sbqa::DevBuf<int64_t> d_ei, d_part_i, d_best_ei;
@@ -123,24 +124,27 @@ struct sbqa_problem {
   cudaGraphExec_t graph = nullptr;
   cudaStream_t cap_stream = nullptr;
   struct Key {
-    int S = -1, P = -1, R = -1, eval = -1, kind = -1, dense = -1, tc = -1, variant = -1;
+    int S = -1, P = -1, R = -1, eval = -1, kind = -1, dense = -1, tc = -1, variant = -1, fvar = -1;
     float kc = 0.f, kx = 0.f;  // step constants are kernel arguments in the graph
     const void *x = nullptr, *kj = nullptr;
     bool operator==(const Key &o) const {
       return S == o.S && P == o.P && R == o.R && eval == o.eval && kind == o.kind &&
-             dense == o.dense && tc == o.tc && variant == o.variant && x == o.x && kj == o.kj &&
+             dense == o.dense && tc == o.tc && variant == o.variant && fvar == o.fvar && x == o.x && kj == o.kj &&
              std::memcmp(&kc, &o.kc, sizeof(float)) == 0 && std::memcmp(&kx, &o.kx, sizeof(float)) == 0;
     }
   } graph_key;
 
   ~sbqa_problem();  // waits for the device, releases every buffer (api.cu)
 
+  bool ballistic() const { return prm.variant == SBQA_VARIANT_BALLISTIC; }
+
   bool tc_persistent_ok() const {
     return use_tc && tc_plan && sbqa::tc_persistent_eligible(Kp, Cp, tc_persist_blocks);
   }
 
   bool persistent_ok() const {
-    return !dense && kind == sbqa::VAL_PM1 && sbqa::persistent_eligible(n, Cp, max_degree, persist_blocks);
+    return !dense && !ballistic() && kind == sbqa::VAL_PM1 &&
+           sbqa::persistent_eligible(n, Cp, max_degree, persist_blocks);
   }
 
   StateView state() const {
@@ -148,6 +152,7 @@ struct sbqa_problem {
     s.N = n; s.C = C; s.Cp = Cp; s.P = P; s.R = R;
     s.x = d_x.p; s.y = d_y.p;
     s.F[0] = d_F0.p; s.F[1] = d_F1.p;
+    s.Fx[0] = d_Fx0.p; s.Fx[1] = d_Fx1.p;
     s.Sg = d_Sg.p;
     return s;
   }

@@ -20,6 +20,7 @@ __device__ __forceinline__ void batched_rows(const SlotDesc &d, int n, int r0, i
   StateView s;
   s.N = d.N; s.C = d.C; s.Cp = d.Cp; s.P = P; s.R = d.R;
   s.x = d.x; s.y = d.y; s.F[0] = d.F0; s.F[1] = d.F1; s.Sg = nullptr;
+  s.Fx[0] = s.Fx[1] = nullptr;
   StepTables t;
   t.ka = d.ka; t.dl = d.dl; t.kj = d.kj; t.kc = d.kc; t.kx = d.kx; t.S = d.S; t.R = d.R;
   const uint8_t *Fc = s.f_of(n) + c4;

@@ -99,3 +99,10 @@ def test_engine_rejects_bad_requests(sb):
     with pytest.raises(sb.SBQAError) as e:
         sb.engine_result(eng, 0)
     assert e.value.status == sb.ERR_INVALID_ARG
+    sb.set_schedule(prob, variant="ballistic")  # served by sbqa_run, not by the engine
+    with pytest.raises(sb.SBQAError) as e:
+        sb.engine_submit(eng, prob, 10, 8, 2)
+    assert e.value.status == sb.ERR_UNSUPPORTED
+    with pytest.raises(sb.SBQAError) as e:
+        sb.set_schedule(prob, variant=2)
+    assert e.value.status == sb.ERR_INVALID_ARG

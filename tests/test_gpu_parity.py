@@ -59,7 +59,7 @@ def _params(**kw):
 
 def _oracle_kwargs(p, pb):
     c0 = p["c0"] if p["c0"] > 0 else oracle.c0_auto(pb)
-    return dict(a0=p["a0"], c0=c0, dt=p["dt"])
+    return dict(a0=p["a0"], c0=c0, dt=p["dt"], variant=p.get("variant", 0))
 
 
 # ---------------------------------------------------------------- initial state
@@ -222,9 +222,9 @@ def test_per_step_dense_tensor_core_sk(sb):
 
 
 # ---------------------------------------------------------------- free-running trajectories
-def _free_running(sb, pb, spec, P, R, S, steps, gamma0, seed=0, prec="auto", pb_oracle=None):
+def _free_running(sb, pb, spec, P, R, S, steps, gamma0, seed=0, prec="auto", pb_oracle=None, **pkw):
     prob = create(sb, spec)
-    p = _params(gamma0=gamma0, precision=prec)
+    p = _params(gamma0=gamma0, precision=prec, **pkw)
     beta, alpha = workloads.linear_params(R)
     sb.set_schedule(prob, beta, alpha, **p)
     sb.run_begin(prob, S, P, R, seed=seed)
@@ -385,6 +385,83 @@ def test_full_run_sk64_energies_exact(sb):
     sb.run(prob, 1000, 8, 16, seed=0)
     best = _check_energies_and_best(sb, pb, prob, 16, 8)
     assert np.all(best["step"] == 999)
+
+
+# ---------------------------------------------------------------- ballistic form f(x) = x
+@pytest.mark.parametrize("case", ["lattice_pm1", "regular_f32_field", "dense_real", "dense_int", "ragged"])
+def test_ballistic_per_step(sb, case):
+    """f(x) = x (the bSB form of Sec. II A): one step from the same FP32 state
+    against the oracle's bSB step, TOL_STEP per (run, replica)."""
+    if case == "lattice_pm1":
+        pb, spec = lattice(6, 2); P, R, prec = 32, 4, "auto"
+    elif case == "regular_f32_field":
+        pb, spec = regular(500, 6, 1); P, R, prec = 16, 8, "fp32"
+    elif case == "dense_real":
+        pb, spec = dense_real(100, 3); P, R, prec = 8, 4, "fp32"
+    elif case == "dense_int":
+        pb, spec = dense_int(300, 4); P, R, prec = 16, 9, "auto"
+    else:
+        pb, spec = lattice(3, 5); P, R, prec = 2, 3, "auto"
+    wx, wy, amb, prob = _per_step(sb, pb, spec, P, R, 400, 30, prec=prec, variant=1, gamma0=4.0 * P)
+    print("bSB %s per-step worst x %.2e y %.2e wall-ambiguous %d" % (case, wx, wy, amb))
+    assert prob.info().step_kernel == (7 if spec[0] == "dense" else 6)
+    assert wx <= TOL_STEP and wy <= TOL_STEP
+
+
+def test_ballistic_bf16_against_rounded_j(sb):
+    pb, spec = regular(500, 6, 2)
+    wx, wy, _, _ = _per_step(sb, pb, spec, 16, 8, 300, 30, prec="bf16", pb_oracle=pb.bf16(), variant=1,
+                             gamma0=64.0)
+    assert wx <= TOL_STEP and wy <= TOL_STEP
+
+
+def test_ballistic_free_running_sk64(sb):
+    """f is continuous in the ballistic form, so FP32 and FP64 trajectories
+    separate only through the dynamics' own amplification: 100 steps at the
+    stable schedule stay within TOL_TRAJ."""
+    pb, spec = sk(64, 0)
+    e = _free_running(sb, pb, spec, 8, 16, 1000, 100, gamma0=32.0, variant=1)
+    print("bSB free-running max x %.2e y %.2e" % tuple(e.max(axis=0)))
+    assert e.max() <= TOL_TRAJ
+
+
+@pytest.mark.parametrize("dense", [False, True])
+def test_ballistic_full_run_energies_and_resume(sb, dense):
+    """A whole ballistic run: exact integer energies of the final spins, a
+    valid best-so-far with readouts every 50 steps, and the same state when
+    the run is split across begin/advance/finish."""
+    pb, spec = sk(200, 5) if dense else lattice(8, 3)
+    P, R, S = 8, 16, 300
+    prob = create(sb, spec)
+    sb.set_schedule(prob, *workloads.autotune_params(R, 1), **_params(variant="ballistic", eval_every=50))
+    sb.run(prob, S, P, R, seed=9)
+    xa, ya, _ = sb.get_state(prob)
+    _check_best_with_readouts(sb, pb, prob, R, S, 50)
+    sb.run_begin(prob, S, P, R, seed=9)
+    sb.run_advance(prob, 77)
+    sb.run_advance(prob, S)
+    sb.run_finish(prob)
+    xb, yb, _ = sb.get_state(prob)
+    assert np.array_equal(xa, xb) and np.array_equal(ya, yb)
+
+
+def test_ballistic_set_state_resume(sb):
+    """set_state restarts the f buffer from x: a run resumed from a dumped
+    state equals the unbroken run bit for bit."""
+    pb, spec = lattice(6, 4)
+    P, R, S = 16, 8, 120
+    prob = create(sb, spec)
+    sb.set_schedule(prob, *workloads.autotune_params(R, 2), **_params(variant="ballistic"))
+    sb.run_begin(prob, S, P, R, seed=2)
+    sb.run_advance(prob, 50)
+    x50, y50, _ = sb.get_state(prob)
+    sb.run_advance(prob, S)
+    xa, ya, _ = sb.get_state(prob)
+    sb.run_begin(prob, S, P, R, seed=777)
+    sb.set_state(prob, x50, y50, 50)
+    sb.run_advance(prob, S)
+    xb, yb, _ = sb.get_state(prob)
+    assert np.array_equal(xa, xb) and np.array_equal(ya, yb)
 
 
 def test_steps_zero_reads_initial_state(sb):
