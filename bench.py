@@ -48,9 +48,19 @@ CONFIGS = {
                    workload="dense SK N=2000, J=+-1; P=32, R=32 (J.X = 2000x2000 @ 2000x1024), 1000 steps"),
     "regular1e5": dict(kind="regular", n=100000, d=6, P=16, R=8, S=5000, prec="bf16",
                        workload="random 6-regular N=1e5, J~N(0,1), h~N(0,0.1^2), CSR, BF16 J, P=16, R=8, 5000 steps"),
+    # large-N sparse family: the lattice16 shape (P=32, R=64) as the state outgrows L2
+    "regular7e5": dict(kind="regular", n=700000, d=6, P=16, R=8, S=1000, prec="bf16",
+                       workload="random 6-regular N=7e5, J~N(0,1), h~N(0,0.1^2), CSR, BF16 J, P=16, R=8, 1000 steps"),
 }
+for _L, _S in ((24, 3000), (32, 1500), (48, 400), (64, 200), (88, 100)):
+    CONFIGS["lattice%d" % _L] = dict(
+        kind="lattice", L=_L, P=32, R=64, S=_S, prec="auto",
+        workload="3D cubic lattice spin glass L=%d (N=%d), periodic, J=+-1, CSR; P=32 replicas, R=64 runs, "
+                 "%d steps; FP32 state, exact int8 product" % (_L, _L ** 3, _S))
+SCALING = ["lattice16", "lattice24", "lattice32", "lattice48", "lattice64", "lattice88", "regular1e5", "regular7e5"]
 DEFAULT = "lattice16"
 BYTES_PER_UPDATE = 16  # x, y FP32 read + write per replica-spin update
+BYTES_PER_UPDATE_BSB = 20  # ballistic form: + the FP32 f (= x) write
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -139,12 +149,13 @@ def oracle_sample(cfg, target_s=15.0):
     beta, alpha = schedule_params(cfg)
     # calibrate on a short slice, then size the sample to about target_s
     t0 = time.perf_counter()
-    oracle.run(pb, S, P, 1, 0, beta[:1], alpha[:1], n_end=2)
+    variant = 1 if cfg.get("variant") == "ballistic" else 0
+    oracle.run(pb, S, P, 1, 0, beta[:1], alpha[:1], n_end=2, variant=variant)
     per_step_run = max((time.perf_counter() - t0) / 2, 1e-6)
     runs = max(1, min(cfg["R"], int(target_s / (per_step_run * 100))))
     steps = int(max(2, min(S, target_s / (per_step_run * runs))))
     t0 = time.perf_counter()
-    oracle.run(pb, S, P, runs, 0, beta[:runs], alpha[:runs], n_end=steps)
+    oracle.run(pb, S, P, runs, 0, beta[:runs], alpha[:runs], n_end=steps, variant=variant)
     dt = time.perf_counter() - t0
     upd = pb.n * P * runs * steps
     return {"value": upd / dt, "unit": "replica-spin updates/s", "cores": 1, "kind": "oracle",
@@ -338,6 +349,34 @@ def run_tte(args):
     return 0
 
 
+# ------------------------------------------------------------------ large-N scaling
+def run_scaling(args):
+    """Runs the sparse family one size at a time (each in its own process,
+    so device memory is returned between sizes) and prints one line with the
+    throughput and roofline fraction of every size: the lattice16 shape from
+    an L2-resident state (84 MB) to 14 GB, and the random regular graphs."""
+    import subprocess
+    points = []
+    for name in SCALING:
+        cmd = [sys.executable, os.path.abspath(__file__), "--config", name, "--steps", str(args.steps),
+               "--warmup", str(args.warmup), "--no-cpu-baseline", "--variant", args.variant]
+        out = subprocess.run(cmd, capture_output=True, text=True)
+        if out.returncode != 0:
+            print(out.stdout[-2000:], out.stderr[-4000:], file=sys.stderr)
+            return out.returncode
+        line = json.loads(out.stdout.strip().splitlines()[-1])
+        c = line["config"]
+        points.append({"config": name, "N": c["N"], "P": c["P"], "R": c["R"],
+                       "state_MB": round(c["state_bytes"] / 1e6, 1), "value": line["value"],
+                       "step_kernel": c["step_kernel"], "step_ms": line["roofline"]["step_ms"],
+                       "achieved_gbs": line["roofline"]["achieved"], "frac": line["roofline"]["frac"],
+                       "e2e": line["e2e"]["value"], "clocks": line["clocks"]})
+    print(json.dumps({"metric": "replica-spin updates/s", "mode": "scaling", "unit": "replica-spin updates/s",
+                      "variant": args.variant, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "points": points}))
+    return 0
+
+
 # ------------------------------------------------------------------ GPU arm
 def main():
     ap = argparse.ArgumentParser()
@@ -345,7 +384,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default=DEFAULT, choices=sorted(CONFIGS) + ["serving", "tte"])
+    ap.add_argument("--config", default=DEFAULT, choices=sorted(CONFIGS) + ["serving", "tte", "scaling"])
+    ap.add_argument("--variant", default="threshold", choices=["threshold", "ballistic"],
+                    help="f of Eq. 8 (SBQA) or f(x) = x (the bSB form)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--requests", type=int, default=48, help="serving: requests in the stream")
@@ -358,7 +399,12 @@ def main():
         return run_serving(args)
     if args.config == "tte":
         return run_tte(args)
-    cfg = CONFIGS[args.config]
+    if args.config == "scaling":
+        return run_scaling(args)
+    cfg = dict(CONFIGS[args.config])
+    if args.variant == "ballistic":
+        cfg["variant"] = "ballistic"
+        cfg["workload"] += "; ballistic form f(x) = x"
     if args.impl == "reference":
         return run_reference(args, cfg)
 
@@ -394,7 +440,8 @@ def main():
 
     stream = torch.cuda.Stream(device=dev)
     prob = create(inst)
-    sb.set_schedule(prob, beta, alpha, precision=cfg["prec"])
+    variant = cfg.get("variant", "threshold")
+    sb.set_schedule(prob, beta, alpha, precision=cfg["prec"], variant=variant)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     seed0 = multi.rank_seed(0, rank)
 
@@ -451,13 +498,15 @@ def main():
                 "step_ms": step_ms, "peak_source": peak_src,
                 "note": "2 N^2 R P flops per step / event-timed step time; FP8 peak = 2 x measured BF16"}
     else:
-        achieved_gbs = BYTES_PER_UPDATE * N * P * R / (step_ms * 1e-3) / 1e9
+        bpu = BYTES_PER_UPDATE_BSB if info.step_kernel in (6, 7) else BYTES_PER_UPDATE
+        achieved_gbs = bpu * N * P * R / (step_ms * 1e-3) / 1e9
         hbm_peak = peaks.get("hbm_gbs", 6800.0)
-        kname = {0: "k_step_csr", 4: "k_solve_csr_persistent", 3: "k_solve_small", 1: "k_step_dense"}[info.step_kernel]
+        kname = {0: "k_step_csr", 4: "k_solve_csr_persistent", 3: "k_solve_small", 1: "k_step_dense",
+                 6: "k_step_csr_bsb", 7: "k_step_dense_bsb"}[info.step_kernel]
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved_gbs / hbm_peak, "traffic": None, "kernel": kname, "step_ms": step_ms,
                 "peak_source": peak_src,
-                "note": "algorithmic 16 B/update x N*P*R per launch / event-timed step time"}
+                "note": "algorithmic %d B/update x N*P*R per launch / event-timed step time" % bpu}
 
     # e2e: host buffers through the C ABI, every step
     src = inst
@@ -476,7 +525,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         pe = create(src)
-        sb.set_schedule(pe, beta, alpha, precision=cfg["prec"])
+        sb.set_schedule(pe, beta, alpha, precision=cfg["prec"], variant=variant)
         sb.run(pe, S, P, R, seed=seed0 + 500 + k, stream=stream)
         best = sb.get_best(pe)
         pe.destroy()
@@ -504,9 +553,11 @@ def main():
                    "precision": cfg["prec"], "l2": "flushed (512 MB write) before every timed solve; "
                                                    "state (%.0f MB) stays L2-resident within a solve"
                                                    % (N * P * R * 10 / 1e6),
+                   "state_bytes": N * P * R * (18 if variant == "ballistic" else 10),
                    "parallelism": "independent runs per GPU (weak scaling)",
                    "step_kernel": ["csr", "dense_cuda_core", "dense_tcgen05_fp8", "dense_small_one_launch",
-                                   "csr_persistent", "dense_tcgen05_persistent"][info.step_kernel],
+                                   "csr_persistent", "dense_tcgen05_persistent", "csr_ballistic",
+                                   "dense_ballistic"][info.step_kernel],
                    "csr_variant": info.step_variant,
                    "autotune_ms_per_step": [round(v, 5) for v in info.variant_ms],
                    "autotune_persistent_ms_per_step": round(info.persistent_ms, 5)},
