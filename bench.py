@@ -133,9 +133,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ reference arm (oracle)
-def oracle_sample(cfg, target_s=15.0):
-    """Times the FP64 oracle on a bounded sample of the workload: the full
-    instance, all P replicas, a few runs and a few hundred steps."""
+def _oracle_problem(cfg):
     import oracle
     inst = make_instance(cfg)
     if inst[0] == "csr":
@@ -143,24 +141,50 @@ def oracle_sample(cfg, target_s=15.0):
         pb = oracle.Problem.csr(n, rp, col, val, h)
     else:
         pb = oracle.Problem.dense(inst[2], inst[3])
-    if cfg["prec"] == "bf16":
-        pb = pb.bf16()
+    return pb.bf16() if cfg["prec"] == "bf16" else pb
+
+
+def oracle_sample(cfg, target_s=15.0, threads=None):
+    """Times the FP64 oracle, as it stands, on a bounded sample of the
+    workload (the full instance, all P replicas, a few runs and steps):
+    single-threaded for about a third of target_s, then on all host cores
+    with one run per thread (runs are independent; the oracle is a C call
+    that releases the interpreter lock) for the rest.  The threaded figure is
+    the baseline; the single-thread one is reported beside it."""
+    import oracle
+    from concurrent.futures import ThreadPoolExecutor
+    pb = _oracle_problem(cfg)
     P, S = cfg["P"], cfg["S"]
-    beta, alpha = schedule_params(cfg)
-    # calibrate on a short slice, then size the sample to about target_s
-    t0 = time.perf_counter()
     variant = 1 if cfg.get("variant") == "ballistic" else 0
+    beta, alpha = schedule_params(cfg)
+    t0 = time.perf_counter()
     oracle.run(pb, S, P, 1, 0, beta[:1], alpha[:1], n_end=2, variant=variant)
     per_step_run = max((time.perf_counter() - t0) / 2, 1e-6)
-    runs = max(1, min(cfg["R"], int(target_s / (per_step_run * 100))))
-    steps = int(max(2, min(S, target_s / (per_step_run * runs))))
+    # single thread: a few runs x a few steps, about target_s / 3
+    t1 = target_s / 3.0
+    runs = max(1, min(cfg["R"], int(t1 / (per_step_run * 100))))
+    steps = int(max(2, min(S, t1 / (per_step_run * runs))))
     t0 = time.perf_counter()
     oracle.run(pb, S, P, runs, 0, beta[:runs], alpha[:runs], n_end=steps, variant=variant)
-    dt = time.perf_counter() - t0
-    upd = pb.n * P * runs * steps
-    return {"value": upd / dt, "unit": "replica-spin updates/s", "cores": 1, "kind": "oracle",
-            "sample": "%d of %d runs x %d of %d steps, full N=%d and P=%d, single thread, %.1f s"
-                      % (runs, cfg["R"], steps, S, pb.n, P, dt)}
+    dt1 = time.perf_counter() - t0
+    single = {"value": pb.n * P * runs * steps / dt1, "cores": 1,
+              "sample": "%d of %d runs x %d of %d steps, single thread, %.1f s" % (runs, cfg["R"], steps, S, dt1)}
+    # all cores: one run per thread, the same number of steps in each
+    T = max(1, min(threads or os.cpu_count() or 1, cfg["R"]))
+    t2 = target_s - t1
+    steps_t = int(max(2, min(S, t2 / per_step_run)))
+
+    def one(r):
+        oracle.run(pb, S, P, 1, r, beta[r:r + 1], alpha[r:r + 1], n_end=steps_t, variant=variant)
+
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=T) as ex:
+        list(ex.map(one, range(T)))
+    dt2 = time.perf_counter() - t0
+    return {"value": pb.n * P * T * steps_t / dt2, "unit": "replica-spin updates/s", "cores": T, "kind": "oracle",
+            "sample": "%d of %d runs (one per thread) x %d of %d steps, full N=%d and P=%d, %d threads, %.1f s"
+                      % (T, cfg["R"], steps_t, S, pb.n, P, T, dt2),
+            "single_thread": single}
 
 
 def run_reference(args, cfg):

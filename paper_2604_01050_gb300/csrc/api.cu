@@ -327,6 +327,14 @@ int autotune_csr(sbqa_problem *p) {
       p->csr_variant_select == p->prm.kernel_select)
     return SBQA_OK;
   p->csr_variant_select = p->prm.kernel_select;
+  if (p->prm.kernel_select >= 3) {  // a forced per-step variant
+    const int v = p->prm.kernel_select - 3;
+    p->csr_variant = csr_step_variant_ok(v, p->Cp) ? v : 0;
+    p->csr_variant_cp = p->Cp;
+    p->csr_variant_kind = p->kind;
+    p->use_persistent = false;
+    return SBQA_OK;
+  }
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   SBQA_CUDA(cudaStreamIsCapturing(p->stream, &cs));
   if (cs != cudaStreamCaptureStatusNone) return SBQA_OK;
@@ -348,7 +356,7 @@ int autotune_csr(sbqa_problem *p) {
     SBQA_CUDA(cudaEventSynchronize(e1));
     float ms = 0.f;
     SBQA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    if (v < 4) p->variant_ms[v] = ms / reps;
+    if (v < 6) p->variant_ms[v] = ms / reps;
     if (ms < best_ms) {
       best_ms = ms;
       best = v;
@@ -717,7 +725,7 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info) {
                                                                : (p->dense ? 1 : (p->use_persistent ? 4 : 0))));
   info->persistent_ms = p->use_tc ? p->tc_persistent_ms : p->persistent_ms;
   info->step_variant = p->dense ? -1 : p->csr_variant;
-  for (int v = 0; v < 4; ++v) info->variant_ms[v] = p->use_tc ? (v == 0 ? p->tc_step_ms : 0.f) : p->variant_ms[v];
+  for (int v = 0; v < 6; ++v) info->variant_ms[v] = p->use_tc ? (v == 0 ? p->tc_step_ms : 0.f) : p->variant_ms[v];
   return SBQA_OK;
 }
 
@@ -733,7 +741,7 @@ int sbqa_set_schedule(sbqa_problem *p, const sbqa_params *q) {
   if (q->precision == SBQA_PREC_EXACT && (!p->j_integer || p->max_abs_j > 16))
     return fail(SBQA_ERR_UNSUPPORTED, "EXACT precision needs integer J with |J_ij| <= 16");
   if (q->eval_every < 0 || q->n_runs < 0) return fail(SBQA_ERR_INVALID_ARG, "negative eval_every or n_runs");
-  if (q->kernel_select < 0 || q->kernel_select > 2) return fail(SBQA_ERR_INVALID_ARG, "kernel_select must be 0, 1 or 2");
+  if (q->kernel_select < 0 || q->kernel_select > 8) return fail(SBQA_ERR_INVALID_ARG, "kernel_select must be 0..8");
   if (q->n_runs > 0 && (!q->beta || !q->alpha)) return fail(SBQA_ERR_INVALID_ARG, "beta/alpha missing");
   std::vector<double> beta, alpha;
   if (q->n_runs > 0) {

@@ -97,7 +97,7 @@ struct sbqa_problem {
   cudaStream_t stream = nullptr;
   int kind = VAL_F32;  // sparse value kind in use
   int csr_variant = -1;  // CSR step kernel variant chosen by the autotuner (-1 = not yet)
-  float variant_ms[4] = {0.f, 0.f, 0.f, 0.f};
+  float variant_ms[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   bool use_persistent = false;  // autotuner: one cooperative launch for all steps
   float persistent_ms = 0.f;    // its timing per step
   int persist_blocks = 0;

@@ -18,7 +18,7 @@ namespace sbqa {
 
 constexpr int kPersistMaxDeg = 8;
 constexpr int kPersistW = 8;                   // columns per lane
-constexpr int kPersistMaxItems = 32;           // items per warp kept in shared memory
+constexpr int kPersistMaxItems = 120;  // items per warp in shared memory: 45 KB per block, under the 48 KB default
 constexpr unsigned kBarrierSpins = 1u << 24;  // polls per grid barrier (with backoff: seconds)
 
 struct PersistArgs {

@@ -15,6 +15,8 @@
 //   VAL_BF16  bfloat16 J, FP32 accumulation
 // Memory per update: x, y read + write (16 B) + F write (1 B); F gathers and
 // the CSR arrays are shared by all columns of a row and mostly hit in cache.
+#include <algorithm>
+
 #include "step_common.cuh"
 
 namespace sbqa {
@@ -58,22 +60,28 @@ struct FVec<16> {
 // f codes per neighbour (U neighbours at a time), accumulates and runs the
 // update.  The row's (col, J) entries are read 32 at a time, one per lane,
 // and broadcast by shuffle.
-template <int P, int KIND, int W>
+// GS = false: grid (ceil(N / 8), Cp / 32 W), one item per warp.  GS = true:
+// one wave of resident blocks; warp g takes items g, g + warps, ... in
+// row-major (row, chunk) order, so no block is launched per item.
+template <int P, int KIND, int W, bool GS>
 __global__ void __launch_bounds__(256, W == 16 ? 2 : (W == 8 ? 3 : 4))
     k_step_csr(StateView s, CsrView J, StepTables t, int n) {
   constexpr int U = W == 16 ? 4 : 8;  // gathers in flight per lane
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i = blockIdx.x * 8 + warp;
-  if (i >= s.N) return;  // whole warp
   const float ka = __ldg(t.ka + n), dnext = __ldg(t.dl + n + 1);
-  const float hi = __ldg(J.h + i);
-  const int e0 = __ldg(J.row_ptr + i), e1 = __ldg(J.row_ptr + i + 1);
-  const int ep = (KIND == VAL_PM1) ? e0 + __ldg(J.npos + i) : e1;
   const uint8_t *Fin = s.f_of(n);
   uint8_t *Fout = s.f_of(n + 1);
-  // chunk blockIdx.y of 32 W columns (one chunk per warp keeps many warps in flight)
-  {
-    const int cw = blockIdx.y * 32 * W;
+  const int chunks = s.Cp / (32 * W);
+  const long long n_items = GS ? (long long)s.N * chunks : 1;
+  const long long stride = GS ? (long long)gridDim.x * 8 : 1;
+  for (long long item = GS ? (long long)blockIdx.x * 8 + warp : 0; item < n_items; item += stride) {
+    const int i = GS ? int(item / chunks) : blockIdx.x * 8 + warp;
+    const int chunk = GS ? int(item - (long long)i * chunks) : blockIdx.y;
+    if (i >= s.N) return;  // whole warp (per-item grid only)
+    const float hi = __ldg(J.h + i);
+    const int e0 = __ldg(J.row_ptr + i), e1 = __ldg(J.row_ptr + i + 1);
+    const int ep = (KIND == VAL_PM1) ? e0 + __ldg(J.npos + i) : e1;
+    const int cw = chunk * 32 * W;
     const int c0 = cw + lane * W;
     float xs[W], ys[W];
     {
@@ -141,31 +149,57 @@ __global__ void __launch_bounds__(256, W == 16 ? 2 : (W == 8 ? 3 : 4))
   }
 }
 
-template <int P, int W>
-static cudaError_t launch_pw(const StateView &s, const CsrView &J, const StepTables &t, int n, cudaStream_t st) {
-  const dim3 blocks(unsigned((s.N + 7) / 8), unsigned(s.Cp / (32 * W)));
-  switch (J.kind) {
-    case VAL_PM1: k_step_csr<P, VAL_PM1, W><<<blocks, 256, 0, st>>>(s, J, t, n); break;
-    case VAL_F32: k_step_csr<P, VAL_F32, W><<<blocks, 256, 0, st>>>(s, J, t, n); break;
-    default: k_step_csr<P, VAL_BF16, W><<<blocks, 256, 0, st>>>(s, J, t, n); break;
+// One wave of resident blocks of kernel fn (cached per kernel).
+static unsigned wave_blocks(const void *fn) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+  return unsigned(sms * per_sm);
+}
+
+template <int P, int KIND, int W, bool GS>
+static cudaError_t launch_k(const StateView &s, const CsrView &J, const StepTables &t, int n, cudaStream_t st) {
+  if constexpr (GS) {
+    static const unsigned wave = wave_blocks((const void *)k_step_csr<P, KIND, W, true>);
+    const long long items = (long long)s.N * (s.Cp / (32 * W));
+    const unsigned blocks = unsigned(std::min<long long>(wave, (items + 7) / 8));
+    k_step_csr<P, KIND, W, true><<<blocks, 256, 0, st>>>(s, J, t, n);
+  } else {
+    const dim3 blocks(unsigned((s.N + 7) / 8), unsigned(s.Cp / (32 * W)));
+    k_step_csr<P, KIND, W, false><<<blocks, 256, 0, st>>>(s, J, t, n);
   }
   return cudaGetLastError();
+}
+
+template <int P, int W, bool GS>
+static cudaError_t launch_pw(const StateView &s, const CsrView &J, const StepTables &t, int n, cudaStream_t st) {
+  switch (J.kind) {
+    case VAL_PM1: return launch_k<P, VAL_PM1, W, GS>(s, J, t, n, st);
+    case VAL_F32: return launch_k<P, VAL_F32, W, GS>(s, J, t, n, st);
+    default: return launch_k<P, VAL_BF16, W, GS>(s, J, t, n, st);
+  }
 }
 
 template <int P>
 static cudaError_t launch_p(const StateView &s, const CsrView &J, const StepTables &t, int n, int variant,
                             cudaStream_t st) {
   switch (variant) {
-    case 2: return launch_pw<P, 16>(s, J, t, n, st);
-    case 1: return launch_pw<P, 8>(s, J, t, n, st);
-    default: return launch_pw<P, 4>(s, J, t, n, st);
+    case 5: return launch_pw<P, 16, true>(s, J, t, n, st);
+    case 4: return launch_pw<P, 8, true>(s, J, t, n, st);
+    case 3: return launch_pw<P, 4, true>(s, J, t, n, st);
+    case 2: return launch_pw<P, 16, false>(s, J, t, n, st);
+    case 1: return launch_pw<P, 8, false>(s, J, t, n, st);
+    default: return launch_pw<P, 4, false>(s, J, t, n, st);
   }
 }
 
-// Variants: W = 4, 8, 16 columns per lane; W needs Cp to be a multiple of 32 W.
-int csr_step_variants() { return 3; }
+// Variants 0-2: W = 4, 8, 16 columns per lane, one item per warp; 3-5: the
+// same widths with one wave of blocks looping over the items.  W needs Cp to
+// be a multiple of 32 W.
+int csr_step_variants() { return 6; }
 
-bool csr_step_variant_ok(int variant, int Cp) { return Cp % (32 * (4 << variant)) == 0; }
+bool csr_step_variant_ok(int variant, int Cp) { return Cp % (32 * (4 << (variant % 3))) == 0; }
 
 cudaError_t launch_step_csr(const StateView &s, const CsrView &J, const StepTables &t, int n, int variant,
                             cudaStream_t st) {

@@ -324,6 +324,38 @@ def test_small_one_launch_solver_matches_per_step_path(sb, N, P, R, S, jmax):
     _check_energies_and_best(sb, pb, prob, R, P)
 
 
+@pytest.mark.parametrize("case", ["lattice", "regular_f32", "regular_bf16", "ragged"])
+def test_csr_step_variants_bit_identical(sb, case):
+    """Every per-step CSR kernel variant (W = 4, 8, 16 columns per lane; one
+    item per warp or one wave of blocks looping over the items), forced with
+    kernel_select = 3 + v, gives the same state bit for bit after 40 steps."""
+    if case == "lattice":
+        pb, spec = lattice(8, 1); P, R, prec = 32, 16, "auto"
+    elif case == "regular_f32":
+        pb, spec = regular(700, 6, 3); P, R, prec = 16, 32, "fp32"
+    elif case == "regular_bf16":
+        pb, spec = regular(700, 5, 4); P, R, prec = 8, 64, "bf16"
+    else:
+        pb, spec = lattice(5, 2); P, R, prec = 32, 5, "auto"  # Cp = 256: W = 16 falls back
+    states = []
+    for v in range(6):
+        prob = create(sb, spec)
+        sb.set_schedule(prob, *workloads.autotune_params(R, 3), **_params(precision=prec, kernel_select=3 + v))
+        sb.run_begin(prob, 300, P, R, seed=11)
+        sb.run_advance(prob, 40)
+        info = prob.info()
+        assert info.step_kernel == 0
+        states.append(sb.get_state(prob)[:2])
+    for v in range(1, 6):
+        assert np.array_equal(states[0][0], states[v][0]) and np.array_equal(states[0][1], states[v][1]), v
+
+
+def test_csr_grid_stride_variant_against_oracle(sb):
+    pb, spec = regular(500, 6, 1)
+    wx, wy, _, _ = _per_step(sb, pb, spec, 16, 8, 300, 30, prec="fp32", kernel_select=3)
+    assert wx <= TOL_STEP and wy <= TOL_STEP
+
+
 @pytest.mark.parametrize("L,P,R", [(10, 16, 32), (8, 32, 8), (6, 8, 64)])
 def test_persistent_csr_solver_matches_per_step(sb, L, P, R):
     """The persistent CSR solver (one cooperative launch, grid barrier per
