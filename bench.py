@@ -373,6 +373,95 @@ def run_tte(args):
     return 0
 
 
+# ------------------------------------------------------------------ (alpha, beta) sensitivity
+SWEEP_BETA = [0.25, 0.5, 0.75, 1.0, 1.25, 1.5, 2.0, 3.0, 4.0, 6.0]
+SWEEP_ALPHA = [0.25, 0.5, 0.75, 1.0, 1.5, 2.0]
+
+
+def sweep_layout(alphas, betas, runs, reps):
+    """Per-run (beta, alpha) of one batched solve covering the whole grid:
+    run index r = ((ia * len(betas) + ib) * runs + q) * reps + t for grid
+    point (alphas[ia], betas[ib]), independent run q and repetition t."""
+    beta, alpha = [], []
+    for a in alphas:
+        for b in betas:
+            for _ in range(runs * reps):
+                beta.append(b)
+                alpha.append(a)
+    return np.array(beta), np.array(alpha)
+
+
+def sweep_table(best_energy, alphas, betas, runs, reps, E0):
+    """Mean optimality gap (Eq. 9) per grid point: a run's energy is the best
+    over its reps repetitions; g is averaged over the runs (the paper's
+    sensitivity study, Sec. II B)."""
+    e = np.asarray(best_energy, dtype=np.float64).reshape(len(alphas), len(betas), runs, reps).min(axis=3)
+    g = (e - E0) / abs(E0)
+    return g.mean(axis=2)
+
+
+def run_sweep(args):
+    """Heat maps of the mean optimality gap in the (alpha, beta) plane on
+    synthetic instances, with the auto-tuning rule (beta ~ U[0.5, 1.5],
+    alpha ~ U[0.5, 1.0] per repetition) beside the grid.  The whole grid of
+    one instance is one batched solve (per-run beta, alpha)."""
+    import math
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2604_01050_gb300 import build as _b
+    _b.build()
+    import paper_2604_01050_gb300 as sb
+    runs, reps, P = 10, 8, 32
+    out = {}
+    insts = {"sk512": ("dense SK N=512, J=+-1, h=0", 1000),
+             "lattice10": ("3D cubic lattice L=10 (N=1000), J=+-1, h=0", 2000)}
+    for name, (desc, S) in insts.items():
+        if name.startswith("sk"):
+            J, h = workloads.sk_pm1(512, 21)
+            prob = sb.create_problem_dense(J, h)
+        else:
+            n, rp, col, val, hh = workloads.cubic_lattice(10, 21)
+            prob = sb.create_problem_csr(n, rp, col, val, hh)
+        beta, alpha = sweep_layout(SWEEP_ALPHA, SWEEP_BETA, runs, reps)
+        R = len(beta)
+        t0 = time.perf_counter()
+        sb.set_schedule(prob, beta, alpha, gamma0=args.gamma0)
+        sb.run(prob, S, P, R, seed=31)
+        grid_best = sb.get_best(prob)["energy"]
+        t_grid = time.perf_counter() - t0
+        ab, aa = workloads.autotune_params(runs * reps, 32)
+        sb.set_schedule(prob, ab, aa, gamma0=args.gamma0)
+        sb.run(prob, S, P, runs * reps, seed=32)
+        auto_best = sb.get_best(prob)["energy"]
+        # control: the same runs with the replica coupling off (plain SB per replica)
+        sb.set_schedule(prob, ab, aa, gamma0=args.gamma0, jperp_enable=0)
+        sb.run(prob, S, P, runs * reps, seed=32)
+        sb_best = sb.get_best(prob)["energy"]
+        # reference energy: the best of everything found plus long auto-tuned searches
+        E0 = min(float(grid_best.min()), float(auto_best.min()), float(sb_best.min()))
+        for sd in range(4):
+            sb.run(prob, 10 * S, P, runs * reps, seed=40 + sd)
+            E0 = min(E0, float(sb.get_best(prob)["energy"].min()))
+        g = sweep_table(grid_best, SWEEP_ALPHA, SWEEP_BETA, runs, reps, E0)
+        g_auto = float(((auto_best.reshape(runs, reps).min(axis=1) - E0) / abs(E0)).mean())
+        g_sb = float(((sb_best.reshape(runs, reps).min(axis=1) - E0) / abs(E0)).mean())
+        gmin = float(g.min())
+        ia, ib = np.unravel_index(int(np.argmin(g)), g.shape)
+        out[name] = {"instance": desc, "steps": S, "P": P, "runs": runs, "repetitions": reps,
+                     "E0": E0, "E0_source": "best over the sweep and 4 x %d auto-tuned runs of %d steps"
+                                           % (runs * reps, 10 * S),
+                     "alpha": SWEEP_ALPHA, "beta": SWEEP_BETA, "g_mean": [[round(float(v), 5) for v in row] for row in g],
+                     "g_min": gmin, "argmin": {"alpha": SWEEP_ALPHA[ia], "beta": SWEEP_BETA[ib]},
+                     "within_35pct_of_best": [[bool(v <= 1.35 * gmin) for v in row] for row in g],
+                     "g_fixed_alpha1_beta1": float(g[SWEEP_ALPHA.index(1.0), SWEEP_BETA.index(1.0)]),
+                     "g_auto_tuned": g_auto, "g_plain_sb_jperp0": g_sb, "grid_solve_s": t_grid,
+                     "grid_updates": int(prob.n) * P * R * S}
+        prob.destroy()
+    print(json.dumps({"metric": "optimality gap g (Eq. 9), mean over runs", "mode": "sweep", "unit": "1",
+                      "n_gpus": 1, "gamma0": args.gamma0, "data": "synthetic", "instances": out}))
+    return 0
+
+
 # ------------------------------------------------------------------ large-N scaling
 def run_scaling(args):
     """Runs the sparse family one size at a time (each in its own process,
@@ -408,7 +497,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default=DEFAULT, choices=sorted(CONFIGS) + ["serving", "tte", "scaling"])
+    ap.add_argument("--config", default=DEFAULT, choices=sorted(CONFIGS) + ["serving", "tte", "scaling", "sweep"])
     ap.add_argument("--variant", default="threshold", choices=["threshold", "ballistic"],
                     help="f of Eq. 8 (SBQA) or f(x) = x (the bSB form)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -425,6 +514,8 @@ def main():
         return run_tte(args)
     if args.config == "scaling":
         return run_scaling(args)
+    if args.config == "sweep":
+        return run_sweep(args)
     cfg = dict(CONFIGS[args.config])
     if args.variant == "ballistic":
         cfg["variant"] = "ballistic"

@@ -312,6 +312,44 @@ cudaError_t issue_step(sbqa_problem *p, int n, cudaStream_t st) {
   return launch_step_csr(s, p->csr(), p->tables, n, p->csr_variant < 0 ? 0 : p->csr_variant, st);
 }
 
+// Device time per launch of `reps` launches issued by issue(stream), replayed
+// as one CUDA graph (as a solve replays its step launches), so launch
+// overhead on the host does not bias the comparison with the persistent
+// solvers.  One untimed replay first.
+template <class Issue>
+static int time_per_launch_in_graph(sbqa_problem *p, int reps, Issue issue, float *ms_per_launch) {
+  if (!p->cap_stream) SBQA_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+  cudaGraph_t graph = nullptr;
+  SBQA_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (int w = 0; w < reps && e == cudaSuccess; ++w) e = issue(p->cap_stream);
+  const cudaError_t e2 = cudaStreamEndCapture(p->cap_stream, &graph);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(SBQA_ERR_CUDA, std::string("autotuner capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(SBQA_ERR_CUDA, std::string("autotuner instantiate: ") + cudaGetErrorString(e));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  float ms = 0.f;
+  e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, p->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(e0, p->stream);
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, p->stream);
+  if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
+  if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaGraphExecDestroy(exec);
+  if (e != cudaSuccess) return fail(SBQA_ERR_CUDA, std::string("autotuner timing: ") + cudaGetErrorString(e));
+  *ms_per_launch = ms / reps;
+  return SBQA_OK;
+}
+
 // Autotuner of the CSR step kernel: times every variant on this problem's
 // shape (a few launches each, on the freshly allocated state buffers, before
 // the initial state is written) and keeps the fastest.  Results are cached
@@ -341,28 +379,26 @@ int autotune_csr(sbqa_problem *p) {
   const StateView s = p->state();
   const CsrView J = p->csr();
   const int nv = csr_step_variants(), reps = 8;
-  cudaEvent_t e0, e1;
-  SBQA_CUDA(cudaEventCreate(&e0));
-  SBQA_CUDA(cudaEventCreate(&e1));
   float best_ms = 1e30f;
   int best = 0;
   const int n = 0;
   for (int v = 0; v < nv && p->S > 0; ++v) {
     if (!csr_step_variant_ok(v, p->Cp)) continue;
-    for (int w = 0; w < 2; ++w) SBQA_CUDA(launch_step_csr(s, J, p->tables, n, v, p->stream));
-    SBQA_CUDA(cudaEventRecord(e0, p->stream));
-    for (int w = 0; w < reps; ++w) SBQA_CUDA(launch_step_csr(s, J, p->tables, n, v, p->stream));
-    SBQA_CUDA(cudaEventRecord(e1, p->stream));
-    SBQA_CUDA(cudaEventSynchronize(e1));
     float ms = 0.f;
-    SBQA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-    if (v < 6) p->variant_ms[v] = ms / reps;
+    const int rc = time_per_launch_in_graph(
+        p, reps, [&](cudaStream_t st) { return launch_step_csr(s, J, p->tables, n, v, st); }, &ms);
+    if (rc != SBQA_OK) return rc;
+    if (v < 6) p->variant_ms[v] = ms;
+    ms *= reps;
     if (ms < best_ms) {
       best_ms = ms;
       best = v;
     }
   }
   // the persistent kernel: a few steps in one cooperative launch
+  cudaEvent_t e0, e1;
+  SBQA_CUDA(cudaEventCreate(&e0));
+  SBQA_CUDA(cudaEventCreate(&e1));
   p->use_persistent = false;
   p->persistent_ms = 0.f;
   if (p->persist_blocks == 0) p->persist_blocks = persistent_blocks();
@@ -371,7 +407,7 @@ int autotune_csr(sbqa_problem *p) {
     p->use_persistent = true;
   } else if (p->prm.kernel_select == 0 && p->S > 0 && p->persistent_ok()) {
     SBQA_CUDA(p->d_bar.alloc(1));
-    const int steps = std::min(p->S, 24);
+    const int steps = std::min(p->S, 64);
     SBQA_CUDA(launch_solve_csr_persistent(s, J, p->tables, 0, std::min(p->S, 4), p->d_bar.p, p->d_err.p,
                                           p->persist_blocks, p->stream));
     SBQA_CUDA(cudaEventRecord(e0, p->stream));
@@ -418,19 +454,20 @@ int autotune_tc(sbqa_problem *p) {
       cudaEvent_t e0, e1;
       SBQA_CUDA(cudaEventCreate(&e0));
       SBQA_CUDA(cudaEventCreate(&e1));
-      const int reps = 8, steps = std::min(p->S, 24);
+      const int reps = 8, steps = std::min(p->S, 64);
       float ms = 0.f;
-      for (int w = 0; w < 2; ++w)
-        SBQA_CUDA(launch_step_dense_tc(p->tc_plan, s, p->Kp, p->d_FT.p, p->d_err.p, p->d_h.p, p->tables, 0,
-                                       p->stream));
-      SBQA_CUDA(cudaEventRecord(e0, p->stream));
-      for (int w = 0; w < reps; ++w)
-        SBQA_CUDA(launch_step_dense_tc(p->tc_plan, s, p->Kp, p->d_FT.p, p->d_err.p, p->d_h.p, p->tables, 0,
-                                       p->stream));
-      SBQA_CUDA(cudaEventRecord(e1, p->stream));
-      SBQA_CUDA(cudaEventSynchronize(e1));
-      SBQA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      p->tc_step_ms = ms / reps;
+      const int rc = time_per_launch_in_graph(
+          p, reps,
+          [&](cudaStream_t st) {
+            return launch_step_dense_tc(p->tc_plan, s, p->Kp, p->d_FT.p, p->d_err.p, p->d_h.p, p->tables, 0, st);
+          },
+          &ms);
+      if (rc != SBQA_OK) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return rc;
+      }
+      p->tc_step_ms = ms;
       SBQA_CUDA(launch_solve_dense_tc_persistent(p->tc_plan, s, p->Kp, p->d_err.p, p->d_h.p, p->tables, 0,
                                                  std::min(p->S, 4), p->d_tc_flags.p, p->stream));
       SBQA_CUDA(cudaEventRecord(e0, p->stream));

@@ -419,6 +419,27 @@ def test_full_run_sk64_energies_exact(sb):
     assert np.all(best["step"] == 999)
 
 
+def test_per_run_schedule_only_affects_its_run(sb):
+    """The (alpha, beta) study batches a whole grid in one solve: run r's
+    result depends only on its own (beta_r, alpha_r) and seed, bit for bit,
+    whatever the other runs' parameters are."""
+    pb, spec = lattice(6, 5)
+    P, R, S = 16, 12, 200
+    b1, a1 = workloads.autotune_params(R, 1)
+    b2, a2 = workloads.autotune_params(R, 2)
+    keep = np.arange(R) % 3 == 0
+    b2[keep], a2[keep] = b1[keep], a1[keep]
+    out = []
+    for beta, alpha in ((b1, a1), (b2, a2)):
+        prob = create(sb, spec)
+        sb.set_schedule(prob, beta, alpha, **_params(gamma0=8.0))
+        sb.run(prob, S, P, R, seed=5)
+        out.append((sb.get_state(prob)[0], sb.get_best(prob)))
+    assert np.array_equal(out[0][0][keep], out[1][0][keep])
+    assert np.array_equal(out[0][1]["energy"][keep], out[1][1]["energy"][keep])
+    assert not np.array_equal(out[0][0][~keep], out[1][0][~keep])
+
+
 # ---------------------------------------------------------------- ballistic form f(x) = x
 @pytest.mark.parametrize("case", ["lattice_pm1", "regular_f32_field", "dense_real", "dense_int", "ragged"])
 def test_ballistic_per_step(sb, case):
