@@ -403,10 +403,10 @@ int autotune_csr(sbqa_problem *p) {
   p->persistent_ms = 0.f;
   if (p->persist_blocks == 0) p->persist_blocks = persistent_blocks();
   if (p->prm.kernel_select == 2 && p->S > 0 && p->persistent_ok()) {
-    SBQA_CUDA(p->d_bar.alloc(1));
+    SBQA_CUDA(p->d_bar.alloc(persistent_barrier_words()));
     p->use_persistent = true;
   } else if (p->prm.kernel_select == 0 && p->S > 0 && p->persistent_ok()) {
-    SBQA_CUDA(p->d_bar.alloc(1));
+    SBQA_CUDA(p->d_bar.alloc(persistent_barrier_words()));
     const int steps = std::min(p->S, 64);
     SBQA_CUDA(launch_solve_csr_persistent(s, J, p->tables, 0, std::min(p->S, 4), p->d_bar.p, p->d_err.p,
                                           p->persist_blocks, p->stream));

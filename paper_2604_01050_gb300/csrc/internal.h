@@ -88,6 +88,7 @@ int set_error(int code, const std::string &msg);
 // All steps of a +-1 CSR run batch in one cooperative launch with a bounded
 // grid barrier between steps (solve_persistent.cu).
 int persistent_blocks();
+int persistent_barrier_words();  // size of the barrier counter buffer
 bool persistent_eligible(int N, int Cp, int max_degree, int blocks);
 cudaError_t launch_solve_csr_persistent(const StateView &s, const CsrView &J, const StepTables &t, int n_begin,
                                         int n_end, unsigned *bar, int *err, int blocks, cudaStream_t st);

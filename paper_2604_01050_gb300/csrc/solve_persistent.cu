@@ -20,6 +20,11 @@ constexpr int kPersistMaxDeg = 8;
 constexpr int kPersistW = 8;                   // columns per lane
 constexpr int kPersistMaxItems = 120;  // items per warp in shared memory: 45 KB per block, under the 48 KB default
 constexpr unsigned kBarrierSpins = 1u << 24;  // polls per grid barrier (with backoff: seconds)
+// Two-level grid barrier: blocks arrive on one of kBarGroups group counters
+// (each on its own 128-byte line); the last arrival of a group adds one to
+// the global counter, which every block polls.  Counter words: global at 0,
+// group g at kBarStride * (g + 1).
+constexpr unsigned kBarGroups = 32, kBarStride = 32;
 
 struct PersistArgs {
   StateView s;
@@ -27,7 +32,7 @@ struct PersistArgs {
   const float *h;
   StepTables t;
   int n_begin, n_end;
-  unsigned *bar;  // grid barrier counter (zeroed by the host before the launch)
+  unsigned *bar;  // grid barrier counters (persistent_barrier_words(), zeroed before the launch)
   int *err;       // error flag
 };
 
@@ -36,18 +41,31 @@ struct ItemIdx {
   int32_t row, chunk, deg, npos;
 };
 
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned target, int *err) {
+// Barrier number k (1, 2, ...) of the launch.  Writes of every block before
+// it are visible to every block after it: a block's fence + group atomic is
+// a release, the group's last arrival (atomic, fence) acquires them and
+// releases them again with its fence + global atomic, and the poll is an
+// acquire load.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned k, int *err) {
   __syncthreads();
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
+    const unsigned G = gridDim.x < kBarGroups ? gridDim.x : kBarGroups;
+    const unsigned g = blockIdx.x % G;
+    const unsigned size_g = (gridDim.x - g + G - 1) / G;  // blocks b with b % G == g
     __threadfence();
-    atomicAdd(bar, 1u);
+    const unsigned old = atomicAdd(bar + kBarStride * (g + 1), 1u);
+    if (old + 1 == size_g * k) {  // last arrival of the group
+      __threadfence();
+      atomicAdd(bar, 1u);
+    }
+    const unsigned target = G * k;
     unsigned v = 0;
     unsigned it = 0;
     for (; it < kBarrierSpins; ++it) {
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
       if (v >= target) break;
-      if (it > 64) __nanosleep(64);
+      __nanosleep(it < 64 ? 32 : 128);
     }
     s_ok = it < kBarrierSpins;
     if (!s_ok) atomicCAS(err, 0, 4);
@@ -80,7 +98,7 @@ __global__ void __launch_bounds__(256, 4) k_solve_csr_persistent(PersistArgs a) 
     }
   }
   __syncwarp();
-  unsigned target = 0;
+  unsigned k = 0;
   for (int n = a.n_begin; n < a.n_end; ++n) {
     const uint8_t *Fin = s.f_of(n);
     uint8_t *Fout = s.f_of(n + 1);
@@ -123,10 +141,11 @@ __global__ void __launch_bounds__(256, 4) k_solve_csr_persistent(PersistArgs a) 
       }
       sb_updateW<P, kPersistW>(s, a.t, ka, dnext, n, i, c0, G, __ldg(a.h + i), xs, ys, Fout);
     }
-    target += gridDim.x;
-    if (!grid_barrier(a.bar, target, a.err)) break;
+    if (!grid_barrier(a.bar, ++k, a.err)) break;
   }
 }
+
+int persistent_barrier_words() { return int(kBarStride * (kBarGroups + 1)); }
 
 int persistent_blocks() {
   int dev = 0, sms = 0, per_sm = 0;
@@ -167,7 +186,7 @@ cudaError_t launch_solve_csr_persistent(const StateView &s, const CsrView &J, co
   a.err = err;
   void *args[] = {&a};
   const size_t smem = 8 * kPersistMaxItems * sizeof(ItemIdx);
-  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
+  cudaError_t e = cudaMemsetAsync(bar, 0, persistent_barrier_words() * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   const void *fn;
   switch (s.P) {
