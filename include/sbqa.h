@@ -117,11 +117,13 @@ typedef struct {
                              and 7 dense CUDA cores for the ballistic form
                              f(x) = x; -1 none                             */
     int32_t step_variant; /* CSR kernel variant picked by the autotuner:
-                             4 << (v % 3) consecutive replica columns per
-                             lane; v >= 3: one wave of blocks looping over
-                             the (row, column chunk) items; -1 before the
-                             first run                                    */
-    float variant_ms[6];  /* autotuner timing of each CSR variant (ms per
+                             0-5: 4 << (v % 3) consecutive replica columns
+                             per lane, v >= 3 with one wave of blocks
+                             looping over the (row, column chunk) items;
+                             6, 7: the ELL form of rows of degree <= 8 (4
+                             or 8 columns per lane); -1 before the first
+                             run                                          */
+    float variant_ms[8];  /* autotuner timing of each CSR variant (ms per
                              step; 0 = not timed / not eligible); for the
                              dense tcgen05 path [0] is the per-step kernel */
     float persistent_ms;  /* autotuner timing of the persistent solver of
@@ -157,7 +159,7 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info);
  *                qualifies, else per-step.  CSR qualifies with +-1 J,
  *                degree <= 8 and R*P a multiple of 256; the dense tensor-core
  *                path when its 128 x 128 tiles (padded N x padded R*P) fit
- *                the device at once (one per SM).  3 + v (v = 0..5) forces
+ *                the device at once (one per SM).  3 + v (v = 0..7) forces
  *                per-step CSR kernel variant v (see step_variant).  Results
  *                are identical whichever kernel runs.
  *   beta, alpha  host, n_runs doubles each: per-run inverse temperature and

@@ -55,7 +55,7 @@ class ProblemInfo(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("is_dense", ctypes.c_int32), ("nnz", ctypes.c_int64),
                 ("is_integer", ctypes.c_int32), ("max_abs_j", ctypes.c_int32),
                 ("c0_auto", ctypes.c_double), ("step_kernel", ctypes.c_int32),
-                ("step_variant", ctypes.c_int32), ("variant_ms", ctypes.c_float * 6),
+                ("step_variant", ctypes.c_int32), ("variant_ms", ctypes.c_float * 8),
                 ("persistent_ms", ctypes.c_float)]
 
 

@@ -64,7 +64,8 @@ sbqa_problem::~sbqa_problem() {
   d_row_ptr.release(); d_col.release(); d_col_pm1.release(); d_npos.release(); d_val_f32.release();
   d_val_bf16.release(); d_dense_f32.release(); d_h.release(); d_e_i32.release();
   d_e_f64.release(); d_h_i64.release(); d_h_f64.release(); d_x.release(); d_y.release();
-  d_F0.release(); d_F1.release(); d_Fx0.release(); d_Fx1.release(); d_Sg.release(); d_ka.release(); d_dl.release();
+  d_F0.release(); d_F1.release(); d_Fx0.release(); d_Fx1.release(); d_Sg.release();
+  d_ell_col.release(); d_ell_meta.release(); d_ell_val.release(); d_ka.release(); d_dl.release();
   d_kj.release(); d_ei.release(); d_part_i.release(); d_best_ei.release(); d_ef.release();
   d_part_f.release(); d_best_e.release(); d_best_k.release(); d_best_step.release();
   d_have.release(); d_best_spins.release(); d_bar.release(); d_tc_flags.release();
@@ -190,6 +191,49 @@ int prepare_sparse_values(sbqa_problem *p, int precision) {
     for (size_t e = 0; e < m; ++e) v[e] = bf16_bits_rne(p->val[e]);
     SBQA_CUDA(p->d_val_bf16.alloc(m));
     SBQA_CUDA(cudaMemcpy(p->d_val_bf16.p, v.data(), m * 2, cudaMemcpyHostToDevice));
+  }
+  if (p->max_degree <= kEllSlots && p->ell_kind != kind && p->n > 0) {
+    // ELL slots: each row's entries in the order the CSR kernels sum them
+    // (+1 entries first for +-1 J), values as the kernels see them (FP32, or
+    // BF16 widened exactly), zero padding; (degree, +1 count) per row
+    const int N = p->n;
+    std::vector<int32_t> ec(size_t(N) * kEllSlots, 0), meta(size_t(N) * 2, 0);
+    std::vector<float> ev(kind == VAL_PM1 ? 0 : size_t(N) * kEllSlots, 0.f);
+    for (int i = 0; i < N; ++i) {
+      const int64_t e0 = p->row_ptr[i], e1 = p->row_ptr[i + 1];
+      int w = 0, npos = 0;
+      if (kind == VAL_PM1) {
+        for (int64_t e = e0; e < e1; ++e)
+          if (p->val[e] > 0) ec[size_t(i) * kEllSlots + w++] = p->col[e];
+        npos = w;
+        for (int64_t e = e0; e < e1; ++e)
+          if (p->val[e] < 0) ec[size_t(i) * kEllSlots + w++] = p->col[e];
+      } else {
+        for (int64_t e = e0; e < e1; ++e, ++w) {
+          ec[size_t(i) * kEllSlots + w] = p->col[e];
+          float v;
+          if (kind == VAL_BF16) {
+            const uint32_t bits = uint32_t(bf16_bits_rne(p->val[e])) << 16;
+            std::memcpy(&v, &bits, sizeof(v));
+          } else {
+            v = float(p->val[e]);
+          }
+          ev[size_t(i) * kEllSlots + w] = v;
+        }
+        npos = w;
+      }
+      meta[2 * size_t(i)] = w;
+      meta[2 * size_t(i) + 1] = npos;
+    }
+    SBQA_CUDA(p->d_ell_col.alloc(ec.size()));
+    SBQA_CUDA(cudaMemcpy(p->d_ell_col.p, ec.data(), ec.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    SBQA_CUDA(p->d_ell_meta.alloc(meta.size()));
+    SBQA_CUDA(cudaMemcpy(p->d_ell_meta.p, meta.data(), meta.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (!ev.empty()) {
+      SBQA_CUDA(p->d_ell_val.alloc(ev.size()));
+      SBQA_CUDA(cudaMemcpy(p->d_ell_val.p, ev.data(), ev.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    p->ell_kind = kind;
   }
   return SBQA_OK;
 }
@@ -365,9 +409,9 @@ int autotune_csr(sbqa_problem *p) {
       p->csr_variant_select == p->prm.kernel_select)
     return SBQA_OK;
   p->csr_variant_select = p->prm.kernel_select;
-  if (p->prm.kernel_select >= 3) {  // a forced per-step variant
+  if (p->prm.kernel_select >= 3 && p->prm.kernel_select <= 10) {  // a forced per-step variant
     const int v = p->prm.kernel_select - 3;
-    p->csr_variant = csr_step_variant_ok(v, p->Cp) ? v : 0;
+    p->csr_variant = csr_step_variant_ok(v, p->Cp, p->csr().ell_col != nullptr) ? v : 0;
     p->csr_variant_cp = p->Cp;
     p->csr_variant_kind = p->kind;
     p->use_persistent = false;
@@ -383,12 +427,12 @@ int autotune_csr(sbqa_problem *p) {
   int best = 0;
   const int n = 0;
   for (int v = 0; v < nv && p->S > 0; ++v) {
-    if (!csr_step_variant_ok(v, p->Cp)) continue;
+    if (!csr_step_variant_ok(v, p->Cp, J.ell_col != nullptr)) continue;
     float ms = 0.f;
     const int rc = time_per_launch_in_graph(
         p, reps, [&](cudaStream_t st) { return launch_step_csr(s, J, p->tables, n, v, st); }, &ms);
     if (rc != SBQA_OK) return rc;
-    if (v < 6) p->variant_ms[v] = ms;
+    if (v < 8) p->variant_ms[v] = ms;
     ms *= reps;
     if (ms < best_ms) {
       best_ms = ms;
@@ -762,7 +806,7 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info) {
                                                                : (p->dense ? 1 : (p->use_persistent ? 4 : 0))));
   info->persistent_ms = p->use_tc ? p->tc_persistent_ms : p->persistent_ms;
   info->step_variant = p->dense ? -1 : p->csr_variant;
-  for (int v = 0; v < 6; ++v) info->variant_ms[v] = p->use_tc ? (v == 0 ? p->tc_step_ms : 0.f) : p->variant_ms[v];
+  for (int v = 0; v < 8; ++v) info->variant_ms[v] = p->use_tc ? (v == 0 ? p->tc_step_ms : 0.f) : p->variant_ms[v];
   return SBQA_OK;
 }
 
@@ -778,7 +822,7 @@ int sbqa_set_schedule(sbqa_problem *p, const sbqa_params *q) {
   if (q->precision == SBQA_PREC_EXACT && (!p->j_integer || p->max_abs_j > 16))
     return fail(SBQA_ERR_UNSUPPORTED, "EXACT precision needs integer J with |J_ij| <= 16");
   if (q->eval_every < 0 || q->n_runs < 0) return fail(SBQA_ERR_INVALID_ARG, "negative eval_every or n_runs");
-  if (q->kernel_select < 0 || q->kernel_select > 8) return fail(SBQA_ERR_INVALID_ARG, "kernel_select must be 0..8");
+  if (q->kernel_select < 0 || q->kernel_select > 10) return fail(SBQA_ERR_INVALID_ARG, "kernel_select must be 0..10");
   if (q->n_runs > 0 && (!q->beta || !q->alpha)) return fail(SBQA_ERR_INVALID_ARG, "beta/alpha missing");
   std::vector<double> beta, alpha;
   if (q->n_runs > 0) {

@@ -50,7 +50,15 @@ struct CsrView {
   const int32_t *npos;     // VAL_PM1: number of +1 entries of each row
   const float *h;          // [N], never null (zeros when h = 0)
   int kind;
+  // ELL form of rows with degree <= kEllSlots (null when not built): slots
+  // [N][kEllSlots] of columns and values (the CSR kernel's entry order, zero
+  // padded) and (degree, +1 count) per row
+  const int32_t *ell_col;
+  const float *ell_val;
+  const int32_t *ell_meta;
 };
+
+constexpr int kEllSlots = 8;
 
 struct DenseView {
   const float *J;  // [N][N] row-major, FP32 (exact for integers)
@@ -160,7 +168,7 @@ cudaError_t launch_refresh_f(const StateView &s, int which, float delta, cudaStr
 // variant v: 4 << v consecutive columns per lane (picked per problem shape by
 // the autotuner in api.cu); valid when Cp is a multiple of 32 * (4 << v).
 int csr_step_variants();
-bool csr_step_variant_ok(int variant, int Cp);
+bool csr_step_variant_ok(int variant, int Cp, bool has_ell);
 cudaError_t launch_step_csr(const StateView &s, const CsrView &J, const StepTables &t,
                             int n, int variant, cudaStream_t st);
 cudaError_t launch_step_dense(const StateView &s, const DenseView &J, const StepTables &t,

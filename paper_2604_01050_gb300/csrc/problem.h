@@ -97,7 +97,7 @@ struct sbqa_problem {
   cudaStream_t stream = nullptr;
   int kind = VAL_F32;  // sparse value kind in use
   int csr_variant = -1;  // CSR step kernel variant chosen by the autotuner (-1 = not yet)
-  float variant_ms[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  float variant_ms[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
   bool use_persistent = false;  // autotuner: one cooperative launch for all steps
   float persistent_ms = 0.f;    // its timing per step
   int persist_blocks = 0;
@@ -111,6 +111,10 @@ struct sbqa_problem {
   sbqa::DevBuf<uint32_t> d_tc_flags;  // per-tile step counters of the persistent solver
   sbqa::DevBuf<float> d_x, d_y;
   sbqa::DevBuf<uint8_t> d_F0, d_F1;
+  // ELL slots of rows with degree <= 8 (built for value kind ell_kind)
+  sbqa::DevBuf<int32_t> d_ell_col, d_ell_meta;
+  sbqa::DevBuf<float> d_ell_val;
+  int ell_kind = -1;
   sbqa::DevBuf<float> d_Fx0, d_Fx1;  // f(x) = x buffers of the ballistic form
   sbqa::DevBuf<int8_t> d_Sg;
   sbqa::DevBuf<float> d_ka, d_dl, d_kj;
@@ -168,6 +172,10 @@ struct sbqa_problem {
     v.col = kind == VAL_PM1 ? d_col_pm1.p : d_col.p;
     v.val = kind == VAL_F32 ? static_cast<const void *>(d_val_f32.p)
                             : static_cast<const void *>(d_val_bf16.p);
+    const bool ell = ell_kind == kind && d_ell_col.p;
+    v.ell_col = ell ? d_ell_col.p : nullptr;
+    v.ell_val = ell ? d_ell_val.p : nullptr;
+    v.ell_meta = ell ? d_ell_meta.p : nullptr;
     return v;
   }
   EnergyView energy() const {

@@ -149,6 +149,108 @@ __global__ void __launch_bounds__(256, W == 16 ? 2 : (W == 8 ? 3 : 4))
   }
 }
 
+// ELL form for rows of degree <= 8 (variants 6, 7): each row's entries sit
+// in 8 slots (column, value; +1 entries first for +-1 J) with (degree, +1
+// count), so one load gives a row's neighbours.  One wave of blocks loops over
+// the (row, chunk) items; while a warp gathers and updates one item it has
+// already issued the next item's slots and x, y, so each item waits for one
+// round of gathers only.  Entries are summed in the CSR kernel's order.
+template <int P, int KIND, int W>
+__global__ void __launch_bounds__(256, W == 8 ? 3 : 4) k_step_ell(StateView s, CsrView J, StepTables t, int n) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float ka = __ldg(t.ka + n), dnext = __ldg(t.dl + n + 1);
+  const uint8_t *Fin = s.f_of(n);
+  uint8_t *Fout = s.f_of(n + 1);
+  const int chunks = s.Cp / (32 * W);
+  const long long n_items = (long long)s.N * chunks;
+  const long long stride = (long long)gridDim.x * 8;
+  long long item = (long long)blockIdx.x * 8 + warp;
+  if (item >= n_items) return;  // whole warp
+  int ni = int(item / chunks), nch = int(item - (long long)ni * chunks);
+  int ncol = 0;
+  float nval = 0.f;
+  int2 nmeta;
+  float nxs[W], nys[W];
+  auto fetch = [&](int row, int ch) {
+    if (lane < kEllSlots) {
+      ncol = __ldg(J.ell_col + size_t(row) * kEllSlots + lane);
+      if constexpr (KIND != VAL_PM1) nval = __ldg(J.ell_val + size_t(row) * kEllSlots + lane);
+    }
+    nmeta = __ldg(reinterpret_cast<const int2 *>(J.ell_meta) + row);
+    const size_t off = size_t(row) * s.Cp + ch * 32 * W + lane * W;
+#pragma unroll
+    for (int q = 0; q < W / 4; ++q) {
+      const float4 a = *reinterpret_cast<const float4 *>(s.x + off + 4 * q);
+      const float4 b = *reinterpret_cast<const float4 *>(s.y + off + 4 * q);
+      nxs[4 * q] = a.x; nxs[4 * q + 1] = a.y; nxs[4 * q + 2] = a.z; nxs[4 * q + 3] = a.w;
+      nys[4 * q] = b.x; nys[4 * q + 1] = b.y; nys[4 * q + 2] = b.z; nys[4 * q + 3] = b.w;
+    }
+  };
+  fetch(ni, nch);
+  for (; item < n_items; item += stride) {
+    const int i = ni, ch = nch;
+    const int my_col = ncol;
+    const float my_w = nval;
+    const int deg = nmeta.x, npos = nmeta.y;
+    float xs[W], ys[W];
+#pragma unroll
+    for (int q = 0; q < W; ++q) {
+      xs[q] = nxs[q];
+      ys[q] = nys[q];
+    }
+    const long long next = item + stride;
+    if (next < n_items) {  // warp-uniform
+      ni = int(next / chunks);
+      nch = int(next - (long long)ni * chunks);
+      fetch(ni, nch);
+    }
+    const int c0 = ch * 32 * W + lane * W;
+    const uint8_t *Fc = Fin + c0;
+    FVec<W> f[kEllSlots];
+#pragma unroll
+    for (int e = 0; e < kEllSlots; ++e) {
+      const int j = __shfl_sync(0xffffffffu, my_col, e);
+      if (e < deg) f[e].load(Fc + size_t(j) * s.Cp);
+      else f[e].zero(KIND == VAL_PM1 ? 0u : kFZero4);
+    }
+    float G[W];
+    if constexpr (KIND == VAL_PM1) {
+      uint32_t ap[W / 4], am[W / 4];
+#pragma unroll
+      for (int q = 0; q < W / 4; ++q) ap[q] = am[q] = 0;
+#pragma unroll
+      for (int e = 0; e < kEllSlots; ++e) {
+        if (e < npos) {
+#pragma unroll
+          for (int q = 0; q < W / 4; ++q) ap[q] += f[e].w[q];
+        } else {
+#pragma unroll
+          for (int q = 0; q < W / 4; ++q) am[q] += f[e].w[q];
+        }
+      }
+      const int bias = (deg - npos) - npos;  // codes carry f + 1; padding slots hold 0
+#pragma unroll
+      for (int c = 0; c < W; ++c)
+        G[c] = float(int((ap[c / 4] >> (8 * (c % 4))) & 0xffu) - int((am[c / 4] >> (8 * (c % 4))) & 0xffu) + bias);
+    } else {
+      float g[W];
+#pragma unroll
+      for (int c = 0; c < W; ++c) g[c] = 0.f;
+#pragma unroll
+      for (int e = 0; e < kEllSlots; ++e) {
+        const float wt = __shfl_sync(0xffffffffu, my_w, e);
+        if (e < deg) {  // the CSR kernel's entries, in its order
+#pragma unroll
+          for (int c = 0; c < W; ++c) g[c] = fmaf(wt, fdec(f[e].w[c / 4], c % 4), g[c]);
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < W; ++c) G[c] = g[c];
+    }
+    sb_updateW<P, W>(s, t, ka, dnext, n, i, c0, G, __ldg(J.h + i), xs, ys, Fout);
+  }
+}
+
 // One wave of resident blocks of kernel fn (cached per kernel).
 static unsigned wave_blocks(const void *fn) {
   int dev = 0, sms = 0, per_sm = 0;
@@ -156,6 +258,24 @@ static unsigned wave_blocks(const void *fn) {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
   return unsigned(sms * per_sm);
+}
+
+template <int P, int KIND, int W>
+static cudaError_t launch_ell(const StateView &s, const CsrView &J, const StepTables &t, int n, cudaStream_t st) {
+  static const unsigned wave = wave_blocks((const void *)k_step_ell<P, KIND, W>);
+  const long long items = (long long)s.N * (s.Cp / (32 * W));
+  const unsigned blocks = unsigned(std::min<long long>(wave, (items + 7) / 8));
+  k_step_ell<P, KIND, W><<<blocks, 256, 0, st>>>(s, J, t, n);
+  return cudaGetLastError();
+}
+
+template <int P, int W>
+static cudaError_t launch_pw_ell(const StateView &s, const CsrView &J, const StepTables &t, int n, cudaStream_t st) {
+  switch (J.kind) {
+    case VAL_PM1: return launch_ell<P, VAL_PM1, W>(s, J, t, n, st);
+    case VAL_F32: return launch_ell<P, VAL_F32, W>(s, J, t, n, st);
+    default: return launch_ell<P, VAL_BF16, W>(s, J, t, n, st);
+  }
 }
 
 template <int P, int KIND, int W, bool GS>
@@ -185,6 +305,8 @@ template <int P>
 static cudaError_t launch_p(const StateView &s, const CsrView &J, const StepTables &t, int n, int variant,
                             cudaStream_t st) {
   switch (variant) {
+    case 7: return launch_pw_ell<P, 8>(s, J, t, n, st);
+    case 6: return launch_pw_ell<P, 4>(s, J, t, n, st);
     case 5: return launch_pw<P, 16, true>(s, J, t, n, st);
     case 4: return launch_pw<P, 8, true>(s, J, t, n, st);
     case 3: return launch_pw<P, 4, true>(s, J, t, n, st);
@@ -195,15 +317,19 @@ static cudaError_t launch_p(const StateView &s, const CsrView &J, const StepTabl
 }
 
 // Variants 0-2: W = 4, 8, 16 columns per lane, one item per warp; 3-5: the
-// same widths with one wave of blocks looping over the items.  W needs Cp to
-// be a multiple of 32 W.
-int csr_step_variants() { return 6; }
+// same widths with one wave of blocks looping over the items; 6, 7: the ELL
+// form (W = 4, 8), when the problem has one (degree <= 8).  W needs Cp to be a
+// multiple of 32 W.
+int csr_step_variants() { return 8; }
 
-bool csr_step_variant_ok(int variant, int Cp) { return Cp % (32 * (4 << (variant % 3))) == 0; }
+bool csr_step_variant_ok(int variant, int Cp, bool has_ell) {
+  if (variant >= 6) return has_ell && Cp % (32 * (4 << (variant - 6))) == 0;
+  return Cp % (32 * (4 << (variant % 3))) == 0;
+}
 
 cudaError_t launch_step_csr(const StateView &s, const CsrView &J, const StepTables &t, int n, int variant,
                             cudaStream_t st) {
-  if (!csr_step_variant_ok(variant, s.Cp)) variant = 0;
+  if (!csr_step_variant_ok(variant, s.Cp, J.ell_col != nullptr)) variant = 0;
   switch (s.P) {
     case 1: return launch_p<1>(s, J, t, n, variant, st);
     case 2: return launch_p<2>(s, J, t, n, variant, st);

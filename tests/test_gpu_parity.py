@@ -324,10 +324,11 @@ def test_small_one_launch_solver_matches_per_step_path(sb, N, P, R, S, jmax):
     _check_energies_and_best(sb, pb, prob, R, P)
 
 
-@pytest.mark.parametrize("case", ["lattice", "regular_f32", "regular_bf16", "ragged"])
+@pytest.mark.parametrize("case", ["lattice", "regular_f32", "regular_bf16", "ragged", "degree12"])
 def test_csr_step_variants_bit_identical(sb, case):
     """Every per-step CSR kernel variant (W = 4, 8, 16 columns per lane; one
-    item per warp or one wave of blocks looping over the items), forced with
+    item per warp or one wave of blocks looping over the items; the ELL form
+    for degree <= 8, which falls back to variant 0 at degree 12), forced with
     kernel_select = 3 + v, gives the same state bit for bit after 40 steps."""
     if case == "lattice":
         pb, spec = lattice(8, 1); P, R, prec = 32, 16, "auto"
@@ -335,10 +336,12 @@ def test_csr_step_variants_bit_identical(sb, case):
         pb, spec = regular(700, 6, 3); P, R, prec = 16, 32, "fp32"
     elif case == "regular_bf16":
         pb, spec = regular(700, 5, 4); P, R, prec = 8, 64, "bf16"
-    else:
+    elif case == "ragged":
         pb, spec = lattice(5, 2); P, R, prec = 32, 5, "auto"  # Cp = 256: W = 16 falls back
+    else:
+        pb, spec = regular(400, 12, 5); P, R, prec = 16, 16, "fp32"
     states = []
-    for v in range(6):
+    for v in range(8):
         prob = create(sb, spec)
         sb.set_schedule(prob, *workloads.autotune_params(R, 3), **_params(precision=prec, kernel_select=3 + v))
         sb.run_begin(prob, 300, P, R, seed=11)
@@ -346,13 +349,15 @@ def test_csr_step_variants_bit_identical(sb, case):
         info = prob.info()
         assert info.step_kernel == 0
         states.append(sb.get_state(prob)[:2])
-    for v in range(1, 6):
+    for v in range(1, 8):
         assert np.array_equal(states[0][0], states[v][0]) and np.array_equal(states[0][1], states[v][1]), v
 
 
-def test_csr_grid_stride_variant_against_oracle(sb):
+@pytest.mark.parametrize("variant", [3, 6])
+def test_csr_grid_stride_and_ell_variants_against_oracle(sb, variant):
     pb, spec = regular(500, 6, 1)
-    wx, wy, _, _ = _per_step(sb, pb, spec, 16, 8, 300, 30, prec="fp32", kernel_select=3)
+    wx, wy, _, prob = _per_step(sb, pb, spec, 16, 8, 300, 30, prec="fp32", kernel_select=3 + variant)
+    assert prob.info().step_variant == variant
     assert wx <= TOL_STEP and wy <= TOL_STEP
 
 
