@@ -160,8 +160,10 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info);
  *                degree <= 8 and R*P a multiple of 256; the dense tensor-core
  *                path when its 128 x 128 tiles (padded N x padded R*P) fit
  *                the device at once (one per SM).  3 + v (v = 0..7) forces
- *                per-step CSR kernel variant v (see step_variant).  Results
- *                are identical whichever kernel runs.
+ *                per-step CSR kernel variant v (see step_variant); 11 forces
+ *                the persistent CSR solver in the mode that caches whole
+ *                rows (otherwise taken only when the items outnumber its
+ *                cache).  Results are identical whichever kernel runs.
  *   beta, alpha  host, n_runs doubles each: per-run inverse temperature and
  *                schedule exponent (the auto-tuning draws them from
  *                [0.5,1.5] x [0.5,1.0]); beta > 0, alpha > 0

@@ -446,17 +446,17 @@ int autotune_csr(sbqa_problem *p) {
   p->use_persistent = false;
   p->persistent_ms = 0.f;
   if (p->persist_blocks == 0) p->persist_blocks = persistent_blocks();
-  if (p->prm.kernel_select == 2 && p->S > 0 && p->persistent_ok()) {
+  if ((p->prm.kernel_select == 2 || p->prm.kernel_select == 11) && p->S > 0 && p->persistent_ok()) {
     SBQA_CUDA(p->d_bar.alloc(persistent_barrier_words()));
     p->use_persistent = true;
   } else if (p->prm.kernel_select == 0 && p->S > 0 && p->persistent_ok()) {
     SBQA_CUDA(p->d_bar.alloc(persistent_barrier_words()));
     const int steps = std::min(p->S, 64);
     SBQA_CUDA(launch_solve_csr_persistent(s, J, p->tables, 0, std::min(p->S, 4), p->d_bar.p, p->d_err.p,
-                                          p->persist_blocks, p->stream));
+                                          p->persist_blocks, p->persist_mode(), p->stream));
     SBQA_CUDA(cudaEventRecord(e0, p->stream));
     SBQA_CUDA(launch_solve_csr_persistent(s, J, p->tables, 0, steps, p->d_bar.p, p->d_err.p, p->persist_blocks,
-                                          p->stream));
+                                          p->persist_mode(), p->stream));
     SBQA_CUDA(cudaEventRecord(e1, p->stream));
     SBQA_CUDA(cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -556,7 +556,7 @@ cudaError_t issue_range(sbqa_problem *p, int n0, int n1, cudaStream_t st) {
       cudaError_t e = tc_persist ? launch_solve_dense_tc_persistent(p->tc_plan, p->state(), p->Kp, p->d_err.p,
                                                                     p->d_h.p, p->tables, n, stop, p->d_tc_flags.p, st)
                                  : launch_solve_csr_persistent(p->state(), p->csr(), p->tables, n, stop, p->d_bar.p,
-                                                               p->d_err.p, p->persist_blocks, st);
+                                                               p->d_err.p, p->persist_blocks, p->persist_mode(), st);
       if (e != cudaSuccess) return e;
       const int last = stop - 1;
       if (K > 0 && (last + 1) % K == 0 && last != p->S - 1) {
@@ -822,7 +822,7 @@ int sbqa_set_schedule(sbqa_problem *p, const sbqa_params *q) {
   if (q->precision == SBQA_PREC_EXACT && (!p->j_integer || p->max_abs_j > 16))
     return fail(SBQA_ERR_UNSUPPORTED, "EXACT precision needs integer J with |J_ij| <= 16");
   if (q->eval_every < 0 || q->n_runs < 0) return fail(SBQA_ERR_INVALID_ARG, "negative eval_every or n_runs");
-  if (q->kernel_select < 0 || q->kernel_select > 10) return fail(SBQA_ERR_INVALID_ARG, "kernel_select must be 0..10");
+  if (q->kernel_select < 0 || q->kernel_select > 11) return fail(SBQA_ERR_INVALID_ARG, "kernel_select must be 0..11");
   if (q->n_runs > 0 && (!q->beta || !q->alpha)) return fail(SBQA_ERR_INVALID_ARG, "beta/alpha missing");
   std::vector<double> beta, alpha;
   if (q->n_runs > 0) {

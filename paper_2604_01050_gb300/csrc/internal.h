@@ -97,9 +97,11 @@ int set_error(int code, const std::string &msg);
 // grid barrier between steps (solve_persistent.cu).
 int persistent_blocks();
 int persistent_barrier_words();  // size of the barrier counter buffer
-bool persistent_eligible(int N, int Cp, int max_degree, int blocks);
+// 0: not eligible; 1: items cached per warp; 2: whole rows cached per warp
+// (force_rows: rows whenever they fit)
+int persistent_mode(int N, int Cp, int max_degree, int blocks, bool force_rows);
 cudaError_t launch_solve_csr_persistent(const StateView &s, const CsrView &J, const StepTables &t, int n_begin,
-                                        int n_end, unsigned *bar, int *err, int blocks, cudaStream_t st);
+                                        int n_end, unsigned *bar, int *err, int blocks, int mode, cudaStream_t st);
 
 // Steps of a dense integer run on the tensor cores in one cooperative launch,
 // x and y resident in tensor memory, per-tile step flags between CTAs

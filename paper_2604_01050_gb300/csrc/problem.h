@@ -146,9 +146,13 @@ struct sbqa_problem {
     return use_tc && tc_plan && sbqa::tc_persistent_eligible(Kp, Cp, tc_persist_blocks);
   }
 
+  int persist_mode() const {
+    return sbqa::persistent_mode(n, Cp, max_degree, persist_blocks, prm.kernel_select == 11);
+  }
+
   bool persistent_ok() const {
     return !dense && !ballistic() && kind == sbqa::VAL_PM1 &&
-           sbqa::persistent_eligible(n, Cp, max_degree, persist_blocks);
+           persist_mode() != 0;
   }
 
   StateView state() const {

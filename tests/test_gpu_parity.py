@@ -189,11 +189,11 @@ def test_persistent_dense_tc_solver_matches_per_step(sb, N, P, R, jmax):
         assert prob.info().step_kernel == (2 if sel == 1 else 5)
         out.append((sb.get_state(prob)[:2], sb.get_energies(prob), sb.get_best(prob)))
     (xa, ya), ea, ba = out[0]
-    (xb, yb), eb, bb = out[1]
-    assert np.array_equal(xa, xb) and np.array_equal(ya, yb)
-    assert np.array_equal(ea[1], eb[1])
-    for k in ba:
-        assert np.array_equal(ba[k], bb[k]), k
+    for (xb, yb), eb, bb in out[1:]:
+        assert np.array_equal(xa, xb) and np.array_equal(ya, yb)
+        assert np.array_equal(ea[1], eb[1])
+        for k in ba:
+            assert np.array_equal(ba[k], bb[k]), k
     _check_best_with_readouts(sb, pb, prob, R, 200, 37)
 
 
@@ -368,7 +368,7 @@ def test_persistent_csr_solver_matches_per_step(sb, L, P, R):
     best-so-far readouts between stretches of steps (N = 343: ragged)."""
     pb, spec = lattice(L, L)
     out = []
-    for sel in (1, 2):
+    for sel in (1, 2, 11):  # per step; persistent caching items; persistent caching rows
         prob = create(sb, spec)
         sb.set_schedule(prob, *workloads.autotune_params(R, L), **_params(kernel_select=sel, eval_every=37))
         sb.run(prob, 200, P, R, seed=L)
