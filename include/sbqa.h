@@ -156,8 +156,8 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info);
  *   kernel_select  0 = let the autotuner choose between the per-step
  *                kernels and the persistent solver (default); 1 = per-step
  *                kernels; 2 = the persistent solver when the instance
- *                qualifies, else per-step.  CSR qualifies with +-1 J,
- *                degree <= 8 and R*P a multiple of 256; the dense tensor-core
+ *                qualifies, else per-step.  CSR qualifies with degree <= 8
+ *                and R*P a multiple of 128; the dense tensor-core
  *                path when its 128 x 128 tiles (padded N x padded R*P) fit
  *                the device at once (one per SM).  3 + v (v = 0..7) forces
  *                per-step CSR kernel variant v (see step_variant); 11 forces

@@ -147,12 +147,11 @@ struct sbqa_problem {
   }
 
   int persist_mode() const {
-    return sbqa::persistent_mode(n, Cp, max_degree, persist_blocks, prm.kernel_select == 11);
+    return sbqa::persistent_mode(n, Cp, max_degree, kind, persist_blocks, prm.kernel_select == 11);
   }
 
   bool persistent_ok() const {
-    return !dense && !ballistic() && kind == sbqa::VAL_PM1 &&
-           persist_mode() != 0;
+    return !dense && !ballistic() && persist_mode() != 0;
   }
 
   StateView state() const {

@@ -1,35 +1,37 @@
 // solve_persistent.cu -- all steps of a CSR run batch in one cooperative launch.
 //
-// For +-1 couplings with row degree <= 8.  The grid is exactly as large as
-// can be co-resident; every warp owns fixed work items (spin row, chunk of
-// 32 W replica columns) for the whole anneal -- individual items, or whole
-// rows with all their chunks when the items outnumber the cache.  Before the
-// first step a warp copies the column indices and signs of its rows into
-// shared memory, so a step needs no index loads: per item it gathers the f codes of the
-// (at most 8) neighbours and the x, y of its columns, sums, updates (same
-// arithmetic as k_step_csr) and writes x, y and the next codes.  The codes
+// For rows of degree <= 8 (+-1, FP32 or BF16 couplings).  The grid is exactly
+// as large as can be co-resident; every warp owns fixed work items (spin row,
+// chunk of 32 W replica columns, W = 4 or 8) for the whole anneal --
+// individual items, or whole rows with all their chunks when the items
+// outnumber the cache.  Before the first step a warp copies the column
+// indices (and signs or values) of its rows into shared memory, so a step
+// needs no index loads: per item it gathers the f codes of the (at most 8)
+// neighbours and the x, y of its columns, sums (same arithmetic and order as
+// k_step_csr), updates and writes x, y and the next codes.  The codes
 // written by other blocks are read through L2 (ld.global.cg), never the
-// non-coherent path.  Between
-// steps all blocks meet at a grid barrier (a counter in global memory); the
+// non-coherent path.  Between steps all blocks meet at a grid barrier; the
 // wait is bounded: after kBarrierSpins polls a block records an error and
 // stops stepping, so a broken grid ends with a status the host reads.
+#include <type_traits>
+
 #include "step_common.cuh"
 
 namespace sbqa {
 
 constexpr int kPersistMaxDeg = 8;
-constexpr int kPersistW = 8;                   // columns per lane
-constexpr int kPersistMaxItems = 120;  // items per warp in shared memory: 45 KB per block, under the 48 KB default
 constexpr unsigned kBarrierSpins = 1u << 24;  // polls per grid barrier (with backoff: seconds)
 // Two-level grid barrier: blocks arrive on one of kBarGroups group counters
 // (each on its own 128-byte line); the last arrival of a group adds one to
 // the global counter, which every block polls.  Counter words: global at 0,
 // group g at kBarStride * (g + 1).
 constexpr unsigned kBarGroups = 32, kBarStride = 32;
+constexpr size_t kPersistSmem = 46080;  // per block: under the 48 KB default with the static barrier flag
 
 struct PersistArgs {
   StateView s;
-  const int32_t *row_ptr, *col, *npos;  // +-1 CSR, each row's +1 entries first
+  const int32_t *row_ptr, *col, *npos;  // CSR (+-1: each row's +1 entries first)
+  const void *val;                      // FP32 or BF16 values (not +-1)
   const float *h;
   StepTables t;
   int n_begin, n_end;
@@ -37,24 +39,47 @@ struct PersistArgs {
   int *err;       // error flag
 };
 
-struct ItemIdx {
+// Cache entries.  Items mode: one (row, chunk) item.  Rows mode: one row; its
+// index is gw + q * warps for the warp's q-th row.  (degree | +1 count << 8)
+// packed in degpos; values only for FP32 / BF16 couplings.
+template <bool VALS>
+struct ItemEntry {
   int32_t col[kPersistMaxDeg];
-  int32_t row, chunk, deg, npos;
+  int32_t row, chunk;
+  uint32_t degpos;
 };
-
-// Rows mode (more items than the item cache holds): a warp owns whole rows,
-// gw + q * warps for q = 0, 1, ..., and walks all column chunks of each; only
-// the row's neighbours and (degree | +1 count << 8) are cached.
-constexpr int kPersistMaxRows = 150;  // 36 B each: 43 KB per block
-struct RowIdx {
+template <>
+struct ItemEntry<true> {
+  int32_t col[kPersistMaxDeg];
+  float val[kPersistMaxDeg];
+  int32_t row, chunk;
+  uint32_t degpos;
+};
+template <bool VALS>
+struct RowEntry {
   int32_t col[kPersistMaxDeg];
   uint32_t degpos;
+};
+template <>
+struct RowEntry<true> {
+  int32_t col[kPersistMaxDeg];
+  float val[kPersistMaxDeg];
+  uint32_t degpos;
+};
+
+template <bool ROWS, bool VALS>
+struct Cache {
+  using Entry = typename std::conditional<ROWS, RowEntry<VALS>, ItemEntry<VALS>>::type;
+  static constexpr int kPerWarp = int(kPersistSmem / 8 / sizeof(Entry));
 };
 
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned k, int *err) {
   __syncthreads();
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
+    // barrier number k (1, 2, ...): a block's fence + group atomic releases its
+    // writes, the group's last arrival (atomic, fence) acquires them and
+    // releases them again with its fence + global atomic, the poll acquires
     const unsigned G = gridDim.x < kBarGroups ? gridDim.x : kBarGroups;
     const unsigned g = blockIdx.x % G;
     const unsigned size_g = (gridDim.x - g + G - 1) / G;  // blocks b with b % G == g
@@ -79,83 +104,121 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned k, int *err
   return s_ok != 0;
 }
 
-// One item: x, y of the lane's columns and the f codes of the row's
-// neighbours for those columns (issued together), packed code sums per sign
-// (as k_step_csr), the update and the stores.
-template <int P>
-__device__ __forceinline__ void persist_item(const PersistArgs &a, int i, int chunk, const int32_t *col, int deg,
-                                             int npos, const uint8_t *Fin, uint8_t *Fout, float ka, float dnext,
-                                             int n, int lane) {
+// W bytes of f codes (one 4- or 8-byte load through L2: other blocks wrote
+// these codes in this launch).
+template <int W>
+struct Codes;
+template <>
+struct Codes<4> {
+  uint32_t w[1];
+  __device__ __forceinline__ void load(const uint8_t *p) { w[0] = __ldcg(reinterpret_cast<const uint32_t *>(p)); }
+  __device__ __forceinline__ void zero(uint32_t z) { w[0] = z; }
+};
+template <>
+struct Codes<8> {
+  uint32_t w[2];
+  __device__ __forceinline__ void load(const uint8_t *p) {
+    const uint2 v = __ldcg(reinterpret_cast<const uint2 *>(p));
+    w[0] = v.x;
+    w[1] = v.y;
+  }
+  __device__ __forceinline__ void zero(uint32_t z) { w[0] = w[1] = z; }
+};
+
+// One item: x, y of the lane's W columns and the f codes of the row's
+// neighbours for those columns (issued together), the coupling sums (+-1:
+// packed code sums per sign; otherwise FP32 FMAs in entry order, as
+// k_step_csr), the update and the stores.
+template <int P, int KIND, int W>
+__device__ __forceinline__ void persist_item(const PersistArgs &a, int i, int chunk, const int32_t *col,
+                                             const float *val, uint32_t degpos, const uint8_t *Fin, uint8_t *Fout,
+                                             float ka, float dnext, int n, int lane) {
   const StateView &s = a.s;
-  const int c0 = chunk * 32 * kPersistW + lane * kPersistW;
+  const int deg = int(degpos & 0xffu), npos = int(degpos >> 8);
+  const int c0 = chunk * 32 * W + lane * W;
   const size_t off = size_t(i) * s.Cp + c0;
-  float xs[kPersistW], ys[kPersistW];
+  float xs[W], ys[W];
 #pragma unroll
-  for (int u = 0; u < kPersistW / 4; ++u) {
+  for (int u = 0; u < W / 4; ++u) {
     const float4 xa = *reinterpret_cast<const float4 *>(s.x + off + 4 * u);
     const float4 ya = *reinterpret_cast<const float4 *>(s.y + off + 4 * u);
     xs[4 * u] = xa.x; xs[4 * u + 1] = xa.y; xs[4 * u + 2] = xa.z; xs[4 * u + 3] = xa.w;
     ys[4 * u] = ya.x; ys[4 * u + 1] = ya.y; ys[4 * u + 2] = ya.z; ys[4 * u + 3] = ya.w;
   }
-  uint2 f[kPersistMaxDeg];
-#pragma unroll
-  for (int e = 0; e < kPersistMaxDeg; ++e)
-    f[e] = e < deg ? __ldcg(reinterpret_cast<const uint2 *>(Fin + size_t(col[e]) * s.Cp + c0))
-                   : make_uint2(0u, 0u);  // L2 loads: other blocks wrote these codes in this launch
-  uint32_t ap0 = 0, ap1 = 0, am0 = 0, am1 = 0;
+  Codes<W> f[kPersistMaxDeg];
 #pragma unroll
   for (int e = 0; e < kPersistMaxDeg; ++e) {
-    if (e < npos) {
-      ap0 += f[e].x;
-      ap1 += f[e].y;
-    } else {
-      am0 += f[e].x;
-      am1 += f[e].y;
+    if (e < deg) f[e].load(Fin + size_t(col[e]) * s.Cp + c0);
+    else f[e].zero(KIND == VAL_PM1 ? 0u : kFZero4);
+  }
+  float G[W];
+  if constexpr (KIND == VAL_PM1) {
+    uint32_t ap[W / 4], am[W / 4];
+#pragma unroll
+    for (int q = 0; q < W / 4; ++q) ap[q] = am[q] = 0;
+#pragma unroll
+    for (int e = 0; e < kPersistMaxDeg; ++e) {
+      if (e < npos) {
+#pragma unroll
+        for (int q = 0; q < W / 4; ++q) ap[q] += f[e].w[q];
+      } else {
+#pragma unroll
+        for (int q = 0; q < W / 4; ++q) am[q] += f[e].w[q];
+      }
+    }
+    const int bias = (deg - npos) - npos;  // codes carry f + 1; missing entries add 0
+#pragma unroll
+    for (int c = 0; c < W; ++c)
+      G[c] = float(int((ap[c / 4] >> (8 * (c % 4))) & 0xffu) - int((am[c / 4] >> (8 * (c % 4))) & 0xffu) + bias);
+  } else {
+#pragma unroll
+    for (int c = 0; c < W; ++c) G[c] = 0.f;
+#pragma unroll
+    for (int e = 0; e < kPersistMaxDeg; ++e) {
+      if (e < deg) {
+        const float w = val[e];
+#pragma unroll
+        for (int c = 0; c < W; ++c) G[c] = fmaf(w, fdec(f[e].w[c / 4], c % 4), G[c]);
+      }
     }
   }
-  const int bias = (deg - npos) - npos;  // codes carry f + 1
-  float G[kPersistW];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    G[c] = float(int((ap0 >> (8 * c)) & 0xffu) - int((am0 >> (8 * c)) & 0xffu) + bias);
-    G[4 + c] = float(int((ap1 >> (8 * c)) & 0xffu) - int((am1 >> (8 * c)) & 0xffu) + bias);
-  }
-  sb_updateW<P, kPersistW>(s, a.t, ka, dnext, n, i, c0, G, __ldg(a.h + i), xs, ys, Fout);
+  sb_updateW<P, W>(s, a.t, ka, dnext, n, i, c0, G, __ldg(a.h + i), xs, ys, Fout);
+}
+
+template <int KIND>
+__device__ __forceinline__ float entry_value(const PersistArgs &a, int e) {
+  if constexpr (KIND == VAL_F32) return static_cast<const float *>(a.val)[e];
+  else return __bfloat162float(static_cast<const __nv_bfloat16 *>(a.val)[e]);
 }
 
 // ROWS = false: warp items (row, chunk) cached; true: whole rows cached.
-template <int P, bool ROWS>
+template <int P, bool ROWS, int KIND, int W>
 __global__ void __launch_bounds__(256, 4) k_solve_csr_persistent(PersistArgs a) {
-  extern __shared__ int32_t s_cache[];  // [8 warps][kPersistMaxItems] ItemIdx or [8][kPersistMaxRows] RowIdx
+  constexpr bool VALS = KIND != VAL_PM1;
+  using C = Cache<ROWS, VALS>;
+  using Entry = typename C::Entry;
+  extern __shared__ int32_t s_cache[];  // [8 warps][C::kPerWarp] entries
   const StateView &s = a.s;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int chunks = s.Cp / (32 * kPersistW);
+  const int chunks = s.Cp / (32 * W);
   const int warps_total = gridDim.x * 8;
   const int gw = blockIdx.x * 8 + warp;
-  ItemIdx *items = reinterpret_cast<ItemIdx *>(s_cache) + warp * kPersistMaxItems;
-  RowIdx *rows = reinterpret_cast<RowIdx *>(s_cache) + warp * kPersistMaxRows;
+  Entry *mine = reinterpret_cast<Entry *>(s_cache) + warp * C::kPerWarp;
   int my_count = 0;
-  if constexpr (ROWS) {
-    for (int row = gw; row < s.N && my_count < kPersistMaxRows; row += warps_total, ++my_count) {
-      if (lane == 0) {
-        const int e0 = a.row_ptr[row], e1 = a.row_ptr[row + 1];
-        RowIdx &m = rows[my_count];
-        m.degpos = uint32_t(e1 - e0) | (uint32_t(a.npos[row]) << 8);
-        for (int q = 0; q < kPersistMaxDeg; ++q) m.col[q] = q < e1 - e0 ? a.col[e0 + q] : 0;
-      }
-    }
-  } else {
-    const int n_items = s.N * chunks;
-    for (int it = gw; it < n_items && my_count < kPersistMaxItems; it += warps_total, ++my_count) {
-      if (lane == 0) {
-        const int row = it / chunks;
-        const int e0 = a.row_ptr[row], e1 = a.row_ptr[row + 1];
-        ItemIdx &m = items[my_count];
+  const int n_units = ROWS ? s.N : s.N * chunks;
+  for (int u = gw; u < n_units && my_count < C::kPerWarp; u += warps_total, ++my_count) {
+    if (lane == 0) {
+      const int row = ROWS ? u : u / chunks;
+      const int e0 = a.row_ptr[row], e1 = a.row_ptr[row + 1];
+      Entry &m = mine[my_count];
+      if constexpr (!ROWS) {
         m.row = row;
-        m.chunk = it - row * chunks;
-        m.deg = e1 - e0;
-        m.npos = a.npos[row];
-        for (int q = 0; q < kPersistMaxDeg; ++q) m.col[q] = q < m.deg ? a.col[e0 + q] : 0;
+        m.chunk = u - row * chunks;
+      }
+      m.degpos = uint32_t(e1 - e0) | (uint32_t(KIND == VAL_PM1 ? a.npos[row] : e1 - e0) << 8);
+      for (int q = 0; q < kPersistMaxDeg; ++q) {
+        m.col[q] = q < e1 - e0 ? a.col[e0 + q] : 0;
+        if constexpr (VALS) m.val[q] = q < e1 - e0 ? entry_value<KIND>(a, e0 + q) : 0.f;
       }
     }
   }
@@ -166,36 +229,56 @@ __global__ void __launch_bounds__(256, 4) k_solve_csr_persistent(PersistArgs a) 
     uint8_t *Fout = s.f_of(n + 1);
     const float ka = __ldg(a.t.ka + n), dnext = __ldg(a.t.dl + n + 1);
     for (int q = 0; q < my_count; ++q) {
+      const Entry &m = mine[q];
+      const float *val = nullptr;
+      if constexpr (VALS) val = m.val;
       if constexpr (ROWS) {
-        const RowIdx &m = rows[q];
-        const int deg = int(m.degpos & 0xffu), npos = int(m.degpos >> 8);
         for (int ch = 0; ch < chunks; ++ch)
-          persist_item<P>(a, gw + q * warps_total, ch, m.col, deg, npos, Fin, Fout, ka, dnext, n, lane);
+          persist_item<P, KIND, W>(a, gw + q * warps_total, ch, m.col, val, m.degpos, Fin, Fout, ka, dnext, n,
+                                   lane);
       } else {
-        const ItemIdx &m = items[q];
-        persist_item<P>(a, m.row, m.chunk, m.col, m.deg, m.npos, Fin, Fout, ka, dnext, n, lane);
+        persist_item<P, KIND, W>(a, m.row, m.chunk, m.col, val, m.degpos, Fin, Fout, ka, dnext, n, lane);
       }
     }
     if (!grid_barrier(a.bar, ++k, a.err)) break;
   }
 }
 
-constexpr size_t kPersistSmem = 8 * (kPersistMaxItems * sizeof(ItemIdx) > kPersistMaxRows * sizeof(RowIdx)
-                                         ? kPersistMaxItems * sizeof(ItemIdx)
-                                         : kPersistMaxRows * sizeof(RowIdx));
-
-template <bool ROWS>
-static const void *persistent_fn(int P) {
+template <bool ROWS, int KIND, int W>
+static const void *persistent_fn_p(int P) {
   switch (P) {
-    case 1: return (const void *)k_solve_csr_persistent<1, ROWS>;
-    case 2: return (const void *)k_solve_csr_persistent<2, ROWS>;
-    case 4: return (const void *)k_solve_csr_persistent<4, ROWS>;
-    case 8: return (const void *)k_solve_csr_persistent<8, ROWS>;
-    case 16: return (const void *)k_solve_csr_persistent<16, ROWS>;
-    case 32: return (const void *)k_solve_csr_persistent<32, ROWS>;
+    case 1: return (const void *)k_solve_csr_persistent<1, ROWS, KIND, W>;
+    case 2: return (const void *)k_solve_csr_persistent<2, ROWS, KIND, W>;
+    case 4: return (const void *)k_solve_csr_persistent<4, ROWS, KIND, W>;
+    case 8: return (const void *)k_solve_csr_persistent<8, ROWS, KIND, W>;
+    case 16: return (const void *)k_solve_csr_persistent<16, ROWS, KIND, W>;
+    case 32: return (const void *)k_solve_csr_persistent<32, ROWS, KIND, W>;
     default: return nullptr;
   }
 }
+
+template <bool ROWS, int W>
+static const void *persistent_fn_k(int P, int kind) {
+  switch (kind) {
+    case VAL_PM1: return persistent_fn_p<ROWS, VAL_PM1, W>(P);
+    case VAL_F32: return persistent_fn_p<ROWS, VAL_F32, W>(P);
+    default: return persistent_fn_p<ROWS, VAL_BF16, W>(P);
+  }
+}
+
+static const void *persistent_fn(int P, bool rows, int kind, int W) {
+  if (W == 8) return rows ? persistent_fn_k<true, 8>(P, kind) : persistent_fn_k<false, 8>(P, kind);
+  return rows ? persistent_fn_k<true, 4>(P, kind) : persistent_fn_k<false, 4>(P, kind);
+}
+
+static int per_warp(bool rows, int kind) {
+  const bool vals = kind != VAL_PM1;
+  if (rows) return vals ? Cache<true, true>::kPerWarp : Cache<true, false>::kPerWarp;
+  return vals ? Cache<false, true>::kPerWarp : Cache<false, false>::kPerWarp;
+}
+
+// W = 8 columns per lane when R * P allows it, else 4.
+static int persist_w(int Cp) { return Cp % 256 == 0 ? 8 : (Cp % 128 == 0 ? 4 : 0); }
 
 int persistent_barrier_words() { return int(kBarStride * (kBarGroups + 1)); }
 
@@ -203,24 +286,27 @@ int persistent_blocks() {
   int dev = 0, sms = 0, best = 1 << 30;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  // the smallest co-resident count over all replica counts and both modes
+  // the smallest co-resident count over all instantiations, so any of them fits the grid
   const int Ps[6] = {1, 2, 4, 8, 16, 32};
   for (int P : Ps)
-    for (int rows = 0; rows < 2; ++rows) {
-      int per_sm = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rows ? persistent_fn<true>(P) : persistent_fn<false>(P),
-                                                        256, kPersistSmem) != cudaSuccess)
-        return 0;
-      best = per_sm < best ? per_sm : best;
-    }
+    for (int kind = 0; kind < 3; ++kind)
+      for (int rows = 0; rows < 2; ++rows)
+        for (int W = 4; W <= 8; W += 4) {
+          int per_sm = 0;
+          if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_fn(P, rows != 0, kind, W), 256,
+                                                            kPersistSmem) != cudaSuccess)
+            return 0;
+          best = per_sm < best ? per_sm : best;
+        }
   return sms * best;
 }
 
-int persistent_mode(int N, int Cp, int max_degree, int blocks, bool force_rows) {
-  if (blocks <= 0 || max_degree > kPersistMaxDeg || Cp % (32 * kPersistW) != 0) return 0;
+int persistent_mode(int N, int Cp, int max_degree, int kind, int blocks, bool force_rows) {
+  const int W = persist_w(Cp);
+  if (blocks <= 0 || max_degree > kPersistMaxDeg || W == 0) return 0;
   const long long warps = (long long)blocks * 8;
-  if (!force_rows && (long long)N * (Cp / (32 * kPersistW)) <= warps * kPersistMaxItems) return 1;
-  if ((long long)N <= warps * kPersistMaxRows) return 2;
+  if (!force_rows && (long long)N * (Cp / (32 * W)) <= warps * per_warp(false, kind)) return 1;
+  if ((long long)N <= warps * per_warp(true, kind)) return 2;
   return 0;
 }
 
@@ -231,6 +317,7 @@ cudaError_t launch_solve_csr_persistent(const StateView &s, const CsrView &J, co
   a.row_ptr = J.row_ptr;
   a.col = J.col;
   a.npos = J.npos;
+  a.val = J.val;
   a.h = J.h;
   a.t = t;
   a.n_begin = n_begin;
@@ -238,8 +325,9 @@ cudaError_t launch_solve_csr_persistent(const StateView &s, const CsrView &J, co
   a.bar = bar;
   a.err = err;
   void *args[] = {&a};
-  const void *fn = mode == 2 ? persistent_fn<true>(s.P) : persistent_fn<false>(s.P);
-  if (!fn || (mode != 1 && mode != 2)) return cudaErrorInvalidValue;
+  const int W = persist_w(s.Cp);
+  const void *fn = (mode == 1 || mode == 2) && W ? persistent_fn(s.P, mode == 2, J.kind, W) : nullptr;
+  if (!fn) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(bar, 0, persistent_barrier_words() * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(256), args, kPersistSmem, st);

@@ -401,6 +401,29 @@ def _check_best_with_readouts(sb, pb, prob, R, S, K):
         assert oracle.energy_int(pb, best["spins"][r]) == best["energy_int"][r] == best["energy"][r]
 
 
+@pytest.mark.parametrize("N,d,P,R,prec", [(600, 6, 16, 8, "bf16"), (500, 5, 8, 32, "fp32"), (300, 8, 32, 4, "fp32")])
+def test_persistent_csr_solver_real_couplings(sb, N, d, P, R, prec):
+    """Random regular graphs with real J (FP32 or BF16 product) and a field:
+    the persistent solver (values cached beside the columns; W = 4 for
+    R*P = 128, W = 8 for 256) in both cache modes equals the per-step kernels
+    bit for bit."""
+    pb, spec = regular(N, d, 7)
+    out = []
+    for sel in (1, 2, 11):
+        prob = create(sb, spec)
+        sb.set_schedule(prob, *workloads.autotune_params(R, 4), **_params(precision=prec, kernel_select=sel,
+                                                                          eval_every=25, gamma0=4.0 * P))
+        sb.run(prob, 120, P, R, seed=3)
+        assert prob.info().step_kernel == (0 if sel == 1 else 4)
+        out.append((sb.get_state(prob)[:2], sb.get_energies(prob), sb.get_best(prob)))
+    (xa, ya), ea, ba = out[0]
+    for (xb, yb), eb, bb in out[1:]:
+        assert np.array_equal(xa, xb) and np.array_equal(ya, yb)
+        assert np.array_equal(ea[0], eb[0])
+        for k in ba:
+            assert np.array_equal(ba[k], bb[k]), k
+
+
 def test_persistent_csr_solver_resume(sb):
     pb, spec = lattice(8, 2)
     prob = create(sb, spec)
