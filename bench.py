@@ -61,6 +61,15 @@ SCALING = ["lattice16", "lattice24", "lattice32", "lattice48", "lattice64", "lat
 DEFAULT = "lattice16"
 BYTES_PER_UPDATE = 16  # x, y FP32 read + write per replica-spin update
 BYTES_PER_UPDATE_BSB = 20  # ballistic form: + the FP32 f (= x) write
+# DRAM traffic per step (dram__bytes_read.sum + dram__bytes_write.sum of one
+# ncu capture of the kernel named, divided by the steps of that launch), for
+# the roofline's "traffic"; reported only while that kernel is the one that
+# runs.  Commands and captures: profiles/*.md.
+TRAFFIC_PER_STEP = {
+    "lattice16": {"kernel": "k_solve_csr_persistent", "bytes_per_step": (77969408 + 4387555584) // 64},
+    "regular1e5": {"kernel": "k_solve_csr_persistent", "bytes_per_step": (7009805056 + 7254402304) // 64},
+    "sk2000": {"kernel": "k_solve_dense_tc_persistent", "bytes_per_step": (22741504 + 480512) // 64},
+}
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -604,22 +613,26 @@ def main():
     except Exception:
         pass
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    kernel_names = {0: "k_step_csr", 1: "k_step_dense", 2: "k_step_dense_tc", 3: "k_solve_small",
+                    4: "k_solve_csr_persistent", 5: "k_solve_dense_tc_persistent", 6: "k_step_csr_bsb",
+                    7: "k_step_dense_bsb"}
+    tr = TRAFFIC_PER_STEP.get(args.config + ("/ballistic" if cfg.get("variant") == "ballistic" else ""))
+    traffic = tr["bytes_per_step"] if tr and tr["kernel"] == kernel_names[info.step_kernel] else None
     if info.step_kernel in (2, 5):  # dense tcgen05 FP8: a contraction, 2 N^2 R P flops per step
         flops = 2.0 * N * N * P * R
         achieved = flops / (step_ms * 1e-3) / 1e12
         peak = 2.0 * peaks.get("bf16_tflops", 1900.0)  # FP8 = 2 x the measured BF16 dense peak
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_step_dense_tc" if info.step_kernel == 2 else "k_solve_dense_tc_persistent",
+                "traffic": traffic, "kernel": kernel_names[info.step_kernel],
                 "step_ms": step_ms, "peak_source": peak_src,
                 "note": "2 N^2 R P flops per step / event-timed step time; FP8 peak = 2 x measured BF16"}
     else:
         bpu = BYTES_PER_UPDATE_BSB if info.step_kernel in (6, 7) else BYTES_PER_UPDATE
         achieved_gbs = bpu * N * P * R / (step_ms * 1e-3) / 1e9
         hbm_peak = peaks.get("hbm_gbs", 6800.0)
-        kname = {0: "k_step_csr", 4: "k_solve_csr_persistent", 3: "k_solve_small", 1: "k_step_dense",
-                 6: "k_step_csr_bsb", 7: "k_step_dense_bsb"}[info.step_kernel]
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved_gbs / hbm_peak, "traffic": None, "kernel": kname, "step_ms": step_ms,
+                "frac": achieved_gbs / hbm_peak, "traffic": traffic, "kernel": kernel_names[info.step_kernel],
+                "step_ms": step_ms,
                 "peak_source": peak_src,
                 "note": "algorithmic %d B/update x N*P*R per launch / event-timed step time" % bpu}
 
