@@ -66,8 +66,6 @@ BYTES_PER_UPDATE_BSB = 20  # ballistic form: + the FP32 f (= x) write
 # the roofline's "traffic"; reported only while that kernel is the one that
 # runs.  Commands and captures: profiles/*.md.
 TRAFFIC_PER_STEP = {
-    "lattice16": {"kernel": "k_solve_csr_persistent", "bytes_per_step": (77969408 + 4387555584) // 64},
-    "regular1e5": {"kernel": "k_solve_csr_persistent", "bytes_per_step": (7009805056 + 7254402304) // 64},
     "sk2000": {"kernel": "k_solve_dense_tc_persistent", "bytes_per_step": (22741504 + 480512) // 64},
 }
 L2_FLUSH_BYTES = 512 << 20

@@ -11,8 +11,10 @@
 // k_step_csr), updates and writes x, y and the next codes.  The codes
 // written by other blocks are read through L2 (ld.global.cg), never the
 // non-coherent path.  Between steps all blocks meet at a grid barrier; the
-// wait is bounded: after kBarrierSpins polls a block records an error and
-// stops stepping, so a broken grid ends with a status the host reads.
+// wait is bounded (1 s, or at once when another block has already failed):
+// a block that gives up records an error and stops stepping, so a broken
+// grid ends with a status the host reads.
+#include <cstdlib>
 #include <type_traits>
 
 #include "step_common.cuh"
@@ -20,7 +22,8 @@
 namespace sbqa {
 
 constexpr int kPersistMaxDeg = 8;
-constexpr unsigned kBarrierSpins = 1u << 24;  // polls per grid barrier (with backoff: seconds)
+constexpr unsigned kBarrierSpins = 1u << 24;     // polls per grid barrier at most
+constexpr uint64_t kBarrierTimeoutNs = 1000000000;  // and at most 1 s of waiting (%globaltimer)
 // Two-level grid barrier: blocks arrive on one of kBarGroups group counters
 // (each on its own 128-byte line); the last arrival of a group adds one to
 // the global counter, which every block polls.  Counter words: global at 0,
@@ -37,6 +40,7 @@ struct PersistArgs {
   int n_begin, n_end;
   unsigned *bar;  // grid barrier counters (persistent_barrier_words(), zeroed before the launch)
   int *err;       // error flag
+  int skip_step;  // test hook: block 0 does not arrive at the barrier after this step (-1: never)
 };
 
 // Cache entries.  Items mode: one (row, chunk) item.  Rows mode: one row; its
@@ -73,7 +77,15 @@ struct Cache {
   static constexpr int kPerWarp = int(kPersistSmem / 8 / sizeof(Entry));
 };
 
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned k, int *err) {
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// skip: this block does not arrive (the test hook), so every block's wait
+// runs out and the launch ends with error code 4.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned k, int *err, bool skip = false) {
   __syncthreads();
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
@@ -84,20 +96,28 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, unsigned k, int *err
     const unsigned g = blockIdx.x % G;
     const unsigned size_g = (gridDim.x - g + G - 1) / G;  // blocks b with b % G == g
     __threadfence();
-    const unsigned old = atomicAdd(bar + kBarStride * (g + 1), 1u);
-    if (old + 1 == size_g * k) {  // last arrival of the group
-      __threadfence();
-      atomicAdd(bar, 1u);
+    if (!skip) {
+      const unsigned old = atomicAdd(bar + kBarStride * (g + 1), 1u);
+      if (old + 1 == size_g * k) {  // last arrival of the group
+        __threadfence();
+        atomicAdd(bar, 1u);
+      }
     }
     const unsigned target = G * k;
+    const uint64_t t0 = globaltimer_ns();
     unsigned v = 0;
     unsigned it = 0;
+    bool ok = false;
     for (; it < kBarrierSpins; ++it) {
       asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
-      if (v >= target) break;
+      if (v >= target) {
+        ok = true;
+        break;
+      }
+      if ((it & 15) == 15 && (globaltimer_ns() - t0 > kBarrierTimeoutNs || *(volatile int *)err != 0)) break;
       __nanosleep(it < 64 ? 32 : 128);
     }
-    s_ok = it < kBarrierSpins;
+    s_ok = ok;
     if (!s_ok) atomicCAS(err, 0, 4);
   }
   __syncthreads();
@@ -240,7 +260,7 @@ __global__ void __launch_bounds__(256, 4) k_solve_csr_persistent(PersistArgs a) 
         persist_item<P, KIND, W>(a, m.row, m.chunk, m.col, val, m.degpos, Fin, Fout, ka, dnext, n, lane);
       }
     }
-    if (!grid_barrier(a.bar, ++k, a.err)) break;
+    if (!grid_barrier(a.bar, ++k, a.err, n == a.skip_step && blockIdx.x == 0)) break;
   }
 }
 
@@ -324,6 +344,10 @@ cudaError_t launch_solve_csr_persistent(const StateView &s, const CsrView &J, co
   a.n_end = n_end;
   a.bar = bar;
   a.err = err;
+  // test hook for the barrier timeout: SBQA_TEST_SKIP_BARRIER_STEP=n makes block 0
+  // skip its arrival after step n of a launch that runs it (not for production use)
+  const char *skip = std::getenv("SBQA_TEST_SKIP_BARRIER_STEP");
+  a.skip_step = skip ? std::atoi(skip) : -1;
   void *args[] = {&a};
   const int W = persist_w(s.Cp);
   const void *fn = (mode == 1 || mode == 2) && W ? persistent_fn(s.P, mode == 2, J.kind, W) : nullptr;
