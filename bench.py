@@ -66,6 +66,8 @@ BYTES_PER_UPDATE_BSB = 20  # ballistic form: + the FP32 f (= x) write
 # the roofline's "traffic"; reported only while that kernel is the one that
 # runs.  Commands and captures: profiles/*.md.
 TRAFFIC_PER_STEP = {
+    "lattice16": {"kernel": "k_solve_csr_persistent", "bytes_per_step": (79867392 + 4435043328) // 64},
+    "regular1e5": {"kernel": "k_solve_csr_persistent", "bytes_per_step": (7006125056 + 7254420736) // 64},
     "sk2000": {"kernel": "k_solve_dense_tc_persistent", "bytes_per_step": (22741504 + 480512) // 64},
 }
 L2_FLUSH_BYTES = 512 << 20
