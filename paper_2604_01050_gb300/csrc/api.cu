@@ -331,8 +331,17 @@ int alloc_run(sbqa_problem *p, int S, int P, int R) {
   return SBQA_OK;
 }
 
+// The FP64 tables cost S * R transcendental evaluations on the host (640 000
+// for 10^4 steps of 64 runs), so they are rebuilt only when the run shape, the
+// schedule or the buffers change.
 int build_tables(sbqa_problem *p) {
-  return problem_build_tables(p, p->S, p->P, p->R, p->d_ka.p, p->d_dl.p, p->d_kj.p, &p->tables, p->stream);
+  sbqa_problem::TablesKey key;
+  key.S = p->S; key.P = p->P; key.R = p->R; key.version = p->params_version;
+  key.ka = p->d_ka.p; key.dl = p->d_dl.p; key.kj = p->d_kj.p;
+  if (key == p->tables_key) return SBQA_OK;
+  const int rc = problem_build_tables(p, p->S, p->P, p->R, p->d_ka.p, p->d_dl.p, p->d_kj.p, &p->tables, p->stream);
+  p->tables_key = rc == SBQA_OK ? key : sbqa_problem::TablesKey{};
+  return rc;
 }
 
 cudaError_t issue_step(sbqa_problem *p, int n, cudaStream_t st) {
@@ -838,6 +847,7 @@ int sbqa_set_schedule(sbqa_problem *p, const sbqa_params *q) {
   p->beta.swap(beta);
   p->alpha.swap(alpha);
   p->have_params = true;
+  ++p->params_version;
   return SBQA_OK;
 }
 

@@ -86,6 +86,16 @@ struct sbqa_problem {
 
   // schedule
   bool have_params = false;
+  uint64_t params_version = 0;  // bumped by every sbqa_set_schedule
+  // the schedule tables on the device were built for this (S, P, R, schedule, buffers)
+  struct TablesKey {
+    int S = -1, P = -1, R = -1;
+    uint64_t version = 0;
+    const void *ka = nullptr, *dl = nullptr, *kj = nullptr;
+    bool operator==(const TablesKey &o) const {
+      return S == o.S && P == o.P && R == o.R && version == o.version && ka == o.ka && dl == o.dl && kj == o.kj;
+    }
+  } tables_key;
   sbqa_params prm{};
   std::vector<double> beta, alpha;
 

@@ -468,6 +468,34 @@ def test_per_run_schedule_only_affects_its_run(sb):
     assert not np.array_equal(out[0][0][~keep], out[1][0][~keep])
 
 
+def test_schedule_tables_follow_schedule_and_shape_changes(sb):
+    """The schedule tables are kept between runs of a handle and rebuilt when
+    the schedule, the step count or the run shape changes: a handle run with
+    schedule A, then B, then A again, then with another S and R equals fresh
+    handles bit for bit."""
+    pb, spec = lattice(6, 4)
+    P = 16
+    ba, aa = workloads.autotune_params(8, 1)
+    bb, ab = workloads.autotune_params(8, 2)
+    sched = {"A": (ba, aa, dict(gamma0=8.0)), "B": (bb, ab, dict(gamma0=32.0, jperp_enable=1)),
+             "C": (ba[:4], aa[:4], dict(gamma0=8.0))}
+
+    def solve(prob, key, S, R, set_schedule=True):
+        b, a, kw = sched[key]
+        if set_schedule:
+            sb.set_schedule(prob, b, a, **_params(**kw))
+        sb.run(prob, S, P, R, seed=3)
+        return sb.get_state(prob)[0]
+
+    reuse = create(sb, spec)
+    seq = [("A", 120, 8), ("A", 120, 8), ("B", 120, 8), ("A", 120, 8), ("A", 90, 8), ("C", 90, 4)]
+    last = None
+    for key, S, R in seq:
+        got = solve(reuse, key, S, R, set_schedule=key != last)  # the same schedule again: tables reused
+        last = key
+        assert np.array_equal(got, solve(create(sb, spec), key, S, R)), (key, S, R)
+
+
 # ---------------------------------------------------------------- ballistic form f(x) = x
 @pytest.mark.parametrize("case", ["lattice_pm1", "regular_f32_field", "dense_real", "dense_int", "ragged"])
 def test_ballistic_per_step(sb, case):
