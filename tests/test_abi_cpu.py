@@ -40,6 +40,33 @@ def test_version_and_strerror(sb):
     assert sb.strerror(-99) == "unknown status"
 
 
+def test_dense_validation_errors_across_row_blocks(sb):
+    """The dense checks run per block of 64 rows and per 64 x 64 tile pair:
+    errors planted far from the diagonal and in the last, partial block are
+    still found (all fail before any device call)."""
+    n = 200
+    rng = np.random.default_rng(0)
+    up = np.triu(rng.choice([-1.0, 1.0], size=(n, n)), 1)
+    base = up + up.T
+    cases = []
+    J = base.copy(); J[3, 190] = -J[3, 190]                       # tile (0, 2) against its mirror
+    cases.append((J, None, sb.ERR_NOT_SYMMETRIC))
+    J = base.copy(); J[150, 70] += 0.5                            # lower triangle, middle blocks
+    cases.append((J, None, sb.ERR_NOT_SYMMETRIC))
+    J = base.copy(); J[199, 199] = 1.0                            # diagonal in the partial last block
+    cases.append((J, None, sb.ERR_NOT_SYMMETRIC))
+    J = base.copy(); J[130, 7] = np.nan; J[7, 130] = np.nan       # NaN
+    cases.append((J, None, sb.ERR_NOT_FINITE))
+    J = base.copy(); J[66, 65] = np.inf; J[65, 66] = np.inf        # inf at a block edge
+    cases.append((J, None, sb.ERR_NOT_FINITE))
+    h = np.zeros(n); h[198] = -np.inf
+    cases.append((base, h, sb.ERR_NOT_FINITE))
+    for J, hh, want in cases:
+        with pytest.raises(sb.SBQAError) as e:
+            sb.create_problem_dense(J, hh)
+        assert e.value.status == want
+
+
 def test_dense_validation_errors(sb):
     J = np.array([[0.0, 1.0], [1.0, 0.0]])
     with pytest.raises(sb.SBQAError) as e:
