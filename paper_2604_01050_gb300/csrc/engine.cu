@@ -127,9 +127,19 @@ struct sbqa_engine {
   size_t items_cap = 0;
   int sms = 0;
   int64_t steps_done_total = 0;  // replica-spin updates issued, for statistics
+  // dense requests run their chunk on a stream of their slot (created on first
+  // use), so small dense problems share the GPU instead of queueing
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> side_done;
+  cudaEvent_t chunk_start = nullptr;
 
   ~sbqa_engine() {
     cudaDeviceSynchronize();
+    for (cudaStream_t x : side)
+      if (x) cudaStreamDestroy(x);
+    for (cudaEvent_t x : side_done)
+      if (x) cudaEventDestroy(x);
+    if (chunk_start) cudaEventDestroy(chunk_start);
     for (auto &r : reqs)
       if (r.tc_plan) tc_plan_free(r.tc_plan);
     if (arena.base) cudaFree(arena.base);
@@ -352,23 +362,39 @@ int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done, int32_t *don
   if (n_items)
     ENG_CUDA(cudaMemcpyAsync(e->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, st));
   ENG_CUDA(cudaMemcpyAsync(e->d_n_items, &n_items, sizeof(int), cudaMemcpyHostToDevice, st));
-  // 3. the chunk: one batched launch per step for the CSR requests, own
-  //    launches for the dense ones
-  const int grid = std::max(1, std::min(n_items, e->sms * 3));
-  for (int j = 0; j < e->chunk; ++j) {
-    if (n_items) ENG_CUDA(launch_step_batched(e->d_slots, e->d_items, e->d_n_items, grid, j, st));
-    for (int id : dense_active) {
-      Request &r = e->reqs[id];
-      const int n = r.n0 + j;
-      if (n >= r.S) continue;
-      cudaError_t err;
-      if (r.prob->use_tc)
-        err = launch_step_dense_tc(r.tc_plan, r.state_view(), r.prob->Kp, r.FT, r.err, r.prob->d_h.p, r.tables, n, st);
-      else
-        err = launch_step_dense(r.state_view(), problem_dense_view(r.prob), r.tables, n, st);
-      if (err != cudaSuccess) return set_error(SBQA_ERR_CUDA, std::string("engine step: ") + cudaGetErrorString(err));
+  // 3. the chunk: the dense requests on their slots' streams (after everything
+  //    issued on `st` so far: admission, tables), one batched launch per step
+  //    for all CSR requests on `st`; `st` then waits for the dense streams
+  if (!dense_active.empty()) {
+    if (!e->chunk_start) ENG_CUDA(cudaEventCreateWithFlags(&e->chunk_start, cudaEventDisableTiming));
+    ENG_CUDA(cudaEventRecord(e->chunk_start, st));
+    if (e->side.empty()) {
+      e->side.assign(e->max_slots, nullptr);
+      e->side_done.assign(e->max_slots, nullptr);
     }
   }
+  for (int id : dense_active) {
+    Request &r = e->reqs[id];
+    cudaStream_t &ds = e->side[r.slot];
+    cudaEvent_t &dv = e->side_done[r.slot];
+    if (!ds) ENG_CUDA(cudaStreamCreateWithFlags(&ds, cudaStreamNonBlocking));
+    if (!dv) ENG_CUDA(cudaEventCreateWithFlags(&dv, cudaEventDisableTiming));
+    ENG_CUDA(cudaStreamWaitEvent(ds, e->chunk_start, 0));
+    for (int j = 0; j < e->chunk && r.n0 + j < r.S; ++j) {
+      const int n = r.n0 + j;
+      cudaError_t err;
+      if (r.prob->use_tc)
+        err = launch_step_dense_tc(r.tc_plan, r.state_view(), r.prob->Kp, r.FT, r.err, r.prob->d_h.p, r.tables, n, ds);
+      else
+        err = launch_step_dense(r.state_view(), problem_dense_view(r.prob), r.tables, n, ds);
+      if (err != cudaSuccess) return set_error(SBQA_ERR_CUDA, std::string("engine step: ") + cudaGetErrorString(err));
+    }
+    ENG_CUDA(cudaEventRecord(dv, ds));
+  }
+  const int grid = std::max(1, std::min(n_items, e->sms * 3));
+  for (int j = 0; j < e->chunk && n_items; ++j)
+    ENG_CUDA(launch_step_batched(e->d_slots, e->d_items, e->d_n_items, grid, j, st));
+  for (int id : dense_active) ENG_CUDA(cudaStreamWaitEvent(st, e->side_done[e->reqs[id].slot], 0));
   // 4. retire the requests that finished inside the chunk
   std::vector<int> finished;
   for (int q = 0; q < e->max_slots; ++q) {
