@@ -57,7 +57,12 @@ for _L, _S in ((24, 3000), (32, 1500), (48, 400), (64, 200), (88, 100)):
         kind="lattice", L=_L, P=32, R=64, S=_S, prec="auto",
         workload="3D cubic lattice spin glass L=%d (N=%d), periodic, J=+-1, CSR; P=32 replicas, R=64 runs, "
                  "%d steps; FP32 state, exact int8 product" % (_L, _L ** 3, _S))
-SCALING = ["lattice16", "lattice24", "lattice32", "lattice48", "lattice64", "lattice88", "regular1e5", "regular7e5"]
+for _n, _S in ((4096, 500), (8192, 200)):
+    CONFIGS["sk%d" % _n] = dict(
+        kind="sk", n=_n, P=32, R=32, S=_S, prec="exact",
+        workload="dense SK N=%d, J=+-1; P=32, R=32 (J.X = %dx%d @ %dx1024), %d steps" % (_n, _n, _n, _n, _S))
+SCALING = ["lattice16", "lattice24", "lattice32", "lattice48", "lattice64", "lattice88", "regular1e5", "regular7e5",
+           "sk2000", "sk4096", "sk8192"]
 DEFAULT = "lattice16"
 BYTES_PER_UPDATE = 16  # x, y FP32 read + write per replica-spin update
 BYTES_PER_UPDATE_BSB = 20  # ballistic form: + the FP32 f (= x) write
@@ -510,7 +515,8 @@ def run_scaling(args):
         points.append({"config": name, "N": c["N"], "P": c["P"], "R": c["R"],
                        "state_MB": round(c["state_bytes"] / 1e6, 1), "value": line["value"],
                        "step_kernel": c["step_kernel"], "step_ms": line["roofline"]["step_ms"],
-                       "achieved_gbs": line["roofline"]["achieved"], "frac": line["roofline"]["frac"],
+                       "achieved": line["roofline"]["achieved"], "unit": line["roofline"]["unit"],
+                       "bound": line["roofline"]["bound"], "frac": line["roofline"]["frac"],
                        "e2e": line["e2e"]["value"], "clocks": line["clocks"]})
     print(json.dumps({"metric": "replica-spin updates/s", "mode": "scaling", "unit": "replica-spin updates/s",
                       "variant": args.variant, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
