@@ -30,7 +30,7 @@
 namespace sbqa {
 
 constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 128, kTcStages = 3;
-constexpr int kTcThreads = 256;          // 8 warps: all run the epilogue
+constexpr int kTcThreads = 512;          // 16 warps: all run the epilogue, one 32-column box each
 constexpr int kTcTile = kTcBM * kTcBK;   // bytes of one operand stage (e4m3)
 constexpr int kTcBox = kTcBM * 128;      // one 128-row x 32-float state box (16 KB)
 constexpr int kTcStateTile = 4 * kTcBox; // x or y tile, 128 rows x 128 columns (64 KB)
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncwarp();
   const float ka = __ldg(t.ka + n), dnext = __ldg(t.dl + n + 1);
   const float *kjn = t.kj + size_t(n) * t.R;
-  const int quarter = warp & 3, half = warp >> 2;
+  const int quarter = warp & 3, b = warp >> 2;  // TMEM lanes 32 (w % 4).., state box w / 4
   const int rl = quarter * 32 + lane;
   const int i = m0 + rl;
   const float hi = i < s.N ? __ldg(a.h + i) : 0.f;
@@ -191,12 +191,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   tc::tc_fence_after();
 
   // Epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (= spin rows) and
-  // columns 64 (w / 4) .. + 63 in two chunks of 32 (one state box each).
+  // columns 32 (w / 4) .. + 31 (one state box).
   uint8_t *sF = sA;  // [128 columns][128 spins] e4m3 f(x_next); the operand stages are consumed
-#pragma unroll 1
-  for (int cc = 0; cc < 2; ++cc) {
-    const int b = half * 2 + cc;  // state box
-    const int cl = 32 * b;        // first column of the chunk inside the tile
+  {
+    const int cl = 32 * b;  // first column of the chunk inside the tile
     const int c0 = n0 + cl;
     uint32_t g[32];
     tc::tmem_ld_32x32b_x32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(cl), g);
