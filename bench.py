@@ -248,11 +248,11 @@ def run_serving(args):
             "steps": len(reqs), "warmup": 6, "ms_per_step": 1e3 * head["mean_s"], "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "Poisson stream of SK +-1 (dense) and 3D lattice (CSR) requests, "
-                                   "N log-uniform in 64..8192, P in {8,16,32}, R=16, 2000 steps; "
+                                   "N uniform in 64..8192, P in {8,16,32}, R=16, 2000 steps; "
                                    "continuous batching engine, chunk 50 steps",
                        "requests": len(reqs), "capacity_req_per_s": capacity,
                        "closed_loop_updates_per_s": closed["updates"] / closed["makespan_s"]},
-            "p50_s": head["p50_s"], "loads": loads, "gpu_launches": None}
+            "p50_s": head["p50_s"], "loads": loads, "gpu_launches": head["kernels_launched"]}
     print(json.dumps(line))
     return 0
 

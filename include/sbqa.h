@@ -305,6 +305,7 @@ typedef struct {
     int32_t queued, active, finished;
     int64_t arena_bytes, arena_used;
     int64_t updates_issued; /* replica-spin updates advanced so far */
+    int64_t kernels_launched; /* kernels the engine has launched so far */
 } sbqa_engine_stats_t;
 
 int sbqa_engine_stats(const sbqa_engine *e, sbqa_engine_stats_t *s);

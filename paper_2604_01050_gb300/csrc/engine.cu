@@ -127,6 +127,7 @@ struct sbqa_engine {
   size_t items_cap = 0;
   int sms = 0;
   int64_t steps_done_total = 0;  // replica-spin updates issued, for statistics
+  int64_t kernels_launched = 0;  // kernels this engine has launched, for statistics
   // dense requests run their chunk on a stream of their slot (created on first
   // use), so small dense problems share the GPU instead of queueing
   std::vector<cudaStream_t> side;
@@ -225,6 +226,7 @@ int admit(sbqa_engine *e, Request &r, int slot, cudaStream_t st) {
   ENG_CUDA(launch_init(s, r.seed, float(p->prm.init_amp), 0.0f, st));
   if (tc) ENG_CUDA(launch_f_to_ft8(s, 0, r.FT, p->Kp, 0, st));
   ENG_CUDA(launch_reset_best(s, r.best_view(), st));
+  e->kernels_launched += tc ? 3 : 2;
   r.slot = slot;
   r.n0 = 0;
   r.state = ACTIVE;
@@ -252,6 +254,7 @@ int readout(sbqa_engine *e, Request &r, cudaStream_t st) {
   cudaError_t err = p->dense ? launch_energy_dense(s, ev, r.best_view(), st)
                              : launch_energy_csr(s, problem_csr_readout_view(p), ev, r.best_view(), st);
   if (err == cudaSuccess) err = launch_best(s, ev, r.best_view(), r.S - 1, st);
+  e->kernels_launched += 4;  // signs, energies, their final sums, best
   if (err != cudaSuccess) return set_error(SBQA_ERR_CUDA, std::string("engine readout: ") + cudaGetErrorString(err));
   r.spins.resize(size_t(r.R) * p->n);
   r.energy.resize(r.R);
@@ -388,12 +391,15 @@ int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done, int32_t *don
       else
         err = launch_step_dense(r.state_view(), problem_dense_view(r.prob), r.tables, n, ds);
       if (err != cudaSuccess) return set_error(SBQA_ERR_CUDA, std::string("engine step: ") + cudaGetErrorString(err));
+      ++e->kernels_launched;
     }
     ENG_CUDA(cudaEventRecord(dv, ds));
   }
   const int grid = std::max(1, std::min(n_items, e->sms * 3));
-  for (int j = 0; j < e->chunk && n_items; ++j)
+  for (int j = 0; j < e->chunk && n_items; ++j) {
     ENG_CUDA(launch_step_batched(e->d_slots, e->d_items, e->d_n_items, grid, j, st));
+    ++e->kernels_launched;
+  }
   for (int id : dense_active) ENG_CUDA(cudaStreamWaitEvent(st, e->side_done[e->reqs[id].slot], 0));
   // 4. retire the requests that finished inside the chunk
   std::vector<int> finished;
@@ -449,6 +455,7 @@ int sbqa_engine_stats(const sbqa_engine *e, sbqa_engine_stats_t *s) {
   s->arena_bytes = int64_t(e->arena.bytes);
   s->arena_used = int64_t(e->arena.used);
   s->updates_issued = e->steps_done_total;
+  s->kernels_launched = e->kernels_launched;
   return SBQA_OK;
 }
 

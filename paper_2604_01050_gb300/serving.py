@@ -14,7 +14,6 @@ sample an instance, a replica count and a seed.
 """
 from __future__ import annotations
 
-import math
 import time
 
 import numpy as np
@@ -28,7 +27,7 @@ def make_pool(n_instances=12, seed=0, n_min=64, n_max=8192, R=16):
     rng = np.random.default_rng(seed)
     pool = []
     for k in range(n_instances):
-        n = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        n = int(rng.integers(n_min, n_max + 1))  # N uniform in [n_min, n_max]
         beta, alpha = workloads.autotune_params(R, seed + k)
         if k % 2 == 0:
             J, _ = workloads.sk_pm1(n, seed + k)
@@ -86,9 +85,10 @@ def run_stream(reqs, rate, arena_bytes=40 << 30, slots=64, chunk=50, seed=2, str
     lat = np.array([done_at[q] - arrivals[q] for q in range(len(reqs))])
     updates = sum(r["inst"]["n"] * r["P"] * r["R"] * r["steps"] for r in reqs)
     results = {rid: sb.engine_result(eng, rid) for rid in id_of}
+    kernels = sb.engine_stats(eng)["kernels_launched"]
     eng.destroy()
     return {"latency_s": lat, "makespan_s": makespan, "updates": updates, "results": results,
-            "arrivals": arrivals}
+            "arrivals": arrivals, "kernels_launched": kernels}
 
 
 def summary(out):
@@ -96,4 +96,4 @@ def summary(out):
     return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "mean_s": float(lat.mean()), "max_s": float(lat.max()),
             "updates_per_s": out["updates"] / out["makespan_s"], "makespan_s": out["makespan_s"],
-            "requests": int(lat.size)}
+            "requests": int(lat.size), "kernels_launched": int(out["kernels_launched"])}
