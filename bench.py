@@ -641,6 +641,8 @@ def main():
     kernel_names = {0: "k_step_csr", 1: "k_step_dense", 2: "k_step_dense_tc", 3: "k_solve_small",
                     4: "k_solve_csr_persistent", 5: "k_solve_dense_tc_persistent", 6: "k_step_csr_bsb",
                     7: "k_step_dense_bsb"}
+    if info.step_kernel == 2 and (-(-P * R // 128) * 128) % 256 == 0:
+        kernel_names[2] = "k_step_dense_tc_wide"  # 128 x 256 tiles when the padded columns allow
     tr = TRAFFIC_PER_STEP.get(args.config + ("/ballistic" if cfg.get("variant") == "ballistic" else ""))
     traffic = tr["bytes_per_step"] if tr and tr["kernel"] == kernel_names[info.step_kernel] else None
     if info.step_kernel in (2, 5):  # dense tcgen05 FP8: a contraction, 2 N^2 R P flops per step

@@ -110,7 +110,9 @@ typedef struct {
     double c0_auto;     /* default c0 = 0.5 sqrt(n / sum_ij J_ij^2)        */
     int32_t step_kernel;  /* coupling-product kernel of the last run: 0 CSR
                              per step, 1 dense CUDA cores, 2 dense tcgen05
-                             FP8, 3 the one-launch small dense solver, 4 the
+                             FP8 per step (128 x 256 tiles when the padded
+                             column count is a multiple of 256, else 128 x
+                             128), 3 the one-launch small dense solver, 4 the
                              persistent CSR solver (one cooperative launch
                              for all steps), 5 the persistent dense tcgen05
                              solver (x, y resident in tensor memory), 6 CSR

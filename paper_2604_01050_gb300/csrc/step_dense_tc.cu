@@ -46,6 +46,7 @@ struct TcArgs {
 
 struct TcMaps {
   CUtensorMap A, B;  // J8 and FT operand tiles (128 x 128 bytes, 128B swizzle)
+  CUtensorMap B2;    // FT operand tiles of 256 columns (256 x 128 bytes, 128B swizzle)
   CUtensorMap X, Y;  // x, y state boxes (128 rows x 32 floats, 128B swizzle)
   CUtensorMap Fst;   // FT tile store (128 columns x 128 spins bytes, no swizzle)
 };
@@ -60,14 +61,38 @@ __device__ __forceinline__ float4 *box_chunk(uint8_t *box, int r, int u) {
   return reinterpret_cast<float4 *>(box + r * 128 + ((u ^ (r & 7)) << 4));
 }
 
+// J_perp of the runs of a 32-column chunk.  For P >= 4 (at most 8 runs) the
+// values are read before the accumulator is ready, off the critical path; for
+// P < 4 (16 or 32 runs, which would not fit beside the tile in registers) they
+// are read inside the update.
+template <int P>
+struct KjChunk {
+  static constexpr int kRuns = 32 / (P < 32 ? P : 32);
+  static constexpr bool kEarly = P >= 4;
+  float v[kEarly ? kRuns : 1];
+  const float *kjn;
+  __device__ __forceinline__ void load(const StateView &s, const float *kj_step, int c0) {
+    kjn = kj_step;
+    if constexpr (kEarly) {
+#pragma unroll
+      for (int q = 0; q < kRuns; ++q) v[q] = (c0 + q * P < s.C) ? __ldg(kjn + c0 / P + q) : 0.f;
+    }
+  }
+  __device__ __forceinline__ float get(int c0, int q) const {
+    if constexpr (kEarly) return v[q];
+    else return __ldg(kjn + c0 / P + q);
+  }
+};
+
 // Update of one spin row for 32 aligned columns c0..c0+31 (whole runs,
 // because P divides 32); x and y are read from and written back to one row of
 // the swizzled shared-memory state boxes.  Same arithmetic, in the same
 // order, as sb_update4.
 template <int P>
 __device__ __forceinline__ void sb_update_row32(const StateView &s, const StepTables &t, float ka, float dnext,
-                                                const float *kjn, int c0, const uint32_t (&g)[32], float hi,
+                                                const KjChunk<P> &kj, int c0, const uint32_t (&g)[32], float hi,
                                                 uint8_t *xbox, uint8_t *ybox, int r, int8_t (&f)[32]) {
+  constexpr int PR = P < 32 ? P : 32;
   float xs[32], ys[32];
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
@@ -75,9 +100,6 @@ __device__ __forceinline__ void sb_update_row32(const StateView &s, const StepTa
     xs[4 * u] = a.x; xs[4 * u + 1] = a.y; xs[4 * u + 2] = a.z; xs[4 * u + 3] = a.w;
     ys[4 * u] = b.x; ys[4 * u + 1] = b.y; ys[4 * u + 2] = b.z; ys[4 * u + 3] = b.w;
   }
-  float kjv[32 / (P < 32 ? P : 32)];
-#pragma unroll
-  for (int q = 0; q < 32 / (P < 32 ? P : 32); ++q) kjv[q] = (c0 + q * P < s.C) ? __ldg(kjn + c0 / P + q) : 0.f;
   float xo[32], yo[32];
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
@@ -87,10 +109,9 @@ __device__ __forceinline__ void sb_update_row32(const StateView &s, const StepTa
     xo[j] = xs[j];
     yo[j] = ys[j];
     if (c0 + j >= s.C) continue;
-    const float kj = kjv[j / (P < 32 ? P : 32)];
     float yn = fmaf(t.kc, __uint_as_float(g[j]) + hi, ys[j]);
     yn = fmaf(-ka, xs[j], yn);
-    yn = fmaf(kj, xm + xp, yn);
+    yn = fmaf(kj.get(c0, j / PR), xm + xp, yn);
     float xn = fmaf(t.kx, yn, xs[j]);
     if (fabsf(xn) > 1.f) {
       xn = copysignf(1.f, xn);
@@ -181,11 +202,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
   __syncwarp();
   const float ka = __ldg(t.ka + n), dnext = __ldg(t.dl + n + 1);
-  const float *kjn = t.kj + size_t(n) * t.R;
   const int quarter = warp & 3, b = warp >> 2;  // TMEM lanes 32 (w % 4).., state box w / 4
   const int rl = quarter * 32 + lane;
   const int i = m0 + rl;
   const float hi = i < s.N ? __ldg(a.h + i) : 0.f;
+  KjChunk<P> kj;
+  kj.load(s, t.kj + size_t(n) * t.R, n0 + 32 * b);
   tc::mbar_wait(done, 0, a.err, tc::ERR_WAIT_DONE);
   tc::mbar_wait(xy_full, 0, a.err, tc::ERR_WAIT_FULL);
   tc::tc_fence_after();
@@ -200,7 +222,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc::tmem_ld_32x32b_x32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(cl), g);
     int8_t f[32];
     if (i < s.N && c0 < s.C) {
-      sb_update_row32<P>(s, t, ka, dnext, kjn, c0, g, hi, sX + b * kTcBox, sY + b * kTcBox, rl, f);
+      sb_update_row32<P>(s, t, ka, dnext, kj, c0, g, hi, sX + b * kTcBox, sY + b * kTcBox, rl, f);
     } else {
 #pragma unroll
       for (int j = 0; j < 32; ++j) f[j] = 0;
@@ -222,6 +244,175 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc::tma_store_commit_and_wait_read();
   }
   if (warp == 0) tc::tmem_dealloc(tmem, 128);
+}
+
+// ---------------------------------------------------------------- wide per-step kernel
+// The same step with 128 x 256 tiles (tcgen05.mma M=128 N=256 K=32), for
+// Cp a multiple of 256.  With N = 128 the tensor core reads a 128 x 32 A
+// slice and a 128 x 32 B slice from shared memory per instruction while TMA
+// writes the next stages into the same memory, and the K loop runs at about
+// half the MMA rate; with N = 256 one A slice serves twice the columns and
+// the loop runs at the MMA rate.  Four stages of 48 KB (A 16 KB, B 32 KB)
+// fill shared memory, so the state tile (x and y of 128 rows x 256 columns,
+// 256 KB) goes through the freed stages after the MMAs in two rounds of 128
+// columns:
+//   box slots (16 KB each): [0, 64K) = A stages, [64K, 192K) = B stages
+//   round 0 (columns 0-127):   x boxes 0-3 at 0-48K, y boxes 0-3 at 64K-112K
+//   round 1 (columns 128-255): x boxes 4-7 at 128K-176K (loaded with round 0),
+//                              y boxes 4-7 at 0-48K once round 0's x boxes
+//                              have been stored
+// f(x_next) of all 256 columns collects in its own 32 KB tile.
+constexpr int kTwBN = 256, kTwStages = 4;
+constexpr int kTwTileB = kTwBN * kTcBK;                       // 32 KB
+constexpr int kTwStageBytes = kTcTile + kTwTileB;             // 48 KB
+constexpr int kTwOperands = kTwStages * kTwStageBytes;        // 192 KB
+constexpr int kTwSmem = kTwOperands + kTcBM * kTwBN + 1024 + 128;
+static_assert(kTwSmem <= 227 * 1024, "wide tile exceeds the shared memory of one CTA");
+static_assert(2 * kTcStateTile + kTcStateTile <= kTwOperands, "state boxes of a round must fit the operand stages");
+
+template <int P>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_step_dense_tc_wide(const __grid_constant__ TcMaps m, StateView s, TcArgs a, StepTables t, int n) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t *sA = smem;                                 // [4][16 KB]
+  uint8_t *sB = smem + kTwStages * kTcTile;           // [4][32 KB]
+  uint8_t *sF = smem + kTwOperands;                   // [256 columns][128 spins] e4m3 f(x_next)
+  uint64_t *full = reinterpret_cast<uint64_t *>(sF + kTcBM * kTwBN);
+  uint64_t *empty = full + kTwStages;
+  uint64_t *done = empty + kTwStages;
+  uint64_t *xy0 = done + 1, *x1 = xy0 + 1, *y1 = x1 + 1;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(y1 + 1);
+  uint8_t *sX0 = smem, *sY0 = smem + kTcStateTile, *sX1 = smem + 2 * kTcStateTile, *sY1 = smem;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * kTwBN;
+  const int KB = a.Kp / kTcBK;
+  const int brow = (n & 1) * s.Cp + n0;  // row of F_n in the [2 Cp][Kp] map
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kTwStages; ++q) {
+      tc::mbar_init(&full[q], 1);
+      tc::mbar_init(&empty[q], 1);
+    }
+    tc::mbar_init(done, 1);
+    tc::mbar_init(xy0, 1);
+    tc::mbar_init(x1, 1);
+    tc::mbar_init(y1, 1);
+    tc::fence_mbar_init();
+    tc::prefetch_tmap(&m.A);
+    tc::prefetch_tmap(&m.B2);
+    tc::prefetch_tmap(&m.X);
+    tc::prefetch_tmap(&m.Y);
+  }
+  if (warp == 0) tc::tmem_alloc(tmem_slot, kTwBN);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    const uint64_t keep = tc::policy_evict_last();
+    for (int kb = 0; kb < KB; ++kb) {
+      const int st = kb % kTwStages, q = kb / kTwStages;
+      if (q > 0 && !tc::mbar_wait(&empty[st], (q - 1) & 1, a.err, tc::ERR_WAIT_EMPTY)) break;
+      tc::mbar_arrive_expect_tx(&full[st], kTwStageBytes);
+      tc::tma_load_2d_hint(sA + st * kTcTile, &m.A, &full[st], kb * kTcBK, m0, keep);
+      tc::tma_load_2d_hint(sB + st * kTwTileB, &m.B2, &full[st], kb * kTcBK, brow, keep);
+    }
+    // the operand stages are free once every MMA has completed: state boxes
+    // of round 0 and the x boxes of round 1 (whatever the wait's outcome, so
+    // that every barrier below completes)
+    tc::mbar_wait(done, 0, a.err, tc::ERR_WAIT_DONE);
+    tc::mbar_arrive_expect_tx(xy0, 2 * kTcStateTile);
+    tc::mbar_arrive_expect_tx(x1, kTcStateTile);
+    for (int b = 0; b < 4; ++b) {
+      tc::tma_load_2d(sX0 + b * kTcBox, &m.X, xy0, n0 + 32 * b, m0);
+      tc::tma_load_2d(sY0 + b * kTcBox, &m.Y, xy0, n0 + 32 * b, m0);
+      tc::tma_load_2d(sX1 + b * kTcBox, &m.X, x1, n0 + 128 + 32 * b, m0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = tc::idesc_f8_e4m3(kTcBM, kTwBN);
+    for (int kb = 0; kb < KB; ++kb) {
+      const int st = kb % kTwStages, q = kb / kTwStages;
+      if (!tc::mbar_wait(&full[st], q & 1, a.err, tc::ERR_WAIT_FULL)) break;
+      tc::tc_fence_after();
+      const uint32_t a0 = tc::smem_u32(sA + st * kTcTile), b0 = tc::smem_u32(sB + st * kTwTileB);
+#pragma unroll
+      for (int kk = 0; kk < kTcBK / 32; ++kk)
+        tc::mma_f8(tmem, tc::smem_desc_sw128(a0 + kk * 32), tc::smem_desc_sw128(b0 + kk * 32), idesc,
+                   (kb | kk) != 0 ? 1u : 0u);
+      tc::mma_commit(&empty[st]);
+    }
+    tc::mma_commit(done);
+  }
+  __syncwarp();
+  const float ka = __ldg(t.ka + n), dnext = __ldg(t.dl + n + 1);
+  const int quarter = warp & 3, b = warp >> 2;  // TMEM lanes 32 (w % 4).., box w / 4 of each round
+  const int rl = quarter * 32 + lane;
+  const int i = m0 + rl;
+  const float hi = i < s.N ? __ldg(a.h + i) : 0.f;
+  KjChunk<P> kj[2];
+  kj[0].load(s, t.kj + size_t(n) * t.R, n0 + 32 * b);
+  kj[1].load(s, t.kj + size_t(n) * t.R, n0 + 128 + 32 * b);
+  tc::mbar_wait(done, 0, a.err, tc::ERR_WAIT_DONE);
+  tc::tc_fence_after();
+
+#pragma unroll 1
+  for (int round = 0; round < 2; ++round) {
+    uint8_t *xbox = (round == 0 ? sX0 : sX1) + b * kTcBox;
+    uint8_t *ybox = (round == 0 ? sY0 : sY1) + b * kTcBox;
+    if (round == 0) {
+      tc::mbar_wait(xy0, 0, a.err, tc::ERR_WAIT_FULL);
+    } else {
+      tc::mbar_wait(x1, 0, a.err, tc::ERR_WAIT_FULL);
+      tc::mbar_wait(y1, 0, a.err, tc::ERR_WAIT_FULL);
+    }
+    const int cl = 128 * round + 32 * b;  // first column of the chunk inside the tile
+    const int c0 = n0 + cl;
+    uint32_t g[32];
+    tc::tmem_ld_32x32b_x32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(cl), g);
+    int8_t f[32];
+    if (i < s.N && c0 < s.C) {
+      sb_update_row32<P>(s, t, ka, dnext, kj[round], c0, g, hi, xbox, ybox, rl, f);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) f[j] = 0;
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) sF[(cl + j) * kTcBM + rl] = f_to_e4m3(f[j]);
+    tc::fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      // the round's x, y boxes back (rows past N are clipped by the tensor map),
+      // x and y as separate store groups
+      for (int q = 0; q < 4; ++q)
+        tc::tma_store_2d(&m.X, (round == 0 ? sX0 : sX1) + q * kTcBox, n0 + 128 * round + 32 * q, m0);
+      tc::tma_store_commit();
+      for (int q = 0; q < 4; ++q)
+        tc::tma_store_2d(&m.Y, (round == 0 ? sY0 : sY1) + q * kTcBox, n0 + 128 * round + 32 * q, m0);
+      tc::tma_store_commit();
+      if (round == 0) {
+        // round 1's y boxes take the place of round 0's x boxes once those are
+        // read (the y group may still be reading)
+        tc::tma_store_wait_read<1>();
+        tc::mbar_arrive_expect_tx(y1, kTcStateTile);
+        for (int q = 0; q < 4; ++q) tc::tma_load_2d(sY1 + q * kTcBox, &m.Y, y1, n0 + 128 + 32 * q, m0);
+      } else {
+        const uint64_t keep = tc::policy_evict_last();
+        // f_{n+1} of this tile into the other FT buffer: columns n0.., spins m0..
+        tc::tma_store_2d_hint(&m.Fst, sF, m0, ((n + 1) & 1) * s.Cp + n0, keep);
+        tc::tma_store_2d_hint(&m.Fst, sF + kTcBM * kTcBN, m0, ((n + 1) & 1) * s.Cp + n0 + kTcBN, keep);
+        tc::tma_store_commit_and_wait_read();
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, kTwBN);
+  }
 }
 
 // ---------------------------------------------------------------- persistent solver
@@ -257,29 +448,6 @@ struct TpArgs {
 // order, as sb_update_row32: all momenta first (they read the old positions of
 // the ring neighbours), then positions, wall and f, whose e4m3 code goes to
 // column j of the transposed f tile (sFcol[j * 128]).
-// J_perp of the runs of a 32-column chunk.  For P >= 4 (at most 8 runs) the
-// values are read before the accumulator is ready, off the critical path; for
-// P < 4 (16 or 32 runs, which would not fit beside the tile in registers) they
-// are read inside the update.
-template <int P>
-struct KjChunk {
-  static constexpr int kRuns = 32 / (P < 32 ? P : 32);
-  static constexpr bool kEarly = P >= 4;
-  float v[kEarly ? kRuns : 1];
-  const float *kjn;
-  __device__ __forceinline__ void load(const StateView &s, const float *kj_step, int c0) {
-    kjn = kj_step;
-    if constexpr (kEarly) {
-#pragma unroll
-      for (int q = 0; q < kRuns; ++q) v[q] = (c0 + q * P < s.C) ? __ldg(kjn + c0 / P + q) : 0.f;
-    }
-  }
-  __device__ __forceinline__ float get(int c0, int q) const {
-    if constexpr (kEarly) return v[q];
-    else return __ldg(kjn + c0 / P + q);
-  }
-};
-
 template <int P>
 __device__ __forceinline__ void sb_update_regs32(const StateView &s, const StepTables &t, float ka, float dnext,
                                                  const KjChunk<P> &kj, int c0, const uint32_t (&g)[32], float hi,
@@ -585,6 +753,7 @@ bool tc_plan_make(void **plan, const uint8_t *J8, uint8_t *FT, int Kp, int Cp, f
   const auto U8 = CU_TENSOR_MAP_DATA_TYPE_UINT8, F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
   const bool ok = make_map(&p->A, J8, U8, 1, uint64_t(Kp), uint64_t(Kp), 128, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
                   make_map(&p->B, FT, U8, 1, uint64_t(2) * Cp, uint64_t(Kp), 128, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
+                  make_map(&p->B2, FT, U8, 1, uint64_t(2) * Cp, uint64_t(Kp), 128, 256, CU_TENSOR_MAP_SWIZZLE_128B) &&
                   make_map(&p->X, x, F32, 4, uint64_t(N), uint64_t(Cp), 32, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
                   make_map(&p->Y, y, F32, 4, uint64_t(N), uint64_t(Cp), 32, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
                   make_map(&p->Fst, FT, U8, 1, uint64_t(2) * Cp, uint64_t(Kp), 128, 128, CU_TENSOR_MAP_SWIZZLE_NONE);
@@ -609,6 +778,13 @@ cudaError_t tc_set_attributes() {
                         (const void *)k_step_dense_tc<16>, (const void *)k_step_dense_tc<32>};
   for (const void *f : fns) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    if (e != cudaSuccess) return e;
+  }
+  const void *wide[6] = {(const void *)k_step_dense_tc_wide<1>, (const void *)k_step_dense_tc_wide<2>,
+                         (const void *)k_step_dense_tc_wide<4>, (const void *)k_step_dense_tc_wide<8>,
+                         (const void *)k_step_dense_tc_wide<16>, (const void *)k_step_dense_tc_wide<32>};
+  for (const void *f : wide) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kTwSmem);
     if (e != cudaSuccess) return e;
   }
   for (const void *f : kTpFns) {
@@ -655,8 +831,13 @@ cudaError_t launch_solve_dense_tc_persistent(const void *plan, const StateView &
 template <int P>
 static cudaError_t launch_tc_p(const TcMaps *p, const StateView &s, const TcArgs &a, const StepTables &t, int n,
                                cudaStream_t st) {
-  dim3 grid(s.Cp / kTcBN, a.Kp / kTcBM);
-  k_step_dense_tc<P><<<grid, kTcThreads, kTcSmem, st>>>(*p, s, a, t, n);
+  if (s.Cp % kTwBN == 0) {
+    dim3 grid(s.Cp / kTwBN, a.Kp / kTcBM);
+    k_step_dense_tc_wide<P><<<grid, kTcThreads, kTwSmem, st>>>(*p, s, a, t, n);
+  } else {
+    dim3 grid(s.Cp / kTcBN, a.Kp / kTcBM);
+    k_step_dense_tc<P><<<grid, kTcThreads, kTcSmem, st>>>(*p, s, a, t, n);
+  }
   return cudaGetLastError();
 }
 

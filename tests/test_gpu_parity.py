@@ -215,9 +215,13 @@ def test_persistent_dense_tc_solver_resume(sb):
     assert np.array_equal(xa, xb) and np.array_equal(ya, yb)
 
 
-def test_per_step_dense_tensor_core_sk(sb):
-    pb, spec = sk(384, 3)
-    wx, wy, _, _ = _per_step(sb, pb, spec, 32, 4, 1000, 40, prec="exact")
+@pytest.mark.parametrize("N,P,R", [(384, 32, 4), (300, 16, 12), (520, 32, 16)])
+def test_per_step_dense_tensor_core_sk(sb, N, P, R):
+    """Per-step tcgen05 kernels against the oracle step by step: 128-column
+    tiles (R * P = 128) and 256-column tiles (R * P = 192 in a padded 256,
+    ragged; 512 in two tiles), ragged spin rows (N = 300, 520)."""
+    pb, spec = sk(N, 3)
+    wx, wy, _, _ = _per_step(sb, pb, spec, P, R, 1000, 40, prec="exact")
     assert wx <= TOL_STEP and wy <= TOL_STEP
 
 
