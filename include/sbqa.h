@@ -117,7 +117,9 @@ typedef struct {
                              for all steps), 5 the persistent dense tcgen05
                              solver (x, y resident in tensor memory), 6 CSR
                              and 7 dense CUDA cores for the ballistic form
-                             f(x) = x; -1 none                             */
+                             f(x) = x, 8 the persistent dense tcgen05
+                             solver with its K loop split across the two
+                             CTAs of a cluster (128 x 256 tiles); -1 none  */
     int32_t step_variant; /* CSR kernel variant picked by the autotuner:
                              0-5: 4 << (v % 3) consecutive replica columns
                              per lane, v >= 3 with one wave of blocks
@@ -165,7 +167,11 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info);
  *                per-step CSR kernel variant v (see step_variant); 11 forces
  *                the persistent CSR solver in the mode that caches whole
  *                rows (otherwise taken only when the items outnumber its
- *                cache).  Results are identical whichever kernel runs.
+ *                cache); 12 = as 2, but the dense tensor-core solver keeps
+ *                its 128 x 128 tiles instead of splitting the K loop across
+ *                2-CTA clusters (taken by default when padded N and padded
+ *                R*P are multiples of 256).  Results are identical
+ *                whichever kernel runs.
  *   beta, alpha  host, n_runs doubles each: per-run inverse temperature and
  *                schedule exponent (the auto-tuning draws them from
  *                [0.5,1.5] x [0.5,1.0]); beta > 0, alpha > 0

@@ -469,7 +469,7 @@ struct TuneKey {
 };
 struct TuneResult {
   int csr_variant = 0;
-  bool use_persistent = false, use_tc_persistent = false;
+  bool use_persistent = false, use_tc_persistent = false, use_tc_split = false;
   float variant_ms[8] = {};
   float persistent_ms = 0.f, tc_step_ms = 0.f, tc_persistent_ms = 0.f;
 };
@@ -556,7 +556,8 @@ int autotune_csr(sbqa_problem *p) {
   p->use_persistent = false;
   p->persistent_ms = 0.f;
   if (p->persist_blocks == 0) p->persist_blocks = persistent_blocks();
-  if ((p->prm.kernel_select == 2 || p->prm.kernel_select == 11) && p->S > 0 && p->persistent_ok()) {
+  if ((p->prm.kernel_select == 2 || p->prm.kernel_select == 11 || p->prm.kernel_select == 12) && p->S > 0 &&
+      p->persistent_ok()) {
     SBQA_CUDA(p->d_bar.alloc(persistent_barrier_words()));
     p->use_persistent = true;
   } else if (p->prm.kernel_select == 0 && p->S > 0 && p->persistent_ok()) {
@@ -591,67 +592,100 @@ int autotune_csr(sbqa_problem *p) {
   return SBQA_OK;
 }
 
-// Autotuner of the dense tensor-core path: times the per-step kernel against
-// the persistent solver (same state buffers, before the initial state is
-// written) and keeps the faster; kernel_select 1 or 2 forces one.  Cached
-// per handle, column count, replica count and selection.
+// Steps [n0, n1) of the persistent dense tcgen05 solver, split-K across 2-CTA
+// clusters where eligible.
+cudaError_t launch_tc_persistent(sbqa_problem *p, const StateView &s, int n0, int n1, cudaStream_t st) {
+  if (p->tc_split_ok())
+    return launch_solve_dense_tc_split(p->tc_plan, s, p->Kp, p->d_err.p, p->d_h.p, p->tables, n0, n1,
+                                       p->d_tc_flags.p, st);
+  return launch_solve_dense_tc_persistent(p->tc_plan, s, p->Kp, p->d_err.p, p->d_h.p, p->tables, n0, n1,
+                                          p->d_tc_flags.p, st);
+}
+
+// Autotuner of the dense tensor-core path: times the per-step kernel, the
+// persistent solver with 128 x 128 tiles and, where the instance qualifies,
+// the split-K persistent solver (same state buffers, before the initial state
+// is written) and keeps the fastest.  kernel_select 1 forces the per-step
+// kernel, 2 the persistent solver (split-K where it qualifies), 12 the
+// persistent solver with 128 x 128 tiles.  Cached per handle, column count,
+// replica count and selection, and process-wide per instance shape.
 int autotune_tc(sbqa_problem *p) {
   if (!p->use_tc) {
-    p->use_tc_persistent = false;
+    p->use_tc_persistent = p->use_tc_split = false;
     return SBQA_OK;
   }
   if (p->tc_select_cp == p->Cp && p->tc_select == p->prm.kernel_select && p->tc_select_p == p->P) return SBQA_OK;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   SBQA_CUDA(cudaStreamIsCapturing(p->stream, &cs));
   if (cs != cudaStreamCaptureStatusNone) return SBQA_OK;
-  p->use_tc_persistent = false;
+  p->use_tc_persistent = p->use_tc_split = false;
   p->tc_step_ms = p->tc_persistent_ms = 0.f;
   if (p->tc_persist_blocks == 0) p->tc_persist_blocks = tc_persistent_blocks();
-  if (p->prm.kernel_select != 1 && p->S > 0 && p->tc_persistent_ok()) {
+  if (p->tc_split_blocks < 0) p->tc_split_blocks = tc_split_blocks();
+  const int sel = p->prm.kernel_select;
+  if (sel != 1 && p->S > 0 && p->tc_persistent_ok()) {
     SBQA_CUDA(p->d_tc_flags.alloc(tc_persistent_flag_count(p->Kp, p->Cp)));
+    if (p->tc_split_possible()) {
+      // a cluster launch the device refuses (not a fault) leaves the plain persistent solver
+      p->use_tc_split = true;
+      if (launch_tc_persistent(p, p->state(), 0, 0, p->stream) != cudaSuccess) {
+        cudaGetLastError();
+        p->tc_split_failed = true;
+      }
+      p->use_tc_split = false;
+    }
     TuneResult known;
-    if (p->prm.kernel_select == 2) {
+    if (sel == 2 || sel == 12) {
       p->use_tc_persistent = true;
+      p->use_tc_split = sel == 2 && p->tc_split_possible();
     } else if (tune_lookup(p, &known)) {
       p->use_tc_persistent = known.use_tc_persistent;
+      p->use_tc_split = known.use_tc_split;
       p->tc_step_ms = known.tc_step_ms;
       p->tc_persistent_ms = known.tc_persistent_ms;
     } else {
       const StateView s = p->state();
-      cudaEvent_t e0, e1;
-      SBQA_CUDA(cudaEventCreate(&e0));
-      SBQA_CUDA(cudaEventCreate(&e1));
-      const int reps = 8, steps = std::min(p->S, 64);
       float ms = 0.f;
       const int rc = time_per_launch_in_graph(
-          p, reps,
+          p, 8,
           [&](cudaStream_t st) {
             return launch_step_dense_tc(p->tc_plan, s, p->Kp, p->d_FT.p, p->d_err.p, p->d_h.p, p->tables, 0, st);
           },
           &ms);
-      if (rc != SBQA_OK) {
+      if (rc != SBQA_OK) return rc;
+      p->tc_step_ms = ms;
+      // the persistent candidates: 128 x 128 tiles, then split-K where it qualifies
+      const int steps = std::min(p->S, 64);
+      float best_persistent = 0.f;
+      bool best_split = false;
+      for (int split = 0; split < (p->tc_split_possible() ? 2 : 1); ++split) {
+        p->use_tc_split = split == 1;
+        cudaEvent_t e0, e1;
+        SBQA_CUDA(cudaEventCreate(&e0));
+        SBQA_CUDA(cudaEventCreate(&e1));
+        cudaError_t e = launch_tc_persistent(p, s, 0, std::min(p->S, 4), p->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, p->stream);
+        if (e == cudaSuccess) e = launch_tc_persistent(p, s, 0, steps, p->stream);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        return rc;
+        SBQA_CUDA(e);
+        if (split == 0 || ms / steps < best_persistent) {
+          best_persistent = ms / steps;
+          best_split = split == 1;
+        }
       }
-      p->tc_step_ms = ms;
-      SBQA_CUDA(launch_solve_dense_tc_persistent(p->tc_plan, s, p->Kp, p->d_err.p, p->d_h.p, p->tables, 0,
-                                                 std::min(p->S, 4), p->d_tc_flags.p, p->stream));
-      SBQA_CUDA(cudaEventRecord(e0, p->stream));
-      SBQA_CUDA(launch_solve_dense_tc_persistent(p->tc_plan, s, p->Kp, p->d_err.p, p->d_h.p, p->tables, 0, steps,
-                                                 p->d_tc_flags.p, p->stream));
-      SBQA_CUDA(cudaEventRecord(e1, p->stream));
-      SBQA_CUDA(cudaEventSynchronize(e1));
-      SBQA_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      p->tc_persistent_ms = ms / steps;
+      p->use_tc_split = best_split;
+      p->tc_persistent_ms = best_persistent;
       p->use_tc_persistent = p->tc_persistent_ms < p->tc_step_ms;
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
       int err = 0;
       SBQA_CUDA(cudaMemcpy(&err, p->d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
       if (err != 0) return fail(SBQA_ERR_TIMEOUT, "a bounded device wait gave up (code " + std::to_string(err) + ")");
       TuneResult r;
       r.use_tc_persistent = p->use_tc_persistent;
+      r.use_tc_split = p->use_tc_split;
       r.tc_step_ms = p->tc_step_ms;
       r.tc_persistent_ms = p->tc_persistent_ms;
       tune_store(p, r);
@@ -681,8 +715,7 @@ cudaError_t issue_range(sbqa_problem *p, int n0, int n1, cudaStream_t st) {
     while (n < n1) {
       int stop = n1;
       if (K > 0) stop = std::min(n1, (n / K + 1) * K);
-      cudaError_t e = tc_persist ? launch_solve_dense_tc_persistent(p->tc_plan, p->state(), p->Kp, p->d_err.p,
-                                                                    p->d_h.p, p->tables, n, stop, p->d_tc_flags.p, st)
+      cudaError_t e = tc_persist ? launch_tc_persistent(p, p->state(), n, stop, st)
                                  : launch_solve_csr_persistent(p->state(), p->csr(), p->tables, n, stop, p->d_bar.p,
                                                                p->d_err.p, p->persist_blocks, p->persist_mode(), st);
       if (e != cudaSuccess) return e;
@@ -967,7 +1000,7 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info) {
   info->step_kernel = !p->begun ? -1
                      : p->ballistic() ? (p->dense ? 7 : 6)
                                  : (p->small_path ? 3
-                                                  : (p->use_tc ? (p->use_tc_persistent && p->tc_persistent_ok() ? 5 : 2)
+                                                  : (p->use_tc ? (p->use_tc_persistent && p->tc_persistent_ok() ? (p->tc_split_ok() ? 8 : 5) : 2)
                                                                : (p->dense ? 1 : (p->use_persistent ? 4 : 0))));
   info->persistent_ms = p->use_tc ? p->tc_persistent_ms : p->persistent_ms;
   info->step_variant = p->dense ? -1 : p->csr_variant;
@@ -987,7 +1020,7 @@ int sbqa_set_schedule(sbqa_problem *p, const sbqa_params *q) {
   if (q->precision == SBQA_PREC_EXACT && (!p->j_integer || p->max_abs_j > 16))
     return fail(SBQA_ERR_UNSUPPORTED, "EXACT precision needs integer J with |J_ij| <= 16");
   if (q->eval_every < 0 || q->n_runs < 0) return fail(SBQA_ERR_INVALID_ARG, "negative eval_every or n_runs");
-  if (q->kernel_select < 0 || q->kernel_select > 11) return fail(SBQA_ERR_INVALID_ARG, "kernel_select must be 0..11");
+  if (q->kernel_select < 0 || q->kernel_select > 12) return fail(SBQA_ERR_INVALID_ARG, "kernel_select must be 0..12");
   if (q->n_runs > 0 && (!q->beta || !q->alpha)) return fail(SBQA_ERR_INVALID_ARG, "beta/alpha missing");
   std::vector<double> beta, alpha;
   if (q->n_runs > 0) {

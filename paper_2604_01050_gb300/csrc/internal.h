@@ -109,6 +109,14 @@ cudaError_t launch_solve_csr_persistent(const StateView &s, const CsrView &J, co
 int tc_persistent_blocks();
 bool tc_persistent_eligible(int Kp, int Cp, int blocks);
 size_t tc_persistent_flag_count(int Kp, int Cp);
+// The same with the K loop split across the two CTAs of a cluster (128 x 256
+// output tiles; Kp and Cp multiples of 256); blocks = co-resident CTAs in
+// 2-CTA clusters (tc_split_blocks()).
+int tc_split_blocks();
+bool tc_split_eligible(int Kp, int Cp, int blocks);
+cudaError_t launch_solve_dense_tc_split(const void *plan, const StateView &s, int Kp, int *err, const float *h,
+                                        const StepTables &t, int n_begin, int n_end, uint32_t *flags,
+                                        cudaStream_t st);
 cudaError_t launch_solve_dense_tc_persistent(const void *plan, const StateView &s, int Kp, int *err, const float *h,
                                              const StepTables &t, int n_begin, int n_end, uint32_t *flags,
                                              cudaStream_t st);

@@ -117,6 +117,9 @@ struct sbqa_problem {
   bool use_tc_persistent = false;
   float tc_step_ms = 0.f, tc_persistent_ms = 0.f;
   int tc_persist_blocks = 0;
+  int tc_split_blocks = -1;      // co-resident CTAs in 2-CTA clusters (-1: not queried yet)
+  bool tc_split_failed = false;  // the cluster launch was refused: plain persistent solver
+  bool use_tc_split = false;     // the persistent dense solver runs split-K (autotuner's or caller's choice)
   int tc_select_cp = -1, tc_select = -1, tc_select_p = -1;
   sbqa::DevBuf<uint32_t> d_tc_flags;  // per-tile step counters of the persistent solver
   sbqa::DevBuf<float> d_x, d_y;
@@ -155,6 +158,13 @@ struct sbqa_problem {
   bool tc_persistent_ok() const {
     return use_tc && tc_plan && sbqa::tc_persistent_eligible(Kp, Cp, tc_persist_blocks);
   }
+
+  // the instance qualifies for the split-K persistent solver on 2-CTA clusters
+  bool tc_split_possible() const {
+    return tc_persistent_ok() && prm.kernel_select != 12 && !tc_split_failed &&
+           sbqa::tc_split_eligible(Kp, Cp, tc_split_blocks);
+  }
+  bool tc_split_ok() const { return use_tc_split && tc_split_possible(); }
 
   int persist_mode() const {
     return sbqa::persistent_mode(n, Cp, max_degree, kind, persist_blocks, prm.kernel_select == 11);

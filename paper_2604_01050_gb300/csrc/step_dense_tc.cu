@@ -712,6 +712,296 @@ __global__ void __launch_bounds__(kTpThreads, 1)
   }
 }
 
+// ---------------------------------------------------------------- split-K persistent solver
+// The persistent solver for Cp and Kp multiples of 256, with the K loop at the
+// MMA rate: a cluster of two CTAs owns one 128 x 256 output tile (spin rows
+// m0.., replica columns n0..); CTA r of the pair runs M=128 N=256 MMAs over
+// half r of the spins j (k-blocks r KB/2 ..), so both keep 256 partial sums
+// per row in TMEM (columns 0-255).  CTA r then finishes columns n0 + 128 r ..
+// + 127: it stages the partial sums of the other half in its freed operand
+// stages and sends them with one bulk copy into the peer's shared memory
+// (completing on the peer's recv_full mbarrier), adds the peer's partial sums
+// of its own half, and updates x and y, which stay in TMEM (columns 256-383
+// and 384-511).  The f tiles are published
+// with per-(row tile, 128-column half) step counters as in the solver above,
+// and a producer waits for both halves of each k-block it loads.  The sum of
+// two exact integer partial sums is the same integer, so the result is bit for
+// bit that of the other kernels.  Flow control: a CTA re-arms recv_full and
+// then arrives on its peer's send_ok once it has read its receive buffer, and
+// sends step q only after send_ok completed phase q; it arrives on its peer's
+// stage_free once the peer's copy has landed, and its producer loads the
+// next step's operands only after stage_free completed the phase of the step
+// before.  Every wait is bounded; a CTA that gives up records an error and
+// both stop at their next step boundary.
+constexpr int kSkStages = 3;
+constexpr int kSkThreads = 512;
+constexpr int kSkStageBytes = kTcTile + kTwTileB;  // 48 KB: A 128 x 128, B 256 x 128 (e4m3)
+constexpr int kSkRecv = kTcBM * kTcBN * 4;          // the peer's partial sums of this CTA's half (64 KB)
+constexpr int kSkSmem = kSkStages * kSkStageBytes + kSkRecv + kTcBM * kTcBN + 1024 + 256;
+static_assert(kSkSmem <= 227 * 1024, "split-K tile exceeds the shared memory of one CTA");
+constexpr uint32_t kSkTmemX = 256, kSkTmemY = 384;
+
+// Byte offset of the 16-byte chunk ch (0..31) of row r in the receive buffer
+// (rows of 512 bytes; chunks permuted within each 128-byte group by r mod 8,
+// so a quarter warp's 16-byte accesses to 8 consecutive rows hit distinct banks).
+__device__ __forceinline__ uint32_t recv_offset(int r, int ch) {
+  return uint32_t(r * 512 + (((ch & ~7) | ((ch & 7) ^ (r & 7))) << 4));
+}
+
+template <int P>
+__global__ void __launch_bounds__(kSkThreads, 1)
+    k_solve_dense_tc_split(const __grid_constant__ TcMaps m, StateView s, TpArgs a, StepTables t) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t *sA = smem;                                  // [3][16 KB]
+  uint8_t *sB = smem + kSkStages * kTcTile;            // [3][32 KB]
+  uint8_t *sR = smem + kSkStages * kSkStageBytes;      // [128 rows][512 B] partial sums from the peer
+  uint8_t *sF = sR + kSkRecv;                          // [128 columns][128 spins] e4m3 f(x_next)
+  uint64_t *full = reinterpret_cast<uint64_t *>(sF + kTcBM * kTcBN);
+  uint64_t *empty = full + kSkStages;
+  uint64_t *done = empty + kSkStages;
+  uint64_t *recv_full = done + 1, *send_ok = recv_full + 1, *stage_free = send_ok + 1;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(stage_free + 1);
+  uint8_t *sS = smem;  // staging of the partial sums sent to the peer (the operand stages, after the MMAs)
+  int *s_abort = reinterpret_cast<int *>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t rank = tc::cluster_ctarank(), peer = rank ^ 1u;
+  const int ct = blockIdx.x >> 1, mt = blockIdx.y;
+  const int m0 = mt * kTcBM, n0 = ct * kTwBN;
+  const int KB = a.Kp / kTcBK, KH = KB / 2, kb_begin = int(rank) * KH, kb_end = kb_begin + KH;
+  const int quarter = warp & 3, chunk = warp >> 2;
+  const int rl = quarter * 32 + lane, i = m0 + rl;
+  const int cl = 32 * chunk, c0 = n0 + kTcBN * int(rank) + cl;
+  const uint32_t lane_off = uint32_t(quarter * 32) << 16;
+  const bool any = a.n_begin < a.n_end;
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kSkStages; ++q) {
+      tc::mbar_init(&full[q], 1);
+      tc::mbar_init(&empty[q], 1);
+    }
+    tc::mbar_init(done, 1);
+    tc::mbar_init(recv_full, 1);
+    tc::mbar_init(send_ok, 1);
+    tc::mbar_init(stage_free, 1);
+    tc::fence_mbar_init();
+    tc::prefetch_tmap(&m.A);
+    tc::prefetch_tmap(&m.B2);
+    tc::prefetch_tmap(&m.Fst);
+    *s_abort = 0;
+  }
+  if (warp == 0) tc::tmem_alloc(tmem_slot, kTmemCols);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  {  // this CTA's half of the state tile into TMEM (rows past N hold zeros and stay unchanged)
+    uint32_t xr[32], yr[32];
+    if (i < s.N) {
+      const float4 *px = reinterpret_cast<const float4 *>(s.x + size_t(i) * s.Cp + c0);
+      const float4 *py = reinterpret_cast<const float4 *>(s.y + size_t(i) * s.Cp + c0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float4 vx = px[u], vy = py[u];
+        xr[4 * u] = __float_as_uint(vx.x); xr[4 * u + 1] = __float_as_uint(vx.y);
+        xr[4 * u + 2] = __float_as_uint(vx.z); xr[4 * u + 3] = __float_as_uint(vx.w);
+        yr[4 * u] = __float_as_uint(vy.x); yr[4 * u + 1] = __float_as_uint(vy.y);
+        yr[4 * u + 2] = __float_as_uint(vy.z); yr[4 * u + 3] = __float_as_uint(vy.w);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) xr[j] = yr[j] = 0u;
+    }
+    __syncwarp();
+    tc::tmem_st_32x32b_x32(tmem + lane_off + kSkTmemX + cl, xr);
+    tc::tmem_st_32x32b_x32(tmem + lane_off + kSkTmemY + cl, yr);
+    tc::tmem_wait_st();
+  }
+  const float hi = i < s.N ? __ldg(a.h + i) : 0.f;
+  if (threadIdx.x == 0 && any) tc::mbar_arrive_expect_tx(recv_full, kSkRecv);  // receive step 0
+  tc::tc_fence_before();
+  tc::cluster_sync();  // both CTAs' barriers initialised, receive buffers armed
+  tc::tc_fence_after();
+  const uint32_t r_recv = tc::map_to_rank(tc::smem_u32(sR), peer);
+  const uint32_t r_full = tc::map_to_rank(tc::smem_u32(recv_full), peer);
+  const uint32_t r_ok = tc::map_to_rank(tc::smem_u32(send_ok), peer);
+  const uint32_t r_free = tc::map_to_rank(tc::smem_u32(stage_free), peer);
+  if (threadIdx.x == 0 && any) tc::mbar_arrive_remote(r_ok);  // the peer may send step 0
+
+  constexpr uint32_t idesc = tc::idesc_f8_e4m3(kTcBM, kTwBN);
+  int n = a.n_begin;
+  for (; n < a.n_end; ++n) {
+    const uint32_t q = uint32_t(n - a.n_begin);
+    if (warp == 0) {
+      // producer: k-blocks of this half as both 128-column f tiles of their row tile are published
+      const int brow = (n & 1) * s.Cp + n0;
+      uint64_t t0 = 0;
+      uint32_t polls = 0;
+      int kb = kb_begin;
+      while (kb < kb_end) {
+        const int kq = kb + (lane >> 1);
+        const bool ok = q == 0 || kq >= kb_end ||
+                        tc::ld_acquire_gpu(a.flags + kq * a.Ct + 2 * ct + (lane & 1)) >= q;
+        const unsigned ball = __ballot_sync(0xffffffffu, ok);
+        int nready = (ball == 0xffffffffu ? 32 : __ffs(~ball) - 1) >> 1;
+        nready = nready < kb_end - kb ? nready : kb_end - kb;
+        if (nready == 0) {
+          int give_up = 0;
+          if (lane == 0) {
+            const uint64_t now = tc::globaltimer_ns();
+            if (t0 == 0) t0 = now;
+            if (*reinterpret_cast<volatile int *>(a.err) != 0) {
+              give_up = 1;
+            } else if (now - t0 > kFlagTimeoutNs || ++polls > (1u << 26)) {
+              atomicCAS(a.err, 0, tc::ERR_WAIT_FLAG);
+              give_up = 1;
+            }
+          }
+          if (__shfl_sync(0xffffffffu, give_up, 0)) {
+            nready = kb_end - kb;  // proceed with whatever the buffer holds; the run reports the error
+          } else {
+            __nanosleep(64);
+            continue;
+          }
+        }
+        if (lane == 0) {
+          asm volatile("fence.acq_rel.gpu;" ::: "memory");
+          tc::fence_proxy_async_global();
+          // the staging of the step before must have reached the peer before the stages are reloaded
+          if (kb == kb_begin && q > 0) tc::mbar_wait_cluster(stage_free, (q - 1) & 1, a.err, tc::ERR_WAIT_PEER);
+          for (int j = kb; j < kb + nready; ++j) {
+            const uint32_t g = q * KH + (j - kb_begin), st = g % kSkStages, use = g / kSkStages;
+            if (use > 0) tc::mbar_wait(&empty[st], (use - 1) & 1, a.err, tc::ERR_WAIT_EMPTY);
+            tc::mbar_arrive_expect_tx(&full[st], kSkStageBytes);
+            tc::tma_load_2d(sA + st * kTcTile, &m.A, &full[st], j * kTcBK, m0);
+            tc::tma_load_2d(sB + st * kTwTileB, &m.B2, &full[st], j * kTcBK, brow);
+          }
+        }
+        __syncwarp();
+        kb += nready;
+      }
+    } else if (warp == 1 && lane == 0) {
+      for (int j = 0; j < KH; ++j) {
+        const uint32_t g = q * KH + j, st = g % kSkStages, use = g / kSkStages;
+        tc::mbar_wait(&full[st], use & 1, a.err, tc::ERR_WAIT_FULL);
+        tc::tc_fence_after();
+        const uint32_t a0 = tc::smem_u32(sA + st * kTcTile), b0 = tc::smem_u32(sB + st * kTwTileB);
+#pragma unroll
+        for (int kk = 0; kk < kTcBK / 32; ++kk)
+          tc::mma_f8(tmem, tc::smem_desc_sw128(a0 + kk * 32), tc::smem_desc_sw128(b0 + kk * 32), idesc,
+                     (j | kk) != 0 ? 1u : 0u);
+        tc::mma_commit(&empty[st]);
+      }
+      tc::mma_commit(done);
+    }
+    __syncwarp();
+    const float ka = __ldg(t.ka + n), dnext = __ldg(t.dl + n + 1);
+    KjChunk<P> kj;
+    kj.load(s, t.kj + size_t(n) * t.R, c0);
+    tc::mbar_wait(done, q & 1, a.err, tc::ERR_WAIT_DONE);
+    tc::tc_fence_after();
+    {  // the peer's half of the partial sums, staged in the receive buffer's layout
+      uint32_t gp[32];
+      tc::tmem_ld_32x32b_x32_nowait(tmem + lane_off + kTcBN * peer + cl, gp);
+      tc::tmem_wait_ld();
+      tc::reg_fence(gp);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        *reinterpret_cast<uint4 *>(sS + recv_offset(rl, chunk * 8 + u)) =
+            make_uint4(gp[4 * u], gp[4 * u + 1], gp[4 * u + 2], gp[4 * u + 3]);
+    }
+    tc::fence_proxy_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (threadIdx.x == 0 && tc::mbar_wait_cluster(send_ok, q & 1, a.err, tc::ERR_WAIT_PEER)) {
+      // one bulk copy into the peer's receive buffer, completing on its recv_full
+      for (int c = 0; c < 4; ++c)
+        tc::bulk_copy_to_peer(r_recv + c * (kSkRecv / 4), sS + c * (kSkRecv / 4), kSkRecv / 4, r_full);
+    }
+    {
+      uint32_t g[32], xr[32], yr[32];
+      tc::tmem_ld_32x32b_x32_nowait(tmem + lane_off + kTcBN * rank + cl, g);
+      tc::tmem_ld_32x32b_x32_nowait(tmem + lane_off + kSkTmemX + cl, xr);
+      tc::tmem_ld_32x32b_x32_nowait(tmem + lane_off + kSkTmemY + cl, yr);
+      tc::tmem_wait_ld();
+      tc::reg_fence(g);
+      tc::reg_fence(xr);
+      tc::reg_fence(yr);
+      const bool got = tc::mbar_wait_cluster(recv_full, q & 1, a.err, tc::ERR_WAIT_PEER);
+      if (threadIdx.x == 32) tc::mbar_arrive_remote(r_free);  // the peer's staging has been copied
+      if (got) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const float4 v = *reinterpret_cast<const float4 *>(sR + recv_offset(rl, chunk * 8 + u));
+          g[4 * u] = __float_as_uint(__uint_as_float(g[4 * u]) + v.x);
+          g[4 * u + 1] = __float_as_uint(__uint_as_float(g[4 * u + 1]) + v.y);
+          g[4 * u + 2] = __float_as_uint(__uint_as_float(g[4 * u + 2]) + v.z);
+          g[4 * u + 3] = __float_as_uint(__uint_as_float(g[4 * u + 3]) + v.w);
+        }
+      }
+      uint8_t *sFcol = sF + cl * kTcBM + rl;
+      if (i < s.N && c0 < s.C) {
+        sb_update_regs32<P>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, sFcol);
+      } else {
+#pragma unroll
+        for (int j = 0; j < 32; ++j) sFcol[j * kTcBM] = 0;
+      }
+      __syncwarp();
+      tc::tmem_st_32x32b_x32(tmem + lane_off + kSkTmemX + cl, xr);
+      tc::tmem_st_32x32b_x32(tmem + lane_off + kSkTmemY + cl, yr);
+      tc::tmem_wait_st();
+    }
+    tc::fence_proxy_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      // publish f_{n+1} of this half: spins m0.., columns n0 + 128 rank.. of the other FT buffer
+      tc::tma_store_2d(&m.Fst, sF, m0, ((n + 1) & 1) * s.Cp + n0 + kTcBN * int(rank));
+      tc::tma_store_commit_and_wait_all();
+      tc::fence_proxy_async_global();
+      tc::st_release_gpu(a.flags + mt * a.Ct + 2 * ct + int(rank), q + 1);
+      if (n + 1 < a.n_end) {
+        // the receive buffer has been read: arm it for the next step, then let the peer send
+        tc::mbar_arrive_expect_tx(recv_full, kSkRecv);
+        tc::mbar_arrive_remote(r_ok);
+      }
+      *s_abort = *reinterpret_cast<volatile int *>(a.err);
+    }
+    __syncthreads();
+    tc::tc_fence_after();
+    if (*s_abort != 0) break;
+  }
+  {  // this CTA's half of the state tile back to global memory
+    uint32_t xr[32], yr[32];
+    tc::tmem_ld_32x32b_x32_nowait(tmem + lane_off + kSkTmemX + cl, xr);
+    tc::tmem_ld_32x32b_x32_nowait(tmem + lane_off + kSkTmemY + cl, yr);
+    tc::tmem_wait_ld();
+    tc::reg_fence(xr);
+    tc::reg_fence(yr);
+    if (i < s.N) {
+      float4 *px = reinterpret_cast<float4 *>(s.x + size_t(i) * s.Cp + c0);
+      float4 *py = reinterpret_cast<float4 *>(s.y + size_t(i) * s.Cp + c0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        px[u] = make_float4(__uint_as_float(xr[4 * u]), __uint_as_float(xr[4 * u + 1]),
+                            __uint_as_float(xr[4 * u + 2]), __uint_as_float(xr[4 * u + 3]));
+        py[u] = make_float4(__uint_as_float(yr[4 * u]), __uint_as_float(yr[4 * u + 1]),
+                            __uint_as_float(yr[4 * u + 2]), __uint_as_float(yr[4 * u + 3]));
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::cluster_sync();  // no CTA leaves while its peer may still write into its shared memory
+  if (warp == 0) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
 // f codes [N][Cp] -> e4m3 f [Cp][Kp] (zeros for padded spins), for buffer b.
 __global__ void k_f_to_ft8(StateView s, int which, uint8_t *FT, int Kp, int b) {
   const size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x;  // over Cp * Kp
@@ -772,6 +1062,11 @@ static const void *const kTpFns[6] = {
     (const void *)k_solve_dense_tc_persistent<4>, (const void *)k_solve_dense_tc_persistent<8>,
     (const void *)k_solve_dense_tc_persistent<16>, (const void *)k_solve_dense_tc_persistent<32>};
 
+static const void *const kSkFns[6] = {
+    (const void *)k_solve_dense_tc_split<1>, (const void *)k_solve_dense_tc_split<2>,
+    (const void *)k_solve_dense_tc_split<4>, (const void *)k_solve_dense_tc_split<8>,
+    (const void *)k_solve_dense_tc_split<16>, (const void *)k_solve_dense_tc_split<32>};
+
 cudaError_t tc_set_attributes() {
   const void *fns[6] = {(const void *)k_step_dense_tc<1>, (const void *)k_step_dense_tc<2>,
                         (const void *)k_step_dense_tc<4>, (const void *)k_step_dense_tc<8>,
@@ -791,7 +1086,67 @@ cudaError_t tc_set_attributes() {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kTpSmem);
     if (e != cudaSuccess) return e;
   }
+  for (const void *f : kSkFns) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kSkSmem);
+    if (e != cudaSuccess) return e;
+  }
   return cudaSuccess;
+}
+
+static void split_config(cudaLaunchConfig_t *cfg, cudaLaunchAttribute *attr, dim3 grid, cudaStream_t st,
+                         bool cooperative) {
+  *cfg = cudaLaunchConfig_t{};
+  cfg->gridDim = grid;
+  cfg->blockDim = dim3(kSkThreads);
+  cfg->dynamicSmemBytes = kSkSmem;
+  cfg->stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeCooperative;
+  attr[1].val.cooperative = 1;
+  cfg->attrs = attr;
+  cfg->numAttrs = cooperative ? 2 : 1;
+}
+
+int tc_split_blocks() {
+  int best = 1 << 30;
+  for (const void *f : kSkFns) {
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[2];
+    split_config(&cfg, attr, dim3(2, 1), 0, false);
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, f, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    best = clusters < best ? clusters : best;
+  }
+  return 2 * best;
+}
+
+bool tc_split_eligible(int Kp, int Cp, int blocks) {
+  return blocks > 0 && Kp % (2 * kTcBM) == 0 && Cp % kTwBN == 0 && (Kp / kTcBM) * (Cp / kTcBN) <= blocks;
+}
+
+cudaError_t launch_solve_dense_tc_split(const void *plan, const StateView &s, int Kp, int *err, const float *h,
+                                        const StepTables &t, int n_begin, int n_end, uint32_t *flags,
+                                        cudaStream_t st) {
+  const int idx = s.P == 1 ? 0 : s.P == 2 ? 1 : s.P == 4 ? 2 : s.P == 8 ? 3 : s.P == 16 ? 4 : s.P == 32 ? 5 : -1;
+  if (idx < 0 || Kp % (2 * kTcBM) != 0 || s.Cp % kTwBN != 0) return cudaErrorInvalidValue;
+  const int Ct = s.Cp / kTcBN;
+  cudaError_t e = cudaMemsetAsync(flags, 0, tc_persistent_flag_count(Kp, s.Cp) * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  TpArgs a{Kp, Ct, n_begin, n_end, err, h, flags};
+  TcMaps maps = *static_cast<const TcMaps *>(plan);
+  StateView sv = s;
+  StepTables tv = t;
+  void *args[] = {&maps, &sv, &a, &tv};
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[2];
+  split_config(&cfg, attr, dim3(2 * (s.Cp / kTwBN), Kp / kTcBM), st, true);
+  return cudaLaunchKernelExC(&cfg, kSkFns[idx], args);
 }
 
 int tc_persistent_blocks() {

@@ -174,19 +174,30 @@ def test_dense_tensor_core_path_bit_exact_with_cuda_cores(sb, jmax, P, R, sel):
     assert np.array_equal(states[0][0], states[1][0]) and np.array_equal(states[0][1], states[1][1])
 
 
-@pytest.mark.parametrize("N,P,R,jmax", [(300, 8, 40, 3), (512, 16, 16, 1), (1000, 32, 32, 1), (260, 4, 33, 16)])
+def _split_k(N, P, R):
+    """The persistent tcgen05 solver splits its K loop across 2-CTA clusters
+    when padded N and padded R * P are multiples of 256."""
+    pad = lambda v: -(-v // 128) * 128
+    return pad(N) % 256 == 0 and pad(P * R) % 256 == 0
+
+
+@pytest.mark.parametrize("N,P,R,jmax", [(300, 8, 40, 3), (512, 16, 16, 1), (1000, 32, 32, 1), (260, 4, 33, 16),
+                                        (500, 8, 48, 5), (700, 2, 128, 1)])
 def test_persistent_dense_tc_solver_matches_per_step(sb, N, P, R, jmax):
-    """The persistent tcgen05 solver (x, y resident in tensor memory, per-tile
-    step flags between CTAs) and the per-step tcgen05 kernel give
-    bit-identical runs, readouts every 37 steps included; ragged row and
-    column tiles (N = 300, 260; R * P = 320, 132)."""
+    """The persistent tcgen05 solvers (x, y resident in tensor memory, per-tile
+    step flags between CTAs; 128 x 128 tiles, and where padded N and R * P
+    are multiples of 256 the split-K solver on 2-CTA clusters) and the
+    per-step tcgen05 kernel give bit-identical runs, readouts every 37 steps
+    included; ragged row and column tiles (N = 300, 260, 500, 700; R * P =
+    320, 132, 384)."""
     pb, spec = dense_int(N, N + R, jmax=jmax)
     out = []
-    for sel in (1, 2):
+    for sel in (1, 2, 12):
         prob = create(sb, spec)
         sb.set_schedule(prob, *workloads.autotune_params(R, N), **_params(kernel_select=sel, eval_every=37))
         sb.run(prob, 200, P, R, seed=N)
-        assert prob.info().step_kernel == (2 if sel == 1 else 5)
+        want = {1: 2, 2: 8 if _split_k(N, P, R) else 5, 12: 5}[sel]
+        assert prob.info().step_kernel == want
         out.append((sb.get_state(prob)[:2], sb.get_energies(prob), sb.get_best(prob)))
     (xa, ya), ea, ba = out[0]
     for (xb, yb), eb, bb in out[1:]:
@@ -197,10 +208,12 @@ def test_persistent_dense_tc_solver_matches_per_step(sb, N, P, R, jmax):
     _check_best_with_readouts(sb, pb, prob, R, 200, 37)
 
 
-def test_persistent_dense_tc_solver_resume(sb):
-    """Stretches of the persistent tcgen05 solver resumed across
-    begin/advance/finish give the state of one uninterrupted run."""
-    pb, spec = sk(384, 9)
+@pytest.mark.parametrize("N,want", [(384, 5), (512, 8)])
+def test_persistent_dense_tc_solver_resume(sb, N, want):
+    """Stretches of the persistent tcgen05 solvers (128 x 128 tiles at N =
+    384; split-K clusters at N = 512) resumed across begin/advance/finish
+    give the state of one uninterrupted run."""
+    pb, spec = sk(N, 9)
     prob = create(sb, spec)
     sb.set_schedule(prob, *workloads.autotune_params(16, 9), **_params(kernel_select=2))
     sb.run(prob, 150, 16, 16, seed=4)
@@ -211,7 +224,7 @@ def test_persistent_dense_tc_solver_resume(sb):
     sb.run_advance(prob, 500)
     sb.run_finish(prob)
     xb, yb, _ = sb.get_state(prob)
-    assert prob.info().step_kernel == 5
+    assert prob.info().step_kernel == want
     assert np.array_equal(xa, xb) and np.array_equal(ya, yb)
 
 
