@@ -61,8 +61,11 @@ for _n, _S in ((4096, 500), (8192, 200)):
     CONFIGS["sk%d" % _n] = dict(
         kind="sk", n=_n, P=32, R=32, S=_S, prec="exact",
         workload="dense SK N=%d, J=+-1; P=32, R=32 (J.X = %dx%d @ %dx1024), %d steps" % (_n, _n, _n, _n, _S))
+# a tall dense instance (many spins, few replica columns): the persistent solver splits its K loop
+CONFIGS["sk8192t"] = dict(kind="sk", n=8192, P=8, R=32, S=200, prec="exact",
+                          workload="dense SK N=8192, J=+-1; P=8, R=32 (J.X = 8192x8192 @ 8192x256), 200 steps")
 SCALING = ["lattice16", "lattice24", "lattice32", "lattice48", "lattice64", "lattice88", "regular1e5", "regular7e5",
-           "sk2000", "sk4096", "sk8192"]
+           "sk2000", "sk4096", "sk8192", "sk8192t"]
 DEFAULT = "lattice16"
 BYTES_PER_UPDATE = 16  # x, y FP32 read + write per replica-spin update
 BYTES_PER_UPDATE_BSB = 20  # ballistic form: + the FP32 f (= x) write
@@ -698,9 +701,9 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         cpu = oracle_sample(cfg, target_s=args.ref_seconds)
     # init + reset_best (+ the f -> e4m3 conversion on the tensor-core path) + steps + 4 readout kernels
-    tc_conv = 1 if info.step_kernel in (2, 5, 8) else 0
+    tc_conv = 1 if info.step_kernel in (2, 5, 8) else 0  # f codes -> FP8 operand; the readout's sign codes
     launches_per_solve = (1 if info.step_kernel == 3 else
-                          2 + tc_conv + (1 if info.step_kernel in (4, 5, 8) else S) + 4)
+                          2 + tc_conv + (1 if info.step_kernel in (4, 5, 8) else S) + 4 + tc_conv)
     line = {
         "metric": "replica-spin updates/s", "value": value, "unit": "replica-spin updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_solve,

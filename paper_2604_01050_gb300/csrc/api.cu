@@ -699,7 +699,12 @@ int autotune_tc(sbqa_problem *p) {
 
 cudaError_t issue_readout(sbqa_problem *p, int step, cudaStream_t st) {
   const StateView s = p->state();
-  cudaError_t e = p->dense ? launch_energy_dense(s, p->energy(), p->best(), st)
+  // integer dense instances on the tensor cores: the sign codes take the FT
+  // buffer of step `step`, which the next step does not read
+  cudaError_t e = p->dense ? (p->use_tc && p->tc_plan ? launch_energy_dense_tc(p->tc_plan, s, p->Kp, p->d_FT.p,
+                                                                               step & 1, p->d_err.p, p->energy(),
+                                                                               p->best(), st)
+                                                      : launch_energy_dense(s, p->energy(), p->best(), st))
                            : launch_energy_csr(s, p->csr_readout(), p->energy(), p->best(), st);
   if (e != cudaSuccess) return e;
   return launch_best(s, p->energy(), p->best(), step, st);

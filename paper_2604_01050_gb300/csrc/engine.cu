@@ -251,10 +251,12 @@ int readout(sbqa_engine *e, Request &r, cudaStream_t st) {
   sbqa_problem *p = r.prob;
   const StateView s = r.state_view();
   const EnergyView ev = problem_energy_view(p);
-  cudaError_t err = p->dense ? launch_energy_dense(s, ev, r.best_view(), st)
-                             : launch_energy_csr(s, problem_csr_readout_view(p), ev, r.best_view(), st);
+  const bool tc = p->dense && r.tc_plan;
+  cudaError_t err = tc ? launch_energy_dense_tc(r.tc_plan, s, p->Kp, r.FT, (r.S - 1) & 1, r.err, ev, r.best_view(), st)
+                       : p->dense ? launch_energy_dense(s, ev, r.best_view(), st)
+                                  : launch_energy_csr(s, problem_csr_readout_view(p), ev, r.best_view(), st);
   if (err == cudaSuccess) err = launch_best(s, ev, r.best_view(), r.S - 1, st);
-  e->kernels_launched += 4;  // signs, energies, their final sums, best
+  e->kernels_launched += tc ? 5 : 4;  // signs, (sign codes,) energies, their final sums, best
   if (err != cudaSuccess) return set_error(SBQA_ERR_CUDA, std::string("engine readout: ") + cudaGetErrorString(err));
   r.spins.resize(size_t(r.R) * p->n);
   r.energy.resize(r.R);

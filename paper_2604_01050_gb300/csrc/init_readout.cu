@@ -258,6 +258,15 @@ cudaError_t launch_energy_dense(const StateView &s, const EnergyView &E, const B
   return launch_final(s, E, b, st);
 }
 
+cudaError_t launch_energy_dense_tc(const void *plan, const StateView &s, int Kp, uint8_t *FT, int buffer, int *err,
+                                   const EnergyView &E, const BestView &b, cudaStream_t st) {
+  cudaError_t e = launch_sign(s, st);
+  if (e != cudaSuccess) return e;
+  e = launch_energy_partials_tc(plan, s, Kp, FT, buffer, err, E.h_i64, b.part_int, b.nblk, st);
+  if (e != cudaSuccess) return e;
+  return launch_final(s, E, b, st);
+}
+
 // ---------------------------------------------------------------- best per run
 // One warp per run: argmin over the P replicas (lowest k on ties), kept if
 // strictly lower than the best so far; then the spins of the winner.

@@ -199,6 +199,14 @@ cudaError_t launch_step_batched(const SlotDesc *slots, const WorkItem *items, co
                                 cudaStream_t st);
 
 int energy_row_blocks(int N);
+// Readout energies of an integer dense instance on the tensor cores: the sign
+// codes go into FT buffer `buffer` (one the next step does not read), then
+// one FP8 GEMM with the row-block partial sums in its epilogue
+// (step_dense_tc.cu, init_readout.cu).
+cudaError_t launch_energy_partials_tc(const void *plan, const StateView &s, int Kp, uint8_t *FT, int b, int *err,
+                                      const int64_t *h_i64, int64_t *part, int nblk, cudaStream_t st);
+cudaError_t launch_energy_dense_tc(const void *plan, const StateView &s, int Kp, uint8_t *FT, int buffer, int *err,
+                                   const EnergyView &E, const BestView &b, cudaStream_t st);
 // sign(x) into Sg, energies of every column into b.e_int / b.e_f64.
 cudaError_t launch_energy_csr(const StateView &s, const CsrView &J, const EnergyView &E,
                               const BestView &b, cudaStream_t st);

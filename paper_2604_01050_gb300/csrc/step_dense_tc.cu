@@ -767,6 +767,11 @@ __global__ void __launch_bounds__(kSkThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t rank = tc::cluster_ctarank(), peer = rank ^ 1u;
+  if (tc::cluster_nctarank() != 2 || rank != (blockIdx.x & 1u)) {
+    // not launched as pairs of CTAs (every access to a peer would be invalid): report, touch nothing
+    if (threadIdx.x == 0) atomicCAS(a.err, 0, tc::ERR_CLUSTER_SHAPE);
+    return;
+  }
   const int ct = blockIdx.x >> 1, mt = blockIdx.y;
   const int m0 = mt * kTcBM, n0 = ct * kTwBN;
   const int KB = a.Kp / kTcBK, KH = KB / 2, kb_begin = int(rank) * KH, kb_end = kb_begin + KH;
@@ -1011,6 +1016,133 @@ __global__ void k_f_to_ft8(StateView s, int which, uint8_t *FT, int Kp, int b) {
   FT[size_t(b) * s.Cp * Kp + e] = f_to_e4m3(f);
 }
 
+// ---------------------------------------------------------------- readout on the tensor cores
+// Energies of the readout spins s = sign(x) for every column (Sec. II B):
+// E = -(1/2) s^T J s - h^T s.  With integer J (|J| <= 16) and s in {-1, +1}
+// the product G = J S is the step's GEMM with f = s, exact in FP8 and in the
+// FP32 accumulator (|G_i| <= 16 N).  Each 128 x 128 tile forms, per spin row
+// i and column c, the exact integer s_ic (G_ic + 2 h_i) and sums the 32 rows
+// of each TMEM quarter into the row-block partial part[i / 32][c] that the
+// CUDA-core energy kernel would write; the same fixed-order final kernel
+// then gives E_c = -(sum over blocks) / 2.
+constexpr int kEtStages = 6;
+constexpr int kEtSmem = 2 * kEtStages * kTcTile + 1024 + 128;
+static_assert(16 * 32 * 33 * 8 <= 2 * kEtStages * kTcTile, "row reductions must fit the operand stages");
+
+// sign codes S [N][Cp] (+1, -1, 0 past C) -> e4m3 [Cp][Kp] in FT buffer b (zeros for padded spins)
+__global__ void k_sign_to_ft8(StateView s, uint8_t *FT, int Kp, int b) {
+  const size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x;  // over Cp * Kp
+  if (e >= size_t(s.Cp) * Kp) return;
+  const int c = int(e / Kp), j = int(e % Kp);
+  const int8_t v = (j < s.N) ? s.Sg[size_t(j) * s.Cp + c] : int8_t(0);
+  FT[size_t(b) * s.Cp * Kp + e] = f_to_e4m3(v);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_energy_dense_tc(const __grid_constant__ TcMaps m, StateView s, int Kp, int b, int *err, const int64_t *h_i64,
+                      int64_t *part, int nblk) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + kEtStages * kTcTile;
+  uint64_t *full = reinterpret_cast<uint64_t *>(sB + kEtStages * kTcTile);
+  uint64_t *empty = full + kEtStages;
+  uint64_t *done = empty + kEtStages;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * kTcBN;
+  const int KB = Kp / kTcBK;
+  const int brow = b * s.Cp + n0;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kEtStages; ++q) {
+      tc::mbar_init(&full[q], 1);
+      tc::mbar_init(&empty[q], 1);
+    }
+    tc::mbar_init(done, 1);
+    tc::fence_mbar_init();
+    tc::prefetch_tmap(&m.A);
+    tc::prefetch_tmap(&m.B);
+  }
+  if (warp == 0) tc::tmem_alloc(tmem_slot, 128);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  if (warp == 0 && lane == 0) {
+    for (int kb = 0; kb < KB; ++kb) {
+      const int st = kb % kEtStages, q = kb / kEtStages;
+      if (q > 0 && !tc::mbar_wait(&empty[st], (q - 1) & 1, err, tc::ERR_WAIT_EMPTY)) break;
+      tc::mbar_arrive_expect_tx(&full[st], 2 * kTcTile);
+      tc::tma_load_2d(sA + st * kTcTile, &m.A, &full[st], kb * kTcBK, m0);
+      tc::tma_load_2d(sB + st * kTcTile, &m.B, &full[st], kb * kTcBK, brow);
+    }
+  } else if (warp == 1 && lane == 0) {
+    constexpr uint32_t idesc = tc::idesc_f8_e4m3(kTcBM, kTcBN);
+    for (int kb = 0; kb < KB; ++kb) {
+      const int st = kb % kEtStages, q = kb / kEtStages;
+      if (!tc::mbar_wait(&full[st], q & 1, err, tc::ERR_WAIT_FULL)) break;
+      tc::tc_fence_after();
+      const uint32_t a0 = tc::smem_u32(sA + st * kTcTile), b0 = tc::smem_u32(sB + st * kTcTile);
+#pragma unroll
+      for (int kk = 0; kk < kTcBK / 32; ++kk)
+        tc::mma_f8(tmem, tc::smem_desc_sw128(a0 + kk * 32), tc::smem_desc_sw128(b0 + kk * 32), idesc,
+                   (kb | kk) != 0 ? 1u : 0u);
+      tc::mma_commit(&empty[st]);
+    }
+    tc::mma_commit(done);
+  }
+  __syncwarp();
+  const int quarter = warp & 3, chunk = warp >> 2;
+  const int i = m0 + quarter * 32 + lane, c0 = n0 + 32 * chunk;
+  int8_t si[32];
+  int64_t h2 = 0;
+  if (i < s.N) {
+    const uint4 *ps = reinterpret_cast<const uint4 *>(s.Sg + size_t(i) * s.Cp + c0);
+    const uint4 u0 = ps[0], u1 = ps[1];
+    const uint32_t w[8] = {u0.x, u0.y, u0.z, u0.w, u1.x, u1.y, u1.z, u1.w};
+#pragma unroll
+    for (int j = 0; j < 32; ++j) si[j] = int8_t(w[j >> 2] >> (8 * (j & 3)));
+    h2 = 2 * h_i64[i];
+  } else {
+#pragma unroll
+    for (int j = 0; j < 32; ++j) si[j] = 0;
+  }
+  tc::mbar_wait(done, 0, err, tc::ERR_WAIT_DONE);
+  tc::tc_fence_after();
+  uint32_t g[32];
+  tc::tmem_ld_32x32b_x32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(32 * chunk), g);
+  // rows of this warp -> columns: [32 rows][33] int64 per warp in the freed operand stages
+  int64_t *red = reinterpret_cast<int64_t *>(smem) + size_t(warp) * 32 * 33;
+#pragma unroll
+  for (int j = 0; j < 32; ++j)
+    red[lane * 33 + j] = int64_t(si[j]) * (int64_t(__float2int_rn(__uint_as_float(g[j]))) + h2);
+  __syncwarp();
+  int64_t acc = 0;
+#pragma unroll 8
+  for (int r = 0; r < 32; ++r) acc += red[r * 33 + lane];
+  const int blk = m0 / 32 + quarter;
+  if (blk < nblk) part[size_t(blk) * s.Cp + c0 + lane] = acc;
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, 128);
+  }
+}
+
+cudaError_t launch_energy_partials_tc(const void *plan, const StateView &s, int Kp, uint8_t *FT, int b, int *err,
+                                      const int64_t *h_i64, int64_t *part, int nblk, cudaStream_t st) {
+  const size_t total = size_t(s.Cp) * Kp;
+  k_sign_to_ft8<<<unsigned((total + 255) / 256), 256, 0, st>>>(s, FT, Kp, b);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  dim3 grid(s.Cp / kTcBN, Kp / kTcBM);
+  k_energy_dense_tc<<<grid, kTcThreads, kEtSmem, st>>>(*static_cast<const TcMaps *>(plan), s, Kp, b, err, h_i64, part,
+                                                     nblk);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- host side
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -1090,7 +1222,7 @@ cudaError_t tc_set_attributes() {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kSkSmem);
     if (e != cudaSuccess) return e;
   }
-  return cudaSuccess;
+  return cudaFuncSetAttribute((const void *)k_energy_dense_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kEtSmem);
 }
 
 static void split_config(cudaLaunchConfig_t *cfg, cudaLaunchAttribute *attr, dim3 grid, cudaStream_t st,

@@ -12,7 +12,8 @@ namespace tc {
 
 constexpr uint32_t kSpinLimit = 1u << 22;  // polls of mbarrier.try_wait
 
-enum : int { ERR_NONE = 0, ERR_WAIT_FULL = 1, ERR_WAIT_EMPTY = 2, ERR_WAIT_DONE = 3, ERR_WAIT_FLAG = 5, ERR_WAIT_PEER = 6 };
+enum : int { ERR_NONE = 0, ERR_WAIT_FULL = 1, ERR_WAIT_EMPTY = 2, ERR_WAIT_DONE = 3, ERR_WAIT_FLAG = 5, ERR_WAIT_PEER = 6,
+             ERR_CLUSTER_SHAPE = 7 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -50,6 +51,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *e
 }
 
 // ---- 2-CTA clusters (distributed shared memory) ----
+__device__ __forceinline__ uint32_t cluster_nctarank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+  return r;
+}
+
 __device__ __forceinline__ uint32_t cluster_ctarank() {
   uint32_t r;
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));

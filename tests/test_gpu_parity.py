@@ -208,6 +208,31 @@ def test_persistent_dense_tc_solver_matches_per_step(sb, N, P, R, jmax):
     _check_best_with_readouts(sb, pb, prob, R, 200, 37)
 
 
+@pytest.mark.parametrize("N,P,R,jmax", [(300, 8, 5, 3), (700, 16, 24, 16), (260, 32, 4, 1)])
+def test_dense_tensor_core_readout_matches_cuda_cores(sb, N, P, R, jmax):
+    """Readout energies of integer dense instances on the tensor cores (sign
+    codes through one FP8 GEMM, exact integer row sums in its epilogue) equal
+    the CUDA-core readout and the oracle's energies of the final spins, and
+    the best-so-far over readouts every 29 steps agrees (ragged N and R * P,
+    integer h)."""
+    pb, spec = dense_int(N, N + 7, jmax=jmax)
+    res = []
+    for prec in ("exact", "fp32"):
+        prob = create(sb, spec)
+        sb.set_schedule(prob, *workloads.autotune_params(R, 5), **_params(precision=prec, eval_every=29))
+        sb.run(prob, 120, P, R, seed=7)
+        assert (prob.info().step_kernel in (2, 5, 8)) if prec == "exact" else prob.info().step_kernel == 1
+        _, ei = sb.get_energies(prob)
+        x, _, _ = sb.get_state(prob)
+        res.append((ei, sb.get_best(prob), x))
+    (ea, ba, xa), (eb, bb, xb) = res
+    assert np.array_equal(xa, xb)
+    assert np.array_equal(ea, eb)
+    for k in ba:
+        assert np.array_equal(ba[k], bb[k]), k
+    assert np.array_equal(ea, oracle.energies(pb, np.where(xa >= 0, 1, -1)))
+
+
 @pytest.mark.parametrize("N,want", [(384, 5), (512, 8)])
 def test_persistent_dense_tc_solver_resume(sb, N, want):
     """Stretches of the persistent tcgen05 solvers (128 x 128 tiles at N =
