@@ -77,6 +77,7 @@ TRAFFIC_PER_STEP = {
     "lattice16": {"kernel": "k_solve_csr_persistent", "bytes_per_step": (79867392 + 4435043328) // 64},
     "regular1e5": {"kernel": "k_solve_csr_persistent", "bytes_per_step": (7006125056 + 7254420736) // 64},
     "sk2000": {"kernel": "k_solve_dense_tc_persistent", "bytes_per_step": (22741504 + 480512) // 64},
+    "sk4096": {"kernel": "k_step_dense_tc_wide", "bytes_per_step": 54591744 + 488960},
 }
 L2_FLUSH_BYTES = 512 << 20
 

@@ -315,7 +315,11 @@ int prepare_dense_values(sbqa_problem *p, int precision) {
   // the FP8 tensor-core product is exact only for f in {-1, 0, 1}: thresholded form only
   p->use_tc = (precision == SBQA_PREC_AUTO || precision == SBQA_PREC_EXACT) && p->j_integer &&
               p->max_abs_j <= 16 && p->n >= kTcMinN && !p->ballistic();
-  if (p->use_tc) return prepare_tc_values(p);
+  if (p->use_tc) return prepare_tc_values(p);  // the readout runs on the tensor cores too
+  if (!p->d_e_i32.p && !p->d_e_f64.p) {
+    const int rc = upload_readout_values(p);
+    if (rc != SBQA_OK) return rc;
+  }
   const int want = precision == SBQA_PREC_BF16 ? SBQA_PREC_BF16 : SBQA_PREC_FP32;
   if (p->d_dense_f32.p && p->dense_prec == want) return SBQA_OK;
   const size_t m = p->val.size();
@@ -872,9 +876,12 @@ int sbqa_create_problem_dense(int32_t n, const double *J, const double *h, sbqa_
     JStats js;
   };
   std::vector<Block> blocks(nb);
+  HostVec<double> vals;  // the library's copy, filled block by block in the same pass
+  vals.resize(m);
   parallel_tasks(nb, [&](int64_t b, int64_t) {
     Block &B = blocks[b];
     const int i0 = int(b) * kB, i1 = std::min(n, i0 + kB);
+    std::memcpy(vals.data() + size_t(i0) * n, J + size_t(i0) * n, size_t(i1 - i0) * n * sizeof(double));
     for (int i = i0; i < i1; ++i) {
       const double *row = J + size_t(i) * n;
       int32_t d = 0;
@@ -915,13 +922,14 @@ int sbqa_create_problem_dense(int32_t n, const double *J, const double *h, sbqa_
   cudaGetDevice(&p->device);
   p->n = n;
   p->dense = true;
-  p->val.assign(J, J + m);
+  p->val = std::move(vals);
   if (h) p->h.assign(h, h + n);
   p->nnz = nnz;
   p->max_degree = maxdeg;
   finish_analysis(p, js);
+  // the readout values of the CUDA-core energy kernel are uploaded when a
+  // schedule leaves the tensor cores (prepare_dense_values)
   int rc = upload_common(p);
-  if (rc == SBQA_OK) rc = upload_readout_values(p);
   if (rc != SBQA_OK) {
     delete p;
     return rc;

@@ -3,6 +3,8 @@
 #pragma once
 #include <cstdint>
 #include <cstring>
+#include <memory>
+#include <utility>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -11,6 +13,27 @@
 #include "internal.h"
 
 namespace sbqa {
+
+// Allocator that leaves value-initialised elements uninitialised, for host
+// arrays that are filled right after they are sized (a dense J of 8192^2
+// doubles is 512 MB).
+template <typename T>
+struct NoInitAlloc : std::allocator<T> {
+  template <typename U>
+  struct rebind {
+    using other = NoInitAlloc<U>;
+  };
+  NoInitAlloc() = default;
+  template <typename U>
+  NoInitAlloc(const NoInitAlloc<U> &) {}
+  template <typename U, typename... A>
+  void construct(U *q, A &&...a) {
+    if constexpr (sizeof...(A) == 0) ::new (static_cast<void *>(q)) U;
+    else ::new (static_cast<void *>(q)) U(std::forward<A>(a)...);
+  }
+};
+template <typename T>
+using HostVec = std::vector<T, NoInitAlloc<T>>;
 
 template <typename T>
 struct DevBuf {
@@ -58,7 +81,7 @@ struct sbqa_problem {
   // host copies (CSR for sparse, row-major for dense)
   std::vector<int64_t> row_ptr;
   std::vector<int32_t> col;
-  std::vector<double> val;  // CSR values or dense N*N
+  sbqa::HostVec<double> val;  // CSR values or dense N*N
   std::vector<double> h;
 
   // device: product operands
