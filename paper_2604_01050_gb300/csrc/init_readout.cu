@@ -268,46 +268,54 @@ cudaError_t launch_energy_dense_tc(const void *plan, const StateView &s, int Kp,
 }
 
 // ---------------------------------------------------------------- best per run
-// One warp per run: argmin over the P replicas (lowest k on ties), kept if
-// strictly lower than the best so far; then the spins of the winner.
-__global__ void k_best(StateView s, EnergyView E, BestView b, int step) {
+// One block per run: warp 0 takes the argmin over the P replicas (lowest k on
+// ties), kept if strictly lower than the best so far; then all threads copy
+// the winner's spins (a strided gather of N bytes).
+constexpr int kBestThreads = 256;
+
+__global__ void __launch_bounds__(kBestThreads) k_best(StateView s, EnergyView E, BestView b, int step) {
+  __shared__ int s_k;  // the winning replica, or -1 when the run does not improve
   const int r = blockIdx.x;
-  const int lane = threadIdx.x;
+  const int lane = threadIdx.x & 31;
   const int P = s.P;
-  long long ei = LLONG_MAX;
-  double ef = DBL_MAX;
-  int k = lane;
-  if (lane < P) {
-    if (E.is_integer) ei = b.e_int[r * P + lane];
-    else ef = b.e_f64[r * P + lane];
+  if (threadIdx.x < 32) {
+    long long ei = LLONG_MAX;
+    double ef = DBL_MAX;
+    int k = lane;
+    if (lane < P) {
+      if (E.is_integer) ei = b.e_int[r * P + lane];
+      else ef = b.e_f64[r * P + lane];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const long long oi = __shfl_down_sync(0xffffffffu, ei, o);
+      const double of = __shfl_down_sync(0xffffffffu, ef, o);
+      const int ok = __shfl_down_sync(0xffffffffu, k, o);
+      const bool better = E.is_integer ? (oi < ei || (oi == ei && ok < k)) : (of < ef || (of == ef && ok < k));
+      if (better) { ei = oi; ef = of; k = ok; }
+    }
+    if (lane == 0) {
+      const bool have = b.have_best[r] != 0;
+      const bool improve = !have || (E.is_integer ? ei < b.best_e_int[r] : ef < b.best_e[r]);
+      s_k = improve ? k : -1;
+      if (improve) {
+        b.best_e_int[r] = E.is_integer ? ei : 0;
+        b.best_e[r] = E.is_integer ? double(ei) : ef;
+        b.best_k[r] = k;
+        b.best_step[r] = step;
+        b.have_best[r] = 1;
+      }
+    }
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    const long long oi = __shfl_down_sync(0xffffffffu, ei, o);
-    const double of = __shfl_down_sync(0xffffffffu, ef, o);
-    const int ok = __shfl_down_sync(0xffffffffu, k, o);
-    const bool better = E.is_integer ? (oi < ei || (oi == ei && ok < k)) : (of < ef || (of == ef && ok < k));
-    if (better) { ei = oi; ef = of; k = ok; }
-  }
-  ei = __shfl_sync(0xffffffffu, ei, 0);
-  ef = __shfl_sync(0xffffffffu, ef, 0);
-  k = __shfl_sync(0xffffffffu, k, 0);
-  const bool have = b.have_best[r] != 0;
-  const bool improve = !have || (E.is_integer ? ei < b.best_e_int[r] : ef < b.best_e[r]);
-  if (!improve) return;
+  __syncthreads();
+  const int k = s_k;
+  if (k < 0) return;
   const int c = r * P + k;
-  for (int i = lane; i < s.N; i += 32) b.best_spins[size_t(r) * s.N + i] = s.Sg[size_t(i) * s.Cp + c];
-  if (lane == 0) {
-    b.best_e_int[r] = E.is_integer ? ei : 0;
-    b.best_e[r] = E.is_integer ? double(ei) : ef;
-    b.best_k[r] = k;
-    b.best_step[r] = step;
-    b.have_best[r] = 1;
-  }
+  for (int i = threadIdx.x; i < s.N; i += kBestThreads) b.best_spins[size_t(r) * s.N + i] = s.Sg[size_t(i) * s.Cp + c];
 }
 
 cudaError_t launch_best(const StateView &s, const EnergyView &E, const BestView &b, int step,
                         cudaStream_t st) {
-  k_best<<<s.R, 32, 0, st>>>(s, E, b, step);
+  k_best<<<s.R, kBestThreads, 0, st>>>(s, E, b, step);
   return cudaGetLastError();
 }
 
