@@ -248,6 +248,27 @@ def run_serving(args):
         out = serving.run_stream(reqs, f * capacity, stream=stream, seed=int(10 * f))
         loads["%.1fx" % f] = serving.summary(out)
     head = loads["0.8x"]
+    # the batched CSR kernel alone: a closed loop of the lattice requests (no dense work beside it)
+    lat_reqs = [r for r in reqs if r["inst"]["kind"] == "lattice"]
+    csr = serving.run_stream(lat_reqs, None, stream=stream)
+    achieved = BYTES_PER_UPDATE * csr["batched_updates"] / (csr["batched_ms"] * 1e-3) / 1e9
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        peaks = {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+            "traffic": None, "kernel": "k_step_batched",
+            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+            "note": "closed loop of the %d lattice requests alone: algorithmic %d B/update x the updates the "
+                    "batched kernel advanced / its event-timed launches" % (len(lat_reqs), BYTES_PER_UPDATE)}
+    cpu = None
+    if not args.no_cpu_baseline:
+        # the oracle on one typical request (lattice L=16, P=16, R=16, 2000 steps), bounded sample
+        cfg = dict(kind="lattice", L=16, P=16, R=16, S=2000, prec="auto")
+        base = oracle_sample(cfg, target_s=args.ref_seconds)
+        per_req = 16 ** 3 * 16 * 16 * 2000 / base["value"]
+        cpu = dict(base, value=per_req, unit="s per request (lattice L=16, P=16, R=16, 2000 steps)")
     line = {"metric": "p99 solve latency", "value": head["p99_s"], "unit": "s", "n_gpus": 1,
             "steps": len(reqs), "warmup": 6, "ms_per_step": 1e3 * head["mean_s"], "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -256,7 +277,8 @@ def run_serving(args):
                                    "continuous batching engine, chunk 50 steps",
                        "requests": len(reqs), "capacity_req_per_s": capacity,
                        "closed_loop_updates_per_s": closed["updates"] / closed["makespan_s"]},
-            "p50_s": head["p50_s"], "loads": loads, "gpu_launches": head["kernels_launched"]}
+            "p50_s": head["p50_s"], "loads": loads, "gpu_launches": head["kernels_launched"],
+            "roofline": roof, "cpu_baseline": cpu}
     print(json.dumps(line))
     return 0
 

@@ -314,6 +314,11 @@ typedef struct {
     int64_t arena_bytes, arena_used;
     int64_t updates_issued; /* replica-spin updates advanced so far */
     int64_t kernels_launched; /* kernels the engine has launched so far */
+    int64_t batched_updates;  /* replica-spin updates of the CSR requests, advanced
+                                 by the batched step kernel */
+    double batched_ms;        /* device time of those batched launches (CUDA
+                                 events around each chunk's launches; dense
+                                 requests may run beside them) */
 } sbqa_engine_stats_t;
 
 int sbqa_engine_stats(const sbqa_engine *e, sbqa_engine_stats_t *s);

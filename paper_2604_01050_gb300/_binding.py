@@ -62,7 +62,8 @@ class ProblemInfo(ctypes.Structure):
 class EngineStats(ctypes.Structure):
     _fields_ = [("queued", ctypes.c_int32), ("active", ctypes.c_int32), ("finished", ctypes.c_int32),
                 ("arena_bytes", ctypes.c_int64), ("arena_used", ctypes.c_int64),
-                ("updates_issued", ctypes.c_int64), ("kernels_launched", ctypes.c_int64)]
+                ("updates_issued", ctypes.c_int64), ("kernels_launched", ctypes.c_int64),
+                ("batched_updates", ctypes.c_int64), ("batched_ms", ctypes.c_double)]
 
 
 class Params(ctypes.Structure):

@@ -128,6 +128,9 @@ struct sbqa_engine {
   int sms = 0;
   int64_t steps_done_total = 0;  // replica-spin updates issued, for statistics
   int64_t kernels_launched = 0;  // kernels this engine has launched, for statistics
+  int64_t batched_updates = 0;   // updates of CSR requests advanced by the batched kernel
+  double batched_ms = 0.0;       // device time of the batched launches
+  cudaEvent_t batched_t0 = nullptr, batched_t1 = nullptr;
   // dense requests run their chunk on a stream of their slot (created on first
   // use), so small dense problems share the GPU instead of queueing
   std::vector<cudaStream_t> side;
@@ -141,6 +144,8 @@ struct sbqa_engine {
     for (cudaEvent_t x : side_done)
       if (x) cudaEventDestroy(x);
     if (chunk_start) cudaEventDestroy(chunk_start);
+    if (batched_t0) cudaEventDestroy(batched_t0);
+    if (batched_t1) cudaEventDestroy(batched_t1);
     for (auto &r : reqs)
       if (r.tc_plan) tc_plan_free(r.tc_plan);
     if (arena.base) cudaFree(arena.base);
@@ -239,10 +244,12 @@ SlotDesc slot_desc(const Request &r) {
   const CsrView v = problem_csr_view(p);
   SlotDesc d{};
   d.row_ptr = v.row_ptr; d.col = v.col; d.npos = v.npos; d.val = v.val; d.h = v.h; d.kind = v.kind;
+  d.ell_col = v.ell_col; d.ell_meta = v.ell_meta; d.ell_val = v.ell_val;
   d.N = p->n; d.C = r.C; d.Cp = r.Cp; d.P = r.P; d.R = r.R; d.S = r.S;
   d.x = r.x; d.y = r.y; d.F0 = r.F0; d.F1 = r.F1;
   d.ka = r.ka; d.dl = r.dl; d.kj = r.kj; d.kc = r.tables.kc; d.kx = r.tables.kx;
   d.n0 = r.n0;
+  d.W = (d.ell_col && r.Cp % 256 == 0) ? 8 : 4;
   return d;
 }
 
@@ -353,7 +360,7 @@ int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done, int32_t *don
       dense_active.push_back(r.id);
       continue;
     }
-    for (int g = 0; g < r.Cp / kColsPerWarp; ++g)
+    for (int g = 0; g < r.Cp / (32 * slots[q].W); ++g)
       for (int r0 = 0; r0 < r.prob->n; r0 += 8) items.push_back(WorkItem{q, r0, g, 0});
   }
   if (items.size() > e->items_cap) {
@@ -397,11 +404,19 @@ int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done, int32_t *don
     }
     ENG_CUDA(cudaEventRecord(dv, ds));
   }
-  const int grid = std::max(1, std::min(n_items, e->sms * 3));
+  const int grid = std::max(1, std::min(n_items, e->sms * batched_blocks_per_sm()));
+  if (n_items) {
+    if (!e->batched_t0) {
+      ENG_CUDA(cudaEventCreate(&e->batched_t0));
+      ENG_CUDA(cudaEventCreate(&e->batched_t1));
+    }
+    ENG_CUDA(cudaEventRecord(e->batched_t0, st));
+  }
   for (int j = 0; j < e->chunk && n_items; ++j) {
-    ENG_CUDA(launch_step_batched(e->d_slots, e->d_items, e->d_n_items, grid, j, st));
+    ENG_CUDA(launch_step_batched(e->d_slots, e->max_slots, e->d_items, e->d_n_items, grid, j, st));
     ++e->kernels_launched;
   }
+  if (n_items) ENG_CUDA(cudaEventRecord(e->batched_t1, st));
   for (int id : dense_active) ENG_CUDA(cudaStreamWaitEvent(st, e->side_done[e->reqs[id].slot], 0));
   // 4. retire the requests that finished inside the chunk
   std::vector<int> finished;
@@ -410,6 +425,7 @@ int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done, int32_t *don
     Request &r = e->reqs[e->slot_req[q]];
     const int done_now = std::min(e->chunk, r.S - r.n0);
     e->steps_done_total += int64_t(done_now) * r.prob->n * r.C;
+    if (!r.prob->dense) e->batched_updates += int64_t(done_now) * r.prob->n * r.C;
     r.n0 += done_now;
     if (r.n0 >= r.S) {
       if ((rc = readout(e, r, st)) != SBQA_OK) return rc;
@@ -417,6 +433,11 @@ int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done, int32_t *don
     }
   }
   ENG_CUDA(cudaStreamSynchronize(st));
+  if (n_items) {
+    float ms = 0.f;
+    ENG_CUDA(cudaEventElapsedTime(&ms, e->batched_t0, e->batched_t1));
+    e->batched_ms += ms;
+  }
   for (int id : finished) {
     Request &r = e->reqs[id];
     int err = 0;
@@ -458,6 +479,8 @@ int sbqa_engine_stats(const sbqa_engine *e, sbqa_engine_stats_t *s) {
   s->arena_used = int64_t(e->arena.used);
   s->updates_issued = e->steps_done_total;
   s->kernels_launched = e->kernels_launched;
+  s->batched_updates = e->batched_updates;
+  s->batched_ms = e->batched_ms;
   return SBQA_OK;
 }
 

@@ -154,6 +154,8 @@ cudaError_t launch_solve_small(const SmallArgs &a, cudaStream_t st);
 // batched step kernel).
 struct SlotDesc {
   const int32_t *row_ptr, *col, *npos;  // CSR (col in the step kernel's order)
+  const int32_t *ell_col, *ell_meta;    // ELL form of rows of degree <= 8 (null when not built)
+  const float *ell_val;
   const void *val;
   const float *h;
   int kind;
@@ -163,10 +165,10 @@ struct SlotDesc {
   const float *ka, *dl, *kj;
   float kc, kx;
   int n0;  // steps completed before the current chunk
-  int pad;
+  int W;   // replica columns per lane of its work items: 8 (ELL form, Cp a multiple of 256) or 4
 };
 
-// 8 spin rows x 128 replica columns of one slot.
+// 8 spin rows x 32 W replica columns of one slot (W of the slot).
 struct WorkItem {
   int slot, row0, colgroup, pad;
 };
@@ -195,8 +197,9 @@ cudaError_t launch_f_to_ft8(const StateView &s, int which, uint8_t *FT, int Kp, 
 
 // Batched CSR step over the work items of all active slots (step_batched.cu);
 // j = step index inside the current chunk, n_items in device memory.
-cudaError_t launch_step_batched(const SlotDesc *slots, const WorkItem *items, const int *n_items, int grid, int j,
-                                cudaStream_t st);
+cudaError_t launch_step_batched(const SlotDesc *slots, int n_slots, const WorkItem *items, const int *n_items,
+                                int grid, int j, cudaStream_t st);
+int batched_blocks_per_sm();  // resident blocks of the batched step kernel per SM (one wave = this x SMs)
 
 int energy_row_blocks(int N);
 // Readout energies of an integer dense instance on the tensor cores: the sign

@@ -1,22 +1,28 @@
 // step_batched.cu -- one SBQA step for many CSR instances of uneven size in a
 // single launch (the batching engine's kernel).
 //
-// Every active request owns a slot: its CSR couplings, its state buffers,
-// its schedule tables and the number of steps it had completed when the
-// current chunk of steps started.  The engine lists the work of all active
-// slots as items of 8 spin rows x 128 replica columns; a persistent grid
-// walks the item list, so one launch advances every request by one step
-// whatever the mix.  The arithmetic per element is the one of k_step_csr
-// (same gathers, same sums in the same order, same update), so a request
-// gives bit-identical results alone and in any mix.
+// Every active request owns a slot: its CSR couplings (and their ELL form for
+// rows of degree <= 8), its state buffers, its schedule tables and the number
+// of steps it had completed when the current chunk of steps started.  The
+// engine lists the work of all active slots as items of 8 spin rows x 128
+// replica columns; one wave of blocks walks the item list (a warp per row of
+// an item), so one launch advances every request by one step whatever the
+// mix.  The slot descriptors sit in shared memory, and a warp issues the
+// loads of its next row (work item two ahead, then x, y, h and the ELL
+// columns) before it gathers and updates the current one, so the memory
+// latency of one row overlaps the work of the previous one.  The arithmetic
+// per element is the one of k_step_csr (same gathers, same sums in the same
+// order, same update), so a request gives bit-identical results alone and in
+// any mix.
 #include "step_common.cuh"
 
 namespace sbqa {
 
 // Step j of the chunk of a slot whose n0 steps were done before the chunk.
 template <int P>
-__device__ __forceinline__ void batched_rows(const SlotDesc &d, int n, int r0, int c4) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+__device__ __forceinline__ void batched_row_csr(const SlotDesc &d, int n, int i, int c4, float4 xv, float4 yv,
+                                                float hi) {
+  const int lane = threadIdx.x & 31;
   StateView s;
   s.N = d.N; s.C = d.C; s.Cp = d.Cp; s.P = P; s.R = d.R;
   s.x = d.x; s.y = d.y; s.F[0] = d.F0; s.F[1] = d.F1; s.Sg = nullptr;
@@ -25,12 +31,6 @@ __device__ __forceinline__ void batched_rows(const SlotDesc &d, int n, int r0, i
   t.ka = d.ka; t.dl = d.dl; t.kj = d.kj; t.kc = d.kc; t.kx = d.kx; t.S = d.S; t.R = d.R;
   const uint8_t *Fc = s.f_of(n) + c4;
   uint8_t *Fout = s.f_of(n + 1);
-  const int i = r0 + warp;
-  if (i >= d.N) return;  // warp-uniform
-  const size_t off = size_t(i) * d.Cp + c4;
-  const float4 xv = *reinterpret_cast<const float4 *>(d.x + off);
-  const float4 yv = *reinterpret_cast<const float4 *>(d.y + off);
-  const float hi = __ldg(d.h + i);
   const int e0 = __ldg(d.row_ptr + i), e1 = __ldg(d.row_ptr + i + 1);
   float G[4];
   if (d.kind == VAL_PM1) {
@@ -88,29 +88,210 @@ __device__ __forceinline__ void batched_rows(const SlotDesc &d, int n, int r0, i
   sb_update4<P>(s, t, n, i, c4, G, hi, xv, yv, Fout);
 }
 
-__global__ void __launch_bounds__(256, 3) k_step_batched(const SlotDesc *slots, const WorkItem *items,
+// Loads of one row of a work item, issued ahead of its use.
+struct RowFetch {
+  int slot, row, n, c0;  // row < 0: nothing to do (past N, or the request has finished)
+  int col;               // lane < 8: ELL column of entry `lane`
+  float val;             // lane < 8: its value (FP32 / BF16 couplings)
+  int2 meta;             // (degree, +1 count)
+  float hi;
+  float ka, dnext;       // this step's schedule values of the slot
+  float kj[4];           // J_perp of the runs of the lane's columns (W = 4)
+  float4 x[2], y[2];     // x, y of the lane's W columns
+};
+
+__device__ __forceinline__ void fetch_row(RowFetch &f, const SlotDesc *D, const WorkItem &w, int sub, int j, int lane) {
+  const SlotDesc &d = D[w.slot];
+  f.slot = w.slot;
+  f.row = w.row0 + sub;
+  f.n = d.n0 + j;
+  if (f.row >= d.N || f.n >= d.S) {  // warp-uniform
+    f.row = -1;
+    return;
+  }
+  const int W = d.W;
+  f.c0 = w.colgroup * 32 * W + lane * W;
+  const size_t off = size_t(f.row) * d.Cp + f.c0;
+  f.x[0] = *reinterpret_cast<const float4 *>(d.x + off);
+  f.y[0] = *reinterpret_cast<const float4 *>(d.y + off);
+  if (W == 8) {
+    f.x[1] = *reinterpret_cast<const float4 *>(d.x + off + 4);
+    f.y[1] = *reinterpret_cast<const float4 *>(d.y + off + 4);
+  }
+  f.hi = __ldg(d.h + f.row);
+  f.ka = __ldg(d.ka + f.n);
+  f.dnext = __ldg(d.dl + f.n + 1);
+  if (W == 4) {
+    const float *kjn = d.kj + size_t(f.n) * d.R;
+    const int lp = __ffs(d.P) - 1;  // P is a power of two
+    if (d.P >= 4) {
+      const float k = f.c0 < d.C ? __ldg(kjn + (f.c0 >> lp)) : 0.f;
+      f.kj[0] = f.kj[1] = f.kj[2] = f.kj[3] = k;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) f.kj[q] = (f.c0 + q < d.C) ? __ldg(kjn + ((f.c0 + q) >> lp)) : 0.f;
+    }
+  }
+  if (d.ell_col) {
+    if (lane < kEllSlots) {
+      f.col = __ldg(d.ell_col + size_t(f.row) * kEllSlots + lane);
+      if (d.kind != VAL_PM1) f.val = __ldg(d.ell_val + size_t(f.row) * kEllSlots + lane);
+    }
+    f.meta = __ldg(reinterpret_cast<const int2 *>(d.ell_meta) + f.row);
+  }
+}
+
+// The W = 4 update's per-lane constants of a row, from its prefetched values
+// (as LaneConsts::load computes them).
+template <int P>
+__device__ __forceinline__ LaneConsts<P> lane_consts(const SlotDesc &d, const RowFetch &f) {
+  LaneConsts<P> L;
+  L.kc2 = make_float2(d.kc, d.kc);
+  L.mka2 = make_float2(-f.ka, -f.ka);
+  L.kx2 = make_float2(d.kx, d.kx);
+  L.dnext = f.dnext;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) L.kj[q] = f.kj[q];
+  L.active = f.c0 < d.C;
+  const int lane = threadIdx.x & 31;
+  const int k0 = f.c0 % P;
+  L.src_l = (k0 == 0) ? lane + P / 4 - 1 : lane - 1;
+  L.src_r = (k0 + 3 == P - 1) ? lane - P / 4 + 1 : lane + 1;
+  return L;
+}
+
+// One row from its ELL slots with W columns per lane: the gathers of its (at
+// most 8) neighbours, the sums in the CSR kernel's order, the update.
+template <int P, int W>
+__device__ __forceinline__ void batched_row_ell(const SlotDesc &d, const RowFetch &f) {
+  StateView s;
+  s.N = d.N; s.C = d.C; s.Cp = d.Cp; s.P = P; s.R = d.R;
+  s.x = d.x; s.y = d.y; s.F[0] = d.F0; s.F[1] = d.F1; s.Sg = nullptr;
+  s.Fx[0] = s.Fx[1] = nullptr;
+  const uint8_t *Fc = s.f_of(f.n) + f.c0;
+  const int deg = f.meta.x, npos = f.meta.y;
+  const bool pm1 = d.kind == VAL_PM1;
+  uint32_t f4[kEllSlots][W / 4];
+#pragma unroll
+  for (int e = 0; e < kEllSlots; ++e) {
+    const int j = __shfl_sync(0xffffffffu, f.col, e);
+    if (e < deg) {
+      if constexpr (W == 8) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(Fc + size_t(j) * d.Cp));
+        f4[e][0] = v.x;
+        f4[e][1] = v.y;
+      } else {
+        f4[e][0] = __ldg(reinterpret_cast<const uint32_t *>(Fc + size_t(j) * d.Cp));
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < W / 4; ++q) f4[e][q] = pm1 ? 0u : kFZero4;
+    }
+  }
+  float G[W];
+  if (pm1) {
+    uint32_t ap[W / 4], am[W / 4];
+#pragma unroll
+    for (int q = 0; q < W / 4; ++q) ap[q] = am[q] = 0;
+#pragma unroll
+    for (int e = 0; e < kEllSlots; ++e) {
+#pragma unroll
+      for (int q = 0; q < W / 4; ++q) {
+        if (e < npos) ap[q] += f4[e][q];
+        else am[q] += f4[e][q];
+      }
+    }
+    const int bias = (deg - npos) - npos;  // codes carry f + 1; padding slots hold 0
+#pragma unroll
+    for (int c = 0; c < W; ++c)
+      G[c] = float(int((ap[c / 4] >> (8 * (c % 4))) & 0xffu) - int((am[c / 4] >> (8 * (c % 4))) & 0xffu) + bias);
+  } else {
+    float g[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) g[c] = 0.f;
+#pragma unroll
+    for (int e = 0; e < kEllSlots; ++e) {
+      const float w = __shfl_sync(0xffffffffu, f.val, e);
+      if (e < deg) {
+#pragma unroll
+        for (int c = 0; c < W; ++c) g[c] = fmaf(w, fdec(f4[e][c / 4], c % 4), g[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < W; ++c) G[c] = g[c];
+  }
+  if constexpr (W == 4) {
+    sb_update4c<P>(s, lane_consts<P>(d, f), f.row, f.c0, G, f.hi, f.x[0], f.y[0], s.f_of(f.n + 1));
+  } else {
+    StepTables t;
+    t.ka = d.ka; t.dl = d.dl; t.kj = d.kj; t.kc = d.kc; t.kx = d.kx; t.S = d.S; t.R = d.R;
+    float xs[8] = {f.x[0].x, f.x[0].y, f.x[0].z, f.x[0].w, f.x[1].x, f.x[1].y, f.x[1].z, f.x[1].w};
+    float ys[8] = {f.y[0].x, f.y[0].y, f.y[0].z, f.y[0].w, f.y[1].x, f.y[1].y, f.y[1].z, f.y[1].w};
+    sb_updateW<P, 8>(s, t, f.ka, f.dnext, f.n, f.row, f.c0, G, f.hi, xs, ys, s.f_of(f.n + 1));
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void batched_row(const SlotDesc &d, const RowFetch &f) {
+  if (!d.ell_col) batched_row_csr<P>(d, f.n, f.row, f.c0, f.x[0], f.y[0], f.hi);
+  else if (d.W == 8) batched_row_ell<P, 8>(d, f);
+  else batched_row_ell<P, 4>(d, f);
+}
+
+constexpr int kBatchSmemSlots = 64;  // slot descriptors kept in shared memory (more: read from global)
+
+__global__ void __launch_bounds__(256, 2) k_step_batched(const SlotDesc *slots, int n_slots, const WorkItem *items,
                                                       const int *n_items, int j) {
-  const int total = *n_items;
-  for (int it = blockIdx.x; it < total; it += gridDim.x) {
-    const WorkItem w = items[it];
-    const SlotDesc &d = slots[w.slot];
-    const int n = d.n0 + j;
-    if (n >= d.S) continue;  // block-uniform: this request is done
-    const int c4 = w.colgroup * kColsPerWarp + (threadIdx.x & 31) * kColsPerLane;
+  __shared__ SlotDesc s_slots[kBatchSmemSlots];
+  const SlotDesc *D = slots;
+  if (n_slots <= kBatchSmemSlots) {
+    const int words = n_slots * int(sizeof(SlotDesc) / 4);
+    for (int q = threadIdx.x; q < words; q += blockDim.x)
+      reinterpret_cast<uint32_t *>(s_slots)[q] = reinterpret_cast<const uint32_t *>(slots)[q];
+    __syncthreads();
+    D = s_slots;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int total = *n_items * 8;  // rows of the work items
+  const int stride = gridDim.x * 8;
+  int u = blockIdx.x * 8 + warp;
+  if (u >= total) return;  // whole warp
+  RowFetch pf;
+  pf.col = 0;
+  pf.val = 0.f;
+  fetch_row(pf, D, items[u >> 3], u & 7, j, lane);
+  WorkItem w_after = u + stride < total ? items[(u + stride) >> 3] : WorkItem{0, 0, 0, 0};
+  for (; u < total; u += stride) {
+    const RowFetch cur = pf;
+    const int nx = u + stride;
+    if (nx < total) {  // warp-uniform: the next row's loads go out before this row's gathers
+      fetch_row(pf, D, w_after, nx & 7, j, lane);
+      if (nx + stride < total) w_after = items[(nx + stride) >> 3];
+    }
+    if (cur.row < 0) continue;
+    const SlotDesc &d = D[cur.slot];
     switch (d.P) {
-      case 1: batched_rows<1>(d, n, w.row0, c4); break;
-      case 2: batched_rows<2>(d, n, w.row0, c4); break;
-      case 4: batched_rows<4>(d, n, w.row0, c4); break;
-      case 8: batched_rows<8>(d, n, w.row0, c4); break;
-      case 16: batched_rows<16>(d, n, w.row0, c4); break;
-      default: batched_rows<32>(d, n, w.row0, c4); break;
+      case 1: batched_row<1>(d, cur); break;
+      case 2: batched_row<2>(d, cur); break;
+      case 4: batched_row<4>(d, cur); break;
+      case 8: batched_row<8>(d, cur); break;
+      case 16: batched_row<16>(d, cur); break;
+      default: batched_row<32>(d, cur); break;
     }
   }
 }
 
-cudaError_t launch_step_batched(const SlotDesc *slots, const WorkItem *items, const int *n_items, int grid, int j,
-                                cudaStream_t st) {
-  k_step_batched<<<grid, 256, 0, st>>>(slots, items, n_items, j);
+int batched_blocks_per_sm() {
+  static int per_sm = 0;
+  if (per_sm == 0 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_batched, 256, 0) != cudaSuccess ||
+                      per_sm < 1))
+    per_sm = 1;
+  return per_sm;
+}
+
+cudaError_t launch_step_batched(const SlotDesc *slots, int n_slots, const WorkItem *items, const int *n_items,
+                                int grid, int j, cudaStream_t st) {
+  k_step_batched<<<grid, 256, 0, st>>>(slots, n_slots, items, n_items, j);
   return cudaGetLastError();
 }
 

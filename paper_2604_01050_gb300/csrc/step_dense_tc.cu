@@ -55,6 +55,11 @@ __device__ __forceinline__ uint8_t f_to_e4m3(int8_t f) {
   return f == 0 ? uint8_t(0) : (f > 0 ? kE4M3One : kE4M3MinusOne);
 }
 
+// e4m3 code of f(x) for the threshold delta >= 0 (Eq. 8: 0 when |x| <= delta).
+__device__ __forceinline__ uint8_t thresh_e4m3(float x, float delta) {
+  return x > delta ? kE4M3One : (x < -delta ? kE4M3MinusOne : uint8_t(0));
+}
+
 // Address of the float4 (16-byte chunk u, 0..7) of row r inside a 128B-swizzled
 // box of 128-byte rows: chunks are permuted by XOR with r mod 8.
 __device__ __forceinline__ float4 *box_chunk(uint8_t *box, int r, int u) {
@@ -86,12 +91,14 @@ struct KjChunk {
 
 // Update of one spin row for 32 aligned columns c0..c0+31 (whole runs,
 // because P divides 32); x and y are read from and written back to one row of
-// the swizzled shared-memory state boxes.  Same arithmetic, in the same
-// order, as sb_update4.
-template <int P>
+// the swizzled shared-memory state boxes; the e4m3 code of f(x_next) of
+// column j goes to sFcol[j * 128] of the transposed f tile.  Same arithmetic,
+// in the same order, as sb_update4.  FULL: all 32 columns are below C (no
+// per-column test).
+template <int P, bool FULL>
 __device__ __forceinline__ void sb_update_row32(const StateView &s, const StepTables &t, float ka, float dnext,
                                                 const KjChunk<P> &kj, int c0, const uint32_t (&g)[32], float hi,
-                                                uint8_t *xbox, uint8_t *ybox, int r, int8_t (&f)[32]) {
+                                                uint8_t *xbox, uint8_t *ybox, int r, uint8_t *sFcol) {
   constexpr int PR = P < 32 ? P : 32;
   float xs[32], ys[32];
 #pragma unroll
@@ -105,10 +112,12 @@ __device__ __forceinline__ void sb_update_row32(const StateView &s, const StepTa
   for (int j = 0; j < 32; ++j) {
     const int k = j % P, base = j - k;
     const float xm = xs[base + (k + P - 1) % P], xp = xs[base + (k + 1) % P];
-    f[j] = 0;
     xo[j] = xs[j];
     yo[j] = ys[j];
-    if (c0 + j >= s.C) continue;
+    if (!FULL && c0 + j >= s.C) {
+      sFcol[j * kTcBM] = 0;
+      continue;
+    }
     float yn = fmaf(t.kc, __uint_as_float(g[j]) + hi, ys[j]);
     yn = fmaf(-ka, xs[j], yn);
     yn = fmaf(kj.get(c0, j / PR), xm + xp, yn);
@@ -119,7 +128,7 @@ __device__ __forceinline__ void sb_update_row32(const StateView &s, const StepTa
     }
     xo[j] = xn;
     yo[j] = yn;
-    f[j] = thresh(xn, dnext);
+    sFcol[j * kTcBM] = thresh_e4m3(xn, dnext);
   }
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
@@ -220,15 +229,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int c0 = n0 + cl;
     uint32_t g[32];
     tc::tmem_ld_32x32b_x32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(cl), g);
-    int8_t f[32];
-    if (i < s.N && c0 < s.C) {
-      sb_update_row32<P>(s, t, ka, dnext, kj, c0, g, hi, sX + b * kTcBox, sY + b * kTcBox, rl, f);
+    uint8_t *sFcol = sF + cl * kTcBM + rl;
+    if (i < s.N && c0 + 32 <= s.C) {
+      sb_update_row32<P, true>(s, t, ka, dnext, kj, c0, g, hi, sX + b * kTcBox, sY + b * kTcBox, rl, sFcol);
+    } else if (i < s.N && c0 < s.C) {
+      sb_update_row32<P, false>(s, t, ka, dnext, kj, c0, g, hi, sX + b * kTcBox, sY + b * kTcBox, rl, sFcol);
     } else {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) f[j] = 0;
+      for (int j = 0; j < 32; ++j) sFcol[j * kTcBM] = 0;
     }
-#pragma unroll
-    for (int j = 0; j < 32; ++j) sF[(cl + j) * kTcBM + rl] = f_to_e4m3(f[j]);
   }
   tc::fence_proxy_async_smem();
   tc::tc_fence_before();
@@ -372,15 +381,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int c0 = n0 + cl;
     uint32_t g[32];
     tc::tmem_ld_32x32b_x32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(cl), g);
-    int8_t f[32];
-    if (i < s.N && c0 < s.C) {
-      sb_update_row32<P>(s, t, ka, dnext, kj[round], c0, g, hi, xbox, ybox, rl, f);
+    uint8_t *sFcol = sF + cl * kTcBM + rl;
+    if (i < s.N && c0 + 32 <= s.C) {
+      sb_update_row32<P, true>(s, t, ka, dnext, kj[round], c0, g, hi, xbox, ybox, rl, sFcol);
+    } else if (i < s.N && c0 < s.C) {
+      sb_update_row32<P, false>(s, t, ka, dnext, kj[round], c0, g, hi, xbox, ybox, rl, sFcol);
     } else {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) f[j] = 0;
+      for (int j = 0; j < 32; ++j) sFcol[j * kTcBM] = 0;
     }
-#pragma unroll
-    for (int j = 0; j < 32; ++j) sF[(cl + j) * kTcBM + rl] = f_to_e4m3(f[j]);
     tc::fence_proxy_async_smem();
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -447,15 +456,16 @@ struct TpArgs {
 // patterns of FP32 x, y and the accumulated G).  Same arithmetic, in the same
 // order, as sb_update_row32: all momenta first (they read the old positions of
 // the ring neighbours), then positions, wall and f, whose e4m3 code goes to
-// column j of the transposed f tile (sFcol[j * 128]).
-template <int P>
+// column j of the transposed f tile (sFcol[j * 128]).  FULL: all 32 columns
+// are below C.
+template <int P, bool FULL>
 __device__ __forceinline__ void sb_update_regs32(const StateView &s, const StepTables &t, float ka, float dnext,
                                                  const KjChunk<P> &kj, int c0, const uint32_t (&g)[32], float hi,
                                                  uint32_t (&xr)[32], uint32_t (&yr)[32], uint8_t *sFcol) {
   constexpr int PR = P < 32 ? P : 32;
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
-    if (c0 + j >= s.C) continue;
+    if (!FULL && c0 + j >= s.C) continue;
     const int k = j % P, base = j - k;
     const float xm = __uint_as_float(xr[base + (k + P - 1) % P]), xp = __uint_as_float(xr[base + (k + 1) % P]);
     const float xj = __uint_as_float(xr[j]);
@@ -467,14 +477,14 @@ __device__ __forceinline__ void sb_update_regs32(const StateView &s, const StepT
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
     uint8_t e = 0;
-    if (c0 + j < s.C) {
+    if (FULL || c0 + j < s.C) {
       float xn = fmaf(t.kx, __uint_as_float(yr[j]), __uint_as_float(xr[j]));
       if (fabsf(xn) > 1.f) {
         xn = copysignf(1.f, xn);
         yr[j] = __float_as_uint(0.f);
       }
       xr[j] = __float_as_uint(xn);
-      e = f_to_e4m3(thresh(xn, dnext));
+      e = thresh_e4m3(xn, dnext);
     }
     sFcol[j * kTcBM] = e;
   }
@@ -648,7 +658,8 @@ __global__ void __launch_bounds__(kTpThreads, 1)
       tc::reg_fence(yr);
       uint8_t *sFcol = sF + cl * kTcBM + rl;
       if (i < s.N && c0 < s.C) {
-        sb_update_regs32<P>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, sFcol);
+        if (c0 + 32 <= s.C) sb_update_regs32<P, true>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, sFcol);
+        else sb_update_regs32<P, false>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, sFcol);
       } else {
 #pragma unroll
         for (int j = 0; j < 32; ++j) sFcol[j * kTcBM] = 0;
@@ -949,7 +960,8 @@ __global__ void __launch_bounds__(kSkThreads, 1)
       }
       uint8_t *sFcol = sF + cl * kTcBM + rl;
       if (i < s.N && c0 < s.C) {
-        sb_update_regs32<P>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, sFcol);
+        if (c0 + 32 <= s.C) sb_update_regs32<P, true>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, sFcol);
+        else sb_update_regs32<P, false>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, sFcol);
       } else {
 #pragma unroll
         for (int j = 0; j < 32; ++j) sFcol[j * kTcBM] = 0;

@@ -85,10 +85,11 @@ def run_stream(reqs, rate, arena_bytes=40 << 30, slots=64, chunk=50, seed=2, str
     lat = np.array([done_at[q] - arrivals[q] for q in range(len(reqs))])
     updates = sum(r["inst"]["n"] * r["P"] * r["R"] * r["steps"] for r in reqs)
     results = {rid: sb.engine_result(eng, rid) for rid in id_of}
-    kernels = sb.engine_stats(eng)["kernels_launched"]
+    stats = sb.engine_stats(eng)
     eng.destroy()
     return {"latency_s": lat, "makespan_s": makespan, "updates": updates, "results": results,
-            "arrivals": arrivals, "kernels_launched": kernels}
+            "arrivals": arrivals, "kernels_launched": stats["kernels_launched"],
+            "batched_updates": stats["batched_updates"], "batched_ms": stats["batched_ms"]}
 
 
 def summary(out):
