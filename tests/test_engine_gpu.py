@@ -31,6 +31,8 @@ def _requests(sb):
             (sk(100, 5)[1], 100, 4, 5, "auto"),       # dense CUDA-core path
             (lattice(5, 2)[1], 50, 2, 3, "auto"),     # ragged columns
             (dense_int(260, 7, jmax=2)[1], 64, 32, 2, "exact"),
+            (lattice(7, 4)[1], 60, 2, 99, "auto"),    # 8 columns per lane, ragged inside a lane (R P = 198)
+            (regular(400, 6, 5)[1], 80, 16, 16, "bf16"),  # 8 columns per lane, ELL values
     ]):
         pb = create(sb, spec)
         sb.set_schedule(pb, *workloads.autotune_params(R, k), precision=prec, eval_every=0)
