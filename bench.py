@@ -240,17 +240,18 @@ def run_serving(args):
     pool = serving.make_pool(12, seed=0)
     reqs = serving.make_requests(pool, args.requests, steps=2000, R=16, seed=1)
     stream = torch.cuda.Stream()
-    serving.run_stream(reqs[:6], None, stream=stream)  # warm-up (autotune, first launches)
-    closed = serving.run_stream(reqs, None, stream=stream)
+    arena = int(args.arena_gb * (1 << 30))
+    serving.run_stream(reqs[:6], None, stream=stream, arena_bytes=arena)  # warm-up (autotune, first launches)
+    closed = serving.run_stream(reqs, None, stream=stream, arena_bytes=arena)
     capacity = len(reqs) / closed["makespan_s"]
     loads = {}
     for f in (0.5, 0.8):
-        out = serving.run_stream(reqs, f * capacity, stream=stream, seed=int(10 * f))
+        out = serving.run_stream(reqs, f * capacity, stream=stream, seed=int(10 * f), arena_bytes=arena)
         loads["%.1fx" % f] = serving.summary(out)
     head = loads["0.8x"]
     # the batched CSR kernel alone: a closed loop of the lattice requests (no dense work beside it)
     lat_reqs = [r for r in reqs if r["inst"]["kind"] == "lattice"]
-    csr = serving.run_stream(lat_reqs, None, stream=stream)
+    csr = serving.run_stream(lat_reqs, None, stream=stream, arena_bytes=arena)
     achieved = BYTES_PER_UPDATE * csr["batched_updates"] / (csr["batched_ms"] * 1e-3) / 1e9
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -275,7 +276,7 @@ def run_serving(args):
             "config": {"workload": "Poisson stream of SK +-1 (dense) and 3D lattice (CSR) requests, "
                                    "N uniform in 64..8192, P in {8,16,32}, R=16, 2000 steps; "
                                    "continuous batching engine, chunk 50 steps",
-                       "requests": len(reqs), "capacity_req_per_s": capacity,
+                       "requests": len(reqs), "arena_gb": args.arena_gb, "capacity_req_per_s": capacity,
                        "closed_loop_updates_per_s": closed["updates"] / closed["makespan_s"]},
             "p50_s": head["p50_s"], "loads": loads, "gpu_launches": head["kernels_launched"],
             "roofline": roof, "cpu_baseline": cpu}
@@ -563,6 +564,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--requests", type=int, default=48, help="serving: requests in the stream")
+    ap.add_argument("--arena-gb", type=float, default=40.0, help="serving: device arena of the engine (GB)")
     ap.add_argument("--eps", type=float, default=0.08, help="tte: target optimality gap of the headline")
     ap.add_argument("--gamma0", type=float, default=16.0, help="tte: Gamma_x(0)")
     ap.add_argument("--tte-L", type=int, default=10)
