@@ -787,6 +787,26 @@ def test_full_size_dense_sk2000_exact(sb):
     assert _sampled_runs(sb, pb, spec, 32, 32, 1000, 5, [0, 31], prec="exact") <= TOL_TRAJ
 
 
+def test_full_size_dense_sk2000_energies(sb):
+    """SK N=2000, P=32, R=32, exact product, 30 steps: the tensor-core readout energies of runs 0, 17
+    and 31 (all replicas) equal the oracle's exact energies of the returned spins, and each run's best
+    is the lowest of its replicas."""
+    pb, spec = sk(2000, 0)
+    prob = create(sb, spec)
+    sb.set_schedule(prob, *workloads.autotune_params(32, 1), **_params(precision="exact"))
+    sb.run(prob, 30, 32, 32, seed=0)
+    assert prob.info().step_kernel in (2, 5, 8)
+    e, ei = sb.get_energies(prob)
+    x, _, _ = sb.get_state(prob)
+    best = sb.get_best(prob)
+    for r in (0, 17, 31):
+        spins = np.where(x[r] >= 0, 1, -1)
+        assert np.array_equal(ei[r], oracle.energies(pb, spins[None])[0])
+        k = int(np.argmin(ei[r]))
+        assert best["replica"][r] == k and best["energy"][r] == ei[r, k]
+        assert np.array_equal(best["spins"][r], spins[k])
+
+
 def test_full_size_regular_1e5_bf16(sb):
     """Random 6-regular N=1e5, J~N(0,1), h~N(0,0.1^2), BF16 product, P=16, R=8: runs 0 and 7 after 5 steps."""
     pb, spec = regular(100000, 6, 0)
