@@ -76,16 +76,6 @@ __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// 16-byte store into another CTA's shared memory that completes `bytes` on
-// that CTA's mbarrier (raddr, rbar: shared::cluster addresses).
-__device__ __forceinline__ void st_async_v4(uint32_t raddr, uint32_t a, uint32_t b, uint32_t c, uint32_t d,
-                                            uint32_t rbar) {
-  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(
-                   raddr),
-               "r"(a), "r"(b), "r"(c), "r"(d), "r"(rbar)
-               : "memory");
-}
-
 // Bulk copy of `bytes` (a multiple of 16) from this CTA's shared memory into
 // another CTA's (dst, rbar: shared::cluster addresses), completing the bytes
 // on that CTA's mbarrier.
@@ -129,16 +119,11 @@ __device__ __forceinline__ void tma_load_2d(void *smem_dst, const void *tmap, ui
       : "memory");
 }
 
-// L2 eviction policies for the cache hints of TMA copies: operands that
-// every step reads again (J, f) are kept ahead of the streamed state.
+// L2 eviction policy for the cache hints of TMA copies: operands that every
+// step reads again (J, f) are kept ahead of the streamed state.
 __device__ __forceinline__ uint64_t policy_evict_last() {
   uint64_t p;
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
-  return p;
-}
-__device__ __forceinline__ uint64_t policy_evict_first() {
-  uint64_t p;
-  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
 
