@@ -182,14 +182,14 @@ def _split_k(N, P, R):
 
 
 @pytest.mark.parametrize("N,P,R,jmax", [(300, 8, 40, 3), (512, 16, 16, 1), (1000, 32, 32, 1), (260, 4, 33, 16),
-                                        (500, 8, 48, 5), (700, 2, 128, 1)])
+                                        (500, 8, 48, 5), (700, 2, 128, 1), (1000, 16, 9, 2)])
 def test_persistent_dense_tc_solver_matches_per_step(sb, N, P, R, jmax):
     """The persistent tcgen05 solvers (x, y resident in tensor memory, per-tile
     step flags between CTAs; 128 x 128 tiles, and where padded N and R * P
     are multiples of 256 the split-K solver on 2-CTA clusters) and the
     per-step tcgen05 kernel give bit-identical runs, readouts every 37 steps
-    included; ragged row and column tiles (N = 300, 260, 500, 700; R * P =
-    320, 132, 384)."""
+    included; ragged row and column tiles (N = 300, 260, 500, 700, 1000; R * P
+    = 320, 132, 384, 144 -- the last on the split-K solver)."""
     pb, spec = dense_int(N, N + R, jmax=jmax)
     out = []
     for sel in (1, 2, 12):
