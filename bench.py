@@ -343,9 +343,19 @@ def run_tte(args):
     _b.build()
     import paper_2604_01050_gb300 as sb
     L, P, R, S, eps = args.tte_L, 16, 64, args.tte_steps, args.eps
-    n, rp, col, val, hh = workloads.cubic_lattice(L, 3)
+    dense = args.tte_kind == "sk"
+    if dense:  # dense SK +-1: the tensor-core path against a dense FP32 matmul per step
+        n = args.tte_n
+        Jd, hh = workloads.sk_pm1(n, 3)
+        prob = sb.create_problem_dense(Jd, hh)
+        sum_j2 = float(np.sum(Jd ** 2))
+        what = "dense SK N=%d, J=+-1" % n
+    else:
+        n, rp, col, val, hh = workloads.cubic_lattice(L, 3)
+        prob = sb.create_problem_csr(n, rp, col, val, hh)
+        sum_j2 = float(np.sum(val ** 2))
+        what = "3D cubic lattice L=%d (N=%d), J=+-1" % (L, n)
     beta, alpha = workloads.autotune_params(R, 3)
-    prob = sb.create_problem_csr(n, rp, col, val, hh)
     sb.set_schedule(prob, beta, alpha, gamma0=args.gamma0)
     # reference energy: best over long, wide searches with the fused path
     E0 = math.inf
@@ -379,12 +389,15 @@ def run_tte(args):
     sb.set_schedule(prob, beta, alpha, gamma0=args.gamma0)
     # plain path: same initial states and tables, FP32 torch ops per step
     ka, dl, kj = schedule_tables(S, P, R, beta, alpha, gamma0=args.gamma0)
-    c0 = 0.5 * math.sqrt(n / float(np.sum(val ** 2)))
+    c0 = 0.5 * math.sqrt(n / sum_j2)
     kc, kx = 0.5 * c0 / P, 0.5 * 1.0 / P
     tabs = (torch.tensor(ka, dtype=torch.float32, device=dev), torch.tensor(dl, dtype=torch.float32, device=dev),
             torch.tensor(kj, dtype=torch.float32, device=dev))
-    Jt = torch.sparse_csr_tensor(torch.tensor(rp), torch.tensor(col.astype(np.int64)), torch.tensor(val),
-                                 size=(n, n), dtype=torch.float32, device=dev)
+    if dense:
+        Jt = torch.tensor(Jd, dtype=torch.float32, device=dev)
+    else:
+        Jt = torch.sparse_csr_tensor(torch.tensor(rp), torch.tensor(col.astype(np.int64)), torch.tensor(val),
+                                     size=(n, n), dtype=torch.float32, device=dev)
     starts = []
     for k in range(reps):
         sb.run_begin(prob, S, P, R, seed=7 + k)
@@ -419,8 +432,7 @@ def run_tte(args):
     line = {"metric": "time-to-epsilon", "value": tte_f, "unit": "s", "n_gpus": 1, "steps": reps, "warmup": 1,
             "ms_per_step": 1e3 * t_fused, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "3D cubic lattice L=%d (N=%d), J=+-1, P=%d, R=%d, %d steps, gamma0=%g"
-                                   % (L, n, P, R, S, args.gamma0),
+            "config": {"workload": "%s, P=%d, R=%d, %d steps, gamma0=%g" % (what, P, R, S, args.gamma0),
                        "epsilon": eps, "E0": E0,
                        "E0_source": "best of 8 x %d runs of %d steps and of every solve timed here" % (R, 20 * S),
                        "p_target": 0.99},
@@ -568,6 +580,8 @@ def main():
     ap.add_argument("--eps", type=float, default=0.08, help="tte: target optimality gap of the headline")
     ap.add_argument("--gamma0", type=float, default=16.0, help="tte: Gamma_x(0)")
     ap.add_argument("--tte-L", type=int, default=10)
+    ap.add_argument("--tte-kind", default="lattice", choices=["lattice", "sk"], help="tte: instance family")
+    ap.add_argument("--tte-n", type=int, default=1024, help="tte: N of the dense SK instance")
     ap.add_argument("--tte-steps", type=int, default=2000)
     args = ap.parse_args()
     if args.config == "serving":
