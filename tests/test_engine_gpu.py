@@ -33,6 +33,8 @@ def _requests(sb):
             (dense_int(260, 7, jmax=2)[1], 64, 32, 2, "exact"),
             (lattice(7, 4)[1], 60, 2, 99, "auto"),    # 8 columns per lane, ragged inside a lane (R P = 198)
             (regular(400, 6, 5)[1], 80, 16, 16, "bf16"),  # 8 columns per lane, ELL values
+            (lattice(6, 6)[1], 40, 2, 201, "auto"),   # 8 columns per lane, ragged inside a lane (R P = 402)
+            (regular(300, 6, 7)[1], 40, 32, 16, "fp32"),  # 8 columns per lane, FP32 ELL values, R P = 512
     ]):
         pb = create(sb, spec)
         sb.set_schedule(pb, *workloads.autotune_params(R, k), precision=prec, eval_every=0)
