@@ -695,6 +695,17 @@ def main():
                 "traffic": traffic, "kernel": kernel_names[info.step_kernel],
                 "step_ms": step_ms, "peak_source": peak_src,
                 "note": "2 N^2 R P flops per step / event-timed step time; FP8 peak = 2 x measured BF16"}
+    elif info.step_kernel == 3:
+        # the one-launch small dense solver computes from shared memory and registers: FP32 ALU work,
+        # 2 N flops of the product + 12 of the update per replica-spin update, against the FP32 FMA
+        # rate of the SMs (152 SMs x 128 lanes x 2 flops x the maximum SM clock)
+        flops = (2.0 * N + 12.0) * N * P * R
+        achieved = flops / (step_ms * 1e-3) / 1e12
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": kernel_names[3], "step_ms": step_ms, "peak_source": "derived",
+                "note": "(2N + 12) FP32 flops per update / event-timed step time; peak = 152 SMs x 128 FP32 lanes "
+                        "x 2 x max SM clock; one CTA per run (%d of 152 SMs busy): latency-bound" % R}
     else:
         bpu = BYTES_PER_UPDATE_BSB if info.step_kernel in (6, 7) else BYTES_PER_UPDATE
         achieved_gbs = bpu * N * P * R / (step_ms * 1e-3) / 1e9
