@@ -76,8 +76,8 @@ BYTES_PER_UPDATE_BSB = 20  # ballistic form: + the FP32 f (= x) write
 TRAFFIC_PER_STEP = {
     "lattice16": {"kernel": "k_solve_csr_persistent", "bytes_per_step": (79867392 + 4435043328) // 64},
     "regular1e5": {"kernel": "k_solve_csr_persistent", "bytes_per_step": (7006125056 + 7254420736) // 64},
-    "sk2000": {"kernel": "k_solve_dense_tc_persistent", "bytes_per_step": (22741504 + 480512) // 64},
-    "sk4096": {"kernel": "k_step_dense_tc_wide", "bytes_per_step": 54591744 + 488960},
+    "sk2000": {"kernel": "k_solve_dense_tc_persistent", "bytes_per_step": (22876160 + 237056) // 1000},
+    "sk4096": {"kernel": "k_step_dense_tc_wide", "bytes_per_step": 54596864 + 632064},
 }
 L2_FLUSH_BYTES = 512 << 20
 
@@ -571,6 +571,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default=DEFAULT, choices=sorted(CONFIGS) + ["serving", "tte", "scaling", "sweep"])
+    ap.add_argument("--kernel-select", type=int, default=0,
+                    help="sbqa_params.kernel_select (0: the autotuner's choice; e.g. 12 pins the 128 x 128 "
+                         "persistent dense solver, for profiles)")
     ap.add_argument("--variant", default="threshold", choices=["threshold", "ballistic"],
                     help="f of Eq. 8 (SBQA) or f(x) = x (the bSB form)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -632,7 +635,7 @@ def main():
     stream = torch.cuda.Stream(device=dev)
     prob = create(inst)
     variant = cfg.get("variant", "threshold")
-    sb.set_schedule(prob, beta, alpha, precision=cfg["prec"], variant=variant)
+    sb.set_schedule(prob, beta, alpha, precision=cfg["prec"], variant=variant, kernel_select=args.kernel_select)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     seed0 = multi.rank_seed(0, rank)
 
@@ -734,7 +737,7 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         pe = create(src)
-        sb.set_schedule(pe, beta, alpha, precision=cfg["prec"], variant=variant)
+        sb.set_schedule(pe, beta, alpha, precision=cfg["prec"], variant=variant, kernel_select=args.kernel_select)
         sb.run(pe, S, P, R, seed=seed0 + 500 + k, stream=stream)
         best = sb.get_best(pe)
         pe.destroy()

@@ -630,11 +630,21 @@ int autotune_tc(sbqa_problem *p) {
   if (sel != 1 && p->S > 0 && p->tc_persistent_ok()) {
     SBQA_CUDA(p->d_tc_flags.alloc(tc_persistent_flag_count(p->Kp, p->Cp)));
     if (p->tc_split_possible()) {
-      // a cluster launch the device refuses (not a fault) leaves the plain persistent solver
+      // a cluster launch the device refuses, or one that does not arrive as 2-CTA
+      // clusters (the kernel then reports ERR_CLUSTER_SHAPE before touching
+      // anything, e.g. under a profiler's replay), leaves the plain persistent solver
       p->use_tc_split = true;
       if (launch_tc_persistent(p, p->state(), 0, 0, p->stream) != cudaSuccess) {
         cudaGetLastError();
         p->tc_split_failed = true;
+      } else {
+        int err = 0;
+        SBQA_CUDA(cudaMemcpyAsync(&err, p->d_err.p, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+        SBQA_CUDA(cudaStreamSynchronize(p->stream));
+        if (err != 0) {
+          p->tc_split_failed = true;
+          SBQA_CUDA(cudaMemsetAsync(p->d_err.p, 0, sizeof(int), p->stream));
+        }
       }
       p->use_tc_split = false;
     }
