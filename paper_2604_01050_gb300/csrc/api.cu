@@ -629,11 +629,13 @@ int autotune_tc(sbqa_problem *p) {
   const int sel = p->prm.kernel_select;
   if (sel != 1 && p->S > 0 && p->tc_persistent_ok()) {
     SBQA_CUDA(p->d_tc_flags.alloc(tc_persistent_flag_count(p->Kp, p->Cp)));
+    SBQA_CUDA(cudaMemsetAsync(p->d_err.p, 0, sizeof(int), p->stream));  // read after the trial launches
     if (p->tc_split_possible()) {
       // a cluster launch the device refuses, or one that does not arrive as 2-CTA
       // clusters (the kernel then reports ERR_CLUSTER_SHAPE before touching
       // anything, e.g. under a profiler's replay), leaves the plain persistent solver
       p->use_tc_split = true;
+      SBQA_CUDA(cudaMemsetAsync(p->d_err.p, 0, sizeof(int), p->stream));
       if (launch_tc_persistent(p, p->state(), 0, 0, p->stream) != cudaSuccess) {
         cudaGetLastError();
         p->tc_split_failed = true;
