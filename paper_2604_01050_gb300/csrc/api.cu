@@ -367,6 +367,7 @@ int alloc_run(sbqa_problem *p, int S, int P, int R) {
   SBQA_CUDA(p->d_have.alloc(R));
   SBQA_CUDA(p->d_best_spins.alloc(size_t(R) * p->n));
   SBQA_CUDA(p->d_err.alloc(1));
+  SBQA_CUDA(cudaMemsetAsync(p->d_err.p, 0, sizeof(int), p->stream));  // no trial launch reads a stale code
   p->S = S; p->P = P; p->R = R; p->C = C; p->Cp = Cp;
   if (p->use_tc) {
     SBQA_CUDA(p->d_FT.alloc(size_t(2) * Cp * p->Kp));
