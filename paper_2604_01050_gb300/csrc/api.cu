@@ -295,13 +295,18 @@ uint8_t e4m3_of_int(int v) {
 int prepare_tc_values(sbqa_problem *p) {
   if (p->d_J8.p) return SBQA_OK;
   const int N = p->n, Kp = (N + 127) / 128 * 128;
-  std::vector<uint8_t> j8(size_t(Kp) * Kp, 0);
+  HostVec<uint8_t> j8(size_t(Kp) * Kp);  // every byte is written below (zeros in the padding)
   uint8_t lut[33];  // e4m3 of -16 .. 16 (the tensor-core path takes |J_ij| <= 16)
   for (int v = -16; v <= 16; ++v) lut[v + 16] = e4m3_of_int(v);
-  parallel_tasks(N, [&](int64_t i, int64_t) {
-    const double *row = p->val.data() + size_t(i) * N;
+  parallel_tasks(Kp, [&](int64_t i, int64_t) {
     uint8_t *out = j8.data() + size_t(i) * Kp;
-    for (int j = 0; j < N; ++j) out[j] = lut[int(std::llround(row[j])) + 16];
+    if (i >= N) {
+      std::memset(out, 0, size_t(Kp));
+      return;
+    }
+    const double *row = p->val.data() + size_t(i) * N;
+    for (int j = 0; j < N; ++j) out[j] = lut[int(row[j]) + 16];  // integers, checked when J was analysed
+    std::memset(out + N, 0, size_t(Kp - N));
   });
   SBQA_CUDA(p->d_J8.alloc(j8.size()));
   SBQA_CUDA(cudaMemcpy(p->d_J8.p, j8.data(), j8.size(), cudaMemcpyHostToDevice));
