@@ -801,19 +801,25 @@ int sbqa::problem_build_tables(const sbqa_problem *p, int S, int P, int R, float
     dl[n] = float(q.delta_slope * tau);                 // Delta(t) = 0.7 t/T
     if (n < S) ka[n] = float(q.dt * (q.a0 - tau) / P);  // a(t) = t/T
   }
-  for (int n = 0; n < S; ++n) {
-    const double tau = double(n) / double(S);
-    for (int r = 0; r < R; ++r) {
-      double jp = 0.0;
-      if (q.jperp_enable) {
-        const double b = p->beta.empty() ? 1.0 : p->beta[r];
-        const double a = p->alpha.empty() ? 1.0 : p->alpha[r];
-        const double gam = q.gamma0 * (std::pow(1.0 - tau, a) + 1e-5);  // Gamma_x(t), Eq. 5
-        jp = -std::log(std::tanh(b * gam / P)) / (2.0 * b);           // J_perp(t), Eq. 5
+  // S * R transcendental evaluations (640 000 for 10^4 steps of 64 runs), in
+  // blocks of steps over the host threads; each entry is computed alone
+  constexpr int kStepsPerTask = 256;
+  parallel_tasks((int64_t(S) + kStepsPerTask - 1) / kStepsPerTask, [&](int64_t task, int64_t) {
+    const int n1 = std::min(S, int(task + 1) * kStepsPerTask);
+    for (int n = int(task) * kStepsPerTask; n < n1; ++n) {
+      const double tau = double(n) / double(S);
+      for (int r = 0; r < R; ++r) {
+        double jp = 0.0;
+        if (q.jperp_enable) {
+          const double b = p->beta.empty() ? 1.0 : p->beta[r];
+          const double a = p->alpha.empty() ? 1.0 : p->alpha[r];
+          const double gam = q.gamma0 * (std::pow(1.0 - tau, a) + 1e-5);  // Gamma_x(t), Eq. 5
+          jp = -std::log(std::tanh(b * gam / P)) / (2.0 * b);           // J_perp(t), Eq. 5
+        }
+        kj[size_t(n) * R + r] = float(q.dt * jp);
       }
-      kj[size_t(n) * R + r] = float(q.dt * jp);
     }
-  }
+  });
   SBQA_CUDA(cudaMemcpyAsync(d_ka, ka.data(), ka.size() * sizeof(float), cudaMemcpyHostToDevice, st));
   SBQA_CUDA(cudaMemcpyAsync(d_dl, dl.data(), dl.size() * sizeof(float), cudaMemcpyHostToDevice, st));
   SBQA_CUDA(cudaMemcpyAsync(d_kj, kj.data(), kj.size() * sizeof(float), cudaMemcpyHostToDevice, st));
