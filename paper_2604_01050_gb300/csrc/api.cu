@@ -211,14 +211,17 @@ int prepare_sparse_values(sbqa_problem *p, int precision) {
   if (kind == VAL_PM1 && !p->d_npos.p) {
     // each row: columns of the +1 entries, then of the -1 entries
     std::vector<int32_t> col(m), npos(p->n);
-    for (int i = 0; i < p->n; ++i) {
-      int64_t w = p->row_ptr[i];
-      for (int64_t e = p->row_ptr[i]; e < p->row_ptr[i + 1]; ++e)
-        if (p->val[e] > 0) col[w++] = p->col[e];
-      npos[i] = int32_t(w - p->row_ptr[i]);
-      for (int64_t e = p->row_ptr[i]; e < p->row_ptr[i + 1]; ++e)
-        if (p->val[e] < 0) col[w++] = p->col[e];
-    }
+    parallel_tasks((int64_t(p->n) + 4095) / 4096, [&](int64_t task, int64_t) {
+      const int i1 = std::min<int64_t>(p->n, (task + 1) * 4096);
+      for (int i = int(task) * 4096; i < i1; ++i) {
+        int64_t w = p->row_ptr[i];
+        for (int64_t e = p->row_ptr[i]; e < p->row_ptr[i + 1]; ++e)
+          if (p->val[e] > 0) col[w++] = p->col[e];
+        npos[i] = int32_t(w - p->row_ptr[i]);
+        for (int64_t e = p->row_ptr[i]; e < p->row_ptr[i + 1]; ++e)
+          if (p->val[e] < 0) col[w++] = p->col[e];
+      }
+    });
     SBQA_CUDA(p->d_npos.alloc(p->n));
     SBQA_CUDA(cudaMemcpy(p->d_npos.p, npos.data(), p->n * sizeof(int32_t), cudaMemcpyHostToDevice));
     if (m) {
@@ -227,12 +230,18 @@ int prepare_sparse_values(sbqa_problem *p, int precision) {
     }
   } else if (kind == VAL_F32 && !p->d_val_f32.p && m) {
     std::vector<float> v(m);
-    for (size_t e = 0; e < m; ++e) v[e] = float(p->val[e]);
+    parallel_tasks((int64_t(m) + 65535) / 65536, [&](int64_t task, int64_t) {
+      const size_t e1 = std::min<size_t>(m, size_t(task + 1) * 65536);
+      for (size_t e = size_t(task) * 65536; e < e1; ++e) v[e] = float(p->val[e]);
+    });
     SBQA_CUDA(p->d_val_f32.alloc(m));
     SBQA_CUDA(cudaMemcpy(p->d_val_f32.p, v.data(), m * sizeof(float), cudaMemcpyHostToDevice));
   } else if (kind == VAL_BF16 && !p->d_val_bf16.p && m) {
     std::vector<uint16_t> v(m);
-    for (size_t e = 0; e < m; ++e) v[e] = bf16_bits_rne(p->val[e]);
+    parallel_tasks((int64_t(m) + 65535) / 65536, [&](int64_t task, int64_t) {
+      const size_t e1 = std::min<size_t>(m, size_t(task + 1) * 65536);
+      for (size_t e = size_t(task) * 65536; e < e1; ++e) v[e] = bf16_bits_rne(p->val[e]);
+    });
     SBQA_CUDA(p->d_val_bf16.alloc(m));
     SBQA_CUDA(cudaMemcpy(p->d_val_bf16.p, v.data(), m * 2, cudaMemcpyHostToDevice));
   }
@@ -243,7 +252,9 @@ int prepare_sparse_values(sbqa_problem *p, int precision) {
     const int N = p->n;
     std::vector<int32_t> ec(size_t(N) * kEllSlots, 0), meta(size_t(N) * 2, 0);
     std::vector<float> ev(kind == VAL_PM1 ? 0 : size_t(N) * kEllSlots, 0.f);
-    for (int i = 0; i < N; ++i) {
+    parallel_tasks((int64_t(N) + 4095) / 4096, [&](int64_t task, int64_t) {
+    const int i1 = std::min<int64_t>(N, (task + 1) * 4096);
+    for (int i = int(task) * 4096; i < i1; ++i) {
       const int64_t e0 = p->row_ptr[i], e1 = p->row_ptr[i + 1];
       int w = 0, npos = 0;
       if (kind == VAL_PM1) {
@@ -269,6 +280,7 @@ int prepare_sparse_values(sbqa_problem *p, int precision) {
       meta[2 * size_t(i)] = w;
       meta[2 * size_t(i) + 1] = npos;
     }
+    });
     SBQA_CUDA(p->d_ell_col.alloc(ec.size()));
     SBQA_CUDA(cudaMemcpy(p->d_ell_col.p, ec.data(), ec.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     SBQA_CUDA(p->d_ell_meta.alloc(meta.size()));
@@ -982,14 +994,26 @@ int sbqa_create_problem_csr(int32_t n, int64_t nnz, const int64_t *row_ptr, cons
       if (e > row_ptr[i] && col_idx[e - 1] >= j) return fail(SBQA_ERR_NOT_SYMMETRIC, "unsorted or duplicate columns");
     }
   }
-  for (int i = 0; i < n; ++i)  // pass 2: the partner (j, i) holds the same value
-    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-      const int32_t j = col_idx[e];
-      const int32_t *b = col_idx + row_ptr[j], *en = col_idx + row_ptr[j + 1];
-      const int32_t *it = std::lower_bound(b, en, i);
-      if (it == en || *it != i || val[row_ptr[j] + (it - b)] != val[e])
-        return fail(SBQA_ERR_NOT_SYMMETRIC, "J != J^T");
-    }
+  {  // pass 2: the partner (j, i) holds the same value (blocks of rows over the host threads)
+    constexpr int kRowsPerTask = 4096;
+    const int64_t tasks = (int64_t(n) + kRowsPerTask - 1) / kRowsPerTask;
+    std::vector<uint8_t> ok(size_t(tasks), 1);
+    parallel_tasks(tasks, [&](int64_t task, int64_t) {
+      const int i1 = std::min<int64_t>(n, (task + 1) * kRowsPerTask);
+      for (int i = int(task) * kRowsPerTask; i < i1 && ok[task]; ++i)
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+          const int32_t j = col_idx[e];
+          const int32_t *b = col_idx + row_ptr[j], *en = col_idx + row_ptr[j + 1];
+          const int32_t *it = std::lower_bound(b, en, i);
+          if (it == en || *it != i || val[row_ptr[j] + (it - b)] != val[e]) {
+            ok[task] = 0;
+            break;
+          }
+        }
+    });
+    for (uint8_t v : ok)
+      if (!v) return fail(SBQA_ERR_NOT_SYMMETRIC, "J != J^T");
+  }
   sbqa_problem *p = new (std::nothrow) sbqa_problem();
   if (!p) return fail(SBQA_ERR_OOM, "host allocation");
   cudaGetDevice(&p->device);
