@@ -685,12 +685,12 @@ def main():
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
     kernel_names = {0: "k_step_csr", 1: "k_step_dense", 2: "k_step_dense_tc", 3: "k_solve_small",
                     4: "k_solve_csr_persistent", 5: "k_solve_dense_tc_persistent", 6: "k_step_csr_bsb",
-                    7: "k_step_dense_bsb", 8: "k_solve_dense_tc_split"}
+                    7: "k_step_dense_bsb", 8: "k_solve_dense_tc_split", 9: "k_solve_dense_tc_pair"}
     if info.step_kernel == 2 and (-(-P * R // 128) * 128) % 256 == 0:
         kernel_names[2] = "k_step_dense_tc_wide"  # 128 x 256 tiles when the padded columns allow
     tr = TRAFFIC_PER_STEP.get(args.config + ("/ballistic" if cfg.get("variant") == "ballistic" else ""))
     traffic = tr["bytes_per_step"] if tr and tr["kernel"] == kernel_names[info.step_kernel] else None
-    if info.step_kernel in (2, 5, 8):  # dense tcgen05 FP8: a contraction, 2 N^2 R P flops per step
+    if info.step_kernel in (2, 5, 8, 9):  # dense tcgen05 FP8: a contraction, 2 N^2 R P flops per step
         flops = 2.0 * N * N * P * R
         achieved = flops / (step_ms * 1e-3) / 1e12
         peak = 2.0 * peaks.get("bf16_tflops", 1900.0)  # FP8 = 2 x the measured BF16 dense peak
@@ -754,9 +754,9 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         cpu = oracle_sample(cfg, target_s=args.ref_seconds)
     # init + reset_best (+ the f -> e4m3 conversion on the tensor-core path) + steps + 4 readout kernels
-    tc_conv = 1 if info.step_kernel in (2, 5, 8) else 0  # f codes -> FP8 operand; the readout's sign codes
+    tc_conv = 1 if info.step_kernel in (2, 5, 8, 9) else 0  # f codes -> FP8 operand; the readout's sign codes
     launches_per_solve = (1 if info.step_kernel == 3 else
-                          2 + tc_conv + (1 if info.step_kernel in (4, 5, 8) else S) + 4 + tc_conv)
+                          2 + tc_conv + (1 if info.step_kernel in (4, 5, 8, 9) else S) + 4 + tc_conv)
     line = {
         "metric": "replica-spin updates/s", "value": value, "unit": "replica-spin updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_solve,
@@ -770,7 +770,8 @@ def main():
                    "parallelism": "independent runs per GPU (weak scaling)",
                    "step_kernel": ["csr", "dense_cuda_core", "dense_tcgen05_fp8", "dense_small_one_launch",
                                    "csr_persistent", "dense_tcgen05_persistent", "csr_ballistic",
-                                   "dense_ballistic", "dense_tcgen05_persistent_split_k"][info.step_kernel],
+                                   "dense_ballistic", "dense_tcgen05_persistent_split_k",
+                                   "dense_tcgen05_persistent_cta_pairs"][info.step_kernel],
                    "csr_variant": info.step_variant,
                    "autotune_ms_per_step": [round(v, 5) for v in info.variant_ms],
                    "autotune_persistent_ms_per_step": round(info.persistent_ms, 5)},

@@ -119,7 +119,10 @@ typedef struct {
                              and 7 dense CUDA cores for the ballistic form
                              f(x) = x, 8 the persistent dense tcgen05
                              solver with its K loop split across the two
-                             CTAs of a cluster (128 x 256 tiles); -1 none  */
+                             CTAs of a cluster (128 x 256 tiles), 9 the
+                             persistent dense tcgen05 solver on CTA pairs
+                             sharing M=256 MMAs (2-CTA clusters, tcgen05
+                             cta_group::2); -1 none                          */
     int32_t step_variant; /* CSR kernel variant picked by the autotuner:
                              0-5: 4 << (v % 3) consecutive replica columns
                              per lane, v >= 3 with one wave of blocks
@@ -170,8 +173,11 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info);
  *                cache); 12 = as 2, but the dense tensor-core solver keeps
  *                its 128 x 128 tiles instead of splitting the K loop across
  *                2-CTA clusters (taken by default when padded N and padded
- *                R*P are multiples of 256).  Results are identical
- *                whichever kernel runs.
+ *                R*P are multiples of 256); 13 = the dense tensor-core
+ *                solver on CTA pairs that share M=256 MMAs (padded N a
+ *                multiple of 256; with kernel_select 0 the autotuner times
+ *                it beside the others).  Results are identical whichever
+ *                kernel runs.
  *   beta, alpha  host, n_runs doubles each: per-run inverse temperature and
  *                schedule exponent (the auto-tuning draws them from
  *                [0.5,1.5] x [0.5,1.0]); beta > 0, alpha > 0

@@ -491,7 +491,7 @@ struct TuneKey {
 };
 struct TuneResult {
   int csr_variant = 0;
-  bool use_persistent = false, use_tc_persistent = false, use_tc_split = false;
+  bool use_persistent = false, use_tc_persistent = false, use_tc_split = false, use_tc_pair = false;
   float variant_ms[8] = {};
   float persistent_ms = 0.f, tc_step_ms = 0.f, tc_persistent_ms = 0.f;
 };
@@ -578,7 +578,7 @@ int autotune_csr(sbqa_problem *p) {
   p->use_persistent = false;
   p->persistent_ms = 0.f;
   if (p->persist_blocks == 0) p->persist_blocks = persistent_blocks();
-  if ((p->prm.kernel_select == 2 || p->prm.kernel_select == 11 || p->prm.kernel_select == 12) && p->S > 0 &&
+  if ((p->prm.kernel_select == 2 || p->prm.kernel_select >= 11) && p->S > 0 &&
       p->persistent_ok()) {
     SBQA_CUDA(p->d_bar.alloc(persistent_barrier_words()));
     p->use_persistent = true;
@@ -614,9 +614,12 @@ int autotune_csr(sbqa_problem *p) {
   return SBQA_OK;
 }
 
-// Steps [n0, n1) of the persistent dense tcgen05 solver, split-K across 2-CTA
-// clusters where eligible.
+// Steps [n0, n1) of the persistent dense tcgen05 solver: on CTA pairs, split-K
+// across 2-CTA clusters, or with 128 x 128 tiles, as chosen.
 cudaError_t launch_tc_persistent(sbqa_problem *p, const StateView &s, int n0, int n1, cudaStream_t st) {
+  if (p->tc_pair_ok())
+    return launch_solve_dense_tc_pair(p->tc_plan, s, p->Kp, p->d_err.p, p->d_h.p, p->tables, n0, n1,
+                                      p->d_tc_flags.p, st);
   if (p->tc_split_ok())
     return launch_solve_dense_tc_split(p->tc_plan, s, p->Kp, p->d_err.p, p->d_h.p, p->tables, n0, n1,
                                        p->d_tc_flags.p, st);
@@ -626,55 +629,64 @@ cudaError_t launch_tc_persistent(sbqa_problem *p, const StateView &s, int n0, in
 
 // Autotuner of the dense tensor-core path: times the per-step kernel, the
 // persistent solver with 128 x 128 tiles and, where the instance qualifies,
-// the split-K persistent solver (same state buffers, before the initial state
-// is written) and keeps the fastest.  kernel_select 1 forces the per-step
-// kernel, 2 the persistent solver (split-K where it qualifies), 12 the
-// persistent solver with 128 x 128 tiles.  Cached per handle, column count,
+// the split-K and the paired persistent solvers (same state buffers, before
+// the initial state is written) and keeps the fastest.  kernel_select 1
+// forces the per-step kernel, 2 the persistent solver (split-K where it
+// qualifies), 12 the persistent solver with 128 x 128 tiles, 13 the paired
+// persistent solver where it qualifies.  Cached per handle, column count,
 // replica count and selection, and process-wide per instance shape.
 int autotune_tc(sbqa_problem *p) {
   if (!p->use_tc) {
-    p->use_tc_persistent = p->use_tc_split = false;
+    p->use_tc_persistent = p->use_tc_split = p->use_tc_pair = false;
     return SBQA_OK;
   }
   if (p->tc_select_cp == p->Cp && p->tc_select == p->prm.kernel_select && p->tc_select_p == p->P) return SBQA_OK;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   SBQA_CUDA(cudaStreamIsCapturing(p->stream, &cs));
   if (cs != cudaStreamCaptureStatusNone) return SBQA_OK;
-  p->use_tc_persistent = p->use_tc_split = false;
+  p->use_tc_persistent = p->use_tc_split = p->use_tc_pair = false;
   p->tc_step_ms = p->tc_persistent_ms = 0.f;
   if (p->tc_persist_blocks == 0) p->tc_persist_blocks = tc_persistent_blocks();
   if (p->tc_split_blocks < 0) p->tc_split_blocks = tc_split_blocks();
+  if (p->tc_pair_blocks < 0) p->tc_pair_blocks = tc_pair_blocks();
   const int sel = p->prm.kernel_select;
   if (sel != 1 && p->S > 0 && p->tc_persistent_ok()) {
     SBQA_CUDA(p->d_tc_flags.alloc(tc_persistent_flag_count(p->Kp, p->Cp)));
     SBQA_CUDA(cudaMemsetAsync(p->d_err.p, 0, sizeof(int), p->stream));  // read after the trial launches
-    if (p->tc_split_possible()) {
-      // a cluster launch the device refuses, or one that does not arrive as 2-CTA
-      // clusters (the kernel then reports ERR_CLUSTER_SHAPE before touching
-      // anything, e.g. under a profiler's replay), leaves the plain persistent solver
-      p->use_tc_split = true;
+    // a cluster launch the device refuses, or one that does not arrive as 2-CTA
+    // clusters (the kernel then reports ERR_CLUSTER_SHAPE before touching
+    // anything, e.g. under a profiler's replay), leaves the plain persistent
+    // solver: a zero-step launch of each cluster solver checks that first
+    auto probe = [&](bool *use, bool *failed) -> int {
+      *use = true;
       SBQA_CUDA(cudaMemsetAsync(p->d_err.p, 0, sizeof(int), p->stream));
       if (launch_tc_persistent(p, p->state(), 0, 0, p->stream) != cudaSuccess) {
         cudaGetLastError();
-        p->tc_split_failed = true;
+        *failed = true;
       } else {
         int err = 0;
         SBQA_CUDA(cudaMemcpyAsync(&err, p->d_err.p, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
         SBQA_CUDA(cudaStreamSynchronize(p->stream));
         if (err != 0) {
-          p->tc_split_failed = true;
+          *failed = true;
           SBQA_CUDA(cudaMemsetAsync(p->d_err.p, 0, sizeof(int), p->stream));
         }
       }
-      p->use_tc_split = false;
-    }
+      *use = false;
+      return SBQA_OK;
+    };
+    int prc = SBQA_OK;
+    if (p->tc_split_possible() && (prc = probe(&p->use_tc_split, &p->tc_split_failed)) != SBQA_OK) return prc;
+    if (p->tc_pair_possible() && (prc = probe(&p->use_tc_pair, &p->tc_pair_failed)) != SBQA_OK) return prc;
     TuneResult known;
-    if (sel == 2 || sel == 12) {
+    if (sel == 2 || sel == 12 || sel == 13) {
       p->use_tc_persistent = true;
       p->use_tc_split = sel == 2 && p->tc_split_possible();
+      p->use_tc_pair = sel == 13 && p->tc_pair_possible();
     } else if (tune_lookup(p, &known)) {
       p->use_tc_persistent = known.use_tc_persistent;
       p->use_tc_split = known.use_tc_split;
+      p->use_tc_pair = known.use_tc_pair;
       p->tc_step_ms = known.tc_step_ms;
       p->tc_persistent_ms = known.tc_persistent_ms;
     } else {
@@ -688,12 +700,14 @@ int autotune_tc(sbqa_problem *p) {
           &ms);
       if (rc != SBQA_OK) return rc;
       p->tc_step_ms = ms;
-      // the persistent candidates: 128 x 128 tiles, then split-K where it qualifies
+      // the persistent candidates: 128 x 128 tiles, then split-K and CTA pairs where they qualify
       const int steps = std::min(p->S, 64);
       float best_persistent = 0.f;
-      bool best_split = false;
-      for (int split = 0; split < (p->tc_split_possible() ? 2 : 1); ++split) {
-        p->use_tc_split = split == 1;
+      int best_cand = 0;
+      for (int cand = 0; cand < 3; ++cand) {
+        if ((cand == 1 && !p->tc_split_possible()) || (cand == 2 && !p->tc_pair_possible())) continue;
+        p->use_tc_split = cand == 1;
+        p->use_tc_pair = cand == 2;
         cudaEvent_t e0, e1;
         SBQA_CUDA(cudaEventCreate(&e0));
         SBQA_CUDA(cudaEventCreate(&e1));
@@ -706,12 +720,13 @@ int autotune_tc(sbqa_problem *p) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         SBQA_CUDA(e);
-        if (split == 0 || ms / steps < best_persistent) {
+        if (cand == 0 || ms / steps < best_persistent) {
           best_persistent = ms / steps;
-          best_split = split == 1;
+          best_cand = cand;
         }
       }
-      p->use_tc_split = best_split;
+      p->use_tc_split = best_cand == 1;
+      p->use_tc_pair = best_cand == 2;
       p->tc_persistent_ms = best_persistent;
       p->use_tc_persistent = p->tc_persistent_ms < p->tc_step_ms;
       int err = 0;
@@ -720,6 +735,7 @@ int autotune_tc(sbqa_problem *p) {
       TuneResult r;
       r.use_tc_persistent = p->use_tc_persistent;
       r.use_tc_split = p->use_tc_split;
+      r.use_tc_pair = p->use_tc_pair;
       r.tc_step_ms = p->tc_step_ms;
       r.tc_persistent_ms = p->tc_persistent_ms;
       tune_store(p, r);
@@ -1061,7 +1077,7 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info) {
   info->step_kernel = !p->begun ? -1
                      : p->ballistic() ? (p->dense ? 7 : 6)
                                  : (p->small_path ? 3
-                                                  : (p->use_tc ? (p->use_tc_persistent && p->tc_persistent_ok() ? (p->tc_split_ok() ? 8 : 5) : 2)
+                                                  : (p->use_tc ? (p->use_tc_persistent && p->tc_persistent_ok() ? (p->tc_pair_ok() ? 9 : p->tc_split_ok() ? 8 : 5) : 2)
                                                                : (p->dense ? 1 : (p->use_persistent ? 4 : 0))));
   info->persistent_ms = p->use_tc ? p->tc_persistent_ms : p->persistent_ms;
   info->step_variant = p->dense ? -1 : p->csr_variant;
@@ -1081,7 +1097,7 @@ int sbqa_set_schedule(sbqa_problem *p, const sbqa_params *q) {
   if (q->precision == SBQA_PREC_EXACT && (!p->j_integer || p->max_abs_j > 16))
     return fail(SBQA_ERR_UNSUPPORTED, "EXACT precision needs integer J with |J_ij| <= 16");
   if (q->eval_every < 0 || q->n_runs < 0) return fail(SBQA_ERR_INVALID_ARG, "negative eval_every or n_runs");
-  if (q->kernel_select < 0 || q->kernel_select > 12) return fail(SBQA_ERR_INVALID_ARG, "kernel_select must be 0..12");
+  if (q->kernel_select < 0 || q->kernel_select > 13) return fail(SBQA_ERR_INVALID_ARG, "kernel_select must be 0..13");
   if (q->n_runs > 0 && (!q->beta || !q->alpha)) return fail(SBQA_ERR_INVALID_ARG, "beta/alpha missing");
   std::vector<double> beta, alpha;
   if (q->n_runs > 0) {

@@ -121,6 +121,16 @@ cudaError_t launch_solve_dense_tc_persistent(const void *plan, const StateView &
                                              const StepTables &t, int n_begin, int n_end, uint32_t *flags,
                                              cudaStream_t st);
 
+// The persistent dense solver on 2-CTA clusters sharing M=256 MMAs
+// (tcgen05 cta_group::2; step_dense_tc.cu): padded N a multiple of 256,
+// row-tile pairs x column tiles co-resident as clusters (tc_pair_blocks()).
+// Same flags and results as launch_solve_dense_tc_persistent.
+int tc_pair_blocks();
+bool tc_pair_eligible(int Kp, int Cp, int blocks);
+cudaError_t launch_solve_dense_tc_pair(const void *plan, const StateView &s, int Kp, int *err, const float *h,
+                                       const StepTables &t, int n_begin, int n_end, uint32_t *flags,
+                                       cudaStream_t st);
+
 // Ballistic form f(x) = x (step_bsb.cu): CSR and dense CUDA-core steps, and
 // the copy x -> Fx[which] that starts the f buffers.
 cudaError_t launch_step_csr_bsb(const StateView &s, const CsrView &J, const StepTables &t, int n, cudaStream_t st);

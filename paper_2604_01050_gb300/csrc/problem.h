@@ -143,6 +143,9 @@ struct sbqa_problem {
   int tc_split_blocks = -1;      // co-resident CTAs in 2-CTA clusters (-1: not queried yet)
   bool tc_split_failed = false;  // the cluster launch was refused: plain persistent solver
   bool use_tc_split = false;     // the persistent dense solver runs split-K (autotuner's or caller's choice)
+  int tc_pair_blocks = -1;       // co-resident CTAs of the paired solver in 2-CTA clusters (-1: not queried yet)
+  bool tc_pair_failed = false;   // its cluster launch was refused or misshaped: not used again on this handle
+  bool use_tc_pair = false;      // the persistent dense solver runs on CTA pairs sharing M=256 MMAs
   int tc_select_cp = -1, tc_select = -1, tc_select_p = -1;
   sbqa::DevBuf<uint32_t> d_tc_flags;  // per-tile step counters of the persistent solver
   sbqa::DevBuf<float> d_x, d_y;
@@ -184,10 +187,17 @@ struct sbqa_problem {
 
   // the instance qualifies for the split-K persistent solver on 2-CTA clusters
   bool tc_split_possible() const {
-    return tc_persistent_ok() && prm.kernel_select != 12 && !tc_split_failed &&
+    return tc_persistent_ok() && prm.kernel_select != 12 && prm.kernel_select != 13 && !tc_split_failed &&
            sbqa::tc_split_eligible(Kp, Cp, tc_split_blocks);
   }
   bool tc_split_ok() const { return use_tc_split && tc_split_possible(); }
+
+  // the instance qualifies for the paired persistent solver (autotuned, or kernel_select 13)
+  bool tc_pair_possible() const {
+    return tc_persistent_ok() && (prm.kernel_select == 0 || prm.kernel_select == 13) && !tc_pair_failed &&
+           sbqa::tc_pair_eligible(Kp, Cp, tc_pair_blocks);
+  }
+  bool tc_pair_ok() const { return use_tc_pair && tc_pair_possible(); }
 
   int persist_mode() const {
     return sbqa::persistent_mode(n, Cp, max_degree, kind, persist_blocks, prm.kernel_select == 11);

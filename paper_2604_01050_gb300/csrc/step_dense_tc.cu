@@ -47,6 +47,7 @@ struct TcArgs {
 struct TcMaps {
   CUtensorMap A, B;  // J8 and FT operand tiles (128 x 128 bytes, 128B swizzle)
   CUtensorMap B2;    // FT operand tiles of 256 columns (256 x 128 bytes, 128B swizzle)
+  CUtensorMap B64;   // FT operand half tiles of a CTA pair (64 x 128 bytes, 128B swizzle)
   CUtensorMap X, Y;  // x, y state boxes (128 rows x 32 floats, 128B swizzle)
   CUtensorMap Fst;   // FT tile store (128 columns x 128 spins bytes, no swizzle)
 };
@@ -439,11 +440,33 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 // of the next step's first stages are loaded while the epilogue runs.  A wait
 // that gives up (2 s, or at once when another CTA has already failed)
 // records an error; every CTA then stops at its next step boundary.
-constexpr int kTpStages = 6;
+//
+// Paired form (PAIR): the CTAs of row tiles 2p and 2p+1 (same column tile)
+// form a 2-CTA cluster that shares one M=256 N=128 MMA per K slice
+// (tcgen05 cta_group::2, issued by the even CTA): each CTA stages its own 128
+// J rows and 64 of the 128 fT rows of the column tile, and each keeps the
+// accumulator rows, x and y of its own 128 spins in its own TMEM.  Per CTA the
+// operands of an MMA are then 24 KB per k-block instead of 32 KB, which is
+// what lets the K loop run at the full MMA rate where 128 x 128 tiles fed by
+// TMA run at half of it.  The even CTA's full barrier collects the bytes of
+// both CTAs' loads; MMA completion is multicast to both CTAs' empty and done
+// barriers; a cluster barrier closes every step (so the next step's MMAs do
+// not overwrite an accumulator the odd CTA still reads) and carries the
+// abort decision, so that both CTAs stop at the same step.
 constexpr int kTpThreads = 512;  // 16 warps: warp w updates TMEM lanes 32 (w % 4).. and columns 32 (w / 4)..
-constexpr int kTpSmem = 2 * kTpStages * kTcTile + kTcBM * kTcBN + 1024 + 256;
 constexpr uint32_t kTmemX = 128, kTmemY = 256, kTmemCols = 512;
 constexpr uint64_t kFlagTimeoutNs = 2000000000ull;
+
+template <bool PAIR>
+struct TpShape {
+  static constexpr int kStages = PAIR ? 8 : 6;
+  static constexpr int kTileB = PAIR ? 64 * kTcBK : kTcTile;  // fT rows staged by this CTA: 64 of the pair's 128, or 128
+  static constexpr int kStageBytes = kTcTile + kTileB;
+  static constexpr uint32_t kExpect = PAIR ? 2 * kStageBytes : kStageBytes;  // bytes completing on one full barrier
+  static constexpr int kSmem = kStages * kStageBytes + kTcBM * kTcBN + 1024 + 256;
+};
+static_assert(TpShape<false>::kSmem <= 227 * 1024 && TpShape<true>::kSmem <= 227 * 1024,
+              "persistent tile exceeds the shared memory of one CTA");
 
 struct TpArgs {
   int Kp, Ct, n_begin, n_end;
@@ -490,45 +513,70 @@ __device__ __forceinline__ void sb_update_regs32(const StateView &s, const StepT
   }
 }
 
-template <int P>
-__global__ void __launch_bounds__(kTpThreads, 1)
-    k_solve_dense_tc_persistent(const __grid_constant__ TcMaps m, StateView s, TpArgs a, StepTables t) {
+template <int P, bool PAIR>
+__device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const StateView &s, const TpArgs &a,
+                                                          const StepTables &t) {
+  using Sh = TpShape<PAIR>;
+  constexpr int kStages = Sh::kStages;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t *sA = smem;
-  uint8_t *sB = smem + kTpStages * kTcTile;
-  uint8_t *sF = sB + kTpStages * kTcTile;  // [128 columns][128 spins] e4m3 f(x_next)
+  uint8_t *sB = smem + kStages * kTcTile;
+  uint8_t *sF = sB + kStages * Sh::kTileB;  // [128 columns][128 spins] e4m3 f(x_next)
   uint64_t *full = reinterpret_cast<uint64_t *>(sF + kTcBM * kTcBN);
-  uint64_t *empty = full + kTpStages;
-  uint64_t *done = empty + kTpStages;
+  uint64_t *empty = full + kStages;
+  uint64_t *done = empty + kStages;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
-  int *s_abort = reinterpret_cast<int *>(tmem_slot + 1);
+  int *s_abort = reinterpret_cast<int *>(tmem_slot + 1);  // PAIR: [step parity][rank]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ct = blockIdx.x, mt = blockIdx.y;
+  uint32_t rank = 0;
+  if constexpr (PAIR) {
+    // both CTAs of a cluster read the same cluster shape, so both return here or neither does
+    if (tc::cluster_nctarank() != 2 || tc::cluster_nctaid_x() != 2) {
+      if (threadIdx.x == 0) atomicCAS(a.err, 0, tc::ERR_CLUSTER_SHAPE);
+      return;
+    }
+    rank = tc::cluster_ctarank();  // = blockIdx.x & 1
+  }
+  const bool leader = rank == 0;
+  const int ct = PAIR ? blockIdx.y : blockIdx.x, mt = PAIR ? blockIdx.x : blockIdx.y;
   const int m0 = mt * kTcBM, n0 = ct * kTcBN;
   const int KB = a.Kp / kTcBK;
-  const int npre = KB < kTpStages ? KB : kTpStages;  // k-blocks whose J tile is loaded ahead
+  const int npre = KB < kStages ? KB : kStages;  // k-blocks whose J tile is loaded ahead
+  // this CTA's operand loads: fT rows (B box) and the full barrier they complete on
+  const CUtensorMap *mapB = PAIR ? &m.B64 : &m.B;
+  const int b_off = PAIR ? 64 * int(rank) : 0;
+  auto load_tile = [&](uint8_t *dst, const CUtensorMap *map, int st, int c0_, int c1_) {
+    if constexpr (PAIR)
+      tc::tma_load_2d_pair(dst, map, tc::map_to_rank(tc::smem_u32(&full[st]), 0), c0_, c1_);
+    else
+      tc::tma_load_2d(dst, map, &full[st], c0_, c1_);
+  };
   const int quarter = warp & 3, chunk = warp >> 2;
   const int rl = quarter * 32 + lane, i = m0 + rl;
   const int cl = 32 * chunk, c0 = n0 + cl;
   const uint32_t lane_off = uint32_t(quarter * 32) << 16;
 
   if (threadIdx.x == 0) {
-    for (int q = 0; q < kTpStages; ++q) {
+    for (int q = 0; q < kStages; ++q) {
       tc::mbar_init(&full[q], 1);
       tc::mbar_init(&empty[q], 1);
     }
     tc::mbar_init(done, 1);
     tc::fence_mbar_init();
     tc::prefetch_tmap(&m.A);
-    tc::prefetch_tmap(&m.B);
+    tc::prefetch_tmap(mapB);
     tc::prefetch_tmap(&m.Fst);
-    *s_abort = 0;
+    for (int q = 0; q < 4; ++q) s_abort[q] = 0;
   }
-  if (warp == 0) tc::tmem_alloc(tmem_slot, kTmemCols);
+  if (warp == 0) {
+    if constexpr (PAIR) tc::tmem_alloc_pair(tmem_slot, kTmemCols);
+    else tc::tmem_alloc(tmem_slot, kTmemCols);
+  }
   tc::tc_fence_before();
-  __syncthreads();
+  if constexpr (PAIR) tc::cluster_sync();  // the pair's barriers and TMEM exist before either CTA uses them
+  else __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -557,15 +605,15 @@ __global__ void __launch_bounds__(kTpThreads, 1)
   const float hi = i < s.N ? __ldg(a.h + i) : 0.f;
   if (warp == 0 && lane == 0 && a.n_begin < a.n_end) {  // J tiles of the first step's first stages
     for (int kb = 0; kb < npre; ++kb) {
-      tc::mbar_arrive_expect_tx(&full[kb], 2 * kTcTile);
-      tc::tma_load_2d(sA + kb * kTcTile, &m.A, &full[kb], kb * kTcBK, m0);
+      if (leader) tc::mbar_arrive_expect_tx(&full[kb], Sh::kExpect);
+      load_tile(sA + kb * kTcTile, &m.A, kb, kb * kTcBK, m0);
     }
   }
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
 
-  constexpr uint32_t idesc = tc::idesc_f8_e4m3(kTcBM, kTcBN);
+  constexpr uint32_t idesc = tc::idesc_f8_e4m3(PAIR ? 2 * kTcBM : kTcBM, kTcBN);
   int n = a.n_begin;
   bool prefetched = a.n_begin < a.n_end;
   for (; n < a.n_end; ++n) {
@@ -605,13 +653,13 @@ __global__ void __launch_bounds__(kTpThreads, 1)
           asm volatile("fence.acq_rel.gpu;" ::: "memory");
           tc::fence_proxy_async_global();
           for (int j = kb; j < kb + nready; ++j) {
-            const uint32_t g = q * KB + j, st = g % kTpStages, use = g / kTpStages;
+            const uint32_t g = q * KB + j, st = g % kStages, use = g / kStages;
             if (j >= npre) {
               if (use > 0) tc::mbar_wait(&empty[st], (use - 1) & 1, a.err, tc::ERR_WAIT_EMPTY);
-              tc::mbar_arrive_expect_tx(&full[st], 2 * kTcTile);
-              tc::tma_load_2d(sA + st * kTcTile, &m.A, &full[st], j * kTcBK, m0);
+              if (leader) tc::mbar_arrive_expect_tx(&full[st], Sh::kExpect);
+              load_tile(sA + st * kTcTile, &m.A, st, j * kTcBK, m0);
             }
-            tc::tma_load_2d(sB + st * kTcTile, &m.B, &full[st], j * kTcBK, brow);
+            load_tile(sB + st * Sh::kTileB, mapB, st, j * kTcBK, brow + b_off);
           }
         }
         __syncwarp();
@@ -621,25 +669,29 @@ __global__ void __launch_bounds__(kTpThreads, 1)
       prefetched = n + 1 < a.n_end;
       if (lane == 0 && prefetched) {
         for (int j = 0; j < npre; ++j) {
-          const uint32_t g = (q + 1) * KB + j, st = g % kTpStages, use = g / kTpStages;
+          const uint32_t g = (q + 1) * KB + j, st = g % kStages, use = g / kStages;
           if (use > 0) tc::mbar_wait(&empty[st], (use - 1) & 1, a.err, tc::ERR_WAIT_EMPTY);
-          tc::mbar_arrive_expect_tx(&full[st], 2 * kTcTile);
-          tc::tma_load_2d(sA + st * kTcTile, &m.A, &full[st], j * kTcBK, m0);
+          if (leader) tc::mbar_arrive_expect_tx(&full[st], Sh::kExpect);
+          load_tile(sA + st * kTcTile, &m.A, st, j * kTcBK, m0);
         }
       }
-    } else if (warp == 1 && lane == 0) {
+    } else if (warp == 1 && lane == 0 && leader) {
       for (int kb = 0; kb < KB; ++kb) {
-        const uint32_t g = q * KB + kb, st = g % kTpStages, use = g / kTpStages;
+        const uint32_t g = q * KB + kb, st = g % kStages, use = g / kStages;
         tc::mbar_wait(&full[st], use & 1, a.err, tc::ERR_WAIT_FULL);
         tc::tc_fence_after();
-        const uint32_t a0 = tc::smem_u32(sA + st * kTcTile), b0 = tc::smem_u32(sB + st * kTcTile);
+        const uint32_t a0 = tc::smem_u32(sA + st * kTcTile), b0 = tc::smem_u32(sB + st * Sh::kTileB);
 #pragma unroll
-        for (int kk = 0; kk < kTcBK / 32; ++kk)
-          tc::mma_f8(tmem, tc::smem_desc_sw128(a0 + kk * 32), tc::smem_desc_sw128(b0 + kk * 32), idesc,
-                     (kb | kk) != 0 ? 1u : 0u);
-        tc::mma_commit(&empty[st]);
+        for (int kk = 0; kk < kTcBK / 32; ++kk) {
+          const uint64_t ad = tc::smem_desc_sw128(a0 + kk * 32), bd = tc::smem_desc_sw128(b0 + kk * 32);
+          if constexpr (PAIR) tc::mma_f8_pair(tmem, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
+          else tc::mma_f8(tmem, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
+        }
+        if constexpr (PAIR) tc::mma_commit_pair(&empty[st]);
+        else tc::mma_commit(&empty[st]);
       }
-      tc::mma_commit(done);
+      if constexpr (PAIR) tc::mma_commit_pair(done);
+      else tc::mma_commit(done);
     }
     __syncwarp();
     const float ka = __ldg(t.ka + n), dnext = __ldg(t.dl + n + 1);
@@ -678,11 +730,20 @@ __global__ void __launch_bounds__(kTpThreads, 1)
       tc::tma_store_commit_and_wait_all();
       tc::fence_proxy_async_global();
       tc::st_release_gpu(a.flags + mt * a.Ct + ct, q + 1);
-      *s_abort = *reinterpret_cast<volatile int *>(a.err);
+      const int v = *reinterpret_cast<volatile int *>(a.err);
+      if constexpr (PAIR) {
+        int *slot = s_abort + 2 * (q & 1) + rank;  // double-buffered by step parity
+        *slot = v;
+        tc::st_cluster_u32(tc::map_to_rank(tc::smem_u32(slot), rank ^ 1u), uint32_t(v));
+      } else {
+        *s_abort = v;
+      }
     }
-    __syncthreads();
+    if constexpr (PAIR) tc::cluster_sync();  // also orders the odd CTA's accumulator reads before the next MMAs
+    else __syncthreads();
     tc::tc_fence_after();
-    if (*s_abort != 0) break;
+    const int stop = PAIR ? (s_abort[2 * (q & 1)] | s_abort[2 * (q & 1) + 1]) : *s_abort;
+    if (stop != 0) break;
   }
   if (n < a.n_end && prefetched && warp == 0 && lane == 0) {
     // stopped early with J tiles of step n + 1 in flight: complete those stages
@@ -690,9 +751,9 @@ __global__ void __launch_bounds__(kTpThreads, 1)
     const uint32_t q = uint32_t(n + 1 - a.n_begin);
     const int brow = ((n + 1) & 1) * s.Cp + n0;
     for (int j = 0; j < npre; ++j) {
-      const uint32_t g = q * KB + j, st = g % kTpStages, use = g / kTpStages;
-      tc::tma_load_2d(sB + st * kTcTile, &m.B, &full[st], j * kTcBK, brow);
-      tc::mbar_wait(&full[st], use & 1, a.err, tc::ERR_WAIT_FULL);
+      const uint32_t g = q * KB + j, st = g % kStages, use = g / kStages;
+      load_tile(sB + st * Sh::kTileB, mapB, st, j * kTcBK, brow + b_off);
+      if (leader) tc::mbar_wait(&full[st], use & 1, a.err, tc::ERR_WAIT_FULL);
     }
   }
   __syncwarp();
@@ -716,11 +777,26 @@ __global__ void __launch_bounds__(kTpThreads, 1)
     }
   }
   tc::tc_fence_before();
-  __syncthreads();
+  // PAIR: neither CTA leaves (or frees its TMEM) while the other's MMAs, loads or reads may still use it
+  if constexpr (PAIR) tc::cluster_sync();
+  else __syncthreads();
   if (warp == 0) {
     tc::tc_fence_after();
-    tc::tmem_dealloc(tmem, kTmemCols);
+    if constexpr (PAIR) tc::tmem_dealloc_pair(tmem, kTmemCols);
+    else tc::tmem_dealloc(tmem, kTmemCols);
   }
+}
+
+template <int P>
+__global__ void __launch_bounds__(kTpThreads, 1)
+    k_solve_dense_tc_persistent(const __grid_constant__ TcMaps m, StateView s, TpArgs a, StepTables t) {
+  solve_dense_tc_persistent<P, false>(m, s, a, t);
+}
+
+template <int P>
+__global__ void __launch_bounds__(kTpThreads, 1)
+    k_solve_dense_tc_pair(const __grid_constant__ TcMaps m, StateView s, TpArgs a, StepTables t) {
+  solve_dense_tc_persistent<P, true>(m, s, a, t);
 }
 
 // ---------------------------------------------------------------- split-K persistent solver
@@ -1188,6 +1264,7 @@ bool tc_plan_make(void **plan, const uint8_t *J8, uint8_t *FT, int Kp, int Cp, f
   const bool ok = make_map(&p->A, J8, U8, 1, uint64_t(Kp), uint64_t(Kp), 128, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
                   make_map(&p->B, FT, U8, 1, uint64_t(2) * Cp, uint64_t(Kp), 128, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
                   make_map(&p->B2, FT, U8, 1, uint64_t(2) * Cp, uint64_t(Kp), 128, 256, CU_TENSOR_MAP_SWIZZLE_128B) &&
+                  make_map(&p->B64, FT, U8, 1, uint64_t(2) * Cp, uint64_t(Kp), 128, 64, CU_TENSOR_MAP_SWIZZLE_128B) &&
                   make_map(&p->X, x, F32, 4, uint64_t(N), uint64_t(Cp), 32, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
                   make_map(&p->Y, y, F32, 4, uint64_t(N), uint64_t(Cp), 32, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
                   make_map(&p->Fst, FT, U8, 1, uint64_t(2) * Cp, uint64_t(Kp), 128, 128, CU_TENSOR_MAP_SWIZZLE_NONE);
@@ -1205,6 +1282,11 @@ static const void *const kTpFns[6] = {
     (const void *)k_solve_dense_tc_persistent<1>, (const void *)k_solve_dense_tc_persistent<2>,
     (const void *)k_solve_dense_tc_persistent<4>, (const void *)k_solve_dense_tc_persistent<8>,
     (const void *)k_solve_dense_tc_persistent<16>, (const void *)k_solve_dense_tc_persistent<32>};
+
+static const void *const kPrFns[6] = {
+    (const void *)k_solve_dense_tc_pair<1>, (const void *)k_solve_dense_tc_pair<2>,
+    (const void *)k_solve_dense_tc_pair<4>, (const void *)k_solve_dense_tc_pair<8>,
+    (const void *)k_solve_dense_tc_pair<16>, (const void *)k_solve_dense_tc_pair<32>};
 
 static const void *const kSkFns[6] = {
     (const void *)k_solve_dense_tc_split<1>, (const void *)k_solve_dense_tc_split<2>,
@@ -1227,7 +1309,11 @@ cudaError_t tc_set_attributes() {
     if (e != cudaSuccess) return e;
   }
   for (const void *f : kTpFns) {
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kTpSmem);
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, TpShape<false>::kSmem);
+    if (e != cudaSuccess) return e;
+  }
+  for (const void *f : kPrFns) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, TpShape<true>::kSmem);
     if (e != cudaSuccess) return e;
   }
   for (const void *f : kSkFns) {
@@ -1237,12 +1323,13 @@ cudaError_t tc_set_attributes() {
   return cudaFuncSetAttribute((const void *)k_energy_dense_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kEtSmem);
 }
 
-static void split_config(cudaLaunchConfig_t *cfg, cudaLaunchAttribute *attr, dim3 grid, cudaStream_t st,
-                         bool cooperative) {
+// Launch configuration of a cooperative grid of 2 x 1 x 1 clusters.
+static void cluster_config(cudaLaunchConfig_t *cfg, cudaLaunchAttribute *attr, dim3 grid, int threads, int smem,
+                           cudaStream_t st, bool cooperative) {
   *cfg = cudaLaunchConfig_t{};
   cfg->gridDim = grid;
-  cfg->blockDim = dim3(kSkThreads);
-  cfg->dynamicSmemBytes = kSkSmem;
+  cfg->blockDim = dim3(threads);
+  cfg->dynamicSmemBytes = smem;
   cfg->stream = st;
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 2;
@@ -1259,7 +1346,7 @@ int tc_split_blocks() {
   for (const void *f : kSkFns) {
     cudaLaunchConfig_t cfg;
     cudaLaunchAttribute attr[2];
-    split_config(&cfg, attr, dim3(2, 1), 0, false);
+    cluster_config(&cfg, attr, dim3(2, 1), kSkThreads, kSkSmem, 0, false);
     int clusters = 0;
     if (cudaOccupancyMaxActiveClusters(&clusters, f, &cfg) != cudaSuccess) {
       cudaGetLastError();
@@ -1289,7 +1376,7 @@ cudaError_t launch_solve_dense_tc_split(const void *plan, const StateView &s, in
   void *args[] = {&maps, &sv, &a, &tv};
   cudaLaunchConfig_t cfg;
   cudaLaunchAttribute attr[2];
-  split_config(&cfg, attr, dim3(2 * (s.Cp / kTwBN), Kp / kTcBM), st, true);
+  cluster_config(&cfg, attr, dim3(2 * (s.Cp / kTwBN), Kp / kTcBM), kSkThreads, kSkSmem, st, true);
   return cudaLaunchKernelExC(&cfg, kSkFns[idx], args);
 }
 
@@ -1299,7 +1386,8 @@ int tc_persistent_blocks() {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   for (const void *f : kTpFns) {
     int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kTpThreads, kTpSmem) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kTpThreads, TpShape<false>::kSmem) != cudaSuccess)
+      return 0;
     best = per_sm < best ? per_sm : best;
   }
   return sms * best;
@@ -1324,7 +1412,48 @@ cudaError_t launch_solve_dense_tc_persistent(const void *plan, const StateView &
   StateView sv = s;
   StepTables tv = t;
   void *args[] = {&maps, &sv, &a, &tv};
-  return cudaLaunchCooperativeKernel(kTpFns[idx], dim3(Ct, Kp / kTcBM), dim3(kTpThreads), args, kTpSmem, st);
+  return cudaLaunchCooperativeKernel(kTpFns[idx], dim3(Ct, Kp / kTcBM), dim3(kTpThreads), args,
+                                     TpShape<false>::kSmem, st);
+}
+
+int tc_pair_blocks() {
+  int best = 1 << 30;
+  for (const void *f : kPrFns) {
+    cudaLaunchConfig_t cfg;
+    cudaLaunchAttribute attr[2];
+    cluster_config(&cfg, attr, dim3(2, 1), kTpThreads, TpShape<true>::kSmem, 0, false);
+    int clusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&clusters, f, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    best = clusters < best ? clusters : best;
+  }
+  return 2 * best;
+}
+
+bool tc_pair_eligible(int Kp, int Cp, int blocks) {
+  return blocks > 0 && Kp % (2 * kTcBM) == 0 && Cp % kTcBN == 0 && (Kp / kTcBM) * (Cp / kTcBN) <= blocks;
+}
+
+cudaError_t launch_solve_dense_tc_pair(const void *plan, const StateView &s, int Kp, int *err, const float *h,
+                                       const StepTables &t, int n_begin, int n_end, uint32_t *flags,
+                                       cudaStream_t st) {
+  const int idx = s.P == 1 ? 0 : s.P == 2 ? 1 : s.P == 4 ? 2 : s.P == 8 ? 3 : s.P == 16 ? 4 : s.P == 32 ? 5 : -1;
+  if (idx < 0 || Kp % (2 * kTcBM) != 0 || s.Cp % kTcBN != 0) return cudaErrorInvalidValue;
+  const int Ct = s.Cp / kTcBN;
+  cudaError_t e = cudaMemsetAsync(flags, 0, tc_persistent_flag_count(Kp, s.Cp) * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  TpArgs a{Kp, Ct, n_begin, n_end, err, h, flags};
+  TcMaps maps = *static_cast<const TcMaps *>(plan);
+  StateView sv = s;
+  StepTables tv = t;
+  void *args[] = {&maps, &sv, &a, &tv};
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[2];
+  // row tiles along x (cluster pairs 2p, 2p+1), column tiles along y
+  cluster_config(&cfg, attr, dim3(Kp / kTcBM, Ct), kTpThreads, TpShape<true>::kSmem, st, true);
+  return cudaLaunchKernelExC(&cfg, kPrFns[idx], args);
 }
 
 template <int P>

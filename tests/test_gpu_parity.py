@@ -181,22 +181,29 @@ def _split_k(N, P, R):
     return pad(N) % 256 == 0 and pad(P * R) % 256 == 0
 
 
+def _pair(N):
+    """The paired persistent solver (2-CTA clusters sharing M=256 MMAs) takes
+    padded N a multiple of 256."""
+    return -(-N // 128) * 128 % 256 == 0
+
+
 @pytest.mark.parametrize("N,P,R,jmax", [(300, 8, 40, 3), (512, 16, 16, 1), (1000, 32, 32, 1), (260, 4, 33, 16),
                                         (500, 8, 48, 5), (700, 2, 128, 1), (1000, 16, 9, 2)])
 def test_persistent_dense_tc_solver_matches_per_step(sb, N, P, R, jmax):
     """The persistent tcgen05 solvers (x, y resident in tensor memory, per-tile
-    step flags between CTAs; 128 x 128 tiles, and where padded N and R * P
-    are multiples of 256 the split-K solver on 2-CTA clusters) and the
-    per-step tcgen05 kernel give bit-identical runs, readouts every 37 steps
-    included; ragged row and column tiles (N = 300, 260, 500, 700, 1000; R * P
-    = 320, 132, 384, 144 -- the last on the split-K solver)."""
+    step flags between CTAs; 128 x 128 tiles; where padded N and R * P are
+    multiples of 256 the split-K solver on 2-CTA clusters; where padded N is
+    a multiple of 256 the paired solver whose 2-CTA clusters share M=256
+    MMAs) and the per-step tcgen05 kernel give bit-identical runs, readouts
+    every 37 steps included; ragged row and column tiles (N = 300, 260, 500,
+    700, 1000; R * P = 320, 132, 384, 144)."""
     pb, spec = dense_int(N, N + R, jmax=jmax)
     out = []
-    for sel in (1, 2, 12):
+    for sel in (1, 2, 12, 13):
         prob = create(sb, spec)
         sb.set_schedule(prob, *workloads.autotune_params(R, N), **_params(kernel_select=sel, eval_every=37))
         sb.run(prob, 200, P, R, seed=N)
-        want = {1: 2, 2: 8 if _split_k(N, P, R) else 5, 12: 5}[sel]
+        want = {1: 2, 2: 8 if _split_k(N, P, R) else 5, 12: 5, 13: 9 if _pair(N) else 5}[sel]
         assert prob.info().step_kernel == want
         out.append((sb.get_state(prob)[:2], sb.get_energies(prob), sb.get_best(prob)))
     (xa, ya), ea, ba = out[0]
@@ -221,7 +228,7 @@ def test_dense_tensor_core_readout_matches_cuda_cores(sb, N, P, R, jmax):
         prob = create(sb, spec)
         sb.set_schedule(prob, *workloads.autotune_params(R, 5), **_params(precision=prec, eval_every=29))
         sb.run(prob, 120, P, R, seed=7)
-        assert (prob.info().step_kernel in (2, 5, 8)) if prec == "exact" else prob.info().step_kernel == 1
+        assert (prob.info().step_kernel in (2, 5, 8, 9)) if prec == "exact" else prob.info().step_kernel == 1
         _, ei = sb.get_energies(prob)
         x, _, _ = sb.get_state(prob)
         res.append((ei, sb.get_best(prob), x))
@@ -233,14 +240,14 @@ def test_dense_tensor_core_readout_matches_cuda_cores(sb, N, P, R, jmax):
     assert np.array_equal(ea, oracle.energies(pb, np.where(xa >= 0, 1, -1)))
 
 
-@pytest.mark.parametrize("N,want", [(384, 5), (512, 8)])
-def test_persistent_dense_tc_solver_resume(sb, N, want):
+@pytest.mark.parametrize("N,sel,want", [(384, 2, 5), (512, 2, 8), (768, 13, 9)])
+def test_persistent_dense_tc_solver_resume(sb, N, sel, want):
     """Stretches of the persistent tcgen05 solvers (128 x 128 tiles at N =
-    384; split-K clusters at N = 512) resumed across begin/advance/finish
-    give the state of one uninterrupted run."""
+    384; split-K clusters at N = 512; CTA pairs at N = 768) resumed across
+    begin/advance/finish give the state of one uninterrupted run."""
     pb, spec = sk(N, 9)
     prob = create(sb, spec)
-    sb.set_schedule(prob, *workloads.autotune_params(16, 9), **_params(kernel_select=2))
+    sb.set_schedule(prob, *workloads.autotune_params(16, 9), **_params(kernel_select=sel))
     sb.run(prob, 150, 16, 16, seed=4)
     xa, ya, _ = sb.get_state(prob)
     sb.run_begin(prob, 150, 16, 16, seed=4)
@@ -795,7 +802,7 @@ def test_full_size_dense_sk2000_energies(sb):
     prob = create(sb, spec)
     sb.set_schedule(prob, *workloads.autotune_params(32, 1), **_params(precision="exact"))
     sb.run(prob, 30, 32, 32, seed=0)
-    assert prob.info().step_kernel in (2, 5, 8)
+    assert prob.info().step_kernel in (2, 5, 8, 9)
     e, ei = sb.get_energies(prob)
     x, _, _ = sb.get_state(prob)
     best = sb.get_best(prob)
