@@ -19,7 +19,9 @@
  * receives it; the caller keeps ownership of its buffers and may free them
  * when the call returns.  Output buffers are owned by the caller and must
  * hold the documented number of elements.  A problem handle owns all device
- * memory it allocates and releases it in sbqa_destroy().
+ * memory it allocates and releases it in sbqa_destroy(), which keeps the
+ * released blocks in a process-wide cache for later handles (a few GiB per
+ * device at most; sbqa_release_cached_memory() returns them to the driver).
  *
  * Threads and streams.  Calls on one handle must not overlap (no internal
  * lock); different handles are independent.  Device work of a handle is
@@ -98,8 +100,16 @@ int sbqa_create_problem_csr(int32_t n, int64_t nnz, const int64_t *row_ptr,
                             const double *h, sbqa_problem **out);
 
 /* Releases every resource of the handle (NULL is ignored).  Waits for the
- * handle's outstanding device work first. */
+ * handle's outstanding device work first.  Its device blocks go to the
+ * library's cache of device memory (see below), not back to the driver. */
 void sbqa_destroy(sbqa_problem *p);
+
+/* Returns every device block held in the library's cache of released
+ * problem buffers (on all devices) to the driver.  Handles created later
+ * allocate afresh.  Safe at any time: cached blocks are not in use.  Returns
+ * SBQA_OK, or SBQA_ERR_CUDA if a cudaFree failed (the remaining blocks are
+ * still released). */
+int sbqa_release_cached_memory(void);
 
 typedef struct {
     int32_t n;          /* spins                                           */

@@ -35,7 +35,7 @@ VARIANTS = {"threshold": VARIANT_THRESHOLD, "ballistic": VARIANT_BALLISTIC}
 
 # Every symbol include/sbqa.h declares.
 EXPORTS = (
-    "sbqa_create_problem_dense", "sbqa_create_problem_csr", "sbqa_destroy",
+    "sbqa_create_problem_dense", "sbqa_create_problem_csr", "sbqa_destroy", "sbqa_release_cached_memory",
     "sbqa_get_problem_info", "sbqa_default_params", "sbqa_set_schedule", "sbqa_run",
     "sbqa_run_begin", "sbqa_run_advance", "sbqa_run_finish", "sbqa_synchronize",
     "sbqa_get_best", "sbqa_get_energies", "sbqa_get_state", "sbqa_set_state",
@@ -87,6 +87,7 @@ def _load():
         "sbqa_create_problem_dense": (ctypes.c_int, [i32, P(dbl), P(dbl), P(vp)]),
         "sbqa_create_problem_csr": (ctypes.c_int, [i32, i64, P(i64), P(i32), P(dbl), P(dbl), P(vp)]),
         "sbqa_destroy": (None, [vp]),
+        "sbqa_release_cached_memory": (ctypes.c_int, []),
         "sbqa_get_problem_info": (ctypes.c_int, [vp, P(ProblemInfo)]),
         "sbqa_default_params": (None, [P(Params)]),
         "sbqa_set_schedule": (ctypes.c_int, [vp, P(Params)]),
@@ -145,6 +146,11 @@ def _stream(stream) -> int:
 
 def version() -> int:
     return int(lib.sbqa_version())
+
+
+def release_cached_memory() -> None:
+    """Return the device blocks the library keeps from destroyed problems to the driver."""
+    _check(lib.sbqa_release_cached_memory(), "release_cached_memory")
 
 
 def default_params() -> Params:

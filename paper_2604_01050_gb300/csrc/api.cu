@@ -58,21 +58,121 @@ struct DeviceGuard {
 
 int sbqa::set_error(int code, const std::string &msg) { return fail(code, msg); }
 
+// ---------------------------------------------------------------- device block cache
+namespace {
+
+constexpr size_t kCacheCapBytes = size_t(4) << 30;  // per device
+
+struct DevCache {
+  std::mutex mu;
+  std::map<int, std::multimap<size_t, void *>> blocks;  // device -> (size class, block)
+  std::map<int, size_t> held;                           // device -> bytes held
+};
+
+DevCache &devcache() {
+  static DevCache *c = new DevCache();  // never destroyed: blocks are left to the driver at exit
+  return *c;
+}
+
+size_t size_class(size_t bytes) {
+  if (bytes <= (size_t(1) << 20)) {
+    size_t c = 512;
+    while (c < bytes) c <<= 1;
+    return c;
+  }
+  const size_t g = size_t(2) << 20;
+  return (bytes + g - 1) / g * g;
+}
+
+// cudaFree of every cached block of device dev (every device if dev < 0);
+// the caller holds the lock.  False if a cudaFree failed.
+bool trim_locked(DevCache &c, int dev) {
+  bool ok = true;
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (auto &kv : c.blocks) {
+    if (dev >= 0 && kv.first != dev) continue;
+    if (!kv.second.empty()) cudaSetDevice(kv.first);
+    for (auto &b : kv.second) ok = cudaFree(b.second) == cudaSuccess && ok;
+    kv.second.clear();
+    c.held[kv.first] = 0;
+  }
+  cudaSetDevice(cur);
+  return ok;
+}
+
+}  // namespace
+
+cudaError_t sbqa::devcache_get(void **p, size_t bytes, size_t *got) {
+  const size_t cls = size_class(bytes);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  DevCache &c = devcache();
+  {
+    std::lock_guard<std::mutex> lk(c.mu);
+    auto &m = c.blocks[dev];
+    auto it = m.find(cls);
+    if (it != m.end()) {
+      *p = it->second;
+      *got = cls;
+      m.erase(it);
+      c.held[dev] -= cls;
+      return cudaSuccess;
+    }
+  }
+  e = cudaMalloc(p, cls);
+  if (e == cudaErrorMemoryAllocation) {  // give the cached blocks back and try once more
+    cudaGetLastError();
+    {
+      std::lock_guard<std::mutex> lk(c.mu);
+      trim_locked(c, dev);
+    }
+    e = cudaMalloc(p, cls);
+  }
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return e;
+  }
+  *got = cls;
+  return cudaSuccess;
+}
+
+void sbqa::devcache_put(void *p, size_t bytes) {
+  if (!p) return;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return;
+  DevCache &c = devcache();
+  std::lock_guard<std::mutex> lk(c.mu);
+  if (c.held[dev] + bytes > kCacheCapBytes) {
+    cudaFree(p);
+    return;
+  }
+  c.blocks[dev].emplace(bytes, p);
+  c.held[dev] += bytes;
+}
+
+bool sbqa::devcache_trim() {
+  DevCache &c = devcache();
+  std::lock_guard<std::mutex> lk(c.mu);
+  return trim_locked(c, -1);
+}
+
 sbqa_problem::~sbqa_problem() {
   DeviceGuard g(device);
   cudaDeviceSynchronize();  // no kernel of this handle may still use the buffers
   if (graph) cudaGraphExecDestroy(graph);
   if (cap_stream) cudaStreamDestroy(cap_stream);
   if (tc_plan) tc_plan_free(tc_plan);
-  d_J8.release(); d_FT.release(); d_err.release();
-  d_row_ptr.release(); d_col.release(); d_col_pm1.release(); d_npos.release(); d_val_f32.release();
-  d_val_bf16.release(); d_dense_f32.release(); d_h.release(); d_e_i32.release();
-  d_e_f64.release(); d_h_i64.release(); d_h_f64.release(); d_x.release(); d_y.release();
-  d_F0.release(); d_F1.release(); d_Fx0.release(); d_Fx1.release(); d_Sg.release();
-  d_ell_col.release(); d_ell_meta.release(); d_ell_val.release(); d_ka.release(); d_dl.release();
-  d_kj.release(); d_ei.release(); d_part_i.release(); d_best_ei.release(); d_ef.release();
-  d_part_f.release(); d_best_e.release(); d_best_k.release(); d_best_step.release();
-  d_have.release(); d_best_spins.release(); d_bar.release(); d_tc_flags.release();
+  d_J8.release(true); d_FT.release(true); d_err.release(true);
+  d_row_ptr.release(true); d_col.release(true); d_col_pm1.release(true); d_npos.release(true); d_val_f32.release(true);
+  d_val_bf16.release(true); d_dense_f32.release(true); d_h.release(true); d_e_i32.release(true);
+  d_e_f64.release(true); d_h_i64.release(true); d_h_f64.release(true); d_x.release(true); d_y.release(true);
+  d_F0.release(true); d_F1.release(true); d_Fx0.release(true); d_Fx1.release(true); d_Sg.release(true);
+  d_ell_col.release(true); d_ell_meta.release(true); d_ell_val.release(true); d_ka.release(true); d_dl.release(true);
+  d_kj.release(true); d_ei.release(true); d_part_i.release(true); d_best_ei.release(true); d_ef.release(true);
+  d_part_f.release(true); d_best_e.release(true); d_best_k.release(true); d_best_step.release(true);
+  d_have.release(true); d_best_spins.release(true); d_bar.release(true); d_tc_flags.release(true);
 }
 
 
@@ -179,17 +279,28 @@ int upload_common(sbqa_problem *p) {
 }
 
 int upload_readout_values(sbqa_problem *p) {
-  const size_t m = p->val.size();
+  const size_t m = p->jcount();
   if (m == 0) return SBQA_OK;
+  const int64_t blk = 1 << 16, tasks = (int64_t(m) + blk - 1) / blk;
   if (p->is_integer) {
-    std::vector<int32_t> vi(m);
-    const int64_t blk = 1 << 16;
-    parallel_tasks((int64_t(m) + blk - 1) / blk, [&](int64_t t, int64_t) {
+    HostVec<int32_t> vi(m);
+    parallel_tasks(tasks, [&](int64_t t, int64_t) {
       const size_t e1 = std::min(m, size_t(t + 1) * blk);
-      for (size_t e = size_t(t) * blk; e < e1; ++e) vi[e] = int32_t(std::llround(p->val[e]));
+      if (!p->val_i8.empty())
+        for (size_t e = size_t(t) * blk; e < e1; ++e) vi[e] = p->val_i8[e];
+      else
+        for (size_t e = size_t(t) * blk; e < e1; ++e) vi[e] = int32_t(std::llround(p->val[e]));
     });
     SBQA_CUDA(p->d_e_i32.alloc(m));
     SBQA_CUDA(cudaMemcpy(p->d_e_i32.p, vi.data(), m * sizeof(int32_t), cudaMemcpyHostToDevice));
+  } else if (!p->val_i8.empty()) {  // integer J beside a real h
+    HostVec<double> vd(m);
+    parallel_tasks(tasks, [&](int64_t t, int64_t) {
+      const size_t e1 = std::min(m, size_t(t + 1) * blk);
+      for (size_t e = size_t(t) * blk; e < e1; ++e) vd[e] = p->val_i8[e];
+    });
+    SBQA_CUDA(p->d_e_f64.alloc(m));
+    SBQA_CUDA(cudaMemcpy(p->d_e_f64.p, vd.data(), m * sizeof(double), cudaMemcpyHostToDevice));
   } else {
     SBQA_CUDA(p->d_e_f64.alloc(m));
     SBQA_CUDA(cudaMemcpy(p->d_e_f64.p, p->val.data(), m * sizeof(double), cudaMemcpyHostToDevice));
@@ -316,8 +427,13 @@ int prepare_tc_values(sbqa_problem *p) {
       std::memset(out, 0, size_t(Kp));
       return;
     }
-    const double *row = p->val.data() + size_t(i) * N;
-    for (int j = 0; j < N; ++j) out[j] = lut[int(row[j]) + 16];  // integers, checked when J was analysed
+    if (!p->val_i8.empty()) {
+      const int8_t *row = p->val_i8.data() + size_t(i) * N;
+      for (int j = 0; j < N; ++j) out[j] = lut[row[j] + 16];  // |J_ij| <= 16, checked when J was analysed
+    } else {
+      const double *row = p->val.data() + size_t(i) * N;
+      for (int j = 0; j < N; ++j) out[j] = lut[int(row[j]) + 16];
+    }
     std::memset(out + N, 0, size_t(Kp - N));
   });
   SBQA_CUDA(p->d_J8.alloc(j8.size()));
@@ -332,23 +448,33 @@ int prepare_dense_values(sbqa_problem *p, int precision) {
   // the FP8 tensor-core product is exact only for f in {-1, 0, 1}: thresholded form only
   p->use_tc = (precision == SBQA_PREC_AUTO || precision == SBQA_PREC_EXACT) && p->j_integer &&
               p->max_abs_j <= 16 && p->n >= kTcMinN && !p->ballistic();
-  if (p->use_tc) return prepare_tc_values(p);  // the readout runs on the tensor cores too
+  if (p->use_tc) {
+    // the readout runs on the tensor cores too when its energies are integers;
+    // with a non-integer h it runs on the CUDA cores in FP64
+    const int rc = prepare_tc_values(p);
+    if (rc != SBQA_OK || p->is_integer || p->d_e_f64.p) return rc;
+    return upload_readout_values(p);
+  }
   if (!p->d_e_i32.p && !p->d_e_f64.p) {
     const int rc = upload_readout_values(p);
     if (rc != SBQA_OK) return rc;
   }
   const int want = precision == SBQA_PREC_BF16 ? SBQA_PREC_BF16 : SBQA_PREC_FP32;
   if (p->d_dense_f32.p && p->dense_prec == want) return SBQA_OK;
-  const size_t m = p->val.size();
-  std::vector<float> v(m);
-  for (size_t e = 0; e < m; ++e) {
-    if (want == SBQA_PREC_BF16) {
-      const uint32_t u = uint32_t(bf16_bits_rne(p->val[e])) << 16;
-      std::memcpy(&v[e], &u, 4);
-    } else {
-      v[e] = float(p->val[e]);
+  const size_t m = p->jcount();
+  HostVec<float> v(m);
+  const int64_t blk = 1 << 16;
+  parallel_tasks((int64_t(m) + blk - 1) / blk, [&](int64_t t, int64_t) {
+    const size_t e1 = std::min(m, size_t(t + 1) * blk);
+    for (size_t e = size_t(t) * blk; e < e1; ++e) {
+      if (want == SBQA_PREC_BF16) {
+        const uint32_t u = uint32_t(bf16_bits_rne(p->jv(e))) << 16;
+        std::memcpy(&v[e], &u, 4);
+      } else {
+        v[e] = float(p->jv(e));
+      }
     }
-  }
+  });
   SBQA_CUDA(p->d_dense_f32.alloc(m));
   SBQA_CUDA(cudaMemcpy(p->d_dense_f32.p, v.data(), m * sizeof(float), cudaMemcpyHostToDevice));
   p->dense_prec = want;
@@ -749,9 +875,9 @@ int autotune_tc(sbqa_problem *p) {
 
 cudaError_t issue_readout(sbqa_problem *p, int step, cudaStream_t st) {
   const StateView s = p->state();
-  // integer dense instances on the tensor cores: the sign codes take the FT
-  // buffer of step `step`, which the next step does not read
-  cudaError_t e = p->dense ? (p->use_tc && p->tc_plan ? launch_energy_dense_tc(p->tc_plan, s, p->Kp, p->d_FT.p,
+  // integer dense instances (J and h) on the tensor cores: the sign codes take
+  // the FT buffer of step `step`, which the next step does not read
+  cudaError_t e = p->dense ? (p->use_tc && p->tc_plan && p->is_integer ? launch_energy_dense_tc(p->tc_plan, s, p->Kp, p->d_FT.p,
                                                                                step & 1, p->d_err.p, p->energy(),
                                                                                p->best(), st)
                                                       : launch_energy_dense(s, p->energy(), p->best(), st))
@@ -831,7 +957,7 @@ int sbqa::problem_build_tables(const sbqa_problem *p, int S, int P, int R, float
   }
   // S * R transcendental evaluations (640 000 for 10^4 steps of 64 runs), in
   // blocks of steps over the host threads; each entry is computed alone
-  constexpr int kStepsPerTask = 256;
+  constexpr int kStepsPerTask = 64;
   parallel_tasks((int64_t(S) + kStepsPerTask - 1) / kStepsPerTask, [&](int64_t task, int64_t) {
     const int n1 = std::min(S, int(task + 1) * kStepsPerTask);
     for (int n = int(task) * kStepsPerTask; n < n1; ++n) {
@@ -928,20 +1054,23 @@ int sbqa_create_problem_dense(int32_t n, const double *J, const double *h, sbqa_
     JStats js;
   };
   std::vector<Block> blocks(nb);
-  HostVec<double> vals;  // the library's copy, filled block by block in the same pass
-  vals.resize(m);
+  // The library's copy: one byte per entry, filled in the same pass, which is
+  // the whole copy when J turns out integer with |J_ij| <= 127 (the FP64 copy
+  // is made afterwards otherwise).
+  HostVec<int8_t> vals8(m);
   parallel_tasks(nb, [&](int64_t b, int64_t) {
     Block &B = blocks[b];
     const int i0 = int(b) * kB, i1 = std::min(n, i0 + kB);
-    std::memcpy(vals.data() + size_t(i0) * n, J + size_t(i0) * n, size_t(i1 - i0) * n * sizeof(double));
     for (int i = i0; i < i1; ++i) {
       const double *row = J + size_t(i) * n;
+      int8_t *row8 = vals8.data() + size_t(i) * n;
       int32_t d = 0;
       for (int j = 0; j < n; ++j) {
         const double v = row[j];
         if (!std::isfinite(v)) B.finite = false;
         d += v != 0.0;
         B.js.add(v);
+        row8[j] = int8_t(v >= -128.0 && v <= 127.0 ? int(v) : 0);
       }
       if (row[i] != 0.0) B.diag = false;
       B.nnz += d;
@@ -974,7 +1103,16 @@ int sbqa_create_problem_dense(int32_t n, const double *J, const double *h, sbqa_
   cudaGetDevice(&p->device);
   p->n = n;
   p->dense = true;
-  p->val = std::move(vals);
+  if (js.j_int && js.mx <= 127.0) {
+    p->val_i8 = std::move(vals8);
+  } else {
+    vals8 = HostVec<int8_t>();
+    p->val.resize(m);
+    parallel_tasks(nb, [&](int64_t b, int64_t) {
+      const int i0 = int(b) * kB, i1 = std::min(n, i0 + kB);
+      std::memcpy(p->val.data() + size_t(i0) * n, J + size_t(i0) * n, size_t(i1 - i0) * n * sizeof(double));
+    });
+  }
   if (h) p->h.assign(h, h + n);
   p->nnz = nnz;
   p->max_degree = maxdeg;
@@ -1065,6 +1203,10 @@ int sbqa_create_problem_csr(int32_t n, int64_t nnz, const int64_t *row_ptr, cons
 }
 
 void sbqa_destroy(sbqa_problem *p) { delete p; }
+
+int sbqa_release_cached_memory(void) {
+  return sbqa::devcache_trim() ? SBQA_OK : fail(SBQA_ERR_CUDA, "cudaFree of a cached block failed");
+}
 
 int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info) {
   if (!p || !info) return fail(SBQA_ERR_INVALID_ARG, "null argument");

@@ -258,7 +258,9 @@ int readout(sbqa_engine *e, Request &r, cudaStream_t st) {
   sbqa_problem *p = r.prob;
   const StateView s = r.state_view();
   const EnergyView ev = problem_energy_view(p);
-  const bool tc = p->dense && r.tc_plan;
+  // the tensor-core readout needs integer energies (J and h); a non-integer h
+  // takes the FP64 CUDA-core readout (the product still runs on the tensor cores)
+  const bool tc = p->dense && r.tc_plan && p->is_integer;
   cudaError_t err = tc ? launch_energy_dense_tc(r.tc_plan, s, p->Kp, r.FT, (r.S - 1) & 1, r.err, ev, r.best_view(), st)
                        : p->dense ? launch_energy_dense(s, ev, r.best_view(), st)
                                   : launch_energy_csr(s, problem_csr_readout_view(p), ev, r.best_view(), st);

@@ -35,23 +35,46 @@ struct NoInitAlloc : std::allocator<T> {
 template <typename T>
 using HostVec = std::vector<T, NoInitAlloc<T>>;
 
+// Process-wide cache of released device blocks (api.cu).  A handle created
+// after another of the same shape takes its buffers from here instead of from
+// cudaMalloc, and a destroyed handle's buffers come back here instead of going
+// to cudaFree.  Blocks are kept per device and size class (powers of two up to
+// 1 MiB, then multiples of 2 MiB) up to a cap per device; a cudaMalloc that
+// fails for lack of memory empties the cache of that device and is tried once
+// more.  devcache_put must only see blocks that no queued or running work can
+// still use.  sbqa_release_cached_memory() empties the cache.
+cudaError_t devcache_get(void **p, size_t bytes, size_t *got);
+void devcache_put(void *p, size_t bytes);
+bool devcache_trim();  // cudaFree of every cached block; false if one failed
+
 template <typename T>
 struct DevBuf {
   T *p = nullptr;
-  size_t n = 0;
+  size_t n = 0;      // elements the block holds (at least the count asked for)
+  size_t bytes = 0;  // its size class
   cudaError_t alloc(size_t count) {
     if (count <= n && p) return cudaSuccess;
     release();
     if (count == 0) return cudaSuccess;
-    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&p), count * sizeof(T));
-    if (e == cudaSuccess) n = count;
-    else p = nullptr;
-    return e;
+    void *q = nullptr;
+    size_t got = 0;
+    const cudaError_t e = devcache_get(&q, count * sizeof(T), &got);
+    if (e != cudaSuccess) return e;
+    p = static_cast<T *>(q);
+    n = got / sizeof(T);
+    bytes = got;
+    return cudaSuccess;
   }
-  void release() {
-    if (p) cudaFree(p);
+  // idle: the caller has synchronized the device, so no work still uses the
+  // block; otherwise this waits for the device first, as cudaFree would.
+  void release(bool idle = false) {
+    if (p) {
+      if (!idle) cudaDeviceSynchronize();
+      devcache_put(p, bytes);
+    }
     p = nullptr;
     n = 0;
+    bytes = 0;
   }
 };
 
@@ -81,7 +104,10 @@ struct sbqa_problem {
   // host copies (CSR for sparse, row-major for dense)
   std::vector<int64_t> row_ptr;
   std::vector<int32_t> col;
-  sbqa::HostVec<double> val;  // CSR values or dense N*N
+  sbqa::HostVec<double> val;  // CSR values or dense N*N (empty when val_i8 holds the dense copy)
+  sbqa::HostVec<int8_t> val_i8;  // dense integer J with |J_ij| <= 127, one byte per entry
+  size_t jcount() const { return val_i8.empty() ? val.size() : val_i8.size(); }
+  double jv(size_t e) const { return val_i8.empty() ? val[e] : double(val_i8[e]); }
   std::vector<double> h;
 
   // device: product operands

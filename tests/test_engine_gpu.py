@@ -21,6 +21,13 @@ def sb():
     return s
 
 
+def _sk_real_h(n, seed):
+    """+-1 SK couplings with a Gaussian field: the product is exact on the
+    tensor cores, the energies are not integers."""
+    J, _ = workloads.sk_pm1(n, seed)
+    return ("dense", J, np.random.default_rng(seed).normal(0.0, 0.5, n))
+
+
 def _requests(sb):
     """(problem handle, steps, P, R, seed, precision) of a mixed workload."""
     out = []
@@ -35,6 +42,7 @@ def _requests(sb):
             (regular(400, 6, 5)[1], 80, 16, 16, "bf16"),  # 8 columns per lane, ELL values
             (lattice(6, 6)[1], 40, 2, 201, "auto"),   # 8 columns per lane, ragged inside a lane (R P = 402)
             (regular(300, 6, 7)[1], 40, 32, 16, "fp32"),  # 8 columns per lane, FP32 ELL values, R P = 512
+            (_sk_real_h(300, 9), 50, 8, 2, "auto"),   # tcgen05 product, FP64 readout (non-integer h)
     ]):
         pb = create(sb, spec)
         sb.set_schedule(pb, *workloads.autotune_params(R, k), precision=prec, eval_every=0)

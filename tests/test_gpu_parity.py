@@ -240,6 +240,54 @@ def test_dense_tensor_core_readout_matches_cuda_cores(sb, N, P, R, jmax):
     assert np.array_equal(ea, oracle.energies(pb, np.where(xa >= 0, 1, -1)))
 
 
+def test_cached_device_blocks_give_identical_runs(sb):
+    """Handles created after others were destroyed take their device buffers
+    from the library's cache, old contents included; their runs equal the
+    first handle's bit for bit, and so do runs after the cache was returned to
+    the driver (dense on the tensor cores, and a +-1 lattice in CSR)."""
+    for spec, P, R in ((sk(384, 3)[1], 16, 8), (lattice(6, 2)[1], 8, 16)):
+        res = []
+        for k in range(4):
+            prob = create(sb, spec)
+            sb.set_schedule(prob, *workloads.autotune_params(R, 2), **_params(eval_every=23))
+            sb.run(prob, 90, P, R, seed=11)
+            res.append((sb.get_state(prob)[:2], sb.get_energies(prob)[1], sb.get_best(prob)))
+            prob.destroy()
+            if k == 2:
+                sb.release_cached_memory()
+        (xa, ya), ea, ba = res[0]
+        for (xb, yb), eb, bb in res[1:]:
+            assert np.array_equal(xa, xb) and np.array_equal(ya, yb) and np.array_equal(ea, eb)
+            for key in ba:
+                assert np.array_equal(ba[key], bb[key]), key
+
+
+@pytest.mark.parametrize("jmax,real_h", [(100, False), (100, True), (200, False), (16, True)])
+def test_dense_host_copy_forms(sb, jmax, real_h):
+    """The library keeps a dense integer J with |J_ij| <= 127 as one byte per
+    entry and any other J in FP64: the readout energies of the final spins
+    equal the oracle's (exact for integer J and h, 1e-12 relative with a real
+    h), with the FP32 step path and the tensor-core path alike."""
+    N, P, R = 300, 4, 6
+    rng = np.random.default_rng(jmax + real_h)
+    up = np.triu(rng.integers(-jmax, jmax + 1, (N, N)).astype(float), 1)
+    J = up + up.T
+    h = rng.normal(0.0, 0.7, N) if real_h else rng.integers(-3, 4, N).astype(float)
+    pb = oracle.Problem.dense(J, h)
+    for prec in (("exact", "fp32") if jmax <= 16 else ("fp32",)):
+        prob = sb.create_problem_dense(J, h)
+        sb.set_schedule(prob, *workloads.autotune_params(R, 4), **_params(precision=prec))
+        sb.run(prob, 60, P, R, seed=5)
+        x, _, _ = sb.get_state(prob)
+        e, ei = sb.get_energies(prob)
+        ref = oracle.energies(pb, np.where(x >= 0, 1, -1))
+        if real_h:
+            assert np.allclose(e, ref, rtol=1e-12, atol=1e-9)
+        else:
+            assert np.array_equal(ei, ref)
+        prob.destroy()
+
+
 @pytest.mark.parametrize("N,sel,want", [(384, 2, 5), (512, 2, 8), (768, 13, 9)])
 def test_persistent_dense_tc_solver_resume(sb, N, sel, want):
     """Stretches of the persistent tcgen05 solvers (128 x 128 tiles at N =
