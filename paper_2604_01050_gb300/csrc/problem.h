@@ -4,6 +4,7 @@
 #include <cstdint>
 #include <cstring>
 #include <memory>
+#include <new>
 #include <utility>
 #include <vector>
 
@@ -14,9 +15,18 @@
 
 namespace sbqa {
 
+// Process-wide cache of large host blocks (api.cu): arrays of 1 MiB and more
+// (copies of J, staging of device uploads) are kept after use, up to a cap,
+// so that the next handle of a similar size writes into pages that are
+// already mapped instead of faulting in fresh ones (64 MB for the byte copy
+// of a dense J at N = 8192).  Size classes are multiples of 1 MiB.
+constexpr size_t kHostCacheMin = size_t(1) << 20;
+void *hostcache_get(size_t bytes);          // a block of at least `bytes`; nullptr when out of memory
+void hostcache_put(void *p, size_t bytes);  // `bytes` as given to hostcache_get
+
 // Allocator that leaves value-initialised elements uninitialised, for host
 // arrays that are filled right after they are sized (a dense J of 8192^2
-// doubles is 512 MB).
+// doubles is 512 MB); blocks of 1 MiB and more come from the host cache.
 template <typename T>
 struct NoInitAlloc : std::allocator<T> {
   template <typename U>
@@ -26,6 +36,18 @@ struct NoInitAlloc : std::allocator<T> {
   NoInitAlloc() = default;
   template <typename U>
   NoInitAlloc(const NoInitAlloc<U> &) {}
+  T *allocate(size_t count) {
+    const size_t bytes = count * sizeof(T);
+    if (bytes < kHostCacheMin) return std::allocator<T>::allocate(count);
+    void *q = hostcache_get(bytes);
+    if (!q) throw std::bad_alloc();
+    return static_cast<T *>(q);
+  }
+  void deallocate(T *q, size_t count) {
+    const size_t bytes = count * sizeof(T);
+    if (bytes < kHostCacheMin) std::allocator<T>::deallocate(q, count);
+    else hostcache_put(q, bytes);
+  }
   template <typename U, typename... A>
   void construct(U *q, A &&...a) {
     if constexpr (sizeof...(A) == 0) ::new (static_cast<void *>(q)) U;
