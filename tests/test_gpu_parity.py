@@ -89,7 +89,14 @@ def _per_step(sb, pb, spec, P, R, S, steps, seed=3, prec="auto", pb_oracle=None,
     x, y, _ = sb.get_state(prob)
     worst_x = worst_y = 0.0
     amb_total = 0
+    thr_total, thr_steps = 0, []
     for n in range(steps):
+        # threshold-sensitive: a position within 1e-6 of the threshold that decides f(x_n) (Eq. 8),
+        # where FP32 and FP64 may take different sides; reported, never excluded
+        near = int((np.abs(np.abs(x.astype(np.float64)) - d[n]) < 1e-6).sum())
+        if near:
+            thr_total += near
+            thr_steps.append(n)
         sb.run_advance(prob, 1)
         xg, yg, sd = sb.get_state(prob)
         assert sd == n + 1
@@ -103,6 +110,8 @@ def _per_step(sb, pb, spec, P, R, S, steps, seed=3, prec="auto", pb_oracle=None,
         yg_c = np.where(amb, 0.0, yg); yo_c = np.where(amb, 0.0, yo)
         worst_y = max(worst_y, rel_err(yg_c, yo_c))
         x, y = xg, yg
+    if thr_total:
+        print("threshold-sensitive positions: %d at steps %s (seed %d)" % (thr_total, thr_steps[:20], seed))
     return worst_x, worst_y, amb_total, prob
 
 
