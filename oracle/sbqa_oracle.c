@@ -39,8 +39,8 @@
  * Readings where the paper is silent:
  *   - integrator: symplectic Euler, y from x(t_n) first, x from the new y,
  *     then the wall; step n uses tau_n = n/S;
- *   - f at the threshold: |x| <= Delta gives 0 (inclusive), decided in the
- *     FP32 precision of the GPU kernel: (float)|x| <= (float)Delta_n;
+ *   - f at the threshold: |x| <= Delta gives 0 (inclusive), compared in
+ *     FP64 like every other step of this file;
  *   - readout sign: x >= 0 gives +1;
  *   - wall: strict |x| > 1 after the position update, then x <- sign(x),
  *     y <- 0;
@@ -166,7 +166,7 @@ double orc_c0_auto(const orc_problem *pb)
 double orc_f(double x, double delta, int variant)
 {
     if (variant == 1) return x;
-    if ((float)fabs(x) <= (float)delta) return 0.0;
+    if (fabs(x) <= delta) return 0.0;
     return x > 0.0 ? 1.0 : -1.0;
 }
 

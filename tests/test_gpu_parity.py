@@ -12,6 +12,10 @@ Bars (stated once here, used below):
     replica mode is stable), and for the first 20 steps at Gamma_x(0) = 1,
     where that mode is linearly unstable from t = 0 and amplifies rounding
     differences;
+  * the threshold f of Eq. 8 is decided in FP32 by the kernels and in FP64 by
+    the oracle: positions within 1e-6 of Delta are counted as
+    threshold-sensitive, and every position where the two decisions differ
+    is listed by seed and step (never excluded from a comparison);
   * integer energies: bit-exact; real energies: 1e-12 relative (FP64 sums in
     another order);
   * BF16 product: against the oracle on the BF16-rounded J, TOL_STEP per step
@@ -90,6 +94,7 @@ def _per_step(sb, pb, spec, P, R, S, steps, seed=3, prec="auto", pb_oracle=None,
     worst_x = worst_y = 0.0
     amb_total = 0
     thr_total, thr_steps = 0, []
+    flips = []
     for n in range(steps):
         # threshold-sensitive: a position within 1e-6 of the threshold that decides f(x_n) (Eq. 8),
         # where FP32 and FP64 may take different sides; reported, never excluded
@@ -97,6 +102,9 @@ def _per_step(sb, pb, spec, P, R, S, steps, seed=3, prec="auto", pb_oracle=None,
         if near:
             thr_total += near
             thr_steps.append(n)
+        nf = _threshold_flips(x, x.astype(np.float64), d[n])
+        if nf:
+            flips.append((n, nf))
         sb.run_advance(prob, 1)
         xg, yg, sd = sb.get_state(prob)
         assert sd == n + 1
@@ -112,7 +120,17 @@ def _per_step(sb, pb, spec, P, R, S, steps, seed=3, prec="auto", pb_oracle=None,
         x, y = xg, yg
     if thr_total:
         print("threshold-sensitive positions: %d at steps %s (seed %d)" % (thr_total, thr_steps[:20], seed))
+    if flips:
+        print("FP32/FP64 threshold flips (step, count): %s (seed %d)" % (flips[:20], seed))
     return worst_x, worst_y, amb_total, prob
+
+
+def _threshold_flips(x32, x64, delta):
+    """Positions whose f of Eq. 8 differs between the kernel's decision (|x| <= Delta compared in
+    FP32, on its FP32 state and the FP32-rounded Delta) and the oracle's (FP64 state, FP64 Delta)."""
+    dev = np.abs(np.asarray(x32, dtype=np.float32)) <= np.float32(delta)
+    orc = np.abs(np.asarray(x64, dtype=np.float64)) <= delta
+    return int((dev != orc).sum())
 
 
 def test_per_step_dense_sk64_default_schedule(sb):
@@ -336,11 +354,19 @@ def _free_running(sb, pb, spec, P, R, S, steps, gamma0, seed=0, prec="auto", pb_
     sb.run_begin(prob, S, P, R, seed=seed)
     ref = oracle.run(pb_oracle or pb, S, P, R, seed, beta, alpha, gamma0=gamma0, n_end=steps, n_traj=steps,
                      **_oracle_kwargs(p, pb))
+    a, d, _ = oracle.schedule(S, P, R, beta, alpha, gamma0)
     errs = []
+    flips = []
     for n in range(steps):
         sb.run_advance(prob, 1)
         xg, yg, _ = sb.get_state(prob)
         errs.append((rel_err(xg, ref["traj_x"][n]), rel_err(yg, ref["traj_y"][n])))
+        # the decision of f (Eq. 8) that the next step takes, on each side's own state
+        nf = _threshold_flips(xg, ref["traj_x"][n], d[n + 1]) if n + 1 < steps else 0
+        if nf:
+            flips.append((n + 1, nf, float(errs[-1][0])))
+    if flips:
+        print("FP32/FP64 threshold flips (step, count, x error before it): %s (seed %d)" % (flips[:20], seed))
     return np.array(errs)
 
 

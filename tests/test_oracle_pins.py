@@ -111,8 +111,10 @@ def test_threshold_function_cases():
     assert oracle.f(1e-30, 0.0) == 1.0
     assert oracle.f(-1e-30, 0.0) == -1.0
     assert oracle.f(0.123, 0.7, variant=1) == 0.123
-    # decided in FP32: a value above Delta only in FP64 counts as on the threshold
-    assert oracle.f(0.3 + 1e-12, 0.3) == 0.0
+    # compared in FP64: a value above Delta by far less than an FP32 ulp is above it
+    assert oracle.f(0.3 + 1e-12, 0.3) == 1.0
+    assert oracle.f(-(0.3 + 1e-12), 0.3) == -1.0
+    assert oracle.f(0.3 - 1e-12, 0.3) == 0.0
 
 
 # ---------------------------------------------------------------- force = -dH/dq
@@ -205,7 +207,7 @@ def _plain_sb(J, h, x, y, S, a0, c0, dt, delta_slope):
     for n in range(S):
         tau = n / S
         d = delta_slope * tau
-        fx = np.where(np.abs(x).astype(np.float32) <= np.float32(d), 0.0, np.sign(x))
+        fx = np.where(np.abs(x) <= d, 0.0, np.sign(x))
         y = y + dt * (-(a0 - tau) * x + c0 * (J @ fx + (h if h is not None else 0.0)))
         x = x + dt * a0 * y
         over = np.abs(x) > 1
