@@ -314,13 +314,18 @@ int sbqa_engine_submit(sbqa_engine *e, sbqa_problem *p, int32_t steps,
  * steps on `stream` (a cudaStream_t), reads out the finished ones and waits
  * for the device.  *n_done receives how many finished; the first `cap` of
  * their ids go to done_ids (host, may be NULL when cap = 0).
- * Errors: CUDA, TIMEOUT. */
+ * Errors: CUDA, TIMEOUT.  TIMEOUT means that a bounded device wait of at
+ * least one finished request gave up: every finished request (failed or
+ * not) has still left its slot and arena space and is listed in done_ids;
+ * sbqa_engine_result returns TIMEOUT for the failed ones and the results of
+ * the others; the engine keeps serving. */
 int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done,
                      int32_t *done_ids, int32_t cap);
 
 /* Result of a finished request (host buffers, any may be NULL):
  * spins R*N int8, energy R doubles, energy_int R int64 (integer instances),
- * replica R int32 -- as sbqa_get_best.  Errors: INVALID_ARG, STATE. */
+ * replica R int32 -- as sbqa_get_best.  Errors: INVALID_ARG, STATE (not
+ * finished), TIMEOUT (the request failed, see sbqa_engine_step). */
 int sbqa_engine_result(sbqa_engine *e, int32_t id, int8_t *spins,
                        double *energy, int64_t *energy_int,
                        int32_t *replica);

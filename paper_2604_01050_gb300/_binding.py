@@ -340,11 +340,18 @@ def engine_submit(eng: Engine, pb: Problem, steps, P, R, seed=0) -> int:
 
 
 def engine_step(eng: Engine, stream=None, cap=4096):
+    """Ids of the requests that finished in this step.  On TIMEOUT the raised
+    SBQAError carries them as ``done_ids`` (failed ones included)."""
     n = ctypes.c_int32()
     ids = np.empty(cap, dtype=np.int32)
-    _check(lib.sbqa_engine_step(eng.handle, _stream(stream) or None, ctypes.byref(n), _p(ids, ctypes.c_int32),
-                                int(cap)), "engine_step")
-    return ids[:min(n.value, cap)].tolist()
+    st = lib.sbqa_engine_step(eng.handle, _stream(stream) or None, ctypes.byref(n), _p(ids, ctypes.c_int32),
+                              int(cap))
+    done = ids[:min(n.value, cap)].tolist()
+    if st != OK:
+        err = SBQAError(st, "engine_step", lib.sbqa_last_error().decode())
+        err.done_ids = done
+        raise err
+    return done
 
 
 def engine_result(eng: Engine, rid):

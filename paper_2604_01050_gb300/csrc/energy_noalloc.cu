@@ -136,18 +136,20 @@ extern "C" int sbqa_energies_csr_noalloc(int32_t n, const int32_t *row_ptr, cons
                                          const double *h_f64, const int8_t *spins, int32_t ld, int32_t count,
                                          int64_t *energy_int, double *energy, void *stream) {
   const bool integer = val_i32 != nullptr;
-  if (n < 1 || count < 1 || ld < count || !row_ptr || !spins || (integer == (val_f64 != nullptr)) ||
+  if (n < 1 || count < 1 || ld < count || !row_ptr || !col_idx || !spins || (integer == (val_f64 != nullptr)) ||
       (!integer && (h_i64 || !energy)) || (integer && (h_f64 || (!energy_int && !energy))))
     return sbqa::set_error(SBQA_ERR_INVALID_ARG,
-                           "sbqa_energies_csr_noalloc: need n, count >= 1, ld >= count, row_ptr, spins, exactly one "
-                           "of val_i32 / val_f64 with the matching h and an output");
-  const int nblk = (n + kRows - 1) / kRows;
-  const int cols_pad = (count + kCols - 1) / kCols * kCols;
-  if (size_t(nblk) * size_t(cols_pad) > kScratchWords)
+                           "sbqa_energies_csr_noalloc: need n, count >= 1, ld >= count, row_ptr, col_idx, spins, "
+                           "exactly one of val_i32 / val_f64 with the matching h and an output");
+  // sizes in 64 bits: count near INT32_MAX must reach the limit check, not overflow before it
+  const int64_t nblk64 = (int64_t(n) + kRows - 1) / kRows;
+  const int64_t cols_pad64 = (int64_t(count) + kCols - 1) / kCols * kCols;
+  if (nblk64 * cols_pad64 > int64_t(kScratchWords))
     return sbqa::set_error(SBQA_ERR_UNSUPPORTED,
                            "sbqa_energies_csr_noalloc: ceil(n/32) * ceil(count/128)*128 = " +
-                               std::to_string(size_t(nblk) * cols_pad) + " exceeds the scratch limit of " +
+                               std::to_string(nblk64 * cols_pad64) + " exceeds the scratch limit of " +
                                std::to_string(kScratchWords) + " partial sums (4 MiB)");
+  const int nblk = int(nblk64), cols_pad = int(cols_pad64);
   void *scratch = nullptr;
   int rc = scratch_for_current_device(&scratch);
   if (rc != SBQA_OK) return rc;

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <cstdlib>
 #include <deque>
 #include <map>
 #include <string>
@@ -69,7 +70,9 @@ struct Arena {
   }
 };
 
-enum ReqState { QUEUED = 0, ACTIVE = 1, DONE = 2 };
+// FAILED: a bounded device wait of the request gave up; it left its slot and
+// arena space like a finished request and has no result.
+enum ReqState { QUEUED = 0, ACTIVE = 1, DONE = 2, FAILED = 3 };
 
 struct Request {
   int id = -1;
@@ -440,21 +443,31 @@ int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done, int32_t *don
     ENG_CUDA(cudaEventElapsedTime(&ms, e->batched_t0, e->batched_t1));
     e->batched_ms += ms;
   }
+  // Every finished request leaves its slot and arena space, also one whose
+  // device wait gave up: it is retired as FAILED and the others still
+  // complete; TIMEOUT is returned once all of them are retired.
+  const char *fail_hook = std::getenv("SBQA_TEST_ENGINE_FAIL_REQUEST");
+  const int fail_id = fail_hook ? std::atoi(fail_hook) : -1;
+  std::string failed_ids;
   for (int id : finished) {
     Request &r = e->reqs[id];
     int err = 0;
     ENG_CUDA(cudaMemcpy(&err, r.err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (err) return set_error(SBQA_ERR_TIMEOUT, "a bounded device wait gave up in request " + std::to_string(id));
+    if (id == fail_id) err = 1;  // test hook: the request's device error word as a failed wait leaves it
     if (r.tc_plan) {
       tc_plan_free(r.tc_plan);
       r.tc_plan = nullptr;
     }
     e->slot_req[r.slot] = -1;
     e->arena.release(r.off, r.bytes);
-    r.state = DONE;
+    r.state = err ? FAILED : DONE;
+    if (err) failed_ids += (failed_ids.empty() ? "" : ", ") + std::to_string(id);
     if (*n_done < cap && done_ids) done_ids[*n_done] = id;
     ++*n_done;
   }
+  if (!failed_ids.empty())
+    return set_error(SBQA_ERR_TIMEOUT, "a bounded device wait gave up in request(s) " + failed_ids +
+                                           "; they were retired without a result, the others completed");
   return SBQA_OK;
 }
 
@@ -462,6 +475,8 @@ int sbqa_engine_result(sbqa_engine *e, int32_t id, int8_t *spins, double *energy
                        int32_t *replica) {
   if (!e || id < 0 || id >= int(e->reqs.size())) return set_error(SBQA_ERR_INVALID_ARG, "unknown request");
   const Request &r = e->reqs[id];
+  if (r.state == FAILED)
+    return set_error(SBQA_ERR_TIMEOUT, "request " + std::to_string(id) + " failed: a bounded device wait gave up");
   if (r.state != DONE) return set_error(SBQA_ERR_STATE, "request not finished");
   if (spins) std::memcpy(spins, r.spins.data(), r.spins.size());
   if (energy) std::memcpy(energy, r.energy.data(), r.energy.size() * sizeof(double));
@@ -476,7 +491,7 @@ int sbqa_engine_stats(const sbqa_engine *e, sbqa_engine_stats_t *s) {
   s->active = 0;
   for (int q : e->slot_req) s->active += q >= 0;
   s->finished = 0;
-  for (const auto &r : e->reqs) s->finished += r.state == DONE;
+  for (const auto &r : e->reqs) s->finished += r.state == DONE || r.state == FAILED;
   s->arena_bytes = int64_t(e->arena.bytes);
   s->arena_used = int64_t(e->arena.used);
   s->updates_issued = e->steps_done_total;

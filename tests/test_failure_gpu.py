@@ -4,7 +4,10 @@ The persistent CSR solver's grid barrier is bounded (1 s by %globaltimer).
 The host-side test hook SBQA_TEST_SKIP_BARRIER_STEP=n makes block 0 skip its
 arrival after step n, so every block's wait runs out; the kernel ends, the
 run reports SBQA_ERR_TIMEOUT at the next synchronisation, and the handle
-stays usable.  Nothing faults, traps or hangs the device.
+stays usable.  The batching engine's host hook
+SBQA_TEST_ENGINE_FAIL_REQUEST=id makes it read one request's device error
+word as set: that request is retired with TIMEOUT and the others complete.
+Nothing faults, traps or hangs the device.
 """
 import numpy as np
 import pytest
@@ -48,3 +51,37 @@ def test_barrier_timeout_is_reported_and_the_handle_recovers(sb, monkeypatch):
     xb, _, _ = sb.get_state(ref)
     assert np.array_equal(xa, xb)
     assert np.array_equal(ea, sb.get_best(ref)["energy"])
+
+
+def test_engine_retires_a_failed_request_and_keeps_serving(sb, monkeypatch):
+    """A request whose device wait gave up (the host hook SBQA_TEST_ENGINE_FAIL_REQUEST=id makes the
+    engine read that request's error word as set) is retired with TIMEOUT: its slot and arena space are
+    released, the requests beside it and after it complete with the result of solving them alone."""
+    specs = [lattice(6, 1)[1], lattice(5, 2)[1], lattice(6, 3)[1], lattice(5, 4)[1]]
+    probs = []
+    for k, spec in enumerate(specs):
+        pb = create(sb, spec)
+        sb.set_schedule(pb, *workloads.autotune_params(4, k), eval_every=0)
+        probs.append(pb)
+    eng = sb.engine_create(256 << 20, 2, 20)  # two slots: the last two requests wait for the first two
+    ids = [sb.engine_submit(eng, pb, 40, 8, 4, seed=10 + k) for k, pb in enumerate(probs)]
+    monkeypatch.setenv("SBQA_TEST_ENGINE_FAIL_REQUEST", str(ids[1]))
+    done, timeouts = [], 0
+    for _ in range(100):
+        try:
+            done += sb.engine_step(eng)
+        except sb.SBQAError as e:
+            assert e.status == sb.ERR_TIMEOUT
+            timeouts += 1
+            done += e.done_ids
+        if len(done) == len(ids):
+            break
+    assert sorted(done) == ids and timeouts == 1
+    with pytest.raises(sb.SBQAError) as e:
+        sb.engine_result(eng, ids[1])
+    assert e.value.status == sb.ERR_TIMEOUT
+    for k in (0, 2, 3):
+        sb.run(probs[k], 40, 8, 4, seed=10 + k)
+        assert np.array_equal(sb.engine_result(eng, ids[k])["energy"], sb.get_best(probs[k])["energy"])
+    st = sb.engine_stats(eng)
+    assert st["active"] == 0 and st["arena_used"] == 0 and st["finished"] == 4

@@ -1,4 +1,4 @@
-"""sbqa_energies_csr_noalloc against the solver's own readout.
+"""sbqa_energies_csr_noalloc against the solver's own readout and the oracle.
 
 The entry point serves callers that cannot allocate device memory where they
 need energies (inside a CUDA graph capture, in loops that must not block in
@@ -10,6 +10,7 @@ run every other test; it also passes when run alone in a fresh process.
 import numpy as np
 import pytest
 
+import oracle
 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -62,6 +63,8 @@ def test_noalloc_integer_energies_match_solver_two_calls(env):
         torch.cuda.synchronize()
         assert np.array_equal(out_i.cpu().numpy(), ei_ref)
         assert np.array_equal(out_f.cpu().numpy(), e_ref)
+        # and the exact integer energies of the oracle (Eq. 4 sign) on the same spins
+        assert np.array_equal(out_i.cpu().numpy(), oracle.energies(oracle.Problem.csr(n, rp, col, val, h), spins))
 
 
 def test_noalloc_real_energies_match_solver_two_calls(env):
@@ -79,6 +82,8 @@ def test_noalloc_real_energies_match_solver_two_calls(env):
                                 val_f64=d_val.data_ptr(), h_f64=d_h.data_ptr(), energy=out.data_ptr())
         torch.cuda.synchronize()
         assert np.allclose(out.cpu().numpy(), e_ref, rtol=1e-12, atol=1e-9)
+        ref = oracle.energies(oracle.Problem.csr(n, rp, col, val, h), spins[:6])
+        assert np.allclose(out.cpu().numpy()[:6], ref, rtol=1e-12, atol=1e-9)
 
 
 def test_noalloc_rejects_sizes_beyond_scratch(env):
@@ -92,3 +97,7 @@ def test_noalloc_rejects_sizes_beyond_scratch(env):
                                 val_i32=rp.data_ptr(), energy_int=out.data_ptr())
     assert e.value.status == sb.ERR_UNSUPPORTED
     assert "scratch" in sb.lib.sbqa_last_error().decode()
+    with pytest.raises(sb.SBQAError) as e:  # a NULL column array is refused before any launch
+        sb.energies_csr_noalloc(8, rp.data_ptr(), 0, sp.data_ptr(), 1, 1,
+                                val_i32=rp.data_ptr(), energy_int=out.data_ptr())
+    assert e.value.status == sb.ERR_INVALID_ARG
