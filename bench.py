@@ -1,10 +1,15 @@
 #!/usr/bin/env python
 """Benchmark of the SBQA hot path (replica-spin updates/s) on GB300.
 
-One benchmark step = one whole solve of the default workload: initial state,
-10^4 steps of the SBQA equations of motion on a periodic 3D cubic lattice
-L=16 (N=4096, J=+-1, CSR) with P=32 Trotter replicas and R=64 auto-tuned runs,
-then the readout (sign, energies of all 2048 replicas, best per run).
+One benchmark step = one whole solve of the headline workload: initial
+state, 5000 steps of the SBQA equations of motion on a random 6-regular graph
+(N=10^5, J ~ N(0,1), h ~ N(0, 0.1^2), CSR, BF16 couplings) with P=16 Trotter
+replicas and R=8 auto-tuned runs, then the readout (sign, energies of all 128
+replicas, best per run).  Its state (128 MB) exceeds the L2 cache, so every
+step streams it through HBM.  The same line carries ``per_config`` records,
+measured the same way, of the 3D cubic lattice L=16 (N=4096, P=32, R=64,
+10^4 steps), the dense SK N=2000 instance on the tensor cores (P=32, R=32,
+1000 steps) and the Poisson serving stream (p50/p99 latency).
 
   value   updates/s = N * P * R * steps / solve time, with J resident on the
           device (CUDA events on the library's stream; L2 flushed before every
@@ -13,7 +18,9 @@ then the readout (sign, energies of all 2048 replicas, best per run).
           problem from pinned host arrays, set the schedule, run, read the best
           result back, destroy -- all inside the timed region
   roofline  the step kernel against the measured HBM copy bandwidth, with the
-          algorithmic 16 bytes per replica-spin update (x, y read + write)
+          algorithmic 16 bytes per replica-spin update (x, y read + write),
+          or, for the dense tensor-core kernels, 2 N^2 R P flops per step
+          against the measured dense GEMM peak of their operand type
 
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the
 same workload instead (rank 0 only).  Under torchrun every rank solves its own
@@ -66,7 +73,6 @@ CONFIGS["sk8192t"] = dict(kind="sk", n=8192, P=8, R=32, S=200, prec="exact",
                           workload="dense SK N=8192, J=+-1; P=8, R=32 (J.X = 8192x8192 @ 8192x256), 200 steps")
 SCALING = ["lattice16", "lattice24", "lattice32", "lattice48", "lattice64", "lattice88", "regular1e5", "regular7e5",
            "sk2000", "sk4096", "sk8192", "sk8192t"]
-DEFAULT = "lattice16"
 BYTES_PER_UPDATE = 16  # x, y FP32 read + write per replica-spin update
 BYTES_PER_UPDATE_BSB = 20  # ballistic form: + the FP32 f (= x) write
 # DRAM traffic per step (dram__bytes_read.sum + dram__bytes_write.sum of one
@@ -206,20 +212,32 @@ def oracle_sample(cfg, target_s=15.0, threads=None):
 
 
 def run_reference(args, cfg):
+    """The reference arm: the oracle as it stands on the host cores.  Each of
+    the K timed steps is one bounded sample of the workload (sized so that
+    the whole run ends within a couple of minutes); ``ms_per_step`` is the
+    measured wall time of one sample, and the time a whole solve would take
+    at the sampled rate is reported separately, marked as extrapolated."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    vals = []
+    per_sample = max(2.0, min(args.ref_seconds, 90.0 / max(1, args.steps)))
     for _ in range(args.warmup):
-        oracle_sample(cfg, target_s=2.0)
-    samples = [oracle_sample(cfg, target_s=args.ref_seconds) for _ in range(args.steps)]
+        oracle_sample(cfg, target_s=1.0)
+    samples, walls = [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        samples.append(oracle_sample(cfg, target_s=per_sample))
+        walls.append(time.perf_counter() - t0)
     vals = [s["value"] for s in samples]
     value = statistics.mean(vals)
     upd_per_solve = n_of(make_instance(cfg)) * cfg["P"] * cfg["R"] * cfg["S"]
     line = {"impl": "reference", "metric": "replica-spin updates/s", "value": value,
             "unit": "replica-spin updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * upd_per_solve / value, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * statistics.mean(walls), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "step_is": "one bounded sample of the workload (ms_per_step = its measured wall time)",
+            "extrapolated_ms_per_solve": {"value": 1e3 * upd_per_solve / value, "extrapolated": True,
+                                          "note": "a whole solve at the sampled rate; not timed"},
             "config": {"workload": cfg["workload"], "sample": samples[-1]["sample"]},
             "cpu_baseline": dict(samples[-1], value=value),
             "e2e": {"value": value, "unit": "replica-spin updates/s", "h2d_bytes_per_step": 0,
@@ -230,16 +248,18 @@ def run_reference(args, cfg):
 
 
 # ------------------------------------------------------------------ serving stream
-def run_serving(args):
-    """Poisson stream through the batching engine: p50/p99 latency."""
+def run_serving(args, stream=None):
+    """Poisson stream through the batching engine: p50/p99 latency.  Returns
+    the JSON record."""
     import torch
-    torch.cuda.set_device(0)
+    if stream is None:
+        torch.cuda.set_device(0)
+        stream = torch.cuda.Stream()
     from paper_2604_01050_gb300 import build as _b
     _b.build()
     from paper_2604_01050_gb300 import serving
     pool = serving.make_pool(12, seed=0)
     reqs = serving.make_requests(pool, args.requests, steps=2000, R=16, seed=1)
-    stream = torch.cuda.Stream()
     arena = int(args.arena_gb * (1 << 30))
     serving.run_stream(reqs[:6], None, stream=stream, arena_bytes=arena)  # warm-up (autotune, first launches)
     closed = serving.run_stream(reqs, None, stream=stream, arena_bytes=arena)
@@ -280,8 +300,9 @@ def run_serving(args):
                        "closed_loop_updates_per_s": closed["updates"] / closed["makespan_s"]},
             "p50_s": head["p50_s"], "loads": loads, "gpu_launches": head["kernels_launched"],
             "roofline": roof, "cpu_baseline": cpu}
-    print(json.dumps(line))
-    return 0
+    for inst in pool:
+        inst["problem"].destroy()
+    return line
 
 
 # ------------------------------------------------------------------ time-to-epsilon
@@ -564,44 +585,27 @@ def run_scaling(args):
 
 
 # ------------------------------------------------------------------ GPU arm
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--config", default=DEFAULT, choices=sorted(CONFIGS) + ["serving", "tte", "scaling", "sweep"])
-    ap.add_argument("--kernel-select", type=int, default=0,
-                    help="sbqa_params.kernel_select (0: the autotuner's choice; e.g. 12 pins the 128 x 128 "
-                         "persistent dense solver, for profiles)")
-    ap.add_argument("--variant", default="threshold", choices=["threshold", "ballistic"],
-                    help="f of Eq. 8 (SBQA) or f(x) = x (the bSB form)")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-seconds", type=float, default=15.0)
-    ap.add_argument("--requests", type=int, default=48, help="serving: requests in the stream")
-    ap.add_argument("--arena-gb", type=float, default=40.0, help="serving: device arena of the engine (GB)")
-    ap.add_argument("--eps", type=float, default=0.08, help="tte: target optimality gap of the headline")
-    ap.add_argument("--gamma0", type=float, default=16.0, help="tte: Gamma_x(0)")
-    ap.add_argument("--tte-L", type=int, default=10)
-    ap.add_argument("--tte-kind", default="lattice", choices=["lattice", "sk"], help="tte: instance family")
-    ap.add_argument("--tte-n", type=int, default=1024, help="tte: N of the dense SK instance")
-    ap.add_argument("--tte-steps", type=int, default=2000)
-    args = ap.parse_args()
-    if args.config == "serving":
-        return run_serving(args)
-    if args.config == "tte":
-        return run_tte(args)
-    if args.config == "scaling":
-        return run_scaling(args)
-    if args.config == "sweep":
-        return run_sweep(args)
-    cfg = dict(CONFIGS[args.config])
-    if args.variant == "ballistic":
-        cfg["variant"] = "ballistic"
-        cfg["workload"] += "; ballistic form f(x) = x"
-    if args.impl == "reference":
-        return run_reference(args, cfg)
+def load_peaks():
+    """Measured HBM copy and BF16 GEMM peaks, plus the FP8 e4m3 GEMM
+    peak measured by ``bench.py --config fp8peak`` and recorded in
+    profiles/fp8_e4m3_dense_peak.md (lines ``fp8_tflops_burst: X``)."""
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    try:
+        for ln in open(os.path.join(ROOT, "profiles", "fp8_e4m3_dense_peak.md")):
+            ln = ln.strip().strip("`")
+            for key in ("fp8_tflops_burst", "fp8_tflops_sustained"):
+                if ln.startswith(key + ":"):
+                    peaks[key] = float(ln.split(":", 1)[1].split()[0])
+    except Exception:
+        pass
+    return peaks
 
+
+def gpu_context():
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -614,17 +618,81 @@ def main():
         dist = None
         torch.cuda.set_device(0)
     dev = torch.device("cuda", torch.cuda.current_device())
-
     from paper_2604_01050_gb300 import build as _b
     _b.build()
     import paper_2604_01050_gb300 as sb
     from paper_2604_01050_gb300 import multi
+    return {"torch": torch, "sb": sb, "multi": multi, "dist": dist, "rank": rank, "world": world, "dev": dev,
+            "stream": torch.cuda.Stream(device=dev), "peaks": load_peaks()}
 
+
+KERNEL_NAMES = {0: "k_step_csr", 1: "k_step_dense", 2: "k_step_dense_tc", 3: "k_solve_small",
+                4: "k_solve_csr_persistent", 5: "k_solve_dense_tc_persistent", 6: "k_step_csr_bsb",
+                7: "k_step_dense_bsb", 8: "k_solve_dense_tc_split", 9: "k_solve_dense_tc_pair",
+                10: "k_step_dense_tc_bf16", 11: "k_solve_dense_tc_persistent_bf16"}
+KERNEL_LABELS = {0: "csr", 1: "dense_cuda_core", 2: "dense_tcgen05_fp8", 3: "dense_small_one_launch",
+                 4: "csr_persistent", 5: "dense_tcgen05_persistent", 6: "csr_ballistic", 7: "dense_ballistic",
+                 8: "dense_tcgen05_persistent_split_k", 9: "dense_tcgen05_persistent_cta_pairs",
+                 10: "dense_tcgen05_bf16", 11: "dense_tcgen05_persistent_bf16"}
+TC_FP8 = (2, 5, 8, 9)
+TC_BF16 = (10, 11)
+
+
+def roofline_of(cfg, name, info, N, P, R, step_ms, peaks):
+    """The step kernel's roofline: algorithmic bytes (or flops) per step over
+    the event-timed step time, against the measured peak of its bound."""
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    kname = KERNEL_NAMES.get(info.step_kernel, "k_%d" % info.step_kernel)
+    if info.step_kernel == 2 and (-(-P * R // 128) * 128) % 256 == 0:
+        kname = "k_step_dense_tc_wide"  # 128 x 256 tiles when the padded columns allow
+    tr = TRAFFIC_PER_STEP.get(name + ("/ballistic" if cfg.get("variant") == "ballistic" else ""))
+    traffic = tr["bytes_per_step"] if tr and tr["kernel"] == kname else None
+    if info.step_kernel in TC_FP8 + TC_BF16:  # a contraction: 2 N^2 R P flops per step
+        flops = 2.0 * N * N * P * R
+        achieved = flops / (step_ms * 1e-3) / 1e12
+        if info.step_kernel in TC_FP8:
+            if "fp8_tflops_burst" in peaks:
+                peak, src = peaks["fp8_tflops_burst"], "measured (e4m3 GEMM, profiles/fp8_e4m3_dense_peak.md)"
+            else:
+                peak, src = 2.0 * peaks.get("bf16_tflops", 1900.0), "derived: 2 x measured BF16"
+            dt = "FP8 e4m3"
+        else:
+            peak, src, dt = peaks.get("bf16_tflops", 1900.0), peak_src + " (BF16 GEMM burst)", "BF16"
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": kname, "step_ms": step_ms, "peak_source": src,
+                "note": "2 N^2 R P flops per step / event-timed step time; %s dense peak" % dt}
+    if info.step_kernel == 3:
+        # the one-launch small dense solver computes from shared memory and registers: FP32 ALU work,
+        # 2 N flops of the product + 12 of the update per replica-spin update, against the FP32 FMA
+        # rate of the SMs (152 SMs x 128 lanes x 2 flops x the maximum SM clock)
+        flops = (2.0 * N + 12.0) * N * P * R
+        achieved = flops / (step_ms * 1e-3) / 1e12
+        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": kname, "step_ms": step_ms, "peak_source": "derived",
+                "note": "(2N + 12) FP32 flops per update / event-timed step time; peak = 152 SMs x 128 FP32 lanes "
+                        "x 2 x max SM clock; one CTA per run (%d of 152 SMs busy): latency-bound" % R}
+    bpu = BYTES_PER_UPDATE_BSB if info.step_kernel in (6, 7) else BYTES_PER_UPDATE
+    achieved_gbs = bpu * N * P * R / (step_ms * 1e-3) / 1e9
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    return {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved_gbs / hbm_peak, "traffic": traffic, "kernel": kname, "step_ms": step_ms,
+            "peak_source": peak_src, "note": "algorithmic %d B/update x N*P*R per launch / event-timed step time" % bpu}
+
+
+def measure_config(name, cfg, args, ctx, cpu_seconds):
+    """One config: W warm-up solves, K timed solves (CUDA events on the
+    library's stream, L2 flushed before each), zero-step solves for the
+    step kernel's share, end to end through the C ABI from pinned host
+    buffers, and the oracle's bounded CPU sample.  Returns the JSON record."""
+    torch, sb, multi, dist = ctx["torch"], ctx["sb"], ctx["multi"], ctx["dist"]
+    rank, world, dev, stream, peaks = ctx["rank"], ctx["world"], ctx["dev"], ctx["stream"], ctx["peaks"]
     inst = make_instance(cfg)
     N = n_of(inst)
     P, R, S = cfg["P"], cfg["R"], cfg["S"]
     beta, alpha = schedule_params(cfg)
     upd_per_solve = N * P * R * S
+    variant = cfg.get("variant", "threshold")
 
     def create(src):
         if src[0] == "csr":
@@ -632,9 +700,7 @@ def main():
             return sb.create_problem_csr(n, rp, col, val, h)
         return sb.create_problem_dense(src[2], src[3])
 
-    stream = torch.cuda.Stream(device=dev)
     prob = create(inst)
-    variant = cfg.get("variant", "threshold")
     sb.set_schedule(prob, beta, alpha, precision=cfg["prec"], variant=variant, kernel_select=args.kernel_select)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     seed0 = multi.rank_seed(0, rank)
@@ -652,7 +718,6 @@ def main():
         # zero-step solves time init + readout alone (for the step kernel's share)
         sb.run(prob, 0, P, R, seed=seed0, stream=stream)
         torch.cuda.synchronize()
-
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         ev0 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         barrier()
@@ -670,54 +735,15 @@ def main():
             sb.run(prob, 0, P, R, seed=seed0 + k, stream=stream)
             ev0[k][1].record(stream)
         torch.cuda.synchronize()
+    prob.destroy()
+    del flush
     ms = [a.elapsed_time(b) for a, b in ev]
     ms0 = [a.elapsed_time(b) for a, b in ev0]
-    ms_solve = statistics.mean(ms)
+    ms_solve = multi.max_over_ranks(statistics.mean(ms))
     ms_zero = statistics.mean(ms0)
-    ms_solve = multi.max_over_ranks(ms_solve)
     value = world * upd_per_solve / (ms_solve * 1e-3)
     step_ms = max(ms_solve - ms_zero, 1e-9) / S
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    kernel_names = {0: "k_step_csr", 1: "k_step_dense", 2: "k_step_dense_tc", 3: "k_solve_small",
-                    4: "k_solve_csr_persistent", 5: "k_solve_dense_tc_persistent", 6: "k_step_csr_bsb",
-                    7: "k_step_dense_bsb", 8: "k_solve_dense_tc_split", 9: "k_solve_dense_tc_pair"}
-    if info.step_kernel == 2 and (-(-P * R // 128) * 128) % 256 == 0:
-        kernel_names[2] = "k_step_dense_tc_wide"  # 128 x 256 tiles when the padded columns allow
-    tr = TRAFFIC_PER_STEP.get(args.config + ("/ballistic" if cfg.get("variant") == "ballistic" else ""))
-    traffic = tr["bytes_per_step"] if tr and tr["kernel"] == kernel_names[info.step_kernel] else None
-    if info.step_kernel in (2, 5, 8, 9):  # dense tcgen05 FP8: a contraction, 2 N^2 R P flops per step
-        flops = 2.0 * N * N * P * R
-        achieved = flops / (step_ms * 1e-3) / 1e12
-        peak = 2.0 * peaks.get("bf16_tflops", 1900.0)  # FP8 = 2 x the measured BF16 dense peak
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": kernel_names[info.step_kernel],
-                "step_ms": step_ms, "peak_source": peak_src,
-                "note": "2 N^2 R P flops per step / event-timed step time; FP8 peak = 2 x measured BF16"}
-    elif info.step_kernel == 3:
-        # the one-launch small dense solver computes from shared memory and registers: FP32 ALU work,
-        # 2 N flops of the product + 12 of the update per replica-spin update, against the FP32 FMA
-        # rate of the SMs (152 SMs x 128 lanes x 2 flops x the maximum SM clock)
-        flops = (2.0 * N + 12.0) * N * P * R
-        achieved = flops / (step_ms * 1e-3) / 1e12
-        peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": kernel_names[3], "step_ms": step_ms, "peak_source": "derived",
-                "note": "(2N + 12) FP32 flops per update / event-timed step time; peak = 152 SMs x 128 FP32 lanes "
-                        "x 2 x max SM clock; one CTA per run (%d of 152 SMs busy): latency-bound" % R}
-    else:
-        bpu = BYTES_PER_UPDATE_BSB if info.step_kernel in (6, 7) else BYTES_PER_UPDATE
-        achieved_gbs = bpu * N * P * R / (step_ms * 1e-3) / 1e9
-        hbm_peak = peaks.get("hbm_gbs", 6800.0)
-        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved_gbs / hbm_peak, "traffic": traffic, "kernel": kernel_names[info.step_kernel],
-                "step_ms": step_ms,
-                "peak_source": peak_src,
-                "note": "algorithmic %d B/update x N*P*R per launch / event-timed step time" % bpu}
+    roof = roofline_of(cfg, name, info, N, P, R, step_ms, peaks)
 
     # e2e: host buffers through the C ABI, every step
     src = inst
@@ -728,7 +754,7 @@ def main():
         h2d = (n + 1) * 4 + len(col) * 4 + len(col) * (1 if cfg["prec"] == "auto" else (2 if cfg["prec"] == "bf16" else 4))
         h2d += len(col) * (4 if h is None else 8) + n * (4 + 8)
     else:
-        h2d = N * N * (4 + 4) + N * (4 + 8)
+        h2d = N * N * (1 if cfg["prec"] == "exact" else 4) + N * (4 + 8)
     h2d += 4 * (2 * S + 1) + 4 * S * R
     d2h = R * N + R * (8 + 8 + 4 + 4)
     e2e_ms = []
@@ -745,33 +771,26 @@ def main():
     e2e_med_ms = multi.max_over_ranks(statistics.median(e2e_ms))  # the slowest rank
     e2e_val = world * upd_per_solve / (e2e_med_ms * 1e-3)
     assert np.all(np.isfinite(best["energy"]))
-
-    if rank != 0:
-        if dist is not None:
-            dist.destroy_process_group()
-        return 0
     cpu = None
-    if not args.no_cpu_baseline and world == 1:
-        cpu = oracle_sample(cfg, target_s=args.ref_seconds)
+    if rank == 0 and not args.no_cpu_baseline and world == 1 and cpu_seconds > 0:
+        cpu = oracle_sample(cfg, target_s=cpu_seconds)
     # init + reset_best (+ the f -> e4m3 conversion on the tensor-core path) + steps + 4 readout kernels
-    tc_conv = 1 if info.step_kernel in (2, 5, 8, 9) else 0  # f codes -> FP8 operand; the readout's sign codes
-    launches_per_solve = (1 if info.step_kernel == 3 else
-                          2 + tc_conv + (1 if info.step_kernel in (4, 5, 8, 9) else S) + 4 + tc_conv)
-    line = {
+    tc_conv = 1 if info.step_kernel in TC_FP8 + TC_BF16 else 0
+    persistent = info.step_kernel in (4, 5, 8, 9, 11)
+    launches_per_solve = 1 if info.step_kernel == 3 else 2 + tc_conv + (1 if persistent else S) + 4 + tc_conv
+    state_b = N * P * R * (18 if variant == "ballistic" else 10)
+    return {
         "metric": "replica-spin updates/s", "value": value, "unit": "replica-spin updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_solve,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": cfg["workload"], "N": N, "P": P, "R": R, "steps_per_solve": S,
-                   "precision": cfg["prec"], "l2": "flushed (512 MB write) before every timed solve; "
-                                                   "state (%.0f MB) stays L2-resident within a solve"
-                                                   % (N * P * R * 10 / 1e6),
-                   "state_bytes": N * P * R * (18 if variant == "ballistic" else 10),
+        "config": {"workload": cfg["workload"], "name": name, "N": N, "P": P, "R": R, "steps_per_solve": S,
+                   "precision": cfg["prec"],
+                   "l2": "flushed (512 MB write) before every timed solve; state %.0f MB %s L2 (126 MB) within "
+                         "a solve" % (state_b / 1e6, "fits in" if state_b < 100e6 else "exceeds"),
+                   "state_bytes": state_b,
                    "parallelism": "independent runs per GPU (weak scaling)",
-                   "step_kernel": ["csr", "dense_cuda_core", "dense_tcgen05_fp8", "dense_small_one_launch",
-                                   "csr_persistent", "dense_tcgen05_persistent", "csr_ballistic",
-                                   "dense_ballistic", "dense_tcgen05_persistent_split_k",
-                                   "dense_tcgen05_persistent_cta_pairs"][info.step_kernel],
+                   "step_kernel": KERNEL_LABELS.get(info.step_kernel, str(info.step_kernel)),
                    "csr_variant": info.step_variant,
                    "autotune_ms_per_step": [round(v, 5) for v in info.variant_ms],
                    "autotune_persistent_ms_per_step": round(info.persistent_ms, 5)},
@@ -782,9 +801,120 @@ def main():
         "gpu_launches": launches_per_solve * args.steps,
         "clocks": clk.summary(),
     }
-    print(json.dumps(line))
-    if dist is not None:
-        dist.destroy_process_group()
+
+
+def run_fp8_peak(args):
+    """Dense FP8 e4m3 GEMM throughput on this GPU (torch._scaled_mm, unit
+    scales, BF16 output, 8192^3): best of 10 single launches (burst) and
+    launches back to back for about 4 s (sustained), with the SM clocks
+    sampled; a BF16 matmul of the same shape is timed beside it."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n = 8192
+    g = torch.Generator(device=dev).manual_seed(0)
+    a = torch.randn(n, n, device=dev, generator=g).to(torch.float8_e4m3fn)
+    b = torch.randn(n, n, device=dev, generator=g).to(torch.float8_e4m3fn).t()  # column-major operand
+    one = torch.tensor(1.0, device=dev)
+    ab = torch.randn(n, n, device=dev, generator=g, dtype=torch.bfloat16)
+    bb = torch.randn(n, n, device=dev, generator=g, dtype=torch.bfloat16)
+    fp8 = lambda: torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)  # noqa: E731
+    bf16 = lambda: ab @ bb  # noqa: E731
+    flops = 2.0 * n ** 3
+    out = {}
+    for name, fn in (("fp8", fp8), ("bf16", bf16)):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        best = float("inf")
+        for _ in range(10):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        with ClockSampler(0) as clk:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = max(1, int(4000.0 / best))
+            e0.record()
+            for _ in range(reps):
+                fn()
+            e1.record()
+            torch.cuda.synchronize()
+        out[name] = {"tflops_burst": flops / (best * 1e-3) / 1e12,
+                     "tflops_sustained": flops * reps / (e0.elapsed_time(e1) * 1e-3) / 1e12,
+                     "sustained_launches": reps, "clocks": clk.summary()}
+    print(json.dumps({"metric": "dense GEMM TFLOP/s", "mode": "fp8peak", "shape": [n, n, n],
+                      "fp8_e4m3": out["fp8"], "bf16": out["bf16"],
+                      "fp8_over_bf16_burst": out["fp8"]["tflops_burst"] / out["bf16"]["tflops_burst"],
+                      "how": "torch._scaled_mm e4m3 x e4m3 (unit scales, BF16 out) and torch.matmul BF16; "
+                             "best of 10 (burst), back to back for ~4 s (sustained)"}))
+    return 0
+
+
+HEADLINE = "regular1e5"  # the largest single-GPU configuration (state above L2)
+SUBRECORDS = ["lattice16", "sk2000"]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--config", default="default",
+                    choices=["default"] + sorted(CONFIGS) + ["serving", "tte", "scaling", "sweep", "fp8peak"],
+                    help="default: the random 6-regular N=1e5 headline with per-config records of the lattice "
+                         "L=16, dense SK N=2000 and the serving stream; a config name measures that config alone")
+    ap.add_argument("--kernel-select", type=int, default=0,
+                    help="sbqa_params.kernel_select (0: the autotuner's choice; e.g. 12 pins the 128 x 128 "
+                         "persistent dense solver, for profiles)")
+    ap.add_argument("--variant", default="threshold", choices=["threshold", "ballistic"],
+                    help="f of Eq. 8 (SBQA) or f(x) = x (the bSB form)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="default config: leave out the serving record")
+    ap.add_argument("--ref-seconds", type=float, default=15.0)
+    ap.add_argument("--requests", type=int, default=48, help="serving: requests in the stream")
+    ap.add_argument("--arena-gb", type=float, default=40.0, help="serving: device arena of the engine (GB)")
+    ap.add_argument("--eps", type=float, default=0.08, help="tte: target optimality gap of the headline")
+    ap.add_argument("--gamma0", type=float, default=16.0, help="tte: Gamma_x(0)")
+    ap.add_argument("--tte-L", type=int, default=10)
+    ap.add_argument("--tte-kind", default="lattice", choices=["lattice", "sk"], help="tte: instance family")
+    ap.add_argument("--tte-n", type=int, default=1024, help="tte: N of the dense SK instance")
+    ap.add_argument("--tte-steps", type=int, default=2000)
+    args = ap.parse_args()
+    if args.config == "serving":
+        print(json.dumps(run_serving(args)))
+        return 0
+    if args.config == "tte":
+        return run_tte(args)
+    if args.config == "scaling":
+        return run_scaling(args)
+    if args.config == "sweep":
+        return run_sweep(args)
+    if args.config == "fp8peak":
+        return run_fp8_peak(args)
+    name = HEADLINE if args.config == "default" else args.config
+    cfg = dict(CONFIGS[name])
+    if args.variant == "ballistic":
+        cfg["variant"] = "ballistic"
+        cfg["workload"] += "; ballistic form f(x) = x"
+    if args.impl == "reference":
+        return run_reference(args, cfg)
+    ctx = gpu_context()
+    line = measure_config(name, cfg, args, ctx, args.ref_seconds)
+    if args.config == "default":
+        per = {}
+        for sub in SUBRECORDS:
+            per[sub] = measure_config(sub, dict(CONFIGS[sub]), args, ctx, min(args.ref_seconds, 10.0))
+        if not args.no_serving and ctx["world"] == 1:
+            per["serving"] = run_serving(args, stream=ctx["stream"])
+        line["per_config"] = per
+    if ctx["rank"] == 0:
+        print(json.dumps(line))
+    if ctx["dist"] is not None:
+        ctx["dist"].destroy_process_group()
     return 0
 
 

@@ -183,7 +183,8 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info);
  *                cache); 12 = as 2, but the dense tensor-core solver keeps
  *                its 128 x 128 tiles instead of splitting the K loop across
  *                2-CTA clusters (taken by default when padded N and padded
- *                R*P are multiples of 256); 13 = the dense tensor-core
+ *                R*P are multiples of 256); with 1 or 12 no cluster kernel
+ *                is launched at all; 13 = the dense tensor-core
  *                solver on CTA pairs that share M=256 MMAs (padded N a
  *                multiple of 256; with kernel_select 0 the autotuner times
  *                it beside the others).  Results are identical whichever

@@ -858,9 +858,15 @@ int autotune_tc(sbqa_problem *p) {
       *use = false;
       return SBQA_OK;
     };
+    // a kernel_select that names a solver without clusters (1, 12) launches
+    // no cluster solver at all, not even the probe
     int prc = SBQA_OK;
-    if (p->tc_split_possible() && (prc = probe(&p->use_tc_split, &p->tc_split_failed)) != SBQA_OK) return prc;
-    if (p->tc_pair_possible() && (prc = probe(&p->use_tc_pair, &p->tc_pair_failed)) != SBQA_OK) return prc;
+    if ((sel == 0 || sel == 2) && p->tc_split_possible() &&
+        (prc = probe(&p->use_tc_split, &p->tc_split_failed)) != SBQA_OK)
+      return prc;
+    if ((sel == 0 || sel == 13) && p->tc_pair_possible() &&
+        (prc = probe(&p->use_tc_pair, &p->tc_pair_failed)) != SBQA_OK)
+      return prc;
     TuneResult known;
     if (sel == 2 || sel == 12 || sel == 13) {
       p->use_tc_persistent = true;

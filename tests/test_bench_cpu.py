@@ -37,6 +37,10 @@ def test_reference_arm_prints_one_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     assert "workload" in d["config"]
+    # a step is one bounded sample: its measured wall time, not a whole solve extrapolated from it
+    assert d["ms_per_step"] < 60e3
+    assert d["extrapolated_ms_per_solve"]["extrapolated"] is True
+    assert d["extrapolated_ms_per_solve"]["value"] > d["ms_per_step"]
 
 
 def test_tte_seconds_eq10():

@@ -840,18 +840,22 @@ def test_repeat_runs_deterministic(sb):
 
 
 # ---------------------------------------------------------------- full-size configurations, sampled
-def _sampled_runs(sb, pb, spec, P, R, S, steps, runs, prec="auto", pb_oracle=None):
+def _sampled_runs(sb, pb, spec, P, R, S, steps, runs, prec="auto", pb_oracle=None, kernels=None, gamma0=1.0):
+    """Free-running parity of the listed runs against the oracle after `steps` steps, at the full size;
+    `kernels` lists the step_kernel codes the autotuner must have picked (the kernel bench.py times)."""
     prob = create(sb, spec)
     beta, alpha = workloads.autotune_params(R, 1)
-    p = _params(precision=prec)
+    p = _params(precision=prec, gamma0=gamma0)
     sb.set_schedule(prob, beta, alpha, **p)
     sb.run_begin(prob, S, P, R, seed=0)
     sb.run_advance(prob, steps)
+    if kernels is not None:
+        assert prob.info().step_kernel in kernels, prob.info().step_kernel
     xg, yg, _ = sb.get_state(prob)
     xi, yi = oracle.init_state(0, pb.n, P, max(runs) + 1, 0.1)
     worst = 0.0
     for r in runs:
-        ref = oracle.run(pb_oracle or pb, S, P, 1, 0, beta[r:r + 1], alpha[r:r + 1], n_end=steps,
+        ref = oracle.run(pb_oracle or pb, S, P, 1, 0, beta[r:r + 1], alpha[r:r + 1], gamma0=gamma0, n_end=steps,
                          x0=xi[r:r + 1], y0=yi[r:r + 1], **_oracle_kwargs(p, pb))
         worst = max(worst, rel_err(xg[r:r + 1], ref["x"]), rel_err(yg[r:r + 1], ref["y"]))
     return worst
@@ -863,6 +867,13 @@ def test_full_size_lattice_L16_P32_R64(sb):
     assert _sampled_runs(sb, pb, spec, 32, 64, 10000, 10, [0, 37, 63]) <= TOL_TRAJ
 
 
+def test_full_size_lattice_L16_persistent_solver_against_oracle(sb):
+    """The kernel the benchmark times at this shape -- the persistent CSR solver (step_kernel 4) -- against
+    the oracle directly: runs 0, 21 and 63 free-running for 24 steps (Gamma_x(0) = 4P, the stable schedule)."""
+    pb, spec = lattice(16, 0)
+    assert _sampled_runs(sb, pb, spec, 32, 64, 10000, 24, [0, 21, 63], kernels=(4,), gamma0=128.0) <= TOL_TRAJ
+
+
 def test_full_size_lattice_energies(sb):
     pb, spec = lattice(16, 0)
     prob = create(sb, spec)
@@ -872,9 +883,12 @@ def test_full_size_lattice_energies(sb):
 
 
 def test_full_size_dense_sk2000_exact(sb):
-    """SK N=2000 +-1, P=32, R=32 (J.X = 2000x2000 @ 2000x1024), exact product: runs 0 and 31 after 5 steps."""
+    """SK N=2000 +-1, P=32, R=32 (J.X = 2000x2000 @ 2000x1024), exact product on a persistent tcgen05
+    solver (step_kernel 5, 8 or 9, the kernels the benchmark times): runs 0 and 31 free-running for
+    20 steps (Gamma_x(0) = 4P)."""
     pb, spec = sk(2000, 0)
-    assert _sampled_runs(sb, pb, spec, 32, 32, 1000, 5, [0, 31], prec="exact") <= TOL_TRAJ
+    assert _sampled_runs(sb, pb, spec, 32, 32, 1000, 20, [0, 31], prec="exact", kernels=(5, 8, 9),
+                         gamma0=128.0) <= TOL_TRAJ
 
 
 def test_full_size_dense_sk2000_energies(sb):
@@ -898,9 +912,12 @@ def test_full_size_dense_sk2000_energies(sb):
 
 
 def test_full_size_regular_1e5_bf16(sb):
-    """Random 6-regular N=1e5, J~N(0,1), h~N(0,0.1^2), BF16 product, P=16, R=8: runs 0 and 7 after 5 steps."""
+    """Random 6-regular N=1e5, J~N(0,1), h~N(0,0.1^2), BF16 product, P=16, R=8, on the persistent CSR
+    solver (step_kernel 4, the kernel the benchmark times): runs 0 and 7 free-running for 20 steps
+    against the oracle on the BF16-rounded J (Gamma_x(0) = 4P)."""
     pb, spec = regular(100000, 6, 0)
-    assert _sampled_runs(sb, pb, spec, 16, 8, 5000, 5, [0, 7], prec="bf16", pb_oracle=pb.bf16()) <= TOL_TRAJ
+    assert _sampled_runs(sb, pb, spec, 16, 8, 5000, 20, [0, 7], prec="bf16", pb_oracle=pb.bf16(), kernels=(4,),
+                         gamma0=64.0) <= TOL_BF16_TRAJ
 
 
 # ---------------------------------------------------------------- errors that need a handle
