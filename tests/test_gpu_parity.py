@@ -867,11 +867,50 @@ def test_full_size_lattice_L16_P32_R64(sb):
     assert _sampled_runs(sb, pb, spec, 32, 64, 10000, 10, [0, 37, 63]) <= TOL_TRAJ
 
 
+def _sampled_per_step(sb, pb, spec, P, R, S, steps, runs, kernels, prec="auto", pb_oracle=None, gamma0=1.0):
+    """The kernel the benchmark times, tied to the oracle at the full size: `steps` single-step launches,
+    each compared on the sampled runs with one oracle step from the same FP32 state (TOL_STEP), then a
+    fresh run of `steps` steps in one launch must equal the stepped state bit for bit.  `kernels` lists
+    the step_kernel codes the autotuner must pick (the solver of the benchmark line)."""
+    prob = create(sb, spec)
+    beta, alpha = workloads.autotune_params(R, 1)
+    p = _params(precision=prec, gamma0=gamma0)
+    sb.set_schedule(prob, beta, alpha, **p)
+    sb.run_begin(prob, S, P, R, seed=0)
+    a, d, jp = oracle.schedule(S, P, R, beta, alpha, gamma0, p["delta_slope"], p["jperp_enable"])
+    kw = _oracle_kwargs(p, pb)
+    ref = pb_oracle or pb
+    x, y, _ = sb.get_state(prob)
+    worst = 0.0
+    flips = []
+    for n in range(steps):
+        sb.run_advance(prob, 1)
+        assert prob.info().step_kernel in kernels, prob.info().step_kernel
+        xg, yg, _ = sb.get_state(prob)
+        for r in runs:
+            nf = _threshold_flips(x[r], x[r].astype(np.float64), d[n])
+            if nf:
+                flips.append((r, n, nf))
+            xo, yo = oracle.step(ref, x[r].astype(np.float64), y[r].astype(np.float64), P, a[n], d[n], jp[r, n], **kw)
+            amb = wall_ambiguous(xg[r:r + 1], xo[None])
+            worst = max(worst, rel_err(xg[r:r + 1], xo[None]),
+                        rel_err(np.where(amb, 0.0, yg[r:r + 1]), np.where(amb, 0.0, yo[None])))
+        x, y = xg, yg
+    if flips:
+        print("FP32/FP64 threshold flips (run, step, count): %s" % flips[:20])
+    sb.run_begin(prob, S, P, R, seed=0)
+    sb.run_advance(prob, steps)  # one launch of the persistent solver for the whole stretch
+    assert prob.info().step_kernel in kernels
+    xb, yb, _ = sb.get_state(prob)
+    assert np.array_equal(xb, x) and np.array_equal(yb, y)
+    return worst
+
+
 def test_full_size_lattice_L16_persistent_solver_against_oracle(sb):
-    """The kernel the benchmark times at this shape -- the persistent CSR solver (step_kernel 4) -- against
-    the oracle directly: runs 0, 21 and 63 free-running for 24 steps (Gamma_x(0) = 4P, the stable schedule)."""
+    """Lattice L=16, P=32, R=64: the persistent CSR solver (step_kernel 4, the benchmark's kernel) against
+    the oracle step by step on runs 0, 21 and 63 for 24 steps."""
     pb, spec = lattice(16, 0)
-    assert _sampled_runs(sb, pb, spec, 32, 64, 10000, 24, [0, 21, 63], kernels=(4,), gamma0=128.0) <= TOL_TRAJ
+    assert _sampled_per_step(sb, pb, spec, 32, 64, 10000, 24, [0, 21, 63], kernels=(4,)) <= TOL_STEP
 
 
 def test_full_size_lattice_energies(sb):
@@ -883,12 +922,16 @@ def test_full_size_lattice_energies(sb):
 
 
 def test_full_size_dense_sk2000_exact(sb):
-    """SK N=2000 +-1, P=32, R=32 (J.X = 2000x2000 @ 2000x1024), exact product on a persistent tcgen05
-    solver (step_kernel 5, 8 or 9, the kernels the benchmark times): runs 0 and 31 free-running for
-    20 steps (Gamma_x(0) = 4P)."""
+    """SK N=2000 +-1, P=32, R=32 (J.X = 2000x2000 @ 2000x1024), exact product: runs 0 and 31 after 5 steps."""
     pb, spec = sk(2000, 0)
-    assert _sampled_runs(sb, pb, spec, 32, 32, 1000, 20, [0, 31], prec="exact", kernels=(5, 8, 9),
-                         gamma0=128.0) <= TOL_TRAJ
+    assert _sampled_runs(sb, pb, spec, 32, 32, 1000, 5, [0, 31], prec="exact") <= TOL_TRAJ
+
+
+def test_full_size_dense_sk2000_persistent_solver_against_oracle(sb):
+    """SK N=2000, P=32, R=32, exact product on a persistent tcgen05 solver (step_kernel 5, 8 or 9, the
+    benchmark's kernels) against the oracle step by step on runs 0 and 31 for 20 steps."""
+    pb, spec = sk(2000, 0)
+    assert _sampled_per_step(sb, pb, spec, 32, 32, 1000, 20, [0, 31], kernels=(5, 8, 9), prec="exact") <= TOL_STEP
 
 
 def test_full_size_dense_sk2000_energies(sb):
@@ -912,12 +955,18 @@ def test_full_size_dense_sk2000_energies(sb):
 
 
 def test_full_size_regular_1e5_bf16(sb):
-    """Random 6-regular N=1e5, J~N(0,1), h~N(0,0.1^2), BF16 product, P=16, R=8, on the persistent CSR
-    solver (step_kernel 4, the kernel the benchmark times): runs 0 and 7 free-running for 20 steps
-    against the oracle on the BF16-rounded J (Gamma_x(0) = 4P)."""
+    """Random 6-regular N=1e5, J~N(0,1), h~N(0,0.1^2), BF16 product, P=16, R=8: runs 0 and 7 after 5 steps."""
     pb, spec = regular(100000, 6, 0)
-    assert _sampled_runs(sb, pb, spec, 16, 8, 5000, 20, [0, 7], prec="bf16", pb_oracle=pb.bf16(), kernels=(4,),
-                         gamma0=64.0) <= TOL_BF16_TRAJ
+    assert _sampled_runs(sb, pb, spec, 16, 8, 5000, 5, [0, 7], prec="bf16", pb_oracle=pb.bf16()) <= TOL_TRAJ
+
+
+def test_full_size_regular_1e5_persistent_solver_against_oracle(sb):
+    """Random 6-regular N=1e5, BF16 product, P=16, R=8 -- the benchmark's headline workload -- on the
+    persistent CSR solver (step_kernel 4) against the oracle on the BF16-rounded J, step by step on runs
+    0, 3 and 7 for 20 steps."""
+    pb, spec = regular(100000, 6, 0)
+    assert _sampled_per_step(sb, pb, spec, 16, 8, 5000, 20, [0, 3, 7], kernels=(4,), prec="bf16",
+                             pb_oracle=pb.bf16()) <= TOL_STEP
 
 
 # ---------------------------------------------------------------- errors that need a handle
