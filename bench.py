@@ -9,7 +9,8 @@ replicas, best per run).  Its state (128 MB) exceeds the L2 cache, so every
 step streams it through HBM.  The same line carries ``per_config`` records,
 measured the same way, of the 3D cubic lattice L=16 (N=4096, P=32, R=64,
 10^4 steps), the dense SK N=2000 instance on the tensor cores (P=32, R=32,
-1000 steps) and the Poisson serving stream (p50/p99 latency).
+1000 steps), the same shape with real Gaussian couplings on the BF16 tensor
+cores, and the Poisson serving stream (p50/p99 latency).
 
   value   updates/s = N * P * R * steps / solve time, with J resident on the
           device (CUDA events on the library's stream; L2 flushed before every
@@ -53,6 +54,10 @@ CONFIGS = {
                  workload="dense SK N=64, J=+-1, h=0; P=8, R=16, 1000 steps, linear schedule"),
     "sk2000": dict(kind="sk", n=2000, P=32, R=32, S=1000, prec="exact",
                    workload="dense SK N=2000, J=+-1; P=32, R=32 (J.X = 2000x2000 @ 2000x1024), 1000 steps"),
+    # real-valued dense couplings (Gaussian SK): the BF16 tensor-core product
+    "skreal2000": dict(kind="skreal", n=2000, P=32, R=32, S=1000, prec="bf16",
+                       workload="dense SK N=2000, J~N(0,1), h~N(0,0.1^2), BF16 J on the tensor cores; P=32, R=32 "
+                                "(J.X = 2000x2000 @ 2000x1024), 1000 steps"),
     "regular1e5": dict(kind="regular", n=100000, d=6, P=16, R=8, S=5000, prec="bf16",
                        workload="random 6-regular N=1e5, J~N(0,1), h~N(0,0.1^2), CSR, BF16 J, P=16, R=8, 5000 steps"),
     # large-N sparse family: the lattice16 shape (P=32, R=64) as the state outgrows L2
@@ -72,7 +77,7 @@ for _n, _S in ((4096, 500), (8192, 200)):
 CONFIGS["sk8192t"] = dict(kind="sk", n=8192, P=8, R=32, S=200, prec="exact",
                           workload="dense SK N=8192, J=+-1; P=8, R=32 (J.X = 8192x8192 @ 8192x256), 200 steps")
 SCALING = ["lattice16", "lattice24", "lattice32", "lattice48", "lattice64", "lattice88", "regular1e5", "regular7e5",
-           "sk2000", "sk4096", "sk8192", "sk8192t"]
+           "sk2000", "sk4096", "sk8192", "sk8192t", "skreal2000"]
 BYTES_PER_UPDATE = 16  # x, y FP32 read + write per replica-spin update
 BYTES_PER_UPDATE_BSB = 20  # ballistic form: + the FP32 f (= x) write
 # DRAM traffic per step (dram__bytes_read.sum + dram__bytes_write.sum of one
@@ -95,6 +100,9 @@ def make_instance(cfg, seed=0):
     if cfg["kind"] == "regular":
         n, rp, col, val, h = workloads.random_regular(cfg["n"], cfg["d"], seed, 0.1)
         return ("csr", n, rp, col, val, h)
+    if cfg["kind"] == "skreal":
+        J, h = workloads.random_dense_real(cfg["n"], seed, 0.1)
+        return ("dense", cfg["n"], J, h)
     J, h = workloads.sk_pm1(cfg["n"], seed)
     return ("dense", cfg["n"], J, h)
 
@@ -629,13 +637,15 @@ def gpu_context():
 KERNEL_NAMES = {0: "k_step_csr", 1: "k_step_dense", 2: "k_step_dense_tc", 3: "k_solve_small",
                 4: "k_solve_csr_persistent", 5: "k_solve_dense_tc_persistent", 6: "k_step_csr_bsb",
                 7: "k_step_dense_bsb", 8: "k_solve_dense_tc_split", 9: "k_solve_dense_tc_pair",
-                10: "k_step_dense_tc_bf16", 11: "k_solve_dense_tc_persistent_bf16"}
+                10: "k_step_dense_tc<bf16>", 11: "k_solve_dense_tc_persistent<bf16>",
+                12: "k_step_dense_tc<bsb>", 13: "k_solve_dense_tc_persistent<bsb>"}
 KERNEL_LABELS = {0: "csr", 1: "dense_cuda_core", 2: "dense_tcgen05_fp8", 3: "dense_small_one_launch",
                  4: "csr_persistent", 5: "dense_tcgen05_persistent", 6: "csr_ballistic", 7: "dense_ballistic",
                  8: "dense_tcgen05_persistent_split_k", 9: "dense_tcgen05_persistent_cta_pairs",
-                 10: "dense_tcgen05_bf16", 11: "dense_tcgen05_persistent_bf16"}
+                 10: "dense_tcgen05_bf16", 11: "dense_tcgen05_persistent_bf16",
+                 12: "dense_tcgen05_ballistic_bf16x2", 13: "dense_tcgen05_persistent_ballistic_bf16x2"}
 TC_FP8 = (2, 5, 8, 9)
-TC_BF16 = (10, 11)
+TC_BF16 = (10, 11, 12, 13)
 
 
 def roofline_of(cfg, name, info, N, P, R, step_ms, peaks):
@@ -754,7 +764,8 @@ def measure_config(name, cfg, args, ctx, cpu_seconds):
         h2d = (n + 1) * 4 + len(col) * 4 + len(col) * (1 if cfg["prec"] == "auto" else (2 if cfg["prec"] == "bf16" else 4))
         h2d += len(col) * (4 if h is None else 8) + n * (4 + 8)
     else:
-        h2d = N * N * (1 if cfg["prec"] == "exact" else 4) + N * (4 + 8)
+        # J as the library uploads it: e4m3 (exact), bfloat16 + the FP64 readout copy (bf16), FP32 + readout copy
+        h2d = N * N * {"exact": 1, "bf16": 10}.get(cfg["prec"], 12) + N * (4 + 8)
     h2d += 4 * (2 * S + 1) + 4 * S * R
     d2h = R * N + R * (8 + 8 + 4 + 4)
     e2e_ms = []
@@ -776,7 +787,7 @@ def measure_config(name, cfg, args, ctx, cpu_seconds):
         cpu = oracle_sample(cfg, target_s=cpu_seconds)
     # init + reset_best (+ the f -> e4m3 conversion on the tensor-core path) + steps + 4 readout kernels
     tc_conv = 1 if info.step_kernel in TC_FP8 + TC_BF16 else 0
-    persistent = info.step_kernel in (4, 5, 8, 9, 11)
+    persistent = info.step_kernel in (4, 5, 8, 9, 11, 13)
     launches_per_solve = 1 if info.step_kernel == 3 else 2 + tc_conv + (1 if persistent else S) + 4 + tc_conv
     state_b = N * P * R * (18 if variant == "ballistic" else 10)
     return {
@@ -854,7 +865,7 @@ def run_fp8_peak(args):
 
 
 HEADLINE = "regular1e5"  # the largest single-GPU configuration (state above L2)
-SUBRECORDS = ["lattice16", "sk2000"]
+SUBRECORDS = ["lattice16", "sk2000", "skreal2000"]
 
 
 def main():

@@ -52,13 +52,21 @@ extern "C" {
 /* ---- enums ------------------------------------------------------------ */
 /* Precision of the coupling product G = J . f(X) (Sec. II A, Eq. 7).  The
  * positions and momenta are FP32 in every mode; f(X) is in {-1, 0, +1}. */
-#define SBQA_PREC_AUTO 0  /* EXACT if J, h are small integers, else FP32      */
-#define SBQA_PREC_FP32 1  /* J in FP32, FP32 accumulation                       */
-#define SBQA_PREC_EXACT 2 /* integer J (|J_ij| <= 16): J.f(X) computed exactly
-                             (int8 adds on CUDA cores, FP8 e4m3 tensor cores
-                             with FP32 accumulation for dense J)               */
+#define SBQA_PREC_AUTO 0  /* EXACT if J is integer with |J_ij| <= 256, else
+                             FP32                                             */
+#define SBQA_PREC_FP32 1  /* J in FP32, FP32 accumulation (CUDA cores)         */
+#define SBQA_PREC_EXACT 2 /* integer J (|J_ij| <= 256): J.f(X) computed exactly
+                             (int8 adds or exact FP32 sums on CUDA cores; for
+                             dense J with N >= 256 tcgen05 tensor cores, e4m3
+                             operands for |J_ij| <= 16 and bfloat16 above,
+                             FP32 accumulation of integers below 2^24)       */
 #define SBQA_PREC_BF16 3  /* J rounded to bfloat16 (round to nearest even),
-                             FP32 accumulation                                  */
+                             FP32 accumulation; dense J with N >= 256 runs on
+                             tcgen05 tensor cores (kind::f16).  With the
+                             ballistic form f(x) = x, dense J on the tensor
+                             cores takes x as two bfloat16 terms, hi =
+                             bf16(x) and lo = bf16(x - hi), so each x_j
+                             enters the product to 2^-16 relative           */
 
 /* Form of f in Eq. 7. */
 #define SBQA_VARIANT_THRESHOLD 0 /* f(x) = 0 if |x| <= Delta(t), else sign(x) (Eq. 8) */
@@ -132,7 +140,11 @@ typedef struct {
                              CTAs of a cluster (128 x 256 tiles), 9 the
                              persistent dense tcgen05 solver on CTA pairs
                              sharing M=256 MMAs (2-CTA clusters, tcgen05
-                             cta_group::2); -1 none                          */
+                             cta_group::2); 10 dense tcgen05 with bfloat16
+                             operands per step (128 x 128 tiles), 11 its
+                             persistent solver; 12 and 13 the same for the
+                             ballistic form (x as bfloat16 hi + lo); -1
+                             none                                            */
     int32_t step_variant; /* CSR kernel variant picked by the autotuner:
                              0-5: 4 << (v % 3) consecutive replica columns
                              per lane, v >= 3 with one wave of blocks
@@ -165,7 +177,9 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info);
  *   variant      SBQA_VARIANT_THRESHOLD (SBQA, Eq. 8) or
  *                SBQA_VARIANT_BALLISTIC (f(x) = x; the product runs on FP32
  *                positions: CSR kernels for sparse J, the CUDA-core kernel
- *                for dense J; not served by the batching engine)
+ *                for dense J, or, with SBQA_PREC_BF16 and dense N >= 256,
+ *                the tensor cores with x as bfloat16 hi + lo; not served by
+ *                the batching engine)
  *   precision    SBQA_PREC_*
  *   eval_every   0: read out only after the last step; K > 0: also after
  *                every step n with (n+1) % K == 0, keeping the best so far

@@ -237,6 +237,10 @@ sbqa_problem::~sbqa_problem() {
 namespace {
 
 constexpr int kTcMinN = 256;  // smaller dense instances stay on the CUDA-core kernel
+// EXACT precision takes integer J up to this magnitude: the products are exact
+// in bfloat16 (and e4m3 up to 16) and every partial sum, an integer below
+// 256 N < 2^24 for N < 65536, is exact in FP32
+constexpr int kExactMaxAbsJ = 256;
 
 bool finite_all(const double *v, size_t n) {
   for (size_t i = 0; i < n; ++i)
@@ -373,8 +377,8 @@ int prepare_sparse_values(sbqa_problem *p, int precision) {
   else if (precision == SBQA_PREC_FP32) kind = VAL_F32;
   else if (p->is_pm1 && p->max_degree <= 127) kind = VAL_PM1;
   else kind = VAL_F32;
-  if (precision == SBQA_PREC_EXACT && (!p->j_integer || p->max_abs_j > 16))
-    return fail(SBQA_ERR_UNSUPPORTED, "EXACT precision needs integer J with |J_ij| <= 16");
+  if (precision == SBQA_PREC_EXACT && (!p->j_integer || p->max_abs_j > kExactMaxAbsJ))
+    return fail(SBQA_ERR_UNSUPPORTED, "EXACT precision needs integer J with |J_ij| <= 256");
   p->kind = kind;
   if (kind == VAL_PM1 && !p->d_npos.p) {
     // each row: columns of the +1 entries, then of the -1 entries
@@ -472,8 +476,35 @@ uint8_t e4m3_of_int(int v) {
   return uint8_t(sign | ((e + 7) << 3) | mant);
 }
 
+// bfloat16 copy of J for the tensor cores (operand forms kTcOpBf16 and
+// kTcOpBsb): round to nearest even from the FP64 values (exact for integers
+// |J_ij| <= 256), zero padding to Kp.
+int prepare_tc_values_bf16(sbqa_problem *p) {
+  const int N = p->n, Kp = (N + 127) / 128 * 128;
+  HostVec<uint16_t> jb(size_t(Kp) * Kp);
+  parallel_tasks(Kp, [&](int64_t i, int64_t) {
+    uint16_t *out = jb.data() + size_t(i) * Kp;
+    if (i >= N) {
+      std::memset(out, 0, size_t(Kp) * 2);
+      return;
+    }
+    for (int j = 0; j < N; ++j) out[j] = bf16_bits_rne(p->jv(size_t(i) * N + j));
+    std::memset(out + N, 0, size_t(Kp - N) * 2);
+  });
+  SBQA_CUDA(p->d_J8.alloc(jb.size() * 2));
+  SBQA_CUDA(cudaMemcpy(p->d_J8.p, jb.data(), jb.size() * 2, cudaMemcpyHostToDevice));
+  p->Kp = Kp;
+  p->j_tc_op = p->tc_op;
+  return SBQA_OK;
+}
+
 int prepare_tc_values(sbqa_problem *p) {
-  if (p->d_J8.p) return SBQA_OK;
+  const bool bf = p->tc_op != kTcOpF8;
+  if (p->d_J8.p && (p->j_tc_op == p->tc_op || (bf && p->j_tc_op != kTcOpF8))) {
+    p->j_tc_op = p->tc_op;
+    return SBQA_OK;
+  }
+  if (bf) return prepare_tc_values_bf16(p);
   const int N = p->n, Kp = (N + 127) / 128 * 128;
   HostVec<uint8_t> j8(size_t(Kp) * Kp);  // every byte is written below (zeros in the padding)
   uint8_t lut[33];  // e4m3 of -16 .. 16 (the tensor-core path takes |J_ij| <= 16)
@@ -496,20 +527,41 @@ int prepare_tc_values(sbqa_problem *p) {
   SBQA_CUDA(p->d_J8.alloc(j8.size()));
   SBQA_CUDA(cudaMemcpy(p->d_J8.p, j8.data(), j8.size(), cudaMemcpyHostToDevice));
   p->Kp = Kp;
+  p->j_tc_op = kTcOpF8;
   return SBQA_OK;
 }
 
 int prepare_dense_values(sbqa_problem *p, int precision) {
-  if (precision == SBQA_PREC_EXACT && (!p->j_integer || p->max_abs_j > 16))
-    return fail(SBQA_ERR_UNSUPPORTED, "EXACT precision needs integer J with |J_ij| <= 16");
-  // the FP8 tensor-core product is exact only for f in {-1, 0, 1}: thresholded form only
-  p->use_tc = (precision == SBQA_PREC_AUTO || precision == SBQA_PREC_EXACT) && p->j_integer &&
-              p->max_abs_j <= 16 && p->n >= kTcMinN && !p->ballistic();
+  if (precision == SBQA_PREC_EXACT && (!p->j_integer || p->max_abs_j > kExactMaxAbsJ))
+    return fail(SBQA_ERR_UNSUPPORTED, "EXACT precision needs integer J with |J_ij| <= 256");
+  // Tensor-core forms (N >= kTcMinN):
+  //  e4m3   exact: integer |J| <= 16 with the thresholded f in {-1, 0, 1}
+  //  bf16   exact for integer |J| <= 256 (AUTO, EXACT), or J rounded to
+  //         bfloat16 (BF16), with the thresholded f
+  //  bsb    the ballistic form f(x) = x with BF16: J rounded to bfloat16, x as
+  //         bfloat16 hi + lo
+  const bool exactish = precision == SBQA_PREC_AUTO || precision == SBQA_PREC_EXACT;
+  int op = -1;
+  if (p->n >= kTcMinN) {
+    if (p->ballistic()) {
+      if (precision == SBQA_PREC_BF16) op = kTcOpBsb;
+    } else if (exactish && p->j_integer && p->max_abs_j <= 16) {
+      op = kTcOpF8;
+    } else if ((exactish && p->j_integer && p->max_abs_j <= kExactMaxAbsJ) || precision == SBQA_PREC_BF16) {
+      op = kTcOpBf16;
+    }
+  }
+  p->use_tc = op >= 0;
   if (p->use_tc) {
-    // the readout runs on the tensor cores too when its energies are integers;
-    // with a non-integer h it runs on the CUDA cores in FP64
+    if (p->tc_op != op && p->tc_plan) {  // the plan's maps are of the other operand type
+      tc_plan_free(p->tc_plan);
+      p->tc_plan = nullptr;
+    }
+    p->tc_op = op;
+    // the readout runs on the tensor cores too when its energies are integers
+    // and the product is e4m3; otherwise on the CUDA cores (exact int64 or FP64)
     const int rc = prepare_tc_values(p);
-    if (rc != SBQA_OK || p->is_integer || p->d_e_f64.p) return rc;
+    if (rc != SBQA_OK || (p->is_integer && op == kTcOpF8) || p->d_e_f64.p || p->d_e_i32.p) return rc;
     return upload_readout_values(p);
   }
   if (!p->d_e_i32.p && !p->d_e_f64.p) {
@@ -546,7 +598,7 @@ int alloc_run(sbqa_problem *p, int S, int P, int R) {
   SBQA_CUDA(p->d_y.alloc(NC));
   SBQA_CUDA(p->d_F0.alloc(NC));
   SBQA_CUDA(p->d_F1.alloc(NC));
-  if (p->ballistic()) {
+  if (p->ballistic() && !p->use_tc) {  // the tensor-core form keeps f(x) = x in its FT buffers
     SBQA_CUDA(p->d_Fx0.alloc(NC));
     SBQA_CUDA(p->d_Fx1.alloc(NC));
     SBQA_CUDA(cudaMemsetAsync(p->d_Fx1.p, 0, NC * sizeof(float), p->stream));
@@ -570,11 +622,12 @@ int alloc_run(sbqa_problem *p, int S, int P, int R) {
   SBQA_CUDA(cudaMemsetAsync(p->d_err.p, 0, sizeof(int), p->stream));  // no trial launch reads a stale code
   p->S = S; p->P = P; p->R = R; p->C = C; p->Cp = Cp;
   if (p->use_tc) {
-    SBQA_CUDA(p->d_FT.alloc(size_t(2) * Cp * p->Kp));
-    if (!p->tc_plan || p->tc_plan_ft != p->d_FT.p || p->tc_plan_cp != Cp || p->tc_plan_x != p->d_x.p) {
+    SBQA_CUDA(p->d_FT.alloc(tc_ft_bytes(p->Kp, Cp, p->tc_op)));
+    if (!p->tc_plan || p->tc_plan_ft != p->d_FT.p || p->tc_plan_cp != Cp || p->tc_plan_x != p->d_x.p ||
+        tc_op_of(p->tc_plan) != p->tc_op) {
       if (p->tc_plan) tc_plan_free(p->tc_plan);
       p->tc_plan = nullptr;
-      if (!tc_plan_make(&p->tc_plan, p->d_J8.p, p->d_FT.p, p->Kp, Cp, p->d_x.p, p->d_y.p, p->n))
+      if (!tc_plan_make(&p->tc_plan, p->d_J8.p, p->d_FT.p, p->Kp, Cp, p->d_x.p, p->d_y.p, p->n, p->tc_op))
         return fail(SBQA_ERR_CUDA, "cuTensorMapEncodeTiled failed");
       SBQA_CUDA(tc_set_attributes());
       p->tc_plan_ft = p->d_FT.p;
@@ -600,6 +653,7 @@ int build_tables(sbqa_problem *p) {
 
 cudaError_t issue_step(sbqa_problem *p, int n, cudaStream_t st) {
   const StateView s = p->state();
+  if (p->use_tc) return launch_step_dense_tc(p->tc_plan, s, p->Kp, p->d_FT.p, p->d_err.p, p->d_h.p, p->tables, n, st);
   if (p->ballistic()) {
     if (p->dense) {
       DenseView d;
@@ -609,7 +663,6 @@ cudaError_t issue_step(sbqa_problem *p, int n, cudaStream_t st) {
     }
     return launch_step_csr_bsb(s, p->csr(), p->tables, n, st);
   }
-  if (p->use_tc) return launch_step_dense_tc(p->tc_plan, s, p->Kp, p->d_FT.p, p->d_err.p, p->d_h.p, p->tables, n, st);
   if (p->dense) {
     DenseView d;
     d.J = p->d_dense_f32.p;
@@ -683,7 +736,7 @@ std::map<TuneKey, TuneResult> g_tune;
 
 TuneKey tune_key(const sbqa_problem *p) {
   TuneKey k;
-  k.dev = p->device; k.dense = p->dense ? 1 : 0; k.n = p->n; k.kind = p->dense ? -1 : p->kind; k.Cp = p->Cp;
+  k.dev = p->device; k.dense = p->dense ? 1 : 0; k.n = p->n; k.kind = p->dense ? -1 - (p->use_tc ? p->tc_op : 8) : p->kind; k.Cp = p->Cp;
   k.P = p->P; k.select = p->prm.kernel_select; k.max_degree = p->max_degree; k.Kp = p->Kp; k.nnz = p->nnz;
   return k;
 }
@@ -942,7 +995,7 @@ cudaError_t issue_readout(sbqa_problem *p, int step, cudaStream_t st) {
   const StateView s = p->state();
   // integer dense instances (J and h) on the tensor cores: the sign codes take
   // the FT buffer of step `step`, which the next step does not read
-  cudaError_t e = p->dense ? (p->use_tc && p->tc_plan && p->is_integer ? launch_energy_dense_tc(p->tc_plan, s, p->Kp, p->d_FT.p,
+  cudaError_t e = p->dense ? (p->use_tc && p->tc_plan && p->is_integer && p->tc_op == kTcOpF8 ? launch_energy_dense_tc(p->tc_plan, s, p->Kp, p->d_FT.p,
                                                                                step & 1, p->d_err.p, p->energy(),
                                                                                p->best(), st)
                                                       : launch_energy_dense(s, p->energy(), p->best(), st))
@@ -1296,11 +1349,15 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info) {
   info->is_integer = p->is_integer ? 1 : 0;
   info->max_abs_j = p->max_abs_j;
   info->c0_auto = p->c0_auto;
+  const bool tc_pers = p->use_tc && p->use_tc_persistent && p->tc_persistent_ok();
+  int tc_kernel = tc_pers ? (p->tc_pair_ok() ? 9 : p->tc_split_ok() ? 8 : 5) : 2;
+  if (p->tc_op == kTcOpBf16) tc_kernel = tc_pers ? 11 : 10;
+  if (p->tc_op == kTcOpBsb) tc_kernel = tc_pers ? 13 : 12;
   info->step_kernel = !p->begun ? -1
+                     : p->use_tc ? tc_kernel
                      : p->ballistic() ? (p->dense ? 7 : 6)
-                                 : (p->small_path ? 3
-                                                  : (p->use_tc ? (p->use_tc_persistent && p->tc_persistent_ok() ? (p->tc_pair_ok() ? 9 : p->tc_split_ok() ? 8 : 5) : 2)
-                                                               : (p->dense ? 1 : (p->use_persistent ? 4 : 0))));
+                     : p->small_path ? 3
+                     : (p->dense ? 1 : (p->use_persistent ? 4 : 0));
   info->persistent_ms = p->use_tc ? p->tc_persistent_ms : p->persistent_ms;
   info->step_variant = p->dense ? -1 : p->csr_variant;
   for (int v = 0; v < 8; ++v) info->variant_ms[v] = p->use_tc ? (v == 0 ? p->tc_step_ms : 0.f) : p->variant_ms[v];
@@ -1316,8 +1373,8 @@ int sbqa_set_schedule(sbqa_problem *p, const sbqa_params *q) {
   if (q->variant != SBQA_VARIANT_THRESHOLD && q->variant != SBQA_VARIANT_BALLISTIC)
     return fail(SBQA_ERR_INVALID_ARG, "variant must be SBQA_VARIANT_THRESHOLD or SBQA_VARIANT_BALLISTIC");
   if (q->precision < SBQA_PREC_AUTO || q->precision > SBQA_PREC_BF16) return fail(SBQA_ERR_INVALID_ARG, "bad precision");
-  if (q->precision == SBQA_PREC_EXACT && (!p->j_integer || p->max_abs_j > 16))
-    return fail(SBQA_ERR_UNSUPPORTED, "EXACT precision needs integer J with |J_ij| <= 16");
+  if (q->precision == SBQA_PREC_EXACT && (!p->j_integer || p->max_abs_j > kExactMaxAbsJ))
+    return fail(SBQA_ERR_UNSUPPORTED, "EXACT precision needs integer J with |J_ij| <= 256");
   if (q->eval_every < 0 || q->n_runs < 0) return fail(SBQA_ERR_INVALID_ARG, "negative eval_every or n_runs");
   if (q->kernel_select < 0 || q->kernel_select > 13) return fail(SBQA_ERR_INVALID_ARG, "kernel_select must be 0..13");
   if (q->n_runs > 0 && (!q->beta || !q->alpha)) return fail(SBQA_ERR_INVALID_ARG, "beta/alpha missing");
@@ -1355,8 +1412,8 @@ int sbqa_run_begin(sbqa_problem *p, int32_t steps, int32_t P, int32_t R, uint64_
   const StateView s = p->state();
   SBQA_CUDA(cudaMemsetAsync(p->d_err.p, 0, sizeof(int), p->stream));
   SBQA_CUDA(launch_init(s, seed, float(p->prm.init_amp), 0.0f, p->stream));
-  if (p->use_tc) SBQA_CUDA(launch_f_to_ft8(s, 0, p->d_FT.p, p->Kp, 0, p->stream));
-  if (p->ballistic()) SBQA_CUDA(launch_copy_fx(s, 0, p->stream));
+  if (p->use_tc) SBQA_CUDA(launch_f_to_ft(s, 0, p->d_FT.p, p->Kp, 0, p->tc_op, p->stream));
+  if (p->ballistic() && !p->use_tc) SBQA_CUDA(launch_copy_fx(s, 0, p->stream));
   SBQA_CUDA(launch_reset_best(s, p->best(), p->stream));
   p->step_done = 0;
   p->begun = true;
@@ -1426,7 +1483,7 @@ int sbqa_run(sbqa_problem *p, int32_t steps, int32_t P, int32_t R, uint64_t seed
   sbqa_problem::Key key;
   key.S = steps; key.P = P; key.R = R; key.eval = p->prm.eval_every; key.kind = p->kind;
   key.dense = p->dense ? 1 : 0; key.x = p->d_x.p; key.kj = p->d_kj.p;
-  key.kc = p->tables.kc; key.kx = p->tables.kx; key.tc = p->use_tc ? 1 : 0; key.variant = p->csr_variant;
+  key.kc = p->tables.kc; key.kx = p->tables.kx; key.tc = p->use_tc ? 1 + p->tc_op : 0; key.variant = p->csr_variant;
   key.fvar = p->prm.variant;
   if (!(p->graph && p->graph_key == key)) {
     if (p->graph) {
@@ -1538,8 +1595,8 @@ int sbqa_set_state(sbqa_problem *p, const float *x, const float *y, int32_t step
   const double tau = p->S > 0 ? double(step_done) / double(p->S) : 0.0;
   SBQA_CUDA(launch_refresh_f(p->state(), step_done & 1, float(p->prm.delta_slope * tau), p->stream));
   if (p->use_tc)
-    SBQA_CUDA(launch_f_to_ft8(p->state(), step_done & 1, p->d_FT.p, p->Kp, step_done & 1, p->stream));
-  if (p->ballistic()) SBQA_CUDA(launch_copy_fx(p->state(), step_done & 1, p->stream));
+    SBQA_CUDA(launch_f_to_ft(p->state(), step_done & 1, p->d_FT.p, p->Kp, step_done & 1, p->tc_op, p->stream));
+  if (p->ballistic() && !p->use_tc) SBQA_CUDA(launch_copy_fx(p->state(), step_done & 1, p->stream));
   p->step_done = step_done;
   p->finished = false;
   return SBQA_OK;

@@ -180,7 +180,7 @@ size_t request_bytes(const sbqa_problem *p, int S, int P, int R, bool tc, int Kp
   b += align_up(nblk * Cp * 8);            // partial sums
   b += align_up(size_t(R) * 8) * 2 + align_up(size_t(R) * 4) * 3 + align_up(size_t(R) * N);
   b += align_up(4);                        // error flag
-  if (tc) b += align_up(size_t(2) * Cp * Kp);
+  if (tc) b += align_up(tc_ft_bytes(Kp, Cp, p->tc_op));
   return b;
 }
 
@@ -212,7 +212,7 @@ void carve(Request &r, uint8_t *base, bool tc, int Kp) {
   r.have = reinterpret_cast<int32_t *>(take(size_t(r.R) * 4));
   r.best_spins = reinterpret_cast<int8_t *>(take(size_t(r.R) * N));
   r.err = reinterpret_cast<int *>(take(4));
-  r.FT = tc ? take(size_t(2) * r.Cp * Kp) : nullptr;
+  r.FT = tc ? take(tc_ft_bytes(Kp, r.Cp, r.prob->tc_op)) : nullptr;
 }
 
 int admit(sbqa_engine *e, Request &r, int slot, cudaStream_t st) {
@@ -225,14 +225,14 @@ int admit(sbqa_engine *e, Request &r, int slot, cudaStream_t st) {
   int rc = problem_build_tables(p, r.S, r.P, r.R, r.ka, r.dl, r.kj, &r.tables, st);
   if (rc != SBQA_OK) return rc;
   if (tc) {
-    if (!tc_plan_make(&r.tc_plan, p->d_J8.p, r.FT, p->Kp, r.Cp, r.x, r.y, p->n))
+    if (!tc_plan_make(&r.tc_plan, p->d_J8.p, r.FT, p->Kp, r.Cp, r.x, r.y, p->n, p->tc_op))
       return set_error(SBQA_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     ENG_CUDA(tc_set_attributes());
   }
   const StateView s = r.state_view();
   ENG_CUDA(cudaMemsetAsync(r.err, 0, sizeof(int), st));
   ENG_CUDA(launch_init(s, r.seed, float(p->prm.init_amp), 0.0f, st));
-  if (tc) ENG_CUDA(launch_f_to_ft8(s, 0, r.FT, p->Kp, 0, st));
+  if (tc) ENG_CUDA(launch_f_to_ft(s, 0, r.FT, p->Kp, 0, p->tc_op, st));
   ENG_CUDA(launch_reset_best(s, r.best_view(), st));
   e->kernels_launched += tc ? 3 : 2;
   r.slot = slot;
@@ -263,7 +263,7 @@ int readout(sbqa_engine *e, Request &r, cudaStream_t st) {
   const EnergyView ev = problem_energy_view(p);
   // the tensor-core readout needs integer energies (J and h); a non-integer h
   // takes the FP64 CUDA-core readout (the product still runs on the tensor cores)
-  const bool tc = p->dense && r.tc_plan && p->is_integer;
+  const bool tc = p->dense && r.tc_plan && p->is_integer && p->tc_op == kTcOpF8;
   cudaError_t err = tc ? launch_energy_dense_tc(r.tc_plan, s, p->Kp, r.FT, (r.S - 1) & 1, r.err, ev, r.best_view(), st)
                        : p->dense ? launch_energy_dense(s, ev, r.best_view(), st)
                                   : launch_energy_csr(s, problem_csr_readout_view(p), ev, r.best_view(), st);

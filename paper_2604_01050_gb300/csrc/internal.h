@@ -195,15 +195,23 @@ cudaError_t launch_step_csr(const StateView &s, const CsrView &J, const StepTabl
                             int n, int variant, cudaStream_t st);
 cudaError_t launch_step_dense(const StateView &s, const DenseView &J, const StepTables &t,
                               int n, cudaStream_t st);
-// Dense integer couplings on tcgen05 (step_dense_tc.cu).  The plan holds the
-// TMA descriptors of J8 [Kp][Kp] and FT [2][Cp][Kp] (e4m3) and of the state
+// Dense couplings on tcgen05 (step_dense_tc.cu).  Operand forms (op):
+// 0 = integer J and f codes in e4m3, 1 = J rounded to bfloat16 and f codes in
+// bfloat16, 2 = the ballistic form, J in bfloat16 and x as bfloat16 hi + lo.
+// The plan holds the TMA descriptors of J [Kp][Kp] and FT [2][Cp][Kp] (of the
+// operand type; for op 2 the lo terms follow the hi terms) and of the state
 // x, y [N][Cp] (FP32) of one run batch.
-bool tc_plan_make(void **plan, const uint8_t *J8, uint8_t *FT, int Kp, int Cp, float *x, float *y, int N);
+constexpr int kTcOpF8 = 0, kTcOpBf16 = 1, kTcOpBsb = 2;
+size_t tc_ft_bytes(int Kp, int Cp, int op);  // bytes of FT
+size_t tc_j_bytes(int Kp, int op);           // bytes of J
+bool tc_plan_make(void **plan, const void *J, void *FT, int Kp, int Cp, float *x, float *y, int N, int op);
 void tc_plan_free(void *plan);
+int tc_op_of(const void *plan);
 cudaError_t tc_set_attributes();  // dynamic shared memory limit of the tcgen05 kernels
 cudaError_t launch_step_dense_tc(const void *plan, const StateView &s, int Kp, uint8_t *FT, int *err,
                                  const float *h, const StepTables &t, int n, cudaStream_t st);
-cudaError_t launch_f_to_ft8(const StateView &s, int which, uint8_t *FT, int Kp, int buffer, cudaStream_t st);
+// FT buffer `buffer` from the f codes of F buffer `which` (op 0, 1) or from x (op 2)
+cudaError_t launch_f_to_ft(const StateView &s, int which, uint8_t *FT, int Kp, int buffer, int op, cudaStream_t st);
 
 // Batched CSR step over the work items of all active slots (step_batched.cu);
 // j = step index inside the current chunk, n_items in device memory.

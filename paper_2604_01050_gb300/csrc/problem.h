@@ -139,8 +139,11 @@ struct sbqa_problem {
   sbqa::DevBuf<__nv_bfloat16> d_val_bf16;
   sbqa::DevBuf<float> d_dense_f32;  // dense J for the CUDA-core path
   int dense_prec = -1;        // precision the dense FP32 copy was built for
-  // dense integer J on the tensor cores: e4m3 copies padded to Kp
+  // dense J on the tensor cores, padded to Kp: e4m3 (integer |J| <= 16) or
+  // bfloat16 copies (operand form tc_op: sbqa::kTcOp*)
   bool use_tc = false;
+  int tc_op = 0;
+  int j_tc_op = -1;  // operand form the device copy d_J8 holds (-1: none)
   int Kp = 0;
   sbqa::DevBuf<uint8_t> d_J8, d_FT;
   void *tc_plan = nullptr;
@@ -235,14 +238,16 @@ struct sbqa_problem {
 
   // the instance qualifies for the split-K persistent solver on 2-CTA clusters
   bool tc_split_possible() const {
-    return tc_persistent_ok() && prm.kernel_select != 12 && prm.kernel_select != 13 && !tc_split_failed &&
+    return tc_persistent_ok() && tc_op == sbqa::kTcOpF8 && prm.kernel_select != 12 && prm.kernel_select != 13 &&
+           !tc_split_failed &&
            sbqa::tc_split_eligible(Kp, Cp, tc_split_blocks);
   }
   bool tc_split_ok() const { return use_tc_split && tc_split_possible(); }
 
   // the instance qualifies for the paired persistent solver (autotuned, or kernel_select 13)
   bool tc_pair_possible() const {
-    return tc_persistent_ok() && (prm.kernel_select == 0 || prm.kernel_select == 13) && !tc_pair_failed &&
+    return tc_persistent_ok() && tc_op == sbqa::kTcOpF8 && (prm.kernel_select == 0 || prm.kernel_select == 13) &&
+           !tc_pair_failed &&
            sbqa::tc_pair_eligible(Kp, Cp, tc_pair_blocks);
   }
   bool tc_pair_ok() const { return use_tc_pair && tc_pair_possible(); }

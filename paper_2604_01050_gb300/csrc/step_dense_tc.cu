@@ -21,7 +21,13 @@
 // reads its 32 TMEM lanes (= spin rows) for 64 columns, updates whole runs of
 // 32 columns in place in the swizzled state boxes and stages f(x_next) as
 // e4m3; finally one thread stores x, y and the transposed f tile with TMA.
+//
+// Real-valued J (and integers up to |J| = 256) take the same kernels with
+// BF16 operands (tcgen05.mma kind::f16, K = 64 elements per 128-byte operand
+// row); the ballistic form f(x) = x carries x as two BF16 terms (hi + lo) in
+// two B operands that share each A tile.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include "step_common.cuh"
@@ -37,6 +43,31 @@ constexpr int kTcStateTile = 4 * kTcBox; // x or y tile, 128 rows x 128 columns 
 constexpr int kTcSmem = 2 * kTcStages * kTcTile + 2 * kTcStateTile + 1024 + 128;
 constexpr uint8_t kE4M3One = 0x38, kE4M3MinusOne = 0xB8;
 
+// Operand forms of the product G = J . F on the tensor cores (TcMaps::op).
+//   kOpF8    integer J (|J_ij| <= 16) and the f codes of Eq. 8 in e4m3: exact
+//   kOpBf16  J rounded to bfloat16 (exact for integers |J_ij| <= 256) and the
+//            f codes of Eq. 8 in bfloat16: exact products, FP32 sums
+//   kOpBsb   the ballistic form f(x) = x: J in bfloat16, and x as the two
+//            bfloat16 terms hi = bf16(x), lo = bf16(x - hi) (x to 2^-16
+//            relative), two B operands sharing each A tile
+constexpr int kOpF8 = kTcOpF8, kOpBf16 = kTcOpBf16, kOpBsb = kTcOpBsb;
+
+template <int OP>
+struct TcOp {
+  static constexpr bool kBf = OP != kOpF8;
+  static constexpr int kKE = kBf ? 64 : 128;       // K elements per 128-byte operand row (one k-block)
+  static constexpr int kEB = kBf ? 2 : 1;          // bytes per operand element
+  static constexpr int kNB = OP == kOpBsb ? 2 : 1;  // B operands per k-block
+  static constexpr int kFTile = kTcBM * kTcBN * kEB;  // one 128 x 128 f tile (bytes)
+  __host__ __device__ static constexpr uint32_t idesc(int M, int N) {
+    return kBf ? tc::idesc_bf16(M, N) : tc::idesc_f8_e4m3(M, N);
+  }
+  __device__ __forceinline__ static void mma(uint32_t d, uint64_t ad, uint64_t bd, uint32_t id, uint32_t acc) {
+    if constexpr (kBf) tc::mma_bf16(d, ad, bd, id, acc);
+    else tc::mma_f8(d, ad, bd, id, acc);
+  }
+};
+
 struct TcArgs {
   int Kp;
   uint8_t *FT;  // [2][Cp][Kp]
@@ -49,7 +80,9 @@ struct TcMaps {
   CUtensorMap B2;    // FT operand tiles of 256 columns (256 x 128 bytes, 128B swizzle)
   CUtensorMap B64;   // FT operand half tiles of a CTA pair (64 x 128 bytes, 128B swizzle)
   CUtensorMap X, Y;  // x, y state boxes (128 rows x 32 floats, 128B swizzle)
-  CUtensorMap Fst;   // FT tile store (128 columns x 128 spins bytes, no swizzle)
+  CUtensorMap Fst;   // FT tile store (128 columns x 128 spins, no swizzle)
+  CUtensorMap Bl, Fstl;  // kOpBsb: the lo terms of x (load and store), as B and Fst
+  int op;                // operand form (kOpF8, kOpBf16, kOpBsb)
 };
 
 __device__ __forceinline__ uint8_t f_to_e4m3(int8_t f) {
@@ -59,6 +92,42 @@ __device__ __forceinline__ uint8_t f_to_e4m3(int8_t f) {
 // e4m3 code of f(x) for the threshold delta >= 0 (Eq. 8: 0 when |x| <= delta).
 __device__ __forceinline__ uint8_t thresh_e4m3(float x, float delta) {
   return x > delta ? kE4M3One : (x < -delta ? kE4M3MinusOne : uint8_t(0));
+}
+
+// Writer of f(x_next) into the transposed f tile of one spin row: base points
+// at column 0 of the thread's 32-column chunk; column j is base[j * 128]
+// elements on.  kOpF8 / kOpBf16: the code of Eq. 8 (0 when |x| <= Delta);
+// kOpBsb: f(x) = x as hi = bf16(x) and lo = bf16(x - hi) (exact in FP32),
+// the lo tile following the hi tile.
+template <int OP>
+struct FOut {
+  uint8_t *base;
+  __device__ __forceinline__ void put(int j, float x, float delta) const {
+    if constexpr (OP == kOpF8) {
+      base[j * kTcBM] = thresh_e4m3(x, delta);
+    } else if constexpr (OP == kOpBf16) {
+      reinterpret_cast<uint16_t *>(base)[j * kTcBM] =
+          x > delta ? uint16_t(0x3F80) : (x < -delta ? uint16_t(0xBF80) : uint16_t(0));
+    } else {
+      const __nv_bfloat16 h = __float2bfloat16_rn(x);
+      const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+      reinterpret_cast<uint16_t *>(base)[j * kTcBM] = __bfloat16_as_ushort(h);
+      reinterpret_cast<uint16_t *>(base + TcOp<OP>::kFTile)[j * kTcBM] = __bfloat16_as_ushort(l);
+    }
+  }
+  __device__ __forceinline__ void zero(int j) const {
+    if constexpr (OP == kOpF8) {
+      base[j * kTcBM] = 0;
+    } else {
+      reinterpret_cast<uint16_t *>(base)[j * kTcBM] = 0;
+      if constexpr (OP == kOpBsb) reinterpret_cast<uint16_t *>(base + TcOp<OP>::kFTile)[j * kTcBM] = 0;
+    }
+  }
+};
+
+template <int OP>
+__device__ __forceinline__ FOut<OP> f_out(uint8_t *sF, int cl, int rl) {
+  return FOut<OP>{sF + (cl * kTcBM + rl) * TcOp<OP>::kEB};
 }
 
 // Address of the float4 (16-byte chunk u, 0..7) of row r inside a 128B-swizzled
@@ -96,10 +165,10 @@ struct KjChunk {
 // column j goes to sFcol[j * 128] of the transposed f tile.  Same arithmetic,
 // in the same order, as sb_update4.  FULL: all 32 columns are below C (no
 // per-column test).
-template <int P, bool FULL>
+template <int P, bool FULL, int OP>
 __device__ __forceinline__ void sb_update_row32(const StateView &s, const StepTables &t, float ka, float dnext,
                                                 const KjChunk<P> &kj, int c0, const uint32_t (&g)[32], float hi,
-                                                uint8_t *xbox, uint8_t *ybox, int r, uint8_t *sFcol) {
+                                                uint8_t *xbox, uint8_t *ybox, int r, const FOut<OP> &fo) {
   constexpr int PR = P < 32 ? P : 32;
   float xs[32], ys[32];
 #pragma unroll
@@ -116,7 +185,7 @@ __device__ __forceinline__ void sb_update_row32(const StateView &s, const StepTa
     xo[j] = xs[j];
     yo[j] = ys[j];
     if (!FULL && c0 + j >= s.C) {
-      sFcol[j * kTcBM] = 0;
+      fo.zero(j);
       continue;
     }
     float yn = fmaf(t.kc, __uint_as_float(g[j]) + hi, ys[j]);
@@ -129,7 +198,7 @@ __device__ __forceinline__ void sb_update_row32(const StateView &s, const StepTa
     }
     xo[j] = xn;
     yo[j] = yn;
-    sFcol[j * kTcBM] = thresh_e4m3(xn, dnext);
+    fo.put(j, xn, dnext);
   }
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
@@ -138,13 +207,19 @@ __device__ __forceinline__ void sb_update_row32(const StateView &s, const StepTa
   }
 }
 
-template <int P>
+template <int P, int OP>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_step_dense_tc(const __grid_constant__ TcMaps m, StateView s, TcArgs a, StepTables t, int n) {
+  using O = TcOp<OP>;
+  // operand stages: 3 of A + B (32 KB), or 2 of A + B hi + B lo (48 KB) for kOpBsb: 96 KB either way
+  constexpr int kStages = O::kNB == 2 ? 2 : kTcStages;
+  constexpr int kStageB = O::kNB * kTcTile;
+  static_assert(kStages * (kTcTile + kStageB) == 2 * kTcStages * kTcTile, "operand stages of the 128 x 128 kernel");
+  static_assert(O::kNB * O::kFTile <= 2 * kTcStages * kTcTile, "f tile must fit the consumed operand stages");
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t *sA = smem;
-  uint8_t *sB = smem + kTcStages * kTcTile;
+  uint8_t *sB = smem + kStages * kTcTile;
   uint8_t *sX = smem + 2 * kTcStages * kTcTile;
   uint8_t *sY = sX + kTcStateTile;
   uint64_t *full = reinterpret_cast<uint64_t *>(sY + kTcStateTile);
@@ -155,11 +230,11 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * kTcBM, n0 = blockIdx.x * kTcBN;
-  const int KB = a.Kp / kTcBK;
+  const int KB = a.Kp / O::kKE;
   const int brow = (n & 1) * s.Cp + n0;  // row of F_n in the [2 Cp][Kp] map
 
   if (threadIdx.x == 0) {
-    for (int q = 0; q < kTcStages; ++q) {
+    for (int q = 0; q < kStages; ++q) {
       tc::mbar_init(&full[q], 1);
       tc::mbar_init(&empty[q], 1);
     }
@@ -168,6 +243,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc::fence_mbar_init();
     tc::prefetch_tmap(&m.A);
     tc::prefetch_tmap(&m.B);
+    if constexpr (O::kNB == 2) tc::prefetch_tmap(&m.Bl);
     tc::prefetch_tmap(&m.X);
     tc::prefetch_tmap(&m.Y);
   }
@@ -180,12 +256,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (warp == 0 && lane == 0) {
     bool xy_issued = false;
     for (int kb = 0; kb < KB; ++kb) {
-      const int st = kb % kTcStages, q = kb / kTcStages;
+      const int st = kb % kStages, q = kb / kStages;
       if (q > 0 && !tc::mbar_wait(&empty[st], (q - 1) & 1, a.err, tc::ERR_WAIT_EMPTY)) break;
-      tc::mbar_arrive_expect_tx(&full[st], 2 * kTcTile);
-      tc::tma_load_2d(sA + st * kTcTile, &m.A, &full[st], kb * kTcBK, m0);
-      tc::tma_load_2d(sB + st * kTcTile, &m.B, &full[st], kb * kTcBK, brow);
-      if (!xy_issued && (kb == kTcStages - 1 || kb == KB - 1)) {
+      tc::mbar_arrive_expect_tx(&full[st], kTcTile + kStageB);
+      tc::tma_load_2d(sA + st * kTcTile, &m.A, &full[st], kb * O::kKE, m0);
+      tc::tma_load_2d(sB + st * kStageB, &m.B, &full[st], kb * O::kKE, brow);
+      if constexpr (O::kNB == 2) tc::tma_load_2d(sB + st * kStageB + kTcTile, &m.Bl, &full[st], kb * O::kKE, brow);
+      if (!xy_issued && (kb == kStages - 1 || kb == KB - 1)) {
         // the state tile, needed only by the epilogue, loads behind the first stages
         tc::mbar_arrive_expect_tx(xy_full, 2 * kTcStateTile);
         for (int b = 0; b < 4; ++b) {
@@ -196,16 +273,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
     }
   } else if (warp == 1 && lane == 0) {
-    constexpr uint32_t idesc = tc::idesc_f8_e4m3(kTcBM, kTcBN);
+    constexpr uint32_t idesc = O::idesc(kTcBM, kTcBN);
     for (int kb = 0; kb < KB; ++kb) {
-      const int st = kb % kTcStages, q = kb / kTcStages;
+      const int st = kb % kStages, q = kb / kStages;
       if (!tc::mbar_wait(&full[st], q & 1, a.err, tc::ERR_WAIT_FULL)) break;
       tc::tc_fence_after();
-      const uint32_t a0 = tc::smem_u32(sA + st * kTcTile), b0 = tc::smem_u32(sB + st * kTcTile);
+      const uint32_t a0 = tc::smem_u32(sA + st * kTcTile), b0 = tc::smem_u32(sB + st * kStageB);
 #pragma unroll
-      for (int kk = 0; kk < kTcBK / 32; ++kk)
-        tc::mma_f8(tmem, tc::smem_desc_sw128(a0 + kk * 32), tc::smem_desc_sw128(b0 + kk * 32), idesc,
-                   (kb | kk) != 0 ? 1u : 0u);
+      for (int kk = 0; kk < 4; ++kk) {
+        O::mma(tmem, tc::smem_desc_sw128(a0 + kk * 32), tc::smem_desc_sw128(b0 + kk * 32), idesc,
+               (kb | kk) != 0 ? 1u : 0u);
+        if constexpr (O::kNB == 2)
+          O::mma(tmem, tc::smem_desc_sw128(a0 + kk * 32), tc::smem_desc_sw128(b0 + kTcTile + kk * 32), idesc, 1u);
+      }
       tc::mma_commit(&empty[st]);
     }
     tc::mma_commit(done);
@@ -224,20 +304,20 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
   // Epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (= spin rows) and
   // columns 32 (w / 4) .. + 31 (one state box).
-  uint8_t *sF = sA;  // [128 columns][128 spins] e4m3 f(x_next); the operand stages are consumed
+  uint8_t *sF = sA;  // [128 columns][128 spins] f(x_next) (kOpBsb: hi, then lo); the operand stages are consumed
   {
     const int cl = 32 * b;  // first column of the chunk inside the tile
     const int c0 = n0 + cl;
     uint32_t g[32];
     tc::tmem_ld_32x32b_x32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(cl), g);
-    uint8_t *sFcol = sF + cl * kTcBM + rl;
+    const FOut<OP> fo = f_out<OP>(sF, cl, rl);
     if (i < s.N && c0 + 32 <= s.C) {
-      sb_update_row32<P, true>(s, t, ka, dnext, kj, c0, g, hi, sX + b * kTcBox, sY + b * kTcBox, rl, sFcol);
+      sb_update_row32<P, true, OP>(s, t, ka, dnext, kj, c0, g, hi, sX + b * kTcBox, sY + b * kTcBox, rl, fo);
     } else if (i < s.N && c0 < s.C) {
-      sb_update_row32<P, false>(s, t, ka, dnext, kj, c0, g, hi, sX + b * kTcBox, sY + b * kTcBox, rl, sFcol);
+      sb_update_row32<P, false, OP>(s, t, ka, dnext, kj, c0, g, hi, sX + b * kTcBox, sY + b * kTcBox, rl, fo);
     } else {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) sFcol[j * kTcBM] = 0;
+      for (int j = 0; j < 32; ++j) fo.zero(j);
     }
   }
   tc::fence_proxy_async_smem();
@@ -251,6 +331,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       tc::tma_store_2d(&m.Y, sY + b * kTcBox, n0 + 32 * b, m0);
     }
     tc::tma_store_2d(&m.Fst, sF, m0, ((n + 1) & 1) * s.Cp + n0);
+    if constexpr (O::kNB == 2) tc::tma_store_2d(&m.Fstl, sF + O::kFTile, m0, ((n + 1) & 1) * s.Cp + n0);
     tc::tma_store_commit_and_wait_read();
   }
   if (warp == 0) tc::tmem_dealloc(tmem, 128);
@@ -382,14 +463,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int c0 = n0 + cl;
     uint32_t g[32];
     tc::tmem_ld_32x32b_x32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(cl), g);
-    uint8_t *sFcol = sF + cl * kTcBM + rl;
+    const FOut<kOpF8> fo = f_out<kOpF8>(sF, cl, rl);
     if (i < s.N && c0 + 32 <= s.C) {
-      sb_update_row32<P, true>(s, t, ka, dnext, kj[round], c0, g, hi, xbox, ybox, rl, sFcol);
+      sb_update_row32<P, true, kOpF8>(s, t, ka, dnext, kj[round], c0, g, hi, xbox, ybox, rl, fo);
     } else if (i < s.N && c0 < s.C) {
-      sb_update_row32<P, false>(s, t, ka, dnext, kj[round], c0, g, hi, xbox, ybox, rl, sFcol);
+      sb_update_row32<P, false, kOpF8>(s, t, ka, dnext, kj[round], c0, g, hi, xbox, ybox, rl, fo);
     } else {
 #pragma unroll
-      for (int j = 0; j < 32; ++j) sFcol[j * kTcBM] = 0;
+      for (int j = 0; j < 32; ++j) fo.zero(j);
     }
     tc::fence_proxy_async_smem();
     __syncthreads();
@@ -457,15 +538,18 @@ constexpr int kTpThreads = 512;  // 16 warps: warp w updates TMEM lanes 32 (w % 
 constexpr uint32_t kTmemX = 128, kTmemY = 256, kTmemCols = 512;
 constexpr uint64_t kFlagTimeoutNs = 2000000000ull;
 
-template <bool PAIR>
+template <bool PAIR, int OP = kOpF8>
 struct TpShape {
-  static constexpr int kStages = PAIR ? 8 : 6;
+  static constexpr int kNB = TcOp<OP>::kNB;
+  static constexpr int kStages = PAIR ? 8 : (kNB == 2 ? 3 : 6);
   static constexpr int kTileB = PAIR ? 64 * kTcBK : kTcTile;  // fT rows staged by this CTA: 64 of the pair's 128, or 128
-  static constexpr int kStageBytes = kTcTile + kTileB;
+  static constexpr int kStageBytes = kTcTile + kNB * kTileB;
   static constexpr uint32_t kExpect = PAIR ? 2 * kStageBytes : kStageBytes;  // bytes completing on one full barrier
-  static constexpr int kSmem = kStages * kStageBytes + kTcBM * kTcBN + 1024 + 256;
+  static constexpr int kFBytes = kNB * TcOp<OP>::kFTile;                 // f tile(s) of the epilogue
+  static constexpr int kSmem = kStages * kStageBytes + kFBytes + 1024 + 256;
 };
-static_assert(TpShape<false>::kSmem <= 227 * 1024 && TpShape<true>::kSmem <= 227 * 1024,
+static_assert(TpShape<false>::kSmem <= 227 * 1024 && TpShape<true>::kSmem <= 227 * 1024 &&
+                  TpShape<false, kOpBf16>::kSmem <= 227 * 1024 && TpShape<false, kOpBsb>::kSmem <= 227 * 1024,
               "persistent tile exceeds the shared memory of one CTA");
 
 struct TpArgs {
@@ -481,10 +565,10 @@ struct TpArgs {
 // the ring neighbours), then positions, wall and f, whose e4m3 code goes to
 // column j of the transposed f tile (sFcol[j * 128]).  FULL: all 32 columns
 // are below C.
-template <int P, bool FULL>
+template <int P, bool FULL, int OP>
 __device__ __forceinline__ void sb_update_regs32(const StateView &s, const StepTables &t, float ka, float dnext,
                                                  const KjChunk<P> &kj, int c0, const uint32_t (&g)[32], float hi,
-                                                 uint32_t (&xr)[32], uint32_t (&yr)[32], uint8_t *sFcol) {
+                                                 uint32_t (&xr)[32], uint32_t (&yr)[32], const FOut<OP> &fo) {
   constexpr int PR = P < 32 ? P : 32;
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
@@ -499,7 +583,6 @@ __device__ __forceinline__ void sb_update_regs32(const StateView &s, const StepT
   }
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
-    uint8_t e = 0;
     if (FULL || c0 + j < s.C) {
       float xn = fmaf(t.kx, __uint_as_float(yr[j]), __uint_as_float(xr[j]));
       if (fabsf(xn) > 1.f) {
@@ -507,23 +590,27 @@ __device__ __forceinline__ void sb_update_regs32(const StateView &s, const StepT
         yr[j] = __float_as_uint(0.f);
       }
       xr[j] = __float_as_uint(xn);
-      e = thresh_e4m3(xn, dnext);
+      fo.put(j, xn, dnext);
+    } else {
+      fo.zero(j);
     }
-    sFcol[j * kTcBM] = e;
   }
 }
 
-template <int P, bool PAIR>
+template <int P, bool PAIR, int OP>
 __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const StateView &s, const TpArgs &a,
                                                           const StepTables &t) {
-  using Sh = TpShape<PAIR>;
+  static_assert(!PAIR || OP == kOpF8, "CTA pairs run the e4m3 product only");
+  using Sh = TpShape<PAIR, OP>;
+  using O = TcOp<OP>;
   constexpr int kStages = Sh::kStages;
+  constexpr int kStageB = O::kNB * Sh::kTileB;  // B bytes of one stage (hi and lo for kOpBsb)
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t *sA = smem;
   uint8_t *sB = smem + kStages * kTcTile;
-  uint8_t *sF = sB + kStages * Sh::kTileB;  // [128 columns][128 spins] e4m3 f(x_next)
-  uint64_t *full = reinterpret_cast<uint64_t *>(sF + kTcBM * kTcBN);
+  uint8_t *sF = sB + kStages * kStageB;  // [128 columns][128 spins] f(x_next) (kOpBsb: hi, then lo)
+  uint64_t *full = reinterpret_cast<uint64_t *>(sF + Sh::kFBytes);
   uint64_t *empty = full + kStages;
   uint64_t *done = empty + kStages;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
@@ -542,7 +629,7 @@ __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const
   const bool leader = rank == 0;
   const int ct = PAIR ? blockIdx.y : blockIdx.x, mt = PAIR ? blockIdx.x : blockIdx.y;
   const int m0 = mt * kTcBM, n0 = ct * kTcBN;
-  const int KB = a.Kp / kTcBK;
+  const int KB = a.Kp / O::kKE;
   const int npre = KB < kStages ? KB : kStages;  // k-blocks whose J tile is loaded ahead
   // this CTA's operand loads: fT rows (B box) and the full barrier they complete on
   const CUtensorMap *mapB = PAIR ? &m.B64 : &m.B;
@@ -568,6 +655,10 @@ __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const
     tc::prefetch_tmap(&m.A);
     tc::prefetch_tmap(mapB);
     tc::prefetch_tmap(&m.Fst);
+    if constexpr (O::kNB == 2) {
+      tc::prefetch_tmap(&m.Bl);
+      tc::prefetch_tmap(&m.Fstl);
+    }
     for (int q = 0; q < 4; ++q) s_abort[q] = 0;
   }
   if (warp == 0) {
@@ -606,14 +697,15 @@ __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const
   if (warp == 0 && lane == 0 && a.n_begin < a.n_end) {  // J tiles of the first step's first stages
     for (int kb = 0; kb < npre; ++kb) {
       if (leader) tc::mbar_arrive_expect_tx(&full[kb], Sh::kExpect);
-      load_tile(sA + kb * kTcTile, &m.A, kb, kb * kTcBK, m0);
+      load_tile(sA + kb * kTcTile, &m.A, kb, kb * O::kKE, m0);
     }
   }
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
 
-  constexpr uint32_t idesc = tc::idesc_f8_e4m3(PAIR ? 2 * kTcBM : kTcBM, kTcBN);
+  constexpr uint32_t idesc = O::idesc(PAIR ? 2 * kTcBM : kTcBM, kTcBN);
+  constexpr int kFlagShift = OP == kOpF8 ? 0 : 1;  // k-blocks per 128-spin row tile: 1 (e4m3) or 2 (bf16)
   int n = a.n_begin;
   bool prefetched = a.n_begin < a.n_end;
   for (; n < a.n_end; ++n) {
@@ -626,7 +718,7 @@ __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const
       int kb = 0;
       while (kb < KB) {
         const int kq = kb + lane;
-        const bool ok = q == 0 || kq >= KB || tc::ld_acquire_gpu(a.flags + kq * a.Ct + ct) >= q;
+        const bool ok = q == 0 || kq >= KB || tc::ld_acquire_gpu(a.flags + (kq >> kFlagShift) * a.Ct + ct) >= q;
         const unsigned ball = __ballot_sync(0xffffffffu, ok);
         int nready = ball == 0xffffffffu ? 32 : __ffs(~ball) - 1;
         nready = nready < KB - kb ? nready : KB - kb;
@@ -657,9 +749,10 @@ __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const
             if (j >= npre) {
               if (use > 0) tc::mbar_wait(&empty[st], (use - 1) & 1, a.err, tc::ERR_WAIT_EMPTY);
               if (leader) tc::mbar_arrive_expect_tx(&full[st], Sh::kExpect);
-              load_tile(sA + st * kTcTile, &m.A, st, j * kTcBK, m0);
+              load_tile(sA + st * kTcTile, &m.A, st, j * O::kKE, m0);
             }
-            load_tile(sB + st * Sh::kTileB, mapB, st, j * kTcBK, brow + b_off);
+            load_tile(sB + st * kStageB, mapB, st, j * O::kKE, brow + b_off);
+            if constexpr (O::kNB == 2) load_tile(sB + st * kStageB + Sh::kTileB, &m.Bl, st, j * O::kKE, brow);
           }
         }
         __syncwarp();
@@ -672,7 +765,7 @@ __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const
           const uint32_t g = (q + 1) * KB + j, st = g % kStages, use = g / kStages;
           if (use > 0) tc::mbar_wait(&empty[st], (use - 1) & 1, a.err, tc::ERR_WAIT_EMPTY);
           if (leader) tc::mbar_arrive_expect_tx(&full[st], Sh::kExpect);
-          load_tile(sA + st * kTcTile, &m.A, st, j * kTcBK, m0);
+          load_tile(sA + st * kTcTile, &m.A, st, j * O::kKE, m0);
         }
       }
     } else if (warp == 1 && lane == 0 && leader) {
@@ -680,12 +773,17 @@ __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const
         const uint32_t g = q * KB + kb, st = g % kStages, use = g / kStages;
         tc::mbar_wait(&full[st], use & 1, a.err, tc::ERR_WAIT_FULL);
         tc::tc_fence_after();
-        const uint32_t a0 = tc::smem_u32(sA + st * kTcTile), b0 = tc::smem_u32(sB + st * Sh::kTileB);
+        const uint32_t a0 = tc::smem_u32(sA + st * kTcTile), b0 = tc::smem_u32(sB + st * kStageB);
 #pragma unroll
-        for (int kk = 0; kk < kTcBK / 32; ++kk) {
+        for (int kk = 0; kk < 4; ++kk) {
           const uint64_t ad = tc::smem_desc_sw128(a0 + kk * 32), bd = tc::smem_desc_sw128(b0 + kk * 32);
-          if constexpr (PAIR) tc::mma_f8_pair(tmem, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
-          else tc::mma_f8(tmem, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
+          if constexpr (PAIR) {
+            tc::mma_f8_pair(tmem, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
+          } else {
+            O::mma(tmem, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
+            if constexpr (O::kNB == 2)
+              O::mma(tmem, ad, tc::smem_desc_sw128(b0 + Sh::kTileB + kk * 32), idesc, 1u);
+          }
         }
         if constexpr (PAIR) tc::mma_commit_pair(&empty[st]);
         else tc::mma_commit(&empty[st]);
@@ -708,13 +806,13 @@ __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const
       tc::reg_fence(g);
       tc::reg_fence(xr);
       tc::reg_fence(yr);
-      uint8_t *sFcol = sF + cl * kTcBM + rl;
+      const FOut<OP> fo = f_out<OP>(sF, cl, rl);
       if (i < s.N && c0 < s.C) {
-        if (c0 + 32 <= s.C) sb_update_regs32<P, true>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, sFcol);
-        else sb_update_regs32<P, false>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, sFcol);
+        if (c0 + 32 <= s.C) sb_update_regs32<P, true, OP>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, fo);
+        else sb_update_regs32<P, false, OP>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, fo);
       } else {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) sFcol[j * kTcBM] = 0;
+        for (int j = 0; j < 32; ++j) fo.zero(j);
       }
       __syncwarp();
       tc::tmem_st_32x32b_x32(tmem + lane_off + kTmemX + cl, xr);
@@ -727,6 +825,7 @@ __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const
     if (threadIdx.x == 0) {
       // publish f_{n+1} of this tile: spins m0.., columns n0.. of the other FT buffer
       tc::tma_store_2d(&m.Fst, sF, m0, ((n + 1) & 1) * s.Cp + n0);
+      if constexpr (O::kNB == 2) tc::tma_store_2d(&m.Fstl, sF + O::kFTile, m0, ((n + 1) & 1) * s.Cp + n0);
       tc::tma_store_commit_and_wait_all();
       tc::fence_proxy_async_global();
       tc::st_release_gpu(a.flags + mt * a.Ct + ct, q + 1);
@@ -752,7 +851,8 @@ __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const
     const int brow = ((n + 1) & 1) * s.Cp + n0;
     for (int j = 0; j < npre; ++j) {
       const uint32_t g = q * KB + j, st = g % kStages, use = g / kStages;
-      load_tile(sB + st * Sh::kTileB, mapB, st, j * kTcBK, brow + b_off);
+      load_tile(sB + st * kStageB, mapB, st, j * O::kKE, brow + b_off);
+      if constexpr (O::kNB == 2) load_tile(sB + st * kStageB + Sh::kTileB, &m.Bl, st, j * O::kKE, brow);
       if (leader) tc::mbar_wait(&full[st], use & 1, a.err, tc::ERR_WAIT_FULL);
     }
   }
@@ -787,16 +887,16 @@ __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const
   }
 }
 
-template <int P>
+template <int P, int OP>
 __global__ void __launch_bounds__(kTpThreads, 1)
     k_solve_dense_tc_persistent(const __grid_constant__ TcMaps m, StateView s, TpArgs a, StepTables t) {
-  solve_dense_tc_persistent<P, false>(m, s, a, t);
+  solve_dense_tc_persistent<P, false, OP>(m, s, a, t);
 }
 
 template <int P>
 __global__ void __launch_bounds__(kTpThreads, 1)
     k_solve_dense_tc_pair(const __grid_constant__ TcMaps m, StateView s, TpArgs a, StepTables t) {
-  solve_dense_tc_persistent<P, true>(m, s, a, t);
+  solve_dense_tc_persistent<P, true, kOpF8>(m, s, a, t);
 }
 
 // ---------------------------------------------------------------- split-K persistent solver
@@ -1034,13 +1134,13 @@ __global__ void __launch_bounds__(kSkThreads, 1)
           g[4 * u + 3] = __float_as_uint(__uint_as_float(g[4 * u + 3]) + v.w);
         }
       }
-      uint8_t *sFcol = sF + cl * kTcBM + rl;
+      const FOut<kOpF8> fo = f_out<kOpF8>(sF, cl, rl);
       if (i < s.N && c0 < s.C) {
-        if (c0 + 32 <= s.C) sb_update_regs32<P, true>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, sFcol);
-        else sb_update_regs32<P, false>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, sFcol);
+        if (c0 + 32 <= s.C) sb_update_regs32<P, true, kOpF8>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, fo);
+        else sb_update_regs32<P, false, kOpF8>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, fo);
       } else {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) sFcol[j * kTcBM] = 0;
+        for (int j = 0; j < 32; ++j) fo.zero(j);
       }
       __syncwarp();
       tc::tmem_st_32x32b_x32(tmem + lane_off + kSkTmemX + cl, xr);
@@ -1102,6 +1202,30 @@ __global__ void k_f_to_ft8(StateView s, int which, uint8_t *FT, int Kp, int b) {
   const int c = int(e / Kp), j = int(e % Kp);
   const int8_t f = (j < s.N) ? int8_t(int(s.f_of(which)[size_t(j) * s.Cp + c]) - 1) : int8_t(0);
   FT[size_t(b) * s.Cp * Kp + e] = f_to_e4m3(f);
+}
+
+// f codes [N][Cp] -> bfloat16 f [Cp][Kp] (zeros for padded spins), for buffer b.
+__global__ void k_f_to_ft16(StateView s, int which, uint16_t *FT, int Kp, int b) {
+  const size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x;  // over Cp * Kp
+  if (e >= size_t(s.Cp) * Kp) return;
+  const int c = int(e / Kp), j = int(e % Kp);
+  const int f = (j < s.N) ? int(s.f_of(which)[size_t(j) * s.Cp + c]) - 1 : 0;
+  FT[size_t(b) * s.Cp * Kp + e] = f == 0 ? uint16_t(0) : (f > 0 ? uint16_t(0x3F80) : uint16_t(0xBF80));
+}
+
+// Ballistic form: f(x) = x of the state [N][Cp] -> hi = bf16(x) into buffer b of
+// the hi terms [2][Cp][Kp], lo = bf16(x - hi) into buffer b of the lo terms
+// that follow them (zeros for padded spins and columns past C).
+__global__ void k_x_to_ft_split(StateView s, uint16_t *FT, int Kp, int b) {
+  const size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x;  // over Cp * Kp
+  if (e >= size_t(s.Cp) * Kp) return;
+  const int c = int(e / Kp), j = int(e % Kp);
+  const float x = (j < s.N && c < s.C) ? s.x[size_t(j) * s.Cp + c] : 0.f;
+  const __nv_bfloat16 h = __float2bfloat16_rn(x);
+  const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
+  const size_t one = size_t(2) * s.Cp * Kp;
+  FT[size_t(b) * s.Cp * Kp + e] = __bfloat16_as_ushort(h);
+  FT[one + size_t(b) * s.Cp * Kp + e] = __bfloat16_as_ushort(l);
 }
 
 // ---------------------------------------------------------------- readout on the tensor cores
@@ -1258,16 +1382,35 @@ static bool make_map(CUtensorMap *m, const void *base, CUtensorMapDataType dt, s
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-bool tc_plan_make(void **plan, const uint8_t *J8, uint8_t *FT, int Kp, int Cp, float *x, float *y, int N) {
+size_t tc_ft_bytes(int Kp, int Cp, int op) {
+  const size_t one = size_t(2) * Cp * Kp;  // [2][Cp][Kp] elements
+  return op == kOpF8 ? one : (op == kOpBf16 ? 2 * one : 4 * one);
+}
+
+size_t tc_j_bytes(int Kp, int op) { return size_t(Kp) * Kp * (op == kOpF8 ? 1 : 2); }
+
+int tc_op_of(const void *plan) { return static_cast<const TcMaps *>(plan)->op; }
+
+bool tc_plan_make(void **plan, const void *J, void *FT, int Kp, int Cp, float *x, float *y, int N, int op) {
   auto *p = new TcMaps();
-  const auto U8 = CU_TENSOR_MAP_DATA_TYPE_UINT8, F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
-  const bool ok = make_map(&p->A, J8, U8, 1, uint64_t(Kp), uint64_t(Kp), 128, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
-                  make_map(&p->B, FT, U8, 1, uint64_t(2) * Cp, uint64_t(Kp), 128, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
-                  make_map(&p->B2, FT, U8, 1, uint64_t(2) * Cp, uint64_t(Kp), 128, 256, CU_TENSOR_MAP_SWIZZLE_128B) &&
-                  make_map(&p->B64, FT, U8, 1, uint64_t(2) * Cp, uint64_t(Kp), 128, 64, CU_TENSOR_MAP_SWIZZLE_128B) &&
-                  make_map(&p->X, x, F32, 4, uint64_t(N), uint64_t(Cp), 32, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
-                  make_map(&p->Y, y, F32, 4, uint64_t(N), uint64_t(Cp), 32, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
-                  make_map(&p->Fst, FT, U8, 1, uint64_t(2) * Cp, uint64_t(Kp), 128, 128, CU_TENSOR_MAP_SWIZZLE_NONE);
+  p->op = op;
+  const auto F32 = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const auto OT = op == kOpF8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const size_t eb = op == kOpF8 ? 1 : 2;
+  const uint32_t ke = uint32_t(128 / eb);  // K elements of one 128-byte operand row
+  const uint64_t rows_ft = uint64_t(2) * Cp;
+  uint8_t *ftl = static_cast<uint8_t *>(FT) + rows_ft * Kp * eb;  // kOpBsb: the lo terms after the hi terms
+  bool ok = make_map(&p->A, J, OT, eb, uint64_t(Kp), uint64_t(Kp), ke, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
+            make_map(&p->B, FT, OT, eb, rows_ft, uint64_t(Kp), ke, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
+            make_map(&p->X, x, F32, 4, uint64_t(N), uint64_t(Cp), 32, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
+            make_map(&p->Y, y, F32, 4, uint64_t(N), uint64_t(Cp), 32, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
+            make_map(&p->Fst, FT, OT, eb, rows_ft, uint64_t(Kp), 128, 128, CU_TENSOR_MAP_SWIZZLE_NONE);
+  if (ok && op == kOpF8)  // the wide, split-K and paired kernels run the e4m3 product only
+    ok = make_map(&p->B2, FT, OT, 1, rows_ft, uint64_t(Kp), 128, 256, CU_TENSOR_MAP_SWIZZLE_128B) &&
+         make_map(&p->B64, FT, OT, 1, rows_ft, uint64_t(Kp), 128, 64, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (ok && op == kOpBsb)
+    ok = make_map(&p->Bl, ftl, OT, 2, rows_ft, uint64_t(Kp), ke, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
+         make_map(&p->Fstl, ftl, OT, 2, rows_ft, uint64_t(Kp), 128, 128, CU_TENSOR_MAP_SWIZZLE_NONE);
   if (!ok) {
     delete p;
     return false;
@@ -1278,10 +1421,18 @@ bool tc_plan_make(void **plan, const uint8_t *J8, uint8_t *FT, int Kp, int Cp, f
 
 void tc_plan_free(void *plan) { delete static_cast<TcMaps *>(plan); }
 
-static const void *const kTpFns[6] = {
-    (const void *)k_solve_dense_tc_persistent<1>, (const void *)k_solve_dense_tc_persistent<2>,
-    (const void *)k_solve_dense_tc_persistent<4>, (const void *)k_solve_dense_tc_persistent<8>,
-    (const void *)k_solve_dense_tc_persistent<16>, (const void *)k_solve_dense_tc_persistent<32>};
+#define SBQA_TC_PS(K, ...)                                                                           \
+  {(const void *)K<1, __VA_ARGS__>, (const void *)K<2, __VA_ARGS__>, (const void *)K<4, __VA_ARGS__>, \
+   (const void *)K<8, __VA_ARGS__>, (const void *)K<16, __VA_ARGS__>, (const void *)K<32, __VA_ARGS__>}
+// [operand form][P index] of the per-step 128 x 128 kernel and the persistent solver
+static const void *const kTcFns[3][6] = {SBQA_TC_PS(k_step_dense_tc, kOpF8), SBQA_TC_PS(k_step_dense_tc, kOpBf16),
+                                         SBQA_TC_PS(k_step_dense_tc, kOpBsb)};
+static const void *const kTpFnsOp[3][6] = {SBQA_TC_PS(k_solve_dense_tc_persistent, kOpF8),
+                                           SBQA_TC_PS(k_solve_dense_tc_persistent, kOpBf16),
+                                           SBQA_TC_PS(k_solve_dense_tc_persistent, kOpBsb)};
+#undef SBQA_TC_PS
+static const int kTpSmemOp[3] = {TpShape<false, kOpF8>::kSmem, TpShape<false, kOpBf16>::kSmem,
+                                 TpShape<false, kOpBsb>::kSmem};
 
 static const void *const kPrFns[6] = {
     (const void *)k_solve_dense_tc_pair<1>, (const void *)k_solve_dense_tc_pair<2>,
@@ -1294,13 +1445,11 @@ static const void *const kSkFns[6] = {
     (const void *)k_solve_dense_tc_split<16>, (const void *)k_solve_dense_tc_split<32>};
 
 cudaError_t tc_set_attributes() {
-  const void *fns[6] = {(const void *)k_step_dense_tc<1>, (const void *)k_step_dense_tc<2>,
-                        (const void *)k_step_dense_tc<4>, (const void *)k_step_dense_tc<8>,
-                        (const void *)k_step_dense_tc<16>, (const void *)k_step_dense_tc<32>};
-  for (const void *f : fns) {
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-    if (e != cudaSuccess) return e;
-  }
+  for (int op = 0; op < 3; ++op)
+    for (const void *f : kTcFns[op]) {
+      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+      if (e != cudaSuccess) return e;
+    }
   const void *wide[6] = {(const void *)k_step_dense_tc_wide<1>, (const void *)k_step_dense_tc_wide<2>,
                          (const void *)k_step_dense_tc_wide<4>, (const void *)k_step_dense_tc_wide<8>,
                          (const void *)k_step_dense_tc_wide<16>, (const void *)k_step_dense_tc_wide<32>};
@@ -1308,10 +1457,11 @@ cudaError_t tc_set_attributes() {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kTwSmem);
     if (e != cudaSuccess) return e;
   }
-  for (const void *f : kTpFns) {
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, TpShape<false>::kSmem);
-    if (e != cudaSuccess) return e;
-  }
+  for (int op = 0; op < 3; ++op)
+    for (const void *f : kTpFnsOp[op]) {
+      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kTpSmemOp[op]);
+      if (e != cudaSuccess) return e;
+    }
   for (const void *f : kPrFns) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, TpShape<true>::kSmem);
     if (e != cudaSuccess) return e;
@@ -1384,12 +1534,13 @@ int tc_persistent_blocks() {
   int dev = 0, sms = 0, best = 1 << 30;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  for (const void *f : kTpFns) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kTpThreads, TpShape<false>::kSmem) != cudaSuccess)
-      return 0;
-    best = per_sm < best ? per_sm : best;
-  }
+  for (int op = 0; op < 3; ++op)
+    for (const void *f : kTpFnsOp[op]) {
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kTpThreads, kTpSmemOp[op]) != cudaSuccess)
+        return 0;
+      best = per_sm < best ? per_sm : best;
+    }
   return sms * best;
 }
 
@@ -1403,7 +1554,8 @@ cudaError_t launch_solve_dense_tc_persistent(const void *plan, const StateView &
                                              const StepTables &t, int n_begin, int n_end, uint32_t *flags,
                                              cudaStream_t st) {
   const int idx = s.P == 1 ? 0 : s.P == 2 ? 1 : s.P == 4 ? 2 : s.P == 8 ? 3 : s.P == 16 ? 4 : s.P == 32 ? 5 : -1;
-  if (idx < 0 || Kp % kTcBM != 0 || s.Cp % kTcBN != 0) return cudaErrorInvalidValue;
+  const int op = tc_op_of(plan);
+  if (idx < 0 || op < 0 || op > 2 || Kp % kTcBM != 0 || s.Cp % kTcBN != 0) return cudaErrorInvalidValue;
   const int Ct = s.Cp / kTcBN;
   cudaError_t e = cudaMemsetAsync(flags, 0, tc_persistent_flag_count(Kp, s.Cp) * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
@@ -1412,8 +1564,8 @@ cudaError_t launch_solve_dense_tc_persistent(const void *plan, const StateView &
   StateView sv = s;
   StepTables tv = t;
   void *args[] = {&maps, &sv, &a, &tv};
-  return cudaLaunchCooperativeKernel(kTpFns[idx], dim3(Ct, Kp / kTcBM), dim3(kTpThreads), args,
-                                     TpShape<false>::kSmem, st);
+  return cudaLaunchCooperativeKernel(kTpFnsOp[op][idx], dim3(Ct, Kp / kTcBM), dim3(kTpThreads), args,
+                                     kTpSmemOp[op], st);
 }
 
 int tc_pair_blocks() {
@@ -1459,12 +1611,15 @@ cudaError_t launch_solve_dense_tc_pair(const void *plan, const StateView &s, int
 template <int P>
 static cudaError_t launch_tc_p(const TcMaps *p, const StateView &s, const TcArgs &a, const StepTables &t, int n,
                                cudaStream_t st) {
-  if (s.Cp % kTwBN == 0) {
-    dim3 grid(s.Cp / kTwBN, a.Kp / kTcBM);
-    k_step_dense_tc_wide<P><<<grid, kTcThreads, kTwSmem, st>>>(*p, s, a, t, n);
+  const dim3 grid(s.Cp / kTcBN, a.Kp / kTcBM);
+  if (p->op == kOpBf16) {
+    k_step_dense_tc<P, kOpBf16><<<grid, kTcThreads, kTcSmem, st>>>(*p, s, a, t, n);
+  } else if (p->op == kOpBsb) {
+    k_step_dense_tc<P, kOpBsb><<<grid, kTcThreads, kTcSmem, st>>>(*p, s, a, t, n);
+  } else if (s.Cp % kTwBN == 0) {
+    k_step_dense_tc_wide<P><<<dim3(s.Cp / kTwBN, a.Kp / kTcBM), kTcThreads, kTwSmem, st>>>(*p, s, a, t, n);
   } else {
-    dim3 grid(s.Cp / kTcBN, a.Kp / kTcBM);
-    k_step_dense_tc<P><<<grid, kTcThreads, kTcSmem, st>>>(*p, s, a, t, n);
+    k_step_dense_tc<P, kOpF8><<<grid, kTcThreads, kTcSmem, st>>>(*p, s, a, t, n);
   }
   return cudaGetLastError();
 }
@@ -1473,6 +1628,7 @@ cudaError_t launch_step_dense_tc(const void *plan, const StateView &s, int Kp, u
                                  const StepTables &t, int n, cudaStream_t st) {
   const auto *p = static_cast<const TcMaps *>(plan);
   TcArgs a{Kp, FT, err, h};
+  if (s.Cp % kTcBN != 0 || Kp % kTcBM != 0) return cudaErrorInvalidValue;
   switch (s.P) {
     case 1: return launch_tc_p<1>(p, s, a, t, n, st);
     case 2: return launch_tc_p<2>(p, s, a, t, n, st);
@@ -1484,9 +1640,13 @@ cudaError_t launch_step_dense_tc(const void *plan, const StateView &s, int Kp, u
   }
 }
 
-cudaError_t launch_f_to_ft8(const StateView &s, int which, uint8_t *FT, int Kp, int buffer, cudaStream_t st) {
+cudaError_t launch_f_to_ft(const StateView &s, int which, uint8_t *FT, int Kp, int buffer, int op, cudaStream_t st) {
   const size_t total = size_t(s.Cp) * Kp;
-  k_f_to_ft8<<<unsigned((total + 255) / 256), 256, 0, st>>>(s, which, FT, Kp, buffer);
+  const unsigned blocks = unsigned((total + 255) / 256);
+  if (op == kOpF8) k_f_to_ft8<<<blocks, 256, 0, st>>>(s, which, FT, Kp, buffer);
+  else if (op == kOpBf16) k_f_to_ft16<<<blocks, 256, 0, st>>>(s, which, reinterpret_cast<uint16_t *>(FT), Kp, buffer);
+  else if (op == kOpBsb) k_x_to_ft_split<<<blocks, 256, 0, st>>>(s, reinterpret_cast<uint16_t *>(FT), Kp, buffer);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 

@@ -260,6 +260,26 @@ __host__ __device__ constexpr uint32_t idesc_f8_e4m3(int M, int N) {
          | (uint32_t(M >> 4) << 24);        // M / 16
 }
 
+// Instruction descriptor of tcgen05.mma kind::f16: D = F32, A = B = BF16,
+// both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4)                          // D format: F32
+         | (1u << 7) | (1u << 10)           // A, B format: BF16
+         | (uint32_t(N >> 3) << 17)         // N / 8
+         | (uint32_t(M >> 4) << 24);        // M / 16
+}
+
+// D (+)= A B with BF16 operands (K = 16 per instruction, 32 bytes of a
+// 128-byte swizzled row), FP32 accumulator in TMEM.
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 __device__ __forceinline__ void mma_f8(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                        uint32_t accumulate) {
   asm volatile(
