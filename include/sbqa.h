@@ -239,9 +239,12 @@ int sbqa_set_schedule(sbqa_problem *p, const sbqa_params *params);
  *   -> `steps` steps of Eqs. 6-7 with the wall rule
  *   -> sign readout, energies of all R*P replicas, per-run best.
  *   steps  >= 0 (0 reads out the initial state)
- *   P      replicas per run: 1, 2, 4, 8, 16 or 32
- *   R      runs, >= 1, R * P <= 2^20; must equal params.n_runs when beta
- *          and alpha were given
+ *   P      Trotter replicas per run, 1 <= P <= 128 (the periodic ring of
+ *          Eqs. 6-7 closes at P for any P; a run occupies the next power of
+ *          two of replica columns on the device, the rest being padding
+ *          that no replica reads; P > 128 gives UNSUPPORTED)
+ *   R      runs, >= 1, R * (P rounded up to a power of two) <= 2^20; must
+ *          equal params.n_runs when beta and alpha were given
  * Errors: STATE (no schedule), INVALID_ARG, UNSUPPORTED, OOM, CUDA.
  * Device buffers for the state are allocated on first use for a given
  * (P, R) and reused by later runs of the same shape.

@@ -17,6 +17,7 @@
 #include <string>
 #include <thread>
 #include <tuple>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/sbqa.h"
@@ -591,7 +592,8 @@ int prepare_dense_values(sbqa_problem *p, int precision) {
 }
 
 int alloc_run(sbqa_problem *p, int S, int P, int R) {
-  const int C = R * P;
+  const int Ps = run_width(P);  // a run's columns: P replicas, then padding up to a power of two
+  const int C = R * Ps;
   const int Cp = (C + kColsPerWarp - 1) / kColsPerWarp * kColsPerWarp;
   const size_t NC = size_t(p->n) * Cp;
   SBQA_CUDA(p->d_x.alloc(NC));
@@ -620,7 +622,7 @@ int alloc_run(sbqa_problem *p, int S, int P, int R) {
   SBQA_CUDA(p->d_best_spins.alloc(size_t(R) * p->n));
   SBQA_CUDA(p->d_err.alloc(1));
   SBQA_CUDA(cudaMemsetAsync(p->d_err.p, 0, sizeof(int), p->stream));  // no trial launch reads a stale code
-  p->S = S; p->P = P; p->R = R; p->C = C; p->Cp = Cp;
+  p->S = S; p->P = P; p->R = R; p->C = C; p->Cp = Cp; p->Ps = Ps;
   if (p->use_tc) {
     SBQA_CUDA(p->d_FT.alloc(tc_ft_bytes(p->Kp, Cp, p->tc_op)));
     if (!p->tc_plan || p->tc_plan_ft != p->d_FT.p || p->tc_plan_cp != Cp || p->tc_plan_x != p->d_x.p ||
@@ -1042,9 +1044,10 @@ int check_run_args(sbqa_problem *p, int32_t steps, int32_t P, int32_t R) {
   if (!p) return fail(SBQA_ERR_INVALID_ARG, "null problem");
   if (!p->have_params) return fail(SBQA_ERR_STATE, "sbqa_set_schedule has not been called");
   if (steps < 0) return fail(SBQA_ERR_INVALID_ARG, "steps must be >= 0");
-  if (!(P == 1 || P == 2 || P == 4 || P == 8 || P == 16 || P == 32))
-    return fail(SBQA_ERR_UNSUPPORTED, "P must be 1, 2, 4, 8, 16 or 32");
-  if (R < 1 || int64_t(R) * P > (1 << 20)) return fail(SBQA_ERR_INVALID_ARG, "need 1 <= R and R*P <= 2^20");
+  if (P < 1) return fail(SBQA_ERR_INVALID_ARG, "P must be >= 1");
+  if (P > kMaxReplicas) return fail(SBQA_ERR_UNSUPPORTED, "P must be at most 128");
+  if (R < 1 || int64_t(R) * run_width(P) > (1 << 20))
+    return fail(SBQA_ERR_INVALID_ARG, "need 1 <= R and R * (P rounded up to a power of two) <= 2^20");
   if (!p->beta.empty() && int(p->beta.size()) != R)
     return fail(SBQA_ERR_INVALID_ARG, "R differs from params.n_runs");
   return SBQA_OK;
@@ -1444,7 +1447,8 @@ int sbqa_run_finish(sbqa_problem *p) {
 int sbqa_run(sbqa_problem *p, int32_t steps, int32_t P, int32_t R, uint64_t seed, void *stream) {
   // small integer dense instances: the whole solve in one launch
   if (p && p->have_params && p->dense && p->is_integer && p->prm.eval_every == 0 &&
-      !p->ballistic() && check_run_args(p, steps, P, R) == SBQA_OK && small_eligible(p->n, P, steps)) {
+      !p->ballistic() && check_run_args(p, steps, P, R) == SBQA_OK && run_width(P) == P && P <= 32 &&
+      small_eligible(p->n, P, steps)) {
     DeviceGuard g(p->device);
     p->stream = static_cast<cudaStream_t>(stream);
     p->begun = p->finished = false;
@@ -1550,9 +1554,17 @@ int sbqa_get_energies(sbqa_problem *p, double *energy, int64_t *energy_int) {
   int rc = sbqa_synchronize(p);
   if (rc != SBQA_OK) return rc;
   DeviceGuard g(p->device);
-  if (energy) SBQA_CUDA(cudaMemcpy(energy, p->d_ef.p, size_t(p->C) * sizeof(double), cudaMemcpyDeviceToHost));
-  if (energy_int && p->is_integer)
-    SBQA_CUDA(cudaMemcpy(energy_int, p->d_ei.p, size_t(p->C) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+  // device energies by column r * Ps + k; the caller gets [r][k] for k < P
+  auto gather = [&](auto *out, const auto *dev) -> int {
+    using T = std::remove_pointer_t<decltype(out)>;
+    std::vector<T> buf(size_t(p->C));
+    SBQA_CUDA(cudaMemcpy(buf.data(), dev, size_t(p->C) * sizeof(T), cudaMemcpyDeviceToHost));
+    for (int r = 0; r < p->R; ++r)
+      for (int k = 0; k < p->P; ++k) out[size_t(r) * p->P + k] = buf[size_t(r) * p->Ps + k];
+    return SBQA_OK;
+  };
+  if (energy && (rc = gather(energy, p->d_ef.p)) != SBQA_OK) return rc;
+  if (energy_int && p->is_integer && (rc = gather(energy_int, p->d_ei.p)) != SBQA_OK) return rc;
   return SBQA_OK;
 }
 
@@ -1569,8 +1581,11 @@ int sbqa_get_state(sbqa_problem *p, float *x, float *y, int32_t *step_done) {
   for (int w = 0; w < 2; ++w) {
     if (!outs[w]) continue;
     SBQA_CUDA(cudaMemcpy(buf.data(), src[w], NC * sizeof(float), cudaMemcpyDeviceToHost));
-    for (int c = 0; c < p->C; ++c)
-      for (int i = 0; i < p->n; ++i) outs[w][size_t(c) * p->n + i] = buf[size_t(i) * p->Cp + c];
+    for (int r = 0; r < p->R; ++r)
+      for (int k = 0; k < p->P; ++k) {
+        const size_t c = size_t(r) * p->Ps + k, o = (size_t(r) * p->P + k) * p->n;
+        for (int i = 0; i < p->n; ++i) outs[w][o + i] = buf[size_t(i) * p->Cp + c];
+      }
   }
   if (step_done) *step_done = p->step_done;
   return SBQA_OK;
@@ -1584,11 +1599,14 @@ int sbqa_set_state(sbqa_problem *p, const float *x, const float *y, int32_t step
   if (rc != SBQA_OK) return rc;
   DeviceGuard g(p->device);
   const size_t NC = size_t(p->n) * p->Cp;
-  std::vector<float> bx(NC, 0.f), by(NC, 0.f);
-  for (int c = 0; c < p->C; ++c)
-    for (int i = 0; i < p->n; ++i) {
-      bx[size_t(i) * p->Cp + c] = x[size_t(c) * p->n + i];
-      by[size_t(i) * p->Cp + c] = y[size_t(c) * p->n + i];
+  std::vector<float> bx(NC, 0.f), by(NC, 0.f);  // padding columns of a run stay at zero
+  for (int r = 0; r < p->R; ++r)
+    for (int k = 0; k < p->P; ++k) {
+      const size_t c = size_t(r) * p->Ps + k, o = (size_t(r) * p->P + k) * p->n;
+      for (int i = 0; i < p->n; ++i) {
+        bx[size_t(i) * p->Cp + c] = x[o + i];
+        by[size_t(i) * p->Cp + c] = y[o + i];
+      }
     }
   SBQA_CUDA(cudaMemcpy(p->d_x.p, bx.data(), NC * sizeof(float), cudaMemcpyHostToDevice));
   SBQA_CUDA(cudaMemcpy(p->d_y.p, by.data(), NC * sizeof(float), cudaMemcpyHostToDevice));

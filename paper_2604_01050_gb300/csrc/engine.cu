@@ -101,7 +101,7 @@ struct Request {
 
   StateView state_view() const {
     StateView s;
-    s.N = prob->n; s.C = C; s.Cp = Cp; s.P = P; s.R = R;
+    s.N = prob->n; s.C = C; s.Cp = Cp; s.P = run_width(P); s.R = R; s.Pr = P;
     s.x = x; s.y = y; s.F[0] = F0; s.F[1] = F1; s.Sg = Sg;
     s.Fx[0] = s.Fx[1] = nullptr;
     return s;
@@ -169,7 +169,7 @@ namespace {
   } while (0)
 
 size_t request_bytes(const sbqa_problem *p, int S, int P, int R, bool tc, int Kp) {
-  const int C = R * P, Cp = (C + kColsPerWarp - 1) / kColsPerWarp * kColsPerWarp;
+  const int C = R * run_width(P), Cp = (C + kColsPerWarp - 1) / kColsPerWarp * kColsPerWarp;
   const size_t N = size_t(p->n), NC = N * Cp;
   const size_t nblk = size_t(energy_row_blocks(p->n));
   size_t b = 0;
@@ -218,7 +218,7 @@ void carve(Request &r, uint8_t *base, bool tc, int Kp) {
 int admit(sbqa_engine *e, Request &r, int slot, cudaStream_t st) {
   sbqa_problem *p = r.prob;
   const bool tc = p->use_tc;
-  r.C = r.R * r.P;
+  r.C = r.R * run_width(r.P);  // a run's columns: P replicas, then padding up to a power of two
   r.Cp = (r.C + kColsPerWarp - 1) / kColsPerWarp * kColsPerWarp;
   r.nblk = energy_row_blocks(p->n);
   carve(r, e->arena.base + r.off, tc, p->Kp);
@@ -248,7 +248,7 @@ SlotDesc slot_desc(const Request &r) {
   SlotDesc d{};
   d.row_ptr = v.row_ptr; d.col = v.col; d.npos = v.npos; d.val = v.val; d.h = v.h; d.kind = v.kind;
   d.ell_col = v.ell_col; d.ell_meta = v.ell_meta; d.ell_val = v.ell_val;
-  d.N = p->n; d.C = r.C; d.Cp = r.Cp; d.P = r.P; d.R = r.R; d.S = r.S;
+  d.N = p->n; d.C = r.C; d.Cp = r.Cp; d.P = run_width(r.P); d.Pr = r.P; d.R = r.R; d.S = r.S;
   d.x = r.x; d.y = r.y; d.F0 = r.F0; d.F1 = r.F1;
   d.ka = r.ka; d.dl = r.dl; d.kj = r.kj; d.kc = r.tables.kc; d.kx = r.tables.kx;
   d.n0 = r.n0;
@@ -429,8 +429,8 @@ int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done, int32_t *don
     if (e->slot_req[q] < 0) continue;
     Request &r = e->reqs[e->slot_req[q]];
     const int done_now = std::min(e->chunk, r.S - r.n0);
-    e->steps_done_total += int64_t(done_now) * r.prob->n * r.C;
-    if (!r.prob->dense) e->batched_updates += int64_t(done_now) * r.prob->n * r.C;
+    e->steps_done_total += int64_t(done_now) * r.prob->n * r.R * r.P;
+    if (!r.prob->dense) e->batched_updates += int64_t(done_now) * r.prob->n * r.R * r.P;
     r.n0 += done_now;
     if (r.n0 >= r.S) {
       if ((rc = readout(e, r, st)) != SBQA_OK) return rc;

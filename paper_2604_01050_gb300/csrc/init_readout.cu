@@ -39,8 +39,9 @@ __global__ void k_init(StateView s, uint64_t seed, float amp, float delta0) {
   const int i = int(e / s.Cp), c = int(e % s.Cp);
   float x = 0.f, y = 0.f;
   uint8_t f = kFZero;
-  if (c < s.C) {
-    const uint64_t el = uint64_t(c) * uint64_t(s.N) + uint64_t(i);  // (r * P + k) * N + i
+  const int r = c / s.P, k = c % s.P;  // run and replica of column c (k >= Pr: padding, left at zero)
+  if (c < s.C && k < s.Pr) {
+    const uint64_t el = (uint64_t(r) * uint64_t(s.Pr) + uint64_t(k)) * uint64_t(s.N) + uint64_t(i);
     x = to_uniform(splitmix64_at(seed, 2ull * el), amp);
     y = to_uniform(splitmix64_at(seed, 2ull * el + 1ull), amp);
     f = uint8_t(fcode(x, delta0));
@@ -268,9 +269,10 @@ cudaError_t launch_energy_dense_tc(const void *plan, const StateView &s, int Kp,
 }
 
 // ---------------------------------------------------------------- best per run
-// One block per run: warp 0 takes the argmin over the P replicas (lowest k on
-// ties), kept if strictly lower than the best so far; then all threads copy
-// the winner's spins (a strided gather of N bytes).
+// One block per run: warp 0 takes the argmin over the Pr replicas (lowest k
+// on ties; replica k of run r is column r * P + k), kept if strictly lower
+// than the best so far; then all threads copy the winner's spins (a strided
+// gather of N bytes).
 constexpr int kBestThreads = 256;
 
 __global__ void __launch_bounds__(kBestThreads) k_best(StateView s, EnergyView E, BestView b, int step) {
@@ -282,9 +284,14 @@ __global__ void __launch_bounds__(kBestThreads) k_best(StateView s, EnergyView E
     long long ei = LLONG_MAX;
     double ef = DBL_MAX;
     int k = lane;
-    if (lane < P) {
-      if (E.is_integer) ei = b.e_int[r * P + lane];
-      else ef = b.e_f64[r * P + lane];
+    for (int q = lane; q < s.Pr; q += 32) {  // each lane: the lowest of its replicas, the first on ties
+      const long long qi = E.is_integer ? b.e_int[r * P + q] : 0;
+      const double qf = E.is_integer ? 0.0 : b.e_f64[r * P + q];
+      if (q == lane || (E.is_integer ? qi < ei : qf < ef)) {
+        ei = E.is_integer ? qi : LLONG_MAX;
+        ef = E.is_integer ? DBL_MAX : qf;
+        k = q;
+      }
     }
     for (int o = 16; o > 0; o >>= 1) {
       const long long oi = __shfl_down_sync(0xffffffffu, ei, o);

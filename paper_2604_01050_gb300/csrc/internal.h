@@ -19,6 +19,15 @@
 namespace sbqa {
 
 constexpr int kColsPerWarp = 128;  // 32 lanes x 4 columns
+constexpr int kMaxReplicas = 128;  // Trotter replicas per run: a run's columns never leave a warp's 128
+
+// Columns a run of P replicas occupies: the smallest power of two >= P
+// (replica k of run r is column r * width + k; the rest of the run is padding).
+inline int run_width(int P) {
+  int w = 1;
+  while (w < P) w <<= 1;
+  return w;
+}
 constexpr int kColsPerLane = 4;
 
 enum ValKind : int { VAL_PM1 = 0, VAL_F32 = 1, VAL_BF16 = 2 };
@@ -32,7 +41,11 @@ struct StepTables {
 };
 
 struct StateView {
+  // P: columns per run (a power of two, the kernels' template width); Pr: the
+  // run's Trotter replicas (1 <= Pr <= P), columns r * P + k for k < Pr; the
+  // columns k >= Pr of a run are padding that no replica reads
   int N, C, Cp, P, R;
+  int Pr;
   float *x, *y;
   uint8_t *F[2];  // f(x) + 1 codes, double-buffered by step parity
   float *Fx[2];   // f(x) = x copies of the ballistic form (null otherwise)
@@ -170,6 +183,7 @@ struct SlotDesc {
   const float *h;
   int kind;
   int N, C, Cp, P, R, S;
+  int Pr;  // replicas of a run (P: its column width, a power of two)
   float *x, *y;
   uint8_t *F0, *F1;
   const float *ka, *dl, *kj;

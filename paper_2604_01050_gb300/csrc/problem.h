@@ -175,6 +175,7 @@ struct sbqa_problem {
 
   // run state
   int S = 0, P = 0, R = 0, C = 0, Cp = 0;
+  int Ps = 0;  // columns per run: run_width(P); C = R * Ps
   int step_done = 0;
   bool small_path = false;  // the last sbqa_run used the one-launch small solver
   bool begun = false, finished = false;
@@ -238,7 +239,8 @@ struct sbqa_problem {
 
   // the instance qualifies for the split-K persistent solver on 2-CTA clusters
   bool tc_split_possible() const {
-    return tc_persistent_ok() && tc_op == sbqa::kTcOpF8 && prm.kernel_select != 12 && prm.kernel_select != 13 &&
+    return tc_persistent_ok() && tc_op == sbqa::kTcOpF8 && Ps <= 32 && P == Ps && prm.kernel_select != 12 &&
+           prm.kernel_select != 13 &&
            !tc_split_failed &&
            sbqa::tc_split_eligible(Kp, Cp, tc_split_blocks);
   }
@@ -246,7 +248,8 @@ struct sbqa_problem {
 
   // the instance qualifies for the paired persistent solver (autotuned, or kernel_select 13)
   bool tc_pair_possible() const {
-    return tc_persistent_ok() && tc_op == sbqa::kTcOpF8 && (prm.kernel_select == 0 || prm.kernel_select == 13) &&
+    return tc_persistent_ok() && tc_op == sbqa::kTcOpF8 && Ps <= 32 && P == Ps &&
+           (prm.kernel_select == 0 || prm.kernel_select == 13) &&
            !tc_pair_failed &&
            sbqa::tc_pair_eligible(Kp, Cp, tc_pair_blocks);
   }
@@ -262,7 +265,7 @@ struct sbqa_problem {
 
   StateView state() const {
     StateView s;
-    s.N = n; s.C = C; s.Cp = Cp; s.P = P; s.R = R;
+    s.N = n; s.C = C; s.Cp = Cp; s.P = Ps; s.R = R; s.Pr = P;
     s.x = d_x.p; s.y = d_y.p;
     s.F[0] = d_F0.p; s.F[1] = d_F1.p;
     s.Fx[0] = d_Fx0.p; s.Fx[1] = d_Fx1.p;

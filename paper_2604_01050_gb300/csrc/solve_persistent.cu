@@ -273,6 +273,8 @@ static const void *persistent_fn_p(int P) {
     case 8: return (const void *)k_solve_csr_persistent<8, ROWS, KIND, W>;
     case 16: return (const void *)k_solve_csr_persistent<16, ROWS, KIND, W>;
     case 32: return (const void *)k_solve_csr_persistent<32, ROWS, KIND, W>;
+    case 64: return (const void *)k_solve_csr_persistent<64, ROWS, KIND, W>;
+    case 128: return (const void *)k_solve_csr_persistent<128, ROWS, KIND, W>;
     default: return nullptr;
   }
 }
@@ -307,7 +309,7 @@ int persistent_blocks() {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   // the smallest co-resident count over all instantiations, so any of them fits the grid
-  const int Ps[6] = {1, 2, 4, 8, 16, 32};
+  const int Ps[8] = {1, 2, 4, 8, 16, 32, 64, 128};
   for (int P : Ps)
     for (int kind = 0; kind < 3; ++kind)
       for (int rows = 0; rows < 2; ++rows)

@@ -24,7 +24,7 @@ __device__ __forceinline__ void batched_row_csr(const SlotDesc &d, int n, int i,
                                                 float hi) {
   const int lane = threadIdx.x & 31;
   StateView s;
-  s.N = d.N; s.C = d.C; s.Cp = d.Cp; s.P = P; s.R = d.R;
+  s.N = d.N; s.C = d.C; s.Cp = d.Cp; s.P = P; s.R = d.R; s.Pr = d.Pr;
   s.x = d.x; s.y = d.y; s.F[0] = d.F0; s.F[1] = d.F1; s.Sg = nullptr;
   s.Fx[0] = s.Fx[1] = nullptr;
   StepTables t;
@@ -123,7 +123,7 @@ __device__ __forceinline__ void fetch_row(RowFetch &f, const SlotDesc *D, const 
   f.dnext = __ldg(d.dl + f.n + 1);
   if (W == 4) {
     const float *kjn = d.kj + size_t(f.n) * d.R;
-    const int lp = __ffs(d.P) - 1;  // P is a power of two
+    const int lp = __ffs(d.P) - 1;  // P (the run's column width) is a power of two
     if (d.P >= 4) {
       const float k = f.c0 < d.C ? __ldg(kjn + (f.c0 >> lp)) : 0.f;
       f.kj[0] = f.kj[1] = f.kj[2] = f.kj[3] = k;
@@ -153,10 +153,7 @@ __device__ __forceinline__ LaneConsts<P> lane_consts(const SlotDesc &d, const Ro
 #pragma unroll
   for (int q = 0; q < 4; ++q) L.kj[q] = f.kj[q];
   L.active = f.c0 < d.C;
-  const int lane = threadIdx.x & 31;
-  const int k0 = f.c0 % P;
-  L.src_l = (k0 == 0) ? lane + P / 4 - 1 : lane - 1;
-  L.src_r = (k0 + 3 == P - 1) ? lane - P / 4 + 1 : lane + 1;
+  L.Pr = d.Pr;
   return L;
 }
 
@@ -165,7 +162,7 @@ __device__ __forceinline__ LaneConsts<P> lane_consts(const SlotDesc &d, const Ro
 template <int P, int W>
 __device__ __forceinline__ void batched_row_ell(const SlotDesc &d, const RowFetch &f) {
   StateView s;
-  s.N = d.N; s.C = d.C; s.Cp = d.Cp; s.P = P; s.R = d.R;
+  s.N = d.N; s.C = d.C; s.Cp = d.Cp; s.P = P; s.R = d.R; s.Pr = d.Pr;
   s.x = d.x; s.y = d.y; s.F[0] = d.F0; s.F[1] = d.F1; s.Sg = nullptr;
   s.Fx[0] = s.Fx[1] = nullptr;
   const uint8_t *Fc = s.f_of(f.n) + f.c0;
@@ -276,7 +273,9 @@ __global__ void __launch_bounds__(256, 2) k_step_batched(const SlotDesc *slots, 
       case 4: batched_row<4>(d, cur); break;
       case 8: batched_row<8>(d, cur); break;
       case 16: batched_row<16>(d, cur); break;
-      default: batched_row<32>(d, cur); break;
+      case 32: batched_row<32>(d, cur); break;
+      case 64: batched_row<64>(d, cur); break;
+      default: batched_row<128>(d, cur); break;
     }
   }
 }

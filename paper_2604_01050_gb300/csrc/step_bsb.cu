@@ -28,8 +28,8 @@ __device__ __forceinline__ void sb_update4_bsb(const StateView &s, const StepTab
   float xs[4] = {xv.x, xv.y, xv.z, xv.w};
   float ys[4] = {yv.x, yv.y, yv.z, yv.w};
   float xm[4], xp[4];
-  ring_neighbours<P>(xs, c4, xm, xp);  // all lanes take part (shuffles)
-  if (c4 >= s.C) return;               // padding columns past R * P
+  ring_neighbours<P>(xs, s.Pr, xm, xp);  // all lanes take part (shuffles)
+  if (c4 >= s.C) return;                 // padding columns past R * P
   const float ka = __ldg(t.ka + n);
   const float *kjn = t.kj + size_t(n) * t.R;
   float kj[4];
@@ -217,6 +217,8 @@ cudaError_t launch_step_csr_bsb(const StateView &s, const CsrView &J, const Step
     case 8: return launch_csr_p<8>(s, J, t, n, st);
     case 16: return launch_csr_p<16>(s, J, t, n, st);
     case 32: return launch_csr_p<32>(s, J, t, n, st);
+    case 64: return launch_csr_p<64>(s, J, t, n, st);
+    case 128: return launch_csr_p<128>(s, J, t, n, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -230,6 +232,8 @@ cudaError_t launch_step_dense_bsb(const StateView &s, const DenseView &J, const 
     case 8: return launch_dense_p<8>(s, J, t, n, st);
     case 16: return launch_dense_p<16>(s, J, t, n, st);
     case 32: return launch_dense_p<32>(s, J, t, n, st);
+    case 64: return launch_dense_p<64>(s, J, t, n, st);
+    case 128: return launch_dense_p<128>(s, J, t, n, st);
     default: return cudaErrorInvalidValue;
   }
 }

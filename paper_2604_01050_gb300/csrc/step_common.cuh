@@ -1,11 +1,12 @@
 // step_common.cuh -- the per-element part of one SBQA step, shared by the
 // sparse and dense step kernels.
 //
-// One lane owns 4 consecutive columns (replicas) of one spin row i.  Because
-// P divides 32 and a warp owns 128 aligned columns, the replica ring of every
-// run (k - 1, k + 1 modulo P; periodic imaginary time, Supplement Eq. S3)
-// lies inside the warp, so the neighbour positions come from warp shuffles
-// and x can be updated in place.
+// One lane owns 4 (or W) consecutive columns of one spin row i.  A run of Pr
+// replicas occupies P columns, P the power of two >= Pr (up to 128), and a
+// warp owns 128 (32 W) aligned columns, so the replica ring of every run
+// (k - 1, k + 1 modulo Pr; periodic imaginary time, Supplement Eq. S3) lies
+// inside the warp: the neighbour positions come from registers and warp
+// shuffles, and x can be updated in place.
 //
 // Update of Sec. II A, Eqs. 6-7 (symplectic Euler, momentum first) with the
 // wall rule stated after Eq. 3 and the threshold f of Eq. 8 for the next step:
@@ -18,33 +19,65 @@
 
 namespace sbqa {
 
-// Neighbour positions of the lane's 4 columns.  c4 = first column (multiple
-// of 4); xs = the lane's positions.  All shuffle sources stay inside the warp
-// because lane 0 starts a run and lane 31 ends one.
-template <int P>
-__device__ __forceinline__ void ring_neighbours(const float xs[4], int c4, float xm[4],
-                                                float xp[4]) {
-  const int lane = threadIdx.x & 31;
-  if constexpr (P == 1) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) { xm[j] = xs[j]; xp[j] = xs[j]; }
-  } else if constexpr (P == 2) {
-    xm[0] = xp[0] = xs[1];
-    xm[1] = xp[1] = xs[0];
-    xm[2] = xp[2] = xs[3];
-    xm[3] = xp[3] = xs[2];
-  } else {
-    const int k0 = c4 % P;        // replica index of the lane's first column
-    const int k3 = k0 + 3;        // and of its last column (same run)
-    const int src_l = (k0 == 0) ? lane + P / 4 - 1 : lane - 1;
-    const int src_r = (k3 == P - 1) ? lane - P / 4 + 1 : lane + 1;
-    const float left = __shfl_sync(0xffffffffu, xs[3], src_l);
-    const float right = __shfl_sync(0xffffffffu, xs[0], src_r);
-    xm[0] = left;  xp[0] = xs[1];
-    xm[1] = xs[0]; xp[1] = xs[2];
-    xm[2] = xs[1]; xp[2] = xs[3];
-    xm[3] = xs[2]; xp[3] = right;
+// Ring neighbours x_{k-1}, x_{k+1} (k modulo Pr, periodic imaginary time) of
+// the W consecutive columns c0 .. c0 + W - 1 of one lane.  Runs occupy P
+// columns (a power of two dividing the warp's 32 W columns, so a run never
+// leaves the warp); the first Pr of them are the run's replicas (P / 2 < Pr
+// <= P) and the rest padding that no replica reads.  P <= W: whole runs
+// inside the lane; P > W: a run spans P / W lanes and the neighbours across
+// lanes come by shuffle.  GEN = false takes Pr = P (no padding); GEN = true
+// handles any Pr without branches, and gives the same values when Pr = P.
+// Every lane takes part (Pr is the same in the whole warp).
+template <int P, int W, bool GEN = true>
+__device__ __forceinline__ void ring_nb(const float (&xs)[W], int Pr, float (&xm)[W], float (&xp)[W]) {
+  if constexpr (P <= 2 || !GEN) {
+    Pr = P;  // a run of 1 or 2 columns has no padding (P = run_width(Pr))
   }
+  if constexpr (P <= W) {
+#pragma unroll
+    for (int base = 0; base < W; base += P) {
+      // replica Pr - 1 of the run (Pr - 1 >= P / 2 when P >= 2)
+      float last = xs[base + P - 1];
+      if constexpr (P > 2 && GEN) {
+#pragma unroll
+        for (int k = P / 2; k < P - 1; ++k) last = (k == Pr - 1) ? xs[base + k] : last;
+      }
+#pragma unroll
+      for (int k = 0; k < P; ++k) {
+        const int j = base + k;
+        xm[j] = k == 0 ? last : xs[j - 1];
+        xp[j] = (k == P - 1 || k == Pr - 1) ? xs[base] : xs[j + 1];
+      }
+    }
+  } else {
+    constexpr int L = P / W;  // lanes per run
+    const int lane = threadIdx.x & 31, part = lane % L, base_lane = lane - part;
+    const float left = __shfl_sync(0xffffffffu, xs[W - 1], part == 0 ? lane : lane - 1);
+    const float right = __shfl_sync(0xffffffffu, xs[0], part == L - 1 ? lane : lane + 1);
+    // replica Pr - 1 sits in lane base_lane + (Pr - 1) / W, slot (Pr - 1) % W
+    float mine = xs[W - 1];
+    if constexpr (GEN) {
+      const int slot = (Pr - 1) % W;
+#pragma unroll
+      for (int u = 0; u < W - 1; ++u) mine = (u == slot) ? xs[u] : mine;
+    }
+    const float last = __shfl_sync(0xffffffffu, mine, base_lane + (Pr - 1) / W);
+    const float first = __shfl_sync(0xffffffffu, xs[0], base_lane);
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+      const int k = part * W + j;
+      xm[j] = j == 0 ? (part == 0 ? last : left) : xs[j - 1];
+      xp[j] = k == Pr - 1 ? first : (j == W - 1 ? right : xs[j + 1]);
+    }
+  }
+}
+
+// Neighbour positions of the lane's 4 columns (c4 = first column, a multiple
+// of 4; a warp owns 128 aligned columns, so with P <= 128 every run lies
+// inside the warp).
+template <int P>
+__device__ __forceinline__ void ring_neighbours(const float (&xs)[4], int Pr, float (&xm)[4], float (&xp)[4]) {
+  ring_nb<P, 4>(xs, Pr, xm, xp);
 }
 
 __device__ __forceinline__ int8_t thresh(float x, float delta) {
@@ -80,8 +113,8 @@ __device__ __forceinline__ void sb_update4(const StateView &s, const StepTables 
   float xs[4] = {xv.x, xv.y, xv.z, xv.w};
   float ys[4] = {yv.x, yv.y, yv.z, yv.w};
   float xm[4], xp[4];
-  ring_neighbours<P>(xs, c4, xm, xp);  // all lanes take part (shuffles)
-  if (c4 >= s.C) return;               // padding columns past R * P
+  ring_neighbours<P>(xs, s.Pr, xm, xp);  // all lanes take part (shuffles)
+  if (c4 >= s.C) return;                 // padding columns past R * P
   const float ka = t.ka[n];
   const float dnext = t.dl[n + 1];
   const float *kjn = t.kj + size_t(n) * t.R;
@@ -147,10 +180,11 @@ struct LaneConsts {
   float2 kc2, mka2, kx2;
   float kj[4];
   float dnext;
-  int src_l, src_r;  // shuffle sources of the ring neighbours (P >= 4)
+  int Pr;            // replicas of a run
   bool active;       // the lane's first column is inside R * P
 
   __device__ __forceinline__ void load(const StateView &s, const StepTables &t, int n, int c4) {
+    Pr = s.Pr;
     const float ka = __ldg(t.ka + n);
     dnext = __ldg(t.dl + n + 1);
     kc2 = make_float2(t.kc, t.kc);
@@ -165,10 +199,6 @@ struct LaneConsts {
 #pragma unroll
       for (int j = 0; j < 4; ++j) kj[j] = (c4 + j < s.C) ? __ldg(kjn + (c4 + j) / P) : 0.f;
     }
-    const int lane = threadIdx.x & 31;
-    const int k0 = c4 % P;
-    src_l = (k0 == 0) ? lane + P / 4 - 1 : lane - 1;
-    src_r = (k0 + 3 == P - 1) ? lane - P / 4 + 1 : lane + 1;
   }
 };
 
@@ -187,12 +217,7 @@ __device__ __forceinline__ void sb_update4c(const StateView &s, const LaneConsts
     xm[0] = xp[0] = xs[1]; xm[1] = xp[1] = xs[0];
     xm[2] = xp[2] = xs[3]; xm[3] = xp[3] = xs[2];
   } else {
-    const float left = __shfl_sync(0xffffffffu, xs[3], L.src_l);
-    const float right = __shfl_sync(0xffffffffu, xs[0], L.src_r);
-    xm[0] = left;  xp[0] = xs[1];
-    xm[1] = xs[0]; xp[1] = xs[2];
-    xm[2] = xs[1]; xp[2] = xs[3];
-    xm[3] = xs[2]; xp[3] = right;
+    ring_nb<P, 4>(xs, L.Pr, xm, xp);
   }
   if (!L.active) return;
   const float2 h2 = make_float2(hi, hi);
@@ -238,29 +263,8 @@ template <int P, int W>
 __device__ __forceinline__ void sb_updateW(const StateView &s, const StepTables &t, float ka, float dnext, int n,
                                            int i, int c0, const float (&G)[W], float hi, float (&xs)[W],
                                            float (&ys)[W], uint8_t *Fout) {
-  const int lane = threadIdx.x & 31;
   float xm[W], xp[W];
-  if constexpr (P <= W) {
-#pragma unroll
-    for (int j = 0; j < W; ++j) {
-      const int k = j % P, base = j - k;
-      xm[j] = xs[base + (k + P - 1) % P];
-      xp[j] = xs[base + (k + 1) % P];
-    }
-  } else {
-    // a run spans P / W lanes; lane part = (lane % (P / W))
-    constexpr int L = P / W;
-    const int part = lane % L;
-    const int src_l = part == 0 ? lane + L - 1 : lane - 1;
-    const int src_r = part == L - 1 ? lane - L + 1 : lane + 1;
-    const float left = __shfl_sync(0xffffffffu, xs[W - 1], src_l);
-    const float right = __shfl_sync(0xffffffffu, xs[0], src_r);
-#pragma unroll
-    for (int j = 0; j < W; ++j) {
-      xm[j] = j == 0 ? left : xs[j - 1];
-      xp[j] = j == W - 1 ? right : xs[j + 1];
-    }
-  }
+  ring_nb<P, W>(xs, s.Pr, xm, xp);  // all lanes take part (shuffles)
   if (c0 >= s.C) return;
   const float *kjn = t.kj + size_t(n) * t.R;
   const float2 kc2 = make_float2(t.kc, t.kc), mka2 = make_float2(-ka, -ka), kx2 = make_float2(t.kx, t.kx);

@@ -89,6 +89,8 @@ cudaError_t launch_step_dense(const StateView &s, const DenseView &J, const Step
     case 8: return launch_p<8>(s, J, t, n, st);
     case 16: return launch_p<16>(s, J, t, n, st);
     case 32: return launch_p<32>(s, J, t, n, st);
+    case 64: return launch_p<64>(s, J, t, n, st);
+    case 128: return launch_p<128>(s, J, t, n, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -159,16 +159,66 @@ struct KjChunk {
   }
 };
 
+// Positions of one spin row just outside a 32-column chunk of a run that
+// spans several chunks (P = 64, 128): the columns left and right of the
+// chunk and the run's replicas 0 and Pr - 1, read before any chunk of the
+// tile is written back.
+struct RingExt {
+  float left, right, first, last;
+};
+
+// Ring neighbours (k modulo Pr) of a row's 32 consecutive columns c0.. held
+// by one thread: runs inside the chunk for P <= 32 (GEN = false: Pr = P,
+// the form of power-of-two replica counts), else from the chunk and the four
+// outside values of e.
+template <int P, bool GEN>
+__device__ __forceinline__ void ring32(const float (&xs)[32], int Pr, int c0, const RingExt &e, float (&xm)[32],
+                                       float (&xp)[32]) {
+  if constexpr (P <= 32) {
+    ring_nb<P, 32, GEN>(xs, Pr, xm, xp);
+  } else {
+    const int part = (c0 % P) / 32;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int k = part * 32 + j;
+      xm[j] = j == 0 ? (part == 0 ? e.last : e.left) : xs[j - 1];
+      xp[j] = k == Pr - 1 ? e.first : (j == 31 ? e.right : xs[j + 1]);
+    }
+  }
+}
+
+// Column c (inside the 128-column tile) of row r in the swizzled state boxes.
+__device__ __forceinline__ float box_at(uint8_t *boxes, int r, int c) {
+  const uint8_t *box = boxes + (c >> 5) * kTcBox;
+  const int e = c & 31;
+  return reinterpret_cast<const float *>(box + r * 128 + (((e >> 2) ^ (r & 7)) << 4))[e & 3];
+}
+
+// The outside values of ring32 for the chunk at tile column cl of row r.
+template <int P>
+__device__ __forceinline__ RingExt ring_ext_boxes(uint8_t *xboxes, int r, int cl, int Pr) {
+  RingExt e{0.f, 0.f, 0.f, 0.f};
+  if constexpr (P > 32) {
+    const int rb = cl - cl % P;  // first column of the run inside the tile
+    e.left = cl > rb ? box_at(xboxes, r, cl - 1) : 0.f;
+    e.right = cl + 32 < rb + P ? box_at(xboxes, r, cl + 32) : 0.f;
+    e.first = box_at(xboxes, r, rb);
+    e.last = box_at(xboxes, r, rb + Pr - 1);
+  }
+  return e;
+}
+
 // Update of one spin row for 32 aligned columns c0..c0+31 (whole runs,
 // because P divides 32); x and y are read from and written back to one row of
 // the swizzled shared-memory state boxes; the e4m3 code of f(x_next) of
 // column j goes to sFcol[j * 128] of the transposed f tile.  Same arithmetic,
 // in the same order, as sb_update4.  FULL: all 32 columns are below C (no
 // per-column test).
-template <int P, bool FULL, int OP>
+template <int P, bool FULL, int OP, bool GEN = false>
 __device__ __forceinline__ void sb_update_row32(const StateView &s, const StepTables &t, float ka, float dnext,
                                                 const KjChunk<P> &kj, int c0, const uint32_t (&g)[32], float hi,
-                                                uint8_t *xbox, uint8_t *ybox, int r, const FOut<OP> &fo) {
+                                                uint8_t *xbox, uint8_t *ybox, int r, const FOut<OP> &fo,
+                                                const RingExt &ext) {
   constexpr int PR = P < 32 ? P : 32;
   float xs[32], ys[32];
 #pragma unroll
@@ -177,11 +227,12 @@ __device__ __forceinline__ void sb_update_row32(const StateView &s, const StepTa
     xs[4 * u] = a.x; xs[4 * u + 1] = a.y; xs[4 * u + 2] = a.z; xs[4 * u + 3] = a.w;
     ys[4 * u] = b.x; ys[4 * u + 1] = b.y; ys[4 * u + 2] = b.z; ys[4 * u + 3] = b.w;
   }
+  float xms[32], xps[32];
+  ring32<P, GEN>(xs, s.Pr, c0, ext, xms, xps);
   float xo[32], yo[32];
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
-    const int k = j % P, base = j - k;
-    const float xm = xs[base + (k + P - 1) % P], xp = xs[base + (k + 1) % P];
+    const float xm = xms[j], xp = xps[j];
     xo[j] = xs[j];
     yo[j] = ys[j];
     if (!FULL && c0 + j >= s.C) {
@@ -207,7 +258,7 @@ __device__ __forceinline__ void sb_update_row32(const StateView &s, const StepTa
   }
 }
 
-template <int P, int OP>
+template <int P, int OP, bool GEN>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_step_dense_tc(const __grid_constant__ TcMaps m, StateView s, TcArgs a, StepTables t, int n) {
   using O = TcOp<OP>;
@@ -308,13 +359,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   {
     const int cl = 32 * b;  // first column of the chunk inside the tile
     const int c0 = n0 + cl;
+    // runs over several chunks (P > 32): their outside neighbours before any chunk is written back
+    const RingExt ext = ring_ext_boxes<P>(sX, rl, cl, s.Pr);
+    if constexpr (P > 32) __syncthreads();
     uint32_t g[32];
     tc::tmem_ld_32x32b_x32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(cl), g);
     const FOut<OP> fo = f_out<OP>(sF, cl, rl);
     if (i < s.N && c0 + 32 <= s.C) {
-      sb_update_row32<P, true, OP>(s, t, ka, dnext, kj, c0, g, hi, sX + b * kTcBox, sY + b * kTcBox, rl, fo);
+      sb_update_row32<P, true, OP, GEN>(s, t, ka, dnext, kj, c0, g, hi, sX + b * kTcBox, sY + b * kTcBox, rl, fo,
+                                        ext);
     } else if (i < s.N && c0 < s.C) {
-      sb_update_row32<P, false, OP>(s, t, ka, dnext, kj, c0, g, hi, sX + b * kTcBox, sY + b * kTcBox, rl, fo);
+      sb_update_row32<P, false, OP, GEN>(s, t, ka, dnext, kj, c0, g, hi, sX + b * kTcBox, sY + b * kTcBox, rl, fo,
+                                         ext);
     } else {
 #pragma unroll
       for (int j = 0; j < 32; ++j) fo.zero(j);
@@ -465,9 +521,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc::tmem_ld_32x32b_x32(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(cl), g);
     const FOut<kOpF8> fo = f_out<kOpF8>(sF, cl, rl);
     if (i < s.N && c0 + 32 <= s.C) {
-      sb_update_row32<P, true, kOpF8>(s, t, ka, dnext, kj[round], c0, g, hi, xbox, ybox, rl, fo);
+      sb_update_row32<P, true, kOpF8>(s, t, ka, dnext, kj[round], c0, g, hi, xbox, ybox, rl, fo, RingExt{});
     } else if (i < s.N && c0 < s.C) {
-      sb_update_row32<P, false, kOpF8>(s, t, ka, dnext, kj[round], c0, g, hi, xbox, ybox, rl, fo);
+      sb_update_row32<P, false, kOpF8>(s, t, ka, dnext, kj[round], c0, g, hi, xbox, ybox, rl, fo, RingExt{});
     } else {
 #pragma unroll
       for (int j = 0; j < 32; ++j) fo.zero(j);
@@ -565,17 +621,21 @@ struct TpArgs {
 // the ring neighbours), then positions, wall and f, whose e4m3 code goes to
 // column j of the transposed f tile (sFcol[j * 128]).  FULL: all 32 columns
 // are below C.
-template <int P, bool FULL, int OP>
+template <int P, bool FULL, int OP, bool GEN = false>
 __device__ __forceinline__ void sb_update_regs32(const StateView &s, const StepTables &t, float ka, float dnext,
                                                  const KjChunk<P> &kj, int c0, const uint32_t (&g)[32], float hi,
-                                                 uint32_t (&xr)[32], uint32_t (&yr)[32], const FOut<OP> &fo) {
+                                                 uint32_t (&xr)[32], uint32_t (&yr)[32], const FOut<OP> &fo,
+                                                 const RingExt &ext) {
   constexpr int PR = P < 32 ? P : 32;
+  float xs[32], xms[32], xps[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) xs[j] = __uint_as_float(xr[j]);
+  ring32<P, GEN>(xs, s.Pr, c0, ext, xms, xps);
 #pragma unroll
   for (int j = 0; j < 32; ++j) {
     if (!FULL && c0 + j >= s.C) continue;
-    const int k = j % P, base = j - k;
-    const float xm = __uint_as_float(xr[base + (k + P - 1) % P]), xp = __uint_as_float(xr[base + (k + 1) % P]);
-    const float xj = __uint_as_float(xr[j]);
+    const float xm = xms[j], xp = xps[j];
+    const float xj = xs[j];
     float yn = fmaf(t.kc, __uint_as_float(g[j]) + hi, __uint_as_float(yr[j]));
     yn = fmaf(-ka, xj, yn);
     yn = fmaf(kj.get(c0, j / PR), xm + xp, yn);
@@ -597,7 +657,7 @@ __device__ __forceinline__ void sb_update_regs32(const StateView &s, const StepT
   }
 }
 
-template <int P, bool PAIR, int OP>
+template <int P, bool PAIR, int OP, bool GEN>
 __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const StateView &s, const TpArgs &a,
                                                           const StepTables &t) {
   static_assert(!PAIR || OP == kOpF8, "CTA pairs run the e4m3 product only");
@@ -802,14 +862,29 @@ __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const
       tc::tmem_ld_32x32b_x32_nowait(tmem + lane_off + cl, g);
       tc::tmem_ld_32x32b_x32_nowait(tmem + lane_off + kTmemX + cl, xr);
       tc::tmem_ld_32x32b_x32_nowait(tmem + lane_off + kTmemY + cl, yr);
+      RingExt ext{0.f, 0.f, 0.f, 0.f};
+      if constexpr (P > 32) {
+        // runs over several chunks: their outside neighbours, read before any warp stores its new x
+        const int rb = cl - cl % P;
+        const uint32_t xb = tmem + lane_off + kTmemX;
+        const uint32_t u0 = tc::tmem_ld_32x32b_x1_nowait(xb + uint32_t(cl > rb ? cl - 1 : cl));
+        const uint32_t u1 = tc::tmem_ld_32x32b_x1_nowait(xb + uint32_t(cl + 32 < rb + P ? cl + 32 : cl));
+        const uint32_t u2 = tc::tmem_ld_32x32b_x1_nowait(xb + uint32_t(rb));
+        const uint32_t u3 = tc::tmem_ld_32x32b_x1_nowait(xb + uint32_t(rb + s.Pr - 1));
+        tc::tmem_wait_ld();
+        ext = RingExt{__uint_as_float(u0), __uint_as_float(u1), __uint_as_float(u2), __uint_as_float(u3)};
+        tc::tc_fence_before();
+        __syncthreads();
+        tc::tc_fence_after();
+      }
       tc::tmem_wait_ld();
       tc::reg_fence(g);
       tc::reg_fence(xr);
       tc::reg_fence(yr);
       const FOut<OP> fo = f_out<OP>(sF, cl, rl);
       if (i < s.N && c0 < s.C) {
-        if (c0 + 32 <= s.C) sb_update_regs32<P, true, OP>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, fo);
-        else sb_update_regs32<P, false, OP>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, fo);
+        if (c0 + 32 <= s.C) sb_update_regs32<P, true, OP, GEN>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, fo, ext);
+        else sb_update_regs32<P, false, OP, GEN>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, fo, ext);
       } else {
 #pragma unroll
         for (int j = 0; j < 32; ++j) fo.zero(j);
@@ -887,16 +962,16 @@ __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const
   }
 }
 
-template <int P, int OP>
+template <int P, int OP, bool GEN>
 __global__ void __launch_bounds__(kTpThreads, 1)
     k_solve_dense_tc_persistent(const __grid_constant__ TcMaps m, StateView s, TpArgs a, StepTables t) {
-  solve_dense_tc_persistent<P, false, OP>(m, s, a, t);
+  solve_dense_tc_persistent<P, false, OP, GEN>(m, s, a, t);
 }
 
 template <int P>
 __global__ void __launch_bounds__(kTpThreads, 1)
     k_solve_dense_tc_pair(const __grid_constant__ TcMaps m, StateView s, TpArgs a, StepTables t) {
-  solve_dense_tc_persistent<P, true, kOpF8>(m, s, a, t);
+  solve_dense_tc_persistent<P, true, kOpF8, false>(m, s, a, t);
 }
 
 // ---------------------------------------------------------------- split-K persistent solver
@@ -1136,8 +1211,8 @@ __global__ void __launch_bounds__(kSkThreads, 1)
       }
       const FOut<kOpF8> fo = f_out<kOpF8>(sF, cl, rl);
       if (i < s.N && c0 < s.C) {
-        if (c0 + 32 <= s.C) sb_update_regs32<P, true, kOpF8>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, fo);
-        else sb_update_regs32<P, false, kOpF8>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, fo);
+        if (c0 + 32 <= s.C) sb_update_regs32<P, true, kOpF8>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, fo, RingExt{});
+        else sb_update_regs32<P, false, kOpF8>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, fo, RingExt{});
       } else {
 #pragma unroll
         for (int j = 0; j < 32; ++j) fo.zero(j);
@@ -1421,16 +1496,33 @@ bool tc_plan_make(void **plan, const void *J, void *FT, int Kp, int Cp, float *x
 
 void tc_plan_free(void *plan) { delete static_cast<TcMaps *>(plan); }
 
-#define SBQA_TC_PS(K, ...)                                                                           \
-  {(const void *)K<1, __VA_ARGS__>, (const void *)K<2, __VA_ARGS__>, (const void *)K<4, __VA_ARGS__>, \
-   (const void *)K<8, __VA_ARGS__>, (const void *)K<16, __VA_ARGS__>, (const void *)K<32, __VA_ARGS__>}
-// [operand form][P index] of the per-step 128 x 128 kernel and the persistent solver
-static const void *const kTcFns[3][6] = {SBQA_TC_PS(k_step_dense_tc, kOpF8), SBQA_TC_PS(k_step_dense_tc, kOpBf16),
-                                         SBQA_TC_PS(k_step_dense_tc, kOpBsb)};
-static const void *const kTpFnsOp[3][6] = {SBQA_TC_PS(k_solve_dense_tc_persistent, kOpF8),
-                                           SBQA_TC_PS(k_solve_dense_tc_persistent, kOpBf16),
-                                           SBQA_TC_PS(k_solve_dense_tc_persistent, kOpBsb)};
+// [operand form][P index: log2 of the run width 1 .. 128][GEN] of the
+// per-step 128 x 128 kernel and the persistent solver.  GEN (replicas fewer
+// than the run width) exists for widths 4 .. 32; widths 1, 2 never have
+// padding and widths 64, 128 handle any replica count in one form.
+#define SBQA_TC_PS(K, OP)                                                                                       \
+  {{(const void *)K<1, OP, false>, (const void *)K<1, OP, false>},                                            \
+   {(const void *)K<2, OP, false>, (const void *)K<2, OP, false>},                                            \
+   {(const void *)K<4, OP, false>, (const void *)K<4, OP, true>},                                             \
+   {(const void *)K<8, OP, false>, (const void *)K<8, OP, true>},                                             \
+   {(const void *)K<16, OP, false>, (const void *)K<16, OP, true>},                                           \
+   {(const void *)K<32, OP, false>, (const void *)K<32, OP, true>},                                           \
+   {(const void *)K<64, OP, true>, (const void *)K<64, OP, true>},                                            \
+   {(const void *)K<128, OP, true>, (const void *)K<128, OP, true>}}
+static const void *const kTcFns[3][8][2] = {SBQA_TC_PS(k_step_dense_tc, kOpF8),
+                                            SBQA_TC_PS(k_step_dense_tc, kOpBf16),
+                                            SBQA_TC_PS(k_step_dense_tc, kOpBsb)};
+static const void *const kTpFnsOp[3][8][2] = {SBQA_TC_PS(k_solve_dense_tc_persistent, kOpF8),
+                                              SBQA_TC_PS(k_solve_dense_tc_persistent, kOpBf16),
+                                              SBQA_TC_PS(k_solve_dense_tc_persistent, kOpBsb)};
 #undef SBQA_TC_PS
+
+// index of a run width P (a power of two, 1 .. kMaxP) in the tables above; -1 otherwise
+static int p_index(int P, int max_p = 128) {
+  for (int q = 0; (1 << q) <= max_p; ++q)
+    if ((1 << q) == P) return q;
+  return -1;
+}
 static const int kTpSmemOp[3] = {TpShape<false, kOpF8>::kSmem, TpShape<false, kOpBf16>::kSmem,
                                  TpShape<false, kOpBsb>::kSmem};
 
@@ -1446,10 +1538,11 @@ static const void *const kSkFns[6] = {
 
 cudaError_t tc_set_attributes() {
   for (int op = 0; op < 3; ++op)
-    for (const void *f : kTcFns[op]) {
-      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-      if (e != cudaSuccess) return e;
-    }
+    for (int q = 0; q < 8; ++q)
+      for (const void *f : kTcFns[op][q]) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+        if (e != cudaSuccess) return e;
+      }
   const void *wide[6] = {(const void *)k_step_dense_tc_wide<1>, (const void *)k_step_dense_tc_wide<2>,
                          (const void *)k_step_dense_tc_wide<4>, (const void *)k_step_dense_tc_wide<8>,
                          (const void *)k_step_dense_tc_wide<16>, (const void *)k_step_dense_tc_wide<32>};
@@ -1458,10 +1551,11 @@ cudaError_t tc_set_attributes() {
     if (e != cudaSuccess) return e;
   }
   for (int op = 0; op < 3; ++op)
-    for (const void *f : kTpFnsOp[op]) {
-      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kTpSmemOp[op]);
-      if (e != cudaSuccess) return e;
-    }
+    for (int q = 0; q < 8; ++q)
+      for (const void *f : kTpFnsOp[op][q]) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kTpSmemOp[op]);
+        if (e != cudaSuccess) return e;
+      }
   for (const void *f : kPrFns) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, TpShape<true>::kSmem);
     if (e != cudaSuccess) return e;
@@ -1535,12 +1629,13 @@ int tc_persistent_blocks() {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   for (int op = 0; op < 3; ++op)
-    for (const void *f : kTpFnsOp[op]) {
-      int per_sm = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kTpThreads, kTpSmemOp[op]) != cudaSuccess)
-        return 0;
-      best = per_sm < best ? per_sm : best;
-    }
+    for (int q = 0; q < 8; ++q)
+      for (const void *f : kTpFnsOp[op][q]) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kTpThreads, kTpSmemOp[op]) != cudaSuccess)
+          return 0;
+        best = per_sm < best ? per_sm : best;
+      }
   return sms * best;
 }
 
@@ -1553,7 +1648,7 @@ size_t tc_persistent_flag_count(int Kp, int Cp) { return size_t(Kp / kTcBM) * (C
 cudaError_t launch_solve_dense_tc_persistent(const void *plan, const StateView &s, int Kp, int *err, const float *h,
                                              const StepTables &t, int n_begin, int n_end, uint32_t *flags,
                                              cudaStream_t st) {
-  const int idx = s.P == 1 ? 0 : s.P == 2 ? 1 : s.P == 4 ? 2 : s.P == 8 ? 3 : s.P == 16 ? 4 : s.P == 32 ? 5 : -1;
+  const int idx = p_index(s.P);
   const int op = tc_op_of(plan);
   if (idx < 0 || op < 0 || op > 2 || Kp % kTcBM != 0 || s.Cp % kTcBN != 0) return cudaErrorInvalidValue;
   const int Ct = s.Cp / kTcBN;
@@ -1564,8 +1659,8 @@ cudaError_t launch_solve_dense_tc_persistent(const void *plan, const StateView &
   StateView sv = s;
   StepTables tv = t;
   void *args[] = {&maps, &sv, &a, &tv};
-  return cudaLaunchCooperativeKernel(kTpFnsOp[op][idx], dim3(Ct, Kp / kTcBM), dim3(kTpThreads), args,
-                                     kTpSmemOp[op], st);
+  return cudaLaunchCooperativeKernel(kTpFnsOp[op][idx][s.Pr != s.P ? 1 : 0], dim3(Ct, Kp / kTcBM),
+                                     dim3(kTpThreads), args, kTpSmemOp[op], st);
 }
 
 int tc_pair_blocks() {
@@ -1611,17 +1706,20 @@ cudaError_t launch_solve_dense_tc_pair(const void *plan, const StateView &s, int
 template <int P>
 static cudaError_t launch_tc_p(const TcMaps *p, const StateView &s, const TcArgs &a, const StepTables &t, int n,
                                cudaStream_t st) {
-  const dim3 grid(s.Cp / kTcBN, a.Kp / kTcBM);
-  if (p->op == kOpBf16) {
-    k_step_dense_tc<P, kOpBf16><<<grid, kTcThreads, kTcSmem, st>>>(*p, s, a, t, n);
-  } else if (p->op == kOpBsb) {
-    k_step_dense_tc<P, kOpBsb><<<grid, kTcThreads, kTcSmem, st>>>(*p, s, a, t, n);
-  } else if (s.Cp % kTwBN == 0) {
-    k_step_dense_tc_wide<P><<<dim3(s.Cp / kTwBN, a.Kp / kTcBM), kTcThreads, kTwSmem, st>>>(*p, s, a, t, n);
-  } else {
-    k_step_dense_tc<P, kOpF8><<<grid, kTcThreads, kTcSmem, st>>>(*p, s, a, t, n);
+  if constexpr (P <= 32) {  // e4m3 with whole power-of-two runs: 128 x 256 tiles where the columns allow
+    if (p->op == kOpF8 && s.Pr == s.P && s.Cp % kTwBN == 0) {
+      k_step_dense_tc_wide<P><<<dim3(s.Cp / kTwBN, a.Kp / kTcBM), kTcThreads, kTwSmem, st>>>(*p, s, a, t, n);
+      return cudaGetLastError();
+    }
   }
-  return cudaGetLastError();
+  TcMaps maps = *p;
+  StateView sv = s;
+  TcArgs av = a;
+  StepTables tv = t;
+  int nv = n;
+  void *args[] = {&maps, &sv, &av, &tv, &nv};
+  const void *fn = kTcFns[p->op][p_index(P)][s.Pr != s.P ? 1 : 0];
+  return cudaLaunchKernel(fn, dim3(s.Cp / kTcBN, a.Kp / kTcBM), dim3(kTcThreads), args, kTcSmem, st);
 }
 
 cudaError_t launch_step_dense_tc(const void *plan, const StateView &s, int Kp, uint8_t *FT, int *err, const float *h,
@@ -1636,6 +1734,8 @@ cudaError_t launch_step_dense_tc(const void *plan, const StateView &s, int Kp, u
     case 8: return launch_tc_p<8>(p, s, a, t, n, st);
     case 16: return launch_tc_p<16>(p, s, a, t, n, st);
     case 32: return launch_tc_p<32>(p, s, a, t, n, st);
+    case 64: return launch_tc_p<64>(p, s, a, t, n, st);
+    case 128: return launch_tc_p<128>(p, s, a, t, n, st);
     default: return cudaErrorInvalidValue;
   }
 }

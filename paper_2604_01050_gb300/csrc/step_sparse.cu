@@ -337,6 +337,8 @@ cudaError_t launch_step_csr(const StateView &s, const CsrView &J, const StepTabl
     case 8: return launch_p<8>(s, J, t, n, variant, st);
     case 16: return launch_p<16>(s, J, t, n, variant, st);
     case 32: return launch_p<32>(s, J, t, n, variant, st);
+    case 64: return launch_p<64>(s, J, t, n, variant, st);
+    case 128: return launch_p<128>(s, J, t, n, variant, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -352,6 +352,14 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32_nowait(uint32_t taddr, uint32
       : "memory");
 }
 
+// One column of the warp's 32 TMEM lanes (lane t of the warp gets lane base
+// + t); complete after tmem_wait_ld().
+__device__ __forceinline__ uint32_t tmem_ld_32x32b_x1_nowait(uint32_t taddr) {
+  uint32_t r;
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x1.b32 {%0}, [%1];" : "=r"(r) : "r"(taddr) : "memory");
+  return r;
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Makes every later use of r depend on a point after the preceding

@@ -106,7 +106,7 @@ def test_engine_rejects_bad_requests(sb):
     assert e.value.status == sb.ERR_STATE  # no schedule yet
     sb.set_schedule(prob)
     with pytest.raises(sb.SBQAError) as e:
-        sb.engine_submit(eng, prob, 10, 3, 2)
+        sb.engine_submit(eng, prob, 10, 200, 2)  # more than 128 replicas per run
     assert e.value.status == sb.ERR_UNSUPPORTED
     with pytest.raises(sb.SBQAError) as e:
         sb.engine_result(eng, 0)

@@ -977,7 +977,8 @@ def test_run_argument_errors(sb):
         sb.run(prob, 10, 8, 2)
     assert e.value.status == sb.ERR_STATE
     sb.set_schedule(prob, *workloads.linear_params(3), **_params())
-    for P, R, code in ((3, 3, sb.ERR_UNSUPPORTED), (8, 4, sb.ERR_INVALID_ARG), (8, 0, sb.ERR_INVALID_ARG)):
+    for P, R, code in ((129, 3, sb.ERR_UNSUPPORTED), (0, 3, sb.ERR_INVALID_ARG), (8, 4, sb.ERR_INVALID_ARG),
+                       (8, 0, sb.ERR_INVALID_ARG)):
         with pytest.raises(sb.SBQAError) as e:
             sb.run(prob, 10, P, R)
         assert e.value.status == code
