@@ -149,7 +149,7 @@ struct Codes<8> {
 // neighbours for those columns (issued together), the coupling sums (+-1:
 // packed code sums per sign; otherwise FP32 FMAs in entry order, as
 // k_step_csr), the update and the stores.
-template <int P, int KIND, int W>
+template <int P, int KIND, int W, bool GEN>
 __device__ __forceinline__ void persist_item(const PersistArgs &a, int i, int chunk, const int32_t *col,
                                              const float *val, uint32_t degpos, const uint8_t *Fin, uint8_t *Fout,
                                              float ka, float dnext, int n, int lane) {
@@ -198,11 +198,11 @@ __device__ __forceinline__ void persist_item(const PersistArgs &a, int i, int ch
       if (e < deg) {
         const float w = val[e];
 #pragma unroll
-        for (int c = 0; c < W; ++c) G[c] = fmaf(w, fdec(f[e].w[c / 4], c % 4), G[c]);
+        acc_codes<W>(G, w, f[e].w);
       }
     }
   }
-  sb_updateW<P, W>(s, a.t, ka, dnext, n, i, c0, G, __ldg(a.h + i), xs, ys, Fout);
+  sb_updateW<P, W, GEN>(s, a.t, ka, dnext, n, i, c0, G, __ldg(a.h + i), xs, ys, Fout);
 }
 
 template <int KIND>
@@ -244,6 +244,8 @@ __global__ void __launch_bounds__(256, 4) k_solve_csr_persistent(PersistArgs a) 
   }
   __syncwarp();
   unsigned k = 0;
+  // replica counts below the run width take the general ring (one form per launch)
+  const bool gen = P > 2 && s.Pr != P;
   for (int n = a.n_begin; n < a.n_end; ++n) {
     const uint8_t *Fin = s.f_of(n);
     uint8_t *Fout = s.f_of(n + 1);
@@ -253,11 +255,19 @@ __global__ void __launch_bounds__(256, 4) k_solve_csr_persistent(PersistArgs a) 
       const float *val = nullptr;
       if constexpr (VALS) val = m.val;
       if constexpr (ROWS) {
-        for (int ch = 0; ch < chunks; ++ch)
-          persist_item<P, KIND, W>(a, gw + q * warps_total, ch, m.col, val, m.degpos, Fin, Fout, ka, dnext, n,
-                                   lane);
+        for (int ch = 0; ch < chunks; ++ch) {
+          if (gen)
+            persist_item<P, KIND, W, true>(a, gw + q * warps_total, ch, m.col, val, m.degpos, Fin, Fout, ka, dnext,
+                                           n, lane);
+          else
+            persist_item<P, KIND, W, false>(a, gw + q * warps_total, ch, m.col, val, m.degpos, Fin, Fout, ka, dnext,
+                                            n, lane);
+        }
       } else {
-        persist_item<P, KIND, W>(a, m.row, m.chunk, m.col, val, m.degpos, Fin, Fout, ka, dnext, n, lane);
+        if (gen)
+          persist_item<P, KIND, W, true>(a, m.row, m.chunk, m.col, val, m.degpos, Fin, Fout, ka, dnext, n, lane);
+        else
+          persist_item<P, KIND, W, false>(a, m.row, m.chunk, m.col, val, m.degpos, Fin, Fout, ka, dnext, n, lane);
       }
     }
     if (!grid_barrier(a.bar, ++k, a.err, n == a.skip_step && blockIdx.x == 0)) break;

@@ -78,14 +78,15 @@ __device__ __forceinline__ void batched_row_csr(const SlotDesc &d, int n, int i,
         for (int u = 0; u < 8; ++u) {
           const float w = __shfl_sync(0xffffffffu, my_w, q + u);
 #pragma unroll
-          for (int c = 0; c < 4; ++c) g[c] = fmaf(w, fdec(f4[u], c), g[c]);
+          acc_codes<4>(g, w, &f4[u]);
         }
       }
     }
 #pragma unroll
     for (int c = 0; c < 4; ++c) G[c] = g[c];
   }
-  sb_update4<P>(s, t, n, i, c4, G, hi, xv, yv, Fout);
+  if (P > 2 && d.Pr != P) sb_update4<P, true>(s, t, n, i, c4, G, hi, xv, yv, Fout);
+  else sb_update4<P, false>(s, t, n, i, c4, G, hi, xv, yv, Fout);
 }
 
 // Loads of one row of a work item, issued ahead of its use.
@@ -211,20 +212,24 @@ __device__ __forceinline__ void batched_row_ell(const SlotDesc &d, const RowFetc
       const float w = __shfl_sync(0xffffffffu, f.val, e);
       if (e < deg) {
 #pragma unroll
-        for (int c = 0; c < W; ++c) g[c] = fmaf(w, fdec(f4[e][c / 4], c % 4), g[c]);
+        acc_codes<W>(g, w, f4[e]);
       }
     }
 #pragma unroll
     for (int c = 0; c < W; ++c) G[c] = g[c];
   }
   if constexpr (W == 4) {
-    sb_update4c<P>(s, lane_consts<P>(d, f), f.row, f.c0, G, f.hi, f.x[0], f.y[0], s.f_of(f.n + 1));
+    if (P > 2 && d.Pr != P)
+      sb_update4c<P, true>(s, lane_consts<P>(d, f), f.row, f.c0, G, f.hi, f.x[0], f.y[0], s.f_of(f.n + 1));
+    else
+      sb_update4c<P, false>(s, lane_consts<P>(d, f), f.row, f.c0, G, f.hi, f.x[0], f.y[0], s.f_of(f.n + 1));
   } else {
     StepTables t;
     t.ka = d.ka; t.dl = d.dl; t.kj = d.kj; t.kc = d.kc; t.kx = d.kx; t.S = d.S; t.R = d.R;
     float xs[8] = {f.x[0].x, f.x[0].y, f.x[0].z, f.x[0].w, f.x[1].x, f.x[1].y, f.x[1].z, f.x[1].w};
     float ys[8] = {f.y[0].x, f.y[0].y, f.y[0].z, f.y[0].w, f.y[1].x, f.y[1].y, f.y[1].z, f.y[1].w};
-    sb_updateW<P, 8>(s, t, f.ka, f.dnext, f.n, f.row, f.c0, G, f.hi, xs, ys, s.f_of(f.n + 1));
+    if (P > 2 && d.Pr != P) sb_updateW<P, 8, true>(s, t, f.ka, f.dnext, f.n, f.row, f.c0, G, f.hi, xs, ys, s.f_of(f.n + 1));
+    else sb_updateW<P, 8, false>(s, t, f.ka, f.dnext, f.n, f.row, f.c0, G, f.hi, xs, ys, s.f_of(f.n + 1));
   }
 }
 

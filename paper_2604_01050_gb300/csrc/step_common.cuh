@@ -75,9 +75,9 @@ __device__ __forceinline__ void ring_nb(const float (&xs)[W], int Pr, float (&xm
 // Neighbour positions of the lane's 4 columns (c4 = first column, a multiple
 // of 4; a warp owns 128 aligned columns, so with P <= 128 every run lies
 // inside the warp).
-template <int P>
+template <int P, bool GEN = true>
 __device__ __forceinline__ void ring_neighbours(const float (&xs)[4], int Pr, float (&xm)[4], float (&xp)[4]) {
-  ring_nb<P, 4>(xs, Pr, xm, xp);
+  ring_nb<P, 4, GEN>(xs, Pr, xm, xp);
 }
 
 __device__ __forceinline__ int8_t thresh(float x, float delta) {
@@ -105,7 +105,7 @@ __device__ __forceinline__ uint32_t pack4(int8_t a, int8_t b, int8_t c, int8_t d
 // codes of the next step.  The FP32 arithmetic runs on column pairs with the
 // packed Blackwell instructions (each lane of __ffma2_rn / __fadd2_rn is an
 // ordinary round-to-nearest fma / add, so results equal the scalar form).
-template <int P>
+template <int P, bool GEN = true>
 __device__ __forceinline__ void sb_update4(const StateView &s, const StepTables &t, int n,
                                            int i, int c4, const float G[4], float hi,
                                            float4 xv, float4 yv, uint8_t *Fout) {
@@ -113,7 +113,7 @@ __device__ __forceinline__ void sb_update4(const StateView &s, const StepTables 
   float xs[4] = {xv.x, xv.y, xv.z, xv.w};
   float ys[4] = {yv.x, yv.y, yv.z, yv.w};
   float xm[4], xp[4];
-  ring_neighbours<P>(xs, s.Pr, xm, xp);  // all lanes take part (shuffles)
+  ring_neighbours<P, GEN>(xs, s.Pr, xm, xp);  // all lanes take part (shuffles)
   if (c4 >= s.C) return;                 // padding columns past R * P
   const float ka = t.ka[n];
   const float dnext = t.dl[n + 1];
@@ -203,7 +203,7 @@ struct LaneConsts {
 };
 
 // sb_update4 with the per-lane constants already loaded (same arithmetic).
-template <int P>
+template <int P, bool GEN = true>
 __device__ __forceinline__ void sb_update4c(const StateView &s, const LaneConsts<P> &L, int i, int c4,
                                             const float G[4], float hi, float4 xv, float4 yv, uint8_t *Fout) {
   const size_t off = size_t(i) * s.Cp + c4;
@@ -217,7 +217,7 @@ __device__ __forceinline__ void sb_update4c(const StateView &s, const LaneConsts
     xm[0] = xp[0] = xs[1]; xm[1] = xp[1] = xs[0];
     xm[2] = xp[2] = xs[3]; xm[3] = xp[3] = xs[2];
   } else {
-    ring_nb<P, 4>(xs, L.Pr, xm, xp);
+    ring_nb<P, 4, GEN>(xs, L.Pr, xm, xp);
   }
   if (!L.active) return;
   const float2 h2 = make_float2(hi, hi);
@@ -259,12 +259,12 @@ __device__ __forceinline__ void sb_update4c(const StateView &s, const LaneConsts
 // 8 or 16; W >= P or P divides W).  Ring neighbours inside the lane's
 // columns are registers; across lanes (P > W) they come by shuffle from the
 // neighbouring lane of the same run.  Same arithmetic as sb_update4.
-template <int P, int W>
+template <int P, int W, bool GEN = true>
 __device__ __forceinline__ void sb_updateW(const StateView &s, const StepTables &t, float ka, float dnext, int n,
                                            int i, int c0, const float (&G)[W], float hi, float (&xs)[W],
                                            float (&ys)[W], uint8_t *Fout) {
   float xm[W], xp[W];
-  ring_nb<P, W>(xs, s.Pr, xm, xp);  // all lanes take part (shuffles)
+  ring_nb<P, W, GEN>(xs, s.Pr, xm, xp);  // all lanes take part (shuffles)
   if (c0 >= s.C) return;
   const float *kjn = t.kj + size_t(n) * t.R;
   const float2 kc2 = make_float2(t.kc, t.kc), mka2 = make_float2(-ka, -ka), kx2 = make_float2(t.kx, t.kx);
@@ -330,6 +330,31 @@ __device__ __forceinline__ void sb_updateW(const StateView &s, const StepTables 
 // Value of f encoded in byte q of a packed word of f codes.
 __device__ __forceinline__ float fdec(uint32_t w, int q) {
   return float(int((w >> (8 * q)) & 0xffu) - 1);
+}
+
+// g[c] += w * f_c for the W f codes of one neighbour (W / 4 packed words),
+// two columns per packed FMA.  One byte permute puts code byte b into the low
+// mantissa bits of 2^23 (0x4B0000cc = 2^23 + code, exact), one packed add of
+// -(2^23 + 1) gives f = code - 1 in {-1, 0, 1} exactly, and each lane of
+// __ffma2_rn is the ordinary round-to-nearest fma: the sums equal
+// fmaf(w, fdec(...), g) term by term, in the same order.
+template <int W>
+__device__ __forceinline__ void acc_codes(float (&g)[W], float w, const uint32_t *cw) {
+  const float2 w2 = make_float2(w, w);
+  const float2 off = make_float2(-8388609.f, -8388609.f);
+#pragma unroll
+  for (int q = 0; q < W / 4; ++q) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t m0 = __byte_perm(cw[q], 0x4B000000u, 0x7540u | uint32_t(2 * h));
+      const uint32_t m1 = __byte_perm(cw[q], 0x4B000000u, 0x7540u | uint32_t(2 * h + 1));
+      const float2 f2 = __fadd2_rn(make_float2(__uint_as_float(m0), __uint_as_float(m1)), off);
+      const int c = 4 * q + 2 * h;
+      const float2 r = __ffma2_rn(w2, f2, make_float2(g[c], g[c + 1]));
+      g[c] = r.x;
+      g[c + 1] = r.y;
+    }
+  }
 }
 
 }  // namespace sbqa

@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256, W == 16 ? 2 : (W == 8 ? 3 : 4))
           } else {
             const float wt = __shfl_sync(0xffffffffu, my_w, q + u);  // 0 past the row end
 #pragma unroll
-            for (int c = 0; c < W; ++c) g[c] = fmaf(wt, fdec(f[u].w[c / 4], c % 4), g[c]);
+            acc_codes<W>(g, wt, f[u].w);
           }
         }
       }
@@ -145,7 +145,8 @@ __global__ void __launch_bounds__(256, W == 16 ? 2 : (W == 8 ? 3 : 4))
 #pragma unroll
       for (int c = 0; c < W; ++c) G[c] = g[c];
     }
-    sb_updateW<P, W>(s, t, ka, dnext, n, i, c0, G, hi, xs, ys, Fout);
+    if (P > 2 && s.Pr != P) sb_updateW<P, W, true>(s, t, ka, dnext, n, i, c0, G, hi, xs, ys, Fout);
+    else sb_updateW<P, W, false>(s, t, ka, dnext, n, i, c0, G, hi, xs, ys, Fout);
   }
 }
 
@@ -241,13 +242,14 @@ __global__ void __launch_bounds__(256, W == 8 ? 3 : 4) k_step_ell(StateView s, C
         const float wt = __shfl_sync(0xffffffffu, my_w, e);
         if (e < deg) {  // the CSR kernel's entries, in its order
 #pragma unroll
-          for (int c = 0; c < W; ++c) g[c] = fmaf(wt, fdec(f[e].w[c / 4], c % 4), g[c]);
+          acc_codes<W>(g, wt, f[e].w);
         }
       }
 #pragma unroll
       for (int c = 0; c < W; ++c) G[c] = g[c];
     }
-    sb_updateW<P, W>(s, t, ka, dnext, n, i, c0, G, __ldg(J.h + i), xs, ys, Fout);
+    if (P > 2 && s.Pr != P) sb_updateW<P, W, true>(s, t, ka, dnext, n, i, c0, G, __ldg(J.h + i), xs, ys, Fout);
+    else sb_updateW<P, W, false>(s, t, ka, dnext, n, i, c0, G, __ldg(J.h + i), xs, ys, Fout);
   }
 }
 
