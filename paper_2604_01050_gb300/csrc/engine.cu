@@ -4,9 +4,14 @@
 // arrival order.  At every chunk boundary the engine admits queued requests
 // while a slot and room in its device arena are free (strict FIFO), builds
 // their schedule tables and initial state, and then advances every active
-// request by up to `chunk` steps: all CSR requests together in one batched
-// launch per step (k_step_batched over a work list of 8-row x 128-column
-// items), dense requests with their own step kernels in the same stream.
+// request by up to `chunk` steps: all CSR requests together in one
+// cooperative launch for the whole chunk (k_solve_batched over a work list
+// of 8-row x 128- or 256-column items, a bounded grid barrier between steps;
+// each slot keeps its own step index on the device, so the launch is
+// captured once in a CUDA graph and replayed every chunk), dense requests
+// with the persistent tensor-core solver (one launch per chunk) when their
+// tiles fill a good part of the device, else per-step kernels on their
+// slot's stream.
 // A request whose last step falls inside the chunk is read out (energies of
 // all replicas, best per run), its result copied to the host and its slot
 // and arena space released.  Each element is computed exactly as by
@@ -21,6 +26,7 @@
 #include <vector>
 
 #include "../../include/sbqa.h"
+#include "grid_sync.cuh"
 #include "internal.h"
 #include "problem.h"
 
@@ -91,6 +97,8 @@ struct Request {
   double *ef, *part_f, *best_e;
   int32_t *best_k, *best_step, *have;
   int *err;
+  uint32_t *tc_flags;  // per-tile step counters of the persistent dense solver (dense tensor-core requests)
+  bool on_side = false;  // this chunk runs on the slot's side stream
   StepTables tables{};
   void *tc_plan = nullptr;
   // results (host)
@@ -134,6 +142,18 @@ struct sbqa_engine {
   int64_t batched_updates = 0;   // updates of CSR requests advanced by the batched kernel
   double batched_ms = 0.0;       // device time of the batched launches
   cudaEvent_t batched_t0 = nullptr, batched_t1 = nullptr;
+  // the CSR requests' chunk: one cooperative launch (k_solve_batched), captured
+  // once in a CUDA graph and replayed every chunk while its grid size and
+  // work-list buffer stay the same (the slots' step indices live on the device)
+  unsigned *d_bar = nullptr;  // grid barrier counters
+  int *d_err = nullptr;       // error flag of the batched launch
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t csr_graph = nullptr;
+  int csr_graph_grid = 0;
+  const void *csr_graph_items = nullptr;
+  bool csr_graph_refused = false;  // capture of the cooperative launch was refused: launch it directly
+  int tc_blocks = -1;              // co-resident CTAs of the persistent dense solver
+  int64_t graph_launches = 0;
   // dense requests run their chunk on a stream of their slot (created on first
   // use), so small dense problems share the GPU instead of queueing
   std::vector<cudaStream_t> side;
@@ -142,6 +162,10 @@ struct sbqa_engine {
 
   ~sbqa_engine() {
     cudaDeviceSynchronize();
+    if (csr_graph) cudaGraphExecDestroy(csr_graph);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (d_bar) cudaFree(d_bar);
+    if (d_err) cudaFree(d_err);
     for (cudaStream_t x : side)
       if (x) cudaStreamDestroy(x);
     for (cudaEvent_t x : side_done)
@@ -180,7 +204,7 @@ size_t request_bytes(const sbqa_problem *p, int S, int P, int R, bool tc, int Kp
   b += align_up(nblk * Cp * 8);            // partial sums
   b += align_up(size_t(R) * 8) * 2 + align_up(size_t(R) * 4) * 3 + align_up(size_t(R) * N);
   b += align_up(4);                        // error flag
-  if (tc) b += align_up(tc_ft_bytes(Kp, Cp, p->tc_op));
+  if (tc) b += align_up(tc_ft_bytes(Kp, Cp, p->tc_op)) + align_up(tc_persistent_flag_count(Kp, Cp) * 4);
   return b;
 }
 
@@ -213,6 +237,7 @@ void carve(Request &r, uint8_t *base, bool tc, int Kp) {
   r.best_spins = reinterpret_cast<int8_t *>(take(size_t(r.R) * N));
   r.err = reinterpret_cast<int *>(take(4));
   r.FT = tc ? take(tc_ft_bytes(Kp, r.Cp, r.prob->tc_op)) : nullptr;
+  r.tc_flags = tc ? reinterpret_cast<uint32_t *>(take(tc_persistent_flag_count(Kp, r.Cp) * 4)) : nullptr;
 }
 
 int admit(sbqa_engine *e, Request &r, int slot, cudaStream_t st) {
@@ -282,6 +307,43 @@ int readout(sbqa_engine *e, Request &r, cudaStream_t st) {
   return SBQA_OK;
 }
 
+// Dense tensor-core requests with at least this many 128 x 128 tiles (most
+// of the device's 152 SMs) run a chunk on the persistent solver; smaller
+// ones take per-step kernels on their slot's stream, where they overlap with
+// other work (a persistent solver of a few dozen tiles would run alone on
+// the engine stream, which serialises the cooperative launches).
+constexpr int kPersistMinTiles = 112;
+
+// The captured graph of the CSR chunk launch for `grid` blocks (recaptured
+// when the grid size or the work-list buffer changes).  A capture that the
+// runtime refuses leaves e->csr_graph null, and the chunk is launched directly.
+int csr_chunk_graph(sbqa_engine *e, int grid) {
+  if (e->csr_graph_refused) return SBQA_OK;
+  if (e->csr_graph && e->csr_graph_grid == grid && e->csr_graph_items == e->d_items) return SBQA_OK;
+  if (e->csr_graph) {
+    cudaGraphExecDestroy(e->csr_graph);
+    e->csr_graph = nullptr;
+  }
+  if (!e->cap_stream) ENG_CUDA(cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking));
+  ENG_CUDA(cudaStreamBeginCapture(e->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t err = launch_solve_batched(e->d_slots, e->max_slots, e->d_items, e->d_n_items, grid, 0, e->chunk,
+                                         e->d_bar, e->d_err, e->cap_stream);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t err2 = cudaStreamEndCapture(e->cap_stream, &graph);
+  cudaGraphExec_t exec = nullptr;
+  if (err == cudaSuccess && err2 == cudaSuccess) err = cudaGraphInstantiate(&exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (err != cudaSuccess || err2 != cudaSuccess || !exec) {
+    cudaGetLastError();  // the refusal is not an error of the engine: launch directly from now on
+    e->csr_graph_refused = true;
+    return SBQA_OK;
+  }
+  e->csr_graph = exec;
+  e->csr_graph_grid = grid;
+  e->csr_graph_items = e->d_items;
+  return SBQA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -305,7 +367,9 @@ int sbqa_engine_create(int64_t arena_bytes, int32_t max_slots, int32_t chunk_ste
   e->arena.bytes = size_t(arena_bytes);
   e->arena.free_blocks[0] = size_t(arena_bytes);
   if (cudaMalloc(&e->d_slots, sizeof(SlotDesc) * max_slots) != cudaSuccess ||
-      cudaMalloc(&e->d_n_items, sizeof(int)) != cudaSuccess)
+      cudaMalloc(&e->d_n_items, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&e->d_bar, sizeof(unsigned) * grid_barrier_words()) != cudaSuccess ||
+      cudaMalloc(&e->d_err, sizeof(int)) != cudaSuccess || cudaMemset(e->d_err, 0, sizeof(int)) != cudaSuccess)
     return fail_free(SBQA_ERR_OOM, "engine tables");
   cudaDeviceGetAttribute(&e->sms, cudaDevAttrMultiProcessorCount, e->device);
   *out = e;
@@ -392,37 +456,65 @@ int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done, int32_t *don
   }
   for (int id : dense_active) {
     Request &r = e->reqs[id];
+    const int steps_now = std::min(e->chunk, r.S - r.n0);
+    const sbqa_problem *p = r.prob;
+    // a tensor-core request whose tiles fill a good part of the device runs its chunk on the
+    // persistent solver (one launch); cooperative launches all go to `st`, one after another,
+    // so no two of them ever wait for each other's blocks
+    const int tiles = p->use_tc ? (p->Kp / 128) * (r.Cp / 128) : 0;
+    if (p->use_tc && e->tc_blocks < 0) {
+      ENG_CUDA(tc_set_attributes());
+      e->tc_blocks = tc_persistent_blocks();
+    }
+    if (p->use_tc && tiles >= kPersistMinTiles && tc_persistent_eligible(p->Kp, r.Cp, e->tc_blocks)) {
+      const cudaError_t err = launch_solve_dense_tc_persistent(r.tc_plan, r.state_view(), p->Kp, r.err, p->d_h.p,
+                                                               r.tables, r.n0, r.n0 + steps_now, r.tc_flags, st);
+      if (err != cudaSuccess) return set_error(SBQA_ERR_CUDA, std::string("engine dense chunk: ") + cudaGetErrorString(err));
+      ++e->kernels_launched;
+      continue;
+    }
     cudaStream_t &ds = e->side[r.slot];
     cudaEvent_t &dv = e->side_done[r.slot];
     if (!ds) ENG_CUDA(cudaStreamCreateWithFlags(&ds, cudaStreamNonBlocking));
     if (!dv) ENG_CUDA(cudaEventCreateWithFlags(&dv, cudaEventDisableTiming));
     ENG_CUDA(cudaStreamWaitEvent(ds, e->chunk_start, 0));
-    for (int j = 0; j < e->chunk && r.n0 + j < r.S; ++j) {
+    for (int j = 0; j < steps_now; ++j) {
       const int n = r.n0 + j;
       cudaError_t err;
-      if (r.prob->use_tc)
-        err = launch_step_dense_tc(r.tc_plan, r.state_view(), r.prob->Kp, r.FT, r.err, r.prob->d_h.p, r.tables, n, ds);
+      if (p->use_tc)
+        err = launch_step_dense_tc(r.tc_plan, r.state_view(), p->Kp, r.FT, r.err, p->d_h.p, r.tables, n, ds);
       else
-        err = launch_step_dense(r.state_view(), problem_dense_view(r.prob), r.tables, n, ds);
+        err = launch_step_dense(r.state_view(), problem_dense_view(p), r.tables, n, ds);
       if (err != cudaSuccess) return set_error(SBQA_ERR_CUDA, std::string("engine step: ") + cudaGetErrorString(err));
       ++e->kernels_launched;
     }
     ENG_CUDA(cudaEventRecord(dv, ds));
+    r.on_side = true;
   }
-  const int grid = std::max(1, std::min(n_items, e->sms * batched_blocks_per_sm()));
   if (n_items) {
     if (!e->batched_t0) {
       ENG_CUDA(cudaEventCreate(&e->batched_t0));
       ENG_CUDA(cudaEventCreate(&e->batched_t1));
     }
+    // every CSR request's chunk in one cooperative launch, replayed from a captured graph
+    const int grid = std::max(1, std::min(n_items, batched_persistent_blocks()));
+    if ((rc = csr_chunk_graph(e, grid)) != SBQA_OK) return rc;
     ENG_CUDA(cudaEventRecord(e->batched_t0, st));
-  }
-  for (int j = 0; j < e->chunk && n_items; ++j) {
-    ENG_CUDA(launch_step_batched(e->d_slots, e->max_slots, e->d_items, e->d_n_items, grid, j, st));
+    if (e->csr_graph) {
+      ENG_CUDA(cudaGraphLaunch(e->csr_graph, st));
+      ++e->graph_launches;
+    } else {
+      ENG_CUDA(launch_solve_batched(e->d_slots, e->max_slots, e->d_items, e->d_n_items, grid, 0, e->chunk, e->d_bar,
+                                    e->d_err, st));
+    }
     ++e->kernels_launched;
+    ENG_CUDA(cudaEventRecord(e->batched_t1, st));
   }
-  if (n_items) ENG_CUDA(cudaEventRecord(e->batched_t1, st));
-  for (int id : dense_active) ENG_CUDA(cudaStreamWaitEvent(st, e->side_done[e->reqs[id].slot], 0));
+  for (int id : dense_active) {
+    Request &r = e->reqs[id];
+    if (r.on_side) ENG_CUDA(cudaStreamWaitEvent(st, e->side_done[r.slot], 0));
+    r.on_side = false;
+  }
   // 4. retire the requests that finished inside the chunk
   std::vector<int> finished;
   for (int q = 0; q < e->max_slots; ++q) {
@@ -438,10 +530,21 @@ int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done, int32_t *don
     }
   }
   ENG_CUDA(cudaStreamSynchronize(st));
+  int csr_err = 0;  // the batched launch's grid barrier gave up: every CSR request of the chunk fails
   if (n_items) {
     float ms = 0.f;
     ENG_CUDA(cudaEventElapsedTime(&ms, e->batched_t0, e->batched_t1));
     e->batched_ms += ms;
+    ENG_CUDA(cudaMemcpy(&csr_err, e->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (csr_err) {
+      ENG_CUDA(cudaMemset(e->d_err, 0, sizeof(int)));
+      for (int q = 0; q < e->max_slots; ++q) {
+        if (e->slot_req[q] < 0) continue;
+        Request &r = e->reqs[e->slot_req[q]];
+        if (r.prob->dense || std::find(finished.begin(), finished.end(), r.id) != finished.end()) continue;
+        finished.push_back(r.id);  // retired below as failed
+      }
+    }
   }
   // Every finished request leaves its slot and arena space, also one whose
   // device wait gave up: it is retired as FAILED and the others still
@@ -454,6 +557,7 @@ int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done, int32_t *don
     int err = 0;
     ENG_CUDA(cudaMemcpy(&err, r.err, sizeof(int), cudaMemcpyDeviceToHost));
     if (id == fail_id) err = 1;  // test hook: the request's device error word as a failed wait leaves it
+    if (csr_err && !r.prob->dense) err = 1;
     if (r.tc_plan) {
       tc_plan_free(r.tc_plan);
       r.tc_plan = nullptr;

@@ -231,6 +231,13 @@ cudaError_t launch_f_to_ft(const StateView &s, int which, uint8_t *FT, int Kp, i
 // j = step index inside the current chunk, n_items in device memory.
 cudaError_t launch_step_batched(const SlotDesc *slots, int n_slots, const WorkItem *items, const int *n_items,
                                 int grid, int j, cudaStream_t st);
+// All steps j0 .. j1 - 1 of a chunk in one cooperative launch of `grid` blocks
+// (at most batched_persistent_blocks(), the co-resident count); bar holds
+// grid_barrier_words() counters (zeroed here); a barrier that gives up
+// records code 4 in *err.
+int batched_persistent_blocks();
+cudaError_t launch_solve_batched(const SlotDesc *slots, int n_slots, const WorkItem *items, const int *n_items,
+                                 int grid, int j0, int j1, unsigned *bar, int *err, cudaStream_t st);
 int batched_blocks_per_sm();  // resident blocks of the batched step kernel per SM (one wave = this x SMs)
 
 int energy_row_blocks(int N);

@@ -14,6 +14,7 @@
 // per element is the one of k_step_csr (same gathers, same sums in the same
 // order, same update), so a request gives bit-identical results alone and in
 // any mix.
+#include "grid_sync.cuh"
 #include "step_common.cuh"
 
 namespace sbqa {
@@ -44,7 +45,7 @@ __device__ __forceinline__ void batched_row_csr(const SlotDesc &d, int n, int i,
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int j = __shfl_sync(0xffffffffu, my_col, q + u);
-          f4[u] = (q + u < cnt) ? __ldg(reinterpret_cast<const uint32_t *>(Fc + size_t(j) * d.Cp)) : 0u;
+          f4[u] = (q + u < cnt) ? __ldcg(reinterpret_cast<const uint32_t *>(Fc + size_t(j) * d.Cp)) : 0u;
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -72,12 +73,11 @@ __device__ __forceinline__ void batched_row_csr(const SlotDesc &d, int n, int i,
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int j = __shfl_sync(0xffffffffu, my_col, q + u);
-          f4[u] = (q + u < cnt) ? __ldg(reinterpret_cast<const uint32_t *>(Fc + size_t(j) * d.Cp)) : kFZero4;
+          f4[u] = (q + u < cnt) ? __ldcg(reinterpret_cast<const uint32_t *>(Fc + size_t(j) * d.Cp)) : kFZero4;
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const float w = __shfl_sync(0xffffffffu, my_w, q + u);
-#pragma unroll
           acc_codes<4>(g, w, &f4[u]);
         }
       }
@@ -175,11 +175,11 @@ __device__ __forceinline__ void batched_row_ell(const SlotDesc &d, const RowFetc
     const int j = __shfl_sync(0xffffffffu, f.col, e);
     if (e < deg) {
       if constexpr (W == 8) {
-        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(Fc + size_t(j) * d.Cp));
+        const uint2 v = __ldcg(reinterpret_cast<const uint2 *>(Fc + size_t(j) * d.Cp));
         f4[e][0] = v.x;
         f4[e][1] = v.y;
       } else {
-        f4[e][0] = __ldg(reinterpret_cast<const uint32_t *>(Fc + size_t(j) * d.Cp));
+        f4[e][0] = __ldcg(reinterpret_cast<const uint32_t *>(Fc + size_t(j) * d.Cp));
       }
     } else {
 #pragma unroll
@@ -211,7 +211,6 @@ __device__ __forceinline__ void batched_row_ell(const SlotDesc &d, const RowFetc
     for (int e = 0; e < kEllSlots; ++e) {
       const float w = __shfl_sync(0xffffffffu, f.val, e);
       if (e < deg) {
-#pragma unroll
         acc_codes<W>(g, w, f4[e]);
       }
     }
@@ -242,19 +241,21 @@ __device__ __forceinline__ void batched_row(const SlotDesc &d, const RowFetch &f
 
 constexpr int kBatchSmemSlots = 64;  // slot descriptors kept in shared memory (more: read from global)
 
-__global__ void __launch_bounds__(256, 2) k_step_batched(const SlotDesc *slots, int n_slots, const WorkItem *items,
-                                                      const int *n_items, int j) {
-  __shared__ SlotDesc s_slots[kBatchSmemSlots];
-  const SlotDesc *D = slots;
-  if (n_slots <= kBatchSmemSlots) {
-    const int words = n_slots * int(sizeof(SlotDesc) / 4);
-    for (int q = threadIdx.x; q < words; q += blockDim.x)
-      reinterpret_cast<uint32_t *>(s_slots)[q] = reinterpret_cast<const uint32_t *>(slots)[q];
-    __syncthreads();
-    D = s_slots;
-  }
+// The slot descriptors into shared memory (when they fit).
+__device__ __forceinline__ const SlotDesc *stage_slots(SlotDesc *s_slots, const SlotDesc *slots, int n_slots) {
+  if (n_slots > kBatchSmemSlots) return slots;
+  const int words = n_slots * int(sizeof(SlotDesc) / 4);
+  for (int q = threadIdx.x; q < words; q += blockDim.x)
+    reinterpret_cast<uint32_t *>(s_slots)[q] = reinterpret_cast<const uint32_t *>(slots)[q];
+  __syncthreads();
+  return s_slots;
+}
+
+// Step j of the chunk for every active slot: the warps of the grid walk the
+// rows of the work items (a warp per row; the next row's loads go out before
+// this row's gathers).  A warp with no row returns from here only.
+__device__ __forceinline__ void batched_pass(const SlotDesc *D, const WorkItem *items, int total, int j) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int total = *n_items * 8;  // rows of the work items
   const int stride = gridDim.x * 8;
   int u = blockIdx.x * 8 + warp;
   if (u >= total) return;  // whole warp
@@ -285,6 +286,31 @@ __global__ void __launch_bounds__(256, 2) k_step_batched(const SlotDesc *slots, 
   }
 }
 
+__global__ void __launch_bounds__(256, 2) k_step_batched(const SlotDesc *slots, int n_slots, const WorkItem *items,
+                                                      const int *n_items, int j) {
+  __shared__ SlotDesc s_slots[kBatchSmemSlots];
+  const SlotDesc *D = stage_slots(s_slots, slots, n_slots);
+  batched_pass(D, items, *n_items * 8, j);
+}
+
+// Steps j0 .. j1 - 1 of the chunk for every active slot in one cooperative
+// launch (the grid exactly co-resident): one pass per step, the bounded grid
+// barrier between steps (each slot keeps its own step index n0 + j, and a
+// slot past its last step has no rows).  The f codes other blocks wrote in
+// the step before are read through L2.  A barrier that gives up records
+// error code 4 in *err and every block stops stepping.
+__global__ void __launch_bounds__(256, 2) k_solve_batched(const SlotDesc *slots, int n_slots, const WorkItem *items,
+                                                       const int *n_items, int j0, int j1, unsigned *bar, int *err) {
+  __shared__ SlotDesc s_slots[kBatchSmemSlots];
+  const SlotDesc *D = stage_slots(s_slots, slots, n_slots);
+  const int total = *n_items * 8;
+  unsigned k = 0;
+  for (int j = j0; j < j1; ++j) {
+    batched_pass(D, items, total, j);
+    if (j + 1 < j1 && !grid_barrier(bar, ++k, err)) break;
+  }
+}
+
 int batched_blocks_per_sm() {
   static int per_sm = 0;
   if (per_sm == 0 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_batched, 256, 0) != cudaSuccess ||
@@ -297,6 +323,27 @@ cudaError_t launch_step_batched(const SlotDesc *slots, int n_slots, const WorkIt
                                 int grid, int j, cudaStream_t st) {
   k_step_batched<<<grid, 256, 0, st>>>(slots, n_slots, items, n_items, j);
   return cudaGetLastError();
+}
+
+int batched_persistent_blocks() {
+  static int blocks = -1;
+  if (blocks < 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_batched, 256, 0) != cudaSuccess) per_sm = 0;
+    blocks = sms * per_sm;
+  }
+  return blocks;
+}
+
+cudaError_t launch_solve_batched(const SlotDesc *slots, int n_slots, const WorkItem *items, const int *n_items,
+                                 int grid, int j0, int j1, unsigned *bar, int *err, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(bar, 0, grid_barrier_words() * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  void *args[] = {(void *)&slots, (void *)&n_slots, (void *)&items, (void *)&n_items, (void *)&j0, (void *)&j1,
+                  (void *)&bar, (void *)&err};
+  return cudaLaunchCooperativeKernel((const void *)k_solve_batched, dim3(grid), dim3(256), args, 0, st);
 }
 
 }  // namespace sbqa

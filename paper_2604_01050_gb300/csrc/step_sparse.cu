@@ -129,7 +129,6 @@ __global__ void __launch_bounds__(256, W == 16 ? 2 : (W == 8 ? 3 : 4))
             }
           } else {
             const float wt = __shfl_sync(0xffffffffu, my_w, q + u);  // 0 past the row end
-#pragma unroll
             acc_codes<W>(g, wt, f[u].w);
           }
         }
@@ -241,7 +240,6 @@ __global__ void __launch_bounds__(256, W == 8 ? 3 : 4) k_step_ell(StateView s, C
       for (int e = 0; e < kEllSlots; ++e) {
         const float wt = __shfl_sync(0xffffffffu, my_w, e);
         if (e < deg) {  // the CSR kernel's entries, in its order
-#pragma unroll
           acc_codes<W>(g, wt, f[e].w);
         }
       }
