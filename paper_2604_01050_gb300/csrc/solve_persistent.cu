@@ -96,13 +96,16 @@ struct Codes<8> {
 // neighbours for those columns (issued together), the coupling sums (+-1:
 // packed code sums per sign; otherwise FP32 FMAs in entry order, as
 // k_step_csr), the update and the stores.
-template <int P, int KIND, int W, bool GEN>
+// LPI lanes own one item of LPI * W columns: the whole warp (32), or half of
+// it (16: the warp works on two items at once, lanes 16-31 on the second;
+// act = false leaves a half without an item idle but in the shuffles).
+template <int P, int KIND, int W, bool GEN, int LPI = 32>
 __device__ __forceinline__ void persist_item(const PersistArgs &a, int i, int chunk, const int32_t *col,
                                              const float *val, uint32_t degpos, const uint8_t *Fin, uint8_t *Fout,
-                                             float ka, float dnext, int n, int lane) {
+                                             float ka, float dnext, int n, int lane, bool act = true) {
   const StateView &s = a.s;
-  const int deg = int(degpos & 0xffu), npos = int(degpos >> 8);
-  const int c0 = chunk * 32 * W + lane * W;
+  const int deg = act ? int(degpos & 0xffu) : 0, npos = int(degpos >> 8);
+  const int c0 = chunk * LPI * W + (lane % LPI) * W;
   const size_t off = size_t(i) * s.Cp + c0;
   float xs[W], ys[W];
 #pragma unroll
@@ -148,7 +151,8 @@ __device__ __forceinline__ void persist_item(const PersistArgs &a, int i, int ch
       }
     }
   }
-  sb_updateW<P, W, GEN>(s, a.t, ka, dnext, n, i, c0, G, __ldg(a.h + i), xs, ys, Fout);
+  // an idle half takes part in the ring shuffles only (a column past C stores nothing)
+  sb_updateW<P, W, GEN>(s, a.t, ka, dnext, n, i, act ? c0 : s.C, G, __ldg(a.h + i), xs, ys, Fout);
 }
 
 template <int KIND>
@@ -158,7 +162,10 @@ __device__ __forceinline__ float entry_value(const PersistArgs &a, int e) {
 }
 
 // ROWS = false: warp items (row, chunk) cached; true: whole rows cached.
-template <int P, bool ROWS, int KIND, int W>
+// LPI = 16 (items mode, W = 8): a half warp per item of 128 columns, two
+// items per warp at a time -- twice the items in flight per warp and half the
+// per-item instructions of W = 4 on a whole warp, same arithmetic per column.
+template <int P, bool ROWS, int KIND, int W, int LPI = 32>
 __global__ void __launch_bounds__(256, 4) k_solve_csr_persistent(PersistArgs a) {
   constexpr bool VALS = KIND != VAL_PM1;
   using C = Cache<ROWS, VALS>;
@@ -166,7 +173,7 @@ __global__ void __launch_bounds__(256, 4) k_solve_csr_persistent(PersistArgs a) 
   extern __shared__ int32_t s_cache[];  // [8 warps][C::kPerWarp] entries
   const StateView &s = a.s;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int chunks = s.Cp / (32 * W);
+  const int chunks = s.Cp / (LPI * W);
   const int warps_total = gridDim.x * 8;
   const int gw = blockIdx.x * 8 + warp;
   Entry *mine = reinterpret_cast<Entry *>(s_cache) + warp * C::kPerWarp;
@@ -209,28 +216,46 @@ __global__ void __launch_bounds__(256, 4) k_solve_csr_persistent(PersistArgs a) 
             persist_item<P, KIND, W, false>(a, gw + q * warps_total, ch, m.col, val, m.degpos, Fin, Fout, ka, dnext,
                                             n, lane);
         }
-      } else {
+      } else if constexpr (LPI == 32) {
         if (gen)
           persist_item<P, KIND, W, true>(a, m.row, m.chunk, m.col, val, m.degpos, Fin, Fout, ka, dnext, n, lane);
         else
           persist_item<P, KIND, W, false>(a, m.row, m.chunk, m.col, val, m.degpos, Fin, Fout, ka, dnext, n, lane);
+      } else {
+        // lanes 16-31 take the next entry (idle past the warp's last one)
+        const int qq = q + (lane >> 4);
+        const bool act = qq < my_count;
+        const Entry &mh = mine[act ? qq : q];
+        const float *valh = nullptr;
+        if constexpr (VALS) valh = mh.val;
+        if (gen)
+          persist_item<P, KIND, W, true, LPI>(a, mh.row, mh.chunk, mh.col, valh, mh.degpos, Fin, Fout, ka, dnext, n,
+                                              lane, act);
+        else
+          persist_item<P, KIND, W, false, LPI>(a, mh.row, mh.chunk, mh.col, valh, mh.degpos, Fin, Fout, ka, dnext,
+                                               n, lane, act);
+        ++q;  // two entries per pass
       }
     }
     if (!grid_barrier(a.bar, ++k, a.err, n == a.skip_step && blockIdx.x == 0)) break;
   }
 }
 
+// Items mode with 128-column items (W = 4 on a whole warp) runs as W = 8 on
+// half warps (LPI = 16); rows mode and 256-column items keep LPI = 32.
 template <bool ROWS, int KIND, int W>
 static const void *persistent_fn_p(int P) {
+  constexpr bool HALF = !ROWS && W == 4;
+  constexpr int WK = HALF ? 8 : W, LPI = HALF ? 16 : 32;
   switch (P) {
-    case 1: return (const void *)k_solve_csr_persistent<1, ROWS, KIND, W>;
-    case 2: return (const void *)k_solve_csr_persistent<2, ROWS, KIND, W>;
-    case 4: return (const void *)k_solve_csr_persistent<4, ROWS, KIND, W>;
-    case 8: return (const void *)k_solve_csr_persistent<8, ROWS, KIND, W>;
-    case 16: return (const void *)k_solve_csr_persistent<16, ROWS, KIND, W>;
-    case 32: return (const void *)k_solve_csr_persistent<32, ROWS, KIND, W>;
-    case 64: return (const void *)k_solve_csr_persistent<64, ROWS, KIND, W>;
-    case 128: return (const void *)k_solve_csr_persistent<128, ROWS, KIND, W>;
+    case 1: return (const void *)k_solve_csr_persistent<1, ROWS, KIND, WK, LPI>;
+    case 2: return (const void *)k_solve_csr_persistent<2, ROWS, KIND, WK, LPI>;
+    case 4: return (const void *)k_solve_csr_persistent<4, ROWS, KIND, WK, LPI>;
+    case 8: return (const void *)k_solve_csr_persistent<8, ROWS, KIND, WK, LPI>;
+    case 16: return (const void *)k_solve_csr_persistent<16, ROWS, KIND, WK, LPI>;
+    case 32: return (const void *)k_solve_csr_persistent<32, ROWS, KIND, WK, LPI>;
+    case 64: return (const void *)k_solve_csr_persistent<64, ROWS, KIND, WK, LPI>;
+    case 128: return (const void *)k_solve_csr_persistent<128, ROWS, KIND, WK, LPI>;
     default: return nullptr;
   }
 }
