@@ -155,29 +155,48 @@ __global__ void __launch_bounds__(256, W == 16 ? 2 : (W == 8 ? 3 : 4))
 // the (row, chunk) items; while a warp gathers and updates one item it has
 // already issued the next item's slots and x, y, so each item waits for one
 // round of gathers only.  Entries are summed in the CSR kernel's order.
-template <int P, int KIND, int W>
-__global__ void __launch_bounds__(256, W == 8 ? 3 : 4) k_step_ell(StateView s, CsrView J, StepTables t, int n) {
+// LPI = 16: a half warp per item of 16 W columns, the warp on two items at a
+// time (lanes 16-31 on the odd one): twice the items in flight per warp and
+// half the per-item instructions; the same sums and update per column.
+// (The half-warp form loads each pass's rows when it starts it, without the
+// one-pass-ahead prefetch: two items per warp are in flight already, and four
+// blocks per SM fit its registers.)
+template <int P, int KIND, int W, int LPI = 32>
+__global__ void __launch_bounds__(256, (W == 8 && LPI == 32) ? 3 : 4)
+    k_step_ell(StateView s, CsrView J, StepTables t, int n) {
+  constexpr int IPW = 32 / LPI;  // items per warp at a time
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sub = lane / LPI, sl = lane % LPI;  // the lane's item of the pass, its place in the item
   const float ka = __ldg(t.ka + n), dnext = __ldg(t.dl + n + 1);
   const uint8_t *Fin = s.f_of(n);
   uint8_t *Fout = s.f_of(n + 1);
-  const int chunks = s.Cp / (32 * W);
+  const int chunks = s.Cp / (LPI * W);
   const long long n_items = (long long)s.N * chunks;
+  const long long n_passes = (n_items + IPW - 1) / IPW;
   const long long stride = (long long)gridDim.x * 8;
-  long long item = (long long)blockIdx.x * 8 + warp;
-  if (item >= n_items) return;  // whole warp
-  int ni = int(item / chunks), nch = int(item - (long long)ni * chunks);
+  long long pass = (long long)blockIdx.x * 8 + warp;
+  if (pass >= n_passes) return;  // whole warp
+  // the item of this lane's group in a pass; a group past the last item repeats the pass's first
+  // item for its loads and stores nothing
+  auto item_of = [&](long long ps, bool &act) {
+    const long long it = ps * IPW + sub;
+    act = it < n_items;
+    return act ? it : ps * IPW;
+  };
+  bool nact;
+  long long nit = item_of(pass, nact);
+  int ni = int(nit / chunks), nch = int(nit - (long long)ni * chunks);
   int ncol = 0;
   float nval = 0.f;
   int2 nmeta;
   float nxs[W], nys[W];
   auto fetch = [&](int row, int ch) {
-    if (lane < kEllSlots) {
-      ncol = __ldg(J.ell_col + size_t(row) * kEllSlots + lane);
-      if constexpr (KIND != VAL_PM1) nval = __ldg(J.ell_val + size_t(row) * kEllSlots + lane);
+    if (sl < kEllSlots) {
+      ncol = __ldg(J.ell_col + size_t(row) * kEllSlots + sl);
+      if constexpr (KIND != VAL_PM1) nval = __ldg(J.ell_val + size_t(row) * kEllSlots + sl);
     }
     nmeta = __ldg(reinterpret_cast<const int2 *>(J.ell_meta) + row);
-    const size_t off = size_t(row) * s.Cp + ch * 32 * W + lane * W;
+    const size_t off = size_t(row) * s.Cp + ch * LPI * W + sl * W;
 #pragma unroll
     for (int q = 0; q < W / 4; ++q) {
       const float4 a = *reinterpret_cast<const float4 *>(s.x + off + 4 * q);
@@ -186,30 +205,39 @@ __global__ void __launch_bounds__(256, W == 8 ? 3 : 4) k_step_ell(StateView s, C
       nys[4 * q] = b.x; nys[4 * q + 1] = b.y; nys[4 * q + 2] = b.z; nys[4 * q + 3] = b.w;
     }
   };
-  fetch(ni, nch);
-  for (; item < n_items; item += stride) {
+  if constexpr (LPI == 32) fetch(ni, nch);
+  for (; pass < n_passes; pass += stride) {
+    if constexpr (LPI != 32) {
+      nit = item_of(pass, nact);
+      ni = int(nit / chunks);
+      nch = int(nit - (long long)ni * chunks);
+      fetch(ni, nch);
+    }
     const int i = ni, ch = nch;
+    const bool act = nact;
     const int my_col = ncol;
     const float my_w = nval;
-    const int deg = nmeta.x, npos = nmeta.y;
+    const int deg = act ? nmeta.x : 0, npos = nmeta.y;
     float xs[W], ys[W];
 #pragma unroll
     for (int q = 0; q < W; ++q) {
       xs[q] = nxs[q];
       ys[q] = nys[q];
     }
-    const long long next = item + stride;
-    if (next < n_items) {  // warp-uniform
-      ni = int(next / chunks);
-      nch = int(next - (long long)ni * chunks);
+    const long long next = pass + stride;
+    if (LPI == 32 && next < n_passes) {  // warp-uniform
+      nit = item_of(next, nact);
+      ni = int(nit / chunks);
+      nch = int(nit - (long long)ni * chunks);
       fetch(ni, nch);
     }
-    const int c0 = ch * 32 * W + lane * W;
+    const int c0 = ch * LPI * W + sl * W;
     const uint8_t *Fc = Fin + c0;
+    const int src0 = sub * LPI;  // lane holding slot 0 of this group's row
     FVec<W> f[kEllSlots];
 #pragma unroll
     for (int e = 0; e < kEllSlots; ++e) {
-      const int j = __shfl_sync(0xffffffffu, my_col, e);
+      const int j = __shfl_sync(0xffffffffu, my_col, src0 + e);
       if (e < deg) f[e].load(Fc + size_t(j) * s.Cp);
       else f[e].zero(KIND == VAL_PM1 ? 0u : kFZero4);
     }
@@ -238,7 +266,7 @@ __global__ void __launch_bounds__(256, W == 8 ? 3 : 4) k_step_ell(StateView s, C
       for (int c = 0; c < W; ++c) g[c] = 0.f;
 #pragma unroll
       for (int e = 0; e < kEllSlots; ++e) {
-        const float wt = __shfl_sync(0xffffffffu, my_w, e);
+        const float wt = __shfl_sync(0xffffffffu, my_w, src0 + e);
         if (e < deg) {  // the CSR kernel's entries, in its order
           acc_codes<W>(g, wt, f[e].w);
         }
@@ -246,8 +274,10 @@ __global__ void __launch_bounds__(256, W == 8 ? 3 : 4) k_step_ell(StateView s, C
 #pragma unroll
       for (int c = 0; c < W; ++c) G[c] = g[c];
     }
-    if (P > 2 && s.Pr != P) sb_updateW<P, W, true>(s, t, ka, dnext, n, i, c0, G, __ldg(J.h + i), xs, ys, Fout);
-    else sb_updateW<P, W, false>(s, t, ka, dnext, n, i, c0, G, __ldg(J.h + i), xs, ys, Fout);
+    // an idle group takes part in the ring shuffles only (a column past C stores nothing)
+    const int cs = act ? c0 : s.C;
+    if (P > 2 && s.Pr != P) sb_updateW<P, W, true>(s, t, ka, dnext, n, i, cs, G, __ldg(J.h + i), xs, ys, Fout);
+    else sb_updateW<P, W, false>(s, t, ka, dnext, n, i, cs, G, __ldg(J.h + i), xs, ys, Fout);
   }
 }
 
@@ -260,12 +290,15 @@ static unsigned wave_blocks(const void *fn) {
   return unsigned(sms * per_sm);
 }
 
+// W = 4 (128-column items) runs as W = 8 on half warps, two items per warp.
 template <int P, int KIND, int W>
 static cudaError_t launch_ell(const StateView &s, const CsrView &J, const StepTables &t, int n, cudaStream_t st) {
-  static const unsigned wave = wave_blocks((const void *)k_step_ell<P, KIND, W>);
-  const long long items = (long long)s.N * (s.Cp / (32 * W));
-  const unsigned blocks = unsigned(std::min<long long>(wave, (items + 7) / 8));
-  k_step_ell<P, KIND, W><<<blocks, 256, 0, st>>>(s, J, t, n);
+  constexpr bool HALF = W == 4;
+  constexpr int WK = HALF ? 8 : W, LPI = HALF ? 16 : 32;
+  static const unsigned wave = wave_blocks((const void *)k_step_ell<P, KIND, WK, LPI>);
+  const long long passes = (long long)s.N * (s.Cp / (32 * W)) / (HALF ? 2 : 1) + 1;
+  const unsigned blocks = unsigned(std::min<long long>(wave, (passes + 7) / 8));
+  k_step_ell<P, KIND, WK, LPI><<<blocks, 256, 0, st>>>(s, J, t, n);
   return cudaGetLastError();
 }
 
