@@ -272,10 +272,16 @@ def run_serving(args, stream=None):
     serving.run_stream(reqs[:6], None, stream=stream, arena_bytes=arena)  # warm-up (autotune, first launches)
     closed = serving.run_stream(reqs, None, stream=stream, arena_bytes=arena)
     capacity = len(reqs) / closed["makespan_s"]
+    # the same closed loop with every small dense request on its own per-step launches
+    unbatched = serving.run_stream(reqs, None, stream=stream, arena_bytes=arena, dense_batching=False)
     loads = {}
     for f in (0.5, 0.8):
         out = serving.run_stream(reqs, f * capacity, stream=stream, seed=int(10 * f), arena_bytes=arena)
         loads["%.1fx" % f] = serving.summary(out)
+    # the same stream at fixed request rates, comparable across builds whose capacity differs
+    for rate in (30.0, 48.0):
+        out = serving.run_stream(reqs, rate, stream=stream, seed=int(rate), arena_bytes=arena)
+        loads["%.0f/s" % rate] = serving.summary(out)
     head = loads["0.8x"]
     # the batched CSR kernel alone: a closed loop of the lattice requests (no dense work beside it)
     lat_reqs = [r for r in reqs if r["inst"]["kind"] == "lattice"]
@@ -305,7 +311,12 @@ def run_serving(args, stream=None):
                                    "N uniform in 64..8192, P in {8,16,32}, R=16, 2000 steps; "
                                    "continuous batching engine, chunk 50 steps",
                        "requests": len(reqs), "arena_gb": args.arena_gb, "capacity_req_per_s": capacity,
-                       "closed_loop_updates_per_s": closed["updates"] / closed["makespan_s"]},
+                       "closed_loop_updates_per_s": closed["updates"] / closed["makespan_s"],
+                       "closed_loop_launches": closed["kernels_launched"],
+                       "dense_batched": {"launches": closed["dense_batched_launches"],
+                                         "request_chunks": closed["dense_batched_chunks"]},
+                       "without_dense_batching": {"capacity_req_per_s": len(reqs) / unbatched["makespan_s"],
+                                                  "launches": unbatched["kernels_launched"]}},
             "p50_s": head["p50_s"], "loads": loads, "gpu_launches": head["kernels_launched"],
             "roofline": roof, "cpu_baseline": cpu}
     for inst in pool:

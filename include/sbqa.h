@@ -322,6 +322,17 @@ int sbqa_engine_create(int64_t arena_bytes, int32_t max_slots,
                        int32_t chunk_steps, sbqa_engine **out);
 void sbqa_engine_destroy(sbqa_engine *e);
 
+/* How the engine runs the chunks of small dense requests on the tensor cores
+ * (fewer 128 x 128 tiles than one wave of the persistent solver holds):
+ *   1 (default)  together, one cooperative launch of the batched persistent
+ *                solver per group of equal operand form and run width, on
+ *                the engine's stream before the CSR requests' chunk
+ *   0            each on a stream of its own slot, one per-step kernel launch
+ *                per step, beside the CSR requests' chunk
+ * Results are the same either way.  Takes effect at the next
+ * sbqa_engine_step.  Errors: INVALID_ARG. */
+int sbqa_engine_set_dense_batching(sbqa_engine *e, int32_t on);
+
 /* Queues a request; *id receives its number (0, 1, ... in submit order).
  * steps >= 1; P and R as for sbqa_run.  Errors: STATE (no schedule),
  * INVALID_ARG, UNSUPPORTED, OOM (request larger than the arena). */
@@ -358,6 +369,10 @@ typedef struct {
     double batched_ms;        /* device time of those batched launches (CUDA
                                  events around each chunk's launches; dense
                                  requests may run beside them) */
+    int64_t dense_batched_launches; /* cooperative launches that advanced the
+                                       chunks of several small dense
+                                       tensor-core requests together */
+    int64_t dense_batched_chunks;   /* request chunks advanced by those launches */
 } sbqa_engine_stats_t;
 
 int sbqa_engine_stats(const sbqa_engine *e, sbqa_engine_stats_t *s);

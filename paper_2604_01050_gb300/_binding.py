@@ -41,7 +41,7 @@ EXPORTS = (
     "sbqa_get_best", "sbqa_get_energies", "sbqa_get_state", "sbqa_set_state",
     "sbqa_strerror", "sbqa_last_error", "sbqa_version", "sbqa_energies_csr_noalloc",
     "sbqa_engine_create", "sbqa_engine_destroy", "sbqa_engine_submit", "sbqa_engine_step",
-    "sbqa_engine_result", "sbqa_engine_stats",
+    "sbqa_engine_result", "sbqa_engine_stats", "sbqa_engine_set_dense_batching",
 )
 
 
@@ -63,7 +63,8 @@ class EngineStats(ctypes.Structure):
     _fields_ = [("queued", ctypes.c_int32), ("active", ctypes.c_int32), ("finished", ctypes.c_int32),
                 ("arena_bytes", ctypes.c_int64), ("arena_used", ctypes.c_int64),
                 ("updates_issued", ctypes.c_int64), ("kernels_launched", ctypes.c_int64),
-                ("batched_updates", ctypes.c_int64), ("batched_ms", ctypes.c_double)]
+                ("batched_updates", ctypes.c_int64), ("batched_ms", ctypes.c_double),
+                ("dense_batched_launches", ctypes.c_int64), ("dense_batched_chunks", ctypes.c_int64)]
 
 
 class Params(ctypes.Structure):
@@ -110,6 +111,7 @@ def _load():
         "sbqa_engine_step": (ctypes.c_int, [vp, vp, P(i32), P(i32), i32]),
         "sbqa_engine_result": (ctypes.c_int, [vp, i32, P(ctypes.c_int8), P(dbl), P(i64), P(i32)]),
         "sbqa_engine_stats": (ctypes.c_int, [vp, P(EngineStats)]),
+        "sbqa_engine_set_dense_batching": (ctypes.c_int, [vp, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -329,6 +331,10 @@ def engine_create(arena_bytes, max_slots, chunk_steps) -> Engine:
     _check(lib.sbqa_engine_create(int(arena_bytes), int(max_slots), int(chunk_steps), ctypes.byref(out)),
            "engine_create")
     return Engine(out.value)
+
+
+def engine_set_dense_batching(eng: Engine, on: bool):
+    _check(lib.sbqa_engine_set_dense_batching(eng.handle, int(on)), "engine_set_dense_batching")
 
 
 def engine_submit(eng: Engine, pb: Problem, steps, P, R, seed=0) -> int:

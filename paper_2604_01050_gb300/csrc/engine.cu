@@ -23,6 +23,7 @@
 #include <deque>
 #include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/sbqa.h"
@@ -154,6 +155,11 @@ struct sbqa_engine {
   bool csr_graph_refused = false;  // capture of the cooperative launch was refused: launch it directly
   int tc_blocks = -1;              // co-resident CTAs of the persistent dense solver
   int64_t graph_launches = 0;
+  // small dense tensor-core requests: their chunks in one cooperative launch
+  // per group of equal operand form and run width (solve_dense_tc_batched.cu)
+  TcBatch *tcb = nullptr;
+  bool dense_batching = true;
+  int64_t dense_batched_launches = 0, dense_batched_chunks = 0;
   // dense requests run their chunk on a stream of their slot (created on first
   // use), so small dense problems share the GPU instead of queueing
   std::vector<cudaStream_t> side;
@@ -171,6 +177,7 @@ struct sbqa_engine {
     for (cudaEvent_t x : side_done)
       if (x) cudaEventDestroy(x);
     if (chunk_start) cudaEventDestroy(chunk_start);
+    tc_batch_destroy(tcb);
     if (batched_t0) cudaEventDestroy(batched_t0);
     if (batched_t1) cudaEventDestroy(batched_t1);
     for (auto &r : reqs)
@@ -348,6 +355,12 @@ int csr_chunk_graph(sbqa_engine *e, int grid) {
 
 extern "C" {
 
+int sbqa_engine_set_dense_batching(sbqa_engine *e, int32_t on) {
+  if (!e || (on != 0 && on != 1)) return set_error(SBQA_ERR_INVALID_ARG, "need an engine and on = 0 or 1");
+  e->dense_batching = on != 0;
+  return SBQA_OK;
+}
+
 int sbqa_engine_create(int64_t arena_bytes, int32_t max_slots, int32_t chunk_steps, sbqa_engine **out) {
   if (!out) return set_error(SBQA_ERR_INVALID_ARG, "out is null");
   *out = nullptr;
@@ -397,6 +410,41 @@ int sbqa_engine_submit(sbqa_engine *e, sbqa_problem *p, int32_t steps, int32_t P
   e->queue.push_back(e->reqs.back().id);
   *id = e->reqs.back().id;
   return SBQA_OK;
+}
+
+// The chunks of the small dense tensor-core requests: grouped by operand form,
+// run width and ring form (one kernel instance each), every group in as few
+// cooperative launches as the co-resident CTAs allow, all on st one after
+// another (no two cooperative grids ever wait for each other's blocks).
+static int dense_batches(sbqa_engine *e, std::vector<int> &ids, cudaStream_t st) {
+  if (!e->tcb) ENG_CUDA(tc_batch_create(&e->tcb, std::min(e->max_slots, e->tc_blocks), e->tc_blocks));
+  auto key = [&](int id) {
+    const Request &r = e->reqs[id];
+    return std::make_tuple(r.prob->tc_op, run_width(r.P), r.P != run_width(r.P));
+  };
+  std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) { return key(a) < key(b); });
+  tc_batch_clear(e->tcb);
+  auto flush = [&]() -> int {
+    if (tc_batch_size(e->tcb) == 0) return SBQA_OK;
+    const cudaError_t err = tc_batch_launch(e->tcb, st);
+    if (err != cudaSuccess) return set_error(SBQA_ERR_CUDA, std::string("engine dense batch: ") + cudaGetErrorString(err));
+    ++e->kernels_launched;
+    ++e->dense_batched_launches;
+    e->dense_batched_chunks += tc_batch_size(e->tcb);
+    tc_batch_clear(e->tcb);
+    return SBQA_OK;
+  };
+  int rc;
+  for (int id : ids) {
+    Request &r = e->reqs[id];
+    const sbqa_problem *p = r.prob;
+    const StateView sv = r.state_view();
+    if (!tc_batch_fits(e->tcb, r.tc_plan, sv, p->Kp) && (rc = flush()) != SBQA_OK) return rc;
+    const int steps_now = std::min(e->chunk, r.S - r.n0);
+    const cudaError_t err = tc_batch_add(e->tcb, r.tc_plan, sv, p->Kp, r.err, p->d_h.p, r.tables, r.n0, r.n0 + steps_now);
+    if (err != cudaSuccess) return set_error(SBQA_ERR_CUDA, std::string("engine dense batch: ") + cudaGetErrorString(err));
+  }
+  return flush();
 }
 
 int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done, int32_t *done_ids, int32_t cap) {
@@ -454,6 +502,7 @@ int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done, int32_t *don
       e->side_done.assign(e->max_slots, nullptr);
     }
   }
+  std::vector<int> batch_ids;
   for (int id : dense_active) {
     Request &r = e->reqs[id];
     const int steps_now = std::min(e->chunk, r.S - r.n0);
@@ -464,13 +513,18 @@ int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done, int32_t *don
     const int tiles = p->use_tc ? (p->Kp / 128) * (r.Cp / 128) : 0;
     if (p->use_tc && e->tc_blocks < 0) {
       ENG_CUDA(tc_set_attributes());
-      e->tc_blocks = tc_persistent_blocks();
+      ENG_CUDA(tc_batch_set_attributes());
+      e->tc_blocks = std::min(tc_persistent_blocks(), tc_batch_blocks());
     }
     if (p->use_tc && tiles >= kPersistMinTiles && tc_persistent_eligible(p->Kp, r.Cp, e->tc_blocks)) {
       const cudaError_t err = launch_solve_dense_tc_persistent(r.tc_plan, r.state_view(), p->Kp, r.err, p->d_h.p,
                                                                r.tables, r.n0, r.n0 + steps_now, r.tc_flags, st);
       if (err != cudaSuccess) return set_error(SBQA_ERR_CUDA, std::string("engine dense chunk: ") + cudaGetErrorString(err));
       ++e->kernels_launched;
+      continue;
+    }
+    if (e->dense_batching && p->use_tc && tc_persistent_eligible(p->Kp, r.Cp, e->tc_blocks)) {
+      batch_ids.push_back(id);  // with the other small tensor-core requests, below
       continue;
     }
     cudaStream_t &ds = e->side[r.slot];
@@ -491,6 +545,7 @@ int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done, int32_t *don
     ENG_CUDA(cudaEventRecord(dv, ds));
     r.on_side = true;
   }
+  if (!batch_ids.empty() && (rc = dense_batches(e, batch_ids, st)) != SBQA_OK) return rc;
   if (n_items) {
     if (!e->batched_t0) {
       ENG_CUDA(cudaEventCreate(&e->batched_t0));
@@ -602,6 +657,8 @@ int sbqa_engine_stats(const sbqa_engine *e, sbqa_engine_stats_t *s) {
   s->kernels_launched = e->kernels_launched;
   s->batched_updates = e->batched_updates;
   s->batched_ms = e->batched_ms;
+  s->dense_batched_launches = e->dense_batched_launches;
+  s->dense_batched_chunks = e->dense_batched_chunks;
   return SBQA_OK;
 }
 

@@ -134,6 +134,26 @@ cudaError_t launch_solve_dense_tc_persistent(const void *plan, const StateView &
                                              const StepTables &t, int n_begin, int n_end, uint32_t *flags,
                                              cudaStream_t st);
 
+// Several dense problems' chunks in one cooperative launch of the persistent
+// tensor-core solver (solve_dense_tc_batched.cu): one CTA per 128 x 128 tile
+// of each problem, tiles of one problem consecutive; the problems of a batch
+// share the operand form, the run width P and the ring form.  A batch holds
+// at most cap_reqs problems and cap_tiles tiles (at most tc_batch_blocks()
+// for one launch).  tc_batch_add returns cudaErrorInvalidValue for a problem
+// that does not fit (tc_batch_fits) or has no persistent form.
+struct TcBatch;
+cudaError_t tc_batch_create(TcBatch **out, int cap_reqs, int cap_tiles);
+void tc_batch_destroy(TcBatch *b);
+void tc_batch_clear(TcBatch *b);
+int tc_batch_tiles(const TcBatch *b);
+int tc_batch_size(const TcBatch *b);
+bool tc_batch_fits(const TcBatch *b, const void *plan, const StateView &s, int Kp);
+cudaError_t tc_batch_add(TcBatch *b, const void *plan, const StateView &s, int Kp, int *err, const float *h,
+                         const StepTables &t, int n_begin, int n_end);
+cudaError_t tc_batch_launch(TcBatch *b, cudaStream_t st);
+cudaError_t tc_batch_set_attributes();
+int tc_batch_blocks();
+
 // The persistent dense solver on 2-CTA clusters sharing M=256 MMAs
 // (tcgen05 cta_group::2; step_dense_tc.cu): padded N a multiple of 256,
 // row-tile pairs x column tiles co-resident as clusters (tc_pair_blocks()).

@@ -26,237 +26,10 @@
 // BF16 operands (tcgen05.mma kind::f16, K = 64 elements per 128-byte operand
 // row); the ballistic form f(x) = x carries x as two BF16 terms (hi + lo) in
 // two B operands that share each A tile.
-#include <cuda.h>
-#include <cuda_bf16.h>
-#include <cudaTypedefs.h>
-
-#include "step_common.cuh"
-#include "tc_common.cuh"
+#include "dense_tc_common.cuh"
+#include "dense_tc_persistent.cuh"
 
 namespace sbqa {
-
-constexpr int kTcBM = 128, kTcBN = 128, kTcBK = 128, kTcStages = 3;
-constexpr int kTcThreads = 512;          // 16 warps: all run the epilogue, one 32-column box each
-constexpr int kTcTile = kTcBM * kTcBK;   // bytes of one operand stage (e4m3)
-constexpr int kTcBox = kTcBM * 128;      // one 128-row x 32-float state box (16 KB)
-constexpr int kTcStateTile = 4 * kTcBox; // x or y tile, 128 rows x 128 columns (64 KB)
-constexpr int kTcSmem = 2 * kTcStages * kTcTile + 2 * kTcStateTile + 1024 + 128;
-constexpr uint8_t kE4M3One = 0x38, kE4M3MinusOne = 0xB8;
-
-// Operand forms of the product G = J . F on the tensor cores (TcMaps::op).
-//   kOpF8    integer J (|J_ij| <= 16) and the f codes of Eq. 8 in e4m3: exact
-//   kOpBf16  J rounded to bfloat16 (exact for integers |J_ij| <= 256) and the
-//            f codes of Eq. 8 in bfloat16: exact products, FP32 sums
-//   kOpBsb   the ballistic form f(x) = x: J in bfloat16, and x as the two
-//            bfloat16 terms hi = bf16(x), lo = bf16(x - hi) (x to 2^-16
-//            relative), two B operands sharing each A tile
-constexpr int kOpF8 = kTcOpF8, kOpBf16 = kTcOpBf16, kOpBsb = kTcOpBsb;
-
-template <int OP>
-struct TcOp {
-  static constexpr bool kBf = OP != kOpF8;
-  static constexpr int kKE = kBf ? 64 : 128;       // K elements per 128-byte operand row (one k-block)
-  static constexpr int kEB = kBf ? 2 : 1;          // bytes per operand element
-  static constexpr int kNB = OP == kOpBsb ? 2 : 1;  // B operands per k-block
-  static constexpr int kFTile = kTcBM * kTcBN * kEB;  // one 128 x 128 f tile (bytes)
-  __host__ __device__ static constexpr uint32_t idesc(int M, int N) {
-    return kBf ? tc::idesc_bf16(M, N) : tc::idesc_f8_e4m3(M, N);
-  }
-  __device__ __forceinline__ static void mma(uint32_t d, uint64_t ad, uint64_t bd, uint32_t id, uint32_t acc) {
-    if constexpr (kBf) tc::mma_bf16(d, ad, bd, id, acc);
-    else tc::mma_f8(d, ad, bd, id, acc);
-  }
-};
-
-struct TcArgs {
-  int Kp;
-  uint8_t *FT;  // [2][Cp][Kp]
-  int *err;     // device error flag (0 = ok)
-  const float *h;
-};
-
-struct TcMaps {
-  CUtensorMap A, B;  // J8 and FT operand tiles (128 x 128 bytes, 128B swizzle)
-  CUtensorMap B2;    // FT operand tiles of 256 columns (256 x 128 bytes, 128B swizzle)
-  CUtensorMap B64;   // FT operand half tiles of a CTA pair (64 x 128 bytes, 128B swizzle)
-  CUtensorMap X, Y;  // x, y state boxes (128 rows x 32 floats, 128B swizzle)
-  CUtensorMap Fst;   // FT tile store (128 columns x 128 spins, no swizzle)
-  CUtensorMap Bl, Fstl;  // kOpBsb: the lo terms of x (load and store), as B and Fst
-  int op;                // operand form (kOpF8, kOpBf16, kOpBsb)
-};
-
-__device__ __forceinline__ uint8_t f_to_e4m3(int8_t f) {
-  return f == 0 ? uint8_t(0) : (f > 0 ? kE4M3One : kE4M3MinusOne);
-}
-
-// e4m3 code of f(x) for the threshold delta >= 0 (Eq. 8: 0 when |x| <= delta).
-__device__ __forceinline__ uint8_t thresh_e4m3(float x, float delta) {
-  return x > delta ? kE4M3One : (x < -delta ? kE4M3MinusOne : uint8_t(0));
-}
-
-// Writer of f(x_next) into the transposed f tile of one spin row: base points
-// at column 0 of the thread's 32-column chunk; column j is base[j * 128]
-// elements on.  kOpF8 / kOpBf16: the code of Eq. 8 (0 when |x| <= Delta);
-// kOpBsb: f(x) = x as hi = bf16(x) and lo = bf16(x - hi) (exact in FP32),
-// the lo tile following the hi tile.
-template <int OP>
-struct FOut {
-  uint8_t *base;
-  __device__ __forceinline__ void put(int j, float x, float delta) const {
-    if constexpr (OP == kOpF8) {
-      base[j * kTcBM] = thresh_e4m3(x, delta);
-    } else if constexpr (OP == kOpBf16) {
-      reinterpret_cast<uint16_t *>(base)[j * kTcBM] =
-          x > delta ? uint16_t(0x3F80) : (x < -delta ? uint16_t(0xBF80) : uint16_t(0));
-    } else {
-      const __nv_bfloat16 h = __float2bfloat16_rn(x);
-      const __nv_bfloat16 l = __float2bfloat16_rn(x - __bfloat162float(h));
-      reinterpret_cast<uint16_t *>(base)[j * kTcBM] = __bfloat16_as_ushort(h);
-      reinterpret_cast<uint16_t *>(base + TcOp<OP>::kFTile)[j * kTcBM] = __bfloat16_as_ushort(l);
-    }
-  }
-  __device__ __forceinline__ void zero(int j) const {
-    if constexpr (OP == kOpF8) {
-      base[j * kTcBM] = 0;
-    } else {
-      reinterpret_cast<uint16_t *>(base)[j * kTcBM] = 0;
-      if constexpr (OP == kOpBsb) reinterpret_cast<uint16_t *>(base + TcOp<OP>::kFTile)[j * kTcBM] = 0;
-    }
-  }
-};
-
-template <int OP>
-__device__ __forceinline__ FOut<OP> f_out(uint8_t *sF, int cl, int rl) {
-  return FOut<OP>{sF + (cl * kTcBM + rl) * TcOp<OP>::kEB};
-}
-
-// Address of the float4 (16-byte chunk u, 0..7) of row r inside a 128B-swizzled
-// box of 128-byte rows: chunks are permuted by XOR with r mod 8.
-__device__ __forceinline__ float4 *box_chunk(uint8_t *box, int r, int u) {
-  return reinterpret_cast<float4 *>(box + r * 128 + ((u ^ (r & 7)) << 4));
-}
-
-// J_perp of the runs of a 32-column chunk.  For P >= 4 (at most 8 runs) the
-// values are read before the accumulator is ready, off the critical path; for
-// P < 4 (16 or 32 runs, which would not fit beside the tile in registers) they
-// are read inside the update.
-template <int P>
-struct KjChunk {
-  static constexpr int kRuns = 32 / (P < 32 ? P : 32);
-  static constexpr bool kEarly = P >= 4;
-  float v[kEarly ? kRuns : 1];
-  const float *kjn;
-  __device__ __forceinline__ void load(const StateView &s, const float *kj_step, int c0) {
-    kjn = kj_step;
-    if constexpr (kEarly) {
-#pragma unroll
-      for (int q = 0; q < kRuns; ++q) v[q] = (c0 + q * P < s.C) ? __ldg(kjn + c0 / P + q) : 0.f;
-    }
-  }
-  __device__ __forceinline__ float get(int c0, int q) const {
-    if constexpr (kEarly) return v[q];
-    else return __ldg(kjn + c0 / P + q);
-  }
-};
-
-// Positions of one spin row just outside a 32-column chunk of a run that
-// spans several chunks (P = 64, 128): the columns left and right of the
-// chunk and the run's replicas 0 and Pr - 1, read before any chunk of the
-// tile is written back.
-struct RingExt {
-  float left, right, first, last;
-};
-
-// Ring neighbours (k modulo Pr) of a row's 32 consecutive columns c0.. held
-// by one thread: runs inside the chunk for P <= 32 (GEN = false: Pr = P,
-// the form of power-of-two replica counts), else from the chunk and the four
-// outside values of e.
-template <int P, bool GEN>
-__device__ __forceinline__ void ring32(const float (&xs)[32], int Pr, int c0, const RingExt &e, float (&xm)[32],
-                                       float (&xp)[32]) {
-  if constexpr (P <= 32) {
-    ring_nb<P, 32, GEN>(xs, Pr, xm, xp);
-  } else {
-    const int part = (c0 % P) / 32;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const int k = part * 32 + j;
-      xm[j] = j == 0 ? (part == 0 ? e.last : e.left) : xs[j - 1];
-      xp[j] = k == Pr - 1 ? e.first : (j == 31 ? e.right : xs[j + 1]);
-    }
-  }
-}
-
-// Column c (inside the 128-column tile) of row r in the swizzled state boxes.
-__device__ __forceinline__ float box_at(uint8_t *boxes, int r, int c) {
-  const uint8_t *box = boxes + (c >> 5) * kTcBox;
-  const int e = c & 31;
-  return reinterpret_cast<const float *>(box + r * 128 + (((e >> 2) ^ (r & 7)) << 4))[e & 3];
-}
-
-// The outside values of ring32 for the chunk at tile column cl of row r.
-template <int P>
-__device__ __forceinline__ RingExt ring_ext_boxes(uint8_t *xboxes, int r, int cl, int Pr) {
-  RingExt e{0.f, 0.f, 0.f, 0.f};
-  if constexpr (P > 32) {
-    const int rb = cl - cl % P;  // first column of the run inside the tile
-    e.left = cl > rb ? box_at(xboxes, r, cl - 1) : 0.f;
-    e.right = cl + 32 < rb + P ? box_at(xboxes, r, cl + 32) : 0.f;
-    e.first = box_at(xboxes, r, rb);
-    e.last = box_at(xboxes, r, rb + Pr - 1);
-  }
-  return e;
-}
-
-// Update of one spin row for 32 aligned columns c0..c0+31 (whole runs,
-// because P divides 32); x and y are read from and written back to one row of
-// the swizzled shared-memory state boxes; the e4m3 code of f(x_next) of
-// column j goes to sFcol[j * 128] of the transposed f tile.  Same arithmetic,
-// in the same order, as sb_update4.  FULL: all 32 columns are below C (no
-// per-column test).
-template <int P, bool FULL, int OP, bool GEN = false>
-__device__ __forceinline__ void sb_update_row32(const StateView &s, const StepTables &t, float ka, float dnext,
-                                                const KjChunk<P> &kj, int c0, const uint32_t (&g)[32], float hi,
-                                                uint8_t *xbox, uint8_t *ybox, int r, const FOut<OP> &fo,
-                                                const RingExt &ext) {
-  constexpr int PR = P < 32 ? P : 32;
-  float xs[32], ys[32];
-#pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    const float4 a = *box_chunk(xbox, r, u), b = *box_chunk(ybox, r, u);
-    xs[4 * u] = a.x; xs[4 * u + 1] = a.y; xs[4 * u + 2] = a.z; xs[4 * u + 3] = a.w;
-    ys[4 * u] = b.x; ys[4 * u + 1] = b.y; ys[4 * u + 2] = b.z; ys[4 * u + 3] = b.w;
-  }
-  float xms[32], xps[32];
-  ring32<P, GEN>(xs, s.Pr, c0, ext, xms, xps);
-  float xo[32], yo[32];
-#pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    const float xm = xms[j], xp = xps[j];
-    xo[j] = xs[j];
-    yo[j] = ys[j];
-    if (!FULL && c0 + j >= s.C) {
-      fo.zero(j);
-      continue;
-    }
-    float yn = fmaf(t.kc, __uint_as_float(g[j]) + hi, ys[j]);
-    yn = fmaf(-ka, xs[j], yn);
-    yn = fmaf(kj.get(c0, j / PR), xm + xp, yn);
-    float xn = fmaf(t.kx, yn, xs[j]);
-    if (fabsf(xn) > 1.f) {
-      xn = copysignf(1.f, xn);
-      yn = 0.f;
-    }
-    xo[j] = xn;
-    yo[j] = yn;
-    fo.put(j, xn, dnext);
-  }
-#pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    *box_chunk(xbox, r, u) = make_float4(xo[4 * u], xo[4 * u + 1], xo[4 * u + 2], xo[4 * u + 3]);
-    *box_chunk(ybox, r, u) = make_float4(yo[4 * u], yo[4 * u + 1], yo[4 * u + 2], yo[4 * u + 3]);
-  }
-}
 
 template <int P, int OP, bool GEN>
 __global__ void __launch_bounds__(kTcThreads, 1)
@@ -562,416 +335,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   }
 }
 
-// ---------------------------------------------------------------- persistent solver
-// All steps of a stretch in one cooperative launch.  Each CTA owns one 128 x
-// 128 tile (spin rows x replica columns) for the whole stretch and keeps its x
-// and y in tensor memory next to the accumulator (TMEM columns 0-127: G,
-// 128-255: x, 256-383: y), so shared memory holds six operand stages and a
-// step moves only J and f through the memory system.  A step of tile (mt, ct)
-// needs f_n of the 128 spins of every row tile kb for its columns, which CTA
-// (kb, ct) wrote at the end of its previous step; instead of a grid barrier
-// every CTA publishes a per-tile step counter (release, after its f tile's
-// TMA store has completed) and the producer warp polls the counters of its
-// column group (acquire, then a proxy fence before the TMA loads of those
-// tiles), issuing k-blocks in order as their tiles become ready.  The J tiles
-// of the next step's first stages are loaded while the epilogue runs.  A wait
-// that gives up (2 s, or at once when another CTA has already failed)
-// records an error; every CTA then stops at its next step boundary.
-//
-// Paired form (PAIR): the CTAs of row tiles 2p and 2p+1 (same column tile)
-// form a 2-CTA cluster that shares one M=256 N=128 MMA per K slice
-// (tcgen05 cta_group::2, issued by the even CTA): each CTA stages its own 128
-// J rows and 64 of the 128 fT rows of the column tile, and each keeps the
-// accumulator rows, x and y of its own 128 spins in its own TMEM.  Per CTA the
-// operands of an MMA are then 24 KB per k-block instead of 32 KB, which is
-// what lets the K loop run at the full MMA rate where 128 x 128 tiles fed by
-// TMA run at half of it.  The even CTA's full barrier collects the bytes of
-// both CTAs' loads; MMA completion is multicast to both CTAs' empty and done
-// barriers; a cluster barrier closes every step (so the next step's MMAs do
-// not overwrite an accumulator the odd CTA still reads) and carries the
-// abort decision, so that both CTAs stop at the same step.
-constexpr int kTpThreads = 512;  // 16 warps: warp w updates TMEM lanes 32 (w % 4).. and columns 32 (w / 4)..
-constexpr uint32_t kTmemX = 128, kTmemY = 256, kTmemCols = 512;
-constexpr uint64_t kFlagTimeoutNs = 2000000000ull;
-
-template <bool PAIR, int OP = kOpF8>
-struct TpShape {
-  static constexpr int kNB = TcOp<OP>::kNB;
-  static constexpr int kStages = PAIR ? 8 : (kNB == 2 ? 3 : 6);
-  static constexpr int kTileB = PAIR ? 64 * kTcBK : kTcTile;  // fT rows staged by this CTA: 64 of the pair's 128, or 128
-  static constexpr int kStageBytes = kTcTile + kNB * kTileB;
-  static constexpr uint32_t kExpect = PAIR ? 2 * kStageBytes : kStageBytes;  // bytes completing on one full barrier
-  static constexpr int kFBytes = kNB * TcOp<OP>::kFTile;                 // f tile(s) of the epilogue
-  static constexpr int kSmem = kStages * kStageBytes + kFBytes + 1024 + 256;
-};
-static_assert(TpShape<false>::kSmem <= 227 * 1024 && TpShape<true>::kSmem <= 227 * 1024 &&
-                  TpShape<false, kOpBf16>::kSmem <= 227 * 1024 && TpShape<false, kOpBsb>::kSmem <= 227 * 1024,
-              "persistent tile exceeds the shared memory of one CTA");
-
-struct TpArgs {
-  int Kp, Ct, n_begin, n_end;
-  int *err;
-  const float *h;
-  uint32_t *flags;  // [Kp / 128][Ct] steps completed in this launch, zeroed by the host
-};
-
-// One run-aligned chunk of 32 columns of spin row i, in registers (bit
-// patterns of FP32 x, y and the accumulated G).  Same arithmetic, in the same
-// order, as sb_update_row32: all momenta first (they read the old positions of
-// the ring neighbours), then positions, wall and f, whose e4m3 code goes to
-// column j of the transposed f tile (sFcol[j * 128]).  FULL: all 32 columns
-// are below C.
-template <int P, bool FULL, int OP, bool GEN = false>
-__device__ __forceinline__ void sb_update_regs32(const StateView &s, const StepTables &t, float ka, float dnext,
-                                                 const KjChunk<P> &kj, int c0, const uint32_t (&g)[32], float hi,
-                                                 uint32_t (&xr)[32], uint32_t (&yr)[32], const FOut<OP> &fo,
-                                                 const RingExt &ext) {
-  constexpr int PR = P < 32 ? P : 32;
-  float xs[32], xms[32], xps[32];
-#pragma unroll
-  for (int j = 0; j < 32; ++j) xs[j] = __uint_as_float(xr[j]);
-  ring32<P, GEN>(xs, s.Pr, c0, ext, xms, xps);
-#pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    if (!FULL && c0 + j >= s.C) continue;
-    const float xm = xms[j], xp = xps[j];
-    const float xj = xs[j];
-    float yn = fmaf(t.kc, __uint_as_float(g[j]) + hi, __uint_as_float(yr[j]));
-    yn = fmaf(-ka, xj, yn);
-    yn = fmaf(kj.get(c0, j / PR), xm + xp, yn);
-    yr[j] = __float_as_uint(yn);
-  }
-#pragma unroll
-  for (int j = 0; j < 32; ++j) {
-    if (FULL || c0 + j < s.C) {
-      float xn = fmaf(t.kx, __uint_as_float(yr[j]), __uint_as_float(xr[j]));
-      if (fabsf(xn) > 1.f) {
-        xn = copysignf(1.f, xn);
-        yr[j] = __float_as_uint(0.f);
-      }
-      xr[j] = __float_as_uint(xn);
-      fo.put(j, xn, dnext);
-    } else {
-      fo.zero(j);
-    }
-  }
-}
-
-template <int P, bool PAIR, int OP, bool GEN>
-__device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const StateView &s, const TpArgs &a,
-                                                          const StepTables &t) {
-  static_assert(!PAIR || OP == kOpF8, "CTA pairs run the e4m3 product only");
-  using Sh = TpShape<PAIR, OP>;
-  using O = TcOp<OP>;
-  constexpr int kStages = Sh::kStages;
-  constexpr int kStageB = O::kNB * Sh::kTileB;  // B bytes of one stage (hi and lo for kOpBsb)
-  extern __shared__ uint8_t smem_raw[];
-  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint8_t *sA = smem;
-  uint8_t *sB = smem + kStages * kTcTile;
-  uint8_t *sF = sB + kStages * kStageB;  // [128 columns][128 spins] f(x_next) (kOpBsb: hi, then lo)
-  uint64_t *full = reinterpret_cast<uint64_t *>(sF + Sh::kFBytes);
-  uint64_t *empty = full + kStages;
-  uint64_t *done = empty + kStages;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
-  int *s_abort = reinterpret_cast<int *>(tmem_slot + 1);  // PAIR: [step parity][rank]
-
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  uint32_t rank = 0;
-  if constexpr (PAIR) {
-    // both CTAs of a cluster read the same cluster shape, so both return here or neither does
-    if (tc::cluster_nctarank() != 2 || tc::cluster_nctaid_x() != 2) {
-      if (threadIdx.x == 0) atomicCAS(a.err, 0, tc::ERR_CLUSTER_SHAPE);
-      return;
-    }
-    rank = tc::cluster_ctarank();  // = blockIdx.x & 1
-  }
-  const bool leader = rank == 0;
-  const int ct = PAIR ? blockIdx.y : blockIdx.x, mt = PAIR ? blockIdx.x : blockIdx.y;
-  const int m0 = mt * kTcBM, n0 = ct * kTcBN;
-  const int KB = a.Kp / O::kKE;
-  const int npre = KB < kStages ? KB : kStages;  // k-blocks whose J tile is loaded ahead
-  // this CTA's operand loads: fT rows (B box) and the full barrier they complete on
-  const CUtensorMap *mapB = PAIR ? &m.B64 : &m.B;
-  const int b_off = PAIR ? 64 * int(rank) : 0;
-  auto load_tile = [&](uint8_t *dst, const CUtensorMap *map, int st, int c0_, int c1_) {
-    if constexpr (PAIR)
-      tc::tma_load_2d_pair(dst, map, tc::map_to_rank(tc::smem_u32(&full[st]), 0), c0_, c1_);
-    else
-      tc::tma_load_2d(dst, map, &full[st], c0_, c1_);
-  };
-  const int quarter = warp & 3, chunk = warp >> 2;
-  const int rl = quarter * 32 + lane, i = m0 + rl;
-  const int cl = 32 * chunk, c0 = n0 + cl;
-  const uint32_t lane_off = uint32_t(quarter * 32) << 16;
-
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < kStages; ++q) {
-      tc::mbar_init(&full[q], 1);
-      tc::mbar_init(&empty[q], 1);
-    }
-    tc::mbar_init(done, 1);
-    tc::fence_mbar_init();
-    tc::prefetch_tmap(&m.A);
-    tc::prefetch_tmap(mapB);
-    tc::prefetch_tmap(&m.Fst);
-    if constexpr (O::kNB == 2) {
-      tc::prefetch_tmap(&m.Bl);
-      tc::prefetch_tmap(&m.Fstl);
-    }
-    for (int q = 0; q < 4; ++q) s_abort[q] = 0;
-  }
-  if (warp == 0) {
-    if constexpr (PAIR) tc::tmem_alloc_pair(tmem_slot, kTmemCols);
-    else tc::tmem_alloc(tmem_slot, kTmemCols);
-  }
-  tc::tc_fence_before();
-  if constexpr (PAIR) tc::cluster_sync();  // the pair's barriers and TMEM exist before either CTA uses them
-  else __syncthreads();
-  tc::tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
-
-  {  // the state tile into TMEM (rows past N hold zeros and stay unchanged)
-    uint32_t xr[32], yr[32];
-    if (i < s.N) {
-      const float4 *px = reinterpret_cast<const float4 *>(s.x + size_t(i) * s.Cp + c0);
-      const float4 *py = reinterpret_cast<const float4 *>(s.y + size_t(i) * s.Cp + c0);
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const float4 vx = px[u], vy = py[u];
-        xr[4 * u] = __float_as_uint(vx.x); xr[4 * u + 1] = __float_as_uint(vx.y);
-        xr[4 * u + 2] = __float_as_uint(vx.z); xr[4 * u + 3] = __float_as_uint(vx.w);
-        yr[4 * u] = __float_as_uint(vy.x); yr[4 * u + 1] = __float_as_uint(vy.y);
-        yr[4 * u + 2] = __float_as_uint(vy.z); yr[4 * u + 3] = __float_as_uint(vy.w);
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < 32; ++j) xr[j] = yr[j] = 0u;
-    }
-    __syncwarp();
-    tc::tmem_st_32x32b_x32(tmem + lane_off + kTmemX + cl, xr);
-    tc::tmem_st_32x32b_x32(tmem + lane_off + kTmemY + cl, yr);
-    tc::tmem_wait_st();
-  }
-  const float hi = i < s.N ? __ldg(a.h + i) : 0.f;
-  if (warp == 0 && lane == 0 && a.n_begin < a.n_end) {  // J tiles of the first step's first stages
-    for (int kb = 0; kb < npre; ++kb) {
-      if (leader) tc::mbar_arrive_expect_tx(&full[kb], Sh::kExpect);
-      load_tile(sA + kb * kTcTile, &m.A, kb, kb * O::kKE, m0);
-    }
-  }
-  tc::tc_fence_before();
-  __syncthreads();
-  tc::tc_fence_after();
-
-  constexpr uint32_t idesc = O::idesc(PAIR ? 2 * kTcBM : kTcBM, kTcBN);
-  constexpr int kFlagShift = OP == kOpF8 ? 0 : 1;  // k-blocks per 128-spin row tile: 1 (e4m3) or 2 (bf16)
-  int n = a.n_begin;
-  bool prefetched = a.n_begin < a.n_end;
-  for (; n < a.n_end; ++n) {
-    const uint32_t q = uint32_t(n - a.n_begin);
-    if (warp == 0) {
-      // producer: f tiles as their row tiles publish step q, J tiles beyond the prefetched ones
-      const int brow = (n & 1) * s.Cp + n0;
-      uint64_t t0 = 0;
-      uint32_t polls = 0;
-      int kb = 0;
-      while (kb < KB) {
-        const int kq = kb + lane;
-        const bool ok = q == 0 || kq >= KB || tc::ld_acquire_gpu(a.flags + (kq >> kFlagShift) * a.Ct + ct) >= q;
-        const unsigned ball = __ballot_sync(0xffffffffu, ok);
-        int nready = ball == 0xffffffffu ? 32 : __ffs(~ball) - 1;
-        nready = nready < KB - kb ? nready : KB - kb;
-        if (nready == 0) {
-          int give_up = 0;
-          if (lane == 0) {
-            const uint64_t now = tc::globaltimer_ns();
-            if (t0 == 0) t0 = now;
-            if (*reinterpret_cast<volatile int *>(a.err) != 0) {
-              give_up = 1;
-            } else if (now - t0 > kFlagTimeoutNs || ++polls > (1u << 26)) {
-              atomicCAS(a.err, 0, tc::ERR_WAIT_FLAG);
-              give_up = 1;
-            }
-          }
-          if (__shfl_sync(0xffffffffu, give_up, 0)) {
-            nready = KB - kb;  // proceed with whatever the buffer holds; the run reports the error
-          } else {
-            __nanosleep(64);
-            continue;
-          }
-        }
-        if (lane == 0) {
-          asm volatile("fence.acq_rel.gpu;" ::: "memory");
-          tc::fence_proxy_async_global();
-          for (int j = kb; j < kb + nready; ++j) {
-            const uint32_t g = q * KB + j, st = g % kStages, use = g / kStages;
-            if (j >= npre) {
-              if (use > 0) tc::mbar_wait(&empty[st], (use - 1) & 1, a.err, tc::ERR_WAIT_EMPTY);
-              if (leader) tc::mbar_arrive_expect_tx(&full[st], Sh::kExpect);
-              load_tile(sA + st * kTcTile, &m.A, st, j * O::kKE, m0);
-            }
-            load_tile(sB + st * kStageB, mapB, st, j * O::kKE, brow + b_off);
-            if constexpr (O::kNB == 2) load_tile(sB + st * kStageB + Sh::kTileB, &m.Bl, st, j * O::kKE, brow);
-          }
-        }
-        __syncwarp();
-        kb += nready;
-      }
-      // J tiles of the next step's first stages, behind this step's MMAs
-      prefetched = n + 1 < a.n_end;
-      if (lane == 0 && prefetched) {
-        for (int j = 0; j < npre; ++j) {
-          const uint32_t g = (q + 1) * KB + j, st = g % kStages, use = g / kStages;
-          if (use > 0) tc::mbar_wait(&empty[st], (use - 1) & 1, a.err, tc::ERR_WAIT_EMPTY);
-          if (leader) tc::mbar_arrive_expect_tx(&full[st], Sh::kExpect);
-          load_tile(sA + st * kTcTile, &m.A, st, j * O::kKE, m0);
-        }
-      }
-    } else if (warp == 1 && lane == 0 && leader) {
-      for (int kb = 0; kb < KB; ++kb) {
-        const uint32_t g = q * KB + kb, st = g % kStages, use = g / kStages;
-        tc::mbar_wait(&full[st], use & 1, a.err, tc::ERR_WAIT_FULL);
-        tc::tc_fence_after();
-        const uint32_t a0 = tc::smem_u32(sA + st * kTcTile), b0 = tc::smem_u32(sB + st * kStageB);
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const uint64_t ad = tc::smem_desc_sw128(a0 + kk * 32), bd = tc::smem_desc_sw128(b0 + kk * 32);
-          if constexpr (PAIR) {
-            tc::mma_f8_pair(tmem, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
-          } else {
-            O::mma(tmem, ad, bd, idesc, (kb | kk) != 0 ? 1u : 0u);
-            if constexpr (O::kNB == 2)
-              O::mma(tmem, ad, tc::smem_desc_sw128(b0 + Sh::kTileB + kk * 32), idesc, 1u);
-          }
-        }
-        if constexpr (PAIR) tc::mma_commit_pair(&empty[st]);
-        else tc::mma_commit(&empty[st]);
-      }
-      if constexpr (PAIR) tc::mma_commit_pair(done);
-      else tc::mma_commit(done);
-    }
-    __syncwarp();
-    const float ka = __ldg(t.ka + n), dnext = __ldg(t.dl + n + 1);
-    KjChunk<P> kj;
-    kj.load(s, t.kj + size_t(n) * t.R, c0);
-    tc::mbar_wait(done, q & 1, a.err, tc::ERR_WAIT_DONE);
-    tc::tc_fence_after();
-    {
-      uint32_t g[32], xr[32], yr[32];
-      tc::tmem_ld_32x32b_x32_nowait(tmem + lane_off + cl, g);
-      tc::tmem_ld_32x32b_x32_nowait(tmem + lane_off + kTmemX + cl, xr);
-      tc::tmem_ld_32x32b_x32_nowait(tmem + lane_off + kTmemY + cl, yr);
-      RingExt ext{0.f, 0.f, 0.f, 0.f};
-      if constexpr (P > 32) {
-        // runs over several chunks: their outside neighbours, read before any warp stores its new x
-        const int rb = cl - cl % P;
-        const uint32_t xb = tmem + lane_off + kTmemX;
-        const uint32_t u0 = tc::tmem_ld_32x32b_x1_nowait(xb + uint32_t(cl > rb ? cl - 1 : cl));
-        const uint32_t u1 = tc::tmem_ld_32x32b_x1_nowait(xb + uint32_t(cl + 32 < rb + P ? cl + 32 : cl));
-        const uint32_t u2 = tc::tmem_ld_32x32b_x1_nowait(xb + uint32_t(rb));
-        const uint32_t u3 = tc::tmem_ld_32x32b_x1_nowait(xb + uint32_t(rb + s.Pr - 1));
-        tc::tmem_wait_ld();
-        ext = RingExt{__uint_as_float(u0), __uint_as_float(u1), __uint_as_float(u2), __uint_as_float(u3)};
-        tc::tc_fence_before();
-        __syncthreads();
-        tc::tc_fence_after();
-      }
-      tc::tmem_wait_ld();
-      tc::reg_fence(g);
-      tc::reg_fence(xr);
-      tc::reg_fence(yr);
-      const FOut<OP> fo = f_out<OP>(sF, cl, rl);
-      if (i < s.N && c0 < s.C) {
-        if (c0 + 32 <= s.C) sb_update_regs32<P, true, OP, GEN>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, fo, ext);
-        else sb_update_regs32<P, false, OP, GEN>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, fo, ext);
-      } else {
-#pragma unroll
-        for (int j = 0; j < 32; ++j) fo.zero(j);
-      }
-      __syncwarp();
-      tc::tmem_st_32x32b_x32(tmem + lane_off + kTmemX + cl, xr);
-      tc::tmem_st_32x32b_x32(tmem + lane_off + kTmemY + cl, yr);
-      tc::tmem_wait_st();
-    }
-    tc::fence_proxy_async_smem();
-    tc::tc_fence_before();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      // publish f_{n+1} of this tile: spins m0.., columns n0.. of the other FT buffer
-      tc::tma_store_2d(&m.Fst, sF, m0, ((n + 1) & 1) * s.Cp + n0);
-      if constexpr (O::kNB == 2) tc::tma_store_2d(&m.Fstl, sF + O::kFTile, m0, ((n + 1) & 1) * s.Cp + n0);
-      tc::tma_store_commit_and_wait_all();
-      tc::fence_proxy_async_global();
-      tc::st_release_gpu(a.flags + mt * a.Ct + ct, q + 1);
-      const int v = *reinterpret_cast<volatile int *>(a.err);
-      if constexpr (PAIR) {
-        int *slot = s_abort + 2 * (q & 1) + rank;  // double-buffered by step parity
-        *slot = v;
-        tc::st_cluster_u32(tc::map_to_rank(tc::smem_u32(slot), rank ^ 1u), uint32_t(v));
-      } else {
-        *s_abort = v;
-      }
-    }
-    if constexpr (PAIR) tc::cluster_sync();  // also orders the odd CTA's accumulator reads before the next MMAs
-    else __syncthreads();
-    tc::tc_fence_after();
-    const int stop = PAIR ? (s_abort[2 * (q & 1)] | s_abort[2 * (q & 1) + 1]) : *s_abort;
-    if (stop != 0) break;
-  }
-  if (n < a.n_end && prefetched && warp == 0 && lane == 0) {
-    // stopped early with J tiles of step n + 1 in flight: complete those stages
-    // (with any f tile) and wait for them, so no copy outlives the block
-    const uint32_t q = uint32_t(n + 1 - a.n_begin);
-    const int brow = ((n + 1) & 1) * s.Cp + n0;
-    for (int j = 0; j < npre; ++j) {
-      const uint32_t g = q * KB + j, st = g % kStages, use = g / kStages;
-      load_tile(sB + st * kStageB, mapB, st, j * O::kKE, brow + b_off);
-      if constexpr (O::kNB == 2) load_tile(sB + st * kStageB + Sh::kTileB, &m.Bl, st, j * O::kKE, brow);
-      if (leader) tc::mbar_wait(&full[st], use & 1, a.err, tc::ERR_WAIT_FULL);
-    }
-  }
-  __syncwarp();
-  {  // the state tile back to global memory
-    uint32_t xr[32], yr[32];
-    tc::tmem_ld_32x32b_x32_nowait(tmem + lane_off + kTmemX + cl, xr);
-    tc::tmem_ld_32x32b_x32_nowait(tmem + lane_off + kTmemY + cl, yr);
-    tc::tmem_wait_ld();
-    tc::reg_fence(xr);
-    tc::reg_fence(yr);
-    if (i < s.N) {
-      float4 *px = reinterpret_cast<float4 *>(s.x + size_t(i) * s.Cp + c0);
-      float4 *py = reinterpret_cast<float4 *>(s.y + size_t(i) * s.Cp + c0);
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        px[u] = make_float4(__uint_as_float(xr[4 * u]), __uint_as_float(xr[4 * u + 1]),
-                            __uint_as_float(xr[4 * u + 2]), __uint_as_float(xr[4 * u + 3]));
-        py[u] = make_float4(__uint_as_float(yr[4 * u]), __uint_as_float(yr[4 * u + 1]),
-                            __uint_as_float(yr[4 * u + 2]), __uint_as_float(yr[4 * u + 3]));
-      }
-    }
-  }
-  tc::tc_fence_before();
-  // PAIR: neither CTA leaves (or frees its TMEM) while the other's MMAs, loads or reads may still use it
-  if constexpr (PAIR) tc::cluster_sync();
-  else __syncthreads();
-  if (warp == 0) {
-    tc::tc_fence_after();
-    if constexpr (PAIR) tc::tmem_dealloc_pair(tmem, kTmemCols);
-    else tc::tmem_dealloc(tmem, kTmemCols);
-  }
-}
-
 template <int P, int OP, bool GEN>
 __global__ void __launch_bounds__(kTpThreads, 1)
     k_solve_dense_tc_persistent(const __grid_constant__ TcMaps m, StateView s, TpArgs a, StepTables t) {
-  solve_dense_tc_persistent<P, false, OP, GEN>(m, s, a, t);
+  solve_dense_tc_persistent<P, false, OP, GEN>(m, s, a, t, blockIdx.y, blockIdx.x);
 }
 
 template <int P>
 __global__ void __launch_bounds__(kTpThreads, 1)
     k_solve_dense_tc_pair(const __grid_constant__ TcMaps m, StateView s, TpArgs a, StepTables t) {
-  solve_dense_tc_persistent<P, true, kOpF8, false>(m, s, a, t);
+  solve_dense_tc_persistent<P, true, kOpF8, false>(m, s, a, t, blockIdx.x, blockIdx.y);
 }
 
 // ---------------------------------------------------------------- split-K persistent solver

@@ -53,16 +53,18 @@ def make_requests(pool, n_requests, steps=2000, R=16, seed=1):
     return reqs
 
 
-def run_stream(reqs, rate, arena_bytes=40 << 30, slots=64, chunk=50, seed=2, stream=None):
+def run_stream(reqs, rate, arena_bytes=40 << 30, slots=64, chunk=50, seed=2, stream=None, dense_batching=True):
     """Open loop at `rate` requests/s (closed loop, all at t = 0, if rate is
     None).  Returns per-request latencies (s), the makespan and the
-    replica-spin updates done."""
+    replica-spin updates done.  dense_batching: small dense requests share
+    cooperative launches (sbqa_engine_set_dense_batching)."""
     rng = np.random.default_rng(seed)
     if rate is None:
         arrivals = np.zeros(len(reqs))
     else:
         arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
     eng = sb.engine_create(arena_bytes, slots, chunk)
+    sb.engine_set_dense_batching(eng, dense_batching)
     id_of = {}
     done_at = {}
     t0 = time.perf_counter()
@@ -89,7 +91,9 @@ def run_stream(reqs, rate, arena_bytes=40 << 30, slots=64, chunk=50, seed=2, str
     eng.destroy()
     return {"latency_s": lat, "makespan_s": makespan, "updates": updates, "results": results,
             "arrivals": arrivals, "kernels_launched": stats["kernels_launched"],
-            "batched_updates": stats["batched_updates"], "batched_ms": stats["batched_ms"]}
+            "batched_updates": stats["batched_updates"], "batched_ms": stats["batched_ms"],
+            "dense_batched_launches": stats["dense_batched_launches"],
+            "dense_batched_chunks": stats["dense_batched_chunks"]}
 
 
 def summary(out):
@@ -97,4 +101,6 @@ def summary(out):
     return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
             "mean_s": float(lat.mean()), "max_s": float(lat.max()),
             "updates_per_s": out["updates"] / out["makespan_s"], "makespan_s": out["makespan_s"],
-            "requests": int(lat.size), "kernels_launched": int(out["kernels_launched"])}
+            "requests": int(lat.size), "kernels_launched": int(out["kernels_launched"]),
+            "dense_batched_launches": int(out.get("dense_batched_launches", 0)),
+            "dense_batched_chunks": int(out.get("dense_batched_chunks", 0))}

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import workloads
-from sbqa_cases import create, dense_int, lattice, regular, sk
+from sbqa_cases import create, dense_int, dense_real, lattice, regular, sk
 
 pytestmark = pytest.mark.gpu
 
@@ -77,6 +77,52 @@ def test_engine_mix_equals_alone(sb, chunk, slots, arena_mb):
         assert np.array_equal(got["replica"], ref["replica"]), rid
     st = sb.engine_stats(eng)
     assert st["finished"] == len(ids) and st["queued"] == 0 and st["active"] == 0 and st["arena_used"] == 0
+
+
+def test_engine_batches_small_dense_requests(sb):
+    """Small dense tensor-core requests share cooperative launches: e4m3 and
+    BF16 operands, run widths 8 and 16, a ring of 6 replicas in 8 columns,
+    step counts that end inside a chunk, and more tiles of one form than one
+    wave holds (two launches for that form).  Every result equals the request
+    solved alone."""
+    reqs = []
+    for k in range(17):
+        if k < 11:
+            spec, prec, P, R = sk(1000, 40 + k)[1], "exact", 16, 16     # 8 x 2 = 16 tiles each
+        elif k < 14:
+            spec, prec, P, R = dense_real(300, 40 + k)[1], "bf16", 8, 4  # BF16 operands, 3 x 1 tiles
+        else:
+            spec, prec, P, R = dense_int(200, 40 + k, jmax=3)[1], "exact", 6, 5  # ring of 6 in 8 columns
+        pb = create(sb, spec)
+        sb.set_schedule(pb, *workloads.autotune_params(R, k), precision=prec, eval_every=0)
+        reqs.append((pb, 40 + 7 * k, P, R, 300 + k))
+    alone = [_alone(sb, r) for r in reqs]
+    for batching in (True, False):
+        eng = sb.engine_create(2 << 30, 32, 25)
+        sb.engine_set_dense_batching(eng, batching)
+        ids = [sb.engine_submit(eng, *r) for r in reqs]
+        done = []
+        for _ in range(1000):
+            done += sb.engine_step(eng)
+            if len(done) == len(ids):
+                break
+        assert sorted(done) == ids
+        for rid, ref in zip(ids, alone):
+            got = sb.engine_result(eng, rid)
+            assert np.array_equal(got["spins"], ref["spins"]), (batching, rid)
+            assert np.array_equal(got["energy"], ref["energy"]), (batching, rid)
+            assert np.array_equal(got["replica"], ref["replica"]), (batching, rid)
+        st = sb.engine_stats(eng)
+        if batching:
+            # the first chunk alone needs two launches of the 16-tile form (176 tiles), one of each other form
+            assert st["dense_batched_launches"] >= 4
+            assert st["dense_batched_chunks"] >= 2 * st["dense_batched_launches"]
+        else:
+            assert st["dense_batched_launches"] == 0 and st["dense_batched_chunks"] == 0
+        eng.destroy()
+    with pytest.raises(sb.SBQAError) as e:
+        sb.engine_set_dense_batching(sb.engine_create(64 << 20, 2, 10), 2)
+    assert e.value.status == sb.ERR_INVALID_ARG
 
 
 def test_engine_admission_waits_for_memory(sb):
