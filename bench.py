@@ -293,7 +293,7 @@ def run_serving(args, stream=None):
         peaks = {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-            "traffic": None, "kernel": "k_step_batched",
+            "traffic": None, "kernel": "k_solve_batched",
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
             "note": "closed loop of the %d lattice requests alone: algorithmic %d B/update x the updates the "
                     "batched kernel advanced / its event-timed launches" % (len(lat_reqs), BYTES_PER_UPDATE)}

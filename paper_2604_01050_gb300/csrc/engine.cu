@@ -135,7 +135,7 @@ struct sbqa_engine {
   std::vector<int> slot_req;  // slot -> request id, -1 free
   SlotDesc *d_slots = nullptr;
   WorkItem *d_items = nullptr;
-  int *d_n_items = nullptr;
+  int *d_n_items = nullptr;  // [units, items] of the work list (device)
   size_t items_cap = 0;
   int sms = 0;
   int64_t steps_done_total = 0;  // replica-spin updates issued, for statistics
@@ -284,7 +284,7 @@ SlotDesc slot_desc(const Request &r) {
   d.x = r.x; d.y = r.y; d.F0 = r.F0; d.F1 = r.F1;
   d.ka = r.ka; d.dl = r.dl; d.kj = r.kj; d.kc = r.tables.kc; d.kx = r.tables.kx;
   d.n0 = r.n0;
-  d.W = (d.ell_col && r.Cp % 256 == 0) ? 8 : 4;
+  d.W = d.ell_col ? 8 : 4;
   return d;
 }
 
@@ -380,7 +380,7 @@ int sbqa_engine_create(int64_t arena_bytes, int32_t max_slots, int32_t chunk_ste
   e->arena.bytes = size_t(arena_bytes);
   e->arena.free_blocks[0] = size_t(arena_bytes);
   if (cudaMalloc(&e->d_slots, sizeof(SlotDesc) * max_slots) != cudaSuccess ||
-      cudaMalloc(&e->d_n_items, sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&e->d_n_items, 2 * sizeof(int)) != cudaSuccess ||
       cudaMalloc(&e->d_bar, sizeof(unsigned) * grid_barrier_words()) != cudaSuccess ||
       cudaMalloc(&e->d_err, sizeof(int)) != cudaSuccess || cudaMemset(e->d_err, 0, sizeof(int)) != cudaSuccess)
     return fail_free(SBQA_ERR_OOM, "engine tables");
@@ -468,18 +468,29 @@ int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done, int32_t *don
   // 2. slot table and work list of the CSR requests
   std::vector<SlotDesc> slots(e->max_slots);
   std::vector<WorkItem> items;
-  std::vector<int> dense_active;
+  std::vector<int> dense_active, ell_slots, other_slots;
   for (int q = 0; q < e->max_slots; ++q) {
     if (e->slot_req[q] < 0) continue;
     Request &r = e->reqs[e->slot_req[q]];
     slots[q] = slot_desc(r);
-    if (r.prob->dense) {
-      dense_active.push_back(r.id);
-      continue;
-    }
-    for (int g = 0; g < r.Cp / (32 * slots[q].W); ++g)
-      for (int r0 = 0; r0 < r.prob->n; r0 += 8) items.push_back(WorkItem{q, r0, g, 0});
+    if (r.prob->dense) dense_active.push_back(r.id);
+    else (slots[q].W == 8 ? ell_slots : other_slots).push_back(q);
   }
+  // units of the ELL slots first, ordered by the code they run (run width,
+  // coupling kind, ring form), so that a warp's contiguous share mostly runs one
+  // form; then the 8-row items of the other slots
+  std::stable_sort(ell_slots.begin(), ell_slots.end(), [&](int a, int b) {
+    const SlotDesc &x = slots[a], &y = slots[b];
+    return std::make_tuple(x.P, x.kind != VAL_PM1, x.Pr != x.P) < std::make_tuple(y.P, y.kind != VAL_PM1, y.Pr != y.P);
+  });
+  for (int q : ell_slots)
+    for (int g = 0; g < slots[q].Cp / kColsPerWarp; ++g)
+      for (int r0 = 0; r0 < slots[q].N; r0 += 2) items.push_back(WorkItem{q, r0, g, 0});
+  int counts[2] = {int(items.size()), 0};
+  for (int q : other_slots)
+    for (int g = 0; g < slots[q].Cp / kColsPerWarp; ++g)
+      for (int r0 = 0; r0 < slots[q].N; r0 += 8) items.push_back(WorkItem{q, r0, g, 0});
+  counts[1] = int(items.size()) - counts[0];
   if (items.size() > e->items_cap) {
     if (e->d_items) cudaFree(e->d_items);
     e->d_items = nullptr;
@@ -490,7 +501,7 @@ int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done, int32_t *don
   ENG_CUDA(cudaMemcpyAsync(e->d_slots, slots.data(), slots.size() * sizeof(SlotDesc), cudaMemcpyHostToDevice, st));
   if (n_items)
     ENG_CUDA(cudaMemcpyAsync(e->d_items, items.data(), items.size() * sizeof(WorkItem), cudaMemcpyHostToDevice, st));
-  ENG_CUDA(cudaMemcpyAsync(e->d_n_items, &n_items, sizeof(int), cudaMemcpyHostToDevice, st));
+  ENG_CUDA(cudaMemcpyAsync(e->d_n_items, counts, sizeof(counts), cudaMemcpyHostToDevice, st));
   // 3. the chunk: the dense requests on their slots' streams (after everything
   //    issued on `st` so far: admission, tables), one batched launch per step
   //    for all CSR requests on `st`; `st` then waits for the dense streams
@@ -552,7 +563,9 @@ int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done, int32_t *don
       ENG_CUDA(cudaEventCreate(&e->batched_t1));
     }
     // every CSR request's chunk in one cooperative launch, replayed from a captured graph
-    const int grid = std::max(1, std::min(n_items, batched_persistent_blocks()));
+    // a block per 8 warp tasks (a unit, or a row of an item), at most one co-resident wave
+    const int64_t tasks = int64_t(counts[0]) + 8 * int64_t(counts[1]);
+    const int grid = int(std::max<int64_t>(1, std::min<int64_t>((tasks + 7) / 8, batched_persistent_blocks())));
     if ((rc = csr_chunk_graph(e, grid)) != SBQA_OK) return rc;
     ENG_CUDA(cudaEventRecord(e->batched_t0, st));
     if (e->csr_graph) {

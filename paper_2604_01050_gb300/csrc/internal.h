@@ -209,10 +209,10 @@ struct SlotDesc {
   const float *ka, *dl, *kj;
   float kc, kx;
   int n0;  // steps completed before the current chunk
-  int W;   // replica columns per lane of its work items: 8 (ELL form, Cp a multiple of 256) or 4
+  int W;   // replica columns per lane: 8 (ELL form: units of two rows on half warps) or 4 (a row per warp)
 };
 
-// 8 spin rows x 32 W replica columns of one slot (W of the slot).
+// 128 replica columns (colgroup) of 2 spin rows (a unit, W = 8) or 8 (an item, W = 4) of one slot.
 struct WorkItem {
   int slot, row0, colgroup, pad;
 };
@@ -247,18 +247,16 @@ cudaError_t launch_step_dense_tc(const void *plan, const StateView &s, int Kp, u
 // FT buffer `buffer` from the f codes of F buffer `which` (op 0, 1) or from x (op 2)
 cudaError_t launch_f_to_ft(const StateView &s, int which, uint8_t *FT, int Kp, int buffer, int op, cudaStream_t st);
 
-// Batched CSR step over the work items of all active slots (step_batched.cu);
-// j = step index inside the current chunk, n_items in device memory.
-cudaError_t launch_step_batched(const SlotDesc *slots, int n_slots, const WorkItem *items, const int *n_items,
-                                int grid, int j, cudaStream_t st);
-// All steps j0 .. j1 - 1 of a chunk in one cooperative launch of `grid` blocks
-// (at most batched_persistent_blocks(), the co-resident count); bar holds
-// grid_barrier_words() counters (zeroed here); a barrier that gives up
-// records code 4 in *err.
+// All steps j0 .. j1 - 1 of a chunk for every active CSR slot in one
+// cooperative launch of `grid` blocks (step_batched.cu; at most
+// batched_persistent_blocks(), the co-resident count).  items: first
+// counts[0] units of 2 rows x 128 columns of slots in ELL form (W = 8), then
+// counts[1] items of 8 rows x 128 columns of the others (W = 4); counts in
+// device memory.  bar holds grid_barrier_words() counters (zeroed here); a
+// barrier that gives up records code 4 in *err.
 int batched_persistent_blocks();
-cudaError_t launch_solve_batched(const SlotDesc *slots, int n_slots, const WorkItem *items, const int *n_items,
+cudaError_t launch_solve_batched(const SlotDesc *slots, int n_slots, const WorkItem *items, const int *counts,
                                  int grid, int j0, int j1, unsigned *bar, int *err, cudaStream_t st);
-int batched_blocks_per_sm();  // resident blocks of the batched step kernel per SM (one wave = this x SMs)
 
 int energy_row_blocks(int N);
 // Readout energies of an integer dense instance on the tensor cores: the sign

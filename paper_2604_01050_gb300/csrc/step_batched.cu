@@ -1,19 +1,22 @@
-// step_batched.cu -- one SBQA step for many CSR instances of uneven size in a
-// single launch (the batching engine's kernel).
+// step_batched.cu -- the steps of many CSR instances of uneven size in one
+// launch (the batching engine's chunk kernel).
 //
 // Every active request owns a slot: its CSR couplings (and their ELL form for
 // rows of degree <= 8), its state buffers, its schedule tables and the number
 // of steps it had completed when the current chunk of steps started.  The
-// engine lists the work of all active slots as items of 8 spin rows x 128
-// replica columns; one wave of blocks walks the item list (a warp per row of
-// an item), so one launch advances every request by one step whatever the
-// mix.  The slot descriptors sit in shared memory, and a warp issues the
-// loads of its next row (work item two ahead, then x, y, h and the ELL
-// columns) before it gathers and updates the current one, so the memory
-// latency of one row overlaps the work of the previous one.  The arithmetic
-// per element is the one of k_step_csr (same gathers, same sums in the same
-// order, same update), so a request gives bit-identical results alone and in
-// any mix.
+// engine lists the work of all active slots: units of 2 spin rows x 128
+// replica columns for slots in ELL form (first, ordered by run width and
+// coupling kind) and items of 8 rows x 128 columns for the others.  One
+// cooperative launch runs all steps of a chunk; a bounded grid barrier
+// separates the steps.  At the start of the launch every warp takes a
+// contiguous share of the units and keeps their neighbour columns, coupling
+// values, degrees and fields in shared memory for the whole chunk; each step
+// it runs them on half warps (one row of a unit per half, 8 columns per lane),
+// units beyond its shared-memory share from global memory.  The items of the
+// other slots are spread over all warps, a row per warp (4 columns per lane).
+// The arithmetic per element is the one of k_step_csr (same gathers, same
+// sums in the same order, same update), so a request gives bit-identical
+// results alone and in any mix.
 #include "grid_sync.cuh"
 #include "step_common.cuh"
 
@@ -89,112 +92,63 @@ __device__ __forceinline__ void batched_row_csr(const SlotDesc &d, int n, int i,
   else sb_update4<P, false>(s, t, n, i, c4, G, hi, xv, yv, Fout);
 }
 
-// Loads of one row of a work item, issued ahead of its use.
-struct RowFetch {
-  int slot, row, n, c0;  // row < 0: nothing to do (past N, or the request has finished)
-  int col;               // lane < 8: ELL column of entry `lane`
-  float val;             // lane < 8: its value (FP32 / BF16 couplings)
-  int2 meta;             // (degree, +1 count)
-  float hi;
-  float ka, dnext;       // this step's schedule values of the slot
-  float kj[4];           // J_perp of the runs of the lane's columns (W = 4)
-  float4 x[2], y[2];     // x, y of the lane's W columns
+// Neighbours of two rows of a unit, kept in shared memory for a chunk.
+struct BatchEntry {
+  int slot, row0, chunk;
+  uint32_t degpos[2];  // per row: degree | +1 count (VAL_PM1) << 8; 0 for a row past N
+  float h[2];
+  int32_t col[2][kEllSlots];
+  float val[2][kEllSlots];  // FP32 / BF16 couplings (unused for VAL_PM1)
+  int pad;
 };
+static_assert(sizeof(BatchEntry) % 16 == 0, "entries start on 16-byte boundaries");
 
-__device__ __forceinline__ void fetch_row(RowFetch &f, const SlotDesc *D, const WorkItem &w, int sub, int j, int lane) {
-  const SlotDesc &d = D[w.slot];
-  f.slot = w.slot;
-  f.row = w.row0 + sub;
-  f.n = d.n0 + j;
-  if (f.row >= d.N || f.n >= d.S) {  // warp-uniform
-    f.row = -1;
-    return;
-  }
-  const int W = d.W;
-  f.c0 = w.colgroup * 32 * W + lane * W;
-  const size_t off = size_t(f.row) * d.Cp + f.c0;
-  f.x[0] = *reinterpret_cast<const float4 *>(d.x + off);
-  f.y[0] = *reinterpret_cast<const float4 *>(d.y + off);
-  if (W == 8) {
-    f.x[1] = *reinterpret_cast<const float4 *>(d.x + off + 4);
-    f.y[1] = *reinterpret_cast<const float4 *>(d.y + off + 4);
-  }
-  f.hi = __ldg(d.h + f.row);
-  f.ka = __ldg(d.ka + f.n);
-  f.dnext = __ldg(d.dl + f.n + 1);
-  if (W == 4) {
-    const float *kjn = d.kj + size_t(f.n) * d.R;
-    const int lp = __ffs(d.P) - 1;  // P (the run's column width) is a power of two
-    if (d.P >= 4) {
-      const float k = f.c0 < d.C ? __ldg(kjn + (f.c0 >> lp)) : 0.f;
-      f.kj[0] = f.kj[1] = f.kj[2] = f.kj[3] = k;
-    } else {
-#pragma unroll
-      for (int q = 0; q < 4; ++q) f.kj[q] = (f.c0 + q < d.C) ? __ldg(kjn + ((f.c0 + q) >> lp)) : 0.f;
-    }
-  }
-  if (d.ell_col) {
-    if (lane < kEllSlots) {
-      f.col = __ldg(d.ell_col + size_t(f.row) * kEllSlots + lane);
-      if (d.kind != VAL_PM1) f.val = __ldg(d.ell_val + size_t(f.row) * kEllSlots + lane);
-    }
-    f.meta = __ldg(reinterpret_cast<const int2 *>(d.ell_meta) + f.row);
-  }
-}
+constexpr int kBatchEntriesPerWarp = 48;  // 8 warps x 48 x 160 B = 61.4 KB of shared memory per block (3 blocks per SM)
+constexpr int kBatchSmem = 8 * kBatchEntriesPerWarp * int(sizeof(BatchEntry));
 
-// The W = 4 update's per-lane constants of a row, from its prefetched values
-// (as LaneConsts::load computes them).
-template <int P>
-__device__ __forceinline__ LaneConsts<P> lane_consts(const SlotDesc &d, const RowFetch &f) {
-  LaneConsts<P> L;
-  L.kc2 = make_float2(d.kc, d.kc);
-  L.mka2 = make_float2(-f.ka, -f.ka);
-  L.kx2 = make_float2(d.kx, d.kx);
-  L.dnext = f.dnext;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) L.kj[q] = f.kj[q];
-  L.active = f.c0 < d.C;
-  L.Pr = d.Pr;
-  return L;
-}
-
-// One row from its ELL slots with W columns per lane: the gathers of its (at
-// most 8) neighbours, the sums in the CSR kernel's order, the update.
-template <int P, int W>
-__device__ __forceinline__ void batched_row_ell(const SlotDesc &d, const RowFetch &f) {
+// One row of a unit on a half warp (8 columns per lane): the gathers of its
+// neighbours' codes, the sums in the CSR kernel's order, the update.  col and
+// val point at the row's entries in shared memory or in the slot's ELL
+// arrays; act = false for the second row of a unit that ends past N (the
+// half repeats the first row's loads and stores nothing).
+template <int P, bool PM1, bool GEN>
+__device__ __forceinline__ void batched_unit_row(const SlotDesc &d, int n, int row, bool act, int c0, int deg,
+                                                 int npos, const int32_t *col, const float *val, float hi) {
+  constexpr int W = 8;
   StateView s;
   s.N = d.N; s.C = d.C; s.Cp = d.Cp; s.P = P; s.R = d.R; s.Pr = d.Pr;
   s.x = d.x; s.y = d.y; s.F[0] = d.F0; s.F[1] = d.F1; s.Sg = nullptr;
   s.Fx[0] = s.Fx[1] = nullptr;
-  const uint8_t *Fc = s.f_of(f.n) + f.c0;
-  const int deg = f.meta.x, npos = f.meta.y;
-  const bool pm1 = d.kind == VAL_PM1;
-  uint32_t f4[kEllSlots][W / 4];
+  StepTables t;
+  t.ka = d.ka; t.dl = d.dl; t.kj = d.kj; t.kc = d.kc; t.kx = d.kx; t.S = d.S; t.R = d.R;
+  const size_t off = size_t(row) * d.Cp + c0;
+  float xs[W], ys[W];
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const float4 xa = *reinterpret_cast<const float4 *>(d.x + off + 4 * u);
+    const float4 ya = *reinterpret_cast<const float4 *>(d.y + off + 4 * u);
+    xs[4 * u] = xa.x; xs[4 * u + 1] = xa.y; xs[4 * u + 2] = xa.z; xs[4 * u + 3] = xa.w;
+    ys[4 * u] = ya.x; ys[4 * u + 1] = ya.y; ys[4 * u + 2] = ya.z; ys[4 * u + 3] = ya.w;
+  }
+  const uint8_t *Fc = s.f_of(n) + c0;
+  uint32_t f4[kEllSlots][2];
 #pragma unroll
   for (int e = 0; e < kEllSlots; ++e) {
-    const int j = __shfl_sync(0xffffffffu, f.col, e);
     if (e < deg) {
-      if constexpr (W == 8) {
-        const uint2 v = __ldcg(reinterpret_cast<const uint2 *>(Fc + size_t(j) * d.Cp));
-        f4[e][0] = v.x;
-        f4[e][1] = v.y;
-      } else {
-        f4[e][0] = __ldcg(reinterpret_cast<const uint32_t *>(Fc + size_t(j) * d.Cp));
-      }
+      const uint2 v = __ldcg(reinterpret_cast<const uint2 *>(Fc + size_t(col[e]) * d.Cp));
+      f4[e][0] = v.x;
+      f4[e][1] = v.y;
     } else {
-#pragma unroll
-      for (int q = 0; q < W / 4; ++q) f4[e][q] = pm1 ? 0u : kFZero4;
+      f4[e][0] = f4[e][1] = PM1 ? 0u : kFZero4;
     }
   }
   float G[W];
-  if (pm1) {
-    uint32_t ap[W / 4], am[W / 4];
-#pragma unroll
-    for (int q = 0; q < W / 4; ++q) ap[q] = am[q] = 0;
+  if constexpr (PM1) {
+    uint32_t ap[2] = {0u, 0u}, am[2] = {0u, 0u};
 #pragma unroll
     for (int e = 0; e < kEllSlots; ++e) {
 #pragma unroll
-      for (int q = 0; q < W / 4; ++q) {
+      for (int q = 0; q < 2; ++q) {
         if (e < npos) ap[q] += f4[e][q];
         else am[q] += f4[e][q];
       }
@@ -204,39 +158,63 @@ __device__ __forceinline__ void batched_row_ell(const SlotDesc &d, const RowFetc
     for (int c = 0; c < W; ++c)
       G[c] = float(int((ap[c / 4] >> (8 * (c % 4))) & 0xffu) - int((am[c / 4] >> (8 * (c % 4))) & 0xffu) + bias);
   } else {
-    float g[W];
 #pragma unroll
-    for (int c = 0; c < W; ++c) g[c] = 0.f;
+    for (int c = 0; c < W; ++c) G[c] = 0.f;
 #pragma unroll
     for (int e = 0; e < kEllSlots; ++e) {
-      const float w = __shfl_sync(0xffffffffu, f.val, e);
-      if (e < deg) {
-        acc_codes<W>(g, w, f4[e]);
-      }
+      if (e < deg) acc_codes<W>(G, val[e], f4[e]);
     }
-#pragma unroll
-    for (int c = 0; c < W; ++c) G[c] = g[c];
   }
-  if constexpr (W == 4) {
-    if (P > 2 && d.Pr != P)
-      sb_update4c<P, true>(s, lane_consts<P>(d, f), f.row, f.c0, G, f.hi, f.x[0], f.y[0], s.f_of(f.n + 1));
-    else
-      sb_update4c<P, false>(s, lane_consts<P>(d, f), f.row, f.c0, G, f.hi, f.x[0], f.y[0], s.f_of(f.n + 1));
-  } else {
-    StepTables t;
-    t.ka = d.ka; t.dl = d.dl; t.kj = d.kj; t.kc = d.kc; t.kx = d.kx; t.S = d.S; t.R = d.R;
-    float xs[8] = {f.x[0].x, f.x[0].y, f.x[0].z, f.x[0].w, f.x[1].x, f.x[1].y, f.x[1].z, f.x[1].w};
-    float ys[8] = {f.y[0].x, f.y[0].y, f.y[0].z, f.y[0].w, f.y[1].x, f.y[1].y, f.y[1].z, f.y[1].w};
-    if (P > 2 && d.Pr != P) sb_updateW<P, 8, true>(s, t, f.ka, f.dnext, f.n, f.row, f.c0, G, f.hi, xs, ys, s.f_of(f.n + 1));
-    else sb_updateW<P, 8, false>(s, t, f.ka, f.dnext, f.n, f.row, f.c0, G, f.hi, xs, ys, s.f_of(f.n + 1));
-  }
+  const float ka = __ldg(d.ka + n), dnext = __ldg(d.dl + n + 1);
+  // an idle half takes part in the ring shuffles only (a column past C stores nothing)
+  sb_updateW<P, W, GEN>(s, t, ka, dnext, n, row, act ? c0 : d.C, G, hi, xs, ys, s.f_of(n + 1));
 }
 
 template <int P>
-__device__ __forceinline__ void batched_row(const SlotDesc &d, const RowFetch &f) {
-  if (!d.ell_col) batched_row_csr<P>(d, f.n, f.row, f.c0, f.x[0], f.y[0], f.hi);
-  else if (d.W == 8) batched_row_ell<P, 8>(d, f);
-  else batched_row_ell<P, 4>(d, f);
+__device__ __forceinline__ void batched_unit_p(const SlotDesc &d, int n, int row, bool act, int c0, int deg, int npos,
+                                               const int32_t *col, const float *val, float hi) {
+  const bool gen = P > 2 && d.Pr != P;
+  if (d.kind == VAL_PM1) {
+    if (gen) batched_unit_row<P, true, true>(d, n, row, act, c0, deg, npos, col, val, hi);
+    else batched_unit_row<P, true, false>(d, n, row, act, c0, deg, npos, col, val, hi);
+  } else {
+    if (gen) batched_unit_row<P, false, true>(d, n, row, act, c0, deg, npos, col, val, hi);
+    else batched_unit_row<P, false, false>(d, n, row, act, c0, deg, npos, col, val, hi);
+  }
+}
+
+// The lane's row of a unit (both halves of a warp run the same slot, so
+// every branch on the slot is warp-uniform).
+__device__ __forceinline__ void batched_unit(const SlotDesc &d, int n, int row, bool act, int c0, int deg, int npos,
+                                             const int32_t *col, const float *val, float hi) {
+  switch (d.P) {
+    case 1: batched_unit_p<1>(d, n, row, act, c0, deg, npos, col, val, hi); break;
+    case 2: batched_unit_p<2>(d, n, row, act, c0, deg, npos, col, val, hi); break;
+    case 4: batched_unit_p<4>(d, n, row, act, c0, deg, npos, col, val, hi); break;
+    case 8: batched_unit_p<8>(d, n, row, act, c0, deg, npos, col, val, hi); break;
+    case 16: batched_unit_p<16>(d, n, row, act, c0, deg, npos, col, val, hi); break;
+    case 32: batched_unit_p<32>(d, n, row, act, c0, deg, npos, col, val, hi); break;
+    case 64: batched_unit_p<64>(d, n, row, act, c0, deg, npos, col, val, hi); break;
+    default: batched_unit_p<128>(d, n, row, act, c0, deg, npos, col, val, hi); break;
+  }
+}
+
+// A row of an item of a slot without ELL form, on a whole warp.
+__device__ __forceinline__ void batched_item_row(const SlotDesc &d, int n, int row, int c4) {
+  const size_t off = size_t(row) * d.Cp + c4;
+  const float4 xv = *reinterpret_cast<const float4 *>(d.x + off);
+  const float4 yv = *reinterpret_cast<const float4 *>(d.y + off);
+  const float hi = __ldg(d.h + row);
+  switch (d.P) {
+    case 1: batched_row_csr<1>(d, n, row, c4, xv, yv, hi); break;
+    case 2: batched_row_csr<2>(d, n, row, c4, xv, yv, hi); break;
+    case 4: batched_row_csr<4>(d, n, row, c4, xv, yv, hi); break;
+    case 8: batched_row_csr<8>(d, n, row, c4, xv, yv, hi); break;
+    case 16: batched_row_csr<16>(d, n, row, c4, xv, yv, hi); break;
+    case 32: batched_row_csr<32>(d, n, row, c4, xv, yv, hi); break;
+    case 64: batched_row_csr<64>(d, n, row, c4, xv, yv, hi); break;
+    default: batched_row_csr<128>(d, n, row, c4, xv, yv, hi); break;
+  }
 }
 
 constexpr int kBatchSmemSlots = 64;  // slot descriptors kept in shared memory (more: read from global)
@@ -251,78 +229,82 @@ __device__ __forceinline__ const SlotDesc *stage_slots(SlotDesc *s_slots, const 
   return s_slots;
 }
 
-// Step j of the chunk for every active slot: the warps of the grid walk the
-// rows of the work items (a warp per row; the next row's loads go out before
-// this row's gathers).  A warp with no row returns from here only.
-__device__ __forceinline__ void batched_pass(const SlotDesc *D, const WorkItem *items, int total, int j) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int stride = gridDim.x * 8;
-  int u = blockIdx.x * 8 + warp;
-  if (u >= total) return;  // whole warp
-  RowFetch pf;
-  pf.col = 0;
-  pf.val = 0.f;
-  fetch_row(pf, D, items[u >> 3], u & 7, j, lane);
-  WorkItem w_after = u + stride < total ? items[(u + stride) >> 3] : WorkItem{0, 0, 0, 0};
-  for (; u < total; u += stride) {
-    const RowFetch cur = pf;
-    const int nx = u + stride;
-    if (nx < total) {  // warp-uniform: the next row's loads go out before this row's gathers
-      fetch_row(pf, D, w_after, nx & 7, j, lane);
-      if (nx + stride < total) w_after = items[(nx + stride) >> 3];
-    }
-    if (cur.row < 0) continue;
-    const SlotDesc &d = D[cur.slot];
-    switch (d.P) {
-      case 1: batched_row<1>(d, cur); break;
-      case 2: batched_row<2>(d, cur); break;
-      case 4: batched_row<4>(d, cur); break;
-      case 8: batched_row<8>(d, cur); break;
-      case 16: batched_row<16>(d, cur); break;
-      case 32: batched_row<32>(d, cur); break;
-      case 64: batched_row<64>(d, cur); break;
-      default: batched_row<128>(d, cur); break;
-    }
+// Entry `m` of unit w: the neighbours of its two rows (lanes 0-15: columns,
+// 16-31: values), then degrees and fields.
+__device__ __forceinline__ void fill_entry(BatchEntry &m, const SlotDesc *D, const WorkItem &w, int lane) {
+  const SlotDesc &d = D[w.slot];
+  const int h = (lane >> 3) & 1, e = lane & 7, row = w.row0 + h;
+  const bool ok = row < d.N;
+  if (lane < 16) m.col[h][e] = ok ? __ldg(d.ell_col + size_t(row) * kEllSlots + e) : 0;
+  else m.val[h][e] = (ok && d.kind != VAL_PM1) ? __ldg(d.ell_val + size_t(row) * kEllSlots + e) : 0.f;
+  if (lane < 2) {
+    const int r = w.row0 + lane;
+    const int2 meta = r < d.N ? __ldg(reinterpret_cast<const int2 *>(d.ell_meta) + r) : make_int2(0, 0);
+    m.degpos[lane] = uint32_t(meta.x) | (uint32_t(meta.y) << 8);
+    m.h[lane] = r < d.N ? __ldg(d.h + r) : 0.f;
   }
-}
-
-__global__ void __launch_bounds__(256, 2) k_step_batched(const SlotDesc *slots, int n_slots, const WorkItem *items,
-                                                      const int *n_items, int j) {
-  __shared__ SlotDesc s_slots[kBatchSmemSlots];
-  const SlotDesc *D = stage_slots(s_slots, slots, n_slots);
-  batched_pass(D, items, *n_items * 8, j);
+  if (lane == 0) {
+    m.slot = w.slot;
+    m.row0 = w.row0;
+    m.chunk = w.colgroup;
+  }
 }
 
 // Steps j0 .. j1 - 1 of the chunk for every active slot in one cooperative
-// launch (the grid exactly co-resident): one pass per step, the bounded grid
-// barrier between steps (each slot keeps its own step index n0 + j, and a
-// slot past its last step has no rows).  The f codes other blocks wrote in
-// the step before are read through L2.  A barrier that gives up records
-// error code 4 in *err and every block stops stepping.
-__global__ void __launch_bounds__(256, 2) k_solve_batched(const SlotDesc *slots, int n_slots, const WorkItem *items,
-                                                       const int *n_items, int j0, int j1, unsigned *bar, int *err) {
+// launch (the grid exactly co-resident).  counts[0] = units (2 rows x 128
+// columns of slots in ELL form, items[0 .. counts[0])), counts[1] = items of
+// 8 rows x 128 columns of the other slots (after the units).  Each slot keeps
+// its own step index n0 + j, and a slot past its last step does nothing.  The
+// f codes other blocks wrote in the step before are read through L2.  A
+// barrier that gives up records error code 4 in *err and every block stops
+// stepping.
+__global__ void __launch_bounds__(256, 3) k_solve_batched(const SlotDesc *slots, int n_slots, const WorkItem *items,
+                                                       const int *counts, int j0, int j1, unsigned *bar, int *err) {
   __shared__ SlotDesc s_slots[kBatchSmemSlots];
+  extern __shared__ BatchEntry s_entries[];
   const SlotDesc *D = stage_slots(s_slots, slots, n_slots);
-  const int total = *n_items * 8;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_units = counts[0], n_items = counts[1];
+  const int warps = gridDim.x * 8, gw = blockIdx.x * 8 + warp;
+  // this warp's units: a contiguous share (neighbouring units run the same code)
+  const int u_begin = int(int64_t(n_units) * gw / warps), u_end = int(int64_t(n_units) * (gw + 1) / warps);
+  const int cached = min(u_end - u_begin, kBatchEntriesPerWarp);
+  BatchEntry *mine = s_entries + warp * kBatchEntriesPerWarp;
+  for (int q = 0; q < cached; ++q) fill_entry(mine[q], D, items[u_begin + q], lane);
+  __syncwarp();
+  const int h = lane >> 4, c_lane = (lane & 15) * 8;
   unsigned k = 0;
   for (int j = j0; j < j1; ++j) {
-    batched_pass(D, items, total, j);
+    for (int q = 0; q < cached; ++q) {
+      const BatchEntry &m = mine[q];
+      const SlotDesc &d = D[m.slot];
+      const int n = d.n0 + j;
+      if (n >= d.S) continue;  // the request has finished (warp-uniform)
+      const bool act = m.row0 + h < d.N;
+      const uint32_t dp = m.degpos[h];
+      batched_unit(d, n, act ? m.row0 + h : m.row0, act, m.chunk * kColsPerWarp + c_lane, act ? int(dp & 0xffu) : 0,
+                   int(dp >> 8), m.col[h], m.val[h], m.h[h]);
+    }
+    for (int u = u_begin + cached; u < u_end; ++u) {  // past this warp's shared-memory share
+      const WorkItem w = items[u];
+      const SlotDesc &d = D[w.slot];
+      const int n = d.n0 + j;
+      if (n >= d.S) continue;
+      const bool act = w.row0 + h < d.N;
+      const int row = act ? w.row0 + h : w.row0;
+      const int2 meta = __ldg(reinterpret_cast<const int2 *>(d.ell_meta) + row);
+      batched_unit(d, n, row, act, w.colgroup * kColsPerWarp + c_lane, act ? meta.x : 0, meta.y,
+                   d.ell_col + size_t(row) * kEllSlots, d.ell_val + size_t(row) * kEllSlots, __ldg(d.h + row));
+    }
+    for (int r = gw; r < n_items * 8; r += warps) {  // the other slots' rows, a row per warp
+      const WorkItem w = items[n_units + (r >> 3)];
+      const SlotDesc &d = D[w.slot];
+      const int n = d.n0 + j, row = w.row0 + (r & 7);
+      if (n >= d.S || row >= d.N) continue;
+      batched_item_row(d, n, row, w.colgroup * kColsPerWarp + lane * 4);
+    }
     if (j + 1 < j1 && !grid_barrier(bar, ++k, err)) break;
   }
-}
-
-int batched_blocks_per_sm() {
-  static int per_sm = 0;
-  if (per_sm == 0 && (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step_batched, 256, 0) != cudaSuccess ||
-                      per_sm < 1))
-    per_sm = 1;
-  return per_sm;
-}
-
-cudaError_t launch_step_batched(const SlotDesc *slots, int n_slots, const WorkItem *items, const int *n_items,
-                                int grid, int j, cudaStream_t st) {
-  k_step_batched<<<grid, 256, 0, st>>>(slots, n_slots, items, n_items, j);
-  return cudaGetLastError();
 }
 
 int batched_persistent_blocks() {
@@ -331,19 +313,23 @@ int batched_persistent_blocks() {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_batched, 256, 0) != cudaSuccess) per_sm = 0;
+    if (cudaFuncSetAttribute((const void *)k_solve_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kBatchSmem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_batched, 256, kBatchSmem) != cudaSuccess)
+      per_sm = 0;
     blocks = sms * per_sm;
   }
   return blocks;
 }
 
-cudaError_t launch_solve_batched(const SlotDesc *slots, int n_slots, const WorkItem *items, const int *n_items,
+cudaError_t launch_solve_batched(const SlotDesc *slots, int n_slots, const WorkItem *items, const int *counts,
                                  int grid, int j0, int j1, unsigned *bar, int *err, cudaStream_t st) {
+  if (batched_persistent_blocks() <= 0) return cudaErrorInvalidConfiguration;
   cudaError_t e = cudaMemsetAsync(bar, 0, grid_barrier_words() * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
-  void *args[] = {(void *)&slots, (void *)&n_slots, (void *)&items, (void *)&n_items, (void *)&j0, (void *)&j1,
+  void *args[] = {(void *)&slots, (void *)&n_slots, (void *)&items, (void *)&counts, (void *)&j0, (void *)&j1,
                   (void *)&bar, (void *)&err};
-  return cudaLaunchCooperativeKernel((const void *)k_solve_batched, dim3(grid), dim3(256), args, 0, st);
+  return cudaLaunchCooperativeKernel((const void *)k_solve_batched, dim3(grid), dim3(256), args, kBatchSmem, st);
 }
 
 }  // namespace sbqa
