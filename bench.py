@@ -256,6 +256,51 @@ def run_reference(args, cfg):
 
 
 # ------------------------------------------------------------------ serving stream
+def batched_csr_roofline(serving, reqs, stream, arena):
+    """The engine's CSR chunk kernel alone: a closed loop of the stream's
+    lattice requests (no dense work beside it), event-timed launches."""
+    lat_reqs = [r for r in reqs if r["inst"]["kind"] == "lattice"]
+    csr = serving.run_stream(lat_reqs, None, stream=stream, arena_bytes=arena)
+    achieved = BYTES_PER_UPDATE * csr["batched_updates"] / (csr["batched_ms"] * 1e-3) / 1e9
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        peaks = {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    per_step = sum(r["inst"]["n"] * r["P"] * r["R"] for r in lat_reqs)
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+            "traffic": None, "kernel": "k_solve_batched",
+            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+            "algorithmic_bytes_per_step": BYTES_PER_UPDATE * per_step,
+            "note": "closed loop of the %d lattice requests alone: algorithmic %d B/update x the updates the "
+                    "batched kernel advanced / its event-timed launches" % (len(lat_reqs), BYTES_PER_UPDATE)}
+
+
+def run_serving_csr(args):
+    """`--config serving_csr`: the closed loop of the serving stream's lattice
+    requests alone (the engine's CSR chunk kernel), each request of
+    --request-steps steps; prints the kernel's roofline record."""
+    import torch
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    from paper_2604_01050_gb300 import build as _b
+    _b.build()
+    from paper_2604_01050_gb300 import serving
+    pool = serving.make_pool(12, seed=0)
+    reqs = serving.make_requests(pool, args.requests, steps=args.request_steps, R=16, seed=1)
+    arena = int(args.arena_gb * (1 << 30))
+    lat = [r for r in reqs if r["inst"]["kind"] == "lattice"]
+    serving.run_stream(lat[:4], None, stream=stream, arena_bytes=arena)  # warm-up
+    roof = batched_csr_roofline(serving, reqs, stream, arena)
+    print(json.dumps({"config": {"workload": "closed loop of the lattice requests of the serving stream "
+                                             "(%d of %d requests, %d steps each)" % (len(lat), len(reqs),
+                                                                                     args.request_steps)},
+                      "roofline": roof}))
+    for inst in pool:
+        inst["problem"].destroy()
+    return 0
+
+
 def run_serving(args, stream=None):
     """Poisson stream through the batching engine: p50/p99 latency.  Returns
     the JSON record."""
@@ -283,20 +328,7 @@ def run_serving(args, stream=None):
         out = serving.run_stream(reqs, rate, stream=stream, seed=int(rate), arena_bytes=arena)
         loads["%.0f/s" % rate] = serving.summary(out)
     head = loads["0.8x"]
-    # the batched CSR kernel alone: a closed loop of the lattice requests (no dense work beside it)
-    lat_reqs = [r for r in reqs if r["inst"]["kind"] == "lattice"]
-    csr = serving.run_stream(lat_reqs, None, stream=stream, arena_bytes=arena)
-    achieved = BYTES_PER_UPDATE * csr["batched_updates"] / (csr["batched_ms"] * 1e-3) / 1e9
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        peaks = {}
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-            "traffic": None, "kernel": "k_solve_batched",
-            "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-            "note": "closed loop of the %d lattice requests alone: algorithmic %d B/update x the updates the "
-                    "batched kernel advanced / its event-timed launches" % (len(lat_reqs), BYTES_PER_UPDATE)}
+    roof = batched_csr_roofline(serving, reqs, stream, arena)
     cpu = None
     if not args.no_cpu_baseline:
         # the oracle on one typical request (lattice L=16, P=16, R=16, 2000 steps), bounded sample
@@ -886,7 +918,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--config", default="default",
-                    choices=["default"] + sorted(CONFIGS) + ["serving", "tte", "scaling", "sweep", "fp8peak"],
+                    choices=["default"] + sorted(CONFIGS) + ["serving", "serving_csr", "tte", "scaling", "sweep",
+                                                             "fp8peak"],
                     help="default: the random 6-regular N=1e5 headline with per-config records of the lattice "
                          "L=16, dense SK N=2000 and the serving stream; a config name measures that config alone")
     ap.add_argument("--kernel-select", type=int, default=0,
@@ -899,6 +932,7 @@ def main():
     ap.add_argument("--ref-seconds", type=float, default=15.0)
     ap.add_argument("--requests", type=int, default=48, help="serving: requests in the stream")
     ap.add_argument("--arena-gb", type=float, default=40.0, help="serving: device arena of the engine (GB)")
+    ap.add_argument("--request-steps", type=int, default=2000, help="serving_csr: steps of each request")
     ap.add_argument("--eps", type=float, default=0.08, help="tte: target optimality gap of the headline")
     ap.add_argument("--gamma0", type=float, default=16.0, help="tte: Gamma_x(0)")
     ap.add_argument("--tte-L", type=int, default=10)
@@ -909,6 +943,8 @@ def main():
     if args.config == "serving":
         print(json.dumps(run_serving(args)))
         return 0
+    if args.config == "serving_csr":
+        return run_serving_csr(args)
     if args.config == "tte":
         return run_tte(args)
     if args.config == "scaling":
