@@ -158,6 +158,12 @@ typedef struct {
     float persistent_ms;  /* autotuner timing of the persistent solver of
                              the path in use, CSR or dense tcgen05 (ms per
                              step; 0 = not timed / not eligible)          */
+    int32_t j_on_device;  /* 1: a dense J of N >= 1024 read by the GPU from
+                             the caller's array (systems where the GPU
+                             reaches pageable host memory through the
+                             host's page tables), with its checks and
+                             statistics, and the library's copy kept in
+                             device memory; 0: read on the host            */
 } sbqa_problem_info;
 
 int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info);

@@ -56,7 +56,7 @@ class ProblemInfo(ctypes.Structure):
                 ("is_integer", ctypes.c_int32), ("max_abs_j", ctypes.c_int32),
                 ("c0_auto", ctypes.c_double), ("step_kernel", ctypes.c_int32),
                 ("step_variant", ctypes.c_int32), ("variant_ms", ctypes.c_float * 8),
-                ("persistent_ms", ctypes.c_float)]
+                ("persistent_ms", ctypes.c_float), ("j_on_device", ctypes.c_int32)]
 
 
 class EngineStats(ctypes.Structure):

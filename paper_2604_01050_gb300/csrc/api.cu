@@ -226,6 +226,7 @@ sbqa_problem::~sbqa_problem() {
   d_row_ptr.release(true); d_col.release(true); d_col_pm1.release(true); d_npos.release(true); d_val_f32.release(true);
   d_val_bf16.release(true); d_dense_f32.release(true); d_h.release(true); d_e_i32.release(true);
   d_e_f64.release(true); d_h_i64.release(true); d_h_f64.release(true); d_x.release(true); d_y.release(true);
+  d_jcopy_i8.release(true);
   d_F0.release(true); d_F1.release(true); d_Fx0.release(true); d_Fx1.release(true); d_Sg.release(true);
   d_ell_col.release(true); d_ell_meta.release(true); d_ell_val.release(true); d_ka.release(true); d_dl.release(true);
   d_kj.release(true); d_ei.release(true); d_part_i.release(true); d_best_ei.release(true); d_ef.release(true);
@@ -238,6 +239,7 @@ sbqa_problem::~sbqa_problem() {
 namespace {
 
 constexpr int kTcMinN = 256;  // smaller dense instances stay on the CUDA-core kernel
+constexpr int kIngestMinN = 1024;  // dense J from N = 1024 on is read by the GPU where it can
 // EXACT precision takes integer J up to this magnitude: the products are exact
 // in bfloat16 (and e4m3 up to 16) and every partial sum, an integer below
 // 256 N < 2^24 for N < 65536, is exact in FP32
@@ -342,7 +344,19 @@ int upload_common(sbqa_problem *p) {
 
 int upload_readout_values(sbqa_problem *p) {
   const size_t m = p->jcount();
-  if (m == 0) return SBQA_OK;
+  if (m == 0 || (p->is_integer ? p->d_e_i32.p != nullptr : p->d_e_f64.p != nullptr)) return SBQA_OK;
+  if (p->j_on_device) {  // converted from the device copy
+    const int8_t *d8 = p->d_jcopy_i8.p;
+    if (p->is_integer) {
+      SBQA_CUDA(p->d_e_i32.alloc(m));
+      SBQA_CUDA(launch_flat_from_device(d8, p->d_e_f64.p, m, kFlatI32, p->d_e_i32.p, nullptr));
+    } else {  // integer J beside a real h (a real J's FP64 copy is already d_e_f64)
+      SBQA_CUDA(p->d_e_f64.alloc(m));
+      SBQA_CUDA(launch_flat_from_device(d8, nullptr, m, kFlatF64, p->d_e_f64.p, nullptr));
+    }
+    SBQA_CUDA(cudaStreamSynchronize(nullptr));
+    return SBQA_OK;
+  }
   const int64_t blk = 1 << 16, tasks = (int64_t(m) + blk - 1) / blk;
   if (p->is_integer) {
     HostVec<int32_t> vi(m);
@@ -482,6 +496,15 @@ uint8_t e4m3_of_int(int v) {
 // |J_ij| <= 256), zero padding to Kp.
 int prepare_tc_values_bf16(sbqa_problem *p) {
   const int N = p->n, Kp = (N + 127) / 128 * 128;
+  if (p->j_on_device) {
+    SBQA_CUDA(p->d_J8.alloc(size_t(Kp) * Kp * 2));
+    SBQA_CUDA(launch_tc_jbf16_from_device(p->d_jcopy_i8.p, p->d_e_f64.p, N, Kp,
+                                          reinterpret_cast<uint16_t *>(p->d_J8.p), nullptr));
+    SBQA_CUDA(cudaStreamSynchronize(nullptr));
+    p->Kp = Kp;
+    p->j_tc_op = p->tc_op;
+    return SBQA_OK;
+  }
   HostVec<uint16_t> jb(size_t(Kp) * Kp);
   parallel_tasks(Kp, [&](int64_t i, int64_t) {
     uint16_t *out = jb.data() + size_t(i) * Kp;
@@ -507,6 +530,14 @@ int prepare_tc_values(sbqa_problem *p) {
   }
   if (bf) return prepare_tc_values_bf16(p);
   const int N = p->n, Kp = (N + 127) / 128 * 128;
+  if (p->j_on_device) {  // integer |J_ij| <= 16: the byte copy is on the device
+    SBQA_CUDA(p->d_J8.alloc(size_t(Kp) * Kp));
+    SBQA_CUDA(launch_tc_j8_from_device(p->d_jcopy_i8.p, N, Kp, p->d_J8.p, nullptr));
+    SBQA_CUDA(cudaStreamSynchronize(nullptr));
+    p->Kp = Kp;
+    p->j_tc_op = kTcOpF8;
+    return SBQA_OK;
+  }
   HostVec<uint8_t> j8(size_t(Kp) * Kp);  // every byte is written below (zeros in the padding)
   uint8_t lut[33];  // e4m3 of -16 .. 16 (the tensor-core path takes |J_ij| <= 16)
   for (int v = -16; v <= 16; ++v) lut[v + 16] = e4m3_of_int(v);
@@ -562,16 +593,24 @@ int prepare_dense_values(sbqa_problem *p, int precision) {
     // the readout runs on the tensor cores too when its energies are integers
     // and the product is e4m3; otherwise on the CUDA cores (exact int64 or FP64)
     const int rc = prepare_tc_values(p);
-    if (rc != SBQA_OK || (p->is_integer && op == kTcOpF8) || p->d_e_f64.p || p->d_e_i32.p) return rc;
+    if (rc != SBQA_OK || (p->is_integer && op == kTcOpF8)) return rc;
     return upload_readout_values(p);
   }
-  if (!p->d_e_i32.p && !p->d_e_f64.p) {
+  {
     const int rc = upload_readout_values(p);
     if (rc != SBQA_OK) return rc;
   }
   const int want = precision == SBQA_PREC_BF16 ? SBQA_PREC_BF16 : SBQA_PREC_FP32;
   if (p->d_dense_f32.p && p->dense_prec == want) return SBQA_OK;
   const size_t m = p->jcount();
+  if (p->j_on_device) {
+    SBQA_CUDA(p->d_dense_f32.alloc(m));
+    SBQA_CUDA(launch_flat_from_device(p->d_jcopy_i8.p, p->d_e_f64.p, m,
+                                      want == SBQA_PREC_BF16 ? kFlatBf16InF32 : kFlatF32, p->d_dense_f32.p, nullptr));
+    SBQA_CUDA(cudaStreamSynchronize(nullptr));
+    p->dense_prec = want;
+    return SBQA_OK;
+  }
   HostVec<float> v(m);
   const int64_t blk = 1 << 16;
   parallel_tasks((int64_t(m) + blk - 1) / blk, [&](int64_t t, int64_t) {
@@ -1108,6 +1147,84 @@ int sbqa::problem_build_tables(const sbqa_problem *p, int S, int P, int R, float
   return SBQA_OK;
 }
 
+// sbqa_create_problem_dense with the checks, statistics and the library's
+// copy of J made on the GPU from the caller's array (ingest_dense.cu): the
+// same errors, in the same order, and the same analysis as the host pass
+// (the rows' sums of squares added in row order).
+static int create_dense_on_device(int32_t n, const double *J, const double *h, sbqa_problem **out) {
+  const size_t m = size_t(n) * n;
+  sbqa_problem *p = new (std::nothrow) sbqa_problem();
+  if (!p) return fail(SBQA_ERR_OOM, "host allocation");
+  cudaGetDevice(&p->device);
+  DevBuf<int8_t> d8;
+  DevBuf<double> d64;
+  DevBuf<IngestRow> drows;
+  DevBuf<int> dasym;
+  std::vector<IngestRow> rows(n);
+  int asym = 0;
+  auto cuda_fail = [&](cudaError_t e) {
+    d8.release(); d64.release(); drows.release(); dasym.release();
+    delete p;
+    return fail(e == cudaErrorMemoryAllocation ? SBQA_ERR_OOM : SBQA_ERR_CUDA,
+                std::string("dense J on the device: ") + cudaGetErrorString(e));
+  };
+  cudaError_t e;
+  if ((e = d8.alloc(m)) != cudaSuccess || (e = d64.alloc(m)) != cudaSuccess || (e = drows.alloc(n)) != cudaSuccess ||
+      (e = dasym.alloc(1)) != cudaSuccess)
+    return cuda_fail(e);
+  if ((e = launch_ingest_dense(J, n, d8.p, d64.p, drows.p, dasym.p, nullptr)) != cudaSuccess ||
+      (e = cudaMemcpy(rows.data(), drows.p, size_t(n) * sizeof(IngestRow), cudaMemcpyDeviceToHost)) != cudaSuccess ||
+      (e = cudaMemcpy(&asym, dasym.p, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e);
+  drows.release(true);
+  dasym.release(true);
+  bool finite = !h || finite_all(h, n), diag = true;
+  int64_t nnz = 0;
+  int32_t maxdeg = 0;
+  JStats js;
+  for (const IngestRow &r : rows) {
+    finite = finite && (r.flags & kIngestFinite);
+    diag = diag && (r.flags & kIngestDiagZero);
+    js.j_int = js.j_int && (r.flags & kIngestInteger);
+    js.pm1 = js.pm1 && (r.flags & kIngestPm1);
+    js.mx = std::max(js.mx, r.mx);
+    js.s2 += r.s2;
+    nnz += r.nnz;
+    maxdeg = std::max(maxdeg, r.nnz);
+  }
+  auto reject = [&](int code, const char *msg) {
+    d8.release(true); d64.release(true);
+    delete p;
+    return fail(code, msg);
+  };
+  if (!finite) return reject(SBQA_ERR_NOT_FINITE, "J or h not finite");
+  if (!diag) return reject(SBQA_ERR_NOT_SYMMETRIC, "nonzero diagonal");
+  if (asym) return reject(SBQA_ERR_NOT_SYMMETRIC, "J != J^T");
+  p->n = n;
+  p->dense = true;
+  p->j_on_device = true;
+  if (js.j_int && js.mx <= 127.0) {
+    p->d_jcopy_i8 = d8;
+    d64.release(true);
+  } else {
+    p->d_e_f64 = d64;  // the FP64 values (also the readout's copy)
+    d8.release(true);
+  }
+  d8 = DevBuf<int8_t>();
+  d64 = DevBuf<double>();
+  if (h) p->h.assign(h, h + n);
+  p->nnz = nnz;
+  p->max_degree = maxdeg;
+  finish_analysis(p, js);
+  const int rc = upload_common(p);
+  if (rc != SBQA_OK) {
+    delete p;
+    return rc;
+  }
+  *out = p;
+  return SBQA_OK;
+}
+
 CsrView sbqa::problem_csr_view(const sbqa_problem *p) { return p->csr(); }
 CsrView sbqa::problem_csr_readout_view(const sbqa_problem *p) { return p->csr_readout(); }
 EnergyView sbqa::problem_energy_view(const sbqa_problem *p) { return p->energy(); }
@@ -1161,6 +1278,10 @@ int sbqa_create_problem_dense(int32_t n, const double *J, const double *h, sbqa_
   if (!out) return fail(SBQA_ERR_INVALID_ARG, "out is null");
   *out = nullptr;
   if (n < 1 || n > 65536 || !J) return fail(SBQA_ERR_INVALID_ARG, "need 1 <= n <= 65536 and J != NULL");
+  // test hook: SBQA_TEST_HOST_INGEST=1 keeps the host pass where the GPU could
+  // read J itself (not for production use)
+  if (n >= kIngestMinN && ingest_on_device_possible() && !std::getenv("SBQA_TEST_HOST_INGEST"))
+    return create_dense_on_device(n, J, h, out);
   const size_t m = size_t(n) * n;
   // One pass over blocks of 64 rows, spread over host threads: finiteness, the
   // diagonal, row degrees and the value statistics of each block, and the
@@ -1364,6 +1485,7 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info) {
   info->persistent_ms = p->use_tc ? p->tc_persistent_ms : p->persistent_ms;
   info->step_variant = p->dense ? -1 : p->csr_variant;
   for (int v = 0; v < 8; ++v) info->variant_ms[v] = p->use_tc ? (v == 0 ? p->tc_step_ms : 0.f) : p->variant_ms[v];
+  info->j_on_device = p->j_on_device ? 1 : 0;
   return SBQA_OK;
 }
 

@@ -134,6 +134,29 @@ cudaError_t launch_solve_dense_tc_persistent(const void *plan, const StateView &
                                              const StepTables &t, int n_begin, int n_end, uint32_t *flags,
                                              cudaStream_t st);
 
+// Dense J read by the GPU from the caller's host array (ingest_dense.cu),
+// where the GPU reaches pageable host memory through the host's page tables.
+// Per row: max |J_ij|, the sum of squares, the nonzeros and the flags below;
+// d8 / d64 [N][N] receive the byte copy (int(v) for v in [-128, 127], else 0)
+// and the FP64 copy; *asym becomes nonzero when J != J^T.
+struct IngestRow {
+  double mx, s2;
+  int32_t nnz;
+  uint32_t flags;
+};
+constexpr uint32_t kIngestFinite = 1, kIngestDiagZero = 2, kIngestInteger = 4, kIngestPm1 = 8;
+bool ingest_on_device_possible();
+cudaError_t launch_ingest_dense(const double *J, int n, int8_t *d8, double *d64, IngestRow *rows, int *asym,
+                                cudaStream_t st);
+// Device forms from the device copy (d8 when it holds J, else d64): padded
+// e4m3 (|J_ij| <= 16) and bfloat16 operands [Kp][Kp], and flat [N][N] forms.
+constexpr int kFlatI32 = 0, kFlatF64 = 1, kFlatF32 = 2, kFlatBf16InF32 = 3;
+cudaError_t launch_tc_j8_from_device(const int8_t *d8, int n, int Kp, uint8_t *out, cudaStream_t st);
+cudaError_t launch_tc_jbf16_from_device(const int8_t *d8, const double *d64, int n, int Kp, uint16_t *out,
+                                        cudaStream_t st);
+cudaError_t launch_flat_from_device(const int8_t *d8, const double *d64, size_t m, int form, void *out,
+                                    cudaStream_t st);
+
 // Several dense problems' chunks in one cooperative launch of the persistent
 // tensor-core solver (solve_dense_tc_batched.cu): one CTA per 128 x 128 tile
 // of each problem, tiles of one problem consecutive; the problems of a batch

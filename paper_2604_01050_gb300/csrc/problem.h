@@ -128,7 +128,15 @@ struct sbqa_problem {
   std::vector<int32_t> col;
   sbqa::HostVec<double> val;  // CSR values or dense N*N (empty when val_i8 holds the dense copy)
   sbqa::HostVec<int8_t> val_i8;  // dense integer J with |J_ij| <= 127, one byte per entry
-  size_t jcount() const { return val_i8.empty() ? val.size() : val_i8.size(); }
+  // dense J read by the GPU from the caller's array: the library's copy is on
+  // the device (d_jcopy_i8 for integer |J_ij| <= 127, else the FP64 values in
+  // d_e_f64) and the host copies above stay empty
+  bool j_on_device = false;
+  sbqa::DevBuf<int8_t> d_jcopy_i8;
+  size_t jcount() const {
+    if (j_on_device) return size_t(n) * size_t(n);
+    return val_i8.empty() ? val.size() : val_i8.size();
+  }
   double jv(size_t e) const { return val_i8.empty() ? val[e] : double(val_i8[e]); }
   std::vector<double> h;
 
