@@ -301,6 +301,67 @@ def run_serving_csr(args):
     return 0
 
 
+def plain_serving_compare(serving, pool, reqs, stream, arena, k=8, steps=200):
+    """The first k requests of the stream (each cut to `steps` steps) through
+    the engine (closed loop) and through the plain per-instance FP32 GPU path
+    (torch ops per step, one request after another, readout of the best
+    energy per run included), on the same device; replica-spin updates per
+    second of each.  The couplings of both sides are resident beforehand."""
+    import math
+    import torch
+    import paper_2604_01050_gb300 as sb
+    dev = torch.device("cuda", torch.cuda.current_device())
+    sample = [dict(r, steps=steps) for r in reqs[:k]]
+    updates = sum(r["inst"]["n"] * r["P"] * r["R"] * steps for r in sample)
+    serving.run_stream(sample[:2], None, stream=stream, arena_bytes=arena)  # warm-up
+    eng = serving.run_stream(sample, None, stream=stream, arena_bytes=arena)
+    mats = {}
+    for r in sample:
+        q = pool.index(r["inst"])
+        if q in mats:
+            continue
+        pb = r["inst"]["problem"]
+        ht = None
+        if r["inst"]["kind"] == "sk":
+            J, _ = workloads.sk_pm1(r["inst"]["n"], q)
+            Jt = torch.tensor(J, dtype=torch.float32, device=dev)
+        else:
+            L = round(r["inst"]["n"] ** (1.0 / 3.0))
+            n, rp, col, val, h = workloads.cubic_lattice(L, q)
+            Jt = torch.sparse_csr_tensor(torch.tensor(rp), torch.tensor(col.astype(np.int64)), torch.tensor(val),
+                                         size=(n, n), dtype=torch.float32, device=dev)
+            ht = None if h is None else torch.tensor(h, dtype=torch.float32, device=dev)
+        beta, alpha = workloads.autotune_params(r["R"], q)
+        mats[q] = (Jt, ht, beta, alpha, pb.info().c0_auto)
+
+    def plain(r, S):
+        Jt, ht, beta, alpha, c0 = mats[pool.index(r["inst"])]
+        n, P, R = r["inst"]["n"], r["P"], r["R"]
+        ka, dl, kj = schedule_tables(S, P, R, beta, alpha)
+        tabs = tuple(torch.tensor(t, dtype=torch.float32, device=dev) for t in (ka, dl, kj))
+        g = torch.Generator(device=dev).manual_seed(r["seed"] % (1 << 31))
+        x0 = (torch.rand(n, R * P, generator=g, device=dev) - 0.5) * 0.2
+        y0 = (torch.rand(n, R * P, generator=g, device=dev) - 0.5) * 0.2
+        xf = plain_fp32_solve(Jt, ht, S, P, R, x0, y0, tabs, 0.5 * c0 / P, 0.5 / P, dev)
+        spins = torch.where(xf >= 0, 1.0, -1.0)
+        e = -0.5 * (spins * (Jt @ spins)).sum(dim=0).double()
+        return e.view(R, P).min(dim=1).values.cpu()
+
+    plain(sample[0], 5)  # warm-up (library handles, kernels)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r in sample:
+        plain(r, steps)
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    return {"requests": k, "steps_per_request": steps,
+            "engine_updates_per_s": updates / eng["makespan_s"], "engine_s": eng["makespan_s"],
+            "plain_fp32_updates_per_s": updates / t_plain, "plain_fp32_s": t_plain,
+            "speedup": t_plain / eng["makespan_s"] if eng["makespan_s"] > 0 else math.inf,
+            "plain_path": "torch FP32: dense matmul (SK) or CSR SpMM (lattice) per step, then the update, wall and "
+                          "threshold as separate elementwise ops; requests one after another"}
+
+
 def run_serving(args, stream=None):
     """Poisson stream through the batching engine: p50/p99 latency.  Returns
     the JSON record."""
@@ -329,6 +390,7 @@ def run_serving(args, stream=None):
         loads["%.0f/s" % rate] = serving.summary(out)
     head = loads["0.8x"]
     roof = batched_csr_roofline(serving, reqs, stream, arena)
+    vs_plain = plain_serving_compare(serving, pool, reqs, stream, arena)
     cpu = None
     if not args.no_cpu_baseline:
         # the oracle on one typical request (lattice L=16, P=16, R=16, 2000 steps), bounded sample
@@ -350,6 +412,7 @@ def run_serving(args, stream=None):
                        "without_dense_batching": {"capacity_req_per_s": len(reqs) / unbatched["makespan_s"],
                                                   "launches": unbatched["kernels_launched"]}},
             "p50_s": head["p50_s"], "loads": loads, "gpu_launches": head["kernels_launched"],
+            "vs_plain_fp32_path": vs_plain,
             "roofline": roof, "cpu_baseline": cpu}
     for inst in pool:
         inst["problem"].destroy()
