@@ -563,9 +563,8 @@ int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done, int32_t *don
       ENG_CUDA(cudaEventCreate(&e->batched_t1));
     }
     // every CSR request's chunk in one cooperative launch, replayed from a captured graph
-    // a block per 8 warp tasks (a unit, or a row of an item), at most one co-resident wave
-    const int64_t tasks = int64_t(counts[0]) + 8 * int64_t(counts[1]);
-    const int grid = int(std::max<int64_t>(1, std::min<int64_t>((tasks + 7) / 8, batched_persistent_blocks())));
+    // a warp per task (a unit, or a row of an item), at most one co-resident wave
+    const int grid = batched_grid(int64_t(counts[0]) + 8 * int64_t(counts[1]));
     if ((rc = csr_chunk_graph(e, grid)) != SBQA_OK) return rc;
     ENG_CUDA(cudaEventRecord(e->batched_t0, st));
     if (e->csr_graph) {

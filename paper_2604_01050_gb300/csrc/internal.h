@@ -278,6 +278,7 @@ cudaError_t launch_f_to_ft(const StateView &s, int which, uint8_t *FT, int Kp, i
 // device memory.  bar holds grid_barrier_words() counters (zeroed here); a
 // barrier that gives up records code 4 in *err.
 int batched_persistent_blocks();
+int batched_grid(int64_t tasks);  // blocks for `tasks` warp tasks (units, or rows of items), at most one wave
 cudaError_t launch_solve_batched(const SlotDesc *slots, int n_slots, const WorkItem *items, const int *counts,
                                  int grid, int j0, int j1, unsigned *bar, int *err, cudaStream_t st);
 

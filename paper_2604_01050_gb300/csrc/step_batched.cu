@@ -103,8 +103,9 @@ struct BatchEntry {
 };
 static_assert(sizeof(BatchEntry) % 16 == 0, "entries start on 16-byte boundaries");
 
-constexpr int kBatchEntriesPerWarp = 48;  // 8 warps x 48 x 160 B = 61.4 KB of shared memory per block (3 blocks per SM)
-constexpr int kBatchSmem = 8 * kBatchEntriesPerWarp * int(sizeof(BatchEntry));
+constexpr int kBatchThreads = 256, kBatchWarps = kBatchThreads / 32, kBatchBlocksPerSM = 3;
+constexpr int kBatchEntriesPerWarp = 48;  // x 160 B per warp: 61.4 KB of shared memory per block of 8 warps
+constexpr int kBatchSmem = kBatchWarps * kBatchEntriesPerWarp * int(sizeof(BatchEntry));
 
 // One row of a unit on a half warp (8 columns per lane): the gathers of its
 // neighbours' codes, the sums in the CSR kernel's order, the update.  col and
@@ -258,14 +259,15 @@ __device__ __forceinline__ void fill_entry(BatchEntry &m, const SlotDesc *D, con
 // f codes other blocks wrote in the step before are read through L2.  A
 // barrier that gives up records error code 4 in *err and every block stops
 // stepping.
-__global__ void __launch_bounds__(256, 3) k_solve_batched(const SlotDesc *slots, int n_slots, const WorkItem *items,
-                                                       const int *counts, int j0, int j1, unsigned *bar, int *err) {
+__global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSM)
+    k_solve_batched(const SlotDesc *slots, int n_slots, const WorkItem *items, const int *counts, int j0, int j1,
+                    unsigned *bar, int *err) {
   __shared__ SlotDesc s_slots[kBatchSmemSlots];
   extern __shared__ BatchEntry s_entries[];
   const SlotDesc *D = stage_slots(s_slots, slots, n_slots);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_units = counts[0], n_items = counts[1];
-  const int warps = gridDim.x * 8, gw = blockIdx.x * 8 + warp;
+  const int warps = gridDim.x * kBatchWarps, gw = blockIdx.x * kBatchWarps + warp;
   // this warp's units: a contiguous share (neighbouring units run the same code)
   const int u_begin = int(int64_t(n_units) * gw / warps), u_end = int(int64_t(n_units) * (gw + 1) / warps);
   const int cached = min(u_end - u_begin, kBatchEntriesPerWarp);
@@ -307,6 +309,12 @@ __global__ void __launch_bounds__(256, 3) k_solve_batched(const SlotDesc *slots,
   }
 }
 
+int batched_grid(int64_t tasks) {
+  const int64_t blocks = (tasks + kBatchWarps - 1) / kBatchWarps;
+  const int most = batched_persistent_blocks();
+  return int(blocks < 1 ? 1 : (blocks < most ? blocks : (most > 0 ? most : 1)));
+}
+
 int batched_persistent_blocks() {
   static int blocks = -1;
   if (blocks < 0) {
@@ -315,7 +323,8 @@ int batched_persistent_blocks() {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (cudaFuncSetAttribute((const void *)k_solve_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              kBatchSmem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_batched, 256, kBatchSmem) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_batched, kBatchThreads, kBatchSmem) !=
+            cudaSuccess)
       per_sm = 0;
     blocks = sms * per_sm;
   }
@@ -329,7 +338,8 @@ cudaError_t launch_solve_batched(const SlotDesc *slots, int n_slots, const WorkI
   if (e != cudaSuccess) return e;
   void *args[] = {(void *)&slots, (void *)&n_slots, (void *)&items, (void *)&counts, (void *)&j0, (void *)&j1,
                   (void *)&bar, (void *)&err};
-  return cudaLaunchCooperativeKernel((const void *)k_solve_batched, dim3(grid), dim3(256), args, kBatchSmem, st);
+  return cudaLaunchCooperativeKernel((const void *)k_solve_batched, dim3(grid), dim3(kBatchThreads), args, kBatchSmem,
+                                     st);
 }
 
 }  // namespace sbqa
