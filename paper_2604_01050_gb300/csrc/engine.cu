@@ -285,6 +285,7 @@ SlotDesc slot_desc(const Request &r) {
   d.ka = r.ka; d.dl = r.dl; d.kj = r.kj; d.kc = r.tables.kc; d.kx = r.tables.kx;
   d.n0 = r.n0;
   d.W = d.ell_col ? 8 : 4;
+  d.wide = d.ell_col && r.Cp % 256 == 0 ? 1 : 0;
   return d;
 }
 
@@ -481,11 +482,14 @@ int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done, int32_t *don
   // form; then the 8-row items of the other slots
   std::stable_sort(ell_slots.begin(), ell_slots.end(), [&](int a, int b) {
     const SlotDesc &x = slots[a], &y = slots[b];
-    return std::make_tuple(x.P, x.kind != VAL_PM1, x.Pr != x.P) < std::make_tuple(y.P, y.kind != VAL_PM1, y.Pr != y.P);
+    return std::make_tuple(x.wide, x.P, x.kind != VAL_PM1, x.Pr != x.P) <
+           std::make_tuple(y.wide, y.P, y.kind != VAL_PM1, y.Pr != y.P);
   });
-  for (int q : ell_slots)
-    for (int g = 0; g < slots[q].Cp / kColsPerWarp; ++g)
-      for (int r0 = 0; r0 < slots[q].N; r0 += 2) items.push_back(WorkItem{q, r0, g, 0});
+  for (int q : ell_slots) {
+    const bool wide = slots[q].wide != 0;  // one row x 256 columns, or two rows x 128
+    for (int g = 0; g < slots[q].Cp / (wide ? 256 : kColsPerWarp); ++g)
+      for (int r0 = 0; r0 < slots[q].N; r0 += wide ? 1 : 2) items.push_back(WorkItem{q, r0, g, 0});
+  }
   int counts[2] = {int(items.size()), 0};
   for (int q : other_slots)
     for (int g = 0; g < slots[q].Cp / kColsPerWarp; ++g)

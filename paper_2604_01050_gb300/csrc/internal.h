@@ -233,9 +233,11 @@ struct SlotDesc {
   float kc, kx;
   int n0;  // steps completed before the current chunk
   int W;   // replica columns per lane: 8 (ELL form: units of two rows on half warps) or 4 (a row per warp)
+  int wide;  // ELL form with Cp a multiple of 256: units of one row x 256 columns on a whole warp
 };
 
-// 128 replica columns (colgroup) of 2 spin rows (a unit, W = 8) or 8 (an item, W = 4) of one slot.
+// 128 replica columns (colgroup) of 2 spin rows (a unit, W = 8), 256 columns of one row (a wide unit), or
+// 128 columns of 8 rows (an item, W = 4) of one slot.
 struct WorkItem {
   int slot, row0, colgroup, pad;
 };

@@ -5,14 +5,17 @@
 // rows of degree <= 8), its state buffers, its schedule tables and the number
 // of steps it had completed when the current chunk of steps started.  The
 // engine lists the work of all active slots: units of 2 spin rows x 128
-// replica columns for slots in ELL form (first, ordered by run width and
-// coupling kind) and items of 8 rows x 128 columns for the others.  One
+// replica columns for slots in ELL form (1 row x 256 columns when the
+// slot's padded width is a multiple of 256; first, ordered by unit shape,
+// run width and coupling kind) and items of 8 rows x 128 columns for the
+// others.  One
 // cooperative launch runs all steps of a chunk; a bounded grid barrier
 // separates the steps.  At the start of the launch every warp takes a
 // contiguous share of the units and keeps their neighbour columns, coupling
 // values, degrees and fields in shared memory for the whole chunk; each step
-// it runs them on half warps (one row of a unit per half, 8 columns per lane),
-// units beyond its shared-memory share from global memory.  The items of the
+// it runs them on half warps (one row of a unit per half, 8 columns per lane;
+// a wide unit on the whole warp), units beyond its shared-memory share from
+// global memory.  The items of the
 // other slots are spread over all warps, a row per warp (4 columns per lane).
 // The arithmetic per element is the one of k_step_csr (same gathers, same
 // sums in the same order, same update), so a request gives bit-identical
@@ -282,6 +285,12 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSM)
       const SlotDesc &d = D[m.slot];
       const int n = d.n0 + j;
       if (n >= d.S) continue;  // the request has finished (warp-uniform)
+      if (d.wide) {  // one row, 256 columns on the whole warp (the entry's first row)
+        const uint32_t dp = m.degpos[0];
+        batched_unit(d, n, m.row0, true, m.chunk * 256 + lane * 8, int(dp & 0xffu), int(dp >> 8), m.col[0], m.val[0],
+                     m.h[0]);
+        continue;
+      }
       const bool act = m.row0 + h < d.N;
       const uint32_t dp = m.degpos[h];
       batched_unit(d, n, act ? m.row0 + h : m.row0, act, m.chunk * kColsPerWarp + c_lane, act ? int(dp & 0xffu) : 0,
@@ -292,6 +301,13 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchBlocksPerSM)
       const SlotDesc &d = D[w.slot];
       const int n = d.n0 + j;
       if (n >= d.S) continue;
+      if (d.wide) {
+        const int2 meta = __ldg(reinterpret_cast<const int2 *>(d.ell_meta) + w.row0);
+        batched_unit(d, n, w.row0, true, w.colgroup * 256 + lane * 8, meta.x, meta.y,
+                     d.ell_col + size_t(w.row0) * kEllSlots, d.ell_val + size_t(w.row0) * kEllSlots,
+                     __ldg(d.h + w.row0));
+        continue;
+      }
       const bool act = w.row0 + h < d.N;
       const int row = act ? w.row0 + h : w.row0;
       const int2 meta = __ldg(reinterpret_cast<const int2 *>(d.ell_meta) + row);
