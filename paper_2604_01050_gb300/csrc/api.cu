@@ -1150,7 +1150,8 @@ int sbqa::problem_build_tables(const sbqa_problem *p, int S, int P, int R, float
 // sbqa_create_problem_dense with the checks, statistics and the library's
 // copy of J made on the GPU from the caller's array (ingest_dense.cu): the
 // same errors, in the same order, and the same analysis as the host pass
-// (the rows' sums of squares added in row order).
+// (each row's sum of squares added per 32-column tile, the tiles in order,
+// then the rows in row order).
 static int create_dense_on_device(int32_t n, const double *J, const double *h, sbqa_problem **out) {
   const size_t m = size_t(n) * n;
   sbqa_problem *p = new (std::nothrow) sbqa_problem();
@@ -1158,25 +1159,26 @@ static int create_dense_on_device(int32_t n, const double *J, const double *h, s
   cudaGetDevice(&p->device);
   DevBuf<int8_t> d8;
   DevBuf<double> d64;
-  DevBuf<IngestRow> drows;
+  DevBuf<IngestRow> drows, dpart;
   DevBuf<int> dasym;
   std::vector<IngestRow> rows(n);
   int asym = 0;
   auto cuda_fail = [&](cudaError_t e) {
-    d8.release(); d64.release(); drows.release(); dasym.release();
+    d8.release(); d64.release(); drows.release(); dpart.release(); dasym.release();
     delete p;
     return fail(e == cudaErrorMemoryAllocation ? SBQA_ERR_OOM : SBQA_ERR_CUDA,
                 std::string("dense J on the device: ") + cudaGetErrorString(e));
   };
   cudaError_t e;
   if ((e = d8.alloc(m)) != cudaSuccess || (e = d64.alloc(m)) != cudaSuccess || (e = drows.alloc(n)) != cudaSuccess ||
-      (e = dasym.alloc(1)) != cudaSuccess)
+      (e = dpart.alloc(ingest_part_count(n))) != cudaSuccess || (e = dasym.alloc(1)) != cudaSuccess)
     return cuda_fail(e);
-  if ((e = launch_ingest_dense(J, n, d8.p, d64.p, drows.p, dasym.p, nullptr)) != cudaSuccess ||
+  if ((e = launch_ingest_dense(J, n, d8.p, d64.p, dpart.p, drows.p, dasym.p, nullptr)) != cudaSuccess ||
       (e = cudaMemcpy(rows.data(), drows.p, size_t(n) * sizeof(IngestRow), cudaMemcpyDeviceToHost)) != cudaSuccess ||
       (e = cudaMemcpy(&asym, dasym.p, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_fail(e);
   drows.release(true);
+  dpart.release(true);
   dasym.release(true);
   bool finite = !h || finite_all(h, n), diag = true;
   int64_t nnz = 0;

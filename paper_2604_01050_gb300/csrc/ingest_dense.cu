@@ -5,8 +5,9 @@
 // page tables (cudaDevAttrPageableMemoryAccessUsesHostPageTables), the
 // checks and statistics that sbqa_create_problem_dense needs -- finiteness,
 // a zero diagonal, symmetry, integrality, +-1, max |J_ij|, the sum of
-// squares (the scale c0 of Eq. 6) and the row degrees -- run as two kernels
-// over the caller's FP64 J, and the library's copy of J stays in device
+// squares (the scale c0 of Eq. 6) and the row degrees -- run in one pass
+// over the caller's FP64 J (tile against mirror tile, every entry read
+// once), and the library's copy of J stays in device
 // memory: one byte per entry (integer values in [-128, 127], exactly as the
 // host pass stores them) and the FP64 values.  The operand and readout forms
 // (e4m3 or bfloat16 for the tensor cores, int32 / FP64 for the readout, FP32
@@ -20,8 +21,6 @@ namespace sbqa {
 
 namespace {
 
-constexpr int kIngestThreads = 256;
-
 // Row statistics, reduced in a fixed order (results do not depend on timing).
 __device__ __forceinline__ void warp_reduce(double &mx, double &s2, int &nnz, unsigned &flags) {
 #pragma unroll
@@ -33,74 +32,81 @@ __device__ __forceinline__ void warp_reduce(double &mx, double &s2, int &nnz, un
   }
 }
 
-// One block per row i of J (host memory): the row's statistics, its byte copy
-// d8 (int(v) for v in [-128, 127], else 0, as the host pass) and its FP64
-// copy d64 (device).
-__global__ void __launch_bounds__(kIngestThreads) k_ingest_rows(const double *__restrict__ J, int n, int8_t *d8,
-                                                                double *d64, IngestRow *rs) {
-  const int i = blockIdx.x;
-  const double *row = J + size_t(i) * n;
-  int8_t *row8 = d8 + size_t(i) * n;
-  double *row64 = d64 + size_t(i) * n;
+// One pass over J (host memory), each entry read once: block (bi, bj), bi <=
+// bj, takes the 32 x 32 tile (bi, bj) and its mirror (bj, bi) (the diagonal
+// tile alone), compares the two for symmetry (any difference sets *asym),
+// writes both tiles' byte copy d8 (int(v) for v in [-128, 127], else 0, as
+// the host pass) and FP64 copy d64, and for every row of each tile the
+// statistics of its 32 entries into part[tile column][row] (warp-shuffle
+// sums in a fixed order).
+__device__ __forceinline__ void tile_row_stats(double v, int i, int j, IngestRow *out) {
   double mx = 0.0, s2 = 0.0;
   int nnz = 0;
   unsigned flags = kIngestFinite | kIngestDiagZero | kIngestInteger | kIngestPm1;
-  for (int j = threadIdx.x; j < n; j += kIngestThreads) {
-    const double v = row[j];
-    if (!isfinite(v)) flags &= ~kIngestFinite;
-    if (v != 0.0) {
-      ++nnz;
-      if (v != rint(v)) flags &= ~kIngestInteger;
-      if (fabs(v) != 1.0) flags &= ~kIngestPm1;
-      mx = fmax(mx, fabs(v));
-      s2 = fma(v, v, s2);
-      if (j == i) flags &= ~kIngestDiagZero;
-    }
-    row8[j] = int8_t(v >= -128.0 && v <= 127.0 ? int(v) : 0);
-    row64[j] = v;
+  if (!isfinite(v)) flags &= ~kIngestFinite;
+  if (v != 0.0) {
+    nnz = 1;
+    if (v != rint(v)) flags &= ~kIngestInteger;
+    if (fabs(v) != 1.0) flags &= ~kIngestPm1;
+    mx = fabs(v);
+    s2 = v * v;
+    if (j == i) flags &= ~kIngestDiagZero;
   }
-  __shared__ double s_mx[kIngestThreads / 32], s_s2[kIngestThreads / 32];
-  __shared__ int s_nnz[kIngestThreads / 32];
-  __shared__ unsigned s_fl[kIngestThreads / 32];
   warp_reduce(mx, s2, nnz, flags);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (lane == 0) {
-    s_mx[warp] = mx;
-    s_s2[warp] = s2;
-    s_nnz[warp] = nnz;
-    s_fl[warp] = flags;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    IngestRow r{0.0, 0.0, 0, kIngestFinite | kIngestDiagZero | kIngestInteger | kIngestPm1};
-    for (int w = 0; w < kIngestThreads / 32; ++w) {
-      r.mx = fmax(r.mx, s_mx[w]);
-      r.s2 += s_s2[w];
-      r.nnz += s_nnz[w];
-      r.flags &= s_fl[w];
-    }
-    rs[i] = r;
-  }
+  if ((threadIdx.x & 31) == 0) *out = IngestRow{mx, s2, nnz, flags};
 }
 
-// Symmetry: tile (bi, bj), bi <= bj, of 32 x 32 entries against its mirror
-// tile, both read from host memory; any difference sets *asym.
-__global__ void __launch_bounds__(256) k_ingest_symmetry(const double *__restrict__ J, int n, int *asym) {
+__global__ void __launch_bounds__(256) k_ingest_tiles(const double *__restrict__ J, int n, int8_t *d8, double *d64,
+                                                      IngestRow *part, int *asym) {
   const int bi = blockIdx.y, bj = blockIdx.x;
   if (bj < bi) return;
-  __shared__ double t[32][33];
+  __shared__ double tb[32][33];  // the mirror tile (bj, bi), or the tile itself on the diagonal
   const int c = threadIdx.x & 31, r0 = threadIdx.x >> 5;
+  const bool diag = bi == bj;
+  // the mirror tile first (its entries are compared against the transposed reads below)
   for (int r = r0; r < 32; r += 8) {
-    const int i = bi * 32 + r, j = bj * 32 + c;
-    t[r][c] = (i < n && j < n) ? J[size_t(i) * n + j] : 0.0;
+    const int i = bj * 32 + r, j = bi * 32 + c;
+    tb[r][c] = (i < n && j < n) ? J[size_t(i) * n + j] : 0.0;
   }
   __syncthreads();
   bool same = true;
   for (int r = r0; r < 32; r += 8) {
-    const int i = bj * 32 + r, j = bi * 32 + c;  // mirror entry of t[c][r]
-    if (i < n && j < n) same = same && J[size_t(i) * n + j] == t[c][r];
+    const int i = bi * 32 + r, j = bj * 32 + c;
+    const bool in = i < n && j < n;
+    const double v = in ? (diag ? tb[r][c] : J[size_t(i) * n + j]) : 0.0;
+    if (in) {
+      same = same && v == tb[c][r];
+      d8[size_t(i) * n + j] = int8_t(v >= -128.0 && v <= 127.0 ? int(v) : 0);
+      d64[size_t(i) * n + j] = v;
+    }
+    if (i < n) tile_row_stats(v, i, j, part + size_t(bj) * n + i);  // padding adds nothing
+    if (!diag) {  // row j' = bj * 32 + r of the mirror tile
+      const int i2 = bj * 32 + r, j2 = bi * 32 + c;
+      const bool in2 = i2 < n && j2 < n;
+      const double w = in2 ? tb[r][c] : 0.0;
+      if (in2) {
+        d8[size_t(i2) * n + j2] = int8_t(w >= -128.0 && w <= 127.0 ? int(w) : 0);
+        d64[size_t(i2) * n + j2] = w;
+      }
+      if (i2 < n) tile_row_stats(w, i2, j2, part + size_t(bi) * n + i2);
+    }
   }
   if (!__all_sync(0xffffffffu, same) && c == 0) atomicOr(asym, 1);
+}
+
+// Row i's statistics from its tiles' partials, in tile-column order.
+__global__ void k_ingest_rows_reduce(const IngestRow *__restrict__ part, int n, int nb, IngestRow *rows) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  IngestRow r{0.0, 0.0, 0, kIngestFinite | kIngestDiagZero | kIngestInteger | kIngestPm1};
+  for (int t = 0; t < nb; ++t) {
+    const IngestRow q = part[size_t(t) * n + i];
+    r.mx = fmax(r.mx, q.mx);
+    r.s2 += q.s2;
+    r.nnz += q.nnz;
+    r.flags &= q.flags;
+  }
+  rows[i] = r;
 }
 
 // bfloat16 bits of v, round to nearest even in one step from FP64 (the host
@@ -182,14 +188,16 @@ bool ingest_on_device_possible() {
   return v == 1;
 }
 
-cudaError_t launch_ingest_dense(const double *J, int n, int8_t *d8, double *d64, IngestRow *rows, int *asym,
-                                cudaStream_t st) {
+size_t ingest_part_count(int n) { return size_t((n + 31) / 32) * size_t(n); }
+
+cudaError_t launch_ingest_dense(const double *J, int n, int8_t *d8, double *d64, IngestRow *part, IngestRow *rows,
+                                int *asym, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(asym, 0, sizeof(int), st);
   if (e != cudaSuccess) return e;
-  k_ingest_rows<<<n, kIngestThreads, 0, st>>>(J, n, d8, d64, rows);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int nb = (n + 31) / 32;
-  k_ingest_symmetry<<<dim3(nb, nb), 256, 0, st>>>(J, n, asym);
+  k_ingest_tiles<<<dim3(nb, nb), 256, 0, st>>>(J, n, d8, d64, part, asym);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_ingest_rows_reduce<<<(n + 255) / 256, 256, 0, st>>>(part, n, nb, rows);
   return cudaGetLastError();
 }
 

@@ -135,10 +135,11 @@ cudaError_t launch_solve_dense_tc_persistent(const void *plan, const StateView &
                                              cudaStream_t st);
 
 // Dense J read by the GPU from the caller's host array (ingest_dense.cu),
-// where the GPU reaches pageable host memory through the host's page tables.
-// Per row: max |J_ij|, the sum of squares, the nonzeros and the flags below;
-// d8 / d64 [N][N] receive the byte copy (int(v) for v in [-128, 127], else 0)
-// and the FP64 copy; *asym becomes nonzero when J != J^T.
+// where the GPU reaches pageable host memory through the host's page tables;
+// one pass, each entry read once.  Per row: max |J_ij|, the sum of squares,
+// the nonzeros and the flags below; d8 / d64 [N][N] receive the byte copy
+// (int(v) for v in [-128, 127], else 0) and the FP64 copy; part holds
+// ingest_part_count(N) per-tile partials; *asym becomes nonzero when J != J^T.
 struct IngestRow {
   double mx, s2;
   int32_t nnz;
@@ -146,8 +147,9 @@ struct IngestRow {
 };
 constexpr uint32_t kIngestFinite = 1, kIngestDiagZero = 2, kIngestInteger = 4, kIngestPm1 = 8;
 bool ingest_on_device_possible();
-cudaError_t launch_ingest_dense(const double *J, int n, int8_t *d8, double *d64, IngestRow *rows, int *asym,
-                                cudaStream_t st);
+size_t ingest_part_count(int n);
+cudaError_t launch_ingest_dense(const double *J, int n, int8_t *d8, double *d64, IngestRow *part, IngestRow *rows,
+                                int *asym, cudaStream_t st);
 // Device forms from the device copy (d8 when it holds J, else d64): padded
 // e4m3 (|J_ij| <= 16) and bfloat16 operands [Kp][Kp], and flat [N][N] forms.
 constexpr int kFlatI32 = 0, kFlatF64 = 1, kFlatF32 = 2, kFlatBf16InF32 = 3;
