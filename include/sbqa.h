@@ -200,7 +200,9 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info);
  *                per-step CSR kernel variant v (see step_variant); 11 forces
  *                the persistent CSR solver in the mode that caches whole
  *                rows (otherwise taken only when the items outnumber its
- *                cache); 12 = as 2, but the dense tensor-core solver keeps
+ *                cache; when the rows outnumber it too, a warp caches the
+ *                items that fit and reads the neighbours of the rest from
+ *                the ELL form every step); 12 = as 2, but the dense tensor-core solver keeps
  *                its 128 x 128 tiles instead of splitting the K loop across
  *                2-CTA clusters (taken by default when padded N and padded
  *                R*P are multiples of 256); with 1 or 12 no cluster kernel

@@ -111,8 +111,10 @@ int set_error(int code, const std::string &msg);
 int persistent_blocks();
 int persistent_barrier_words();  // size of the barrier counter buffer
 // 0: not eligible; 1: items cached per warp; 2: whole rows cached per warp
-// (force_rows: rows whenever they fit); kind = the CSR value kind
-int persistent_mode(int N, int Cp, int max_degree, int kind, int blocks, bool force_rows);
+// (force_rows: rows whenever they fit); 3: items, as many cached per warp as
+// fit and the rest read from the ELL arrays every step (ell: the ELL form
+// exists); kind = the CSR value kind
+int persistent_mode(int N, int Cp, int max_degree, int kind, int blocks, bool force_rows, bool ell);
 cudaError_t launch_solve_csr_persistent(const StateView &s, const CsrView &J, const StepTables &t, int n_begin,
                                         int n_end, unsigned *bar, int *err, int blocks, int mode, cudaStream_t st);
 

@@ -264,7 +264,8 @@ struct sbqa_problem {
   bool tc_pair_ok() const { return use_tc_pair && tc_pair_possible(); }
 
   int persist_mode() const {
-    return sbqa::persistent_mode(n, Cp, max_degree, kind, persist_blocks, prm.kernel_select == 11);
+    return sbqa::persistent_mode(n, Cp, max_degree, kind, persist_blocks, prm.kernel_select == 11,
+                                 ell_kind == kind && d_ell_col.p != nullptr);
   }
 
   bool persistent_ok() const {

@@ -14,6 +14,7 @@
 // wait is bounded (1 s, or at once when another block has already failed):
 // a block that gives up records an error and stops stepping, so a broken
 // grid ends with a status the host reads.
+#include <algorithm>
 #include <cstdlib>
 #include <type_traits>
 
@@ -30,11 +31,15 @@ struct PersistArgs {
   const int32_t *row_ptr, *col, *npos;  // CSR (+-1: each row's +1 entries first)
   const void *val;                      // FP32 or BF16 values (not +-1)
   const float *h;
+  // ELL form (mode 3: the items beyond a warp's cache read their neighbours here)
+  const int32_t *ell_col, *ell_meta;
+  const float *ell_val;
   StepTables t;
   int n_begin, n_end;
   unsigned *bar;  // grid barrier counters (persistent_barrier_words(), zeroed before the launch)
   int *err;       // error flag
   int skip_step;  // test hook: block 0 does not arrive at the barrier after this step (-1: never)
+  int cache_cap;  // items (or rows) a warp caches at most
 };
 
 // Cache entries.  Items mode: one (row, chunk) item.  Rows mode: one row; its
@@ -179,7 +184,8 @@ __global__ void __launch_bounds__(256, 4) k_solve_csr_persistent(PersistArgs a) 
   Entry *mine = reinterpret_cast<Entry *>(s_cache) + warp * C::kPerWarp;
   int my_count = 0;
   const int n_units = ROWS ? s.N : s.N * chunks;
-  for (int u = gw; u < n_units && my_count < C::kPerWarp; u += warps_total, ++my_count) {
+  const int cap = C::kPerWarp < a.cache_cap ? C::kPerWarp : a.cache_cap;
+  for (int u = gw; u < n_units && my_count < cap; u += warps_total, ++my_count) {
     if (lane == 0) {
       const int row = ROWS ? u : u / chunks;
       const int e0 = a.row_ptr[row], e1 = a.row_ptr[row + 1];
@@ -235,6 +241,23 @@ __global__ void __launch_bounds__(256, 4) k_solve_csr_persistent(PersistArgs a) 
           persist_item<P, KIND, W, false, LPI>(a, mh.row, mh.chunk, mh.col, valh, mh.degpos, Fin, Fout, ka, dnext,
                                                n, lane, act);
         ++q;  // two entries per pass
+      }
+    }
+    if constexpr (!ROWS) {
+      // items past the warp's cache (mode 3): neighbours from the ELL arrays
+      for (int u0 = gw + my_count * warps_total; u0 < n_units; u0 += (32 / LPI) * warps_total) {
+        const int uh = u0 + (LPI == 16 ? (lane >> 4) * warps_total : 0);
+        const bool act = uh < n_units;
+        const int u = act ? uh : u0;
+        const int row = u / chunks, ch = u - row * chunks;
+        const int2 meta = __ldg(reinterpret_cast<const int2 *>(a.ell_meta) + row);
+        const uint32_t dp = uint32_t(meta.x) | (uint32_t(KIND == VAL_PM1 ? meta.y : meta.x) << 8);
+        const int32_t *colp = a.ell_col + size_t(row) * kPersistMaxDeg;
+        const float *valp = VALS ? a.ell_val + size_t(row) * kPersistMaxDeg : nullptr;
+        if (gen)
+          persist_item<P, KIND, W, true, LPI>(a, row, ch, colp, valp, dp, Fin, Fout, ka, dnext, n, lane, act);
+        else
+          persist_item<P, KIND, W, false, LPI>(a, row, ch, colp, valp, dp, Fin, Fout, ka, dnext, n, lane, act);
       }
     }
     if (!grid_barrier(a.bar, ++k, a.err, n == a.skip_step && blockIdx.x == 0)) break;
@@ -304,12 +327,21 @@ int persistent_blocks() {
   return sms * best;
 }
 
-int persistent_mode(int N, int Cp, int max_degree, int kind, int blocks, bool force_rows) {
+// Test hook: SBQA_TEST_PERSIST_CACHE=k caches at most k items or rows per
+// warp, so that small instances take mode 3 (not for production use).
+static int cache_cap_hook() {
+  const char *v = std::getenv("SBQA_TEST_PERSIST_CACHE");
+  const int k = v ? std::atoi(v) : 0;
+  return k > 0 ? k : (1 << 30);
+}
+
+int persistent_mode(int N, int Cp, int max_degree, int kind, int blocks, bool force_rows, bool ell) {
   const int W = persist_w(Cp);
   if (blocks <= 0 || max_degree > kPersistMaxDeg || W == 0) return 0;
-  const long long warps = (long long)blocks * 8;
-  if (!force_rows && (long long)N * (Cp / (32 * W)) <= warps * per_warp(false, kind)) return 1;
-  if ((long long)N <= warps * per_warp(true, kind)) return 2;
+  const long long warps = (long long)blocks * 8, cap = cache_cap_hook();
+  if (!force_rows && (long long)N * (Cp / (32 * W)) <= warps * std::min<long long>(per_warp(false, kind), cap)) return 1;
+  if ((long long)N <= warps * std::min<long long>(per_warp(true, kind), cap)) return 2;
+  if (!force_rows && ell) return 3;
   return 0;
 }
 
@@ -322,6 +354,9 @@ cudaError_t launch_solve_csr_persistent(const StateView &s, const CsrView &J, co
   a.npos = J.npos;
   a.val = J.val;
   a.h = J.h;
+  a.ell_col = J.ell_col;
+  a.ell_meta = J.ell_meta;
+  a.ell_val = J.ell_val;
   a.t = t;
   a.n_begin = n_begin;
   a.n_end = n_end;
@@ -331,10 +366,12 @@ cudaError_t launch_solve_csr_persistent(const StateView &s, const CsrView &J, co
   // skip its arrival after step n of a launch that runs it (not for production use)
   const char *skip = std::getenv("SBQA_TEST_SKIP_BARRIER_STEP");
   a.skip_step = skip ? std::atoi(skip) : -1;
+  a.cache_cap = cache_cap_hook();
   void *args[] = {&a};
   const int W = persist_w(s.Cp);
-  const void *fn = (mode == 1 || mode == 2) && W ? persistent_fn(s.P, mode == 2, J.kind, W) : nullptr;
-  if (!fn) return cudaErrorInvalidValue;
+  const void *fn = (mode == 1 || mode == 2 || mode == 3) && W ? persistent_fn(s.P, mode == 2, J.kind, W) : nullptr;
+  if (!fn || (mode == 3 && (!J.ell_col || !J.ell_meta || (J.kind != VAL_PM1 && !J.ell_val))))
+    return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(bar, 0, persistent_barrier_words() * sizeof(unsigned), st);
   if (e != cudaSuccess) return e;
   return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(256), args, kPersistSmem, st);
