@@ -403,7 +403,7 @@ def run_serving(args, stream=None):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "Poisson stream of SK +-1 (dense) and 3D lattice (CSR) requests, "
                                    "N uniform in 64..8192, P in {8,16,32}, R=16, 2000 steps; "
-                                   "continuous batching engine, chunk 50 steps",
+                                   "continuous batching engine, chunk 100 steps",
                        "requests": len(reqs), "arena_gb": args.arena_gb, "capacity_req_per_s": capacity,
                        "closed_loop_updates_per_s": closed["updates"] / closed["makespan_s"],
                        "closed_loop_launches": closed["kernels_launched"],

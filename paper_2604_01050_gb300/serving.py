@@ -53,7 +53,7 @@ def make_requests(pool, n_requests, steps=2000, R=16, seed=1):
     return reqs
 
 
-def run_stream(reqs, rate, arena_bytes=40 << 30, slots=64, chunk=50, seed=2, stream=None, dense_batching=True):
+def run_stream(reqs, rate, arena_bytes=40 << 30, slots=64, chunk=100, seed=2, stream=None, dense_batching=True):
     """Open loop at `rate` requests/s (closed loop, all at t = 0, if rate is
     None).  Returns per-request latencies (s), the makespan and the
     replica-spin updates done.  dense_batching: small dense requests share
