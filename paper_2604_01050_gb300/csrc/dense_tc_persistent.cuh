@@ -57,6 +57,7 @@ struct TpArgs {
   int *err;
   const float *h;
   uint32_t *flags;  // [Kp / 128][Ct] steps completed in this launch, zeroed by the host
+  int hold_step;    // test hook: tile (0, 0) leaves its counter unpublished after this step (-1: never)
 };
 
 // One run-aligned chunk of 32 columns of spin row i, in registers (bit
@@ -346,7 +347,7 @@ __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const
       if constexpr (O::kNB == 2) tc::tma_store_2d(&m.Fstl, sF + O::kFTile, m0, ((n + 1) & 1) * s.Cp + n0);
       tc::tma_store_commit_and_wait_all();
       tc::fence_proxy_async_global();
-      tc::st_release_gpu(a.flags + mt * a.Ct + ct, q + 1);
+      if (n != a.hold_step || mt != 0 || ct != 0) tc::st_release_gpu(a.flags + mt * a.Ct + ct, q + 1);
       const int v = *reinterpret_cast<volatile int *>(a.err);
       if constexpr (PAIR) {
         int *slot = s_abort + 2 * (q & 1) + rank;  // double-buffered by step parity

@@ -436,13 +436,19 @@ static int dense_batches(sbqa_engine *e, std::vector<int> &ids, cudaStream_t st)
     return SBQA_OK;
   };
   int rc;
+  // test hook: SBQA_TEST_ENGINE_HOLD_DENSE=id makes that request's tile (0, 0) leave its step
+  // counter unpublished after the chunk's first step, so that its other tiles' bounded waits
+  // run out on the device (not for production use)
+  const char *hold_hook = std::getenv("SBQA_TEST_ENGINE_HOLD_DENSE");
+  const int hold_id = hold_hook ? std::atoi(hold_hook) : -1;
   for (int id : ids) {
     Request &r = e->reqs[id];
     const sbqa_problem *p = r.prob;
     const StateView sv = r.state_view();
     if (!tc_batch_fits(e->tcb, r.tc_plan, sv, p->Kp) && (rc = flush()) != SBQA_OK) return rc;
     const int steps_now = std::min(e->chunk, r.S - r.n0);
-    const cudaError_t err = tc_batch_add(e->tcb, r.tc_plan, sv, p->Kp, r.err, p->d_h.p, r.tables, r.n0, r.n0 + steps_now);
+    const cudaError_t err = tc_batch_add(e->tcb, r.tc_plan, sv, p->Kp, r.err, p->d_h.p, r.tables, r.n0,
+                                         r.n0 + steps_now, id == hold_id ? r.n0 : -1);
     if (err != cudaSuccess) return set_error(SBQA_ERR_CUDA, std::string("engine dense batch: ") + cudaGetErrorString(err));
   }
   return flush();

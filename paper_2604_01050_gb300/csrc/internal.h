@@ -175,8 +175,10 @@ void tc_batch_clear(TcBatch *b);
 int tc_batch_tiles(const TcBatch *b);
 int tc_batch_size(const TcBatch *b);
 bool tc_batch_fits(const TcBatch *b, const void *plan, const StateView &s, int Kp);
+// hold_step: test hook, the request's tile (0, 0) leaves its step counter
+// unpublished after that step, so its other tiles' waits run out (-1: never)
 cudaError_t tc_batch_add(TcBatch *b, const void *plan, const StateView &s, int Kp, int *err, const float *h,
-                         const StepTables &t, int n_begin, int n_end);
+                         const StepTables &t, int n_begin, int n_end, int hold_step = -1);
 cudaError_t tc_batch_launch(TcBatch *b, cudaStream_t st);
 cudaError_t tc_batch_set_attributes();
 int tc_batch_blocks();

@@ -128,7 +128,7 @@ bool tc_batch_fits(const TcBatch *b, const void *plan, const StateView &s, int K
 }
 
 cudaError_t tc_batch_add(TcBatch *b, const void *plan, const StateView &s, int Kp, int *err, const float *h,
-                         const StepTables &t, int n_begin, int n_end) {
+                         const StepTables &t, int n_begin, int n_end, int hold_step) {
   const int op = tc_op_of(plan);
   if (op < 0 || op > 2 || log2_width(s.P) < 0 || Kp % kTcBM != 0 || s.Cp % kTcBN != 0 || n_end < n_begin ||
       !tc_batch_fits(b, plan, s, Kp))
@@ -136,7 +136,7 @@ cudaError_t tc_batch_add(TcBatch *b, const void *plan, const StateView &s, int K
   TbReq &d = b->host[b->n];
   std::memcpy(&d.m, plan, sizeof(TcMaps));
   d.s = s;
-  d.a = TpArgs{Kp, s.Cp / kTcBN, n_begin, n_end, err, h, b->flags + b->tiles};
+  d.a = TpArgs{Kp, s.Cp / kTcBN, n_begin, n_end, err, h, b->flags + b->tiles, hold_step};
   d.t = t;
   d.tile0 = b->tiles;
   b->op = op;

@@ -986,7 +986,7 @@ cudaError_t launch_solve_dense_tc_split(const void *plan, const StateView &s, in
   const int Ct = s.Cp / kTcBN;
   cudaError_t e = cudaMemsetAsync(flags, 0, tc_persistent_flag_count(Kp, s.Cp) * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
-  TpArgs a{Kp, Ct, n_begin, n_end, err, h, flags};
+  TpArgs a{Kp, Ct, n_begin, n_end, err, h, flags, -1};
   TcMaps maps = *static_cast<const TcMaps *>(plan);
   StateView sv = s;
   StepTables tv = t;
@@ -1027,7 +1027,7 @@ cudaError_t launch_solve_dense_tc_persistent(const void *plan, const StateView &
   const int Ct = s.Cp / kTcBN;
   cudaError_t e = cudaMemsetAsync(flags, 0, tc_persistent_flag_count(Kp, s.Cp) * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
-  TpArgs a{Kp, Ct, n_begin, n_end, err, h, flags};
+  TpArgs a{Kp, Ct, n_begin, n_end, err, h, flags, -1};
   TcMaps maps = *static_cast<const TcMaps *>(plan);
   StateView sv = s;
   StepTables tv = t;
@@ -1064,7 +1064,7 @@ cudaError_t launch_solve_dense_tc_pair(const void *plan, const StateView &s, int
   const int Ct = s.Cp / kTcBN;
   cudaError_t e = cudaMemsetAsync(flags, 0, tc_persistent_flag_count(Kp, s.Cp) * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
-  TpArgs a{Kp, Ct, n_begin, n_end, err, h, flags};
+  TpArgs a{Kp, Ct, n_begin, n_end, err, h, flags, -1};
   TcMaps maps = *static_cast<const TcMaps *>(plan);
   StateView sv = s;
   StepTables tv = t;
