@@ -399,15 +399,6 @@ __device__ __forceinline__ void fence_proxy_async_global() {
   asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned)
-// from global memory into this CTA's shared memory, completing on bar
-// (complete_tx of `bytes`).
-__device__ __forceinline__ void bulk_load_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   smem_u32(dst)),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
-}
 
 // Commit the outstanding TMA stores and wait until they are complete (the
 // global writes performed, not only the shared-memory source read).
