@@ -91,6 +91,7 @@ TRAFFIC_PER_STEP = {
     "skreal2000": {"kernel": "k_solve_dense_tc_persistent<bf16>", "bytes_per_step": (29517312 + 1124864) // 1000},
 }
 L2_FLUSH_BYTES = 512 << 20
+BATCHED_CSR_UPDATES_PER_STEP = 13896704  # the 48-request serving stream's lattice requests
 
 
 def make_instance(cfg, seed=0):
@@ -268,8 +269,11 @@ def batched_csr_roofline(serving, reqs, stream, arena):
         peaks = {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     per_step = sum(r["inst"]["n"] * r["P"] * r["R"] for r in lat_reqs)
+    # DRAM traffic per step of one ncu capture of this closed loop (the 48-request stream's 19
+    # lattice requests, 100-step chunks; profiles/k_solve_batched_serving.md), for that stream only
+    traffic = (11023973000 + 12441357000) // 100 if per_step == BATCHED_CSR_UPDATES_PER_STEP else None
     return {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-            "traffic": None, "kernel": "k_solve_batched",
+            "traffic": traffic, "kernel": "k_solve_batched",
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
             "algorithmic_bytes_per_step": BYTES_PER_UPDATE * per_step,
             "note": "closed loop of the %d lattice requests alone: algorithmic %d B/update x the updates the "
