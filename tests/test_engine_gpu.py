@@ -5,6 +5,7 @@ admission order."""
 import numpy as np
 import pytest
 
+import oracle
 import workloads
 from sbqa_cases import create, dense_int, dense_real, lattice, regular, sk
 
@@ -28,9 +29,10 @@ def _sk_real_h(n, seed):
     return ("dense", J, np.random.default_rng(seed).normal(0.0, 0.5, n))
 
 
-def _requests(sb):
-    """(problem handle, steps, P, R, seed, precision) of a mixed workload."""
-    out = []
+def _requests(sb, with_oracle=False):
+    """(problem handle, steps, P, R, seed) of a mixed workload (and the oracle's
+    problem of each, with_oracle=True)."""
+    out, orc = [], []
     for k, (spec, steps, P, R, prec) in enumerate([
             (lattice(8, 1)[1], 90, 8, 4, "auto"),
             (regular(500, 6, 3)[1], 130, 16, 2, "bf16"),
@@ -47,7 +49,10 @@ def _requests(sb):
         pb = create(sb, spec)
         sb.set_schedule(pb, *workloads.autotune_params(R, k), precision=prec, eval_every=0)
         out.append((pb, steps, P, R, 100 + k))
-    return out
+        if with_oracle:
+            orc.append(oracle.Problem.dense(spec[1], spec[2]) if spec[0] == "dense"
+                       else oracle.Problem.csr(*spec[1:]))
+    return (out, orc) if with_oracle else out
 
 
 def _alone(sb, req):
@@ -58,7 +63,7 @@ def _alone(sb, req):
 
 @pytest.mark.parametrize("chunk,slots,arena_mb", [(32, 16, 512), (7, 3, 512), (50, 16, 40)])
 def test_engine_mix_equals_alone(sb, chunk, slots, arena_mb):
-    reqs = _requests(sb)
+    reqs, orcs = _requests(sb, with_oracle=True)
     alone = [_alone(sb, r) for r in reqs]
     eng = sb.engine_create(arena_mb << 20, slots, chunk)
     ids = [sb.engine_submit(eng, *r) for r in reqs]
@@ -70,11 +75,17 @@ def test_engine_mix_equals_alone(sb, chunk, slots, arena_mb):
         if len(done) == len(ids):
             break
     assert sorted(done) == ids
-    for rid, ref in zip(ids, alone):
+    for rid, ref, pbo in zip(ids, alone, orcs):
         got = sb.engine_result(eng, rid)
         assert np.array_equal(got["spins"], ref["spins"]), rid
         assert np.array_equal(got["energy"], ref["energy"]), rid
         assert np.array_equal(got["replica"], ref["replica"]), rid
+        # and directly against the oracle: the energies of the returned spins
+        e_o = oracle.energies(pbo, got["spins"])
+        if pbo.is_integer:
+            assert np.array_equal(got["energy_int"], e_o), rid
+        else:
+            assert np.allclose(got["energy"], e_o, rtol=1e-12, atol=1e-9), rid
     st = sb.engine_stats(eng)
     assert st["finished"] == len(ids) and st["queued"] == 0 and st["active"] == 0 and st["arena_used"] == 0
 
