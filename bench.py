@@ -87,8 +87,8 @@ BYTES_PER_UPDATE_BSB = 20  # ballistic form: + the FP32 f (= x) write
 TRAFFIC_PER_STEP = {
     "regular1e5": {"kernel": "k_solve_csr_persistent", "bytes_per_step": (6372881664 + 7261387008) // 64},
     "lattice16": {"kernel": "k_solve_csr_persistent", "bytes_per_step": (81332736 + 4403397376) // 64},
-    "sk2000": {"kernel": "k_solve_dense_tc_persistent", "bytes_per_step": (23229696 + 365056) // 1000},
-    "skreal2000": {"kernel": "k_solve_dense_tc_persistent<bf16>", "bytes_per_step": (29517312 + 1124864) // 1000},
+    "sk2000": {"kernel": "k_solve_dense_tc_persistent", "bytes_per_step": (23017216 + 292608) // 1000},
+    "skreal2000": {"kernel": "k_solve_dense_tc_persistent<bf16>", "bytes_per_step": (29531392 + 1040896) // 1000},
 }
 L2_FLUSH_BYTES = 512 << 20
 BATCHED_CSR_UPDATES_PER_STEP = 13896704  # the 48-request serving stream's lattice requests

@@ -96,14 +96,15 @@ def test_engine_batches_small_dense_requests(sb):
     step counts that end inside a chunk, and more tiles of one form than one
     wave holds (two launches for that form).  Every result equals the request
     solved alone."""
-    reqs = []
+    reqs, orcs = [], []
     for k in range(17):
         if k < 11:
-            spec, prec, P, R = sk(1000, 40 + k)[1], "exact", 16, 16     # 8 x 2 = 16 tiles each
+            (pbo, spec), prec, P, R = sk(1000, 40 + k), "exact", 16, 16     # 8 x 2 = 16 tiles each
         elif k < 14:
-            spec, prec, P, R = dense_real(300, 40 + k)[1], "bf16", 8, 4  # BF16 operands, 3 x 1 tiles
+            (pbo, spec), prec, P, R = dense_real(300, 40 + k), "bf16", 8, 4  # BF16 operands, 3 x 1 tiles
         else:
-            spec, prec, P, R = dense_int(200, 40 + k, jmax=3)[1], "exact", 6, 5  # ring of 6 in 8 columns
+            (pbo, spec), prec, P, R = dense_int(200, 40 + k, jmax=3), "exact", 6, 5  # ring of 6 in 8 columns
+        orcs.append(pbo)
         pb = create(sb, spec)
         sb.set_schedule(pb, *workloads.autotune_params(R, k), precision=prec, eval_every=0)
         reqs.append((pb, 40 + 7 * k, P, R, 300 + k))
@@ -118,11 +119,16 @@ def test_engine_batches_small_dense_requests(sb):
             if len(done) == len(ids):
                 break
         assert sorted(done) == ids
-        for rid, ref in zip(ids, alone):
+        for rid, ref, pbo in zip(ids, alone, orcs):
             got = sb.engine_result(eng, rid)
             assert np.array_equal(got["spins"], ref["spins"]), (batching, rid)
             assert np.array_equal(got["energy"], ref["energy"]), (batching, rid)
             assert np.array_equal(got["replica"], ref["replica"]), (batching, rid)
+            e_o = oracle.energies(pbo, got["spins"])
+            if pbo.is_integer:
+                assert np.array_equal(got["energy_int"], e_o), (batching, rid)
+            else:
+                assert np.allclose(got["energy"], e_o, rtol=1e-12, atol=1e-9), (batching, rid)
         st = sb.engine_stats(eng)
         if batching:
             # the first chunk alone needs two launches of the 16-tile form (176 tiles), one of each other form
