@@ -8,7 +8,9 @@
 // The step loop of a full run is captured once per shape in a CUDA graph and
 // replayed.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <condition_variable>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -19,6 +21,8 @@
 #include <tuple>
 #include <type_traits>
 #include <vector>
+
+#include <unistd.h>
 
 #include "../../include/sbqa.h"
 #include "internal.h"
@@ -263,23 +267,101 @@ uint16_t bf16_bits_rne(double v) {
   return uint16_t(u >> 16);
 }
 
-// Runs fn(task, worker) for task = 0 .. n_tasks-1, spread over up to 16 host
-// threads (task t on worker t % threads); the split never changes a result,
-// because each task writes only its own outputs.
+// Host threads of parallel_tasks: up to 15 workers beside the calling
+// thread, started on first use and kept for the life of the process (a job
+// wakes them instead of creating threads).  One job at a time; its tasks go
+// to whichever thread takes the next index.
+class HostPool {
+ public:
+  static HostPool &get() {
+    static HostPool pool;
+    return pool;
+  }
+  template <class Fn>
+  void run(int64_t n_tasks, Fn &fn) {
+    if (started_ && getpid() != owner_) {  // a forked child: the workers stayed in the parent
+      for (int64_t t = 0; t < n_tasks; ++t) fn(t, 0);
+      return;
+    }
+    std::lock_guard<std::mutex> job(job_mu_);
+    if (!started_) start();
+    {
+      std::lock_guard<std::mutex> l(mu_);
+      invoke_ = [](void *c, int64_t t) { (*static_cast<Fn *>(c))(t, 0); };
+      ctx_ = &fn;
+      n_ = n_tasks;
+      next_.store(0);
+      busy_ = int(th_->size());
+      ++gen_;
+    }
+    cv_.notify_all();
+    for (int64_t t; (t = next_.fetch_add(1)) < n_tasks;) fn(t, 0);
+    std::unique_lock<std::mutex> l(mu_);
+    done_cv_.wait(l, [&] { return busy_ == 0; });  // every worker is past this job
+  }
+  ~HostPool() {
+    // a forked child leaves the parent's thread handles alone (none runs here)
+    if (!started_ || getpid() != owner_) return;
+    {
+      std::lock_guard<std::mutex> l(mu_);
+      stop_ = true;
+    }
+    cv_.notify_all();
+    for (auto &x : *th_) x.join();
+    delete th_;
+  }
+
+ private:
+  void start() {
+    started_ = true;
+    owner_ = getpid();
+    const unsigned hw = std::thread::hardware_concurrency();
+    const int T = int(std::max(1u, std::min(hw ? hw : 1u, 16u)));
+    th_ = new std::vector<std::thread>();
+    for (int w = 1; w < T; ++w) th_->emplace_back([this] { loop(); });
+  }
+  void loop() {
+    uint64_t seen = 0;
+    for (;;) {
+      std::unique_lock<std::mutex> l(mu_);
+      cv_.wait(l, [&] { return stop_ || gen_ != seen; });
+      if (stop_) return;
+      seen = gen_;
+      void (*invoke)(void *, int64_t) = invoke_;
+      void *ctx = ctx_;
+      const int64_t n = n_;
+      l.unlock();
+      for (int64_t t; (t = next_.fetch_add(1)) < n;) invoke(ctx, t);
+      l.lock();
+      if (--busy_ == 0) done_cv_.notify_one();
+    }
+  }
+  std::mutex job_mu_, mu_;
+  std::condition_variable cv_, done_cv_;
+  std::vector<std::thread> *th_ = nullptr;  // released only by the process that started them
+  std::atomic<bool> started_{false};
+  bool stop_ = false;
+  pid_t owner_ = 0;
+  void (*invoke_)(void *, int64_t) = nullptr;
+  void *ctx_ = nullptr;
+  int64_t n_ = 0;
+  std::atomic<int64_t> next_{0};
+  int busy_ = 0;
+  uint64_t gen_ = 0;
+};
+
+// Runs fn(task, 0) for task = 0 .. n_tasks-1 on the host pool; the split
+// never changes a result, because each task writes only its own outputs.
 template <class Fn>
 void parallel_tasks(int64_t n_tasks, Fn fn) {
-  unsigned hw = std::thread::hardware_concurrency();
-  const int64_t T = std::max<int64_t>(1, std::min<int64_t>({int64_t(hw ? hw : 1), 16, n_tasks}));
-  auto work = [&](int64_t w) {
-    for (int64_t t = w; t < n_tasks; t += T) fn(t, w);
-  };
-  std::vector<std::thread> th;
-  for (int64_t w = 1; w < T; ++w) th.emplace_back(work, w);
-  work(0);
-  for (auto &x : th) x.join();
+  if (n_tasks <= 1) {
+    for (int64_t t = 0; t < n_tasks; ++t) fn(t, 0);
+    return;
+  }
+  HostPool::get().run(n_tasks, fn);
 }
 
-// Statistics of the stored couplings behind analyse_values.
+// Statistics of the stored couplings (merged in a fixed order of blocks).
 struct JStats {
   bool j_int = true, pm1 = true;
   double mx = 0.0, s2 = 0.0;
@@ -299,12 +381,6 @@ struct JStats {
 };
 
 void finish_analysis(sbqa_problem *p, JStats js);
-
-void analyse_values(sbqa_problem *p) {
-  JStats js;
-  for (double v : p->val) js.add(v);
-  finish_analysis(p, js);
-}
 
 void finish_analysis(sbqa_problem *p, JStats js) {
   bool j_int = js.j_int, pm1 = js.pm1, h_int = true;
@@ -1396,37 +1472,66 @@ int sbqa_create_problem_csr(int32_t n, int64_t nnz, const int64_t *row_ptr, cons
   if (row_ptr[0] != 0 || row_ptr[n] != nnz) return fail(SBQA_ERR_NOT_SYMMETRIC, "row_ptr ends do not match nnz");
   for (int i = 0; i < n; ++i)
     if (row_ptr[i + 1] < row_ptr[i]) return fail(SBQA_ERR_NOT_SYMMETRIC, "row_ptr decreasing");
-  if (!finite_all(val, size_t(nnz)) || (h && !finite_all(h, n))) return fail(SBQA_ERR_NOT_FINITE, "J or h not finite");
-  int32_t maxdeg = 0;
-  for (int i = 0; i < n; ++i) {  // pass 1: indices, order, diagonal
-    maxdeg = std::max<int32_t>(maxdeg, int32_t(row_ptr[i + 1] - row_ptr[i]));
-    for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-      const int32_t j = col_idx[e];
-      if (j < 0 || j >= n) return fail(SBQA_ERR_INVALID_ARG, "column index out of range");
-      if (j == i) return fail(SBQA_ERR_NOT_SYMMETRIC, "diagonal entry in CSR");
-      if (e > row_ptr[i] && col_idx[e - 1] >= j) return fail(SBQA_ERR_NOT_SYMMETRIC, "unsorted or duplicate columns");
-    }
-  }
-  {  // pass 2: the partner (j, i) holds the same value (blocks of rows over the host threads)
-    constexpr int kRowsPerTask = 4096;
-    const int64_t tasks = (int64_t(n) + kRowsPerTask - 1) / kRowsPerTask;
-    std::vector<uint8_t> ok(size_t(tasks), 1);
-    parallel_tasks(tasks, [&](int64_t task, int64_t) {
-      const int i1 = std::min<int64_t>(n, (task + 1) * kRowsPerTask);
-      for (int i = int(task) * kRowsPerTask; i < i1 && ok[task]; ++i)
-        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
-          const int32_t j = col_idx[e];
-          const int32_t *b = col_idx + row_ptr[j], *en = col_idx + row_ptr[j + 1];
-          const int32_t *it = std::lower_bound(b, en, i);
-          if (it == en || *it != i || val[row_ptr[j] + (it - b)] != val[e]) {
-            ok[task] = 0;
-            break;
-          }
+  // One pass over blocks of rows spread over the host threads: finiteness and
+  // the value statistics, indices in range, sorted and off the diagonal, and
+  // the partner (j, i) of every entry holding the same value.  The errors keep
+  // the precedence of separate passes: non-finite values first, then the first
+  // index error in row order, then asymmetry.
+  constexpr int kRowsPerTask = 4096;
+  const int64_t tasks = (int64_t(n) + kRowsPerTask - 1) / kRowsPerTask;
+  struct Block {
+    bool finite = true, sym = true;
+    int err = SBQA_OK;
+    const char *msg = nullptr;
+    int32_t maxdeg = 0;
+    JStats js;
+  };
+  std::vector<Block> blocks(static_cast<size_t>(tasks));
+  parallel_tasks(tasks, [&](int64_t task, int64_t) {
+    Block B;
+    const int i1 = int(std::min<int64_t>(n, (task + 1) * kRowsPerTask));
+    for (int i = int(task) * kRowsPerTask; i < i1; ++i) {
+      const int64_t e0 = row_ptr[i], e1 = row_ptr[i + 1];
+      B.maxdeg = std::max<int32_t>(B.maxdeg, int32_t(e1 - e0));
+      for (int64_t e = e0; e < e1; ++e) {
+        const double v = val[e];
+        B.finite = B.finite && std::isfinite(v);
+        B.js.add(v);
+      }
+      if (B.err != SBQA_OK) continue;
+      for (int64_t e = e0; e < e1 && B.err == SBQA_OK; ++e) {
+        const int32_t j = col_idx[e];
+        if (j < 0 || j >= n) B.err = SBQA_ERR_INVALID_ARG, B.msg = "column index out of range";
+        else if (j == i) B.err = SBQA_ERR_NOT_SYMMETRIC, B.msg = "diagonal entry in CSR";
+        else if (e > e0 && col_idx[e - 1] >= j) B.err = SBQA_ERR_NOT_SYMMETRIC, B.msg = "unsorted or duplicate columns";
+      }
+      if (B.err != SBQA_OK || !B.sym) continue;
+      for (int64_t e = e0; e < e1; ++e) {  // the row's columns are valid: the partner lookups stay in range
+        const int32_t j = col_idx[e];
+        const int32_t *b = col_idx + row_ptr[j], *en = col_idx + row_ptr[j + 1];
+        const int32_t *it = std::lower_bound(b, en, i);
+        if (it == en || *it != i || val[row_ptr[j] + (it - b)] != val[e]) {
+          B.sym = false;
+          break;
         }
-    });
-    for (uint8_t v : ok)
-      if (!v) return fail(SBQA_ERR_NOT_SYMMETRIC, "J != J^T");
+      }
+    }
+    blocks[size_t(task)] = B;
+  });
+  bool finite = !h || finite_all(h, n), sym = true;
+  int32_t maxdeg = 0;
+  JStats js_all;
+  const Block *first_err = nullptr;
+  for (const Block &B : blocks) {  // in row order: the same results whatever the threads
+    finite = finite && B.finite;
+    sym = sym && B.sym;
+    maxdeg = std::max(maxdeg, B.maxdeg);
+    js_all.merge(B.js);
+    if (!first_err && B.err != SBQA_OK) first_err = &B;
   }
+  if (!finite) return fail(SBQA_ERR_NOT_FINITE, "J or h not finite");
+  if (first_err) return fail(first_err->err, first_err->msg);
+  if (!sym) return fail(SBQA_ERR_NOT_SYMMETRIC, "J != J^T");
   sbqa_problem *p = new (std::nothrow) sbqa_problem();
   if (!p) return fail(SBQA_ERR_OOM, "host allocation");
   cudaGetDevice(&p->device);
@@ -1438,7 +1543,7 @@ int sbqa_create_problem_csr(int32_t n, int64_t nnz, const int64_t *row_ptr, cons
   p->col.assign(col_idx, col_idx + nnz);
   p->val.assign(val, val + nnz);
   if (h) p->h.assign(h, h + n);
-  analyse_values(p);
+  finish_analysis(p, js_all);
   std::vector<int32_t> rp32(n + 1);
   for (int i = 0; i <= n; ++i) rp32[i] = int32_t(row_ptr[i]);
   auto upload = [&]() -> int {
