@@ -748,12 +748,13 @@ KERNEL_NAMES = {0: "k_step_csr", 1: "k_step_dense", 2: "k_step_dense_tc", 3: "k_
                 4: "k_solve_csr_persistent", 5: "k_solve_dense_tc_persistent", 6: "k_step_csr_bsb",
                 7: "k_step_dense_bsb", 8: "k_solve_dense_tc_split", 9: "k_solve_dense_tc_pair",
                 10: "k_step_dense_tc<bf16>", 11: "k_solve_dense_tc_persistent<bf16>",
-                12: "k_step_dense_tc<bsb>", 13: "k_solve_dense_tc_persistent<bsb>"}
+                12: "k_step_dense_tc<bsb>", 13: "k_solve_dense_tc_persistent<bsb>", 14: "k_solve_csr_persistent_bsb"}
 KERNEL_LABELS = {0: "csr", 1: "dense_cuda_core", 2: "dense_tcgen05_fp8", 3: "dense_small_one_launch",
                  4: "csr_persistent", 5: "dense_tcgen05_persistent", 6: "csr_ballistic", 7: "dense_ballistic",
                  8: "dense_tcgen05_persistent_split_k", 9: "dense_tcgen05_persistent_cta_pairs",
                  10: "dense_tcgen05_bf16", 11: "dense_tcgen05_persistent_bf16",
-                 12: "dense_tcgen05_ballistic_bf16x2", 13: "dense_tcgen05_persistent_ballistic_bf16x2"}
+                 12: "dense_tcgen05_ballistic_bf16x2", 13: "dense_tcgen05_persistent_ballistic_bf16x2",
+                 14: "csr_persistent_ballistic"}
 TC_FP8 = (2, 5, 8, 9)
 TC_BF16 = (10, 11, 12, 13)
 
@@ -792,7 +793,7 @@ def roofline_of(cfg, name, info, N, P, R, step_ms, peaks):
                 "traffic": None, "kernel": kname, "step_ms": step_ms, "peak_source": "derived",
                 "note": "(2N + 12) FP32 flops per update / event-timed step time; peak = 152 SMs x 128 FP32 lanes "
                         "x 2 x max SM clock; one CTA per run (%d of 152 SMs busy): latency-bound" % R}
-    bpu = BYTES_PER_UPDATE_BSB if info.step_kernel in (6, 7) else BYTES_PER_UPDATE
+    bpu = BYTES_PER_UPDATE_BSB if info.step_kernel in (6, 7, 14) else BYTES_PER_UPDATE
     achieved_gbs = bpu * N * P * R / (step_ms * 1e-3) / 1e9
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     return {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",

@@ -143,8 +143,9 @@ typedef struct {
                              cta_group::2); 10 dense tcgen05 with bfloat16
                              operands per step (128 x 128 tiles), 11 its
                              persistent solver; 12 and 13 the same for the
-                             ballistic form (x as bfloat16 hi + lo); -1
-                             none                                            */
+                             ballistic form (x as bfloat16 hi + lo); 14
+                             the persistent CSR solver of the ballistic
+                             form; -1 none                                   */
     int32_t step_variant; /* CSR kernel variant picked by the autotuner:
                              0-5: 4 << (v % 3) consecutive replica columns
                              per lane, v >= 3 with one wave of blocks
@@ -209,7 +210,11 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info);
  *                is launched at all; 13 = the dense tensor-core
  *                solver on CTA pairs that share M=256 MMAs (padded N a
  *                multiple of 256; with kernel_select 0 the autotuner times
- *                it beside the others).  Results are identical whichever
+ *                it beside the others).  For the ballistic form on CSR, 2
+ *                takes its persistent solver when each warp's share of the
+ *                (row, 128-column) items fits its cache (degree <= 8), 0
+ *                times it beside the per-step kernel, any other value keeps
+ *                the per-step kernel.  Results are identical whichever
  *                kernel runs.
  *   beta, alpha  host, n_runs doubles each: per-run inverse temperature and
  *                schedule exponent (the auto-tuning draws them from

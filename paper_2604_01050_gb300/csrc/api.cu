@@ -854,6 +854,7 @@ std::map<TuneKey, TuneResult> g_tune;
 TuneKey tune_key(const sbqa_problem *p) {
   TuneKey k;
   k.dev = p->device; k.dense = p->dense ? 1 : 0; k.n = p->n; k.kind = p->dense ? -1 - (p->use_tc ? p->tc_op : 8) : p->kind; k.Cp = p->Cp;
+  if (p->ballistic()) k.kind += 16;  // the ballistic form's choices are its own
   k.P = p->P; k.select = p->prm.kernel_select; k.max_degree = p->max_degree; k.Kp = p->Kp; k.nnz = p->nnz;
   return k;
 }
@@ -871,13 +872,72 @@ void tune_store(const sbqa_problem *p, const TuneResult &r) {
   g_tune[tune_key(p)] = r;
 }
 
+// The ballistic form has one per-step kernel and, where the items fit the
+// cache, the persistent solver: kernel_select 1 keeps the per-step kernel, 2
+// the persistent solver, 0 times both (a few steps each) and keeps the faster.
+int autotune_csr_bsb(sbqa_problem *p) {
+  if (p->csr_variant < 0) p->csr_variant = 0;
+  const int sel = p->prm.kernel_select;
+  if (p->csr_variant_cp == p->Cp && p->csr_variant_kind == p->kind && p->csr_variant_select == sel) return SBQA_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  SBQA_CUDA(cudaStreamIsCapturing(p->stream, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return SBQA_OK;
+  p->use_persistent = false;
+  p->persistent_ms = 0.f;
+  if (p->persist_blocks == 0) p->persist_blocks = persistent_blocks();
+  if (p->S > 0 && (sel == 0 || sel == 2) && p->persistent_ok()) {
+    SBQA_CUDA(p->d_bar.alloc(persistent_barrier_words()));
+    TuneResult known;
+    const StateView s = p->state();
+    const CsrView J = p->csr();
+    if (sel == 2) {
+      p->use_persistent = true;
+    } else if (tune_lookup(p, &known)) {
+      p->variant_ms[0] = known.variant_ms[0];
+      p->persistent_ms = known.persistent_ms;
+      p->use_persistent = known.use_persistent;
+    } else {
+      const int reps = 8, steps = std::min(p->S, 64);
+      float step_ms = 0.f;
+      int rc = time_per_launch_in_graph(
+          p, reps, [&](cudaStream_t st) { return launch_step_csr_bsb(s, J, p->tables, 0, st); }, &step_ms);
+      if (rc != SBQA_OK) return rc;
+      cudaEvent_t e0, e1;
+      SBQA_CUDA(cudaEventCreate(&e0));
+      SBQA_CUDA(cudaEventCreate(&e1));
+      cudaError_t e = launch_solve_csr_persistent_bsb(s, J, p->tables, 0, std::min(p->S, 4), p->d_bar.p, p->d_err.p,
+                                                      p->persist_blocks, p->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, p->stream);
+      if (e == cudaSuccess)
+        e = launch_solve_csr_persistent_bsb(s, J, p->tables, 0, steps, p->d_bar.p, p->d_err.p, p->persist_blocks,
+                                            p->stream);
+      if (e == cudaSuccess) e = cudaEventRecord(e1, p->stream);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      SBQA_CUDA(e);
+      SBQA_CUDA(cudaMemsetAsync(p->d_err.p, 0, sizeof(int), p->stream));
+      p->variant_ms[0] = step_ms;
+      p->persistent_ms = ms / steps;
+      p->use_persistent = p->persistent_ms < step_ms;
+      TuneResult r;
+      r.variant_ms[0] = step_ms;
+      r.persistent_ms = p->persistent_ms;
+      r.use_persistent = p->use_persistent;
+      tune_store(p, r);
+    }
+  }
+  p->csr_variant_cp = p->Cp;
+  p->csr_variant_kind = p->kind;
+  p->csr_variant_select = sel;
+  return SBQA_OK;
+}
+
 int autotune_csr(sbqa_problem *p) {
   if (p->dense) return SBQA_OK;
-  if (p->ballistic()) {  // one kernel form; nothing to choose
-    p->use_persistent = false;
-    if (p->csr_variant < 0) p->csr_variant = 0;
-    return SBQA_OK;
-  }
+  if (p->ballistic()) return autotune_csr_bsb(p);
   if (p->csr_variant >= 0 && p->csr_variant_cp == p->Cp && p->csr_variant_kind == p->kind &&
       p->csr_variant_select == p->prm.kernel_select)
     return SBQA_OK;
@@ -1131,9 +1191,12 @@ cudaError_t issue_range(sbqa_problem *p, int n0, int n1, cudaStream_t st) {
     while (n < n1) {
       int stop = n1;
       if (K > 0) stop = std::min(n1, (n / K + 1) * K);
-      cudaError_t e = tc_persist ? launch_tc_persistent(p, p->state(), n, stop, st)
-                                 : launch_solve_csr_persistent(p->state(), p->csr(), p->tables, n, stop, p->d_bar.p,
-                                                               p->d_err.p, p->persist_blocks, p->persist_mode(), st);
+      cudaError_t e = tc_persist      ? launch_tc_persistent(p, p->state(), n, stop, st)
+                      : p->ballistic() ? launch_solve_csr_persistent_bsb(p->state(), p->csr(), p->tables, n, stop,
+                                                                          p->d_bar.p, p->d_err.p, p->persist_blocks, st)
+                                       : launch_solve_csr_persistent(p->state(), p->csr(), p->tables, n, stop,
+                                                                     p->d_bar.p, p->d_err.p, p->persist_blocks,
+                                                                     p->persist_mode(), st);
       if (e != cudaSuccess) return e;
       const int last = stop - 1;
       if (K > 0 && (last + 1) % K == 0 && last != p->S - 1) {
@@ -1586,7 +1649,7 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info) {
   if (p->tc_op == kTcOpBsb) tc_kernel = tc_pers ? 13 : 12;
   info->step_kernel = !p->begun ? -1
                      : p->use_tc ? tc_kernel
-                     : p->ballistic() ? (p->dense ? 7 : 6)
+                     : p->ballistic() ? (p->dense ? 7 : p->use_persistent && p->persistent_ok() ? 14 : 6)
                      : p->small_path ? 3
                      : (p->dense ? 1 : (p->use_persistent ? 4 : 0));
   info->persistent_ms = p->use_tc ? p->tc_persistent_ms : p->persistent_ms;

@@ -117,6 +117,12 @@ int persistent_barrier_words();  // size of the barrier counter buffer
 int persistent_mode(int N, int Cp, int max_degree, int kind, int blocks, bool force_rows, bool ell);
 cudaError_t launch_solve_csr_persistent(const StateView &s, const CsrView &J, const StepTables &t, int n_begin,
                                         int n_end, unsigned *bar, int *err, int blocks, int mode, cudaStream_t st);
+// The ballistic form f(x) = x in one cooperative launch (items of 128 columns
+// cached per warp; f buffers Fx in FP32): eligible when the items fit the
+// cache (persistent_bsb_ok); results equal launch_step_csr_bsb bit for bit.
+bool persistent_bsb_ok(int N, int Cp, int max_degree, int kind, int blocks);
+cudaError_t launch_solve_csr_persistent_bsb(const StateView &s, const CsrView &J, const StepTables &t, int n_begin,
+                                            int n_end, unsigned *bar, int *err, int blocks, cudaStream_t st);
 
 // Steps of a dense integer run on the tensor cores in one cooperative launch,
 // x and y resident in tensor memory, per-tile step flags between CTAs

@@ -269,7 +269,9 @@ struct sbqa_problem {
   }
 
   bool persistent_ok() const {
-    return !dense && !ballistic() && persist_mode() != 0;
+    if (dense) return false;
+    if (ballistic()) return sbqa::persistent_bsb_ok(n, Cp, max_degree, kind, persist_blocks);
+    return persist_mode() != 0;
   }
 
   StateView state() const {

@@ -264,6 +264,101 @@ __global__ void __launch_bounds__(256, 4) k_solve_csr_persistent(PersistArgs a) 
   }
 }
 
+// The ballistic form f(x) = x (the bSB choice named in Sec. II A): the same
+// persistent scheme in items mode with items of 128 columns on whole warps
+// (4 columns per lane), gathering the neighbours' FP32 positions of the step
+// before (written by other blocks: read through L2).  The sum runs over the
+// row's eight cache slots in order, a zero weight and a zero position past the
+// degree -- the sequence of fused multiply-adds of k_step_csr_bsb -- and the
+// update is sb_update4_bsb, so results equal the per-step kernel bit for bit.
+template <int P, int KIND>
+__global__ void __launch_bounds__(256, 4) k_solve_csr_persistent_bsb(PersistArgs a) {
+  constexpr bool VALS = KIND != VAL_PM1;
+  using C = Cache<false, VALS>;
+  using Entry = typename C::Entry;
+  extern __shared__ int32_t s_cache[];
+  const StateView &s = a.s;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int chunks = s.Cp / kColsPerWarp;
+  const int warps_total = gridDim.x * 8;
+  const int gw = blockIdx.x * 8 + warp;
+  Entry *mine = reinterpret_cast<Entry *>(s_cache) + warp * C::kPerWarp;
+  int my_count = 0;
+  const int n_units = s.N * chunks;
+  const int cap = C::kPerWarp < a.cache_cap ? C::kPerWarp : a.cache_cap;
+  for (int u = gw; u < n_units && my_count < cap; u += warps_total, ++my_count) {
+    if (lane == 0) {
+      const int row = u / chunks;
+      const int e0 = a.row_ptr[row], e1 = a.row_ptr[row + 1];
+      Entry &m = mine[my_count];
+      m.row = row;
+      m.chunk = u - row * chunks;
+      m.degpos = uint32_t(e1 - e0) | (uint32_t(KIND == VAL_PM1 ? a.npos[row] : e1 - e0) << 8);
+      for (int q = 0; q < kPersistMaxDeg; ++q) {
+        m.col[q] = q < e1 - e0 ? a.col[e0 + q] : 0;
+        if constexpr (VALS) m.val[q] = q < e1 - e0 ? entry_value<KIND>(a, e0 + q) : 0.f;
+      }
+    }
+  }
+  __syncwarp();
+  unsigned k = 0;
+  for (int n = a.n_begin; n < a.n_end; ++n) {
+    const float *Fin = s.fx_of(n);
+    float *Fout = s.fx_of(n + 1);
+    for (int q = 0; q < my_count; ++q) {
+      const Entry &m = mine[q];
+      const int i = m.row, c4 = m.chunk * kColsPerWarp + lane * 4;
+      const size_t off = size_t(i) * s.Cp + c4;
+      const float4 xv = *reinterpret_cast<const float4 *>(s.x + off);
+      const float4 yv = *reinterpret_cast<const float4 *>(s.y + off);
+      const int deg = int(m.degpos & 0xffu), npos = int(m.degpos >> 8);
+      float4 f[kPersistMaxDeg];
+#pragma unroll
+      for (int e = 0; e < kPersistMaxDeg; ++e)
+        f[e] = e < deg ? __ldcg(reinterpret_cast<const float4 *>(Fin + size_t(m.col[e]) * s.Cp + c4))
+                       : make_float4(0.f, 0.f, 0.f, 0.f);
+      float g[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int e = 0; e < kPersistMaxDeg; ++e) {
+        float w = 0.f;
+        if (e < deg) {
+          if constexpr (VALS) w = m.val[e];
+          else w = e < npos ? 1.f : -1.f;
+        }
+        g[0] = fmaf(w, f[e].x, g[0]);
+        g[1] = fmaf(w, f[e].y, g[1]);
+        g[2] = fmaf(w, f[e].z, g[2]);
+        g[3] = fmaf(w, f[e].w, g[3]);
+      }
+      sb_update4_bsb<P>(s, a.t, n, i, c4, g, __ldg(a.h + i), xv, yv, Fout);
+    }
+    if (!grid_barrier(a.bar, ++k, a.err, n == a.skip_step && blockIdx.x == 0)) break;
+  }
+}
+
+template <int KIND>
+static const void *persistent_bsb_fn_k(int P) {
+  switch (P) {
+    case 1: return (const void *)k_solve_csr_persistent_bsb<1, KIND>;
+    case 2: return (const void *)k_solve_csr_persistent_bsb<2, KIND>;
+    case 4: return (const void *)k_solve_csr_persistent_bsb<4, KIND>;
+    case 8: return (const void *)k_solve_csr_persistent_bsb<8, KIND>;
+    case 16: return (const void *)k_solve_csr_persistent_bsb<16, KIND>;
+    case 32: return (const void *)k_solve_csr_persistent_bsb<32, KIND>;
+    case 64: return (const void *)k_solve_csr_persistent_bsb<64, KIND>;
+    case 128: return (const void *)k_solve_csr_persistent_bsb<128, KIND>;
+    default: return nullptr;
+  }
+}
+
+static const void *persistent_bsb_fn(int P, int kind) {
+  switch (kind) {
+    case VAL_PM1: return persistent_bsb_fn_k<VAL_PM1>(P);
+    case VAL_F32: return persistent_bsb_fn_k<VAL_F32>(P);
+    default: return persistent_bsb_fn_k<VAL_BF16>(P);
+  }
+}
+
 // Items mode with 128-column items (W = 4 on a whole warp) runs as W = 8 on
 // half warps (LPI = 16); rows mode and 256-column items keep LPI = 32.
 template <bool ROWS, int KIND, int W>
@@ -308,6 +403,14 @@ static int persist_w(int Cp) { return Cp % 256 == 0 ? 8 : (Cp % 128 == 0 ? 4 : 0
 
 int persistent_barrier_words() { return int(kBarStride * (kBarGroups + 1)); }
 
+// Test hook: SBQA_TEST_PERSIST_CACHE=k caches at most k items or rows per
+// warp, so that small instances take mode 3 (not for production use).
+static int cache_cap_hook() {
+  const char *v = std::getenv("SBQA_TEST_PERSIST_CACHE");
+  const int k = v ? std::atoi(v) : 0;
+  return k > 0 ? k : (1 << 30);
+}
+
 int persistent_blocks() {
   int dev = 0, sms = 0, best = 1 << 30;
   cudaGetDevice(&dev);
@@ -324,16 +427,51 @@ int persistent_blocks() {
             return 0;
           best = per_sm < best ? per_sm : best;
         }
+  for (int P : Ps)
+    for (int kind = 0; kind < 3; ++kind) {
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_bsb_fn(P, kind), 256, kPersistSmem) !=
+          cudaSuccess)
+        return 0;
+      best = per_sm < best ? per_sm : best;
+    }
   return sms * best;
 }
 
-// Test hook: SBQA_TEST_PERSIST_CACHE=k caches at most k items or rows per
-// warp, so that small instances take mode 3 (not for production use).
-static int cache_cap_hook() {
-  const char *v = std::getenv("SBQA_TEST_PERSIST_CACHE");
-  const int k = v ? std::atoi(v) : 0;
-  return k > 0 ? k : (1 << 30);
+bool persistent_bsb_ok(int N, int Cp, int max_degree, int kind, int blocks) {
+  if (blocks <= 0 || max_degree > kPersistMaxDeg || Cp % kColsPerWarp != 0) return false;
+  return (long long)N * (Cp / kColsPerWarp) <= (long long)blocks * 8 * std::min<long long>(per_warp(false, kind),
+                                                                                         cache_cap_hook());
 }
+
+cudaError_t launch_solve_csr_persistent_bsb(const StateView &s, const CsrView &J, const StepTables &t, int n_begin,
+                                            int n_end, unsigned *bar, int *err, int blocks, cudaStream_t st) {
+  PersistArgs a;
+  a.s = s;
+  a.row_ptr = J.row_ptr;
+  a.col = J.col;
+  a.npos = J.npos;
+  a.val = J.val;
+  a.h = J.h;
+  a.ell_col = J.ell_col;
+  a.ell_meta = J.ell_meta;
+  a.ell_val = J.ell_val;
+  a.t = t;
+  a.n_begin = n_begin;
+  a.n_end = n_end;
+  a.bar = bar;
+  a.err = err;
+  const char *skip = std::getenv("SBQA_TEST_SKIP_BARRIER_STEP");
+  a.skip_step = skip ? std::atoi(skip) : -1;
+  a.cache_cap = cache_cap_hook();
+  const void *fn = persistent_bsb_fn(s.P, J.kind);
+  if (!fn || !persistent_bsb_ok(s.N, s.Cp, kPersistMaxDeg, J.kind, blocks)) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(bar, 0, persistent_barrier_words() * sizeof(unsigned), st);
+  if (e != cudaSuccess) return e;
+  void *args[] = {&a};
+  return cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(256), args, kPersistSmem, st);
+}
+
 
 int persistent_mode(int N, int Cp, int max_degree, int kind, int blocks, bool force_rows, bool ell) {
   const int W = persist_w(Cp);

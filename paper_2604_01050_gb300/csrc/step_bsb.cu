@@ -19,60 +19,6 @@
 
 namespace sbqa {
 
-// sb_update4 with f(x) = x: same momentum, position and wall arithmetic,
-// writes the new x into the f buffer of the next step.
-template <int P>
-__device__ __forceinline__ void sb_update4_bsb(const StateView &s, const StepTables &t, int n, int i, int c4,
-                                               const float G[4], float hi, float4 xv, float4 yv, float *Fout) {
-  const size_t off = size_t(i) * s.Cp + c4;
-  float xs[4] = {xv.x, xv.y, xv.z, xv.w};
-  float ys[4] = {yv.x, yv.y, yv.z, yv.w};
-  float xm[4], xp[4];
-  ring_neighbours<P>(xs, s.Pr, xm, xp);  // all lanes take part (shuffles)
-  if (c4 >= s.C) return;                 // padding columns past R * P
-  const float ka = __ldg(t.ka + n);
-  const float *kjn = t.kj + size_t(n) * t.R;
-  float kj[4];
-  if constexpr (P >= 4) {
-    const float k = __ldg(kjn + c4 / P);
-    kj[0] = kj[1] = kj[2] = kj[3] = k;
-  } else {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) kj[j] = (c4 + j < s.C) ? __ldg(kjn + (c4 + j) / P) : 0.f;
-  }
-  const float2 kc2 = make_float2(t.kc, t.kc), mka2 = make_float2(-ka, -ka);
-  const float2 kx2 = make_float2(t.kx, t.kx), h2 = make_float2(hi, hi);
-  float xo[4], yo[4];
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const int a = 2 * q, b = 2 * q + 1;
-    const float2 x2 = make_float2(xs[a], xs[b]);
-    float2 y2 = make_float2(ys[a], ys[b]);
-    y2 = __ffma2_rn(kc2, __fadd2_rn(make_float2(G[a], G[b]), h2), y2);
-    y2 = __ffma2_rn(mka2, x2, y2);
-    y2 = __ffma2_rn(make_float2(kj[a], kj[b]), __fadd2_rn(make_float2(xm[a], xm[b]), make_float2(xp[a], xp[b])), y2);
-    const float2 xn2 = __ffma2_rn(kx2, y2, x2);
-    xo[a] = xn2.x; xo[b] = xn2.y;
-    yo[a] = y2.x; yo[b] = y2.y;
-  }
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const float xc = fminf(fmaxf(xo[j], -1.f), 1.f);  // wall: clamping changes x iff |x| > 1
-    float yn = (xc != xo[j]) ? 0.f : yo[j];
-    float xn = xc;
-    if (P < 4 && c4 + j >= s.C) {  // ragged tail: leave the padding column alone
-      xn = xs[j];
-      yn = ys[j];
-    }
-    xo[j] = xn;
-    yo[j] = yn;
-  }
-  const float4 xnew = make_float4(xo[0], xo[1], xo[2], xo[3]);
-  *reinterpret_cast<float4 *>(s.x + off) = xnew;
-  *reinterpret_cast<float4 *>(s.y + off) = make_float4(yo[0], yo[1], yo[2], yo[3]);
-  *reinterpret_cast<float4 *>(Fout + off) = xnew;
-}
-
 template <int KIND>
 __device__ __forceinline__ float bsb_weight(const CsrView &J, int e, int ep) {
   if constexpr (KIND == VAL_PM1) return e < ep ? 1.f : -1.f;
