@@ -748,15 +748,18 @@ KERNEL_NAMES = {0: "k_step_csr", 1: "k_step_dense", 2: "k_step_dense_tc", 3: "k_
                 4: "k_solve_csr_persistent", 5: "k_solve_dense_tc_persistent", 6: "k_step_csr_bsb",
                 7: "k_step_dense_bsb", 8: "k_solve_dense_tc_split", 9: "k_solve_dense_tc_pair",
                 10: "k_step_dense_tc<bf16>", 11: "k_solve_dense_tc_persistent<bf16>",
-                12: "k_step_dense_tc<bsb>", 13: "k_solve_dense_tc_persistent<bsb>", 14: "k_solve_csr_persistent_bsb"}
+                12: "k_step_dense_tc<bsb>", 13: "k_solve_dense_tc_persistent<bsb>", 14: "k_solve_csr_persistent_bsb",
+                15: "k_solve_dense_tc_f4"}
 KERNEL_LABELS = {0: "csr", 1: "dense_cuda_core", 2: "dense_tcgen05_fp8", 3: "dense_small_one_launch",
                  4: "csr_persistent", 5: "dense_tcgen05_persistent", 6: "csr_ballistic", 7: "dense_ballistic",
                  8: "dense_tcgen05_persistent_split_k", 9: "dense_tcgen05_persistent_cta_pairs",
                  10: "dense_tcgen05_bf16", 11: "dense_tcgen05_persistent_bf16",
                  12: "dense_tcgen05_ballistic_bf16x2", 13: "dense_tcgen05_persistent_ballistic_bf16x2",
-                 14: "csr_persistent_ballistic"}
+                 14: "csr_persistent_ballistic", 15: "dense_tcgen05_persistent_e2m1"}
 TC_FP8 = (2, 5, 8, 9)
 TC_BF16 = (10, 11, 12, 13)
+TC_FP4 = (15,)
+FP4_OVER_FP8 = 3.0  # nominal dense e2m1 / e4m3 tensor rate of the GB300 (13.5 / 4.5 PFLOP/s)
 
 
 def roofline_of(cfg, name, info, N, P, R, step_ms, peaks):
@@ -768,9 +771,19 @@ def roofline_of(cfg, name, info, N, P, R, step_ms, peaks):
         kname = "k_step_dense_tc_wide"  # 128 x 256 tiles when the padded columns allow
     tr = TRAFFIC_PER_STEP.get(name + ("/ballistic" if cfg.get("variant") == "ballistic" else ""))
     traffic = tr["bytes_per_step"] if tr and tr["kernel"] == kname else None
-    if info.step_kernel in TC_FP8 + TC_BF16:  # a contraction: 2 N^2 R P flops per step
+    if info.step_kernel in TC_FP8 + TC_BF16 + TC_FP4:  # a contraction: 2 N^2 R P flops per step
         flops = 2.0 * N * N * P * R
         achieved = flops / (step_ms * 1e-3) / 1e12
+        if info.step_kernel in TC_FP4:
+            fp8 = peaks.get("fp8_tflops_burst", 2.0 * peaks.get("bf16_tflops", 1900.0))
+            peak = FP4_OVER_FP8 * fp8
+            src = "derived: %.0f x measured e4m3 GEMM (profiles/fp8_e4m3_dense_peak.md), nominal e2m1/e4m3 ratio" % (
+                FP4_OVER_FP8)
+            return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": traffic, "kernel": kname, "step_ms": step_ms,
+                    "peak_source": src, "frac_of_fp8_peak": achieved / fp8,
+                    "note": "2 N^2 R P flops per step / event-timed step time; packed e2m1 operands "
+                            "(kind::mxf4), dense e2m1 peak; frac_of_fp8_peak compares with the e4m3 solvers"}
         if info.step_kernel in TC_FP8:
             if "fp8_tflops_burst" in peaks:
                 peak, src = peaks["fp8_tflops_burst"], "measured (e4m3 GEMM, profiles/fp8_e4m3_dense_peak.md)"

@@ -145,7 +145,10 @@ typedef struct {
                              persistent solver; 12 and 13 the same for the
                              ballistic form (x as bfloat16 hi + lo); 14
                              the persistent CSR solver of the ballistic
-                             form; -1 none                                   */
+                             form; 15 the persistent dense tcgen05 solver
+                             with packed e2m1 operands (kind::mxf4, unit
+                             scale factors) and J resident in shared
+                             memory; -1 none                                 */
     int32_t step_variant; /* CSR kernel variant picked by the autotuner:
                              0-5: 4 << (v % 3) consecutive replica columns
                              per lane, v >= 3 with one wave of blocks
@@ -210,7 +213,12 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info);
  *                is launched at all; 13 = the dense tensor-core
  *                solver on CTA pairs that share M=256 MMAs (padded N a
  *                multiple of 256; with kernel_select 0 the autotuner times
- *                it beside the others).  For the ballistic form on CSR, 2
+ *                it beside the others); 14 = the dense tensor-core
+ *                solver with packed e2m1 operands (integer |J_ij| <= 4,
+ *                padded N <= 2304: each CTA keeps its 128 rows of J in
+ *                shared memory and only f streams in), else as 12; with
+ *                kernel_select 0 the autotuner times it beside the others.
+ *                For the ballistic form on CSR, 2
  *                takes its persistent solver when each warp's share of the
  *                (row, 128-column) items fits its cache (degree <= 8), 0
  *                times it beside the per-step kernel, any other value keeps

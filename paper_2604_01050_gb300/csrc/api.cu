@@ -226,6 +226,7 @@ sbqa_problem::~sbqa_problem() {
   if (graph) cudaGraphExecDestroy(graph);
   if (cap_stream) cudaStreamDestroy(cap_stream);
   if (tc_plan) tc_plan_free(tc_plan);
+  if (tc4_plan) tc4_plan_free(tc4_plan);
   d_J8.release(true); d_FT.release(true); d_err.release(true);
   d_row_ptr.release(true); d_col.release(true); d_col_pm1.release(true); d_npos.release(true); d_val_f32.release(true);
   d_val_bf16.release(true); d_dense_f32.release(true); d_h.release(true); d_e_i32.release(true);
@@ -236,6 +237,7 @@ sbqa_problem::~sbqa_problem() {
   d_kj.release(true); d_ei.release(true); d_part_i.release(true); d_best_ei.release(true); d_ef.release(true);
   d_part_f.release(true); d_best_e.release(true); d_best_k.release(true); d_best_step.release(true);
   d_have.release(true); d_best_spins.release(true); d_bar.release(true); d_tc_flags.release(true);
+  d_J4.release(true); d_FT4.release(true);
 }
 
 
@@ -844,7 +846,8 @@ struct TuneKey {
 };
 struct TuneResult {
   int csr_variant = 0;
-  bool use_persistent = false, use_tc_persistent = false, use_tc_split = false, use_tc_pair = false;
+  bool use_persistent = false, use_tc_persistent = false, use_tc_split = false, use_tc_pair = false,
+       use_tc_f4 = false;
   float variant_ms[8] = {};
   float persistent_ms = 0.f, tc_step_ms = 0.f, tc_persistent_ms = 0.f;
 };
@@ -855,6 +858,7 @@ TuneKey tune_key(const sbqa_problem *p) {
   TuneKey k;
   k.dev = p->device; k.dense = p->dense ? 1 : 0; k.n = p->n; k.kind = p->dense ? -1 - (p->use_tc ? p->tc_op : 8) : p->kind; k.Cp = p->Cp;
   if (p->ballistic()) k.kind += 16;  // the ballistic form's choices are its own
+  if (p->dense && p->use_tc && p->tc_f4_possible()) k.kind -= 32;  // the e2m1 solver is a candidate
   k.P = p->P; k.select = p->prm.kernel_select; k.max_degree = p->max_degree; k.Kp = p->Kp; k.nnz = p->nnz;
   return k;
 }
@@ -1030,6 +1034,9 @@ int autotune_csr(sbqa_problem *p) {
 // Steps [n0, n1) of the persistent dense tcgen05 solver: on CTA pairs, split-K
 // across 2-CTA clusters, or with 128 x 128 tiles, as chosen.
 cudaError_t launch_tc_persistent(sbqa_problem *p, const StateView &s, int n0, int n1, cudaStream_t st) {
+  if (p->tc_f4_ok())
+    return launch_solve_dense_tc_f4(p->tc4_plan, s, p->Kp, p->d_err.p, p->d_h.p, p->tables, n0, n1,
+                                    p->d_tc_flags.p, st);
   if (p->tc_pair_ok())
     return launch_solve_dense_tc_pair(p->tc_plan, s, p->Kp, p->d_err.p, p->d_h.p, p->tables, n0, n1,
                                       p->d_tc_flags.p, st);
@@ -1040,31 +1047,60 @@ cudaError_t launch_tc_persistent(sbqa_problem *p, const StateView &s, int n0, in
                                           p->d_tc_flags.p, st);
 }
 
+// Operands of the e2m1 solver: J4 from the e4m3 copy of J (once per
+// problem), FT4 for the run's column count (zeroed, so the bytes past Kp
+// that no tile writes stay zero), and their tensor maps.
+int prepare_tc_f4(sbqa_problem *p) {
+  const int Kh = tc_f4_row_bytes(p->Kp);
+  if (!p->d_J4.p) {
+    SBQA_CUDA(p->d_J4.alloc(size_t(p->Kp) * Kh));
+    SBQA_CUDA(launch_j4_from_j8(p->d_J8.p, p->Kp, p->d_J4.p, p->stream));
+  }
+  SBQA_CUDA(p->d_FT4.alloc(size_t(2) * p->Cp * Kh));
+  if (!p->tc4_plan || p->tc4_plan_ft != p->d_FT4.p || p->tc4_plan_cp != p->Cp || p->tc4_plan_j != p->d_J4.p) {
+    SBQA_CUDA(cudaMemsetAsync(p->d_FT4.p, 0, size_t(2) * p->Cp * Kh, p->stream));
+    if (p->tc4_plan) tc4_plan_free(p->tc4_plan);
+    p->tc4_plan = nullptr;
+    if (!tc4_plan_make(&p->tc4_plan, p->d_J4.p, p->d_FT4.p, p->Kp, p->Cp))
+      return fail(SBQA_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    p->tc4_plan_ft = p->d_FT4.p;
+    p->tc4_plan_j = p->d_J4.p;
+    p->tc4_plan_cp = p->Cp;
+  }
+  return SBQA_OK;
+}
+
 // Autotuner of the dense tensor-core path: times the per-step kernel, the
 // persistent solver with 128 x 128 tiles and, where the instance qualifies,
 // the split-K and the paired persistent solvers (same state buffers, before
 // the initial state is written) and keeps the fastest.  kernel_select 1
 // forces the per-step kernel, 2 the persistent solver (split-K where it
 // qualifies), 12 the persistent solver with 128 x 128 tiles, 13 the paired
-// persistent solver where it qualifies.  Cached per handle, column count,
-// replica count and selection, and process-wide per instance shape.
+// persistent solver where it qualifies, 14 the e2m1 solver where it
+// qualifies (else as 12).  Cached per handle, column count, replica count
+// and selection, and process-wide per instance shape.
 int autotune_tc(sbqa_problem *p) {
   if (!p->use_tc) {
-    p->use_tc_persistent = p->use_tc_split = p->use_tc_pair = false;
+    p->use_tc_persistent = p->use_tc_split = p->use_tc_pair = p->use_tc_f4 = false;
     return SBQA_OK;
   }
   if (p->tc_select_cp == p->Cp && p->tc_select == p->prm.kernel_select && p->tc_select_p == p->P) return SBQA_OK;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   SBQA_CUDA(cudaStreamIsCapturing(p->stream, &cs));
   if (cs != cudaStreamCaptureStatusNone) return SBQA_OK;
-  p->use_tc_persistent = p->use_tc_split = p->use_tc_pair = false;
+  p->use_tc_persistent = p->use_tc_split = p->use_tc_pair = p->use_tc_f4 = false;
   p->tc_step_ms = p->tc_persistent_ms = 0.f;
   if (p->tc_persist_blocks == 0) p->tc_persist_blocks = tc_persistent_blocks();
   if (p->tc_split_blocks < 0) p->tc_split_blocks = tc_split_blocks();
   if (p->tc_pair_blocks < 0) p->tc_pair_blocks = tc_pair_blocks();
+  if (p->tc_f4_blocks < 0) p->tc_f4_blocks = tc_f4_blocks();
   const int sel = p->prm.kernel_select;
   if (sel != 1 && p->S > 0 && p->tc_persistent_ok()) {
     SBQA_CUDA(p->d_tc_flags.alloc(tc_persistent_flag_count(p->Kp, p->Cp)));
+    if (p->tc_f4_possible()) {
+      const int frc = prepare_tc_f4(p);
+      if (frc != SBQA_OK) return frc;
+    }
     SBQA_CUDA(cudaMemsetAsync(p->d_err.p, 0, sizeof(int), p->stream));  // read after the trial launches
     // a cluster launch the device refuses, or one that does not arrive as 2-CTA
     // clusters (the kernel then reports ERR_CLUSTER_SHAPE before touching
@@ -1098,14 +1134,16 @@ int autotune_tc(sbqa_problem *p) {
         (prc = probe(&p->use_tc_pair, &p->tc_pair_failed)) != SBQA_OK)
       return prc;
     TuneResult known;
-    if (sel == 2 || sel == 12 || sel == 13) {
+    if (sel == 2 || sel == 12 || sel == 13 || sel == 14) {
       p->use_tc_persistent = true;
       p->use_tc_split = sel == 2 && p->tc_split_possible();
       p->use_tc_pair = sel == 13 && p->tc_pair_possible();
+      p->use_tc_f4 = sel == 14 && p->tc_f4_possible();
     } else if (tune_lookup(p, &known)) {
       p->use_tc_persistent = known.use_tc_persistent;
       p->use_tc_split = known.use_tc_split;
       p->use_tc_pair = known.use_tc_pair;
+      p->use_tc_f4 = known.use_tc_f4;
       p->tc_step_ms = known.tc_step_ms;
       p->tc_persistent_ms = known.tc_persistent_ms;
     } else {
@@ -1119,14 +1157,17 @@ int autotune_tc(sbqa_problem *p) {
           &ms);
       if (rc != SBQA_OK) return rc;
       p->tc_step_ms = ms;
-      // the persistent candidates: 128 x 128 tiles, then split-K and CTA pairs where they qualify
+      // the persistent candidates: 128 x 128 tiles, then split-K, CTA pairs and e2m1 where they qualify
       const int steps = std::min(p->S, 64);
       float best_persistent = 0.f;
       int best_cand = 0;
-      for (int cand = 0; cand < 3; ++cand) {
-        if ((cand == 1 && !p->tc_split_possible()) || (cand == 2 && !p->tc_pair_possible())) continue;
+      for (int cand = 0; cand < 4; ++cand) {
+        if ((cand == 1 && !p->tc_split_possible()) || (cand == 2 && !p->tc_pair_possible()) ||
+            (cand == 3 && !p->tc_f4_possible()))
+          continue;
         p->use_tc_split = cand == 1;
         p->use_tc_pair = cand == 2;
+        p->use_tc_f4 = cand == 3;
         cudaEvent_t e0, e1;
         SBQA_CUDA(cudaEventCreate(&e0));
         SBQA_CUDA(cudaEventCreate(&e1));
@@ -1148,6 +1189,7 @@ int autotune_tc(sbqa_problem *p) {
       }
       p->use_tc_split = best_cand == 1;
       p->use_tc_pair = best_cand == 2;
+      p->use_tc_f4 = best_cand == 3;
       p->tc_persistent_ms = best_persistent;
       p->use_tc_persistent = p->tc_persistent_ms < p->tc_step_ms;
       int err = 0;
@@ -1157,6 +1199,7 @@ int autotune_tc(sbqa_problem *p) {
       r.use_tc_persistent = p->use_tc_persistent;
       r.use_tc_split = p->use_tc_split;
       r.use_tc_pair = p->use_tc_pair;
+      r.use_tc_f4 = p->use_tc_f4;
       r.tc_step_ms = p->tc_step_ms;
       r.tc_persistent_ms = p->tc_persistent_ms;
       tune_store(p, r);
@@ -1644,7 +1687,7 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info) {
   info->max_abs_j = p->max_abs_j;
   info->c0_auto = p->c0_auto;
   const bool tc_pers = p->use_tc && p->use_tc_persistent && p->tc_persistent_ok();
-  int tc_kernel = tc_pers ? (p->tc_pair_ok() ? 9 : p->tc_split_ok() ? 8 : 5) : 2;
+  int tc_kernel = tc_pers ? (p->tc_f4_ok() ? 15 : p->tc_pair_ok() ? 9 : p->tc_split_ok() ? 8 : 5) : 2;
   if (p->tc_op == kTcOpBf16) tc_kernel = tc_pers ? 11 : 10;
   if (p->tc_op == kTcOpBsb) tc_kernel = tc_pers ? 13 : 12;
   info->step_kernel = !p->begun ? -1
@@ -1671,7 +1714,7 @@ int sbqa_set_schedule(sbqa_problem *p, const sbqa_params *q) {
   if (q->precision == SBQA_PREC_EXACT && (!p->j_integer || p->max_abs_j > kExactMaxAbsJ))
     return fail(SBQA_ERR_UNSUPPORTED, "EXACT precision needs integer J with |J_ij| <= 256");
   if (q->eval_every < 0 || q->n_runs < 0) return fail(SBQA_ERR_INVALID_ARG, "negative eval_every or n_runs");
-  if (q->kernel_select < 0 || q->kernel_select > 13) return fail(SBQA_ERR_INVALID_ARG, "kernel_select must be 0..13");
+  if (q->kernel_select < 0 || q->kernel_select > 14) return fail(SBQA_ERR_INVALID_ARG, "kernel_select must be 0..14");
   if (q->n_runs > 0 && (!q->beta || !q->alpha)) return fail(SBQA_ERR_INVALID_ARG, "beta/alpha missing");
   std::vector<double> beta, alpha;
   if (q->n_runs > 0) {
@@ -1708,6 +1751,7 @@ int sbqa_run_begin(sbqa_problem *p, int32_t steps, int32_t P, int32_t R, uint64_
   SBQA_CUDA(cudaMemsetAsync(p->d_err.p, 0, sizeof(int), p->stream));
   SBQA_CUDA(launch_init(s, seed, float(p->prm.init_amp), 0.0f, p->stream));
   if (p->use_tc) SBQA_CUDA(launch_f_to_ft(s, 0, p->d_FT.p, p->Kp, 0, p->tc_op, p->stream));
+  if (p->tc_f4_ok()) SBQA_CUDA(launch_f_to_ft4(s, 0, p->d_FT4.p, p->Kp, 0, p->stream));
   if (p->ballistic() && !p->use_tc) SBQA_CUDA(launch_copy_fx(s, 0, p->stream));
   SBQA_CUDA(launch_reset_best(s, p->best(), p->stream));
   p->step_done = 0;
@@ -1906,6 +1950,8 @@ int sbqa_set_state(sbqa_problem *p, const float *x, const float *y, int32_t step
   SBQA_CUDA(launch_refresh_f(p->state(), step_done & 1, float(p->prm.delta_slope * tau), p->stream));
   if (p->use_tc)
     SBQA_CUDA(launch_f_to_ft(p->state(), step_done & 1, p->d_FT.p, p->Kp, step_done & 1, p->tc_op, p->stream));
+  if (p->tc_f4_ok())
+    SBQA_CUDA(launch_f_to_ft4(p->state(), step_done & 1, p->d_FT4.p, p->Kp, step_done & 1, p->stream));
   if (p->ballistic() && !p->use_tc) SBQA_CUDA(launch_copy_fx(p->state(), step_done & 1, p->stream));
   p->step_done = step_done;
   p->finished = false;

@@ -44,6 +44,11 @@ struct TcOp {
   }
 };
 
+// 2D tensor map [rows][cols] (cols contiguous) with the given box and
+// swizzle (step_dense_tc.cu); false when the driver refuses it.
+bool tc_make_map(CUtensorMap *m, const void *base, CUtensorMapDataType dt, size_t esize, uint64_t rows,
+                 uint64_t cols, uint32_t box_cols, uint32_t box_rows, CUtensorMapSwizzle sw);
+
 struct TcArgs {
   int Kp;
   uint8_t *FT;  // [2][Cp][Kp]

@@ -189,6 +189,23 @@ cudaError_t tc_batch_launch(TcBatch *b, cudaStream_t st);
 cudaError_t tc_batch_set_attributes();
 int tc_batch_blocks();
 
+// The persistent dense solver with the product in packed e2m1 on the
+// block-scaled tensor cores (tcgen05.mma kind::mxf4, unit scale factors;
+// solve_dense_tc_f4.cu): integer |J_ij| <= 4, a CTA's J rows resident in
+// shared memory (Kp <= 2304).  J4 [Kp][Kh] and FT4 [2][Cp][Kh] bytes, Kh =
+// tc_f4_row_bytes(Kp), two spins per byte; the same flags, step protocol and
+// results (bit for bit) as launch_solve_dense_tc_persistent.
+int tc_f4_row_bytes(int Kp);
+int tc_f4_blocks();
+bool tc_f4_eligible(int Kp, int Cp, int blocks);
+cudaError_t tc_f4_set_attributes();
+bool tc4_plan_make(void **plan, const void *J4, void *FT4, int Kp, int Cp);
+void tc4_plan_free(void *plan);
+cudaError_t launch_j4_from_j8(const uint8_t *J8, int Kp, uint8_t *J4, cudaStream_t st);
+cudaError_t launch_f_to_ft4(const StateView &s, int which, uint8_t *FT4, int Kp, int buffer, cudaStream_t st);
+cudaError_t launch_solve_dense_tc_f4(const void *plan, const StateView &s, int Kp, int *err, const float *h,
+                                     const StepTables &t, int n_begin, int n_end, uint32_t *flags, cudaStream_t st);
+
 // The persistent dense solver on 2-CTA clusters sharing M=256 MMAs
 // (tcgen05 cta_group::2; step_dense_tc.cu): padded N a multiple of 256,
 // row-tile pairs x column tiles co-resident as clusters (tc_pair_blocks()).

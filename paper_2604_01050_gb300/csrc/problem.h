@@ -208,6 +208,13 @@ struct sbqa_problem {
   bool use_tc_pair = false;      // the persistent dense solver runs on CTA pairs sharing M=256 MMAs
   int tc_select_cp = -1, tc_select = -1, tc_select_p = -1;
   sbqa::DevBuf<uint32_t> d_tc_flags;  // per-tile step counters of the persistent solver
+  // the persistent solver in packed e2m1 (integer |J_ij| <= 4, J rows resident in shared memory)
+  sbqa::DevBuf<uint8_t> d_J4, d_FT4;
+  void *tc4_plan = nullptr;
+  const void *tc4_plan_ft = nullptr, *tc4_plan_j = nullptr;
+  int tc4_plan_cp = 0;
+  int tc_f4_blocks = -1;  // co-resident CTAs of the e2m1 solver (-1: not queried yet)
+  bool use_tc_f4 = false;
   sbqa::DevBuf<float> d_x, d_y;
   sbqa::DevBuf<uint8_t> d_F0, d_F1;
   // ELL slots of rows with degree <= 8 (built for value kind ell_kind)
@@ -262,6 +269,13 @@ struct sbqa_problem {
            sbqa::tc_pair_eligible(Kp, Cp, tc_pair_blocks);
   }
   bool tc_pair_ok() const { return use_tc_pair && tc_pair_possible(); }
+
+  // the instance qualifies for the persistent solver with e2m1 operands (autotuned, or kernel_select 14)
+  bool tc_f4_possible() const {
+    return tc_persistent_ok() && tc_op == sbqa::kTcOpF8 && j_integer && max_abs_j <= 4 &&
+           (prm.kernel_select == 0 || prm.kernel_select == 14) && sbqa::tc_f4_eligible(Kp, Cp, tc_f4_blocks);
+  }
+  bool tc_f4_ok() const { return use_tc_f4 && tc4_plan && tc_f4_possible(); }
 
   int persist_mode() const {
     return sbqa::persistent_mode(n, Cp, max_degree, kind, persist_blocks, prm.kernel_select == 11,

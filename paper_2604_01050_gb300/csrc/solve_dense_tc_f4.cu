@@ -1,0 +1,470 @@
+// solve_dense_tc_f4.cu -- the persistent dense solver with the coupling
+// product G = J . f in packed 4-bit floats (e2m1) on the block-scaled
+// tensor-core path, tcgen05.mma kind::mxf4 (Sec. II A, Eqs. 5-8).
+//
+// Integer couplings |J_ij| <= 4 and the codes f in {-1, 0, 1} of Eq. 8 are
+// exact in e2m1 (0, 1, 2, 3, 4 and their negatives are e2m1 values).  Every
+// scale factor is 2^0: the two scale-factor regions of tensor memory are
+// filled with the ue8m0 code 127 before the first MMA, whatever part of them
+// an MMA reads.  The products are summed in FP32 in TMEM, so G_ic is the same
+// integer as in the e4m3 solver and the states agree bit for bit.
+//
+// Two values share a byte, so a step moves half the operand bytes of the e4m3
+// form, and the 128 rows of J of a CTA (Kh bytes each, at most 144 KB for
+// Kp <= 2304) stay in shared memory for the whole launch: per step only the
+// f tiles stream in (16 KB per 256 spins).  That removes most of the traffic
+// that bounds the e4m3 solver's K loop, where the MMAs' shared-memory reads
+// and the TMA writes of both operands into the same memory serialise.
+//
+// Layout: J4 [Kp][Kh] and FT4 [2][Cp][Kh] bytes with Kh = 128 ceil(Kp / 256)
+// (zeros past Kp); spin 2t in the low nibble of byte t, 2t + 1 in the high
+// nibble.  The MMA pairs element k of A with element k of B, so any nibble
+// order that both operands share gives the same sums.
+//
+// Step counters, bounded waits, the epilogue (sb_update_regs32) and the stop
+// protocol are those of the e4m3 persistent solver (dense_tc_persistent.cuh);
+// a k-block of 256 spins waits for the counters of its two row tiles.
+#include "dense_tc_persistent.cuh"
+
+namespace sbqa {
+
+constexpr int kOpF4 = 3;
+constexpr int kF4Stages = 4;
+constexpr int kF4MaxKB = 9;                 // resident J boxes of 256 spins: Kp <= 2304
+constexpr int kF4Box = kTcBM * 128;         // 128 rows x 128 bytes (256 e2m1 values per row)
+constexpr int kF4FTile = kTcBN * 64;        // packed f tile: 128 columns x 64 bytes (128 spins)
+constexpr uint32_t kTmemSfa = 384, kTmemSfb = 416;  // scale factors of A and B, 32 columns each
+constexpr uint32_t kUnitScales = 0x7F7F7F7Fu;       // four ue8m0 codes of 2^0
+constexpr int kF4Smem = (kF4MaxKB + kF4Stages) * kF4Box + kF4FTile + 1024 + 256;
+static_assert(kF4Smem <= 227 * 1024, "resident J, stages and f tile exceed the shared memory of one CTA");
+static_assert(kTmemSfb + 32 <= kTmemCols, "scale-factor regions outside the allocated tensor memory");
+
+// Instruction descriptor of tcgen05.mma kind::mxf4 (block-scaled): A = B =
+// e2m1, both K-major, ue8m0 scale factors (ids 0), shape M x N.
+__host__ __device__ constexpr uint32_t idesc_mxf4(int M, int N) {
+  return (1u << 7) | (1u << 10)        // A, B format: e2m1
+         | (uint32_t(N >> 3) << 17)    // N / 8
+         | (1u << 23)                  // scale-factor type: ue8m0
+         | (uint32_t(M >> 7) << 27);   // M / 128
+}
+
+// D (+)= (A . scale A) (B . scale B) with packed e2m1 operands (K = 64 per
+// instruction: 32 bytes of a 128-byte swizzled row), two scale factors per
+// row and instruction (blocks of 32 along K), FP32 accumulator in TMEM.
+__device__ __forceinline__ void mma_mxf4(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t tmem_sfa, uint32_t tmem_sfb, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %6, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(tmem_sfa), "r"(tmem_sfb), "r"(accumulate)
+      : "memory");
+}
+
+// f codes of one spin row's 32 columns as e2m1 nibbles in registers: column
+// j at bits 4 (j % 8) of word j / 8 (+1 = 0x2, -1 = 0xA, 0 = 0); the warp
+// pairs rows 2t and 2t + 1 into bytes afterwards.
+template <>
+struct FOut<kOpF4> {
+  uint32_t *nib;
+  __device__ __forceinline__ void put(int j, float x, float delta) const {
+    const uint32_t c = x > delta ? 0x2u : (x < -delta ? 0xAu : 0u);
+    nib[j >> 3] |= c << (4 * (j & 7));
+  }
+  __device__ __forceinline__ void zero(int) const {}
+};
+
+struct Tc4Maps {
+  CUtensorMap A;    // J4 [Kp][Kh]: 128 rows x 128 bytes, 128B swizzle
+  CUtensorMap B;    // FT4 [2 Cp][Kh]: 128 columns x 128 bytes, 128B swizzle
+  CUtensorMap Fst;  // FT4 tile store: 128 columns x 64 bytes, no swizzle
+  int Kh;           // bytes per row of J4 and FT4 (a multiple of 128)
+};
+
+// Steps [a.n_begin, a.n_end) of tile (blockIdx.y, blockIdx.x): 128 spin rows
+// x 128 replica columns, x and y resident in TMEM (columns 128-383, the
+// accumulator in 0-127, the scale factors in 384-447).
+template <int P, bool GEN>
+__global__ void __launch_bounds__(kTpThreads, 1)
+    k_solve_dense_tc_f4(const __grid_constant__ Tc4Maps m, StateView s, TpArgs a, StepTables t) {
+  const int mt = blockIdx.y, ct = blockIdx.x;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int KB = m.Kh / 128;     // k-blocks of 256 spins
+  const int Mt = a.Kp / kTcBM;   // row tiles: step counters per column tile
+  uint8_t *sA = smem;                     // this tile's J rows, KB boxes, loaded once
+  uint8_t *sB = sA + KB * kF4Box;         // f stages
+  uint8_t *sF = sB + kF4Stages * kF4Box;  // packed f(x_next) tile [128 columns][64 bytes]
+  uint64_t *full = reinterpret_cast<uint64_t *>(sF + kF4FTile);
+  uint64_t *empty = full + kF4Stages;
+  uint64_t *done = empty + kF4Stages;
+  uint64_t *jfull = done + 1;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(jfull + 1);
+  int *s_abort = reinterpret_cast<int *>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = mt * kTcBM, n0 = ct * kTcBN;
+  const int quarter = warp & 3, chunk = warp >> 2;
+  const int rl = quarter * 32 + lane, i = m0 + rl;
+  const int cl = 32 * chunk, c0 = n0 + cl;
+  const uint32_t lane_off = uint32_t(quarter * 32) << 16;
+
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kF4Stages; ++q) {
+      tc::mbar_init(&full[q], 1);
+      tc::mbar_init(&empty[q], 1);
+    }
+    tc::mbar_init(done, 1);
+    tc::mbar_init(jfull, 1);
+    tc::fence_mbar_init();
+    tc::prefetch_tmap(&m.A);
+    tc::prefetch_tmap(&m.B);
+    tc::prefetch_tmap(&m.Fst);
+    *s_abort = 0;
+  }
+  if (warp == 0) tc::tmem_alloc(tmem_slot, kTmemCols);
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  {  // the state tile (rows past N hold zeros and stay unchanged) and the unit scale factors into TMEM
+    uint32_t xr[32], yr[32];
+    if (i < s.N) {
+      const float4 *px = reinterpret_cast<const float4 *>(s.x + size_t(i) * s.Cp + c0);
+      const float4 *py = reinterpret_cast<const float4 *>(s.y + size_t(i) * s.Cp + c0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float4 vx = px[u], vy = py[u];
+        xr[4 * u] = __float_as_uint(vx.x); xr[4 * u + 1] = __float_as_uint(vx.y);
+        xr[4 * u + 2] = __float_as_uint(vx.z); xr[4 * u + 3] = __float_as_uint(vx.w);
+        yr[4 * u] = __float_as_uint(vy.x); yr[4 * u + 1] = __float_as_uint(vy.y);
+        yr[4 * u + 2] = __float_as_uint(vy.z); yr[4 * u + 3] = __float_as_uint(vy.w);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 32; ++j) xr[j] = yr[j] = 0u;
+    }
+    __syncwarp();
+    tc::tmem_st_32x32b_x32(tmem + lane_off + kTmemX + cl, xr);
+    tc::tmem_st_32x32b_x32(tmem + lane_off + kTmemY + cl, yr);
+    if (chunk < 2) {  // warps 0-3: scale factors of A, warps 4-7: of B (all 128 lanes, 32 columns each)
+      uint32_t sf[32];
+#pragma unroll
+      for (int j = 0; j < 32; ++j) sf[j] = kUnitScales;
+      tc::tmem_st_32x32b_x32(tmem + lane_off + (chunk == 0 ? kTmemSfa : kTmemSfb), sf);
+    }
+    tc::tmem_wait_st();
+  }
+  const float hi = i < s.N ? __ldg(a.h + i) : 0.f;
+  if (warp == 0 && lane == 0 && a.n_begin < a.n_end) {  // this tile's J rows, resident for the launch
+    tc::mbar_arrive_expect_tx(jfull, uint32_t(KB * kF4Box));
+    for (int kb = 0; kb < KB; ++kb) tc::tma_load_2d(sA + kb * kF4Box, &m.A, jfull, kb * 128, m0);
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  tc::tc_fence_after();
+
+  constexpr uint32_t idesc = idesc_mxf4(kTcBM, kTcBN);
+  int n = a.n_begin;
+  for (; n < a.n_end; ++n) {
+    const uint32_t q = uint32_t(n - a.n_begin);
+    if (warp == 0) {
+      // producer: the f tiles of k-block kb once row tiles 2 kb and 2 kb + 1 have published step q
+      const int brow = (n & 1) * s.Cp + n0;
+      uint64_t t0 = 0;
+      uint32_t polls = 0;
+      int kb = 0;
+      while (kb < KB) {
+        const int kq = kb + lane;
+        bool ok = q == 0 || kq >= KB;
+        if (!ok) {
+          const int r1 = 2 * kq + 1;
+          ok = tc::ld_acquire_gpu(a.flags + (2 * kq) * a.Ct + ct) >= q &&
+               (r1 >= Mt || tc::ld_acquire_gpu(a.flags + r1 * a.Ct + ct) >= q);
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, ok);
+        int nready = ball == 0xffffffffu ? 32 : __ffs(~ball) - 1;
+        nready = nready < KB - kb ? nready : KB - kb;
+        if (nready == 0) {
+          int give_up = 0;
+          if (lane == 0) {
+            const uint64_t now = tc::globaltimer_ns();
+            if (t0 == 0) t0 = now;
+            if (*reinterpret_cast<volatile int *>(a.err) != 0) {
+              give_up = 1;
+            } else if (now - t0 > kFlagTimeoutNs || ++polls > (1u << 26)) {
+              atomicCAS(a.err, 0, tc::ERR_WAIT_FLAG);
+              give_up = 1;
+            }
+          }
+          if (__shfl_sync(0xffffffffu, give_up, 0)) {
+            nready = KB - kb;  // proceed with whatever the buffer holds; the run reports the error
+          } else {
+            __nanosleep(64);
+            continue;
+          }
+        }
+        if (lane == 0) {
+          asm volatile("fence.acq_rel.gpu;" ::: "memory");
+          tc::fence_proxy_async_global();
+          for (int j = kb; j < kb + nready; ++j) {
+            const uint32_t g = q * KB + j, st = g % kF4Stages, use = g / kF4Stages;
+            if (use > 0) tc::mbar_wait(&empty[st], (use - 1) & 1, a.err, tc::ERR_WAIT_EMPTY);
+            tc::mbar_arrive_expect_tx(&full[st], kF4Box);
+            tc::tma_load_2d(sB + st * kF4Box, &m.B, &full[st], j * 128, brow);
+          }
+        }
+        __syncwarp();
+        kb += nready;
+      }
+    } else if (warp == 1 && lane == 0) {
+      if (q == 0) tc::mbar_wait(jfull, 0, a.err, tc::ERR_WAIT_FULL);
+      for (int kb = 0; kb < KB; ++kb) {
+        const uint32_t g = q * KB + kb, st = g % kF4Stages, use = g / kF4Stages;
+        tc::mbar_wait(&full[st], use & 1, a.err, tc::ERR_WAIT_FULL);
+        tc::tc_fence_after();
+        const uint32_t a0 = tc::smem_u32(sA + kb * kF4Box), b0 = tc::smem_u32(sB + st * kF4Box);
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk)
+          mma_mxf4(tmem, tc::smem_desc_sw128(a0 + kk * 32), tc::smem_desc_sw128(b0 + kk * 32), idesc,
+                   tmem + kTmemSfa, tmem + kTmemSfb, (kb | kk) != 0 ? 1u : 0u);
+        tc::mma_commit(&empty[st]);
+      }
+      tc::mma_commit(done);
+    }
+    __syncwarp();
+    const float ka = __ldg(t.ka + n), dnext = __ldg(t.dl + n + 1);
+    KjChunk<P> kj;
+    kj.load(s, t.kj + size_t(n) * t.R, c0);
+    tc::mbar_wait(done, q & 1, a.err, tc::ERR_WAIT_DONE);
+    tc::tc_fence_after();
+    {
+      uint32_t g[32], xr[32], yr[32];
+      tc::tmem_ld_32x32b_x32_nowait(tmem + lane_off + cl, g);
+      tc::tmem_ld_32x32b_x32_nowait(tmem + lane_off + kTmemX + cl, xr);
+      tc::tmem_ld_32x32b_x32_nowait(tmem + lane_off + kTmemY + cl, yr);
+      RingExt ext{0.f, 0.f, 0.f, 0.f};
+      if constexpr (P > 32) {
+        // runs over several chunks: their outside neighbours, read before any warp stores its new x
+        const int rb = cl - cl % P;
+        const uint32_t xb = tmem + lane_off + kTmemX;
+        const uint32_t u0 = tc::tmem_ld_32x32b_x1_nowait(xb + uint32_t(cl > rb ? cl - 1 : cl));
+        const uint32_t u1 = tc::tmem_ld_32x32b_x1_nowait(xb + uint32_t(cl + 32 < rb + P ? cl + 32 : cl));
+        const uint32_t u2 = tc::tmem_ld_32x32b_x1_nowait(xb + uint32_t(rb));
+        const uint32_t u3 = tc::tmem_ld_32x32b_x1_nowait(xb + uint32_t(rb + s.Pr - 1));
+        tc::tmem_wait_ld();
+        ext = RingExt{__uint_as_float(u0), __uint_as_float(u1), __uint_as_float(u2), __uint_as_float(u3)};
+        tc::tc_fence_before();
+        __syncthreads();
+        tc::tc_fence_after();
+      }
+      tc::tmem_wait_ld();
+      tc::reg_fence(g);
+      tc::reg_fence(xr);
+      tc::reg_fence(yr);
+      uint32_t nib[4] = {0u, 0u, 0u, 0u};
+      const FOut<kOpF4> fo{nib};
+      if (i < s.N && c0 < s.C) {
+        if (c0 + 32 <= s.C) sb_update_regs32<P, true, kOpF4, GEN>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, fo, ext);
+        else sb_update_regs32<P, false, kOpF4, GEN>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, fo, ext);
+      }
+      // rows 2t (even lane) and 2t + 1 (the next lane) share byte t of each column of the f tile
+#pragma unroll
+      for (int w = 0; w < 4; ++w) {
+        const uint32_t o = __shfl_down_sync(0xffffffffu, nib[w], 1);
+        if ((lane & 1) == 0) {
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            sF[(cl + 8 * w + c) * 64 + (rl >> 1)] = uint8_t(((nib[w] >> (4 * c)) & 0xFu) | (((o >> (4 * c)) & 0xFu) << 4));
+        }
+      }
+      __syncwarp();
+      tc::tmem_st_32x32b_x32(tmem + lane_off + kTmemX + cl, xr);
+      tc::tmem_st_32x32b_x32(tmem + lane_off + kTmemY + cl, yr);
+      tc::tmem_wait_st();
+    }
+    tc::fence_proxy_async_smem();
+    tc::tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      // publish f_{n+1} of this tile: spins m0.. (bytes m0 / 2..), columns n0.. of the other FT4 buffer
+      tc::tma_store_2d(&m.Fst, sF, m0 / 2, ((n + 1) & 1) * s.Cp + n0);
+      tc::tma_store_commit_and_wait_all();
+      tc::fence_proxy_async_global();
+      if (n != a.hold_step || mt != 0 || ct != 0) tc::st_release_gpu(a.flags + mt * a.Ct + ct, q + 1);
+      *s_abort = *reinterpret_cast<volatile int *>(a.err);
+    }
+    __syncthreads();
+    tc::tc_fence_after();
+    if (*s_abort != 0) break;
+  }
+  __syncwarp();
+  {  // the state tile back to global memory
+    uint32_t xr[32], yr[32];
+    tc::tmem_ld_32x32b_x32_nowait(tmem + lane_off + kTmemX + cl, xr);
+    tc::tmem_ld_32x32b_x32_nowait(tmem + lane_off + kTmemY + cl, yr);
+    tc::tmem_wait_ld();
+    tc::reg_fence(xr);
+    tc::reg_fence(yr);
+    if (i < s.N) {
+      float4 *px = reinterpret_cast<float4 *>(s.x + size_t(i) * s.Cp + c0);
+      float4 *py = reinterpret_cast<float4 *>(s.y + size_t(i) * s.Cp + c0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        px[u] = make_float4(__uint_as_float(xr[4 * u]), __uint_as_float(xr[4 * u + 1]),
+                            __uint_as_float(xr[4 * u + 2]), __uint_as_float(xr[4 * u + 3]));
+        py[u] = make_float4(__uint_as_float(yr[4 * u]), __uint_as_float(yr[4 * u + 1]),
+                            __uint_as_float(yr[4 * u + 2]), __uint_as_float(yr[4 * u + 3]));
+      }
+    }
+  }
+  tc::tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc::tc_fence_after();
+    tc::tmem_dealloc(tmem, kTmemCols);
+  }
+}
+
+// e2m1 nibble of an e4m3 byte holding an integer |v| <= 4 (the only values
+// an eligible instance has): 1, 2, 3, 4 -> 0x2, 0x4, 0x5, 0x6, sign in bit 3.
+__device__ __forceinline__ uint32_t e2m1_of_e4m3_int(uint8_t e) {
+  const uint32_t mag = e & 0x7Fu;
+  const uint32_t m = mag == 0x38u ? 0x2u : mag == 0x40u ? 0x4u : mag == 0x44u ? 0x5u : mag == 0x48u ? 0x6u : 0u;
+  return m == 0u ? 0u : (m | ((e & 0x80u) >> 4));
+}
+
+// J8 (e4m3 [Kp][Kp]) -> J4 ([Kp][Kh] bytes, two spins per byte, zeros past Kp).
+__global__ void k_j4_from_j8(const uint8_t *J8, int Kp, int Kh, uint8_t *J4) {
+  const size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x;  // over Kp * Kh
+  if (e >= size_t(Kp) * Kh) return;
+  const int r = int(e / Kh), j = 2 * int(e % Kh);
+  uint32_t v = 0;
+  if (j < Kp) v = e2m1_of_e4m3_int(J8[size_t(r) * Kp + j]);
+  if (j + 1 < Kp) v |= e2m1_of_e4m3_int(J8[size_t(r) * Kp + j + 1]) << 4;
+  J4[e] = uint8_t(v);
+}
+
+// f codes of F buffer `which` ([N][Cp], f + 1) -> FT4 buffer b ([Cp][Kh],
+// spins 2t and 2t + 1 in byte t, zeros for padded spins).
+__global__ void k_f_to_ft4(StateView s, int which, uint8_t *FT4, int Kh, int b) {
+  const size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x;  // over Cp * Kh
+  if (e >= size_t(s.Cp) * Kh) return;
+  const int c = int(e / Kh), j = 2 * int(e % Kh);
+  uint32_t v = 0;
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    if (j + u < s.N) {
+      const int f = int(s.f_of(which)[size_t(j + u) * s.Cp + c]) - 1;
+      v |= (f == 0 ? 0u : (f > 0 ? 0x2u : 0xAu)) << (4 * u);
+    }
+  }
+  FT4[size_t(b) * s.Cp * Kh + e] = uint8_t(v);
+}
+
+// ---------------------------------------------------------------- host side
+#define SBQA_F4_PS(K)                                                                                        \
+  {{(const void *)K<1, false>, (const void *)K<1, false>},                                                   \
+   {(const void *)K<2, false>, (const void *)K<2, false>},                                                   \
+   {(const void *)K<4, false>, (const void *)K<4, true>},                                                    \
+   {(const void *)K<8, false>, (const void *)K<8, true>},                                                    \
+   {(const void *)K<16, false>, (const void *)K<16, true>},                                                  \
+   {(const void *)K<32, false>, (const void *)K<32, true>},                                                  \
+   {(const void *)K<64, true>, (const void *)K<64, true>},                                                   \
+   {(const void *)K<128, true>, (const void *)K<128, true>}}
+static const void *const kF4Fns[8][2] = SBQA_F4_PS(k_solve_dense_tc_f4);
+#undef SBQA_F4_PS
+
+static int f4_p_index(int P) {
+  for (int q = 0; q < 8; ++q)
+    if ((1 << q) == P) return q;
+  return -1;
+}
+
+int tc_f4_row_bytes(int Kp) { return (Kp + 255) / 256 * 128; }
+
+static int f4_smem(int Kp) { return (tc_f4_row_bytes(Kp) / 128 + kF4Stages) * kF4Box + kF4FTile + 1024 + 256; }
+
+cudaError_t tc_f4_set_attributes() {
+  for (int q = 0; q < 8; ++q)
+    for (const void *f : kF4Fns[q]) {
+      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kF4Smem);
+      if (e != cudaSuccess) return e;
+    }
+  return cudaSuccess;
+}
+
+int tc_f4_blocks() {
+  int dev = 0, sms = 0, best = 1 << 30;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (tc_f4_set_attributes() != cudaSuccess) return 0;
+  for (int q = 0; q < 8; ++q)
+    for (const void *f : kF4Fns[q]) {
+      int per_sm = 0;
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kTpThreads, kF4Smem) != cudaSuccess) return 0;
+      best = per_sm < best ? per_sm : best;
+    }
+  return sms * best;
+}
+
+bool tc_f4_eligible(int Kp, int Cp, int blocks) {
+  return blocks > 0 && Kp % kTcBM == 0 && Cp % kTcBN == 0 && tc_f4_row_bytes(Kp) / 128 <= kF4MaxKB &&
+         (Kp / kTcBM) * (Cp / kTcBN) <= blocks;
+}
+
+bool tc4_plan_make(void **plan, const void *J4, void *FT4, int Kp, int Cp) {
+  auto *p = new Tc4Maps();
+  const auto U8 = CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  const int Kh = tc_f4_row_bytes(Kp);
+  p->Kh = Kh;
+  const uint64_t rows_ft = uint64_t(2) * Cp;
+  const bool ok =
+      tc_make_map(&p->A, J4, U8, 1, uint64_t(Kp), uint64_t(Kh), 128, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
+      tc_make_map(&p->B, FT4, U8, 1, rows_ft, uint64_t(Kh), 128, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
+      tc_make_map(&p->Fst, FT4, U8, 1, rows_ft, uint64_t(Kh), 64, 128, CU_TENSOR_MAP_SWIZZLE_NONE);
+  if (!ok) {
+    delete p;
+    return false;
+  }
+  *plan = p;
+  return true;
+}
+
+void tc4_plan_free(void *plan) { delete static_cast<Tc4Maps *>(plan); }
+
+cudaError_t launch_j4_from_j8(const uint8_t *J8, int Kp, uint8_t *J4, cudaStream_t st) {
+  const int Kh = tc_f4_row_bytes(Kp);
+  const size_t total = size_t(Kp) * Kh;
+  k_j4_from_j8<<<unsigned((total + 255) / 256), 256, 0, st>>>(J8, Kp, Kh, J4);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_f_to_ft4(const StateView &s, int which, uint8_t *FT4, int Kp, int buffer, cudaStream_t st) {
+  const int Kh = tc_f4_row_bytes(Kp);
+  const size_t total = size_t(s.Cp) * Kh;
+  k_f_to_ft4<<<unsigned((total + 255) / 256), 256, 0, st>>>(s, which, FT4, Kh, buffer);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve_dense_tc_f4(const void *plan, const StateView &s, int Kp, int *err, const float *h,
+                                     const StepTables &t, int n_begin, int n_end, uint32_t *flags, cudaStream_t st) {
+  const int idx = f4_p_index(s.P);
+  const auto *m = static_cast<const Tc4Maps *>(plan);
+  if (idx < 0 || Kp % kTcBM != 0 || s.Cp % kTcBN != 0 || m->Kh != tc_f4_row_bytes(Kp) ||
+      m->Kh / 128 > kF4MaxKB)
+    return cudaErrorInvalidValue;
+  const int Ct = s.Cp / kTcBN;
+  cudaError_t e = cudaMemsetAsync(flags, 0, tc_persistent_flag_count(Kp, s.Cp) * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  TpArgs a{Kp, Ct, n_begin, n_end, err, h, flags, -1};
+  Tc4Maps maps = *m;
+  StateView sv = s;
+  StepTables tv = t;
+  void *args[] = {&maps, &sv, &a, &tv};
+  return cudaLaunchCooperativeKernel(kF4Fns[idx][s.Pr != s.P ? 1 : 0], dim3(Ct, Kp / kTcBM), dim3(kTpThreads), args,
+                                     f4_smem(Kp), st);
+}
+
+}  // namespace sbqa

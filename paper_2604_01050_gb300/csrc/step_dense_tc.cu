@@ -818,7 +818,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }
 
 // 2D tensor map [rows][cols] (cols contiguous) with the given box and swizzle.
-static bool make_map(CUtensorMap *m, const void *base, CUtensorMapDataType dt, size_t esize, uint64_t rows,
+bool tc_make_map(CUtensorMap *m, const void *base, CUtensorMapDataType dt, size_t esize, uint64_t rows,
                      uint64_t cols, uint32_t box_cols, uint32_t box_rows, CUtensorMapSwizzle sw) {
   auto fn = encode_fn();
   if (!fn) return false;
@@ -848,17 +848,17 @@ bool tc_plan_make(void **plan, const void *J, void *FT, int Kp, int Cp, float *x
   const uint32_t ke = uint32_t(128 / eb);  // K elements of one 128-byte operand row
   const uint64_t rows_ft = uint64_t(2) * Cp;
   uint8_t *ftl = static_cast<uint8_t *>(FT) + rows_ft * Kp * eb;  // kOpBsb: the lo terms after the hi terms
-  bool ok = make_map(&p->A, J, OT, eb, uint64_t(Kp), uint64_t(Kp), ke, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
-            make_map(&p->B, FT, OT, eb, rows_ft, uint64_t(Kp), ke, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
-            make_map(&p->X, x, F32, 4, uint64_t(N), uint64_t(Cp), 32, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
-            make_map(&p->Y, y, F32, 4, uint64_t(N), uint64_t(Cp), 32, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
-            make_map(&p->Fst, FT, OT, eb, rows_ft, uint64_t(Kp), 128, 128, CU_TENSOR_MAP_SWIZZLE_NONE);
+  bool ok = tc_make_map(&p->A, J, OT, eb, uint64_t(Kp), uint64_t(Kp), ke, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
+            tc_make_map(&p->B, FT, OT, eb, rows_ft, uint64_t(Kp), ke, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
+            tc_make_map(&p->X, x, F32, 4, uint64_t(N), uint64_t(Cp), 32, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
+            tc_make_map(&p->Y, y, F32, 4, uint64_t(N), uint64_t(Cp), 32, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
+            tc_make_map(&p->Fst, FT, OT, eb, rows_ft, uint64_t(Kp), 128, 128, CU_TENSOR_MAP_SWIZZLE_NONE);
   if (ok && op == kOpF8)  // the wide, split-K and paired kernels run the e4m3 product only
-    ok = make_map(&p->B2, FT, OT, 1, rows_ft, uint64_t(Kp), 128, 256, CU_TENSOR_MAP_SWIZZLE_128B) &&
-         make_map(&p->B64, FT, OT, 1, rows_ft, uint64_t(Kp), 128, 64, CU_TENSOR_MAP_SWIZZLE_128B);
+    ok = tc_make_map(&p->B2, FT, OT, 1, rows_ft, uint64_t(Kp), 128, 256, CU_TENSOR_MAP_SWIZZLE_128B) &&
+         tc_make_map(&p->B64, FT, OT, 1, rows_ft, uint64_t(Kp), 128, 64, CU_TENSOR_MAP_SWIZZLE_128B);
   if (ok && op == kOpBsb)
-    ok = make_map(&p->Bl, ftl, OT, 2, rows_ft, uint64_t(Kp), ke, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
-         make_map(&p->Fstl, ftl, OT, 2, rows_ft, uint64_t(Kp), 128, 128, CU_TENSOR_MAP_SWIZZLE_NONE);
+    ok = tc_make_map(&p->Bl, ftl, OT, 2, rows_ft, uint64_t(Kp), ke, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
+         tc_make_map(&p->Fstl, ftl, OT, 2, rows_ft, uint64_t(Kp), 128, 128, CU_TENSOR_MAP_SWIZZLE_NONE);
   if (!ok) {
     delete p;
     return false;
