@@ -749,16 +749,17 @@ KERNEL_NAMES = {0: "k_step_csr", 1: "k_step_dense", 2: "k_step_dense_tc", 3: "k_
                 7: "k_step_dense_bsb", 8: "k_solve_dense_tc_split", 9: "k_solve_dense_tc_pair",
                 10: "k_step_dense_tc<bf16>", 11: "k_solve_dense_tc_persistent<bf16>",
                 12: "k_step_dense_tc<bsb>", 13: "k_solve_dense_tc_persistent<bsb>", 14: "k_solve_csr_persistent_bsb",
-                15: "k_solve_dense_tc_f4"}
+                15: "k_solve_dense_tc_f4", 16: "k_solve_dense_tc_f4_pair"}
 KERNEL_LABELS = {0: "csr", 1: "dense_cuda_core", 2: "dense_tcgen05_fp8", 3: "dense_small_one_launch",
                  4: "csr_persistent", 5: "dense_tcgen05_persistent", 6: "csr_ballistic", 7: "dense_ballistic",
                  8: "dense_tcgen05_persistent_split_k", 9: "dense_tcgen05_persistent_cta_pairs",
                  10: "dense_tcgen05_bf16", 11: "dense_tcgen05_persistent_bf16",
                  12: "dense_tcgen05_ballistic_bf16x2", 13: "dense_tcgen05_persistent_ballistic_bf16x2",
-                 14: "csr_persistent_ballistic", 15: "dense_tcgen05_persistent_e2m1"}
+                 14: "csr_persistent_ballistic", 15: "dense_tcgen05_persistent_e2m1",
+                 16: "dense_tcgen05_persistent_e2m1_cta_pairs"}
 TC_FP8 = (2, 5, 8, 9)
 TC_BF16 = (10, 11, 12, 13)
-TC_FP4 = (15,)
+TC_FP4 = (15, 16)
 FP4_OVER_FP8 = 3.0  # nominal dense e2m1 / e4m3 tensor rate of the GB300 (13.5 / 4.5 PFLOP/s)
 
 

@@ -148,7 +148,8 @@ typedef struct {
                              form; 15 the persistent dense tcgen05 solver
                              with packed e2m1 operands (kind::mxf4, unit
                              scale factors) and J resident in shared
-                             memory; -1 none                                 */
+                             memory, 16 its paired form (2-CTA clusters
+                             sharing M=256 MMAs); -1 none                    */
     int32_t step_variant; /* CSR kernel variant picked by the autotuner:
                              0-5: 4 << (v % 3) consecutive replica columns
                              per lane, v >= 3 with one wave of blocks
@@ -216,8 +217,11 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info);
  *                it beside the others); 14 = the dense tensor-core
  *                solver with packed e2m1 operands (integer |J_ij| <= 4,
  *                padded N <= 2304: each CTA keeps its 128 rows of J in
- *                shared memory and only f streams in), else as 12; with
- *                kernel_select 0 the autotuner times it beside the others.
+ *                shared memory and only f streams in), on CTA pairs that
+ *                share M=256 MMAs where padded N is a multiple of 256,
+ *                else as 12; 15 = the same solver without clusters; with
+ *                kernel_select 0 the autotuner times both forms beside the
+ *                others.
  *                For the ballistic form on CSR, 2
  *                takes its persistent solver when each warp's share of the
  *                (row, 128-column) items fits its cache (degree <= 8), 0

@@ -847,7 +847,7 @@ struct TuneKey {
 struct TuneResult {
   int csr_variant = 0;
   bool use_persistent = false, use_tc_persistent = false, use_tc_split = false, use_tc_pair = false,
-       use_tc_f4 = false;
+       use_tc_f4 = false, use_tc_f4_pair = false;
   float variant_ms[8] = {};
   float persistent_ms = 0.f, tc_step_ms = 0.f, tc_persistent_ms = 0.f;
 };
@@ -1035,8 +1035,11 @@ int autotune_csr(sbqa_problem *p) {
 // across 2-CTA clusters, or with 128 x 128 tiles, as chosen.
 cudaError_t launch_tc_persistent(sbqa_problem *p, const StateView &s, int n0, int n1, cudaStream_t st) {
   if (p->tc_f4_ok())
-    return launch_solve_dense_tc_f4(p->tc4_plan, s, p->Kp, p->d_err.p, p->d_h.p, p->tables, n0, n1,
-                                    p->d_tc_flags.p, st);
+    return p->tc_f4_pair_ok()
+               ? launch_solve_dense_tc_f4_pair(p->tc4_plan, s, p->Kp, p->d_err.p, p->d_h.p, p->tables, n0, n1,
+                                               p->d_tc_flags.p, st)
+               : launch_solve_dense_tc_f4(p->tc4_plan, s, p->Kp, p->d_err.p, p->d_h.p, p->tables, n0, n1,
+                                          p->d_tc_flags.p, st);
   if (p->tc_pair_ok())
     return launch_solve_dense_tc_pair(p->tc_plan, s, p->Kp, p->d_err.p, p->d_h.p, p->tables, n0, n1,
                                       p->d_tc_flags.p, st);
@@ -1077,23 +1080,25 @@ int prepare_tc_f4(sbqa_problem *p) {
 // forces the per-step kernel, 2 the persistent solver (split-K where it
 // qualifies), 12 the persistent solver with 128 x 128 tiles, 13 the paired
 // persistent solver where it qualifies, 14 the e2m1 solver where it
-// qualifies (else as 12).  Cached per handle, column count, replica count
+// qualifies (its paired form where that qualifies; else as 12), 15 the e2m1
+// solver without clusters (else as 12).  Cached per handle, column count, replica count
 // and selection, and process-wide per instance shape.
 int autotune_tc(sbqa_problem *p) {
   if (!p->use_tc) {
-    p->use_tc_persistent = p->use_tc_split = p->use_tc_pair = p->use_tc_f4 = false;
+    p->use_tc_persistent = p->use_tc_split = p->use_tc_pair = p->use_tc_f4 = p->use_tc_f4_pair = false;
     return SBQA_OK;
   }
   if (p->tc_select_cp == p->Cp && p->tc_select == p->prm.kernel_select && p->tc_select_p == p->P) return SBQA_OK;
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   SBQA_CUDA(cudaStreamIsCapturing(p->stream, &cs));
   if (cs != cudaStreamCaptureStatusNone) return SBQA_OK;
-  p->use_tc_persistent = p->use_tc_split = p->use_tc_pair = p->use_tc_f4 = false;
+  p->use_tc_persistent = p->use_tc_split = p->use_tc_pair = p->use_tc_f4 = p->use_tc_f4_pair = false;
   p->tc_step_ms = p->tc_persistent_ms = 0.f;
   if (p->tc_persist_blocks == 0) p->tc_persist_blocks = tc_persistent_blocks();
   if (p->tc_split_blocks < 0) p->tc_split_blocks = tc_split_blocks();
   if (p->tc_pair_blocks < 0) p->tc_pair_blocks = tc_pair_blocks();
   if (p->tc_f4_blocks < 0) p->tc_f4_blocks = tc_f4_blocks();
+  if (p->tc_f4_pair_blocks < 0) p->tc_f4_pair_blocks = tc_f4_pair_blocks();
   const int sel = p->prm.kernel_select;
   if (sel != 1 && p->S > 0 && p->tc_persistent_ok()) {
     SBQA_CUDA(p->d_tc_flags.alloc(tc_persistent_flag_count(p->Kp, p->Cp)));
@@ -1133,17 +1138,25 @@ int autotune_tc(sbqa_problem *p) {
     if ((sel == 0 || sel == 13) && p->tc_pair_possible() &&
         (prc = probe(&p->use_tc_pair, &p->tc_pair_failed)) != SBQA_OK)
       return prc;
+    if ((sel == 0 || sel == 14) && p->tc_f4_pair_possible()) {
+      p->use_tc_f4 = true;
+      prc = probe(&p->use_tc_f4_pair, &p->tc_f4_pair_failed);
+      p->use_tc_f4 = false;
+      if (prc != SBQA_OK) return prc;
+    }
     TuneResult known;
-    if (sel == 2 || sel == 12 || sel == 13 || sel == 14) {
+    if (sel == 2 || sel == 12 || sel == 13 || sel == 14 || sel == 15) {
       p->use_tc_persistent = true;
       p->use_tc_split = sel == 2 && p->tc_split_possible();
       p->use_tc_pair = sel == 13 && p->tc_pair_possible();
-      p->use_tc_f4 = sel == 14 && p->tc_f4_possible();
+      p->use_tc_f4 = (sel == 14 || sel == 15) && p->tc_f4_possible();
+      p->use_tc_f4_pair = sel == 14 && p->tc_f4_pair_possible();
     } else if (tune_lookup(p, &known)) {
       p->use_tc_persistent = known.use_tc_persistent;
       p->use_tc_split = known.use_tc_split;
       p->use_tc_pair = known.use_tc_pair;
       p->use_tc_f4 = known.use_tc_f4;
+      p->use_tc_f4_pair = known.use_tc_f4_pair;
       p->tc_step_ms = known.tc_step_ms;
       p->tc_persistent_ms = known.tc_persistent_ms;
     } else {
@@ -1161,13 +1174,14 @@ int autotune_tc(sbqa_problem *p) {
       const int steps = std::min(p->S, 64);
       float best_persistent = 0.f;
       int best_cand = 0;
-      for (int cand = 0; cand < 4; ++cand) {
+      for (int cand = 0; cand < 5; ++cand) {
         if ((cand == 1 && !p->tc_split_possible()) || (cand == 2 && !p->tc_pair_possible()) ||
-            (cand == 3 && !p->tc_f4_possible()))
+            (cand == 3 && !p->tc_f4_possible()) || (cand == 4 && !p->tc_f4_pair_possible()))
           continue;
         p->use_tc_split = cand == 1;
         p->use_tc_pair = cand == 2;
-        p->use_tc_f4 = cand == 3;
+        p->use_tc_f4 = cand >= 3;
+        p->use_tc_f4_pair = cand == 4;
         cudaEvent_t e0, e1;
         SBQA_CUDA(cudaEventCreate(&e0));
         SBQA_CUDA(cudaEventCreate(&e1));
@@ -1189,7 +1203,8 @@ int autotune_tc(sbqa_problem *p) {
       }
       p->use_tc_split = best_cand == 1;
       p->use_tc_pair = best_cand == 2;
-      p->use_tc_f4 = best_cand == 3;
+      p->use_tc_f4 = best_cand >= 3;
+      p->use_tc_f4_pair = best_cand == 4;
       p->tc_persistent_ms = best_persistent;
       p->use_tc_persistent = p->tc_persistent_ms < p->tc_step_ms;
       int err = 0;
@@ -1200,6 +1215,7 @@ int autotune_tc(sbqa_problem *p) {
       r.use_tc_split = p->use_tc_split;
       r.use_tc_pair = p->use_tc_pair;
       r.use_tc_f4 = p->use_tc_f4;
+      r.use_tc_f4_pair = p->use_tc_f4_pair;
       r.tc_step_ms = p->tc_step_ms;
       r.tc_persistent_ms = p->tc_persistent_ms;
       tune_store(p, r);
@@ -1687,7 +1703,9 @@ int sbqa_get_problem_info(const sbqa_problem *p, sbqa_problem_info *info) {
   info->max_abs_j = p->max_abs_j;
   info->c0_auto = p->c0_auto;
   const bool tc_pers = p->use_tc && p->use_tc_persistent && p->tc_persistent_ok();
-  int tc_kernel = tc_pers ? (p->tc_f4_ok() ? 15 : p->tc_pair_ok() ? 9 : p->tc_split_ok() ? 8 : 5) : 2;
+  int tc_kernel =
+      tc_pers ? (p->tc_f4_ok() ? (p->tc_f4_pair_ok() ? 16 : 15) : p->tc_pair_ok() ? 9 : p->tc_split_ok() ? 8 : 5)
+              : 2;
   if (p->tc_op == kTcOpBf16) tc_kernel = tc_pers ? 11 : 10;
   if (p->tc_op == kTcOpBsb) tc_kernel = tc_pers ? 13 : 12;
   info->step_kernel = !p->begun ? -1
@@ -1714,7 +1732,7 @@ int sbqa_set_schedule(sbqa_problem *p, const sbqa_params *q) {
   if (q->precision == SBQA_PREC_EXACT && (!p->j_integer || p->max_abs_j > kExactMaxAbsJ))
     return fail(SBQA_ERR_UNSUPPORTED, "EXACT precision needs integer J with |J_ij| <= 256");
   if (q->eval_every < 0 || q->n_runs < 0) return fail(SBQA_ERR_INVALID_ARG, "negative eval_every or n_runs");
-  if (q->kernel_select < 0 || q->kernel_select > 14) return fail(SBQA_ERR_INVALID_ARG, "kernel_select must be 0..14");
+  if (q->kernel_select < 0 || q->kernel_select > 15) return fail(SBQA_ERR_INVALID_ARG, "kernel_select must be 0..15");
   if (q->n_runs > 0 && (!q->beta || !q->alpha)) return fail(SBQA_ERR_INVALID_ARG, "beta/alpha missing");
   std::vector<double> beta, alpha;
   if (q->n_runs > 0) {

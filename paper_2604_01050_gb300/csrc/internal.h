@@ -205,6 +205,15 @@ cudaError_t launch_j4_from_j8(const uint8_t *J8, int Kp, uint8_t *J4, cudaStream
 cudaError_t launch_f_to_ft4(const StateView &s, int which, uint8_t *FT4, int Kp, int buffer, cudaStream_t st);
 cudaError_t launch_solve_dense_tc_f4(const void *plan, const StateView &s, int Kp, int *err, const float *h,
                                      const StepTables &t, int n_begin, int n_end, uint32_t *flags, cudaStream_t st);
+// Its paired form: the CTAs of row tiles 2p, 2p + 1 share M=256 MMAs (2-CTA
+// clusters, tcgen05 cta_group::2) and each stages half of every f tile, so a
+// step's f tiles are in flight at once; padded N a multiple of 256, blocks
+// = co-resident CTAs in 2-CTA clusters (tc_f4_pair_blocks()).
+int tc_f4_pair_blocks();
+bool tc_f4_pair_eligible(int Kp, int Cp, int blocks);
+cudaError_t launch_solve_dense_tc_f4_pair(const void *plan, const StateView &s, int Kp, int *err, const float *h,
+                                          const StepTables &t, int n_begin, int n_end, uint32_t *flags,
+                                          cudaStream_t st);
 
 // The persistent dense solver on 2-CTA clusters sharing M=256 MMAs
 // (tcgen05 cta_group::2; step_dense_tc.cu): padded N a multiple of 256,

@@ -215,6 +215,9 @@ struct sbqa_problem {
   int tc4_plan_cp = 0;
   int tc_f4_blocks = -1;  // co-resident CTAs of the e2m1 solver (-1: not queried yet)
   bool use_tc_f4 = false;
+  int tc_f4_pair_blocks = -1;     // co-resident CTAs of its paired form in 2-CTA clusters
+  bool tc_f4_pair_failed = false;  // the paired form's cluster launch was refused or misshaped
+  bool use_tc_f4_pair = false;
   sbqa::DevBuf<float> d_x, d_y;
   sbqa::DevBuf<uint8_t> d_F0, d_F1;
   // ELL slots of rows with degree <= 8 (built for value kind ell_kind)
@@ -270,12 +273,19 @@ struct sbqa_problem {
   }
   bool tc_pair_ok() const { return use_tc_pair && tc_pair_possible(); }
 
-  // the instance qualifies for the persistent solver with e2m1 operands (autotuned, or kernel_select 14)
+  // the instance qualifies for the persistent solver with e2m1 operands (autotuned, or kernel_select 14, 15)
   bool tc_f4_possible() const {
     return tc_persistent_ok() && tc_op == sbqa::kTcOpF8 && j_integer && max_abs_j <= 4 &&
-           (prm.kernel_select == 0 || prm.kernel_select == 14) && sbqa::tc_f4_eligible(Kp, Cp, tc_f4_blocks);
+           (prm.kernel_select == 0 || prm.kernel_select == 14 || prm.kernel_select == 15) &&
+           sbqa::tc_f4_eligible(Kp, Cp, tc_f4_blocks);
   }
   bool tc_f4_ok() const { return use_tc_f4 && tc4_plan && tc_f4_possible(); }
+  // ... and for its paired form (not with kernel_select 15)
+  bool tc_f4_pair_possible() const {
+    return tc_f4_possible() && prm.kernel_select != 15 && !tc_f4_pair_failed &&
+           sbqa::tc_f4_pair_eligible(Kp, Cp, tc_f4_pair_blocks);
+  }
+  bool tc_f4_pair_ok() const { return use_tc_f4_pair && tc_f4_ok() && tc_f4_pair_possible(); }
 
   int persist_mode() const {
     return sbqa::persistent_mode(n, Cp, max_degree, kind, persist_blocks, prm.kernel_select == 11,

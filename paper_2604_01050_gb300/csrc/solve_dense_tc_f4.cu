@@ -29,14 +29,25 @@
 namespace sbqa {
 
 constexpr int kOpF4 = 3;
-constexpr int kF4Stages = 4;
 constexpr int kF4MaxKB = 9;                 // resident J boxes of 256 spins: Kp <= 2304
 constexpr int kF4Box = kTcBM * 128;         // 128 rows x 128 bytes (256 e2m1 values per row)
 constexpr int kF4FTile = kTcBN * 64;        // packed f tile: 128 columns x 64 bytes (128 spins)
+// f stages: a single CTA stages whole 128-column k-blocks (16 KB, four
+// stages beside the resident J); a CTA of a pair stages its 64 of the pair's
+// 128 columns (8 KB), so eight stages hold every k-block of a step at once.
+template <bool PAIR>
+struct F4Shape {
+  static constexpr int kStages = PAIR ? 8 : 4;
+  static constexpr int kStageBytes = PAIR ? kF4Box / 2 : kF4Box;
+};
+constexpr int kF4Stages = 4;  // the larger staging footprint of the two forms (4 x 16 KB = 8 x 8 KB)
 constexpr uint32_t kTmemSfa = 384, kTmemSfb = 416;  // scale factors of A and B, 32 columns each
 constexpr uint32_t kUnitScales = 0x7F7F7F7Fu;       // four ue8m0 codes of 2^0
 constexpr int kF4Smem = (kF4MaxKB + kF4Stages) * kF4Box + kF4FTile + 1024 + 256;
 static_assert(kF4Smem <= 227 * 1024, "resident J, stages and f tile exceed the shared memory of one CTA");
+static_assert(F4Shape<true>::kStages * F4Shape<true>::kStageBytes == kF4Stages * kF4Box &&
+                  F4Shape<false>::kStages * F4Shape<false>::kStageBytes == kF4Stages * kF4Box,
+              "both forms fit the same shared-memory layout");
 static_assert(kTmemSfb + 32 <= kTmemCols, "scale-factor regions outside the allocated tensor memory");
 
 // Instruction descriptor of tcgen05.mma kind::mxf4 (block-scaled): A = B =
@@ -61,6 +72,19 @@ __device__ __forceinline__ void mma_mxf4(uint32_t tmem_d, uint64_t adesc, uint64
       : "memory");
 }
 
+// The same MMA for a CTA pair, issued by the even CTA: A (M = 256) is the two
+// CTAs' 128-row tiles at the same shared-memory address, B the two CTAs'
+// 64-column halves; each CTA's TMEM receives its own 128 rows.
+__device__ __forceinline__ void mma_mxf4_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                              uint32_t tmem_sfa, uint32_t tmem_sfb, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %6, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(tmem_sfa), "r"(tmem_sfb), "r"(accumulate)
+      : "memory");
+}
+
 // f codes of one spin row's 32 columns as e2m1 nibbles in registers: column
 // j at bits 4 (j % 8) of word j / 8 (+1 = 0x2, -1 = 0xA, 0 = 0); the warp
 // pairs rows 2t and 2t + 1 into bytes afterwards.
@@ -77,40 +101,72 @@ struct FOut<kOpF4> {
 struct Tc4Maps {
   CUtensorMap A;    // J4 [Kp][Kh]: 128 rows x 128 bytes, 128B swizzle
   CUtensorMap B;    // FT4 [2 Cp][Kh]: 128 columns x 128 bytes, 128B swizzle
+  CUtensorMap B64;  // FT4 half tiles of a CTA pair: 64 columns x 128 bytes, 128B swizzle
   CUtensorMap Fst;  // FT4 tile store: 128 columns x 64 bytes, no swizzle
   int Kh;           // bytes per row of J4 and FT4 (a multiple of 128)
 };
 
-// Steps [a.n_begin, a.n_end) of tile (blockIdx.y, blockIdx.x): 128 spin rows
-// x 128 replica columns, x and y resident in TMEM (columns 128-383, the
-// accumulator in 0-127, the scale factors in 384-447).
-template <int P, bool GEN>
-__global__ void __launch_bounds__(kTpThreads, 1)
-    k_solve_dense_tc_f4(const __grid_constant__ Tc4Maps m, StateView s, TpArgs a, StepTables t) {
-  const int mt = blockIdx.y, ct = blockIdx.x;
+// Steps [a.n_begin, a.n_end) of tile (mt, ct): 128 spin rows x 128 replica
+// columns, x and y resident in TMEM (columns 128-383, the accumulator in
+// 0-127, the scale factors in 384-447).
+//
+// Paired form (PAIR): the CTAs of row tiles 2p and 2p + 1 of one column tile
+// form a 2-CTA cluster sharing one M=256 N=128 MMA per K slice (tcgen05
+// cta_group::2, issued by the even CTA).  Each CTA keeps its own 128 J rows
+// resident and stages 64 of the 128 f columns of every k-block, so a step's
+// f tiles fit the eight stages at once and the K loop waits for one round
+// trip to L2 instead of two.  The loads of both CTAs complete on the even
+// CTA's barriers; MMA completion is multicast to both CTAs' empty and done
+// barriers; a cluster barrier closes every step (ordering the odd CTA's
+// accumulator reads before the next step's MMAs) and carries the abort
+// decision, so both CTAs stop at the same step.
+template <int P, bool GEN, bool PAIR>
+__device__ __forceinline__ void solve_dense_tc_f4(const Tc4Maps &m, const StateView &s, const TpArgs &a,
+                                                  const StepTables &t, int mt, int ct) {
+  using Sh = F4Shape<PAIR>;
+  constexpr int kStages = Sh::kStages, kStageB = Sh::kStageBytes;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int KB = m.Kh / 128;     // k-blocks of 256 spins
   const int Mt = a.Kp / kTcBM;   // row tiles: step counters per column tile
-  uint8_t *sA = smem;                     // this tile's J rows, KB boxes, loaded once
-  uint8_t *sB = sA + KB * kF4Box;         // f stages
-  uint8_t *sF = sB + kF4Stages * kF4Box;  // packed f(x_next) tile [128 columns][64 bytes]
+  uint8_t *sA = smem;                          // this tile's J rows, KB boxes, loaded once
+  uint8_t *sB = sA + KB * kF4Box;              // f stages
+  uint8_t *sF = sB + kF4Stages * kF4Box;       // packed f(x_next) tile [128 columns][64 bytes]
   uint64_t *full = reinterpret_cast<uint64_t *>(sF + kF4FTile);
-  uint64_t *empty = full + kF4Stages;
-  uint64_t *done = empty + kF4Stages;
+  uint64_t *empty = full + kStages;
+  uint64_t *done = empty + kStages;
   uint64_t *jfull = done + 1;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(jfull + 1);
-  int *s_abort = reinterpret_cast<int *>(tmem_slot + 1);
+  int *s_abort = reinterpret_cast<int *>(tmem_slot + 1);  // PAIR: [step parity][rank]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint32_t rank = 0;
+  if constexpr (PAIR) {
+    // both CTAs of a cluster read the same cluster shape, so both return here or neither does
+    if (tc::cluster_nctarank() != 2 || tc::cluster_nctaid_x() != 2) {
+      if (threadIdx.x == 0) atomicCAS(a.err, 0, tc::ERR_CLUSTER_SHAPE);
+      return;
+    }
+    rank = tc::cluster_ctarank();
+  }
+  const bool leader = rank == 0;
   const int m0 = mt * kTcBM, n0 = ct * kTcBN;
   const int quarter = warp & 3, chunk = warp >> 2;
   const int rl = quarter * 32 + lane, i = m0 + rl;
   const int cl = 32 * chunk, c0 = n0 + cl;
   const uint32_t lane_off = uint32_t(quarter * 32) << 16;
+  const CUtensorMap *mapB = PAIR ? &m.B64 : &m.B;
+  const int b_off = PAIR ? 64 * int(rank) : 0;
+  // a load completing on the (even CTA's) full barrier of stage st, or on jfull
+  auto load_tile = [&](uint8_t *dst, const CUtensorMap *map, uint64_t *bar, int c0_, int c1_) {
+    if constexpr (PAIR)
+      tc::tma_load_2d_pair(dst, map, tc::map_to_rank(tc::smem_u32(bar), 0), c0_, c1_);
+    else
+      tc::tma_load_2d(dst, map, bar, c0_, c1_);
+  };
 
   if (threadIdx.x == 0) {
-    for (int q = 0; q < kF4Stages; ++q) {
+    for (int q = 0; q < kStages; ++q) {
       tc::mbar_init(&full[q], 1);
       tc::mbar_init(&empty[q], 1);
     }
@@ -118,13 +174,17 @@ __global__ void __launch_bounds__(kTpThreads, 1)
     tc::mbar_init(jfull, 1);
     tc::fence_mbar_init();
     tc::prefetch_tmap(&m.A);
-    tc::prefetch_tmap(&m.B);
+    tc::prefetch_tmap(mapB);
     tc::prefetch_tmap(&m.Fst);
-    *s_abort = 0;
+    for (int q = 0; q < 4; ++q) s_abort[q] = 0;
   }
-  if (warp == 0) tc::tmem_alloc(tmem_slot, kTmemCols);
+  if (warp == 0) {
+    if constexpr (PAIR) tc::tmem_alloc_pair(tmem_slot, kTmemCols);
+    else tc::tmem_alloc(tmem_slot, kTmemCols);
+  }
   tc::tc_fence_before();
-  __syncthreads();
+  if constexpr (PAIR) tc::cluster_sync();  // the pair's barriers and TMEM exist before either CTA uses them
+  else __syncthreads();
   tc::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -158,20 +218,21 @@ __global__ void __launch_bounds__(kTpThreads, 1)
   }
   const float hi = i < s.N ? __ldg(a.h + i) : 0.f;
   if (warp == 0 && lane == 0 && a.n_begin < a.n_end) {  // this tile's J rows, resident for the launch
-    tc::mbar_arrive_expect_tx(jfull, uint32_t(KB * kF4Box));
-    for (int kb = 0; kb < KB; ++kb) tc::tma_load_2d(sA + kb * kF4Box, &m.A, jfull, kb * 128, m0);
+    if (leader) tc::mbar_arrive_expect_tx(jfull, uint32_t((PAIR ? 2 : 1) * KB * kF4Box));
+    for (int kb = 0; kb < KB; ++kb) load_tile(sA + kb * kF4Box, &m.A, jfull, kb * 128, m0);
   }
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
 
-  constexpr uint32_t idesc = idesc_mxf4(kTcBM, kTcBN);
+  constexpr uint32_t idesc = idesc_mxf4(PAIR ? 2 * kTcBM : kTcBM, kTcBN);
+  constexpr uint32_t kExpect = (PAIR ? 2 : 1) * kStageB;  // bytes completing on one full barrier
   int n = a.n_begin;
   for (; n < a.n_end; ++n) {
     const uint32_t q = uint32_t(n - a.n_begin);
     if (warp == 0) {
       // producer: the f tiles of k-block kb once row tiles 2 kb and 2 kb + 1 have published step q
-      const int brow = (n & 1) * s.Cp + n0;
+      const int brow = (n & 1) * s.Cp + n0 + b_off;
       uint64_t t0 = 0;
       uint32_t polls = 0;
       int kb = 0;
@@ -209,29 +270,34 @@ __global__ void __launch_bounds__(kTpThreads, 1)
           asm volatile("fence.acq_rel.gpu;" ::: "memory");
           tc::fence_proxy_async_global();
           for (int j = kb; j < kb + nready; ++j) {
-            const uint32_t g = q * KB + j, st = g % kF4Stages, use = g / kF4Stages;
+            const uint32_t g = q * KB + j, st = g % kStages, use = g / kStages;
             if (use > 0) tc::mbar_wait(&empty[st], (use - 1) & 1, a.err, tc::ERR_WAIT_EMPTY);
-            tc::mbar_arrive_expect_tx(&full[st], kF4Box);
-            tc::tma_load_2d(sB + st * kF4Box, &m.B, &full[st], j * 128, brow);
+            if (leader) tc::mbar_arrive_expect_tx(&full[st], kExpect);
+            load_tile(sB + st * kStageB, mapB, &full[st], j * 128, brow);
           }
         }
         __syncwarp();
         kb += nready;
       }
-    } else if (warp == 1 && lane == 0) {
+    } else if (warp == 1 && lane == 0 && leader) {
       if (q == 0) tc::mbar_wait(jfull, 0, a.err, tc::ERR_WAIT_FULL);
       for (int kb = 0; kb < KB; ++kb) {
-        const uint32_t g = q * KB + kb, st = g % kF4Stages, use = g / kF4Stages;
+        const uint32_t g = q * KB + kb, st = g % kStages, use = g / kStages;
         tc::mbar_wait(&full[st], use & 1, a.err, tc::ERR_WAIT_FULL);
         tc::tc_fence_after();
-        const uint32_t a0 = tc::smem_u32(sA + kb * kF4Box), b0 = tc::smem_u32(sB + st * kF4Box);
+        const uint32_t a0 = tc::smem_u32(sA + kb * kF4Box), b0 = tc::smem_u32(sB + st * kStageB);
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk)
-          mma_mxf4(tmem, tc::smem_desc_sw128(a0 + kk * 32), tc::smem_desc_sw128(b0 + kk * 32), idesc,
-                   tmem + kTmemSfa, tmem + kTmemSfb, (kb | kk) != 0 ? 1u : 0u);
-        tc::mma_commit(&empty[st]);
+        for (int kk = 0; kk < 4; ++kk) {
+          const uint64_t ad = tc::smem_desc_sw128(a0 + kk * 32), bd = tc::smem_desc_sw128(b0 + kk * 32);
+          const uint32_t acc = (kb | kk) != 0 ? 1u : 0u;
+          if constexpr (PAIR) mma_mxf4_pair(tmem, ad, bd, idesc, tmem + kTmemSfa, tmem + kTmemSfb, acc);
+          else mma_mxf4(tmem, ad, bd, idesc, tmem + kTmemSfa, tmem + kTmemSfb, acc);
+        }
+        if constexpr (PAIR) tc::mma_commit_pair(&empty[st]);
+        else tc::mma_commit(&empty[st]);
       }
-      tc::mma_commit(done);
+      if constexpr (PAIR) tc::mma_commit_pair(done);
+      else tc::mma_commit(done);
     }
     __syncwarp();
     const float ka = __ldg(t.ka + n), dnext = __ldg(t.dl + n + 1);
@@ -293,11 +359,20 @@ __global__ void __launch_bounds__(kTpThreads, 1)
       tc::tma_store_commit_and_wait_all();
       tc::fence_proxy_async_global();
       if (n != a.hold_step || mt != 0 || ct != 0) tc::st_release_gpu(a.flags + mt * a.Ct + ct, q + 1);
-      *s_abort = *reinterpret_cast<volatile int *>(a.err);
+      const int v = *reinterpret_cast<volatile int *>(a.err);
+      if constexpr (PAIR) {
+        int *slot = s_abort + 2 * (q & 1) + rank;  // double-buffered by step parity
+        *slot = v;
+        tc::st_cluster_u32(tc::map_to_rank(tc::smem_u32(slot), rank ^ 1u), uint32_t(v));
+      } else {
+        *s_abort = v;
+      }
     }
-    __syncthreads();
+    if constexpr (PAIR) tc::cluster_sync();  // also orders the odd CTA's accumulator reads before the next MMAs
+    else __syncthreads();
     tc::tc_fence_after();
-    if (*s_abort != 0) break;
+    const int stop = PAIR ? (s_abort[2 * (q & 1)] | s_abort[2 * (q & 1) + 1]) : *s_abort;
+    if (stop != 0) break;
   }
   __syncwarp();
   {  // the state tile back to global memory
@@ -320,11 +395,27 @@ __global__ void __launch_bounds__(kTpThreads, 1)
     }
   }
   tc::tc_fence_before();
-  __syncthreads();
+  // PAIR: neither CTA leaves (or frees its TMEM) while the other's MMAs, loads or reads may still use it
+  if constexpr (PAIR) tc::cluster_sync();
+  else __syncthreads();
   if (warp == 0) {
     tc::tc_fence_after();
-    tc::tmem_dealloc(tmem, kTmemCols);
+    if constexpr (PAIR) tc::tmem_dealloc_pair(tmem, kTmemCols);
+    else tc::tmem_dealloc(tmem, kTmemCols);
   }
+}
+
+template <int P, bool GEN>
+__global__ void __launch_bounds__(kTpThreads, 1)
+    k_solve_dense_tc_f4(const __grid_constant__ Tc4Maps m, StateView s, TpArgs a, StepTables t) {
+  solve_dense_tc_f4<P, GEN, false>(m, s, a, t, blockIdx.y, blockIdx.x);
+}
+
+// Row tiles along x (cluster pairs 2p, 2p + 1), column tiles along y.
+template <int P, bool GEN>
+__global__ void __launch_bounds__(kTpThreads, 1)
+    k_solve_dense_tc_f4_pair(const __grid_constant__ Tc4Maps m, StateView s, TpArgs a, StepTables t) {
+  solve_dense_tc_f4<P, GEN, true>(m, s, a, t, blockIdx.x, blockIdx.y);
 }
 
 // e2m1 nibble of an e4m3 byte holding an integer |v| <= 4 (the only values
@@ -374,6 +465,7 @@ __global__ void k_f_to_ft4(StateView s, int which, uint8_t *FT4, int Kh, int b) 
    {(const void *)K<64, true>, (const void *)K<64, true>},                                                   \
    {(const void *)K<128, true>, (const void *)K<128, true>}}
 static const void *const kF4Fns[8][2] = SBQA_F4_PS(k_solve_dense_tc_f4);
+static const void *const kF4PairFns[8][2] = SBQA_F4_PS(k_solve_dense_tc_f4_pair);
 #undef SBQA_F4_PS
 
 static int f4_p_index(int P) {
@@ -388,11 +480,52 @@ static int f4_smem(int Kp) { return (tc_f4_row_bytes(Kp) / 128 + kF4Stages) * kF
 
 cudaError_t tc_f4_set_attributes() {
   for (int q = 0; q < 8; ++q)
-    for (const void *f : kF4Fns[q]) {
-      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kF4Smem);
-      if (e != cudaSuccess) return e;
-    }
+    for (int pair = 0; pair < 2; ++pair)
+      for (const void *f : (pair ? kF4PairFns : kF4Fns)[q]) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kF4Smem);
+        if (e != cudaSuccess) return e;
+      }
   return cudaSuccess;
+}
+
+// Launch configuration of a cooperative grid of 2 x 1 x 1 clusters.
+static void f4_cluster_config(cudaLaunchConfig_t *cfg, cudaLaunchAttribute *attr, dim3 grid, int smem,
+                              cudaStream_t st, bool cooperative) {
+  *cfg = cudaLaunchConfig_t{};
+  cfg->gridDim = grid;
+  cfg->blockDim = dim3(kTpThreads);
+  cfg->dynamicSmemBytes = smem;
+  cfg->stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeCooperative;
+  attr[1].val.cooperative = 1;
+  cfg->attrs = attr;
+  cfg->numAttrs = cooperative ? 2 : 1;
+}
+
+int tc_f4_pair_blocks() {
+  if (tc_f4_set_attributes() != cudaSuccess) return 0;
+  int best = 1 << 30;
+  for (int q = 0; q < 8; ++q)
+    for (const void *f : kF4PairFns[q]) {
+      cudaLaunchConfig_t cfg;
+      cudaLaunchAttribute attr[2];
+      f4_cluster_config(&cfg, attr, dim3(2, 1), kF4Smem, 0, false);
+      int clusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&clusters, f, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+      }
+      best = clusters < best ? clusters : best;
+    }
+  return 2 * best;
+}
+
+bool tc_f4_pair_eligible(int Kp, int Cp, int blocks) {
+  return tc_f4_eligible(Kp, Cp, blocks) && Kp % (2 * kTcBM) == 0;
 }
 
 int tc_f4_blocks() {
@@ -423,6 +556,7 @@ bool tc4_plan_make(void **plan, const void *J4, void *FT4, int Kp, int Cp) {
   const bool ok =
       tc_make_map(&p->A, J4, U8, 1, uint64_t(Kp), uint64_t(Kh), 128, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
       tc_make_map(&p->B, FT4, U8, 1, rows_ft, uint64_t(Kh), 128, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
+      tc_make_map(&p->B64, FT4, U8, 1, rows_ft, uint64_t(Kh), 128, 64, CU_TENSOR_MAP_SWIZZLE_128B) &&
       tc_make_map(&p->Fst, FT4, U8, 1, rows_ft, uint64_t(Kh), 64, 128, CU_TENSOR_MAP_SWIZZLE_NONE);
   if (!ok) {
     delete p;
@@ -465,6 +599,29 @@ cudaError_t launch_solve_dense_tc_f4(const void *plan, const StateView &s, int K
   void *args[] = {&maps, &sv, &a, &tv};
   return cudaLaunchCooperativeKernel(kF4Fns[idx][s.Pr != s.P ? 1 : 0], dim3(Ct, Kp / kTcBM), dim3(kTpThreads), args,
                                      f4_smem(Kp), st);
+}
+
+cudaError_t launch_solve_dense_tc_f4_pair(const void *plan, const StateView &s, int Kp, int *err, const float *h,
+                                          const StepTables &t, int n_begin, int n_end, uint32_t *flags,
+                                          cudaStream_t st) {
+  const int idx = f4_p_index(s.P);
+  const auto *m = static_cast<const Tc4Maps *>(plan);
+  if (idx < 0 || Kp % (2 * kTcBM) != 0 || s.Cp % kTcBN != 0 || m->Kh != tc_f4_row_bytes(Kp) ||
+      m->Kh / 128 > kF4MaxKB)
+    return cudaErrorInvalidValue;
+  const int Ct = s.Cp / kTcBN;
+  cudaError_t e = cudaMemsetAsync(flags, 0, tc_persistent_flag_count(Kp, s.Cp) * sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  TpArgs a{Kp, Ct, n_begin, n_end, err, h, flags, -1};
+  Tc4Maps maps = *m;
+  StateView sv = s;
+  StepTables tv = t;
+  void *args[] = {&maps, &sv, &a, &tv};
+  cudaLaunchConfig_t cfg;
+  cudaLaunchAttribute attr[2];
+  // row tiles along x (cluster pairs 2p, 2p + 1), column tiles along y
+  f4_cluster_config(&cfg, attr, dim3(Kp / kTcBM, Ct), f4_smem(Kp), st, true);
+  return cudaLaunchKernelExC(&cfg, kF4PairFns[idx][s.Pr != s.P ? 1 : 0], args);
 }
 
 }  // namespace sbqa

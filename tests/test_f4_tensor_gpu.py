@@ -1,6 +1,7 @@
 """The persistent dense tensor-core solver with packed e2m1 operands
 (tcgen05.mma kind::mxf4 with unit scale factors, J rows resident in shared
-memory; step_kernel 15).
+memory; step_kernel 15) and its paired form (2-CTA clusters sharing M=256
+MMAs, each CTA staging half of every f tile; step_kernel 16).
 
 For integer |J_ij| <= 4 and f in {-1, 0, 1} (Eq. 8) every product and every
 partial sum of G = J f is an exact small integer, so the e2m1 solver must
@@ -54,40 +55,49 @@ def _run(sb, spec, P, R, S, sel, eval_every=13, split=None, seed=4):
     return prob
 
 
+def _pairs(N):
+    """The paired form takes padded N a multiple of 256."""
+    return -(-N // 128) * 128 % 256 == 0
+
+
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_e2m1_solver_equals_e4m3_persistent(sb, name):
+@pytest.mark.parametrize("sel", [15, 14])
+def test_e2m1_solver_equals_e4m3_persistent(sb, name, sel):
     make, P, R = CASES[name]
     pb, spec = make()
     S = 60
     ref = _run(sb, spec, P, R, S, 12)
     assert ref.info().step_kernel == 5
     xr, yr, _ = sb.get_state(ref)
-    got = _run(sb, spec, P, R, S, 14)
-    assert got.info().step_kernel == 15
+    want = 16 if sel == 14 and _pairs(pb.n) else 15
+    got = _run(sb, spec, P, R, S, sel)
+    assert got.info().step_kernel == want
     xg, yg, _ = sb.get_state(got)
     assert np.array_equal(xg, xr) and np.array_equal(yg, yr)
     assert np.array_equal(sb.get_best(got)["energy"], sb.get_best(ref)["energy"])
     _, ei = sb.get_energies(got)
     spins = np.where(xg >= 0, 1, -1).astype(np.int8)
     assert np.array_equal(ei, oracle.energies(pb, spins))
-    split = _run(sb, spec, P, R, S, 14, split=23)
+    split = _run(sb, spec, P, R, S, sel, split=23)
+    assert split.info().step_kernel == want
     xs, ys, _ = sb.get_state(split)
     assert np.array_equal(xs, xr) and np.array_equal(ys, yr)
 
 
-def test_e2m1_solver_resume_through_set_state(sb):
+@pytest.mark.parametrize("N,sel,want", [(600, 14, 15), (1000, 14, 16), (1000, 15, 15)])
+def test_e2m1_solver_resume_through_set_state(sb, N, sel, want):
     """set_state rebuilds the packed f buffer from the state: a run resumed
     from a dumped mid-run state equals the unbroken run bit for bit."""
-    pb, spec = dense_int(600, 11, jmax=4)
+    pb, spec = dense_int(N, 11, jmax=4)
     P, R, S = 16, 16, 80
     prob = create(sb, spec)
-    sb.set_schedule(prob, *workloads.autotune_params(R, 5), precision="exact", kernel_select=14, gamma0=32.0)
+    sb.set_schedule(prob, *workloads.autotune_params(R, 5), precision="exact", kernel_select=sel, gamma0=32.0)
     sb.run_begin(prob, S, P, R, seed=9)
     sb.run_advance(prob, 31)
     x31, y31, _ = sb.get_state(prob)
     sb.run_advance(prob, S)
     xa, ya, _ = sb.get_state(prob)
-    assert prob.info().step_kernel == 15
+    assert prob.info().step_kernel == want
     sb.run_begin(prob, S, P, R, seed=1234)
     sb.set_state(prob, x31, y31, 31)
     sb.run_advance(prob, S)
@@ -114,6 +124,6 @@ def test_autotuner_times_the_e2m1_solver(sb):
     auto = _run(sb, spec, P, R, S, 0)
     info = auto.info()
     print("autotuner: step_kernel %d, persistent %.2f us/step" % (info.step_kernel, 1e3 * info.persistent_ms))
-    assert info.step_kernel in (2, 5, 8, 9, 15)
+    assert info.step_kernel in (2, 5, 8, 9, 15, 16)
     ref = _run(sb, spec, P, R, S, 12)
     assert np.array_equal(sb.get_state(auto)[0], sb.get_state(ref)[0])

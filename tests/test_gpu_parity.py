@@ -232,7 +232,7 @@ def test_persistent_dense_tc_solver_matches_per_step(sb, N, P, R, jmax):
         sb.set_schedule(prob, *workloads.autotune_params(R, N), **_params(kernel_select=sel, eval_every=37))
         sb.run(prob, 200, P, R, seed=N)
         want = {1: 2, 2: 8 if _split_k(N, P, R) else 5, 12: 5, 13: 9 if _pair(N) else 5,
-                14: 15 if jmax <= 4 else 5}[sel]
+                14: (16 if _pair(N) else 15) if jmax <= 4 else 5}[sel]
         assert prob.info().step_kernel == want
         out.append((sb.get_state(prob)[:2], sb.get_energies(prob), sb.get_best(prob)))
     (xa, ya), ea, ba = out[0]
@@ -257,7 +257,7 @@ def test_dense_tensor_core_readout_matches_cuda_cores(sb, N, P, R, jmax):
         prob = create(sb, spec)
         sb.set_schedule(prob, *workloads.autotune_params(R, 5), **_params(precision=prec, eval_every=29))
         sb.run(prob, 120, P, R, seed=7)
-        assert (prob.info().step_kernel in (2, 5, 8, 9, 15)) if prec == "exact" else prob.info().step_kernel == 1
+        assert (prob.info().step_kernel in (2, 5, 8, 9, 15, 16)) if prec == "exact" else prob.info().step_kernel == 1
         _, ei = sb.get_energies(prob)
         x, _, _ = sb.get_state(prob)
         res.append((ei, sb.get_best(prob), x))
@@ -987,11 +987,11 @@ def test_full_size_dense_sk2000_exact(sb):
 
 
 def test_full_size_dense_sk2000_persistent_solver_against_oracle(sb):
-    """SK N=2000, P=32, R=32, exact product on a persistent tcgen05 solver (step_kernel 5, 8, 9 or 15,
-    the benchmark's kernels; 15 with e2m1 operands) against the oracle step by step on runs 0 and 31 for
-    20 steps."""
+    """SK N=2000, P=32, R=32, exact product on a persistent tcgen05 solver (step_kernel 5, 8, 9, 15
+    or 16, the benchmark's kernels; 15 and 16 with e2m1 operands) against the oracle step by step on
+    runs 0 and 31 for 20 steps."""
     pb, spec = sk(2000, 0)
-    assert _sampled_per_step(sb, pb, spec, 32, 32, 1000, 20, [0, 31], kernels=(5, 8, 9, 15),
+    assert _sampled_per_step(sb, pb, spec, 32, 32, 1000, 20, [0, 31], kernels=(5, 8, 9, 15, 16),
                              prec="exact") <= TOL_STEP
 
 
@@ -1003,7 +1003,7 @@ def test_full_size_dense_sk2000_energies(sb):
     prob = create(sb, spec)
     sb.set_schedule(prob, *workloads.autotune_params(32, 1), **_params(precision="exact"))
     sb.run(prob, 30, 32, 32, seed=0)
-    assert prob.info().step_kernel in (2, 5, 8, 9, 15)
+    assert prob.info().step_kernel in (2, 5, 8, 9, 15, 16)
     e, ei = sb.get_energies(prob)
     x, _, _ = sb.get_state(prob)
     best = sb.get_best(prob)
