@@ -48,6 +48,10 @@ struct TcOp {
 // swizzle (step_dense_tc.cu); false when the driver refuses it.
 bool tc_make_map(CUtensorMap *m, const void *base, CUtensorMapDataType dt, size_t esize, uint64_t rows,
                  uint64_t cols, uint32_t box_cols, uint32_t box_rows, CUtensorMapSwizzle sw);
+// The same for `rank` dimensions (dims[0] contiguous; strides[k] in bytes
+// between consecutive indices of dimension k + 1).
+bool tc_make_map_nd(CUtensorMap *m, const void *base, CUtensorMapDataType dt, int rank, const uint64_t *dims,
+                    const uint64_t *strides, const uint32_t *box, CUtensorMapSwizzle sw);
 
 struct TcArgs {
   int Kp;

@@ -16,8 +16,12 @@
 // that bounds the e4m3 solver's K loop, where the MMAs' shared-memory reads
 // and the TMA writes of both operands into the same memory serialise.
 //
-// Layout: J4 [Kp][Kh] and FT4 [2][Cp][Kh] bytes with Kh = 128 ceil(Kp / 256)
-// (zeros past Kp); spin 2t in the low nibble of byte t, 2t + 1 in the high
+// Layout: J4 [Kp][Kh] bytes with Kh = 128 ceil(Kp / 256) (zeros past Kp), and
+// FT4 [2][Kh / 128][Cp][128] bytes, k-block-major, so that one 4D TMA box
+// brings several k-blocks of a column tile: the number of boxes a CTA keeps
+// in flight, not their size, is what bounds the f loads (about one box per
+// 300 ns per SM measured with one 16 KB box per k-block).  Spin 2t in the
+// low nibble of byte t (within its k-block of 256 spins), 2t + 1 in the high
 // nibble.  The MMA pairs element k of A with element k of B, so any nibble
 // order that both operands share gives the same sums.
 //
@@ -32,21 +36,24 @@ constexpr int kOpF4 = 3;
 constexpr int kF4MaxKB = 9;                 // resident J boxes of 256 spins: Kp <= 2304
 constexpr int kF4Box = kTcBM * 128;         // 128 rows x 128 bytes (256 e2m1 values per row)
 constexpr int kF4FTile = kTcBN * 64;        // packed f tile: 128 columns x 64 bytes (128 spins)
-// f stages: a single CTA stages whole 128-column k-blocks (16 KB, four
-// stages beside the resident J); a CTA of a pair stages its 64 of the pair's
-// 128 columns (8 KB), so eight stages hold every k-block of a step at once.
+// f staging: two slots of 32 KB beside the resident J, each filled by one
+// box of kG k-blocks.  A single CTA stages whole 128-column k-blocks (16 KB,
+// two per box); a CTA of a pair stages its 64 of the pair's 128 columns
+// (8 KB, four per box), so both slots hold every k-block of a step at once.
 template <bool PAIR>
 struct F4Shape {
-  static constexpr int kStages = PAIR ? 8 : 4;
-  static constexpr int kStageBytes = PAIR ? kF4Box / 2 : kF4Box;
+  static constexpr int kG = PAIR ? 4 : 2;                         // k-blocks per box
+  static constexpr int kKbBytes = PAIR ? kF4Box / 2 : kF4Box;     // one k-block of this CTA's columns
+  static constexpr int kSlotBytes = kG * kKbBytes;
+  static constexpr int kSlots = 2;
 };
-constexpr int kF4Stages = 4;  // the larger staging footprint of the two forms (4 x 16 KB = 8 x 8 KB)
+constexpr int kF4Stages = 4;  // staging bytes in 16 KB units: 2 slots x 32 KB
 constexpr uint32_t kTmemSfa = 384, kTmemSfb = 416;  // scale factors of A and B, 32 columns each
 constexpr uint32_t kUnitScales = 0x7F7F7F7Fu;       // four ue8m0 codes of 2^0
 constexpr int kF4Smem = (kF4MaxKB + kF4Stages) * kF4Box + kF4FTile + 1024 + 256;
 static_assert(kF4Smem <= 227 * 1024, "resident J, stages and f tile exceed the shared memory of one CTA");
-static_assert(F4Shape<true>::kStages * F4Shape<true>::kStageBytes == kF4Stages * kF4Box &&
-                  F4Shape<false>::kStages * F4Shape<false>::kStageBytes == kF4Stages * kF4Box,
+static_assert(F4Shape<true>::kSlots * F4Shape<true>::kSlotBytes == kF4Stages * kF4Box &&
+                  F4Shape<false>::kSlots * F4Shape<false>::kSlotBytes == kF4Stages * kF4Box,
               "both forms fit the same shared-memory layout");
 static_assert(kTmemSfb + 32 <= kTmemCols, "scale-factor regions outside the allocated tensor memory");
 
@@ -100,9 +107,9 @@ struct FOut<kOpF4> {
 
 struct Tc4Maps {
   CUtensorMap A;    // J4 [Kp][Kh]: 128 rows x 128 bytes, 128B swizzle
-  CUtensorMap B;    // FT4 [2 Cp][Kh]: 128 columns x 128 bytes, 128B swizzle
-  CUtensorMap B64;  // FT4 half tiles of a CTA pair: 64 columns x 128 bytes, 128B swizzle
-  CUtensorMap Fst;  // FT4 tile store: 128 columns x 64 bytes, no swizzle
+  CUtensorMap B;    // FT4 [2][KB][Cp][128]: boxes of 2 k-blocks x 128 columns x 128 bytes, 128B swizzle
+  CUtensorMap B64;  // FT4 boxes of a CTA of a pair: 4 k-blocks x 64 columns x 128 bytes, 128B swizzle
+  CUtensorMap Fst;  // FT4 tile store: 128 columns x 64 bytes of one k-block, no swizzle
   int Kh;           // bytes per row of J4 and FT4 (a multiple of 128)
 };
 
@@ -124,17 +131,18 @@ template <int P, bool GEN, bool PAIR>
 __device__ __forceinline__ void solve_dense_tc_f4(const Tc4Maps &m, const StateView &s, const TpArgs &a,
                                                   const StepTables &t, int mt, int ct) {
   using Sh = F4Shape<PAIR>;
-  constexpr int kStages = Sh::kStages, kStageB = Sh::kStageBytes;
+  constexpr int kSlots = Sh::kSlots, kSlotB = Sh::kSlotBytes, kG = Sh::kG, kKbB = Sh::kKbBytes;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int KB = m.Kh / 128;     // k-blocks of 256 spins
+  const int NG = (KB + kG - 1) / kG;  // f boxes per step (the last one may reach past KB: zeros)
   const int Mt = a.Kp / kTcBM;   // row tiles: step counters per column tile
   uint8_t *sA = smem;                          // this tile's J rows, KB boxes, loaded once
   uint8_t *sB = sA + KB * kF4Box;              // f stages
   uint8_t *sF = sB + kF4Stages * kF4Box;       // packed f(x_next) tile [128 columns][64 bytes]
   uint64_t *full = reinterpret_cast<uint64_t *>(sF + kF4FTile);
-  uint64_t *empty = full + kStages;
-  uint64_t *done = empty + kStages;
+  uint64_t *empty = full + kSlots;
+  uint64_t *done = empty + kSlots;
   uint64_t *jfull = done + 1;
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(jfull + 1);
   int *s_abort = reinterpret_cast<int *>(tmem_slot + 1);  // PAIR: [step parity][rank]
@@ -156,17 +164,23 @@ __device__ __forceinline__ void solve_dense_tc_f4(const Tc4Maps &m, const StateV
   const int cl = 32 * chunk, c0 = n0 + cl;
   const uint32_t lane_off = uint32_t(quarter * 32) << 16;
   const CUtensorMap *mapB = PAIR ? &m.B64 : &m.B;
-  const int b_off = PAIR ? 64 * int(rank) : 0;
-  // a load completing on the (even CTA's) full barrier of stage st, or on jfull
-  auto load_tile = [&](uint8_t *dst, const CUtensorMap *map, uint64_t *bar, int c0_, int c1_) {
+  const int bcol = n0 + (PAIR ? 64 * int(rank) : 0);  // first f column this CTA stages
+  // loads completing on the (even CTA's) barrier bar
+  auto load_j = [&](uint8_t *dst, uint64_t *bar, int c0_, int c1_) {
     if constexpr (PAIR)
-      tc::tma_load_2d_pair(dst, map, tc::map_to_rank(tc::smem_u32(bar), 0), c0_, c1_);
+      tc::tma_load_2d_pair(dst, &m.A, tc::map_to_rank(tc::smem_u32(bar), 0), c0_, c1_);
     else
-      tc::tma_load_2d(dst, map, bar, c0_, c1_);
+      tc::tma_load_2d(dst, &m.A, bar, c0_, c1_);
+  };
+  auto load_f = [&](uint8_t *dst, uint64_t *bar, int gi, int buf) {
+    if constexpr (PAIR)
+      tc::tma_load_4d_pair(dst, mapB, tc::map_to_rank(tc::smem_u32(bar), 0), 0, bcol, gi * kG, buf);
+    else
+      tc::tma_load_4d(dst, mapB, bar, 0, bcol, gi * kG, buf);
   };
 
   if (threadIdx.x == 0) {
-    for (int q = 0; q < kStages; ++q) {
+    for (int q = 0; q < kSlots; ++q) {
       tc::mbar_init(&full[q], 1);
       tc::mbar_init(&empty[q], 1);
     }
@@ -219,20 +233,20 @@ __device__ __forceinline__ void solve_dense_tc_f4(const Tc4Maps &m, const StateV
   const float hi = i < s.N ? __ldg(a.h + i) : 0.f;
   if (warp == 0 && lane == 0 && a.n_begin < a.n_end) {  // this tile's J rows, resident for the launch
     if (leader) tc::mbar_arrive_expect_tx(jfull, uint32_t((PAIR ? 2 : 1) * KB * kF4Box));
-    for (int kb = 0; kb < KB; ++kb) load_tile(sA + kb * kF4Box, &m.A, jfull, kb * 128, m0);
+    for (int kb = 0; kb < KB; ++kb) load_j(sA + kb * kF4Box, jfull, kb * 128, m0);
   }
   tc::tc_fence_before();
   __syncthreads();
   tc::tc_fence_after();
 
   constexpr uint32_t idesc = idesc_mxf4(PAIR ? 2 * kTcBM : kTcBM, kTcBN);
-  constexpr uint32_t kExpect = (PAIR ? 2 : 1) * kStageB;  // bytes completing on one full barrier
+  constexpr uint32_t kExpect = (PAIR ? 2 : 1) * kSlotB;  // bytes completing on one full barrier
   int n = a.n_begin;
   for (; n < a.n_end; ++n) {
     const uint32_t q = uint32_t(n - a.n_begin);
     if (warp == 0) {
-      // producer: the f tiles of k-block kb once row tiles 2 kb and 2 kb + 1 have published step q
-      const int brow = (n & 1) * s.Cp + n0 + b_off;
+      // producer: box gi (k-blocks kG gi ..) once row tiles 2 kb and 2 kb + 1 of each of its
+      // k-blocks have published step q
       uint64_t t0 = 0;
       uint32_t polls = 0;
       int kb = 0;
@@ -247,7 +261,8 @@ __device__ __forceinline__ void solve_dense_tc_f4(const Tc4Maps &m, const StateV
         const unsigned ball = __ballot_sync(0xffffffffu, ok);
         int nready = ball == 0xffffffffu ? 32 : __ffs(~ball) - 1;
         nready = nready < KB - kb ? nready : KB - kb;
-        if (nready == 0) {
+        int ng = kb + nready >= KB ? NG - kb / kG : nready / kG;  // whole boxes ready (kb is a box start)
+        if (ng == 0) {
           int give_up = 0;
           if (lane == 0) {
             const uint64_t now = tc::globaltimer_ns();
@@ -260,7 +275,7 @@ __device__ __forceinline__ void solve_dense_tc_f4(const Tc4Maps &m, const StateV
             }
           }
           if (__shfl_sync(0xffffffffu, give_up, 0)) {
-            nready = KB - kb;  // proceed with whatever the buffer holds; the run reports the error
+            ng = NG - kb / kG;  // proceed with whatever the buffer holds; the run reports the error
           } else {
             __nanosleep(64);
             continue;
@@ -269,32 +284,35 @@ __device__ __forceinline__ void solve_dense_tc_f4(const Tc4Maps &m, const StateV
         if (lane == 0) {
           asm volatile("fence.acq_rel.gpu;" ::: "memory");
           tc::fence_proxy_async_global();
-          for (int j = kb; j < kb + nready; ++j) {
-            const uint32_t g = q * KB + j, st = g % kStages, use = g / kStages;
-            if (use > 0) tc::mbar_wait(&empty[st], (use - 1) & 1, a.err, tc::ERR_WAIT_EMPTY);
-            if (leader) tc::mbar_arrive_expect_tx(&full[st], kExpect);
-            load_tile(sB + st * kStageB, mapB, &full[st], j * 128, brow);
+          for (int gi = kb / kG; gi < kb / kG + ng; ++gi) {
+            const uint32_t g = q * NG + gi, sl = g % kSlots, use = g / kSlots;
+            if (use > 0) tc::mbar_wait(&empty[sl], (use - 1) & 1, a.err, tc::ERR_WAIT_EMPTY);
+            if (leader) tc::mbar_arrive_expect_tx(&full[sl], kExpect);
+            load_f(sB + sl * kSlotB, &full[sl], gi, n & 1);
           }
         }
         __syncwarp();
-        kb += nready;
+        kb += ng * kG;
       }
     } else if (warp == 1 && lane == 0 && leader) {
       if (q == 0) tc::mbar_wait(jfull, 0, a.err, tc::ERR_WAIT_FULL);
-      for (int kb = 0; kb < KB; ++kb) {
-        const uint32_t g = q * KB + kb, st = g % kStages, use = g / kStages;
-        tc::mbar_wait(&full[st], use & 1, a.err, tc::ERR_WAIT_FULL);
+      for (int gi = 0; gi < NG; ++gi) {
+        const uint32_t g = q * NG + gi, sl = g % kSlots, use = g / kSlots;
+        tc::mbar_wait(&full[sl], use & 1, a.err, tc::ERR_WAIT_FULL);
         tc::tc_fence_after();
-        const uint32_t a0 = tc::smem_u32(sA + kb * kF4Box), b0 = tc::smem_u32(sB + st * kStageB);
+        for (int u = 0; u < kG && gi * kG + u < KB; ++u) {
+          const int kb = gi * kG + u;
+          const uint32_t a0 = tc::smem_u32(sA + kb * kF4Box), b0 = tc::smem_u32(sB + sl * kSlotB + u * kKbB);
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-          const uint64_t ad = tc::smem_desc_sw128(a0 + kk * 32), bd = tc::smem_desc_sw128(b0 + kk * 32);
-          const uint32_t acc = (kb | kk) != 0 ? 1u : 0u;
-          if constexpr (PAIR) mma_mxf4_pair(tmem, ad, bd, idesc, tmem + kTmemSfa, tmem + kTmemSfb, acc);
-          else mma_mxf4(tmem, ad, bd, idesc, tmem + kTmemSfa, tmem + kTmemSfb, acc);
+          for (int kk = 0; kk < 4; ++kk) {
+            const uint64_t ad = tc::smem_desc_sw128(a0 + kk * 32), bd = tc::smem_desc_sw128(b0 + kk * 32);
+            const uint32_t acc = (kb | kk) != 0 ? 1u : 0u;
+            if constexpr (PAIR) mma_mxf4_pair(tmem, ad, bd, idesc, tmem + kTmemSfa, tmem + kTmemSfb, acc);
+            else mma_mxf4(tmem, ad, bd, idesc, tmem + kTmemSfa, tmem + kTmemSfb, acc);
+          }
         }
-        if constexpr (PAIR) tc::mma_commit_pair(&empty[st]);
-        else tc::mma_commit(&empty[st]);
+        if constexpr (PAIR) tc::mma_commit_pair(&empty[sl]);
+        else tc::mma_commit(&empty[sl]);
       }
       if constexpr (PAIR) tc::mma_commit_pair(done);
       else tc::mma_commit(done);
@@ -354,8 +372,9 @@ __device__ __forceinline__ void solve_dense_tc_f4(const Tc4Maps &m, const StateV
     tc::tc_fence_before();
     __syncthreads();
     if (threadIdx.x == 0) {
-      // publish f_{n+1} of this tile: spins m0.. (bytes m0 / 2..), columns n0.. of the other FT4 buffer
-      tc::tma_store_2d(&m.Fst, sF, m0 / 2, ((n + 1) & 1) * s.Cp + n0);
+      // publish f_{n+1} of this tile: spins m0.. (half mt & 1 of k-block mt / 2), columns n0.., of the
+      // other FT4 buffer
+      tc::tma_store_4d(&m.Fst, sF, 64 * (mt & 1), n0, mt >> 1, (n + 1) & 1);
       tc::tma_store_commit_and_wait_all();
       tc::fence_proxy_async_global();
       if (n != a.hold_step || mt != 0 || ct != 0) tc::st_release_gpu(a.flags + mt * a.Ct + ct, q + 1);
@@ -437,12 +456,15 @@ __global__ void k_j4_from_j8(const uint8_t *J8, int Kp, int Kh, uint8_t *J4) {
   J4[e] = uint8_t(v);
 }
 
-// f codes of F buffer `which` ([N][Cp], f + 1) -> FT4 buffer b ([Cp][Kh],
-// spins 2t and 2t + 1 in byte t, zeros for padded spins).
+// f codes of F buffer `which` ([N][Cp], f + 1) -> FT4 buffer b ([KB][Cp][128]:
+// byte t of k-block kb holds spins 256 kb + 2t and + 2t + 1; zeros for
+// padded spins).
 __global__ void k_f_to_ft4(StateView s, int which, uint8_t *FT4, int Kh, int b) {
-  const size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x;  // over Cp * Kh
+  const size_t e = size_t(blockIdx.x) * blockDim.x + threadIdx.x;  // over KB * Cp * 128
   if (e >= size_t(s.Cp) * Kh) return;
-  const int c = int(e / Kh), j = 2 * int(e % Kh);
+  const size_t per_kb = size_t(s.Cp) * 128;
+  const int kb = int(e / per_kb), r = int(e % per_kb);
+  const int c = r / 128, j = 256 * kb + 2 * (r % 128);
   uint32_t v = 0;
 #pragma unroll
   for (int u = 0; u < 2; ++u) {
@@ -552,12 +574,17 @@ bool tc4_plan_make(void **plan, const void *J4, void *FT4, int Kp, int Cp) {
   const auto U8 = CU_TENSOR_MAP_DATA_TYPE_UINT8;
   const int Kh = tc_f4_row_bytes(Kp);
   p->Kh = Kh;
-  const uint64_t rows_ft = uint64_t(2) * Cp;
+  const uint64_t KB = uint64_t(Kh / 128);
+  const uint64_t dims[4] = {128, uint64_t(Cp), KB, 2};  // FT4 [2][KB][Cp][128]
+  const uint64_t strides[3] = {128, uint64_t(Cp) * 128, KB * Cp * 128};
+  const uint32_t box_b[4] = {128, 128, uint32_t(F4Shape<false>::kG), 1};
+  const uint32_t box_b64[4] = {128, 64, uint32_t(F4Shape<true>::kG), 1};
+  const uint32_t box_st[4] = {64, 128, 1, 1};
   const bool ok =
       tc_make_map(&p->A, J4, U8, 1, uint64_t(Kp), uint64_t(Kh), 128, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
-      tc_make_map(&p->B, FT4, U8, 1, rows_ft, uint64_t(Kh), 128, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
-      tc_make_map(&p->B64, FT4, U8, 1, rows_ft, uint64_t(Kh), 128, 64, CU_TENSOR_MAP_SWIZZLE_128B) &&
-      tc_make_map(&p->Fst, FT4, U8, 1, rows_ft, uint64_t(Kh), 64, 128, CU_TENSOR_MAP_SWIZZLE_NONE);
+      tc_make_map_nd(&p->B, FT4, U8, 4, dims, strides, box_b, CU_TENSOR_MAP_SWIZZLE_128B) &&
+      tc_make_map_nd(&p->B64, FT4, U8, 4, dims, strides, box_b64, CU_TENSOR_MAP_SWIZZLE_128B) &&
+      tc_make_map_nd(&p->Fst, FT4, U8, 4, dims, strides, box_st, CU_TENSOR_MAP_SWIZZLE_NONE);
   if (!ok) {
     delete p;
     return false;

@@ -830,6 +830,22 @@ bool tc_make_map(CUtensorMap *m, const void *base, CUtensorMapDataType dt, size_
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+bool tc_make_map_nd(CUtensorMap *m, const void *base, CUtensorMapDataType dt, int rank, const uint64_t *dims,
+                    const uint64_t *strides, const uint32_t *box, CUtensorMapSwizzle sw) {
+  auto fn = encode_fn();
+  if (!fn || rank < 1 || rank > 5) return false;
+  cuuint64_t d[5], st[4];
+  cuuint32_t b[5], estr[5];
+  for (int k = 0; k < rank; ++k) {
+    d[k] = dims[k];
+    b[k] = box[k];
+    estr[k] = 1;
+    if (k + 1 < rank) st[k] = strides[k];
+  }
+  return fn(m, dt, cuuint32_t(rank), const_cast<void *>(base), d, st, b, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 size_t tc_ft_bytes(int Kp, int Cp, int op) {
   const size_t one = size_t(2) * Cp * Kp;  // [2][Cp][Kp] elements
   return op == kOpF8 ? one : (op == kOpBf16 ? 2 * one : 4 * one);
