@@ -67,6 +67,9 @@ struct TcMaps {
   CUtensorMap X, Y;  // x, y state boxes (128 rows x 32 floats, 128B swizzle)
   CUtensorMap Fst;   // FT tile store (128 columns x 128 spins, no swizzle)
   CUtensorMap Bl, Fstl;  // kOpBsb: the lo terms of x (load and store), as B and Fst
+  // kOpF8, kOpBf16: 3D views (128 bytes, rows, k-blocks; strides one row and
+  // 128 bytes) of J and FT, boxes of two consecutive k-blocks of 128 rows
+  CUtensorMap A3, B3;
   int op;                // operand form (kOpF8, kOpBf16, kOpBsb)
 };
 

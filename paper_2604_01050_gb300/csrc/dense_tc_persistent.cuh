@@ -42,6 +42,12 @@ template <bool PAIR, int OP = kOpF8>
 struct TpShape {
   static constexpr int kNB = TcOp<OP>::kNB;
   static constexpr int kStages = PAIR ? 8 : (kNB == 2 ? 3 : 6);
+  // k-blocks per TMA box: the single-CTA e4m3 and bfloat16 forms bring two
+  // consecutive k-blocks of J and of f per box (3D views of the same
+  // buffers), because the loads are bound by the boxes a CTA keeps in flight
+  // more than by their bytes; slots of kG stages
+  static constexpr int kG = (PAIR || kNB == 2) ? 1 : 2;
+  static constexpr int kSlots = kStages / kG;
   static constexpr int kTileB = PAIR ? 64 * kTcBK : kTcTile;  // fT rows staged by this CTA: 64 of the pair's 128, or 128
   static constexpr int kStageBytes = kTcTile + kNB * kTileB;
   static constexpr uint32_t kExpect = PAIR ? 2 * kStageBytes : kStageBytes;  // bytes completing on one full barrier
@@ -108,8 +114,9 @@ __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const
   static_assert(!PAIR || OP == kOpF8, "CTA pairs run the e4m3 product only");
   using Sh = TpShape<PAIR, OP>;
   using O = TcOp<OP>;
-  constexpr int kStages = Sh::kStages;
+  constexpr int kStages = Sh::kStages, kG = Sh::kG, kSlots = Sh::kSlots;
   constexpr int kStageB = O::kNB * Sh::kTileB;  // B bytes of one stage (hi and lo for kOpBsb)
+  static_assert(kSlots * kG == kStages, "slots of whole stages");
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint8_t *sA = smem;
@@ -134,7 +141,8 @@ __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const
   const bool leader = rank == 0;
   const int m0 = mt * kTcBM, n0 = ct * kTcBN;
   const int KB = a.Kp / O::kKE;
-  const int npre = KB < kStages ? KB : kStages;  // k-blocks whose J tile is loaded ahead
+  const int NS = (KB + kG - 1) / kG;             // slot loads per step (a last box past KB reads zeros)
+  const int npre = NS < kSlots ? NS : kSlots;    // slot loads whose J box is loaded ahead
   // this CTA's operand loads: fT rows (B box) and the full barrier they complete on
   const CUtensorMap *mapB = PAIR ? &m.B64 : &m.B;
   const int b_off = PAIR ? 64 * int(rank) : 0;
@@ -144,6 +152,20 @@ __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const
     else
       tc::tma_load_2d(dst, map, &full[st], c0_, c1_);
   };
+  // J box of slot load js (k-blocks kG js ..) into slot sl, and its f box(es) at f row brow
+  auto load_a = [&](int sl, int js) {
+    if constexpr (kG == 1) load_tile(sA + sl * kTcTile, &m.A, sl, js * O::kKE, m0);
+    else tc::tma_load_3d(sA + sl * kG * kTcTile, &m.A3, &full[sl], 0, m0, js * kG);
+  };
+  auto load_b = [&](int sl, int js, int brow) {
+    if constexpr (kG == 1) {
+      load_tile(sB + sl * kStageB, mapB, sl, js * O::kKE, brow + b_off);
+      if constexpr (O::kNB == 2) load_tile(sB + sl * kStageB + Sh::kTileB, &m.Bl, sl, js * O::kKE, brow);
+    } else {
+      tc::tma_load_3d(sB + sl * kG * kStageB, &m.B3, &full[sl], 0, brow, js * kG);
+    }
+  };
+  constexpr uint32_t kSlotExpect = kG * Sh::kExpect;  // bytes completing on one full barrier
   const int quarter = warp & 3, chunk = warp >> 2;
   const int rl = quarter * 32 + lane, i = m0 + rl;
   const int cl = 32 * chunk, c0 = n0 + cl;
@@ -158,6 +180,10 @@ __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const
     tc::fence_mbar_init();
     tc::prefetch_tmap(&m.A);
     tc::prefetch_tmap(mapB);
+    if constexpr (kG > 1) {
+      tc::prefetch_tmap(&m.A3);
+      tc::prefetch_tmap(&m.B3);
+    }
     tc::prefetch_tmap(&m.Fst);
     if constexpr (O::kNB == 2) {
       tc::prefetch_tmap(&m.Bl);
@@ -199,9 +225,9 @@ __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const
   }
   const float hi = i < s.N ? __ldg(a.h + i) : 0.f;
   if (warp == 0 && lane == 0 && a.n_begin < a.n_end) {  // J tiles of the first step's first stages
-    for (int kb = 0; kb < npre; ++kb) {
-      if (leader) tc::mbar_arrive_expect_tx(&full[kb], Sh::kExpect);
-      load_tile(sA + kb * kTcTile, &m.A, kb, kb * O::kKE, m0);
+    for (int js = 0; js < npre; ++js) {
+      if (leader) tc::mbar_arrive_expect_tx(&full[js], kSlotExpect);
+      load_a(js, js);
     }
   }
   tc::tc_fence_before();
@@ -226,7 +252,8 @@ __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const
         const unsigned ball = __ballot_sync(0xffffffffu, ok);
         int nready = ball == 0xffffffffu ? 32 : __ffs(~ball) - 1;
         nready = nready < KB - kb ? nready : KB - kb;
-        if (nready == 0) {
+        int ns = kb + nready >= KB ? NS - kb / kG : nready / kG;  // whole slot loads ready (kb starts one)
+        if (ns == 0) {
           int give_up = 0;
           if (lane == 0) {
             const uint64_t now = tc::globaltimer_ns();
@@ -239,7 +266,7 @@ __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const
             }
           }
           if (__shfl_sync(0xffffffffu, give_up, 0)) {
-            nready = KB - kb;  // proceed with whatever the buffer holds; the run reports the error
+            ns = NS - kb / kG;  // proceed with whatever the buffer holds; the run reports the error
           } else {
             __nanosleep(64);
             continue;
@@ -248,35 +275,38 @@ __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const
         if (lane == 0) {
           asm volatile("fence.acq_rel.gpu;" ::: "memory");
           tc::fence_proxy_async_global();
-          for (int j = kb; j < kb + nready; ++j) {
-            const uint32_t g = q * KB + j, st = g % kStages, use = g / kStages;
-            if (j >= npre) {
-              if (use > 0) tc::mbar_wait(&empty[st], (use - 1) & 1, a.err, tc::ERR_WAIT_EMPTY);
-              if (leader) tc::mbar_arrive_expect_tx(&full[st], Sh::kExpect);
-              load_tile(sA + st * kTcTile, &m.A, st, j * O::kKE, m0);
+          for (int js = kb / kG; js < kb / kG + ns; ++js) {
+            const uint32_t g = q * NS + js, sl = g % kSlots, use = g / kSlots;
+            if (js >= npre) {
+              if (use > 0) tc::mbar_wait(&empty[sl], (use - 1) & 1, a.err, tc::ERR_WAIT_EMPTY);
+              if (leader) tc::mbar_arrive_expect_tx(&full[sl], kSlotExpect);
+              load_a(int(sl), js);
             }
-            load_tile(sB + st * kStageB, mapB, st, j * O::kKE, brow + b_off);
-            if constexpr (O::kNB == 2) load_tile(sB + st * kStageB + Sh::kTileB, &m.Bl, st, j * O::kKE, brow);
+            load_b(int(sl), js, brow);
           }
         }
         __syncwarp();
-        kb += nready;
+        kb += ns * kG;
       }
-      // J tiles of the next step's first stages, behind this step's MMAs
+      // J boxes of the next step's first slot loads, behind this step's MMAs
       prefetched = n + 1 < a.n_end;
       if (lane == 0 && prefetched) {
-        for (int j = 0; j < npre; ++j) {
-          const uint32_t g = (q + 1) * KB + j, st = g % kStages, use = g / kStages;
-          if (use > 0) tc::mbar_wait(&empty[st], (use - 1) & 1, a.err, tc::ERR_WAIT_EMPTY);
-          if (leader) tc::mbar_arrive_expect_tx(&full[st], Sh::kExpect);
-          load_tile(sA + st * kTcTile, &m.A, st, j * O::kKE, m0);
+        for (int js = 0; js < npre; ++js) {
+          const uint32_t g = (q + 1) * NS + js, sl = g % kSlots, use = g / kSlots;
+          if (use > 0) tc::mbar_wait(&empty[sl], (use - 1) & 1, a.err, tc::ERR_WAIT_EMPTY);
+          if (leader) tc::mbar_arrive_expect_tx(&full[sl], kSlotExpect);
+          load_a(int(sl), js);
         }
       }
     } else if (warp == 1 && lane == 0 && leader) {
       for (int kb = 0; kb < KB; ++kb) {
-        const uint32_t g = q * KB + kb, st = g % kStages, use = g / kStages;
-        tc::mbar_wait(&full[st], use & 1, a.err, tc::ERR_WAIT_FULL);
-        tc::tc_fence_after();
+        const int js = kb / kG, u = kb - js * kG;
+        const uint32_t g = q * NS + js, sl = g % kSlots, use = g / kSlots;
+        if (u == 0) {
+          tc::mbar_wait(&full[sl], use & 1, a.err, tc::ERR_WAIT_FULL);
+          tc::tc_fence_after();
+        }
+        const int st = int(sl) * kG + u;  // the stage (memory) of k-block kb
         const uint32_t a0 = tc::smem_u32(sA + st * kTcTile), b0 = tc::smem_u32(sB + st * kStageB);
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
@@ -289,8 +319,10 @@ __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const
               O::mma(tmem, ad, tc::smem_desc_sw128(b0 + Sh::kTileB + kk * 32), idesc, 1u);
           }
         }
-        if constexpr (PAIR) tc::mma_commit_pair(&empty[st]);
-        else tc::mma_commit(&empty[st]);
+        if (u == kG - 1 || kb == KB - 1) {
+          if constexpr (PAIR) tc::mma_commit_pair(&empty[sl]);
+          else tc::mma_commit(&empty[sl]);
+        }
       }
       if constexpr (PAIR) tc::mma_commit_pair(done);
       else tc::mma_commit(done);
@@ -368,11 +400,10 @@ __device__ __forceinline__ void solve_dense_tc_persistent(const TcMaps &m, const
     // (with any f tile) and wait for them, so no copy outlives the block
     const uint32_t q = uint32_t(n + 1 - a.n_begin);
     const int brow = ((n + 1) & 1) * s.Cp + n0;
-    for (int j = 0; j < npre; ++j) {
-      const uint32_t g = q * KB + j, st = g % kStages, use = g / kStages;
-      load_tile(sB + st * kStageB, mapB, st, j * O::kKE, brow + b_off);
-      if constexpr (O::kNB == 2) load_tile(sB + st * kStageB + Sh::kTileB, &m.Bl, st, j * O::kKE, brow);
-      if (leader) tc::mbar_wait(&full[st], use & 1, a.err, tc::ERR_WAIT_FULL);
+    for (int js = 0; js < npre; ++js) {
+      const uint32_t g = q * NS + js, sl = g % kSlots, use = g / kSlots;
+      load_b(int(sl), js, brow);
+      if (leader) tc::mbar_wait(&full[sl], use & 1, a.err, tc::ERR_WAIT_FULL);
     }
   }
   __syncwarp();

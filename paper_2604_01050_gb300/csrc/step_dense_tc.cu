@@ -872,6 +872,14 @@ bool tc_plan_make(void **plan, const void *J, void *FT, int Kp, int Cp, float *x
   if (ok && op == kOpF8)  // the wide, split-K and paired kernels run the e4m3 product only
     ok = tc_make_map(&p->B2, FT, OT, 1, rows_ft, uint64_t(Kp), 128, 256, CU_TENSOR_MAP_SWIZZLE_128B) &&
          tc_make_map(&p->B64, FT, OT, 1, rows_ft, uint64_t(Kp), 128, 64, CU_TENSOR_MAP_SWIZZLE_128B);
+  if (ok && op != kOpBsb) {  // two k-blocks per box: the same buffers seen as [rows][k-block][128 bytes]
+    const uint64_t kbs = uint64_t(Kp) / ke;
+    const uint64_t dims_a[3] = {ke, uint64_t(Kp), kbs}, dims_b[3] = {ke, rows_ft, kbs};
+    const uint64_t strides[2] = {uint64_t(Kp) * eb, 128};
+    const uint32_t box[3] = {ke, 128, 2};
+    ok = tc_make_map_nd(&p->A3, J, OT, 3, dims_a, strides, box, CU_TENSOR_MAP_SWIZZLE_128B) &&
+         tc_make_map_nd(&p->B3, FT, OT, 3, dims_b, strides, box, CU_TENSOR_MAP_SWIZZLE_128B);
+  }
   if (ok && op == kOpBsb)
     ok = tc_make_map(&p->Bl, ftl, OT, 2, rows_ft, uint64_t(Kp), ke, 128, CU_TENSOR_MAP_SWIZZLE_128B) &&
          tc_make_map(&p->Fstl, ftl, OT, 2, rows_ft, uint64_t(Kp), 128, 128, CU_TENSOR_MAP_SWIZZLE_NONE);
