@@ -353,14 +353,18 @@ __device__ __forceinline__ void solve_dense_tc_f4(const Tc4Maps &m, const StateV
         if (c0 + 32 <= s.C) sb_update_regs32<P, true, kOpF4, GEN>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, fo, ext);
         else sb_update_regs32<P, false, kOpF4, GEN>(s, t, ka, dnext, kj, c0, g, hi, xr, yr, fo, ext);
       }
-      // rows 2t (even lane) and 2t + 1 (the next lane) share byte t of each column of the f tile
+      // rows 2t (even lane) and 2t + 1 (the next lane) share byte t of each column of the f tile;
+      // both lanes of a pair hold both rows' nibbles and store alternate columns (the two rows of
+      // one store instruction lie 64 bytes apart: no bank conflict)
+      const int par = lane & 1;
 #pragma unroll
       for (int w = 0; w < 4; ++w) {
-        const uint32_t o = __shfl_down_sync(0xffffffffu, nib[w], 1);
-        if ((lane & 1) == 0) {
+        const uint32_t o = __shfl_xor_sync(0xffffffffu, nib[w], 1);
+        const uint32_t lo = par ? o : nib[w], hi = par ? nib[w] : o;
 #pragma unroll
-          for (int c = 0; c < 8; ++c)
-            sF[(cl + 8 * w + c) * 64 + (rl >> 1)] = uint8_t(((nib[w] >> (4 * c)) & 0xFu) | (((o >> (4 * c)) & 0xFu) << 4));
+        for (int i = 0; i < 4; ++i) {
+          const int c = 2 * i + par;
+          sF[(cl + 8 * w + c) * 64 + (rl >> 1)] = uint8_t(((lo >> (4 * c)) & 0xFu) | (((hi >> (4 * c)) & 0xFu) << 4));
         }
       }
       __syncwarp();
