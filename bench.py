@@ -87,10 +87,10 @@ BYTES_PER_UPDATE_BSB = 20  # ballistic form: + the FP32 f (= x) write
 TRAFFIC_PER_STEP = {
     "regular1e5": {"kernel": "k_solve_csr_persistent", "bytes_per_step": (6372881664 + 7261387008) // 64},
     "lattice16": {"kernel": "k_solve_csr_persistent", "bytes_per_step": (81332736 + 4403397376) // 64},
-    "sk2000": {"kernel": "k_solve_dense_tc_f4", "bytes_per_step": (19728896 + 314112) // 1000},
+    "sk2000": {"kernel": "k_solve_dense_tc_f4", "bytes_per_step": (19729664 + 266496) // 1000},
     "lattice16/ballistic": {"kernel": "k_solve_csr_persistent_bsb",
                             "bytes_per_step": (1015867000000 + 999486978000) // 10000},
-    "skreal2000": {"kernel": "k_solve_dense_tc_persistent<bf16>", "bytes_per_step": (29531392 + 1040896) // 1000},
+    "skreal2000": {"kernel": "k_solve_dense_tc_persistent<bf16>", "bytes_per_step": (29526528 + 961280) // 1000},
 }
 L2_FLUSH_BYTES = 512 << 20
 BATCHED_CSR_UPDATES_PER_STEP = 13896704  # the 48-request serving stream's lattice requests
