@@ -1051,3 +1051,8 @@ def test_run_argument_errors(sb):
     with pytest.raises(sb.SBQAError) as e:
         sb.set_schedule(probr, **_params(precision="exact"))
     assert e.value.status == sb.ERR_UNSUPPORTED
+    sb.set_schedule(prob, *workloads.linear_params(3), **_params(kernel_select=15))  # the largest selection
+    for bad in (-1, 16):
+        with pytest.raises(sb.SBQAError) as e:
+            sb.set_schedule(prob, *workloads.linear_params(3), **_params(kernel_select=bad))
+        assert e.value.status == sb.ERR_INVALID_ARG
