@@ -708,6 +708,26 @@ int prepare_dense_values(sbqa_problem *p, int precision) {
   return SBQA_OK;
 }
 
+// Per-device memo of the solvers' co-resident block counts: the occupancy
+// queries (and the shared-memory attributes the first one sets, which last
+// for the context) cost tens of microseconds each, and every new handle
+// would repeat them.
+int memo_blocks(int (*query)()) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int (*)()>, int> memo;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return query();
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = memo.find({dev, query});
+  if (it != memo.end()) return it->second;
+  const int v = query();
+  memo[{dev, query}] = v;
+  return v;
+}
+
+// The tensor-core kernels' shared-memory limits, set once per device (they last for the context).
+int tc_attributes_once() { return tc_set_attributes() == cudaSuccess ? 1 : 0; }
+
 int alloc_run(sbqa_problem *p, int S, int P, int R) {
   const int Ps = run_width(P);  // a run's columns: P replicas, then padding up to a power of two
   const int C = R * Ps;
@@ -748,7 +768,7 @@ int alloc_run(sbqa_problem *p, int S, int P, int R) {
       p->tc_plan = nullptr;
       if (!tc_plan_make(&p->tc_plan, p->d_J8.p, p->d_FT.p, p->Kp, Cp, p->d_x.p, p->d_y.p, p->n, p->tc_op))
         return fail(SBQA_ERR_CUDA, "cuTensorMapEncodeTiled failed");
-      SBQA_CUDA(tc_set_attributes());
+      if (memo_blocks(tc_attributes_once) != 1) return fail(SBQA_ERR_CUDA, "cudaFuncSetAttribute failed");
       p->tc_plan_ft = p->d_FT.p;
       p->tc_plan_cp = Cp;
       p->tc_plan_x = p->d_x.p;
@@ -888,7 +908,7 @@ int autotune_csr_bsb(sbqa_problem *p) {
   if (cs != cudaStreamCaptureStatusNone) return SBQA_OK;
   p->use_persistent = false;
   p->persistent_ms = 0.f;
-  if (p->persist_blocks == 0) p->persist_blocks = persistent_blocks();
+  if (p->persist_blocks == 0) p->persist_blocks = memo_blocks(persistent_blocks);
   if (p->S > 0 && (sel == 0 || sel == 2) && p->persistent_ok()) {
     SBQA_CUDA(p->d_bar.alloc(persistent_barrier_words()));
     TuneResult known;
@@ -957,7 +977,7 @@ int autotune_csr(sbqa_problem *p) {
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   SBQA_CUDA(cudaStreamIsCapturing(p->stream, &cs));
   if (cs != cudaStreamCaptureStatusNone) return SBQA_OK;
-  if (p->persist_blocks == 0) p->persist_blocks = persistent_blocks();
+  if (p->persist_blocks == 0) p->persist_blocks = memo_blocks(persistent_blocks);
   TuneResult known;
   if (p->S > 0 && tune_lookup(p, &known)) {
     p->csr_variant = known.csr_variant;
@@ -994,7 +1014,7 @@ int autotune_csr(sbqa_problem *p) {
   SBQA_CUDA(cudaEventCreate(&e1));
   p->use_persistent = false;
   p->persistent_ms = 0.f;
-  if (p->persist_blocks == 0) p->persist_blocks = persistent_blocks();
+  if (p->persist_blocks == 0) p->persist_blocks = memo_blocks(persistent_blocks);
   if ((p->prm.kernel_select == 2 || p->prm.kernel_select >= 11) && p->S > 0 &&
       p->persistent_ok()) {
     SBQA_CUDA(p->d_bar.alloc(persistent_barrier_words()));
@@ -1094,11 +1114,11 @@ int autotune_tc(sbqa_problem *p) {
   if (cs != cudaStreamCaptureStatusNone) return SBQA_OK;
   p->use_tc_persistent = p->use_tc_split = p->use_tc_pair = p->use_tc_f4 = p->use_tc_f4_pair = false;
   p->tc_step_ms = p->tc_persistent_ms = 0.f;
-  if (p->tc_persist_blocks == 0) p->tc_persist_blocks = tc_persistent_blocks();
-  if (p->tc_split_blocks < 0) p->tc_split_blocks = tc_split_blocks();
-  if (p->tc_pair_blocks < 0) p->tc_pair_blocks = tc_pair_blocks();
-  if (p->tc_f4_blocks < 0) p->tc_f4_blocks = tc_f4_blocks();
-  if (p->tc_f4_pair_blocks < 0) p->tc_f4_pair_blocks = tc_f4_pair_blocks();
+  if (p->tc_persist_blocks == 0) p->tc_persist_blocks = memo_blocks(tc_persistent_blocks);
+  if (p->tc_split_blocks < 0) p->tc_split_blocks = memo_blocks(tc_split_blocks);
+  if (p->tc_pair_blocks < 0) p->tc_pair_blocks = memo_blocks(tc_pair_blocks);
+  if (p->tc_f4_blocks < 0) p->tc_f4_blocks = memo_blocks(tc_f4_blocks);
+  if (p->tc_f4_pair_blocks < 0) p->tc_f4_pair_blocks = memo_blocks(tc_f4_pair_blocks);
   const int sel = p->prm.kernel_select;
   if (sel != 1 && p->S > 0 && p->tc_persistent_ok()) {
     SBQA_CUDA(p->d_tc_flags.alloc(tc_persistent_flag_count(p->Kp, p->Cp)));

@@ -53,6 +53,9 @@ bool tc_make_map(CUtensorMap *m, const void *base, CUtensorMapDataType dt, size_
 bool tc_make_map_nd(CUtensorMap *m, const void *base, CUtensorMapDataType dt, int rank, const uint64_t *dims,
                     const uint64_t *strides, const uint32_t *box, CUtensorMapSwizzle sw);
 
+// k-blocks per TMA box of the single-CTA persistent e4m3 and bfloat16 solvers
+constexpr int kTpGroup = 3;
+
 struct TcArgs {
   int Kp;
   uint8_t *FT;  // [2][Cp][Kp]
@@ -68,7 +71,7 @@ struct TcMaps {
   CUtensorMap Fst;   // FT tile store (128 columns x 128 spins, no swizzle)
   CUtensorMap Bl, Fstl;  // kOpBsb: the lo terms of x (load and store), as B and Fst
   // kOpF8, kOpBf16: 3D views (128 bytes, rows, k-blocks; strides one row and
-  // 128 bytes) of J and FT, boxes of two consecutive k-blocks of 128 rows
+  // 128 bytes) of J and FT, boxes of kTpGroup consecutive k-blocks of 128 rows
   CUtensorMap A3, B3;
   int op;                // operand form (kOpF8, kOpBf16, kOpBsb)
 };

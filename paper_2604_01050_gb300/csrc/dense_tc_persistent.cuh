@@ -42,11 +42,11 @@ template <bool PAIR, int OP = kOpF8>
 struct TpShape {
   static constexpr int kNB = TcOp<OP>::kNB;
   static constexpr int kStages = PAIR ? 8 : (kNB == 2 ? 3 : 6);
-  // k-blocks per TMA box: the single-CTA e4m3 and bfloat16 forms bring two
-  // consecutive k-blocks of J and of f per box (3D views of the same
+  // k-blocks per TMA box: the single-CTA e4m3 and bfloat16 forms bring
+  // kTpGroup consecutive k-blocks of J and of f per box (3D views of the same
   // buffers), because the loads are bound by the boxes a CTA keeps in flight
   // more than by their bytes; slots of kG stages
-  static constexpr int kG = (PAIR || kNB == 2) ? 1 : 2;
+  static constexpr int kG = (PAIR || kNB == 2) ? 1 : kTpGroup;
   static constexpr int kSlots = kStages / kG;
   static constexpr int kTileB = PAIR ? 64 * kTcBK : kTcTile;  // fT rows staged by this CTA: 64 of the pair's 128, or 128
   static constexpr int kStageBytes = kTcTile + kNB * kTileB;

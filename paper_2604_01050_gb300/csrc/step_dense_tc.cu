@@ -876,7 +876,7 @@ bool tc_plan_make(void **plan, const void *J, void *FT, int Kp, int Cp, float *x
     const uint64_t kbs = uint64_t(Kp) / ke;
     const uint64_t dims_a[3] = {ke, uint64_t(Kp), kbs}, dims_b[3] = {ke, rows_ft, kbs};
     const uint64_t strides[2] = {uint64_t(Kp) * eb, 128};
-    const uint32_t box[3] = {ke, 128, 2};
+    const uint32_t box[3] = {ke, 128, uint32_t(kTpGroup)};
     ok = tc_make_map_nd(&p->A3, J, OT, 3, dims_a, strides, box, CU_TENSOR_MAP_SWIZZLE_128B) &&
          tc_make_map_nd(&p->B3, FT, OT, 3, dims_b, strides, box, CU_TENSOR_MAP_SWIZZLE_128B);
   }
