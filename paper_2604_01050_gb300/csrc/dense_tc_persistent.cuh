@@ -17,8 +17,10 @@ namespace sbqa {
 // every CTA publishes a per-tile step counter (release, after its f tile's
 // TMA store has completed) and the producer warp polls the counters of its
 // column group (acquire, then a proxy fence before the TMA loads of those
-// tiles), issuing k-blocks in order as their tiles become ready.  The J tiles
-// of the next step's first stages are loaded while the epilogue runs.  A wait
+// tiles), issuing k-blocks in order as their tiles become ready (kTpGroup
+// consecutive k-blocks of J and of f per TMA box in the single-CTA e4m3 and
+// bfloat16 forms, one per box otherwise).  The J tiles of the next step's
+// first stages are loaded while the epilogue runs.  A wait
 // that gives up (2 s, or at once when another CTA has already failed)
 // records an error; every CTA then stops at its next step boundary.
 //
