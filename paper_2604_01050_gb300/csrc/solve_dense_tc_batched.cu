@@ -47,6 +47,9 @@ __global__ void __launch_bounds__(kTpThreads, 1) k_solve_dense_tc_batched(const 
     if constexpr (OP == kOpBsb) {
       tc::fence_tmap_acquire_sys(&d.m.Bl);
       tc::fence_tmap_acquire_sys(&d.m.Fstl);
+    } else {  // the views with several k-blocks per box
+      tc::fence_tmap_acquire_sys(&d.m.A3);
+      tc::fence_tmap_acquire_sys(&d.m.B3);
     }
   }
   const StateView s = d.s;
