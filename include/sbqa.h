@@ -398,6 +398,8 @@ typedef struct {
                                        chunks of several small dense
                                        tensor-core requests together */
     int64_t dense_batched_chunks;   /* request chunks advanced by those launches */
+    int64_t dense_e2m1_requests;    /* dense requests served by the solver with
+                                       packed e2m1 operands (integer |J| <= 4) */
 } sbqa_engine_stats_t;
 
 int sbqa_engine_stats(const sbqa_engine *e, sbqa_engine_stats_t *s);

@@ -64,7 +64,8 @@ class EngineStats(ctypes.Structure):
                 ("arena_bytes", ctypes.c_int64), ("arena_used", ctypes.c_int64),
                 ("updates_issued", ctypes.c_int64), ("kernels_launched", ctypes.c_int64),
                 ("batched_updates", ctypes.c_int64), ("batched_ms", ctypes.c_double),
-                ("dense_batched_launches", ctypes.c_int64), ("dense_batched_chunks", ctypes.c_int64)]
+                ("dense_batched_launches", ctypes.c_int64), ("dense_batched_chunks", ctypes.c_int64),
+                ("dense_e2m1_requests", ctypes.c_int64)]
 
 
 class Params(ctypes.Structure):

@@ -93,6 +93,9 @@ struct Request {
   // carved device buffers
   float *x, *y, *ka, *dl, *kj;
   uint8_t *F0, *F1, *FT;
+  uint8_t *FT4 = nullptr;  // packed e2m1 f buffers of the e2m1 dense solver (f4 requests)
+  bool f4 = false;         // a dense request on the e2m1 solver (integer |J| <= 4, its tiles co-resident)
+  void *tc4_plan = nullptr;
   int8_t *Sg, *best_spins;
   int64_t *ei, *part_i, *best_ei;
   double *ef, *part_f, *best_e;
@@ -158,8 +161,11 @@ struct sbqa_engine {
   // small dense tensor-core requests: their chunks in one cooperative launch
   // per group of equal operand form and run width (solve_dense_tc_batched.cu)
   TcBatch *tcb = nullptr;
+  Tc4Batch *tc4b = nullptr;  // the same for the requests on the e2m1 solver
+  int f4_blocks = -1;        // co-resident CTAs of the e2m1 solvers (-1: not queried yet)
   bool dense_batching = true;
   int64_t dense_batched_launches = 0, dense_batched_chunks = 0;
+  int64_t dense_e2m1_requests = 0;  // requests admitted on the e2m1 solver
   // dense requests run their chunk on a stream of their slot (created on first
   // use), so small dense problems share the GPU instead of queueing
   std::vector<cudaStream_t> side;
@@ -178,10 +184,13 @@ struct sbqa_engine {
       if (x) cudaEventDestroy(x);
     if (chunk_start) cudaEventDestroy(chunk_start);
     tc_batch_destroy(tcb);
+    tc4_batch_destroy(tc4b);
     if (batched_t0) cudaEventDestroy(batched_t0);
     if (batched_t1) cudaEventDestroy(batched_t1);
-    for (auto &r : reqs)
+    for (auto &r : reqs) {
       if (r.tc_plan) tc_plan_free(r.tc_plan);
+      if (r.tc4_plan) tc4_plan_free(r.tc4_plan);
+    }
     if (arena.base) cudaFree(arena.base);
     if (d_slots) cudaFree(d_slots);
     if (d_items) cudaFree(d_items);
@@ -199,7 +208,7 @@ namespace {
                        std::string(#call) + ": " + cudaGetErrorString(e_));                     \
   } while (0)
 
-size_t request_bytes(const sbqa_problem *p, int S, int P, int R, bool tc, int Kp) {
+size_t request_bytes(const sbqa_problem *p, int S, int P, int R, bool tc, int Kp, bool f4) {
   const int C = R * run_width(P), Cp = (C + kColsPerWarp - 1) / kColsPerWarp * kColsPerWarp;
   const size_t N = size_t(p->n), NC = N * Cp;
   const size_t nblk = size_t(energy_row_blocks(p->n));
@@ -212,6 +221,7 @@ size_t request_bytes(const sbqa_problem *p, int S, int P, int R, bool tc, int Kp
   b += align_up(size_t(R) * 8) * 2 + align_up(size_t(R) * 4) * 3 + align_up(size_t(R) * N);
   b += align_up(4);                        // error flag
   if (tc) b += align_up(tc_ft_bytes(Kp, Cp, p->tc_op)) + align_up(tc_persistent_flag_count(Kp, Cp) * 4);
+  if (f4) b += align_up(size_t(2) * Cp * tc_f4_row_bytes(Kp));
   return b;
 }
 
@@ -245,6 +255,19 @@ void carve(Request &r, uint8_t *base, bool tc, int Kp) {
   r.err = reinterpret_cast<int *>(take(4));
   r.FT = tc ? take(tc_ft_bytes(Kp, r.Cp, r.prob->tc_op)) : nullptr;
   r.tc_flags = tc ? reinterpret_cast<uint32_t *>(take(tc_persistent_flag_count(Kp, r.Cp) * 4)) : nullptr;
+  r.FT4 = r.f4 ? take(size_t(2) * r.Cp * tc_f4_row_bytes(Kp)) : nullptr;
+}
+
+// A dense request runs on the e2m1 solver when its couplings are integers |J| <= 4 (exact in e2m1),
+// the e4m3 form is in use, its tiles fit the device at once and the problem's kernel_select allows
+// it (0, 14 or 15); decided at submission, so that the arena holds its packed f buffers.
+bool request_f4(sbqa_engine *e, const sbqa_problem *p, int P, int R) {
+  if (!p->dense || !p->use_tc || p->tc_op != kTcOpF8 || !p->j_integer || p->max_abs_j > 4) return false;
+  const int ks = p->prm.kernel_select;
+  if (ks != 0 && ks != 14 && ks != 15) return false;
+  const int C = R * run_width(P), Cp = (C + kColsPerWarp - 1) / kColsPerWarp * kColsPerWarp;
+  if (e->f4_blocks < 0) e->f4_blocks = tc_f4_blocks();
+  return tc_f4_eligible(p->Kp, Cp, e->f4_blocks);
 }
 
 int admit(sbqa_engine *e, Request &r, int slot, cudaStream_t st) {
@@ -261,12 +284,29 @@ int admit(sbqa_engine *e, Request &r, int slot, cudaStream_t st) {
       return set_error(SBQA_ERR_CUDA, "cuTensorMapEncodeTiled failed");
     ENG_CUDA(tc_set_attributes());
   }
+  if (r.f4) {
+    // the problem's packed J (once per problem), this request's plan and zeroed f buffers (the
+    // bytes past Kp that no tile writes stay zero)
+    const int Kh = tc_f4_row_bytes(p->Kp);
+    if (!p->d_J4.p) {
+      ENG_CUDA(p->d_J4.alloc(size_t(p->Kp) * Kh));
+      ENG_CUDA(launch_j4_from_j8(p->d_J8.p, p->Kp, p->d_J4.p, st));
+      ++e->kernels_launched;
+    }
+    if (!tc4_plan_make(&r.tc4_plan, p->d_J4.p, r.FT4, p->Kp, r.Cp))
+      return set_error(SBQA_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+    ENG_CUDA(cudaMemsetAsync(r.FT4, 0, size_t(2) * r.Cp * Kh, st));
+  }
   const StateView s = r.state_view();
   ENG_CUDA(cudaMemsetAsync(r.err, 0, sizeof(int), st));
   ENG_CUDA(launch_init(s, r.seed, float(p->prm.init_amp), 0.0f, st));
   if (tc) ENG_CUDA(launch_f_to_ft(s, 0, r.FT, p->Kp, 0, p->tc_op, st));
+  if (r.f4) {
+    ENG_CUDA(launch_f_to_ft4(s, 0, r.FT4, p->Kp, 0, st));
+    ++e->dense_e2m1_requests;
+  }
   ENG_CUDA(launch_reset_best(s, r.best_view(), st));
-  e->kernels_launched += tc ? 3 : 2;
+  e->kernels_launched += (tc ? 3 : 2) + (r.f4 ? 1 : 0);
   r.slot = slot;
   r.n0 = 0;
   r.state = ACTIVE;
@@ -405,7 +445,8 @@ int sbqa_engine_submit(sbqa_engine *e, sbqa_problem *p, int32_t steps, int32_t P
   r.id = int(e->reqs.size());
   r.prob = p;
   r.S = steps; r.P = P; r.R = R; r.seed = seed;
-  r.bytes = request_bytes(p, steps, P, R, p->use_tc, p->Kp);
+  r.f4 = request_f4(e, p, P, R);
+  r.bytes = request_bytes(p, steps, P, R, p->use_tc, p->Kp, r.f4);
   if (r.bytes > e->arena.bytes) return set_error(SBQA_ERR_OOM, "request larger than the engine arena");
   e->reqs.push_back(std::move(r));
   e->queue.push_back(e->reqs.back().id);
@@ -449,6 +490,44 @@ static int dense_batches(sbqa_engine *e, std::vector<int> &ids, cudaStream_t st)
     const int steps_now = std::min(e->chunk, r.S - r.n0);
     const cudaError_t err = tc_batch_add(e->tcb, r.tc_plan, sv, p->Kp, r.err, p->d_h.p, r.tables, r.n0,
                                          r.n0 + steps_now, id == hold_id ? r.n0 : -1);
+    if (err != cudaSuccess) return set_error(SBQA_ERR_CUDA, std::string("engine dense batch: ") + cudaGetErrorString(err));
+  }
+  return flush();
+}
+
+// The chunks of the small requests on the e2m1 solver: grouped by run width
+// and ring form, every group in as few cooperative launches as the
+// co-resident CTAs allow, on st one after another.
+static int dense_batches_f4(sbqa_engine *e, std::vector<int> &ids, cudaStream_t st) {
+  if (!e->tc4b) ENG_CUDA(tc4_batch_create(&e->tc4b, std::min(e->max_slots, e->f4_blocks), e->f4_blocks));
+  auto key = [&](int id) {
+    const Request &r = e->reqs[id];
+    return std::make_pair(run_width(r.P), r.P != run_width(r.P));
+  };
+  std::stable_sort(ids.begin(), ids.end(), [&](int a, int b) { return key(a) < key(b); });
+  tc4_batch_clear(e->tc4b);
+  auto flush = [&]() -> int {
+    if (tc4_batch_size(e->tc4b) == 0) return SBQA_OK;
+    const cudaError_t err = tc4_batch_launch(e->tc4b, st);
+    if (err != cudaSuccess) return set_error(SBQA_ERR_CUDA, std::string("engine dense batch: ") + cudaGetErrorString(err));
+    ++e->kernels_launched;
+    ++e->dense_batched_launches;
+    e->dense_batched_chunks += tc4_batch_size(e->tc4b);
+    tc4_batch_clear(e->tc4b);
+    return SBQA_OK;
+  };
+  int rc;
+  // test hook: as in dense_batches
+  const char *hold_hook = std::getenv("SBQA_TEST_ENGINE_HOLD_DENSE");
+  const int hold_id = hold_hook ? std::atoi(hold_hook) : -1;
+  for (int id : ids) {
+    Request &r = e->reqs[id];
+    const sbqa_problem *p = r.prob;
+    const StateView sv = r.state_view();
+    if (!tc4_batch_fits(e->tc4b, sv, p->Kp) && (rc = flush()) != SBQA_OK) return rc;
+    const int steps_now = std::min(e->chunk, r.S - r.n0);
+    const cudaError_t err = tc4_batch_add(e->tc4b, r.tc4_plan, sv, p->Kp, r.err, p->d_h.p, r.tables, r.n0,
+                                          r.n0 + steps_now, id == hold_id ? r.n0 : -1);
     if (err != cudaSuccess) return set_error(SBQA_ERR_CUDA, std::string("engine dense batch: ") + cudaGetErrorString(err));
   }
   return flush();
@@ -523,11 +602,23 @@ int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done, int32_t *don
       e->side_done.assign(e->max_slots, nullptr);
     }
   }
-  std::vector<int> batch_ids;
+  std::vector<int> batch_ids, batch_f4_ids;
   for (int id : dense_active) {
     Request &r = e->reqs[id];
     const int steps_now = std::min(e->chunk, r.S - r.n0);
     const sbqa_problem *p = r.prob;
+    if (r.f4) {  // the e2m1 solver: with the other small ones in one launch, or alone
+      const int f4_tiles = (p->Kp / 128) * (r.Cp / 128);
+      if (e->dense_batching && f4_tiles < kPersistMinTiles) {
+        batch_f4_ids.push_back(id);
+        continue;
+      }
+      const cudaError_t err = launch_solve_dense_tc_f4(r.tc4_plan, r.state_view(), p->Kp, r.err, p->d_h.p, r.tables,
+                                                       r.n0, r.n0 + steps_now, r.tc_flags, st);
+      if (err != cudaSuccess) return set_error(SBQA_ERR_CUDA, std::string("engine dense chunk: ") + cudaGetErrorString(err));
+      ++e->kernels_launched;
+      continue;
+    }
     // a tensor-core request whose tiles fill a good part of the device runs its chunk on the
     // persistent solver (one launch); cooperative launches all go to `st`, one after another,
     // so no two of them ever wait for each other's blocks
@@ -567,6 +658,7 @@ int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done, int32_t *don
     r.on_side = true;
   }
   if (!batch_ids.empty() && (rc = dense_batches(e, batch_ids, st)) != SBQA_OK) return rc;
+  if (!batch_f4_ids.empty() && (rc = dense_batches_f4(e, batch_f4_ids, st)) != SBQA_OK) return rc;
   if (n_items) {
     if (!e->batched_t0) {
       ENG_CUDA(cudaEventCreate(&e->batched_t0));
@@ -639,6 +731,10 @@ int sbqa_engine_step(sbqa_engine *e, void *stream, int32_t *n_done, int32_t *don
       tc_plan_free(r.tc_plan);
       r.tc_plan = nullptr;
     }
+    if (r.tc4_plan) {
+      tc4_plan_free(r.tc4_plan);
+      r.tc4_plan = nullptr;
+    }
     e->slot_req[r.slot] = -1;
     e->arena.release(r.off, r.bytes);
     r.state = err ? FAILED : DONE;
@@ -681,6 +777,7 @@ int sbqa_engine_stats(const sbqa_engine *e, sbqa_engine_stats_t *s) {
   s->batched_ms = e->batched_ms;
   s->dense_batched_launches = e->dense_batched_launches;
   s->dense_batched_chunks = e->dense_batched_chunks;
+  s->dense_e2m1_requests = e->dense_e2m1_requests;
   return SBQA_OK;
 }
 

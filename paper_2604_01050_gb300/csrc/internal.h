@@ -205,6 +205,18 @@ cudaError_t launch_j4_from_j8(const uint8_t *J8, int Kp, uint8_t *J4, cudaStream
 cudaError_t launch_f_to_ft4(const StateView &s, int which, uint8_t *FT4, int Kp, int buffer, cudaStream_t st);
 cudaError_t launch_solve_dense_tc_f4(const void *plan, const StateView &s, int Kp, int *err, const float *h,
                                      const StepTables &t, int n_begin, int n_end, uint32_t *flags, cudaStream_t st);
+// Its batched form for many small problems in one cooperative launch (the
+// engine): the same protocol as TcBatch below; tc_f4_blocks() covers its
+// occupancy and attributes.
+struct Tc4Batch;
+cudaError_t tc4_batch_create(Tc4Batch **out, int cap_reqs, int cap_tiles);
+void tc4_batch_destroy(Tc4Batch *b);
+void tc4_batch_clear(Tc4Batch *b);
+int tc4_batch_size(const Tc4Batch *b);
+bool tc4_batch_fits(const Tc4Batch *b, const StateView &s, int Kp);
+cudaError_t tc4_batch_add(Tc4Batch *b, const void *plan4, const StateView &s, int Kp, int *err, const float *h,
+                          const StepTables &t, int n_begin, int n_end, int hold_step = -1);
+cudaError_t tc4_batch_launch(Tc4Batch *b, cudaStream_t st);
 // Its paired form: the CTAs of row tiles 2p, 2p + 1 share M=256 MMAs (2-CTA
 // clusters, tcgen05 cta_group::2) and each stages half of every f tile, so a
 // step's f tiles are in flight at once; padded N a multiple of 256, blocks

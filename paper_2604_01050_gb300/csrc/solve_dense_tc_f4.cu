@@ -30,6 +30,9 @@
 // a k-block of 256 spins waits for the counters of its two row tiles.
 #include "dense_tc_persistent.cuh"
 
+#include <cstdlib>
+#include <cstring>
+
 namespace sbqa {
 
 constexpr int kOpF4 = 3;
@@ -441,6 +444,40 @@ __global__ void __launch_bounds__(kTpThreads, 1)
   solve_dense_tc_f4<P, GEN, true>(m, s, a, t, blockIdx.x, blockIdx.y);
 }
 
+// ---------------------------------------------------------------- batched form
+// The chunks of several small problems in one cooperative launch (as the
+// batched e4m3 solver, solve_dense_tc_batched.cu): CTAs tile0 .. tile0 + Mt *
+// Ct - 1 run problem r's tiles, row-tile major; the problem's tensor maps are
+// read from the descriptor table in device memory (fenced into the tensormap
+// proxy by the thread that issues the TMA copies), its step counters sit in
+// the batch's flag array at tile0, and its error flag and step range are its
+// own.  All problems of a launch share the run width P and the ring form.
+struct Tb4Req {
+  Tc4Maps m;  // first, so that every map of every entry is 64-byte aligned
+  StateView s;
+  TpArgs a;
+  StepTables t;
+  int tile0;
+};
+
+template <int P, bool GEN>
+__global__ void __launch_bounds__(kTpThreads, 1) k_solve_dense_tc_f4_batched(const Tb4Req *__restrict__ q, int nq) {
+  int r = 0;
+  for (int k = 1; k < nq; ++k)
+    if (int(blockIdx.x) >= q[k].tile0) r = k;
+  const Tb4Req &d = q[r];
+  if (threadIdx.x == 0) {  // the one thread that issues this CTA's TMA loads and stores
+    tc::fence_tmap_acquire_sys(&d.m.A);
+    tc::fence_tmap_acquire_sys(&d.m.B);
+    tc::fence_tmap_acquire_sys(&d.m.Fst);
+  }
+  const StateView s = d.s;
+  const TpArgs a = d.a;
+  const StepTables t = d.t;
+  const int local = int(blockIdx.x) - d.tile0;
+  solve_dense_tc_f4<P, GEN, false>(d.m, s, a, t, local / a.Ct, local % a.Ct);
+}
+
 // e2m1 nibble of an e4m3 byte holding an integer |v| <= 4 (the only values
 // an eligible instance has): 1, 2, 3, 4 -> 0x2, 0x4, 0x5, 0x6, sign in bit 3.
 __device__ __forceinline__ uint32_t e2m1_of_e4m3_int(uint8_t e) {
@@ -492,6 +529,7 @@ __global__ void k_f_to_ft4(StateView s, int which, uint8_t *FT4, int Kh, int b) 
    {(const void *)K<128, true>, (const void *)K<128, true>}}
 static const void *const kF4Fns[8][2] = SBQA_F4_PS(k_solve_dense_tc_f4);
 static const void *const kF4PairFns[8][2] = SBQA_F4_PS(k_solve_dense_tc_f4_pair);
+static const void *const kF4BatchFns[8][2] = SBQA_F4_PS(k_solve_dense_tc_f4_batched);
 #undef SBQA_F4_PS
 
 static int f4_p_index(int P) {
@@ -506,8 +544,8 @@ static int f4_smem(int Kp) { return (tc_f4_row_bytes(Kp) / 128 + kF4Stages) * kF
 
 cudaError_t tc_f4_set_attributes() {
   for (int q = 0; q < 8; ++q)
-    for (int pair = 0; pair < 2; ++pair)
-      for (const void *f : (pair ? kF4PairFns : kF4Fns)[q]) {
+    for (int form = 0; form < 3; ++form)
+      for (const void *f : (form == 2 ? kF4BatchFns : form == 1 ? kF4PairFns : kF4Fns)[q]) {
         cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kF4Smem);
         if (e != cudaSuccess) return e;
       }
@@ -560,11 +598,12 @@ int tc_f4_blocks() {
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (tc_f4_set_attributes() != cudaSuccess) return 0;
   for (int q = 0; q < 8; ++q)
-    for (const void *f : kF4Fns[q]) {
-      int per_sm = 0;
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kTpThreads, kF4Smem) != cudaSuccess) return 0;
-      best = per_sm < best ? per_sm : best;
-    }
+    for (int form = 0; form < 2; ++form)
+      for (const void *f : (form ? kF4BatchFns : kF4Fns)[q]) {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kTpThreads, kF4Smem) != cudaSuccess) return 0;
+        best = per_sm < best ? per_sm : best;
+      }
   return sms * best;
 }
 
@@ -653,6 +692,85 @@ cudaError_t launch_solve_dense_tc_f4_pair(const void *plan, const StateView &s, 
   // row tiles along x (cluster pairs 2p, 2p + 1), column tiles along y
   f4_cluster_config(&cfg, attr, dim3(Kp / kTcBM, Ct), f4_smem(Kp), st, true);
   return cudaLaunchKernelExC(&cfg, kF4PairFns[idx][s.Pr != s.P ? 1 : 0], args);
+}
+
+
+struct Tc4Batch {
+  int cap_reqs = 0, cap_tiles = 0;
+  Tb4Req *host = nullptr;     // staging, 64-byte aligned
+  Tb4Req *dev = nullptr;      // descriptor table
+  uint32_t *flags = nullptr;  // step counters of all tiles of a launch
+  int n = 0, tiles = 0, P = 0, gen = 0;
+};
+
+cudaError_t tc4_batch_create(Tc4Batch **out, int cap_reqs, int cap_tiles) {
+  *out = nullptr;
+  if (cap_reqs < 1 || cap_tiles < 1) return cudaErrorInvalidValue;
+  Tc4Batch *b = new Tc4Batch;
+  b->cap_reqs = cap_reqs;
+  b->cap_tiles = cap_tiles;
+  const size_t hb = (sizeof(Tb4Req) * size_t(cap_reqs) + 63) / 64 * 64;
+  b->host = static_cast<Tb4Req *>(std::aligned_alloc(64, hb));
+  cudaError_t e = b->host ? cudaSuccess : cudaErrorMemoryAllocation;
+  if (e == cudaSuccess) e = cudaMalloc(&b->dev, sizeof(Tb4Req) * size_t(cap_reqs));
+  if (e == cudaSuccess) e = cudaMalloc(&b->flags, sizeof(uint32_t) * size_t(cap_tiles));
+  if (e != cudaSuccess) {
+    tc4_batch_destroy(b);
+    return e;
+  }
+  *out = b;
+  return cudaSuccess;
+}
+
+void tc4_batch_destroy(Tc4Batch *b) {
+  if (!b) return;
+  std::free(b->host);
+  if (b->dev) cudaFree(b->dev);
+  if (b->flags) cudaFree(b->flags);
+  delete b;
+}
+
+void tc4_batch_clear(Tc4Batch *b) { b->n = b->tiles = 0; }
+
+int tc4_batch_size(const Tc4Batch *b) { return b->n; }
+
+bool tc4_batch_fits(const Tc4Batch *b, const StateView &s, int Kp) {
+  const int tiles = (Kp / kTcBM) * (s.Cp / kTcBN);
+  if (b->n >= b->cap_reqs || b->tiles + tiles > b->cap_tiles) return false;
+  return b->n == 0 || (b->P == s.P && b->gen == (s.Pr != s.P ? 1 : 0));
+}
+
+cudaError_t tc4_batch_add(Tc4Batch *b, const void *plan4, const StateView &s, int Kp, int *err, const float *h,
+                          const StepTables &t, int n_begin, int n_end, int hold_step) {
+  const auto *m = static_cast<const Tc4Maps *>(plan4);
+  if (f4_p_index(s.P) < 0 || Kp % kTcBM != 0 || s.Cp % kTcBN != 0 || n_end < n_begin ||
+      m->Kh != tc_f4_row_bytes(Kp) || m->Kh / 128 > kF4MaxKB || !tc4_batch_fits(b, s, Kp))
+    return cudaErrorInvalidValue;
+  Tb4Req &d = b->host[b->n];
+  std::memcpy(&d.m, m, sizeof(Tc4Maps));
+  d.s = s;
+  d.a = TpArgs{Kp, s.Cp / kTcBN, n_begin, n_end, err, h, b->flags + b->tiles, hold_step};
+  d.t = t;
+  d.tile0 = b->tiles;
+  b->P = s.P;
+  b->gen = s.Pr != s.P ? 1 : 0;
+  b->tiles += (Kp / kTcBM) * (s.Cp / kTcBN);
+  ++b->n;
+  return cudaSuccess;
+}
+
+// Copies the descriptors (pageable staging: the call returns once the host
+// buffer has been read), zeroes the flags and launches, all ordered on st.
+cudaError_t tc4_batch_launch(Tc4Batch *b, cudaStream_t st) {
+  if (b->n == 0) return cudaSuccess;
+  cudaError_t e = cudaMemcpyAsync(b->dev, b->host, sizeof(Tb4Req) * size_t(b->n), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b->flags, 0, sizeof(uint32_t) * size_t(b->tiles), st);
+  if (e != cudaSuccess) return e;
+  const Tb4Req *q = b->dev;
+  int nq = b->n;
+  void *args[] = {&q, &nq};
+  return cudaLaunchCooperativeKernel(kF4BatchFns[f4_p_index(b->P)][b->gen], dim3(b->tiles), dim3(kTpThreads), args,
+                                     kF4Smem, st);
 }
 
 }  // namespace sbqa

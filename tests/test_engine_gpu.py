@@ -130,6 +130,7 @@ def test_engine_batches_small_dense_requests(sb):
             else:
                 assert np.allclose(got["energy"], e_o, rtol=1e-12, atol=1e-9), (batching, rid)
         st = sb.engine_stats(eng)
+        assert st["dense_e2m1_requests"] == 11  # the +-1 requests (N=200 stays below the tensor cores)
         if batching:
             # the first chunk alone needs two launches of the 16-tile form (176 tiles), one of each other form
             assert st["dense_batched_launches"] >= 4
@@ -140,6 +141,36 @@ def test_engine_batches_small_dense_requests(sb):
     with pytest.raises(sb.SBQAError) as e:
         sb.engine_set_dense_batching(sb.engine_create(64 << 20, 2, 10), 2)
     assert e.value.status == sb.ERR_INVALID_ARG
+
+
+def test_engine_e2m1_and_e4m3_requests_agree(sb):
+    """Dense requests with integer |J| <= 4 run on the e2m1 solver in the
+    engine -- batched, or alone when their tiles fill most of the device (SK
+    N=2000, R*P=1024: 128 tiles) -- and with kernel_select 12 on the e4m3
+    solvers; both give the same spins and the oracle's energies of them."""
+    specs = [(sk(700, 60), 16, 8), (dense_int(300, 61, jmax=4), 8, 16), (sk(2000, 62), 32, 32),
+             (dense_int(500, 63, jmax=2), 5, 24)]
+    results = {}
+    for sel in (0, 12):
+        eng = sb.engine_create(2 << 30, 8, 30)
+        ids = []
+        for k, ((pbo, spec), P, R) in enumerate(specs):
+            pb = create(sb, spec)
+            sb.set_schedule(pb, *workloads.autotune_params(R, k), precision="exact", eval_every=0,
+                            kernel_select=sel)
+            ids.append(sb.engine_submit(eng, pb, 75, P, R, seed=500 + k))
+        done = []
+        for _ in range(1000):
+            done += sb.engine_step(eng)
+            if len(done) == len(ids):
+                break
+        assert sorted(done) == ids
+        results[sel] = [sb.engine_result(eng, i) for i in ids]
+        assert sb.engine_stats(eng)["dense_e2m1_requests"] == (len(specs) if sel == 0 else 0)
+        eng.destroy()
+    for a, b, ((pbo, _), _, _) in zip(results[0], results[12], specs):
+        assert np.array_equal(a["spins"], b["spins"]) and np.array_equal(a["energy_int"], b["energy_int"])
+        assert np.array_equal(a["energy_int"], oracle.energies(pbo, a["spins"]))
 
 
 def test_engine_admission_waits_for_memory(sb):
