@@ -90,7 +90,7 @@ TRAFFIC_PER_STEP = {
     "sk2000": {"kernel": "k_solve_dense_tc_f4", "bytes_per_step": (19729664 + 266496) // 1000},
     "lattice16/ballistic": {"kernel": "k_solve_csr_persistent_bsb",
                             "bytes_per_step": (1015867000000 + 999486978000) // 10000},
-    "skreal2000": {"kernel": "k_solve_dense_tc_persistent<bf16>", "bytes_per_step": (29526528 + 961280) // 1000},
+    "skreal2000": {"kernel": "k_solve_dense_tc_persistent<bf16>", "bytes_per_step": (29336832 + 934400) // 1000},
 }
 L2_FLUSH_BYTES = 512 << 20
 BATCHED_CSR_UPDATES_PER_STEP = 13896704  # the 48-request serving stream's lattice requests
