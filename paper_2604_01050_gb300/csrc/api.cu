@@ -1214,9 +1214,12 @@ int autotune_tc(sbqa_problem *p) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         SBQA_CUDA(e);
-        // a cluster solver must beat the 128 x 128 one by a margin: at shapes
-        // where they tie (N=2000, R*P=1024) a 64-step trial picks either by noise
-        if (cand == 0 || ms / steps < best_persistent * (best_cand == 0 ? 0.97f : 1.f)) {
+        // a cluster solver (split-K, CTA pairs, e2m1 pairs) must beat the best
+        // single-CTA one by a margin: at shapes where they tie (N=2000, R*P=1024)
+        // a 64-step trial picks either by noise
+        auto cluster = [](int c) { return c == 1 || c == 2 || c == 4; };
+        const float margin = cluster(cand) && !cluster(best_cand) ? 0.97f : 1.f;
+        if (cand == 0 || ms / steps < best_persistent * margin) {
           best_persistent = ms / steps;
           best_cand = cand;
         }
