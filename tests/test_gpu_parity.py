@@ -707,7 +707,8 @@ def test_ballistic_set_state_resume(sb):
     assert np.array_equal(xa, xb) and np.array_equal(ya, yb)
 
 
-@pytest.mark.parametrize("case", ["lattice_pm1", "regular_f32_field", "regular_bf16", "general_p", "ragged"])
+@pytest.mark.parametrize("case", ["lattice_pm1", "regular_f32_field", "regular_bf16", "general_p", "ragged",
+                                  "runs_of_64", "runs_of_128"])
 def test_ballistic_persistent_equals_per_step(sb, case):
     """The persistent CSR solver of the ballistic form (14) runs the same
     fused multiply-adds in the same order as the per-step kernel (6): whole
@@ -723,6 +724,10 @@ def test_ballistic_persistent_equals_per_step(sb, case):
         pb, spec = regular(600, 5, 4); prec = "bf16"
     elif case == "general_p":
         pb, spec = lattice(6, 5); P, R = 6, 24
+    elif case == "runs_of_64":
+        pb, spec = lattice(6, 7); P, R = 64, 4
+    elif case == "runs_of_128":
+        pb, spec = regular(400, 6, 8); P, R, prec = 128, 2, "fp32"
     else:
         pb, spec = lattice(3, 6); P, R = 2, 3
     S = 200
