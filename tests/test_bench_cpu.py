@@ -68,3 +68,36 @@ def test_plain_path_tables_match_the_oracle_schedule():
     assert np.allclose(ka, dt * (1.0 - a) / P, rtol=1e-14, atol=0)
     assert np.allclose(dl, d, rtol=1e-14, atol=0)
     assert np.allclose(kj, dt * jp.T, rtol=1e-12, atol=0)
+
+
+class _Info:
+    def __init__(self, step_kernel):
+        self.step_kernel = step_kernel
+
+
+def test_roofline_bookkeeping():
+    """bench.roofline_of: the dense e2m1 kernels divide 2 N^2 R P flops per step
+    by the larger of the measured e2m1 GEMM figures and also report the
+    fraction of the e4m3 peak; the ballistic kernels count 20 bytes per
+    update, the others 16; a traffic figure is attached only while the kernel
+    it was captured on is the one that runs."""
+    peaks = {"hbm_gbs": 6633.3, "bf16_tflops": 1908.9, "fp8_tflops_burst": 3587.7, "fp4_tflops_burst": 4687.5,
+             "fp4_tflops_sustained": 6949.2}
+    N, P, R, ms = 2000, 32, 32, 0.0075
+    flops = 2.0 * N * N * P * R
+    for k in (15, 16):
+        r = bench.roofline_of({}, "sk2000", _Info(k), N, P, R, ms, peaks)
+        assert r["bound"] == "tensor" and r["peak"] == 6949.2
+        assert math.isclose(r["achieved"], flops / (ms * 1e-3) / 1e12, rel_tol=1e-12)
+        assert math.isclose(r["frac_of_fp8_peak"], r["achieved"] / 3587.7, rel_tol=1e-12)
+        assert (r["traffic"] is not None) == (bench.KERNEL_NAMES[k] == bench.TRAFFIC_PER_STEP["sk2000"]["kernel"])
+    derived = bench.roofline_of({}, "sk2000", _Info(15), N, P, R, ms, {"fp8_tflops_burst": 3587.7})
+    assert math.isclose(derived["peak"], bench.FP4_OVER_FP8 * 3587.7, rel_tol=1e-12)
+    for k, bpu in ((6, 20), (14, 20), (4, 16), (0, 16)):
+        r = bench.roofline_of({}, "lattice16", _Info(k), 4096, 32, 64, 0.0369, peaks)
+        assert r["bound"] == "hbm"
+        assert math.isclose(r["achieved"], bpu * 4096 * 32 * 64 / (0.0369e-3) / 1e9, rel_tol=1e-12)
+    bal = bench.roofline_of({"variant": "ballistic"}, "lattice16", _Info(14), 4096, 32, 64, 0.0369, peaks)
+    assert bal["traffic"] == bench.TRAFFIC_PER_STEP["lattice16/ballistic"]["bytes_per_step"]
+    thr = bench.roofline_of({}, "lattice16", _Info(6), 4096, 32, 64, 0.0369, peaks)
+    assert thr["traffic"] is None  # captured on k_solve_csr_persistent, not the per-step ballistic kernel
